@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the exhaustive all-pairs workload on GB300.
+
+One step = the whole path over one synthetic dictionary of 600,000 words
+(lengths round(N(8, 3)) on [1, 25], 40 codes with Zipf(1.1) usage, index =
+frequency rank): ingest and length bucketing on the device, every one of the
+179,999,700,000 upper-triangle pairs scored by the DPX alignment kernel, the
+on-device per-word top-10 and score histogram, list finalisation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is pairs/s with the words already in
+HBM; `e2e` is the same metric through the C ABI with host buffers (the H2D copy
+of the words and the D2H copy of lists and histogram inside the timed region).
+With N > 1 ranks every rank scores its own replica of the workload (the pairs
+are independent; no collective is on the data path), so `value` counts the
+pairs of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NW pairs/s + GCUPS (% DPX peak); top-10 graph time at ≥0.99 recall vs exact"
+UNIT = "pairs/s"
+SCORING = (1, -1, -1)
+K_NEIGHBOURS = 10
+L2_FLUSH_BYTES = 512 << 20
+
+# DRAM traffic of the alignment kernel from the ncu capture summarised in
+# profiles/ (bytes per launch, averaged over the launches of one step), valid
+# only for the kernel source it was measured on.
+TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("nw_dp.cuh", "nw_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2509_01654_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def workload_config(n, w, info):
+    return {
+        "workload": f"exhaustive all-pairs NW, {n:,} synthetic words (lengths round(N(8,3)) on [1,25], "
+                    f"40 codes Zipf(1.1)), scoring (+1,-1,-1), per-word top-{K_NEIGHBOURS} + score histogram",
+        "n_words": n,
+        "k": K_NEIGHBOURS,
+        "pairs_per_step": int(info["pairs"]),
+        "cells_per_step": int(info["cells"]),
+        "max_len": int(info["max_len"]),
+        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); inputs 7 MB < L2",
+        "parallelism": "replicas (one independent workload per rank)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd.insert(1, f"--id=GPU-{uuid}")
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (bounded sample of the same workload)
+
+def oracle_sample(w, rows_target_s: float, min_rows: int = 8, max_rows: int = 5000):
+    """Times the oracle's top-k on sampled words against the whole dictionary;
+    returns (pairs/s, rows, seconds, threads)."""
+    import oracle
+    from paper_2509_01654_gb300 import synth
+
+    threads = oracle.default_threads()
+    probe = synth.sample_rows(w.n, min_rows, seed=7)
+    t0 = time.perf_counter()
+    oracle.topk_rows(w, probe, K_NEIGHBOURS, SCORING, nthreads=threads)
+    dt = time.perf_counter() - t0
+    rows = int(max(min_rows, min(max_rows, min_rows * rows_target_s / max(dt, 1e-3))))
+    rows -= rows % threads if rows > threads else 0
+    sample = synth.sample_rows(w.n, rows, seed=6)
+    t0 = time.perf_counter()
+    oracle.topk_rows(w, sample, K_NEIGHBOURS, SCORING, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return rows * (w.n - 1) / dt, rows, dt, threads
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from paper_2509_01654_gb300 import synth
+    w = synth.exhaustive_words(args.n)
+    per_step_s = float(os.environ.get("NW_REF_STEP_S", "10"))
+    vals, rows_used, threads = [], 0, 1
+    for s in range(args.warmup + args.steps):
+        v, rows, dt, threads = oracle_sample(w, per_step_s)
+        if s >= args.warmup:
+            vals.append((v, rows, dt))
+    value = statistics.median(v for v, _, _ in vals)
+    rows_used = vals[0][1]
+    ms = 1e3 * statistics.median(dt for _, _, dt in vals)
+    lens = w.lengths
+    cells_per_pair = (lens.sum() ** 2 - (lens ** 2).sum()) / 2 / (w.n * (w.n - 1) / 2)
+    sample = (f"per step: top-{K_NEIGHBOURS} of {rows_used} sampled words against all {w.n:,} words "
+              f"({rows_used * (w.n - 1):,} pairs), full (la+1)x(lb+1) int32 matrix per pair")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"exhaustive all-pairs NW, {w.n:,} synthetic words, scoring (+1,-1,-1), "
+                               f"per-word top-{K_NEIGHBOURS}; each step a bounded sample of rows",
+                   "n_words": w.n, "k": K_NEIGHBOURS},
+        "gcups": value * cells_per_pair / 1e9,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU path
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_01654_gb300 import build as nw_build
+    from paper_2509_01654_gb300 import nw, synth
+
+    nw_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = synth.exhaustive_words(args.n)
+    ctx = nw.Context(local_rank, stream=stream)
+    codes_d = torch.from_numpy(w.codes).to(dev)
+    offs_d = torch.from_numpy(w.offsets.astype(np.int32)).to(dev)
+    probe = ctx.load_dictionary(w.codes, w.offsets, 40, SCORING)
+    info = probe.info()
+    probe.free()
+    n, k, nbins = w.n, K_NEIGHBOURS, info["nbins"]
+    idx_d = torch.empty((n, k), dtype=torch.int32, device=dev)
+    score_d = torch.empty((n, k), dtype=torch.int16, device=dev)
+    hist_d = torch.empty(nbins, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx.set_profiling(True)
+
+    def step_device():
+        d = ctx.load_dictionary(codes_d, offs_d, 40, SCORING)
+        d.all_pairs_topk(k, nbr_idx=idx_d, nbr_score=score_d, hist=hist_d)
+        prof = ctx.last_profile()
+        d.free()
+        return prof
+
+    # pinned host buffers for the end-to-end leg
+    codes_h = torch.from_numpy(w.codes).pin_memory()
+    offs_h = torch.from_numpy(w.offsets.view(np.int32)).pin_memory()
+    idx_h = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    score_h = torch.empty((n, k), dtype=torch.int16).pin_memory()
+    hist_h = torch.empty(nbins, dtype=torch.int64).pin_memory()
+    codes_np, offs_np = codes_h.numpy(), offs_h.numpy().view(np.uint32)
+    idx_np, score_np, hist_np = idx_h.numpy().view(np.uint32), score_h.numpy(), hist_h.numpy()
+
+    def step_e2e():
+        d = ctx.load_dictionary(codes_np, offs_np, 40, SCORING)
+        d.all_pairs_topk(k, nbr_idx=idx_np, nbr_score=score_np, hist=hist_np)
+        d.free()
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    rates = ctx.measure_int_rates(300.0)
+
+    sampler = ClockSampler(str(torch.cuda.get_device_properties(dev).uuid)) if rank == 0 else None
+    times, dp_ms, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.fill_(len(times))
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prof = step_device()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        times.append(e0.elapsed_time(e1))
+        dp_ms.append(prof["dp_ms"])
+        launches += 4 + prof["launches"]  # 4 ingest kernels + alignment launches + finalisation
+    clocks = sampler.stop() if sampler else None
+
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(len(e2e_times))
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_times.append(e0.elapsed_time(e1))
+    # the host leg wrote real results: check them against the device leg
+    assert np.array_equal(idx_np, idx_d.cpu().numpy().view(np.uint32))
+    assert int(hist_np.sum()) == info["pairs"]
+
+    total_ms = sum(times)
+    total_e2e = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([total_ms, total_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, total_e2e = t.tolist()
+    if rank != 0:
+        return
+    pairs, cells = info["pairs"], info["cells"]
+    value = world * pairs * args.steps / (total_ms / 1e3)
+    e2e_value = world * pairs * len(e2e_times) / (total_e2e / 1e3)
+
+    # roofline of the alignment kernel: algorithmic cells over its launches' event time
+    dp_avg_ms = statistics.mean(dp_ms)
+    achieved = cells / (dp_avg_ms / 1e3) / 1e9
+    c_min = 3.0  # packed instructions per two cells in the fewest-instruction cell update
+    peak = 2.0 * rates["viaddmax_s16x2"] / c_min / 1e9
+    sha = kernel_sha()
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == sha else None
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, rows, dt, threads = oracle_sample(w, float(os.environ.get("NW_CPU_BASELINE_S", "15")))
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"top-{k} of {rows} sampled words against all {n:,} words ({rows * (n - 1):,} pairs) "
+                         f"in {dt:.1f} s; full (la+1)x(lb+1) int32 matrix per pair"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+        "config": workload_config(n, w, info),
+        "gcups": world * cells * args.steps / (total_ms / 1e3) / 1e9,
+        "dp_kernel_ms_per_step": dp_avg_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": f"2 cells x measured __viaddmax_s16x2 rate ({rates['viaddmax_s16x2']:.4g}/s, "
+                                   f"{rates['sm_count']} SMs at {rates['sm_clock_mhz']:.0f} MHz) / {c_min:g} "
+                                   f"packed instructions per cell pair; cell-mix microbenchmark "
+                                   f"{2 * rates['nw_cell_mix'] / 1e9:.0f} GCUPS",
+                     "rates_per_s": {key: rates[key] for key in ("viaddmax_s16x2", "vimax3_s16x2",
+                                                                  "vimax_s16x2_relu", "iadd3", "lop3")}},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(codes_np.nbytes + offs_np.nbytes),
+                "d2h_bytes_per_step": int(idx_np.nbytes + score_np.nbytes + hist_np.nbytes),
+                "ms_per_step": total_e2e / len(e2e_times)},
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=600_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

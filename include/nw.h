@@ -1,0 +1,237 @@
+/*
+ * nw.h -- C ABI of libnw: all-pairs Needleman-Wunsch scoring of phoneme-coded
+ * words on one GB300 GPU (sm_103a).
+ *
+ * Method: arxiv 2509.01654, "Parallel Needleman-Wunsch on CUDA to measure word
+ * similarity based on phonetic transcriptions".  A word is a sequence of
+ * integer phoneme codes (Section 3, the encoding table); two words are scored
+ * by the Needleman-Wunsch recurrence of Algorithm 1 with a similarity of
+ * `match` for equal codes and `mismatch` otherwise and a gap value p added per
+ * gap column (Section 2; Section 4 fixes match 1, mismatch -1, p = -1).  Edges
+ * are undirected and self pairs are excluded, so only the upper triangle of
+ * the word-by-word matrix is scored (Section 4.1).
+ *
+ * Conventions for every call:
+ *  - Return value: NW_OK or a negative nw_status; a message for the last
+ *    failure is available from nw_last_error().  The library never aborts,
+ *    traps or exits.  On failure no output buffer has been partially written
+ *    unless the message says otherwise.
+ *  - Ownership: input buffers are borrowed for the duration of the call and
+ *    copied; the library keeps no caller pointer.  Output buffers are
+ *    allocated by the caller.
+ *  - Host or device buffers: buffers are host memory unless the call's
+ *    `flags` contain NW_DEVICE_PTRS, in which case every buffer argument of
+ *    that call is a device pointer on the context's device.
+ *  - Ordering: all GPU work is issued on the context's stream.  Calls return
+ *    after that work has finished unless NW_ASYNC is given together with
+ *    NW_DEVICE_PTRS, in which case outputs are valid once the stream reaches
+ *    the point where the call returned.
+ *  - Indices in results are the caller's original word indices.  Missing
+ *    neighbours (fewer than k candidates) are reported as index UINT32_MAX
+ *    and score INT16_MIN.
+ *  - Thread safety: a context and its dictionaries are used by one host
+ *    thread at a time; distinct contexts are independent.
+ */
+#ifndef NW_H
+#define NW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Longest word accepted by the kernels (the paper's words have at most ~25
+ * symbols, Section 4.1; queries and batched dictionaries go up to 40). */
+#define NW_MAX_WORD_LEN 40
+/* Largest neighbour-list length k. */
+#define NW_MAX_K 128
+
+typedef enum {
+    NW_OK = 0,
+    NW_EINVAL = -1,   /* invalid argument: null pointer, n < 2, k out of range, code >= alphabet, word too long, unsupported scoring */
+    NW_ENOMEM = -2,   /* device allocation failed or the context's memory budget would be exceeded */
+    NW_ERANGE = -3,   /* a score bound does not fit the output type, or nbins is too small */
+    NW_ECUDA = -4,    /* a CUDA runtime error (message from the runtime in nw_last_error) */
+    NW_ETIMEOUT = -5, /* a bounded device-side retry loop gave up; results are not valid */
+    NW_EBUSY = -6     /* the context is in use by another call */
+} nw_status;
+
+/* call flags */
+#define NW_DEVICE_PTRS 0x1u /* buffer arguments are device pointers */
+#define NW_ASYNC 0x2u       /* with NW_DEVICE_PTRS: do not wait for the stream before returning */
+
+/* Similarity and gap values (Algorithm 1, Section 2): similarity(a, b) is
+ * `match` when a == b and `mismatch` otherwise; `gap` (the paper's p, normally
+ * negative) is added once per gap column.  The kernels require
+ * mismatch <= match, 2*gap <= match and |match|, |mismatch|, |gap| <= 1024;
+ * other values give NW_EINVAL. */
+typedef struct {
+    int32_t match;
+    int32_t mismatch;
+    int32_t gap;
+} nw_scoring;
+
+typedef struct nw_ctx nw_ctx;
+typedef struct nw_dict nw_dict;
+
+/* Facts about a loaded dictionary. */
+typedef struct {
+    uint32_t n;          /* words */
+    uint32_t alphabet;   /* codes are < alphabet */
+    uint32_t min_len, max_len;
+    int32_t score_lo;    /* lowest score any pair of this dictionary can reach */
+    int32_t score_hi;    /* highest score any pair can reach */
+    uint32_t nbins;      /* score_hi - score_lo + 1: histogram bins nw_all_pairs_topk needs */
+    uint32_t pad_;
+    uint64_t pairs;      /* n(n-1)/2, the edge count of Section 4.2 */
+    uint64_t cells;      /* sum over pairs of len(a)*len(b): DP cells of all pairs */
+    uint64_t device_bytes; /* device memory held by the dictionary */
+} nw_dict_info;
+
+/* Timings of the last call, filled when profiling is enabled.  Durations come
+ * from CUDA events recorded on the context's stream around each launch. */
+typedef struct {
+    double dp_ms;          /* summed duration of the alignment-kernel launches */
+    double finalize_ms;    /* summed duration of the list-finalising launches */
+    double total_ms;       /* first to last event of the call */
+    uint32_t dp_launches;  /* alignment-kernel launches of the call */
+    uint32_t launches;     /* all kernel launches of the call */
+    uint64_t pairs;        /* pairs scored by the call */
+    uint64_t cells;        /* DP cells of those pairs */
+    uint64_t list_inserts; /* candidate neighbours that reached a global list */
+} nw_profile;
+
+/* Creates a context on CUDA device `device`.  `mem_budget_bytes` caps the
+ * device memory the context may hold (0 = no cap); `cuda_stream` is a
+ * cudaStream_t to issue work on, or NULL for a stream the context owns.  The
+ * stream is borrowed and must outlive the context. */
+nw_status nw_create(nw_ctx **out, int device, size_t mem_budget_bytes, void *cuda_stream);
+
+/* Frees the context and every dictionary still loaded in it. */
+void nw_destroy(nw_ctx *ctx);
+
+/* Message for the last failed call on `ctx` ("" if none).  Valid until the
+ * next call on the context.  With ctx == NULL: the message of the last failed
+ * nw_create on this thread. */
+const char *nw_last_error(const nw_ctx *ctx);
+
+/* Turns per-call event timing on or off (off by default). */
+nw_status nw_set_profiling(nw_ctx *ctx, int enable);
+
+/* Copies the profile of the last call made with profiling on. */
+nw_status nw_last_profile(const nw_ctx *ctx, nw_profile *out);
+
+/* Loads a dictionary of n words given in CSR form: word i is
+ * codes[offsets[i] .. offsets[i+1]), offsets has n+1 entries with
+ * offsets[0] == 0, every code is < alphabet (alphabet <= 256) and every word
+ * has at most NW_MAX_WORD_LEN codes (empty words are allowed).  The words are
+ * the nodes of the paper's graph (Section 3 encoding; Section 5 caps the
+ * frequency-sorted list at n).  `flags` may hold NW_DEVICE_PTRS.  The
+ * scoring is fixed for the dictionary's lifetime.  On the device the words
+ * are sorted stably by length into buckets and encoded for the kernels. */
+nw_status nw_load_dictionary(nw_ctx *ctx, const uint8_t *codes, const uint32_t *offsets, uint32_t n,
+                             uint32_t alphabet, const nw_scoring *scoring, uint32_t flags,
+                             nw_dict **out);
+
+/* Fills `out` with facts about the dictionary. */
+nw_status nw_dict_info_get(const nw_dict *dict, nw_dict_info *out);
+
+/* Frees a dictionary (NULL is ignored). */
+void nw_dict_free(nw_dict *dict);
+
+/* Scores every pair i < j of the dictionary and writes the int8 score of
+ * (i, j) at out[S(i-1) + (j - i - 1)], S(i-1) = i(2n - i - 1)/2: the paper's
+ * row-major traversal of the upper triangle, (0,1), (0,2), ..., (n-2, n-1),
+ * one signed byte per edge (Section 4.1; offsets as in Section 4.2).  `out`
+ * holds n(n-1)/2 bytes.  NW_ERANGE if a score of this dictionary can fall
+ * outside [-128, 127]. */
+nw_status nw_all_pairs_matrix(nw_dict *dict, int8_t *out, uint32_t flags);
+
+/* Scores every pair i < j once and reduces on the device to, for every word,
+ * its k best neighbours over all other words (higher score first, lower
+ * original index first on equal scores) -- the per-word ego-network lists of
+ * Section 5 -- plus the histogram of all n(n-1)/2 scores (Section 5's
+ * edge-weight histogram).
+ *   nbr_idx[i*k + r], nbr_score[i*k + r]: rank r of word i (n*k entries each).
+ *   hist: NULL, or nbins int64 counts; hist[b] counts pairs scoring
+ *         *hist_lo + b.  nbins must be >= nw_dict_info.nbins (else NW_ERANGE).
+ *   hist_lo: receives the score of bin 0 (may be NULL when hist is NULL).
+ * k in [1, NW_MAX_K].  NW_EINVAL if n < 2. */
+nw_status nw_all_pairs_topk(nw_dict *dict, uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score,
+                            int64_t *hist, int32_t *hist_lo, uint32_t nbins, uint32_t flags);
+
+/* The same reduction over shard `shard` of `nshards` disjoint parts of the
+ * pair set (every unordered pair belongs to exactly one shard).  The lists
+ * hold each word's k best neighbours among the pairs of that shard and the
+ * histogram counts that shard's pairs; nw_topk_merge combines the lists of
+ * all shards into the full result and histograms add. */
+nw_status nw_all_pairs_topk_shard(nw_dict *dict, uint32_t shard, uint32_t nshards, uint32_t k,
+                                  uint32_t *nbr_idx, int16_t *nbr_score, int64_t *hist,
+                                  int32_t *hist_lo, uint32_t nbins, uint32_t flags);
+
+/* Host-only: merges `nparts` partial neighbour lists of n words (each n*k,
+ * ranked as above, missing entries UINT32_MAX / INT16_MIN) into the k best of
+ * their union per word, in the same order.  Entries with the same index in
+ * several parts must carry the same score; they are kept once.  Host
+ * pointers; no GPU is used. */
+nw_status nw_topk_merge(uint32_t n, uint32_t k, uint32_t nparts, const uint32_t *const *idx_parts,
+                        const int16_t *const *score_parts, uint32_t *idx_out, int16_t *score_out);
+
+/* Scores m explicit pairs (i[p], j[p]) of dictionary words (original indices,
+ * i == j allowed) into out[p] (int16).  Each score is Algorithm 1's
+ * bottom-right cell for the two words. */
+nw_status nw_score_pairs(nw_dict *dict, const uint32_t *i, const uint32_t *j, size_t m, int16_t *out,
+                         uint32_t flags);
+
+/* Scores nq query words (CSR as in nw_load_dictionary, codes < the
+ * dictionary's alphabet) against every dictionary word and returns each
+ * query's k best dictionary neighbours (nbr_idx/nbr_score: nq*k entries,
+ * ranked as in nw_all_pairs_topk; a query is not a dictionary word, so no
+ * dictionary word is excluded).  This is the "find phonetically similar
+ * words" use of Section 6.  flags: NW_DEVICE_PTRS, NW_ASYNC. */
+nw_status nw_query(nw_dict *dict, const uint8_t *qcodes, const uint32_t *qoffsets, uint32_t nq,
+                   uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score, uint32_t flags);
+
+/* ---- measurement and testing helpers (no counterpart in the paper) ---- */
+
+/* Issue rates of the integer instructions the alignment kernel is built from,
+ * measured on the context's device by a throughput microbenchmark over all
+ * SMs: dependent chains with 8-way instruction-level parallelism, enough warps
+ * to fill every SM, repeated for `ms_target` milliseconds of device time.
+ * Rates are per second for the whole GPU, counting one 32-bit instruction per
+ * thread as one operation (a packed 16x2 instruction is one operation). */
+typedef struct {
+    double viaddmax_s16x2;  /* __viaddmax_s16x2 */
+    double vimax3_s16x2;    /* __vimax3_s16x2 */
+    double vimax_s16x2_relu;/* __vimax_s16x2_relu */
+    double iadd3;           /* three-input 32-bit add */
+    double lop3;            /* three-input 32-bit logic op */
+    double nw_cell_mix;     /* the alignment kernel's per-cell instruction mix, in packed cells/s */
+    double sm_clock_mhz;    /* SM clock seen by the benchmark (clock64 cycles / event time) */
+    uint32_t sm_count;
+    uint32_t pad_;
+} nw_int_rates;
+
+nw_status nw_measure_int_rates(nw_ctx *ctx, double ms_target, nw_int_rates *out);
+
+/* Host-only: the pairs the all-pairs kernels of a dictionary with these word
+ * lengths would score for shard `shard` of `nshards`, as original-index pairs
+ * (a[p], b[p]), in task order.  Writes at most `cap` pairs and sets *count to
+ * the total.  Runs the same planner and task-to-pair mapping as the kernels,
+ * on the CPU, so tests can check that every unordered pair is covered exactly
+ * once. */
+nw_status nw_debug_enumerate_pairs(const uint32_t *lengths, uint32_t n, uint32_t shard,
+                                   uint32_t nshards, uint32_t *a, uint32_t *b, uint64_t cap,
+                                   uint64_t *count);
+
+/* Test hook: the `countdown`-th device allocation of the context from now on
+ * fails as if the device were out of memory (0 disables).  Host-side only. */
+nw_status nw_debug_fail_alloc(nw_ctx *ctx, uint32_t countdown);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NW_H */

@@ -1,0 +1,262 @@
+// nw_dp.cuh -- the all-pairs alignment kernel (sm_103a), templated on the
+// length LB of the longer word of every pair it scores.
+//
+// Recurrence.  Algorithm 1 of the paper fills H[i][j] = max(H[i-1][j-1] +
+// sim(A[i-1], B[j-1]), H[i-1][j] + p, H[i][j-1] + p) from H[i][0] = p*i and
+// H[0][j] = p*j and returns H[la][lb].  With G[i][j] = H[i][j] - p*(i + j)
+// the same recurrence reads
+//     G[i][j] = max(G[i-1][j-1] + s'(a, b), G[i-1][j], G[i][j-1]),
+//     G[i][0] = G[0][j] = 0,   s'(a, b) = sim(a, b) - 2p,
+// so the gap terms vanish, every G is >= 0 and the score is
+// G[la][lb] + p*(la + lb).  This is an exact rewrite (same maximising paths).
+//
+// Packing.  A lane holds two B words of length LB (lo and hi 16-bit halves
+// of each register) and their DP row G[i][1..LB] in LB registers; the warp
+// streams one A word at a time (the same symbol in both halves), so each
+// packed instruction advances two alignments by one cell.  Per packed cell:
+//     xt = a2 ^ b2[j]                  per half: -1 - (e(a) ^ e(b))
+//     f  = viaddmax(xt, s'_m + 1, s'_x) per half: s'_m if a == b else s'_x
+//     m  = vimax_relu(up, left)         max(G[i-1][j], G[i][j-1])   (G >= 0)
+//     h  = viaddmax(diag, f, m)         max(G[i-1][j-1] + s', m)
+// The codes are stored shifted (e(c) = c << shift, 2^shift >= match -
+// mismatch), so for different codes e(a) ^ e(b) >= match - mismatch and
+// s'_m - (e(a) ^ e(b)) <= s'_x: the max with s'_x then selects the mismatch
+// value.  One LOP3 and three DPX instructions per two cells.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <limits.h>
+
+#include "nw_internal.cuh"
+
+namespace nw {
+
+template <int LB>
+struct BRow {
+  uint32_t v[LB > 0 ? LB : 1];
+};
+
+// DP over the la rows of one A word against the lane's two B words; returns
+// the packed G[la][LB] (0 when la == 0 or LB == 0).
+template <int LB>
+__device__ __forceinline__ uint32_t dp_word(const uint32_t* __restrict__ arow, int la,
+                                            const BRow<LB>& b, uint32_t C1, uint32_t C2) {
+  if constexpr (LB == 0) {
+    return 0u;
+  } else {
+    uint32_t G[LB];
+#pragma unroll
+    for (int j = 0; j < LB; ++j) G[j] = 0u;
+#pragma unroll 1
+    for (int i = 0; i < la; ++i) {
+      const uint32_t a2 = __ldg(arow + i);
+      uint32_t diag = 0u, left = 0u;
+#pragma unroll
+      for (int j = 0; j < LB; ++j) {
+        const uint32_t xt = a2 ^ b.v[j];
+        const uint32_t f = __viaddmax_s16x2(xt, C1, C2);
+        const uint32_t up = G[j];
+        const uint32_t m = __vimax_s16x2_relu(up, left);
+        const uint32_t h = __viaddmax_s16x2(diag, f, m);
+        diag = up;
+        G[j] = h;
+        left = h;
+      }
+    }
+    return G[LB - 1];
+  }
+}
+
+template <int LB>
+__device__ __forceinline__ void load_brow(const uint4* __restrict__ rec, BRow<LB>& b) {
+  if constexpr (LB > 0) {
+    constexpr int Q = ceil4(LB) / 4;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint4 v = __ldg(rec + q);
+      if (4 * q + 0 < LB) b.v[4 * q + 0] = v.x;
+      if (4 * q + 1 < LB) b.v[4 * q + 1] = v.y;
+      if (4 * q + 2 < LB) b.v[4 * q + 2] = v.z;
+      if (4 * q + 3 < LB) b.v[4 * q + 3] = v.w;
+    }
+  }
+}
+
+__device__ __forceinline__ int score_threshold(uint32_t thr_key, uint32_t ib, int32_t key_lo) {
+  return thr_key == 0u ? INT_MIN : (int)(thr_key >> ib) + key_lo;
+}
+
+// Offers `key` to a word's list of k slots.  The slots always hold the k
+// largest keys offered so far (0 = empty); keys of one list are distinct.
+// The smallest slot is replaced by compare-and-swap; a failed swap means
+// another thread changed that slot, so the scan repeats (bounded).  Slots only
+// grow, so a stale read can only make the swap fail, never corrupt the set.
+// Returns a lower bound of the list's current smallest key and raises it in
+// *thr.
+__device__ __forceinline__ uint32_t list_offer(uint32_t* row, uint32_t* thr, uint32_t k,
+                                               uint32_t key, uint32_t* err, uint32_t& inserts) {
+  for (int it = 0; it < kInsertMaxIters; ++it) {
+    uint32_t m1 = 0xffffffffu, m2 = 0xffffffffu, mi = 0;
+    for (uint32_t s = 0; s < k; ++s) {
+      const uint32_t v = __ldcg(row + s);
+      if (v < m1) { m2 = m1; m1 = v; mi = s; }
+      else if (v < m2) { m2 = v; }
+    }
+    if (key <= m1) {
+      atomicMax(thr, m1);
+      return m1;
+    }
+    if (atomicCAS(row + mi, m1, key) == m1) {
+      const uint32_t nm = m2 < key ? m2 : key;
+      atomicMax(thr, nm);
+      ++inserts;
+      return nm;
+    }
+  }
+  atomicOr(err, kErrRetry);
+  return 0xffffffffu;
+}
+
+__device__ __forceinline__ uint64_t upper_offset(uint64_t i, uint64_t j, uint64_t n) {
+  // pair (i, j), i < j, in the row-major upper triangle: S(i-1) + (j - i - 1)
+  return i * (2 * n - i - 1) / 2 + (j - i - 1);
+}
+
+__device__ __forceinline__ void hist_add(const DpParams& P, uint32_t* wh, int s) {
+  const uint32_t bi = (uint32_t)(s - P.hist_lo);
+  if (bi >= P.nbins) { atomicOr(P.err, kErrHistRange); return; }
+  if (P.hist_mode == kHistSmem) atomicAdd(wh + bi, 1u);
+  else atomicAdd(P.hist + bi, 1ull);
+}
+
+__device__ __forceinline__ void hist_flush(const DpParams& P, uint32_t* wh, int lane) {
+  __syncwarp();
+  for (uint32_t b = lane; b < P.nbins; b += 32) {
+    const uint32_t c = wh[b];
+    if (c) { atomicAdd(P.hist + b, (unsigned long long)c); wh[b] = 0u; }
+  }
+  __syncwarp();
+}
+
+template <int LB>
+__global__ void __launch_bounds__(kBlock) nw_dp_kernel(const DpParams P) {
+  extern __shared__ uint32_t s_hist[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  uint32_t* wh = s_hist + (size_t)wib * P.nbins;
+  const bool use_smem_hist = P.hist_mode == kHistSmem;
+  if (use_smem_hist) {
+    for (uint32_t b = lane; b < P.nbins; b += 32) wh[b] = 0u;
+    __syncwarp();
+  }
+  uint64_t wpairs = 0;
+  uint32_t inserts = 0;
+  const bool listsA = P.A.slots != nullptr;
+  const bool listsB = P.B.slots != nullptr;
+
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(P.counter, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0) + P.task_lo;
+    if (t >= P.task_hi) break;
+
+    const Seg S = P.segs[find_seg(P.segs, P.nsegs, t)];
+    const TaskGeom g = task_geom(S, t, P.TA);
+    const uint32_t blo = g.b0 + 2u * lane;
+    const uint32_t bhi = blo + 1u;
+    const bool vlo = blo < g.bend;
+    const bool vhi = bhi < g.bend;
+    const int la = S.la;
+    const int pconst = P.gap * (la + LB);
+
+    BRow<LB> brow;
+    if constexpr (LB > 0) {
+#pragma unroll
+      for (int j = 0; j < LB; ++j) brow.v[j] = 0xffffffffu;
+      if (vlo) load_brow<LB>(P.b_rec + S.brec_base + (size_t)(g.cb * (kWarpB / 2) + lane) * (ceil4(LB) / 4), brow);
+    }
+    const uint32_t ob_lo = vlo ? __ldg(P.B.perm + blo) : 0u;
+    const uint32_t ob_hi = vhi ? __ldg(P.B.perm + bhi) : 0u;
+    uint32_t thrB_lo = 0u, thrB_hi = 0u;
+    int sthrB_lo = INT_MAX, sthrB_hi = INT_MAX;
+    if (listsB) {
+      if (vlo) { thrB_lo = __ldcg(P.B.thr + blo); sthrB_lo = score_threshold(thrB_lo, P.ib, P.key_lo); }
+      if (vhi) { thrB_hi = __ldcg(P.B.thr + bhi); sthrB_hi = score_threshold(thrB_hi, P.ib, P.key_lo); }
+    }
+
+    for (uint32_t a = g.a0; a < g.a1; ++a) {
+      const uint32_t oa = __ldg(P.A.perm + a);
+      uint32_t thrA = 0u;
+      if (listsA) thrA = __ldcg(P.A.thr + a);
+      const uint32_t* arow = P.a_enc + S.aenc_base + (size_t)(a - S.a_beg) * (uint32_t)la;
+      const uint32_t res = dp_word<LB>(arow, la, brow, P.C1, P.C2);
+      const int s_lo = (int)(int16_t)(res & 0xffffu) + pconst;
+      const int s_hi = (int)(int16_t)(res >> 16) + pconst;
+      const bool ok_lo = pair_valid(g, a, blo);
+      const bool ok_hi = pair_valid(g, a, bhi);
+
+      if (P.mode == kModeMatrix) {
+        if (ok_lo) {
+          const uint64_t i = oa < ob_lo ? oa : ob_lo, j = oa < ob_lo ? ob_lo : oa;
+          P.mat[upper_offset(i, j, P.n)] = (int8_t)s_lo;
+        }
+        if (ok_hi) {
+          const uint64_t i = oa < ob_hi ? oa : ob_hi, j = oa < ob_hi ? ob_hi : oa;
+          P.mat[upper_offset(i, j, P.n)] = (int8_t)s_hi;
+        }
+        continue;
+      }
+
+      if (P.hist_mode != kHistNone) {
+        if (ok_lo) hist_add(P, wh, s_lo);
+        if (ok_hi) hist_add(P, wh, s_hi);
+        if (use_smem_hist) {
+          wpairs += 64;
+          if (wpairs >= (1ull << 30)) { hist_flush(P, wh, lane); wpairs = 0; }
+        }
+      }
+      // B-side lists: the lane's own words take the A word as a neighbour.
+      if (listsB) {
+        if (ok_lo && s_lo >= sthrB_lo) {
+          const uint32_t key = ((uint32_t)(s_lo - P.key_lo) << P.ib) | (P.imask - oa);
+          if (key > thrB_lo) {
+            const uint32_t nm = list_offer(P.B.slots + (size_t)blo * P.k, P.B.thr + blo, P.k, key, P.err, inserts);
+            if (nm > thrB_lo) { thrB_lo = nm; sthrB_lo = score_threshold(nm, P.ib, P.key_lo); }
+          }
+        }
+        if (ok_hi && s_hi >= sthrB_hi) {
+          const uint32_t key = ((uint32_t)(s_hi - P.key_lo) << P.ib) | (P.imask - oa);
+          if (key > thrB_hi) {
+            const uint32_t nm = list_offer(P.B.slots + (size_t)bhi * P.k, P.B.thr + bhi, P.k, key, P.err, inserts);
+            if (nm > thrB_hi) { thrB_hi = nm; sthrB_hi = score_threshold(nm, P.ib, P.key_lo); }
+          }
+        }
+      }
+      // A-side list: the warp's A word takes the lanes' words as neighbours.
+      if (listsA) {
+        const int sthrA = score_threshold(thrA, P.ib, P.key_lo);
+        const bool c_lo = ok_lo && s_lo >= sthrA;
+        const bool c_hi = ok_hi && s_hi >= sthrA;
+        if (__any_sync(0xffffffffu, c_lo || c_hi)) {
+          uint32_t* row = P.A.slots + (size_t)a * P.k;
+          if (c_lo) {
+            const uint32_t key = ((uint32_t)(s_lo - P.key_lo) << P.ib) | (P.imask - ob_lo);
+            if (key > thrA) list_offer(row, P.A.thr + a, P.k, key, P.err, inserts);
+          }
+          if (c_hi) {
+            const uint32_t key = ((uint32_t)(s_hi - P.key_lo) << P.ib) | (P.imask - ob_hi);
+            if (key > thrA) list_offer(row, P.A.thr + a, P.k, key, P.err, inserts);
+          }
+        }
+      }
+    }
+  }
+
+  if (use_smem_hist) hist_flush(P, wh, lane);
+  if (P.stats) {
+    for (int o = 16; o > 0; o >>= 1) inserts += __shfl_xor_sync(0xffffffffu, inserts, o);
+    if (lane == 0 && inserts) atomicAdd(P.stats, (unsigned long long)inserts);
+  }
+}
+
+}  // namespace nw

@@ -1,0 +1,147 @@
+// nw_internal.cuh -- data layout, task geometry and kernel parameters of libnw.
+//
+// Words of a set (a dictionary or a batch of queries) are sorted stably by
+// length into buckets (bucket L holds the words of length L in original-index
+// order).  A word is addressed by its sorted position.  Every unordered pair
+// of words is scored once: by the alignment kernel instantiated for LB = the
+// longer length, with the longer word held by a lane ("B side") and the
+// shorter word streamed to the whole warp ("A side").
+//
+// Encoded symbols (both built at load time for the scoring of the set):
+//   e(c)  = c << shift, with 2^shift >= match - mismatch, so two different
+//           codes differ by at least match - mismatch after XOR.
+//   a_enc = e(c) replicated into both 16-bit halves, one uint32 per symbol,
+//           each word's symbols contiguous.
+//   b_rec = pair records: the words at even/odd positions 2m, 2m+1 of a bucket
+//           share a record of ceil4(L) uint32, entry j = (~e(c_2m[j]) & 0xffff)
+//           | (~e(c_2m+1[j]) << 16); a lane loads one record with 16-byte loads.
+#pragma once
+
+#include <stdint.h>
+
+#include "nw.h"
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace nw {
+
+constexpr int kMaxLen = NW_MAX_WORD_LEN;
+constexpr int kBuckets = kMaxLen + 1;  // lengths 0 .. kMaxLen
+constexpr int kBlock = 256;            // threads per block of the alignment kernel
+constexpr int kWarpB = 64;             // B words per warp task (two per lane)
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr uint32_t kDefaultTA = 256;   // A words per task
+constexpr uint32_t kHistSmemMaxBins = 1024;
+constexpr int kInsertMaxIters = 1 << 20;
+
+// error bits raised by kernels (read back by the host)
+constexpr uint32_t kErrRetry = 1u;      // a list insertion exceeded its retry bound
+constexpr uint32_t kErrHistRange = 2u;  // a score fell outside the histogram bins
+constexpr uint32_t kErrInput = 4u;      // invalid input seen on the device (code/length/index)
+
+__host__ __device__ constexpr int ceil4(int x) { return (x + 3) & ~3; }
+
+// Bucket tables of a word set, by length.
+struct Buckets {
+  uint32_t count[kBuckets];      // words of length L
+  uint32_t start[kBuckets + 1];  // first sorted position of bucket L
+  uint32_t aenc_base[kBuckets];  // a_enc index of the bucket's first symbol
+  uint32_t brec_word_base[kBuckets];  // b_rec uint32 offset of the bucket's first record (multiple of 4)
+};
+
+// A rectangle of pairs: A positions [a_beg, a_end) x B positions [b_beg, b_end),
+// all A words of length la and all B words of the launch's length LB.  With tri,
+// A and B are the same bucket of the same set and only pairs a < b are scored.
+struct Seg {
+  uint32_t a_beg, a_end;
+  uint32_t b_beg, b_end;
+  uint32_t aenc_base;   // a_enc index of word a_beg's first symbol
+  uint32_t brec_base;   // uint4 index into b_rec of the record holding b_beg
+                        // (b_beg - bucket start is even; records of bucket LB are ceil4(LB)/4 uint4 apart)
+  uint16_t la;
+  uint16_t tri;
+  uint32_t nca;         // A chunks (tasks = nca * ceil((b_end - b_beg) / kWarpB))
+  uint64_t task0;       // first task of the segment within its launch
+};
+
+struct TaskGeom {
+  uint32_t a0, a1;      // A positions of the task
+  uint32_t b0, bend;    // B chunk [b0, bend)
+  uint32_t ca, cb;      // chunk coordinates
+  bool tri;
+};
+
+__host__ __device__ __forceinline__ uint32_t find_seg(const Seg* segs, uint32_t nsegs, uint64_t t) {
+  uint32_t lo = 0, hi = nsegs;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (segs[mid].task0 <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ TaskGeom task_geom(const Seg& S, uint64_t t, uint32_t TA) {
+  TaskGeom g;
+  uint64_t local = t - S.task0;
+  g.ca = (uint32_t)(local % S.nca);
+  g.cb = (uint32_t)(local / S.nca);
+  g.a0 = S.a_beg + g.ca * TA;
+  g.a1 = S.a_end < g.a0 + TA ? S.a_end : g.a0 + TA;
+  g.b0 = S.b_beg + g.cb * (uint32_t)kWarpB;
+  g.bend = S.b_end < g.b0 + (uint32_t)kWarpB ? S.b_end : g.b0 + (uint32_t)kWarpB;
+  g.tri = S.tri != 0;
+  if (g.tri && g.a1 > g.bend - 1) g.a1 = g.bend - 1;  // some b > a must exist
+  if (g.a1 < g.a0) g.a1 = g.a0;
+  return g;
+}
+
+__host__ __device__ __forceinline__ bool pair_valid(const TaskGeom& g, uint32_t a, uint32_t b) {
+  return b < g.bend && (!g.tri || a < b);
+}
+
+// One side of a launch: the word set providing A (or B) words.
+struct SideView {
+  const uint32_t* perm;   // sorted position -> original index of the set
+  uint32_t* slots;        // k list slots per word (sorted position), or null
+  uint32_t* thr;          // per-word lower bound of the k-th best key, or null
+};
+
+enum { kModeMatrix = 0, kModeLists = 1 };
+enum { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2 };
+
+struct DpParams {
+  const Seg* segs;
+  uint32_t nsegs;
+  uint32_t TA;
+  uint64_t task_lo, task_hi;      // task slice handled by this launch
+  unsigned long long* counter;    // zeroed before the launch
+  const uint32_t* a_enc;          // A set
+  const uint4* b_rec;             // B set
+  SideView A, B;
+  uint32_t C1, C2;                // packed (s'_m + 1) and s'_x, see the kernel
+  int32_t gap;
+  int32_t mode;
+  int8_t* mat;                    // matrix mode: row-major upper triangle
+  uint64_t n;
+  uint32_t k, ib, imask;          // list key = ((s - key_lo) << ib) | (imask - partner)
+  int32_t key_lo;
+  int32_t hist_mode;
+  unsigned long long* hist;
+  int32_t hist_lo;
+  uint32_t nbins;
+  unsigned long long* stats;      // [0] list inserts
+  uint32_t* err;
+};
+
+// Scoring constants of the shifted recurrence (see the kernel).
+struct ShiftedScoring {
+  int32_t sm, sx;   // s'_m = match - 2*gap, s'_x = mismatch - 2*gap
+  uint32_t shift;   // code shift of the XOR encoding
+  uint32_t C1, C2;  // packed 16x2 constants
+};
+
+}  // namespace nw

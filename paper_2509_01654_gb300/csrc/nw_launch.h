@@ -1,0 +1,61 @@
+// nw_launch.h -- host-side entry points of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nw_internal.cuh"
+
+namespace nw {
+
+// alignment kernel for the longer length LB (0 .. kMaxLen); nullptr if LB is out of range
+const void* dp_kernel(int LB);
+
+// ingest: stable bucketing by length and encoding of a word set
+cudaError_t launch_ingest_count(const uint8_t* codes, const uint32_t* offsets, uint32_t n,
+                                uint32_t alphabet, uint32_t* block_counts, uint32_t* err,
+                                cudaStream_t s);
+cudaError_t launch_ingest_scan(uint32_t* block_counts, uint32_t nblk, uint32_t* bucket_count,
+                               cudaStream_t s);
+cudaError_t launch_ingest_scatter(const uint32_t* offsets, uint32_t n, const uint32_t* block_base,
+                                  const Buckets& bk, uint32_t* perm, uint32_t* rank, uint8_t* slen,
+                                  cudaStream_t s);
+cudaError_t launch_ingest_encode(const uint8_t* codes, const uint32_t* offsets, uint32_t n,
+                                 const uint32_t* perm, const uint8_t* slen, const Buckets& bk,
+                                 uint32_t shift, uint32_t* a_enc, uint32_t* aoff,
+                                 uint32_t* b_rec, uint32_t* brec_w, cudaStream_t s);
+constexpr uint32_t kIngestBlock = 256;
+
+// lists -> ranked (index, score) rows
+cudaError_t launch_finalize(const uint32_t* slots, uint32_t nlists, uint32_t k, const uint32_t* perm,
+                            uint32_t ib, uint32_t imask, int32_t key_lo, uint32_t* out_idx,
+                            int16_t* out_score, cudaStream_t s);
+
+// explicit pairs of one encoded set
+struct PairsParams {
+  const uint32_t* pi;
+  const uint32_t* pj;
+  uint64_t m;
+  uint32_t n;
+  const uint32_t* rank;
+  const uint8_t* slen;
+  const uint32_t* aoff;
+  const uint32_t* brec_w;
+  const uint32_t* a_enc;
+  const uint32_t* b_rec;
+  uint32_t C1, C2;
+  int32_t gap;
+  int16_t* out;
+  uint32_t* err;
+};
+cudaError_t launch_pairs(const PairsParams& p, cudaStream_t s);
+
+// microbenchmarks of the integer instruction rates
+enum RateOp { kRateViaddmax = 0, kRateVimax3, kRateVimaxRelu, kRateIadd3, kRateLop3, kRateCell, kRateOps };
+cudaError_t launch_rate(int op, int blocks, int iters, const uint32_t* in, uint32_t* out,
+                        unsigned long long* cycles, cudaStream_t s);
+// operations per thread per iteration of launch_rate for `op`
+double rate_ops_per_iter(int op);
+constexpr int kRateBlock = 256;
+
+}  // namespace nw

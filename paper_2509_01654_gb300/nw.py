@@ -1,0 +1,348 @@
+"""Python binding of libnw (include/nw.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+(host buffers) or CUDA torch tensors (device buffers, passed with
+NW_DEVICE_PTRS) into pointers and raises ``NwError`` for a failed status.
+The library must have been built (``python -m paper_2509_01654_gb300.build``);
+``load_library`` raises if it is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libnw.so")
+
+NW_OK, NW_EINVAL, NW_ENOMEM, NW_ERANGE, NW_ECUDA, NW_ETIMEOUT, NW_EBUSY = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "NW_OK", -1: "NW_EINVAL", -2: "NW_ENOMEM", -3: "NW_ERANGE", -4: "NW_ECUDA",
+                -5: "NW_ETIMEOUT", -6: "NW_EBUSY"}
+NW_DEVICE_PTRS = 0x1
+NW_ASYNC = 0x2
+MAX_WORD_LEN = 40
+MAX_K = 128
+MISSING_IDX = 0xFFFFFFFF
+MISSING_SCORE = -32768
+
+EXPORTED = [
+    "nw_create", "nw_destroy", "nw_last_error", "nw_set_profiling", "nw_last_profile",
+    "nw_load_dictionary", "nw_dict_info_get", "nw_dict_free", "nw_all_pairs_matrix",
+    "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
+    "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc",
+]
+
+
+class NwError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Scoring(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap", ctypes.c_int32)]
+
+
+class DictInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("alphabet", ctypes.c_uint32), ("min_len", ctypes.c_uint32),
+                ("max_len", ctypes.c_uint32), ("score_lo", ctypes.c_int32), ("score_hi", ctypes.c_int32),
+                ("nbins", ctypes.c_uint32), ("pad_", ctypes.c_uint32), ("pairs", ctypes.c_uint64),
+                ("cells", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("dp_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("dp_launches", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("pairs", ctypes.c_uint64),
+                ("cells", ctypes.c_uint64), ("list_inserts", ctypes.c_uint64)]
+
+
+class IntRates(ctypes.Structure):
+    _fields_ = [("viaddmax_s16x2", ctypes.c_double), ("vimax3_s16x2", ctypes.c_double),
+                ("vimax_s16x2_relu", ctypes.c_double), ("iadd3", ctypes.c_double), ("lop3", ctypes.c_double),
+                ("nw_cell_mix", ctypes.c_double), ("sm_clock_mhz", ctypes.c_double), ("sm_count", ctypes.c_uint32),
+                ("pad_", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libnw.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnw is not built ({path} missing); run paper_2509_01654_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, u32, i32, u64, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_size_t
+    L.nw_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, sz, vp]
+    L.nw_destroy.argtypes = [vp]
+    L.nw_destroy.restype = None
+    L.nw_last_error.argtypes = [vp]
+    L.nw_last_error.restype = ctypes.c_char_p
+    L.nw_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.nw_last_profile.argtypes = [vp, ctypes.POINTER(Profile)]
+    L.nw_load_dictionary.argtypes = [vp, vp, vp, u32, u32, ctypes.POINTER(Scoring), u32, ctypes.POINTER(vp)]
+    L.nw_dict_info_get.argtypes = [vp, ctypes.POINTER(DictInfo)]
+    L.nw_dict_free.argtypes = [vp]
+    L.nw_dict_free.restype = None
+    L.nw_all_pairs_matrix.argtypes = [vp, vp, u32]
+    L.nw_all_pairs_topk.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
+    L.nw_all_pairs_topk_shard.argtypes = [vp, u32, u32, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
+    L.nw_topk_merge.argtypes = [u32, u32, u32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
+    L.nw_score_pairs.argtypes = [vp, vp, vp, sz, vp, u32]
+    L.nw_query.argtypes = [vp, vp, vp, u32, u32, vp, vp, u32]
+    L.nw_measure_int_rates.argtypes = [vp, ctypes.c_double, ctypes.POINTER(IntRates)]
+    L.nw_debug_enumerate_pairs.argtypes = [vp, u32, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
+    L.nw_debug_fail_alloc.argtypes = [vp, u32]
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# buffers
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, is_device) of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), bool(x.is_cuda)
+    if not isinstance(x, np.ndarray) or not x.flags.c_contiguous:
+        raise ValueError("arrays must be C-contiguous numpy arrays or torch tensors")
+    return ctypes.c_void_p(x.ctypes.data), False
+
+
+def _flags(*bufs, async_: bool = False) -> int:
+    kinds = {_ptr(b)[1] for b in bufs if b is not None}
+    if len(kinds) > 1:
+        raise ValueError("mixing host and device buffers in one call is not supported")
+    dev = kinds == {True}
+    return (NW_DEVICE_PTRS if dev else 0) | (NW_ASYNC if (async_ and dev) else 0)
+
+
+def _check(ctx_handle, status):
+    if status != NW_OK:
+        msg = load_library().nw_last_error(ctx_handle)
+        raise NwError(status, msg.decode() if msg else "")
+
+
+def _empty_like_kind(ref, shape, np_dtype, torch_dtype):
+    if ref is not None and _is_torch(ref):
+        import torch
+        return torch.empty(shape, dtype=torch_dtype, device=ref.device)
+    return np.empty(shape, dtype=np_dtype)
+
+
+# ---------------------------------------------------------------------------
+# API
+
+class Context:
+    """nw_create / nw_destroy.  `stream`: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0, stream=None):
+        L = load_library()
+        h = ctypes.c_void_p()
+        sp = None
+        if stream is not None:
+            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        st = L.nw_create(ctypes.byref(h), device, mem_budget_bytes, sp)
+        if st != NW_OK:
+            raise NwError(st, (L.nw_last_error(None) or b"").decode())
+        self.handle = h
+        self.device = device
+        self._stream = stream
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().nw_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return (load_library().nw_last_error(self.handle) or b"").decode()
+
+    def set_profiling(self, on: bool = True):
+        _check(self.handle, load_library().nw_set_profiling(self.handle, int(on)))
+
+    def last_profile(self) -> dict:
+        p = Profile()
+        _check(self.handle, load_library().nw_last_profile(self.handle, ctypes.byref(p)))
+        return {f: getattr(p, f) for f, _ in Profile._fields_}
+
+    def measure_int_rates(self, ms_target: float = 200.0) -> dict:
+        r = IntRates()
+        _check(self.handle, load_library().nw_measure_int_rates(self.handle, ms_target, ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in IntRates._fields_ if f != "pad_"}
+
+    def debug_fail_alloc(self, countdown: int):
+        _check(self.handle, load_library().nw_debug_fail_alloc(self.handle, countdown))
+
+    def load_dictionary(self, codes, offsets, alphabet: int, scoring) -> "Dictionary":
+        return Dictionary(self, codes, offsets, alphabet, scoring)
+
+
+class Dictionary:
+    """nw_load_dictionary / nw_dict_free and the calls on a dictionary."""
+
+    def __init__(self, ctx: Context, codes, offsets, alphabet: int, scoring):
+        L = load_library()
+        self.ctx = ctx
+        self.scoring = tuple(int(v) for v in scoring)
+        if not _is_torch(codes):
+            codes = np.ascontiguousarray(codes, dtype=np.uint8)
+            if codes.size == 0:
+                codes = np.zeros(1, np.uint8)
+            offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+        n = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
+        sc = Scoring(*self.scoring)
+        h = ctypes.c_void_p()
+        st = L.nw_load_dictionary(ctx.handle, _ptr(codes)[0], _ptr(offsets)[0], n, alphabet, ctypes.byref(sc),
+                                  _flags(codes, offsets), ctypes.byref(h))
+        _check(ctx.handle, st)
+        self.handle = h
+        self.n = n
+
+    def free(self):
+        if getattr(self, "handle", None) and getattr(self.ctx, "handle", None):
+            load_library().nw_dict_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = DictInfo()
+        _check(self.ctx.handle, load_library().nw_dict_info_get(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in DictInfo._fields_ if f != "pad_"}
+
+    def all_pairs_matrix(self, out=None, async_: bool = False):
+        """int8 scores of all pairs i < j, row-major upper triangle (n(n-1)/2 entries)."""
+        E = self.n * (self.n - 1) // 2
+        if out is None:
+            out = np.empty(E, dtype=np.int8)
+        _check(self.ctx.handle, load_library().nw_all_pairs_matrix(self.handle, _ptr(out)[0], _flags(out, async_=async_)))
+        return out
+
+    def all_pairs_topk(self, k: int, nbr_idx=None, nbr_score=None, hist=True, shard=None, async_: bool = False):
+        """(idx[n, k] uint32, score[n, k] int16, hist int64 or None, hist_lo)."""
+        n = self.n
+        if nbr_idx is None:
+            nbr_idx = _empty_like_kind(None, (n, k), np.uint32, None)
+        if nbr_score is None:
+            nbr_score = _empty_like_kind(nbr_idx, (n, k), np.int16, _torch_dtype("int16"))
+        h = None
+        nbins = 0
+        if hist is True:
+            nbins = self.info()["nbins"]
+            h = _empty_like_kind(nbr_idx, (nbins,), np.int64, _torch_dtype("int64"))
+        elif hist is not None and hist is not False:
+            h = hist
+            nbins = int(h.shape[0])
+        lo = ctypes.c_int32(0)
+        L = load_library()
+        flags = _flags(nbr_idx, nbr_score, h, async_=async_)
+        if shard is None:
+            st = L.nw_all_pairs_topk(self.handle, k, _ptr(nbr_idx)[0], _ptr(nbr_score)[0], _ptr(h)[0],
+                                     ctypes.byref(lo), nbins, flags)
+        else:
+            g, G = shard
+            st = L.nw_all_pairs_topk_shard(self.handle, g, G, k, _ptr(nbr_idx)[0], _ptr(nbr_score)[0], _ptr(h)[0],
+                                           ctypes.byref(lo), nbins, flags)
+        _check(self.ctx.handle, st)
+        return nbr_idx, nbr_score, h, int(lo.value)
+
+    def score_pairs(self, i, j, out=None, async_: bool = False):
+        if not _is_torch(i):
+            i = np.ascontiguousarray(i, dtype=np.uint32)
+            j = np.ascontiguousarray(j, dtype=np.uint32)
+        m = int(i.shape[0])
+        if out is None:
+            out = _empty_like_kind(i, (m,), np.int16, _torch_dtype("int16"))
+        _check(self.ctx.handle, load_library().nw_score_pairs(self.handle, _ptr(i)[0], _ptr(j)[0], m, _ptr(out)[0],
+                                                              _flags(i, j, out, async_=async_)))
+        return out
+
+    def query(self, qcodes, qoffsets, k: int, nbr_idx=None, nbr_score=None):
+        if not _is_torch(qoffsets):
+            qcodes = np.ascontiguousarray(qcodes, dtype=np.uint8)
+            if qcodes.size == 0:
+                qcodes = np.zeros(1, np.uint8)
+            qoffsets = np.ascontiguousarray(qoffsets, dtype=np.uint32)
+        nq = int(qoffsets.shape[0]) - 1
+        if nbr_idx is None:
+            nbr_idx = _empty_like_kind(qoffsets if _is_torch(qoffsets) else None, (nq, k), np.uint32,
+                                       _torch_dtype("int32"))
+        if nbr_score is None:
+            nbr_score = _empty_like_kind(nbr_idx, (nq, k), np.int16, _torch_dtype("int16"))
+        _check(self.ctx.handle, load_library().nw_query(self.handle, _ptr(qcodes)[0], _ptr(qoffsets)[0], nq, k,
+                                                        _ptr(nbr_idx)[0], _ptr(nbr_score)[0],
+                                                        _flags(qcodes, qoffsets, nbr_idx, nbr_score)))
+        return nbr_idx, nbr_score
+
+
+def _torch_dtype(name):
+    try:
+        import torch
+        return getattr(torch, name)
+    except ImportError:
+        return None
+
+
+def topk_merge(parts, k: int):
+    """nw_topk_merge over host parts [(idx[n, k] uint32, score[n, k] int16), ...]."""
+    L = load_library()
+    idx_parts = [np.ascontiguousarray(p[0], dtype=np.uint32) for p in parts]
+    sc_parts = [np.ascontiguousarray(p[1], dtype=np.int16) for p in parts]
+    n = idx_parts[0].shape[0] if parts else 0
+    ip = (ctypes.c_void_p * len(parts))(*[ctypes.c_void_p(a.ctypes.data) for a in idx_parts])
+    sp = (ctypes.c_void_p * len(parts))(*[ctypes.c_void_p(a.ctypes.data) for a in sc_parts])
+    oi = np.empty((n, k), dtype=np.uint32)
+    os_ = np.empty((n, k), dtype=np.int16)
+    st = L.nw_topk_merge(n, k, len(parts), ctypes.cast(ip, ctypes.POINTER(ctypes.c_void_p)),
+                         ctypes.cast(sp, ctypes.POINTER(ctypes.c_void_p)), ctypes.c_void_p(oi.ctypes.data),
+                         ctypes.c_void_p(os_.ctypes.data))
+    if st != NW_OK:
+        raise NwError(st, "nw_topk_merge failed")
+    return oi, os_
+
+
+def debug_enumerate_pairs(lengths, shard: int = 0, nshards: int = 1):
+    """The (a, b) original-index pairs the all-pairs kernels would score, in task order."""
+    L = load_library()
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint32)
+    n = lengths.size
+    cnt = ctypes.c_uint64(0)
+    st = L.nw_debug_enumerate_pairs(ctypes.c_void_p(lengths.ctypes.data), n, shard, nshards, None, None, 0,
+                                    ctypes.byref(cnt))
+    if st != NW_OK:
+        raise NwError(st, "nw_debug_enumerate_pairs failed")
+    a = np.empty(max(1, cnt.value), dtype=np.uint32)
+    b = np.empty(max(1, cnt.value), dtype=np.uint32)
+    st = L.nw_debug_enumerate_pairs(ctypes.c_void_p(lengths.ctypes.data), n, shard, nshards,
+                                    ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(b.ctypes.data), cnt.value,
+                                    ctypes.byref(cnt))
+    if st != NW_OK:
+        raise NwError(st, "nw_debug_enumerate_pairs failed")
+    return a[:cnt.value], b[:cnt.value]

@@ -1,0 +1,125 @@
+"""Host-side checks of libnw that need no GPU: the library loads and exports
+every entry point of include/nw.h, the pair planner covers every unordered
+pair exactly once (in every shard split), the host merge of partial lists is
+exact, and calls fail loudly without a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2509_01654_gb300 import build as nwbuild
+from paper_2509_01654_gb300 import nw, synth
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nwbuild.build()
+    return nw.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "nw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nw_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declarations_are_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(nw.EXPORTED)
+
+
+def all_unordered(n):
+    i, j = np.triu_indices(n, 1)
+    return set(zip(i.tolist(), j.tolist()))
+
+
+def as_set(a, b):
+    lo = np.minimum(a, b)
+    hi = np.maximum(a, b)
+    pairs = list(zip(lo.tolist(), hi.tolist()))
+    return pairs, set(pairs)
+
+
+@pytest.mark.parametrize("case", ["mixed", "single_len", "with_empty", "ragged_big", "long_words"])
+def test_planner_covers_each_pair_once(lib, case):
+    rng = np.random.default_rng(hash(case) % 1000)
+    if case == "mixed":
+        L = rng.integers(1, 12, 300)
+    elif case == "single_len":
+        L = np.full(777, 5)               # one bucket, several A chunks, odd size
+    elif case == "with_empty":
+        L = rng.integers(0, 4, 150)       # empty words share a bucket
+    elif case == "ragged_big":
+        L = synth.exhaustive_words(1500).lengths
+    else:
+        L = rng.integers(30, 41, 200)
+    a, b = nw.debug_enumerate_pairs(L)
+    pairs, s = as_set(a, b)
+    assert len(pairs) == len(s) == L.size * (L.size - 1) // 2
+    assert s == all_unordered(L.size)
+    assert np.all(a != b)
+    # the longer word is always the lane (B) word
+    assert np.all(L[b] >= L[a])
+
+
+@pytest.mark.parametrize("nshards", [2, 3, 7])
+def test_planner_shards_partition_pairs(lib, nshards):
+    L = synth.pr1_words(400).lengths
+    seen = []
+    for g in range(nshards):
+        a, b = nw.debug_enumerate_pairs(L, g, nshards)
+        seen.extend(as_set(a, b)[0])
+    assert len(seen) == len(set(seen)) == 400 * 399 // 2
+
+
+def test_planner_degenerate_sizes(lib):
+    for L in ([3], [0], [2, 2], [0, 0], [1, 40], list(range(41))):
+        a, b = nw.debug_enumerate_pairs(np.array(L))
+        assert as_set(a, b)[1] == all_unordered(len(L))
+
+
+def test_topk_merge_matches_full_lists(lib, oracle_mod):
+    w = synth.make_words(90, 5, 1.0, 4.0, 2.0, 1, 8, seed=12)
+    sc = (1, -1, -1)
+    k = 6
+    full_idx, full_sc = oracle_mod.topk_rows(w, np.arange(w.n), k, sc)
+    # split each word's candidates into 3 disjoint parts and rank within each part
+    M = np.full((w.n, w.n), -10 ** 6, dtype=np.int64)
+    iu = np.triu_indices(w.n, 1)
+    vals = oracle_mod.all_pairs(w, sc)
+    M[iu] = vals
+    M[(iu[1], iu[0])] = vals
+    part_of = (np.add.outer(np.arange(w.n), np.arange(w.n)) % 3)
+    parts = []
+    for p in range(3):
+        pi = np.full((w.n, k), nw.MISSING_IDX, dtype=np.uint32)
+        ps = np.full((w.n, k), nw.MISSING_SCORE, dtype=np.int16)
+        for i in range(w.n):
+            js = np.array([j for j in range(w.n) if j != i and part_of[i, j] == p])
+            if js.size == 0:
+                continue
+            order = np.lexsort((js, -M[i, js]))[:k]
+            pi[i, :order.size] = js[order]
+            ps[i, :order.size] = M[i, js[order]]
+        parts.append((pi, ps))
+    mi, ms = nw.topk_merge(parts, k)
+    assert np.array_equal(mi, full_idx)
+    assert np.array_equal(ms, full_sc.astype(np.int16))
+    # merging a part with itself changes nothing (duplicates kept once)
+    mi2, ms2 = nw.topk_merge([(full_idx, full_sc.astype(np.int16))] * 2, k)
+    assert np.array_equal(mi2, full_idx)
+
+
+def test_calls_fail_loudly_without_gpu(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(nw.NwError) as e:
+        nw.Context(0)
+    assert e.value.status in (nw.NW_ECUDA, nw.NW_EINVAL)
+    assert str(e.value)
