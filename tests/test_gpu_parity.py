@@ -286,7 +286,7 @@ def test_matrix_range_error(ctx):
 
 def test_memory_budget_and_injected_failure():
     w = synth.pr1_words(500)
-    with nw.Context(0, mem_budget_bytes=64 * 1024) as c:
+    with nw.Context(0, mem_budget_bytes=8 * 1024) as c:
         with pytest.raises(nw.NwError) as e:
             c.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
         assert e.value.status == nw.NW_ENOMEM and "budget" in str(e.value)
