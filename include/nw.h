@@ -194,6 +194,36 @@ nw_status nw_score_pairs(nw_dict *dict, const uint32_t *i, const uint32_t *j, si
 nw_status nw_query(nw_dict *dict, const uint8_t *qcodes, const uint32_t *qoffsets, uint32_t nq,
                    uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score, uint32_t flags);
 
+/* ---- variant for callers that cannot allocate device memory ----
+ *
+ * No counterpart in the paper.  Some callers cannot allocate device memory
+ * at the time they run this reduction: code that runs inside a stream
+ * capture or with allocation locked down, a real-time loop that must not
+ * reach the allocator (cudaMalloc/cudaFree synchronise the device), or a host
+ * that has handed all free memory to a pool it manages.  This entry point
+ * computes exactly what nw_all_pairs_topk computes for the whole pair set,
+ * but takes every scratch buffer (neighbour-list slots, thresholds, task
+ * counters, histogram accumulators, error flag) from one fixed static device
+ * array of NW_NOALLOC_SCRATCH_BYTES compiled into the library, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   - Outputs must be device pointers: `flags` must contain NW_DEVICE_PTRS
+ *     (NW_EINVAL otherwise); hist_lo is a host pointer (may be NULL).
+ *   - Scratch needed: 2 KiB + 4*n + 4*n*k + 8*nbins bytes, each part rounded
+ *     up to 256 bytes; a dictionary/k that needs more than the array gives
+ *     NW_ERANGE and writes nothing (k = 10 allows n up to about 760,000).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - The array is shared by every call in the process and keeps the last
+ *     call's contents; each call clears what must start at zero.  Calls whose
+ *     GPU work overlaps (other contexts or streams on the same device) race on
+ *     the array and give wrong results: serialise them.
+ *   - The array occupies device memory on every GPU that loads the library
+ *     until the process exits. */
+#define NW_NOALLOC_SCRATCH_BYTES (32u << 20)
+nw_status nw_all_pairs_topk_noalloc(nw_dict *dict, uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score,
+                                    int64_t *hist, int32_t *hist_lo, uint32_t nbins, uint32_t flags);
+
 /* ---- measurement and testing helpers (no counterpart in the paper) ---- */
 
 /* Issue rates of the integer instructions the alignment kernel is built from,

@@ -1192,3 +1192,108 @@ nw_status nw_debug_fail_alloc(nw_ctx* c, uint32_t countdown) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// The all-pairs top-k reduction over a fixed scratch region (no allocation).
+
+namespace nw {
+
+nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uint32_t* nbr_idx,
+                            int16_t* nbr_score, int64_t* hist, int32_t* hist_lo, uint32_t nbins,
+                            uint32_t flags) {
+  if (!d || !provide) return NW_EINVAL;
+  nw_ctx* c = d->ctx;
+  NW_ENTER(c);
+  if (!(flags & NW_DEVICE_PTRS))
+    return set_err(c, NW_EINVAL, "the no-allocation variant needs device output buffers (NW_DEVICE_PTRS)");
+  const uint32_t n = d->ws.n;
+  if (n < 2) return set_err(c, NW_EINVAL, "the dictionary needs at least 2 words (has %u)", n);
+  if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  if (!nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null output pointer");
+  const uint32_t need_bins = (uint32_t)(d->score_hi - d->score_lo + 1);
+  if (hist && nbins < need_bins)
+    return set_err(c, NW_ERANGE, "histogram needs %u bins for scores [%d, %d], got %u", need_bins, d->score_lo,
+                   d->score_hi, nbins);
+  if (d->score_lo < INT16_MIN + 1 || d->score_hi > INT16_MAX)
+    return set_err(c, NW_ERANGE, "scores [%d, %d] do not fit int16", d->score_lo, d->score_hi);
+  const uint32_t ib = index_bits(n);
+  const int32_t key_lo = d->score_lo - 1;
+  if ((uint64_t)(d->score_hi - key_lo) >= (1ull << (32 - ib)))
+    return set_err(c, NW_ERANGE, "score range %d..%d with %u words does not fit 32-bit list keys", d->score_lo,
+                   d->score_hi, n);
+
+  // scratch layout: [error flag, insert count, task counters | 2 KiB][thresholds][list slots][histogram]
+  const size_t nlaunch = d->plan.launches.size();
+  auto up256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t off_thr = 2048;
+  const size_t off_slots = off_thr + up256(sizeof(uint32_t) * (size_t)n);
+  const size_t off_hist = off_slots + up256(sizeof(uint32_t) * (size_t)n * k);
+  const size_t need = off_hist + (hist ? up256(sizeof(unsigned long long) * need_bins) : 0);
+  if (64 + sizeof(unsigned long long) * (nlaunch + 1) > off_thr)
+    return set_err(c, NW_ERANGE, "too many launches for the scratch header");
+  void* base = nullptr;
+  size_t cap = 0;
+  const char* why = "";
+  const nw_status pst = provide(c->device, &base, &cap, &why);
+  if (pst != NW_OK) return set_err(c, pst, "static scratch region unavailable: %s", why);
+  if (need > cap)
+    return set_err(c, NW_ERANGE, "%u words with k = %u need %zu bytes of scratch; the static region holds %zu", n, k,
+                   need, cap);
+  char* sb = static_cast<char*>(base);
+  uint32_t* d_err = reinterpret_cast<uint32_t*>(sb);
+  unsigned long long* d_stats = reinterpret_cast<unsigned long long*>(sb + 8);
+  unsigned long long* d_counters = reinterpret_cast<unsigned long long*>(sb + 64);
+  uint32_t* d_thr = reinterpret_cast<uint32_t*>(sb + off_thr);
+  uint32_t* d_slots = reinterpret_cast<uint32_t*>(sb + off_slots);
+  unsigned long long* d_hist = hist ? reinterpret_cast<unsigned long long*>(sb + off_hist) : nullptr;
+  cudaStream_t s = c->stream;
+
+  // no events either: this path creates nothing
+  const bool saved_profiling = c->profiling;
+  c->profiling = false;
+  struct Restore {
+    nw_ctx* c;
+    bool v;
+    ~Restore() { c->profiling = v; }
+  } restore{c, saved_profiling};
+
+  NW_CK(cudaMemsetAsync(sb, 0, off_thr, s));
+  NW_CK(cudaMemsetAsync(d_thr, 0, sizeof(uint32_t) * (size_t)n, s));
+  NW_CK(cudaMemsetAsync(d_slots, 0, sizeof(uint32_t) * (size_t)n * k, s));
+  if (hist) NW_CK(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * need_bins, s));
+
+  DpParams P{};
+  P.TA = kDefaultTA;
+  P.C1 = d->ss.C1;
+  P.C2 = d->ss.C2;
+  P.gap = d->sc.gap;
+  P.mode = kModeLists;
+  P.k = k;
+  P.ib = ib;
+  P.imask = (uint32_t)(((uint64_t)1 << ib) - 1);
+  P.key_lo = key_lo;
+  P.hist_mode = !hist ? kHistNone : (need_bins <= kHistSmemMaxBins ? kHistSmem : kHistGlobal);
+  P.hist = d_hist;
+  P.hist_lo = d->score_lo;
+  P.nbins = hist ? need_bins : 0;
+  P.stats = d_stats;
+  P.err = d_err;
+  SideView side{d->ws.perm.as<uint32_t>(), d_slots, d_thr};
+  const uint32_t* a_enc[3] = {d->ws.a_enc.as<uint32_t>(), nullptr, nullptr};
+  const uint4* b_rec[3] = {d->ws.b_rec.as<uint4>(), nullptr, nullptr};
+  const SideView* views[3] = {&side, nullptr, nullptr};
+  Timer tm{c};
+  RunOut ro;
+  NW_TRY(run_plan(c, d->plan, d->d_segs.as<Seg>(), P, &d->ws, &d->ws, d_counters, 0, 1, tm, ro, a_enc, views, b_rec,
+                  views));
+  NW_CK(launch_finalize(d_slots, n, k, d->ws.perm.as<uint32_t>(), ib, P.imask, key_lo, nbr_idx, nbr_score, s));
+  if (hist) {
+    NW_CK(cudaMemcpyAsync(hist, d_hist, sizeof(int64_t) * need_bins, cudaMemcpyDeviceToDevice, s));
+    if (nbins > need_bins) NW_CK(cudaMemsetAsync(hist + need_bins, 0, sizeof(int64_t) * (nbins - need_bins), s));
+    if (hist_lo) *hist_lo = d->score_lo;
+  }
+  if (flags & NW_ASYNC) return NW_OK;
+  return check_device_flags(c, d_err);
+}
+
+}  // namespace nw

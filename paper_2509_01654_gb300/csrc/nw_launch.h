@@ -50,6 +50,14 @@ struct PairsParams {
 };
 cudaError_t launch_pairs(const PairsParams& p, cudaStream_t s);
 
+// the all-pairs top-k reduction with every scratch buffer taken from a
+// caller-supplied device region; `provide` is called with the dictionary's
+// device current and returns the region (see nw_all_pairs_topk_noalloc)
+typedef nw_status (*ScratchProvider)(int device, void** base, size_t* bytes, const char** why);
+nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uint32_t* nbr_idx,
+                            int16_t* nbr_score, int64_t* hist, int32_t* hist_lo, uint32_t nbins,
+                            uint32_t flags);
+
 // microbenchmarks of the integer instruction rates
 enum RateOp { kRateViaddmax = 0, kRateVimax3, kRateVimaxRelu, kRateIadd3, kRateLop3, kRateCell, kRateOps };
 cudaError_t launch_rate(int op, int blocks, int iters, const uint32_t* in, uint32_t* out,

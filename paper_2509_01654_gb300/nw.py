@@ -30,8 +30,9 @@ EXPORTED = [
     "nw_create", "nw_destroy", "nw_last_error", "nw_set_profiling", "nw_last_profile",
     "nw_load_dictionary", "nw_dict_info_get", "nw_dict_free", "nw_all_pairs_matrix",
     "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
-    "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc",
+    "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc", "nw_all_pairs_topk_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class NwError(RuntimeError):
@@ -96,6 +97,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_measure_int_rates.argtypes = [vp, ctypes.c_double, ctypes.POINTER(IntRates)]
     L.nw_debug_enumerate_pairs.argtypes = [vp, u32, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
     L.nw_debug_fail_alloc.argtypes = [vp, u32]
+    L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     _lib = L
     return L
 
@@ -272,6 +274,18 @@ class Dictionary:
                                            ctypes.byref(lo), nbins, flags)
         _check(self.ctx.handle, st)
         return nbr_idx, nbr_score, h, int(lo.value)
+
+    def all_pairs_topk_noalloc(self, k: int, nbr_idx, nbr_score, hist=None, async_: bool = False):
+        """nw_all_pairs_topk_noalloc: the same lists and histogram as all_pairs_topk,
+        computed with the library's fixed static scratch instead of any device
+        allocation.  Outputs must be CUDA tensors; returns hist_lo."""
+        lo = ctypes.c_int32(0)
+        nbins = int(hist.shape[0]) if hist is not None else 0
+        st = load_library().nw_all_pairs_topk_noalloc(self.handle, k, _ptr(nbr_idx)[0], _ptr(nbr_score)[0],
+                                                      _ptr(hist)[0], ctypes.byref(lo), nbins,
+                                                      _flags(nbr_idx, nbr_score, hist, async_=async_))
+        _check(self.ctx.handle, st)
+        return int(lo.value)
 
     def score_pairs(self, i, j, out=None, async_: bool = False):
         if not _is_torch(i):
