@@ -194,7 +194,7 @@ nw_status make_shifted(nw_ctx* c, const nw_scoring& s, uint32_t alphabet, Shifte
   out.sx = sx;
   out.shift = shift;
   out.C1 = pack16(sm + 1);
-  out.C2 = pack16(sx);
+  out.C2 = pack16(std::max(sx, 0));  // a negative mismatch term never wins (see nw_dp.cuh)
   return NW_OK;
 }
 
@@ -250,9 +250,13 @@ Seg make_seg(const Buckets& A, int La, uint32_t a_beg, uint32_t a_end, const Buc
   return s;
 }
 
+// Launches run in increasing longer length: a word of length L first meets
+// partners of its own length (the segment La == LB leads launch L), where its
+// best neighbours usually are, so list thresholds rise before the many
+// low-scoring pairs of very different lengths arrive.
 void order_launches(Plan& p) {
   std::stable_sort(p.launches.begin(), p.launches.end(),
-                   [](const LaunchPlan& x, const LaunchPlan& y) { return x.cells > y.cells; });
+                   [](const LaunchPlan& x, const LaunchPlan& y) { return x.LB < y.LB; });
 }
 
 // Every unordered pair of one set, once: launch LB holds the pairs whose
@@ -528,7 +532,7 @@ nw_status run_plan(nw_ctx* c, const Plan& plan, const Seg* d_segs, const DpParam
     P.A = *A_by_role[lp.role];
     P.b_rec = b_rec_by_role[lp.role];
     P.B = *B_by_role[lp.role];
-    const size_t smem = P.hist_mode == kHistSmem ? (size_t)kWarpsPerBlock * P.nbins * sizeof(uint32_t) : 0;
+    const size_t smem = hist_smem_bytes(P.hist_mode, P.nbins);
     const void* fn = dp_kernel(lp.LB);
     if (!fn) return set_err(c, NW_EINVAL, "no kernel for length %d", lp.LB);
     int occ = 0;
@@ -615,7 +619,7 @@ nw_status topk_impl(nw_dict* d, uint32_t shard, uint32_t nshards, uint32_t k, ui
   base.ib = ib;
   base.imask = (uint32_t)(((uint64_t)1 << ib) - 1);
   base.key_lo = key_lo;
-  base.hist_mode = !hist ? kHistNone : (need_bins <= kHistSmemMaxBins ? kHistSmem : kHistGlobal);
+  base.hist_mode = !hist ? kHistNone : hist_mode_for(need_bins);
   base.hist = hist ? c->ws_hist.as<unsigned long long>() : nullptr;
   base.hist_lo = d->score_lo;
   base.nbins = hist ? need_bins : 0;
@@ -1272,7 +1276,7 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
   P.ib = ib;
   P.imask = (uint32_t)(((uint64_t)1 << ib) - 1);
   P.key_lo = key_lo;
-  P.hist_mode = !hist ? kHistNone : (need_bins <= kHistSmemMaxBins ? kHistSmem : kHistGlobal);
+  P.hist_mode = !hist ? kHistNone : hist_mode_for(need_bins);
   P.hist = d_hist;
   P.hist_lo = d->score_lo;
   P.nbins = hist ? need_bins : 0;

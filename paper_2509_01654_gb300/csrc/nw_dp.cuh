@@ -14,14 +14,19 @@
 // of each register) and their DP row G[i][1..LB] in LB registers; the warp
 // streams one A word at a time (the same symbol in both halves), so each
 // packed instruction advances two alignments by one cell.  Per packed cell:
-//     xt = a2 ^ b2[j]                  per half: -1 - (e(a) ^ e(b))
-//     f  = viaddmax(xt, s'_m + 1, s'_x) per half: s'_m if a == b else s'_x
-//     m  = vimax_relu(up, left)         max(G[i-1][j], G[i][j-1])   (G >= 0)
-//     h  = viaddmax(diag, f, m)         max(G[i-1][j-1] + s', m)
+//     xt = a2 ^ b2[j]                    per half: -1 - (e(a) ^ e(b))
+//     f  = viaddmax(xt, s'_m + 1, s'_x+) per half: s'_m if a == b else s'_x+
+//     d  = diag + f                      plain 32-bit add (both halves >= 0)
+//     h  = vimax3(d, up, left)           max(G[i-1][j-1] + s', G[i-1][j], G[i][j-1])
 // The codes are stored shifted (e(c) = c << shift, 2^shift >= match -
 // mismatch), so for different codes e(a) ^ e(b) >= match - mismatch and
 // s'_m - (e(a) ^ e(b)) <= s'_x: the max with s'_x then selects the mismatch
-// value.  One LOP3 and three DPX instructions per two cells.
+// value.  s'_x+ = max(s'_x, 0): G is non-decreasing along rows and columns,
+// so G[i-1][j-1] + s'_x < 0 + G[i-1][j-1] <= G[i-1][j] whenever s'_x < 0 and
+// raising the mismatch term to 0 changes no maximum; it keeps f >= 0, so the
+// packed add never carries between halves (G + f <= s'_m * LB < 2^15).
+// Per two cells: one LOP3, one add and two DPX instructions; rows go two at
+// a time so the two rows' dependency chains interleave.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,6 +41,23 @@ struct BRow {
   uint32_t v[LB > 0 ? LB : 1];
 };
 
+// One row of the shifted recurrence: G[1..LB] of row i-1 becomes row i.
+template <int LB>
+__device__ __forceinline__ void dp_row(uint32_t (&G)[LB], uint32_t a2, const BRow<LB>& b, uint32_t C1,
+                                       uint32_t C2) {
+  uint32_t diag = 0u, left = 0u;
+#pragma unroll
+  for (int j = 0; j < LB; ++j) {
+    const uint32_t xt = a2 ^ b.v[j];
+    const uint32_t f = __viaddmax_s16x2(xt, C1, C2);
+    const uint32_t up = G[j];
+    const uint32_t h = __vimax3_s16x2(diag + f, up, left);
+    diag = up;
+    G[j] = h;
+    left = h;
+  }
+}
+
 // DP over the la rows of one A word against the lane's two B words; returns
 // the packed G[la][LB] (0 when la == 0 or LB == 0).
 template <int LB>
@@ -47,22 +69,15 @@ __device__ __forceinline__ uint32_t dp_word(const uint32_t* __restrict__ arow, i
     uint32_t G[LB];
 #pragma unroll
     for (int j = 0; j < LB; ++j) G[j] = 0u;
+    int i = 0;
 #pragma unroll 1
-    for (int i = 0; i < la; ++i) {
-      const uint32_t a2 = __ldg(arow + i);
-      uint32_t diag = 0u, left = 0u;
-#pragma unroll
-      for (int j = 0; j < LB; ++j) {
-        const uint32_t xt = a2 ^ b.v[j];
-        const uint32_t f = __viaddmax_s16x2(xt, C1, C2);
-        const uint32_t up = G[j];
-        const uint32_t m = __vimax_s16x2_relu(up, left);
-        const uint32_t h = __viaddmax_s16x2(diag, f, m);
-        diag = up;
-        G[j] = h;
-        left = h;
-      }
+    for (; i + 1 < la; i += 2) {
+      const uint32_t a0 = __ldg(arow + i);
+      const uint32_t a1 = __ldg(arow + i + 1);
+      dp_row<LB>(G, a0, b, C1, C2);
+      dp_row<LB>(G, a1, b, C1, C2);
     }
+    if (i < la) dp_row<LB>(G, __ldg(arow + i), b, C1, C2);
     return G[LB - 1];
   }
 }
@@ -80,10 +95,6 @@ __device__ __forceinline__ void load_brow(const uint4* __restrict__ rec, BRow<LB
       if (4 * q + 3 < LB) b.v[4 * q + 3] = v.w;
     }
   }
-}
-
-__device__ __forceinline__ int score_threshold(uint32_t thr_key, uint32_t ib, int32_t key_lo) {
-  return thr_key == 0u ? INT_MIN : (int)(thr_key >> ib) + key_lo;
 }
 
 // Offers `key` to a word's list of k slots.  The slots always hold the k
@@ -122,20 +133,44 @@ __device__ __forceinline__ uint64_t upper_offset(uint64_t i, uint64_t j, uint64_
   return i * (2 * n - i - 1) / 2 + (j - i - 1);
 }
 
-__device__ __forceinline__ void hist_add(const DpParams& P, uint32_t* wh, int s) {
-  const uint32_t bi = (uint32_t)(s - P.hist_lo);
+// Histogram accumulation.  kHistLane: every lane owns a column of the warp's
+// shared array (bin b of lane l at b*32 + l), so the shared atomics of a warp
+// never collide; kHistSmem: one shared array per warp; kHistGlobal: global
+// atomics.  `bin` is the score minus the histogram's lowest score.
+__device__ __forceinline__ void hist_add(const DpParams& P, uint32_t* wh, int lane, int bin) {
+  const uint32_t bi = (uint32_t)bin;
   if (bi >= P.nbins) { atomicOr(P.err, kErrHistRange); return; }
-  if (P.hist_mode == kHistSmem) atomicAdd(wh + bi, 1u);
+  if (P.hist_mode == kHistLane) atomicAdd(wh + bi * 32u + (uint32_t)lane, 1u);
+  else if (P.hist_mode == kHistSmem) atomicAdd(wh + bi, 1u);
   else atomicAdd(P.hist + bi, 1ull);
 }
 
 __device__ __forceinline__ void hist_flush(const DpParams& P, uint32_t* wh, int lane) {
   __syncwarp();
-  for (uint32_t b = lane; b < P.nbins; b += 32) {
-    const uint32_t c = wh[b];
-    if (c) { atomicAdd(P.hist + b, (unsigned long long)c); wh[b] = 0u; }
+  if (P.hist_mode == kHistLane) {
+    for (uint32_t b = lane; b < P.nbins; b += 32) {
+      uint32_t c = 0;
+      for (int l = 0; l < 32; ++l) {
+        const uint32_t q = b * 32u + (uint32_t)((l + lane) & 31);  // rotated: no bank conflicts
+        c += wh[q];
+      }
+      if (c) atomicAdd(P.hist + b, (unsigned long long)c);
+    }
+    __syncwarp();
+    for (uint32_t q = lane; q < P.nbins * 32u; q += 32) wh[q] = 0u;
+  } else {
+    for (uint32_t b = lane; b < P.nbins; b += 32) {
+      const uint32_t c = wh[b];
+      if (c) { atomicAdd(P.hist + b, (unsigned long long)c); wh[b] = 0u; }
+    }
   }
   __syncwarp();
+}
+
+// G-space candidate threshold of a list whose smallest key is >= thr_key:
+// a pair can enter the list only if its packed G value reaches this bound.
+__device__ __forceinline__ int g_threshold(uint32_t thr_key, uint32_t ib, int32_t key_lo, int pconst) {
+  return thr_key == 0u ? INT_MIN : (int)(thr_key >> ib) + key_lo - pconst;
 }
 
 template <int LB>
@@ -143,10 +178,11 @@ __global__ void __launch_bounds__(kBlock) nw_dp_kernel(const DpParams P) {
   extern __shared__ uint32_t s_hist[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  uint32_t* wh = s_hist + (size_t)wib * P.nbins;
-  const bool use_smem_hist = P.hist_mode == kHistSmem;
-  if (use_smem_hist) {
-    for (uint32_t b = lane; b < P.nbins; b += 32) wh[b] = 0u;
+  const bool smem_hist = P.hist_mode == kHistLane || P.hist_mode == kHistSmem;
+  const uint32_t wstride = P.hist_mode == kHistLane ? P.nbins * 32u : P.nbins;
+  uint32_t* wh = s_hist + (size_t)wib * wstride;
+  if (smem_hist) {
+    for (uint32_t q = lane; q < wstride; q += 32) wh[q] = 0u;
     __syncwarp();
   }
   uint64_t wpairs = 0;
@@ -167,7 +203,8 @@ __global__ void __launch_bounds__(kBlock) nw_dp_kernel(const DpParams P) {
     const bool vlo = blo < g.bend;
     const bool vhi = bhi < g.bend;
     const int la = S.la;
-    const int pconst = P.gap * (la + LB);
+    const int pconst = P.gap * (la + LB);  // score = G + pconst
+    const int hoff = pconst - P.hist_lo;   // histogram bin = G + hoff
 
     BRow<LB> brow;
     if constexpr (LB > 0) {
@@ -177,82 +214,85 @@ __global__ void __launch_bounds__(kBlock) nw_dp_kernel(const DpParams P) {
     }
     const uint32_t ob_lo = vlo ? __ldg(P.B.perm + blo) : 0u;
     const uint32_t ob_hi = vhi ? __ldg(P.B.perm + bhi) : 0u;
+    // B-side lists: cached smallest keys and their G-space candidate bounds
     uint32_t thrB_lo = 0u, thrB_hi = 0u;
-    int sthrB_lo = INT_MAX, sthrB_hi = INT_MAX;
+    int tB_lo = INT_MAX, tB_hi = INT_MAX;
     if (listsB) {
-      if (vlo) { thrB_lo = __ldcg(P.B.thr + blo); sthrB_lo = score_threshold(thrB_lo, P.ib, P.key_lo); }
-      if (vhi) { thrB_hi = __ldcg(P.B.thr + bhi); sthrB_hi = score_threshold(thrB_hi, P.ib, P.key_lo); }
+      if (vlo) { thrB_lo = __ldcg(P.B.thr + blo); tB_lo = g_threshold(thrB_lo, P.ib, P.key_lo, pconst); }
+      if (vhi) { thrB_hi = __ldcg(P.B.thr + bhi); tB_hi = g_threshold(thrB_hi, P.ib, P.key_lo, pconst); }
     }
 
     for (uint32_t a = g.a0; a < g.a1; ++a) {
-      const uint32_t oa = __ldg(P.A.perm + a);
-      uint32_t thrA = 0u;
-      if (listsA) thrA = __ldcg(P.A.thr + a);
+      const uint32_t thrA = listsA ? __ldcg(P.A.thr + a) : 0u;
       const uint32_t* arow = P.a_enc + S.aenc_base + (size_t)(a - S.a_beg) * (uint32_t)la;
       const uint32_t res = dp_word<LB>(arow, la, brow, P.C1, P.C2);
-      const int s_lo = (int)(int16_t)(res & 0xffffu) + pconst;
-      const int s_hi = (int)(int16_t)(res >> 16) + pconst;
+      const int g_lo = (int)(res & 0xffffu);  // G >= 0
+      const int g_hi = (int)(res >> 16);
       const bool ok_lo = pair_valid(g, a, blo);
       const bool ok_hi = pair_valid(g, a, bhi);
 
       if (P.mode == kModeMatrix) {
+        const uint32_t oa = __ldg(P.A.perm + a);
         if (ok_lo) {
           const uint64_t i = oa < ob_lo ? oa : ob_lo, j = oa < ob_lo ? ob_lo : oa;
-          P.mat[upper_offset(i, j, P.n)] = (int8_t)s_lo;
+          P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_lo + pconst);
         }
         if (ok_hi) {
           const uint64_t i = oa < ob_hi ? oa : ob_hi, j = oa < ob_hi ? ob_hi : oa;
-          P.mat[upper_offset(i, j, P.n)] = (int8_t)s_hi;
+          P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_hi + pconst);
         }
         continue;
       }
 
       if (P.hist_mode != kHistNone) {
-        if (ok_lo) hist_add(P, wh, s_lo);
-        if (ok_hi) hist_add(P, wh, s_hi);
-        if (use_smem_hist) {
+        if (ok_lo) hist_add(P, wh, lane, g_lo + hoff);
+        if (ok_hi) hist_add(P, wh, lane, g_hi + hoff);
+        if (smem_hist) {
           wpairs += 64;
           if (wpairs >= (1ull << 30)) { hist_flush(P, wh, lane); wpairs = 0; }
         }
       }
-      // B-side lists: the lane's own words take the A word as a neighbour.
-      if (listsB) {
-        if (ok_lo && s_lo >= sthrB_lo) {
-          const uint32_t key = ((uint32_t)(s_lo - P.key_lo) << P.ib) | (P.imask - oa);
-          if (key > thrB_lo) {
-            const uint32_t nm = list_offer(P.B.slots + (size_t)blo * P.k, P.B.thr + blo, P.k, key, P.err, inserts);
-            if (nm > thrB_lo) { thrB_lo = nm; sthrB_lo = score_threshold(nm, P.ib, P.key_lo); }
+      // One compare per half against the lower of the two lists' bounds; the
+      // exact keys are formed only for the rare candidates.
+      const int tA = listsA ? g_threshold(thrA, P.ib, P.key_lo, pconst) : INT_MAX;
+      const bool c_lo = ok_lo && g_lo >= min(tB_lo, tA);
+      const bool c_hi = ok_hi && g_hi >= min(tB_hi, tA);
+      if (c_lo || c_hi) {
+        const uint32_t oa = __ldg(P.A.perm + a);
+        uint32_t* rowA = listsA ? P.A.slots + (size_t)a * P.k : nullptr;
+        if (c_lo) {
+          const uint32_t s = (uint32_t)(g_lo + pconst - P.key_lo);
+          if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
+            const uint32_t key = (s << P.ib) | (P.imask - oa);
+            if (key > thrB_lo) {
+              const uint32_t nm = list_offer(P.B.slots + (size_t)blo * P.k, P.B.thr + blo, P.k, key, P.err, inserts);
+              if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_threshold(nm, P.ib, P.key_lo, pconst); }
+            }
+          }
+          if (g_lo >= tA) {     // the A word takes the lane's word as a neighbour
+            const uint32_t key = (s << P.ib) | (P.imask - ob_lo);
+            if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
           }
         }
-        if (ok_hi && s_hi >= sthrB_hi) {
-          const uint32_t key = ((uint32_t)(s_hi - P.key_lo) << P.ib) | (P.imask - oa);
-          if (key > thrB_hi) {
-            const uint32_t nm = list_offer(P.B.slots + (size_t)bhi * P.k, P.B.thr + bhi, P.k, key, P.err, inserts);
-            if (nm > thrB_hi) { thrB_hi = nm; sthrB_hi = score_threshold(nm, P.ib, P.key_lo); }
+        if (c_hi) {
+          const uint32_t s = (uint32_t)(g_hi + pconst - P.key_lo);
+          if (g_hi >= tB_hi) {
+            const uint32_t key = (s << P.ib) | (P.imask - oa);
+            if (key > thrB_hi) {
+              const uint32_t nm = list_offer(P.B.slots + (size_t)bhi * P.k, P.B.thr + bhi, P.k, key, P.err, inserts);
+              if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_threshold(nm, P.ib, P.key_lo, pconst); }
+            }
           }
-        }
-      }
-      // A-side list: the warp's A word takes the lanes' words as neighbours.
-      if (listsA) {
-        const int sthrA = score_threshold(thrA, P.ib, P.key_lo);
-        const bool c_lo = ok_lo && s_lo >= sthrA;
-        const bool c_hi = ok_hi && s_hi >= sthrA;
-        if (__any_sync(0xffffffffu, c_lo || c_hi)) {
-          uint32_t* row = P.A.slots + (size_t)a * P.k;
-          if (c_lo) {
-            const uint32_t key = ((uint32_t)(s_lo - P.key_lo) << P.ib) | (P.imask - ob_lo);
-            if (key > thrA) list_offer(row, P.A.thr + a, P.k, key, P.err, inserts);
-          }
-          if (c_hi) {
-            const uint32_t key = ((uint32_t)(s_hi - P.key_lo) << P.ib) | (P.imask - ob_hi);
-            if (key > thrA) list_offer(row, P.A.thr + a, P.k, key, P.err, inserts);
+          if (g_hi >= tA) {
+            const uint32_t key = (s << P.ib) | (P.imask - ob_hi);
+            if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
           }
         }
       }
     }
   }
 
-  if (use_smem_hist) hist_flush(P, wh, lane);
+  if (smem_hist) hist_flush(P, wh, lane);
   if (P.stats) {
     for (int o = 16; o > 0; o >>= 1) inserts += __shfl_xor_sync(0xffffffffu, inserts, o);
     if (lane == 0 && inserts) atomicAdd(P.stats, (unsigned long long)inserts);

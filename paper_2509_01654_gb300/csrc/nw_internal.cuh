@@ -111,7 +111,21 @@ struct SideView {
 };
 
 enum { kModeMatrix = 0, kModeLists = 1 };
-enum { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2 };
+enum { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2, kHistLane = 3 };
+
+// Histogram accumulation mode for `nbins` bins and the dynamic shared memory
+// it needs per block: per-lane columns while they fit in 48 KiB, else one
+// shared array per warp, else global atomics.
+inline int hist_mode_for(uint32_t nbins) {
+  if ((size_t)nbins * 32u * sizeof(uint32_t) * kWarpsPerBlock <= 48u * 1024u) return kHistLane;
+  if (nbins <= kHistSmemMaxBins) return kHistSmem;
+  return kHistGlobal;
+}
+inline size_t hist_smem_bytes(int mode, uint32_t nbins) {
+  if (mode == kHistLane) return (size_t)kWarpsPerBlock * nbins * 32u * sizeof(uint32_t);
+  if (mode == kHistSmem) return (size_t)kWarpsPerBlock * nbins * sizeof(uint32_t);
+  return 0;
+}
 
 struct DpParams {
   const Seg* segs;
@@ -122,7 +136,7 @@ struct DpParams {
   const uint32_t* a_enc;          // A set
   const uint4* b_rec;             // B set
   SideView A, B;
-  uint32_t C1, C2;                // packed (s'_m + 1) and s'_x, see the kernel
+  uint32_t C1, C2;                // packed (s'_m + 1) and max(s'_x, 0), see the kernel
   int32_t gap;
   int32_t mode;
   int8_t* mat;                    // matrix mode: row-major upper triangle

@@ -4,6 +4,7 @@
 #include <limits.h>
 #include <stdint.h>
 
+#include "nw_dp.cuh"
 #include "nw_launch.h"
 
 namespace nw {
@@ -207,19 +208,20 @@ __global__ void __launch_bounds__(kRateBlock) rate_kernel(const uint32_t* __rest
   if (threadIdx.x == 0) atomicAdd(cycles, (unsigned long long)(t1 - t0));
 }
 
-// The alignment core alone: each thread aligns an 8-symbol word from shared
-// memory against two 16-symbol words held in registers, repeatedly.
+// The alignment core alone (the kernel's dp_row, rows two at a time): each
+// thread aligns an 8-symbol word from shared memory against two 16-symbol
+// words held in registers, repeatedly.
 __global__ void __launch_bounds__(kRateBlock) rate_cell_kernel(const uint32_t* __restrict__ in,
                                                                uint32_t* __restrict__ out, int iters,
                                                                unsigned long long* cycles) {
   constexpr int LB = 16, LA = 8;
   __shared__ uint32_t sa[LA * 4];
-  if (threadIdx.x < LA * 4) sa[threadIdx.x] = in[threadIdx.x & 15] & 0x003f003fu;
+  if (threadIdx.x < LA * 4) sa[threadIdx.x] = (in[threadIdx.x & 15] & 0x001f001fu) << 1;
   __syncthreads();
-  uint32_t b[LB];
+  BRow<LB> b;
 #pragma unroll
-  for (int j = 0; j < LB; ++j) b[j] = ~(in[(j + threadIdx.x) & 15] & 0x003f003fu);
-  const uint32_t C1 = 0x00040004u, C2 = 0x00010001u;
+  for (int j = 0; j < LB; ++j) b.v[j] = ~((in[(j + threadIdx.x) & 15] & 0x001f001fu) << 1);
+  const uint32_t C1 = 0x00040004u, C2 = 0x00010001u;  // scoring (+1, -1, -1)
   uint32_t acc = 0;
   const long long t0 = clock64();
   for (int it = 0; it < iters; ++it) {
@@ -228,20 +230,9 @@ __global__ void __launch_bounds__(kRateBlock) rate_cell_kernel(const uint32_t* _
     for (int j = 0; j < LB; ++j) G[j] = acc & 1u;
     const uint32_t* arow = sa + (it & 3) * LA;
 #pragma unroll 1
-    for (int i = 0; i < LA; ++i) {
-      const uint32_t a2 = arow[i];
-      uint32_t diag = 0u, left = 0u;
-#pragma unroll
-      for (int j = 0; j < LB; ++j) {
-        const uint32_t xt = a2 ^ b[j];
-        const uint32_t f = __viaddmax_s16x2(xt, C1, C2);
-        const uint32_t up = G[j];
-        const uint32_t m = __vimax_s16x2_relu(up, left);
-        const uint32_t h = __viaddmax_s16x2(diag, f, m);
-        diag = up;
-        G[j] = h;
-        left = h;
-      }
+    for (int i = 0; i < LA; i += 2) {
+      dp_row<LB>(G, arow[i], b, C1, C2);
+      dp_row<LB>(G, arow[i + 1], b, C1, C2);
     }
     acc += G[LB - 1];
   }
