@@ -532,9 +532,11 @@ nw_status run_plan(nw_ctx* c, const Plan& plan, const Seg* d_segs, const DpParam
     P.A = *A_by_role[lp.role];
     P.b_rec = b_rec_by_role[lp.role];
     P.B = *B_by_role[lp.role];
-    const size_t smem = hist_smem_bytes(P.hist_mode, P.nbins);
-    const void* fn = dp_kernel(lp.LB);
+    const size_t smem = hist_smem_bytes(P.hist_mode, P.nbins) + dp_stage_bytes(lp.LB);
+    const int epi = P.mode == kModeMatrix ? kEpiMatrix : (P.hist_mode == kHistLane ? kEpiListsLaneHist : kEpiLists);
+    const void* fn = dp_kernel(lp.LB, epi);
     if (!fn) return set_err(c, NW_EINVAL, "no kernel for length %d", lp.LB);
+    NW_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     NW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, smem));
     if (occ < 1) occ = 1;
@@ -613,6 +615,8 @@ nw_status topk_impl(nw_dict* d, uint32_t shard, uint32_t nshards, uint32_t k, ui
   base.TA = kDefaultTA;
   base.C1 = d->ss.C1;
   base.C2 = d->ss.C2;
+  base.match = d->sc.match;
+  base.mismatch = d->sc.mismatch;
   base.gap = d->sc.gap;
   base.mode = kModeLists;
   base.k = k;
@@ -845,6 +849,8 @@ nw_status nw_all_pairs_matrix(nw_dict* d, int8_t* out, uint32_t flags) {
   base.TA = kDefaultTA;
   base.C1 = d->ss.C1;
   base.C2 = d->ss.C2;
+  base.match = d->sc.match;
+  base.mismatch = d->sc.mismatch;
   base.gap = d->sc.gap;
   base.mode = kModeMatrix;
   base.mat = dst;
@@ -1046,6 +1052,8 @@ nw_status nw_query(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, 
   base.TA = kDefaultTA;
   base.C1 = d->ss.C1;
   base.C2 = d->ss.C2;
+  base.match = d->sc.match;
+  base.mismatch = d->sc.mismatch;
   base.gap = d->sc.gap;
   base.mode = kModeLists;
   base.k = k;
@@ -1270,6 +1278,8 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
   P.TA = kDefaultTA;
   P.C1 = d->ss.C1;
   P.C2 = d->ss.C2;
+  P.match = d->sc.match;
+  P.mismatch = d->sc.mismatch;
   P.gap = d->sc.gap;
   P.mode = kModeLists;
   P.k = k;

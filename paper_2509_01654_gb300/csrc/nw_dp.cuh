@@ -58,6 +58,20 @@ __device__ __forceinline__ void dp_row(uint32_t (&G)[LB], uint32_t a2, const BRo
   }
 }
 
+// The first row (i = 1): diag and up are G[0][*] = 0 and f, left >= 0, so
+// the cell is max(f, left) and no row of zeros needs setting up.
+template <int LB>
+__device__ __forceinline__ void dp_row_first(uint32_t (&G)[LB], uint32_t a2, const BRow<LB>& b, uint32_t C1,
+                                             uint32_t C2) {
+  uint32_t left = 0u;
+#pragma unroll
+  for (int j = 0; j < LB; ++j) {
+    const uint32_t f = __viaddmax_s16x2(a2 ^ b.v[j], C1, C2);
+    left = __vimax_s16x2_relu(f, left);
+    G[j] = left;
+  }
+}
+
 // DP over the la rows of one A word against the lane's two B words; returns
 // the packed G[la][LB] (0 when la == 0 or LB == 0).
 template <int LB>
@@ -78,6 +92,31 @@ __device__ __forceinline__ uint32_t dp_word(const uint32_t* __restrict__ arow, i
       dp_row<LB>(G, a1, b, C1, C2);
     }
     if (i < la) dp_row<LB>(G, __ldg(arow + i), b, C1, C2);
+    return G[LB - 1];
+  }
+}
+
+// The same DP with the A word's symbols in shared memory, symbol i at
+// acol[32 * i] (the staging layout of the all-pairs kernel; every lane reads
+// the same address, so each load is a broadcast).
+template <int LB>
+__device__ __forceinline__ uint32_t dp_word_staged(const uint32_t* acol, int la, const BRow<LB>& b, uint32_t C1,
+                                                   uint32_t C2) {
+  if constexpr (LB == 0) {
+    return 0u;
+  } else {
+    if (la == 0) return 0u;
+    uint32_t G[LB];
+    dp_row_first<LB>(G, acol[0], b, C1, C2);
+    int i = 1;
+#pragma unroll 1
+    for (; i + 1 < la; i += 2) {
+      const uint32_t a0 = acol[32 * i];
+      const uint32_t a1 = acol[32 * (i + 1)];
+      dp_row<LB>(G, a0, b, C1, C2);
+      dp_row<LB>(G, a1, b, C1, C2);
+    }
+    if (i < la) dp_row<LB>(G, acol[32 * i], b, C1, C2);
     return G[LB - 1];
   }
 }
@@ -173,22 +212,43 @@ __device__ __forceinline__ int g_threshold(uint32_t thr_key, uint32_t ib, int32_
   return thr_key == 0u ? INT_MIN : (int)(thr_key >> ib) + key_lo - pconst;
 }
 
-template <int LB>
-__global__ void __launch_bounds__(kBlock) nw_dp_kernel(const DpParams P) {
-  extern __shared__ uint32_t s_hist[];
+// Lowest and highest score any pair of lengths la <= lb can reach: the
+// all-gap alignment and the alignment with min(la, lb) diagonal columns bound
+// the optimum from below, and no alignment beats the diagonal one with every
+// diagonal column a match from above (for gap <= 0; with gap > 0 the all-gap
+// alignment is the larger).
+__device__ __forceinline__ void pair_score_bounds(const DpParams& P, int la, int lb, int& lo, int& hi) {
+  const int allgap = (la + lb) * P.gap;
+  const int diag_lo = la * P.mismatch + (lb - la) * P.gap;
+  const int diag_hi = la * P.match + (lb - la) * P.gap;
+  lo = allgap > diag_lo ? allgap : diag_lo;
+  hi = allgap > diag_hi ? allgap : diag_hi;
+}
+
+// The all-pairs kernel.  EPI selects the per-pair epilogue at compile time:
+// kEpiMatrix writes the int8 upper triangle, kEpiLists updates neighbour lists
+// (and a shared or global histogram), kEpiListsLaneHist updates lists and the
+// per-lane shared histogram columns.
+template <int LB, int EPI>
+__global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const DpParams P) {
+  extern __shared__ uint32_t s_dyn[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const bool smem_hist = P.hist_mode == kHistLane || P.hist_mode == kHistSmem;
-  const uint32_t wstride = P.hist_mode == kHistLane ? P.nbins * 32u : P.nbins;
-  uint32_t* wh = s_hist + (size_t)wib * wstride;
+  const bool smem_hist = EPI == kEpiListsLaneHist || (EPI == kEpiLists && P.hist_mode == kHistSmem);
+  const uint32_t wstride = EPI == kEpiListsLaneHist ? P.nbins * 32u : (smem_hist ? P.nbins : 0u);
+  uint32_t* wh = s_dyn + (size_t)wib * wstride;
+  // this warp's staging area: symbol i of the chunk's word w at sA[32 * i + w],
+  // followed by the 32 words' list bounds (raw keys) at sT[w]
+  uint32_t* sA = s_dyn + (size_t)kWarpsPerBlock * wstride + (size_t)wib * 32u * (uint32_t)(LB + 1);
+  uint32_t* sT = sA + 32u * (uint32_t)LB;
   if (smem_hist) {
     for (uint32_t q = lane; q < wstride; q += 32) wh[q] = 0u;
     __syncwarp();
   }
   uint64_t wpairs = 0;
   uint32_t inserts = 0;
-  const bool listsA = P.A.slots != nullptr;
-  const bool listsB = P.B.slots != nullptr;
+  const bool listsA = EPI != kEpiMatrix && P.A.slots != nullptr;
+  const bool listsB = EPI != kEpiMatrix && P.B.slots != nullptr;
 
   for (;;) {
     unsigned long long t = 0;
@@ -202,9 +262,23 @@ __global__ void __launch_bounds__(kBlock) nw_dp_kernel(const DpParams P) {
     const uint32_t bhi = blo + 1u;
     const bool vlo = blo < g.bend;
     const bool vhi = bhi < g.bend;
+    const bool check = g.tri && g.a1 > g.b0;  // the task straddles the diagonal: test a < b
     const int la = S.la;
     const int pconst = P.gap * (la + LB);  // score = G + pconst
     const int hoff = pconst - P.hist_lo;   // histogram bin = G + hoff
+
+    // every bin this task can produce lies inside the histogram (proven
+    // bounds); checked once here instead of per pair
+    bool hist_on = EPI != kEpiMatrix && P.hist_mode != kHistNone;
+    if (hist_on) {
+      int lo, hi;
+      pair_score_bounds(P, la, LB, lo, hi);
+      if (lo < P.hist_lo || hi - P.hist_lo >= (int)P.nbins) {
+        if (lane == 0) atomicOr(P.err, kErrHistRange);
+        hist_on = false;
+      }
+    }
+    uint32_t* hcol = wh + (ptrdiff_t)lane + (ptrdiff_t)hoff * 32;  // lane column shifted so bin = G
 
     BRow<LB> brow;
     if constexpr (LB > 0) {
@@ -222,73 +296,99 @@ __global__ void __launch_bounds__(kBlock) nw_dp_kernel(const DpParams P) {
       if (vhi) { thrB_hi = __ldcg(P.B.thr + bhi); tB_hi = g_threshold(thrB_hi, P.ib, P.key_lo, pconst); }
     }
 
-    for (uint32_t a = g.a0; a < g.a1; ++a) {
-      const uint32_t thrA = listsA ? __ldcg(P.A.thr + a) : 0u;
-      const uint32_t* arow = P.a_enc + S.aenc_base + (size_t)(a - S.a_beg) * (uint32_t)la;
-      const uint32_t res = dp_word<LB>(arow, la, brow, P.C1, P.C2);
-      const int g_lo = (int)(res & 0xffffu);  // G >= 0
-      const int g_hi = (int)(res >> 16);
-      const bool ok_lo = pair_valid(g, a, blo);
-      const bool ok_hi = pair_valid(g, a, bhi);
-
-      if (P.mode == kModeMatrix) {
-        const uint32_t oa = __ldg(P.A.perm + a);
-        if (ok_lo) {
-          const uint64_t i = oa < ob_lo ? oa : ob_lo, j = oa < ob_lo ? ob_lo : oa;
-          P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_lo + pconst);
-        }
-        if (ok_hi) {
-          const uint64_t i = oa < ob_hi ? oa : ob_hi, j = oa < ob_hi ? ob_hi : oa;
-          P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_hi + pconst);
-        }
-        continue;
+    for (uint32_t c0 = g.a0; c0 < g.a1; c0 += 32u) {
+      // Stage 32 A words: lane l copies word c0 + l (la symbols) and its list
+      // bound; the warp then reads symbols as shared-memory broadcasts and the
+      // G-space bound by shuffle.
+      const uint32_t nA = g.a1 - c0 < 32u ? g.a1 - c0 : 32u;
+      const uint32_t my_a = c0 + (uint32_t)lane;
+      const bool have = (uint32_t)lane < nA;
+      const uint32_t my_orig = (EPI == kEpiMatrix && have) ? __ldg(P.A.perm + my_a) : 0u;
+      const uint32_t my_thr = (listsA && have) ? __ldcg(P.A.thr + my_a) : 0u;
+      const int my_tA = listsA ? g_threshold(my_thr, P.ib, P.key_lo, pconst) : INT_MAX;
+      __syncwarp();
+      if (have) {
+        const uint32_t* src = P.a_enc + S.aenc_base + (size_t)(my_a - S.a_beg) * (uint32_t)la;
+        for (int i = 0; i < la; ++i) sA[32 * i + lane] = __ldg(src + i);
+        sT[lane] = my_thr;
       }
+      __syncwarp();
 
-      if (P.hist_mode != kHistNone) {
-        if (ok_lo) hist_add(P, wh, lane, g_lo + hoff);
-        if (ok_hi) hist_add(P, wh, lane, g_hi + hoff);
-        if (smem_hist) {
-          wpairs += 64;
-          if (wpairs >= (1ull << 30)) { hist_flush(P, wh, lane); wpairs = 0; }
+      for (uint32_t w = 0; w < nA; ++w) {
+        const uint32_t a = c0 + w;
+        const uint32_t res = dp_word_staged<LB>(sA + w, la, brow, P.C1, P.C2);
+        const int g_lo = (int)(res & 0xffffu);  // G >= 0
+        const int g_hi = (int)(res >> 16);
+        bool ok_lo = vlo, ok_hi = vhi;
+        if (check) {
+          ok_lo = ok_lo && a < blo;
+          ok_hi = ok_hi && a < bhi;
         }
-      }
-      // One compare per half against the lower of the two lists' bounds; the
-      // exact keys are formed only for the rare candidates.
-      const int tA = listsA ? g_threshold(thrA, P.ib, P.key_lo, pconst) : INT_MAX;
-      const bool c_lo = ok_lo && g_lo >= min(tB_lo, tA);
-      const bool c_hi = ok_hi && g_hi >= min(tB_hi, tA);
-      if (c_lo || c_hi) {
-        const uint32_t oa = __ldg(P.A.perm + a);
-        uint32_t* rowA = listsA ? P.A.slots + (size_t)a * P.k : nullptr;
-        if (c_lo) {
-          const uint32_t s = (uint32_t)(g_lo + pconst - P.key_lo);
-          if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
-            const uint32_t key = (s << P.ib) | (P.imask - oa);
-            if (key > thrB_lo) {
-              const uint32_t nm = list_offer(P.B.slots + (size_t)blo * P.k, P.B.thr + blo, P.k, key, P.err, inserts);
-              if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_threshold(nm, P.ib, P.key_lo, pconst); }
+
+        if constexpr (EPI == kEpiMatrix) {
+          const uint32_t oa = __shfl_sync(0xffffffffu, my_orig, (int)w);
+          if (ok_lo) {
+            const uint64_t i = oa < ob_lo ? oa : ob_lo, j = oa < ob_lo ? ob_lo : oa;
+            P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_lo + pconst);
+          }
+          if (ok_hi) {
+            const uint64_t i = oa < ob_hi ? oa : ob_hi, j = oa < ob_hi ? ob_hi : oa;
+            P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_hi + pconst);
+          }
+        } else {
+          if (hist_on) {
+            if constexpr (EPI == kEpiListsLaneHist) {
+              if (ok_lo) atomicAdd(hcol + 32 * g_lo, 1u);
+              if (ok_hi) atomicAdd(hcol + 32 * g_hi, 1u);
+            } else {
+              if (ok_lo) hist_add(P, wh, lane, g_lo + hoff);
+              if (ok_hi) hist_add(P, wh, lane, g_hi + hoff);
             }
           }
-          if (g_lo >= tA) {     // the A word takes the lane's word as a neighbour
-            const uint32_t key = (s << P.ib) | (P.imask - ob_lo);
-            if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
-          }
-        }
-        if (c_hi) {
-          const uint32_t s = (uint32_t)(g_hi + pconst - P.key_lo);
-          if (g_hi >= tB_hi) {
-            const uint32_t key = (s << P.ib) | (P.imask - oa);
-            if (key > thrB_hi) {
-              const uint32_t nm = list_offer(P.B.slots + (size_t)bhi * P.k, P.B.thr + bhi, P.k, key, P.err, inserts);
-              if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_threshold(nm, P.ib, P.key_lo, pconst); }
+          // One compare per half against the lower of the two lists' bounds;
+          // exact keys are formed only for the rare candidates.
+          const int tA = __shfl_sync(0xffffffffu, my_tA, (int)w);
+          const bool c_lo = ok_lo && g_lo >= min(tB_lo, tA);
+          const bool c_hi = ok_hi && g_hi >= min(tB_hi, tA);
+          if (c_lo || c_hi) {
+            const uint32_t oa = __ldg(P.A.perm + a);
+            const uint32_t thrA = sT[w];
+            uint32_t* rowA = listsA ? P.A.slots + (size_t)a * P.k : nullptr;
+            if (c_lo) {
+              const uint32_t s = (uint32_t)(g_lo + pconst - P.key_lo);
+              if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
+                const uint32_t key = (s << P.ib) | (P.imask - oa);
+                if (key > thrB_lo) {
+                  const uint32_t nm = list_offer(P.B.slots + (size_t)blo * P.k, P.B.thr + blo, P.k, key, P.err, inserts);
+                  if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_threshold(nm, P.ib, P.key_lo, pconst); }
+                }
+              }
+              if (g_lo >= tA) {  // the A word takes the lane's word as a neighbour
+                const uint32_t key = (s << P.ib) | (P.imask - ob_lo);
+                if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
+              }
             }
-          }
-          if (g_hi >= tA) {
-            const uint32_t key = (s << P.ib) | (P.imask - ob_hi);
-            if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
+            if (c_hi) {
+              const uint32_t s = (uint32_t)(g_hi + pconst - P.key_lo);
+              if (g_hi >= tB_hi) {
+                const uint32_t key = (s << P.ib) | (P.imask - oa);
+                if (key > thrB_hi) {
+                  const uint32_t nm = list_offer(P.B.slots + (size_t)bhi * P.k, P.B.thr + bhi, P.k, key, P.err, inserts);
+                  if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_threshold(nm, P.ib, P.key_lo, pconst); }
+                }
+              }
+              if (g_hi >= tA) {
+                const uint32_t key = (s << P.ib) | (P.imask - ob_hi);
+                if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
+              }
+            }
           }
         }
       }
+    }
+    if (smem_hist) {  // 32-bit shared counters: flush long before they could wrap
+      wpairs += (uint64_t)(g.a1 - g.a0) * 64u;
+      if (wpairs >= (1ull << 30)) { hist_flush(P, wh, lane); wpairs = 0; }
     }
   }
 

@@ -113,6 +113,20 @@ struct SideView {
 enum { kModeMatrix = 0, kModeLists = 1 };
 enum { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2, kHistLane = 3 };
 
+// Blocks per SM the alignment kernel is compiled for: the register budget
+// shrinks with LB (the lane keeps LB registers of B symbols and LB of DP row).
+__host__ __device__ constexpr int dp_min_blocks(int LB) { return LB <= 10 ? 4 : (LB <= 20 ? 3 : 2); }
+
+// Shared memory each block of the LB kernel stages A words in: every warp
+// holds 32 words of at most LB symbols and their 32 list bounds (after the
+// histogram area).
+__host__ __device__ constexpr size_t dp_stage_bytes(int LB) {
+  return (size_t)kWarpsPerBlock * 32u * (size_t)(LB + 1) * sizeof(uint32_t);
+}
+
+// per-pair epilogue of the all-pairs kernel (a template parameter)
+enum { kEpiMatrix = 0, kEpiLists = 1, kEpiListsLaneHist = 2, kEpiKinds = 3 };
+
 // Histogram accumulation mode for `nbins` bins and the dynamic shared memory
 // it needs per block: per-lane columns while they fit in 48 KiB, else one
 // shared array per warp, else global atomics.
@@ -137,7 +151,7 @@ struct DpParams {
   const uint4* b_rec;             // B set
   SideView A, B;
   uint32_t C1, C2;                // packed (s'_m + 1) and max(s'_x, 0), see the kernel
-  int32_t gap;
+  int32_t match, mismatch, gap;
   int32_t mode;
   int8_t* mat;                    // matrix mode: row-major upper triangle
   uint64_t n;

@@ -8,8 +8,8 @@
 
 namespace nw {
 
-// alignment kernel for the longer length LB (0 .. kMaxLen); nullptr if LB is out of range
-const void* dp_kernel(int LB);
+// alignment kernel for the longer length LB (0 .. kMaxLen) and epilogue kind; nullptr if out of range
+const void* dp_kernel(int LB, int epi);
 
 // ingest: stable bucketing by length and encoding of a word set
 cudaError_t launch_ingest_count(const uint8_t* codes, const uint32_t* offsets, uint32_t n,
