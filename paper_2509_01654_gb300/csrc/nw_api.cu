@@ -1102,9 +1102,9 @@ nw_status nw_measure_int_rates(nw_ctx* c, double ms_target, nw_int_rates* out) {
   if (!out) return set_err(c, NW_EINVAL, "null output pointer");
   if (ms_target <= 0) ms_target = 200;
   cudaStream_t s = c->stream;
-  const int blocks = c->sm_count * (2048 / kRateBlock);  // one full wave of 2048 threads per SM
+  const int max_blocks = c->sm_count * (2048 / kRateBlock);  // at most 2048 resident threads per SM
   DevBuf buf;
-  NW_TRY(ctx_alloc(c, buf, 4096 + sizeof(uint32_t) * (size_t)blocks * kRateBlock, "rate buffers"));
+  NW_TRY(ctx_alloc(c, buf, 4096 + sizeof(uint32_t) * (size_t)max_blocks * kRateBlock, "rate buffers"));
   struct BFree {
     nw_ctx* c;
     DevBuf& b;
@@ -1123,6 +1123,9 @@ nw_status nw_measure_int_rates(nw_ctx* c, double ms_target, nw_int_rates* out) {
   double clock_sum = 0;
   int clock_n = 0;
   for (int op = 0; op < kRateOps; ++op) {
+    // exactly one wave, so every block runs for the whole kernel and
+    // clock64 cycles per block over the event time give the SM clock
+    const int blocks = std::min(max_blocks, c->sm_count * rate_blocks_per_sm(op));
     int iters = op == kRateCell ? 64 : 2048;
     double ms = 0;
     unsigned long long cyc = 0;

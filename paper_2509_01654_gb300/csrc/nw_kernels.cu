@@ -243,6 +243,24 @@ __global__ void __launch_bounds__(kRateBlock) rate_cell_kernel(const uint32_t* _
 
 double rate_ops_per_iter(int op) { return op == kRateCell ? 8.0 * 16.0 : 8.0; }
 
+int rate_blocks_per_sm(int op) {
+  const void* fn = nullptr;
+  switch (op) {
+    case kRateViaddmax: fn = reinterpret_cast<const void*>(&rate_kernel<kRateViaddmax>); break;
+    case kRateVimax3: fn = reinterpret_cast<const void*>(&rate_kernel<kRateVimax3>); break;
+    case kRateVimaxRelu: fn = reinterpret_cast<const void*>(&rate_kernel<kRateVimaxRelu>); break;
+    case kRateIadd3: fn = reinterpret_cast<const void*>(&rate_kernel<kRateIadd3>); break;
+    case kRateLop3: fn = reinterpret_cast<const void*>(&rate_kernel<kRateLop3>); break;
+    default: fn = reinterpret_cast<const void*>(&rate_cell_kernel); break;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kRateBlock, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
 cudaError_t launch_rate(int op, int blocks, int iters, const uint32_t* in, uint32_t* out,
                         unsigned long long* cycles, cudaStream_t s) {
   switch (op) {

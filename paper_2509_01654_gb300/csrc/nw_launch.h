@@ -64,6 +64,8 @@ cudaError_t launch_rate(int op, int blocks, int iters, const uint32_t* in, uint3
                         unsigned long long* cycles, cudaStream_t s);
 // operations per thread per iteration of launch_rate for `op`
 double rate_ops_per_iter(int op);
+// resident blocks of launch_rate's kernel per SM (one full wave = SMs x this)
+int rate_blocks_per_sm(int op);
 constexpr int kRateBlock = 256;
 
 }  // namespace nw
