@@ -280,6 +280,19 @@ def run_ours(args, rank, world, local_rank):
     sha = kernel_sha()
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == sha else None
 
+    # the serving form of the same dictionary: open-loop Poisson load on the query server
+    serving_stats = None
+    if args.serving_requests > 0:
+        from paper_2509_01654_gb300 import serving
+        d = ctx.load_dictionary(codes_d, offs_d, 40, SCORING)
+        with nw.Server(d, k=k, max_batch_queries=8192, max_inflight=4) as srv:
+            serving_stats = serving.run_load(srv, synth.serving_queries(200_000), n_requests=args.serving_requests,
+                                             rate_hz=args.serving_rate, max_batch=4096)
+        d.free()
+        serving_stats["workload"] = (f"Poisson arrivals at {args.serving_rate:g}/s, request sizes log-uniform on "
+                                     f"[1, 4096] words of lengths U[1,30], exact top-{k} against the {n:,}-word "
+                                     f"dictionary")
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, rows, dt, threads = oracle_sample(w, float(os.environ.get("NW_CPU_BASELINE_S", "15")))
@@ -309,6 +322,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(idx_np.nbytes + score_np.nbytes + hist_np.nbytes),
                 "ms_per_step": total_e2e / len(e2e_times)},
         "gpu_launches": launches,
+        "serving": serving_stats,
     }
     print(json.dumps(line), flush=True)
 
@@ -321,6 +335,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=600_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=150,
+                    help="requests of the query-server load (0 skips it)")
+    ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrivals per second")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

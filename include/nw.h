@@ -194,6 +194,62 @@ nw_status nw_score_pairs(nw_dict *dict, const uint32_t *i, const uint32_t *j, si
 nw_status nw_query(nw_dict *dict, const uint8_t *qcodes, const uint32_t *qoffsets, uint32_t nq,
                    uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score, uint32_t flags);
 
+/* ---- serving: continuous batching of query requests ----
+ *
+ * A query service over one device-resident dictionary (Section 6's finding of
+ * similar-sounding words, run as a service).  Requests (each a CSR batch of
+ * query words) are queued by nw_server_submit from any thread.  A worker
+ * thread packs queued requests into GPU batches of at most max_batch_queries
+ * words and runs each batch on its own stream, with up to max_inflight
+ * batches on the device at once: requests that arrive while others run are
+ * admitted as soon as a batch slot frees.  Every slot's device buffers are
+ * allocated at creation and counted against mem_budget_bytes, which caps the
+ * number of slots (admission by memory).  Results are exact and do not depend
+ * on which requests share a batch: each query's k best dictionary neighbours,
+ * as nw_query returns them.  The dictionary must outlive the server. */
+typedef struct nw_server nw_server;
+
+typedef struct {
+    uint32_t k;                  /* neighbours per query, 1..NW_MAX_K */
+    uint32_t max_batch_queries;  /* words per GPU batch; also the largest request */
+    uint32_t max_inflight;       /* batches on the GPU at once (one stream each) */
+    uint32_t pad_;
+    size_t mem_budget_bytes;     /* device memory for the slots (0 = no cap) */
+} nw_server_config;
+
+typedef struct {
+    double submit_s, start_s, done_s; /* steady-clock seconds: queued, batch launched, results ready */
+    uint32_t nq;                      /* queries of the request */
+    uint32_t batch_queries;           /* queries in the batch that carried it */
+    uint32_t batch_requests;          /* requests in that batch */
+    uint32_t inflight_at_start;       /* batches already on the GPU when it launched */
+} nw_request_info;
+
+/* Creates a server for `dict` on the dictionary's device.  NW_ENOMEM if not
+ * even one batch slot fits the budget. */
+nw_status nw_server_create(nw_dict *dict, const nw_server_config *cfg, nw_server **out);
+
+/* Queues a request of nq host query words (CSR as in nw_load_dictionary;
+ * codes < the dictionary's alphabet; 1 <= nq <= max_batch_queries).  The
+ * words are copied; *request_id identifies the request. */
+nw_status nw_server_submit(nw_server *srv, const uint8_t *qcodes, const uint32_t *qoffsets, uint32_t nq,
+                           uint64_t *request_id);
+
+/* Waits up to timeout_ms (< 0: forever) for a request.  On completion copies
+ * its nq*k results to host nbr_idx/nbr_score (ranked as nw_query), fills
+ * *info (may be NULL), forgets the request and returns its status.  Returns
+ * NW_EBUSY if it is still pending, NW_EINVAL for an unknown id. */
+nw_status nw_server_wait(nw_server *srv, uint64_t request_id, int timeout_ms, uint32_t *nbr_idx,
+                         int16_t *nbr_score, nw_request_info *info);
+
+/* Message for the last failure of a server call or batch ("" if none); with
+ * srv == NULL, the message of the last failed nw_server_create on this thread. */
+const char *nw_server_last_error(const nw_server *srv);
+
+/* Stops the worker after the batches on the GPU finish, fails queued
+ * requests and frees the server. */
+void nw_server_destroy(nw_server *srv);
+
 /* ---- variant for callers that cannot allocate device memory ----
  *
  * No counterpart in the paper.  Some callers cannot allocate device memory

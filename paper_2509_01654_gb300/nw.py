@@ -31,6 +31,7 @@ EXPORTED = [
     "nw_load_dictionary", "nw_dict_info_get", "nw_dict_free", "nw_all_pairs_matrix",
     "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
     "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc", "nw_all_pairs_topk_noalloc",
+    "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -63,6 +64,17 @@ class IntRates(ctypes.Structure):
                 ("vimax_s16x2_relu", ctypes.c_double), ("iadd3", ctypes.c_double), ("lop3", ctypes.c_double),
                 ("nw_cell_mix", ctypes.c_double), ("sm_clock_mhz", ctypes.c_double), ("sm_count", ctypes.c_uint32),
                 ("pad_", ctypes.c_uint32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("pad_", ctypes.c_uint32), ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("nq", ctypes.c_uint32), ("batch_queries", ctypes.c_uint32), ("batch_requests", ctypes.c_uint32),
+                ("inflight_at_start", ctypes.c_uint32)]
 
 
 _lib = None
@@ -98,6 +110,13 @@ def load_library(path: str = LIB_PATH):
     L.nw_debug_enumerate_pairs.argtypes = [vp, u32, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
     L.nw_debug_fail_alloc.argtypes = [vp, u32]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
+    L.nw_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    L.nw_server_submit.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u64)]
+    L.nw_server_wait.argtypes = [vp, u64, ctypes.c_int, vp, vp, ctypes.POINTER(RequestInfo)]
+    L.nw_server_last_error.argtypes = [vp]
+    L.nw_server_last_error.restype = ctypes.c_char_p
+    L.nw_server_destroy.argtypes = [vp]
+    L.nw_server_destroy.restype = None
     _lib = L
     return L
 
@@ -360,3 +379,69 @@ def debug_enumerate_pairs(lengths, shard: int = 0, nshards: int = 1):
     if st != NW_OK:
         raise NwError(st, "nw_debug_enumerate_pairs failed")
     return a[:cnt.value], b[:cnt.value]
+
+
+class Server:
+    """nw_server_*: continuous-batching query service over a loaded dictionary."""
+
+    def __init__(self, dictionary: "Dictionary", k: int = 10, max_batch_queries: int = 8192, max_inflight: int = 4,
+                 mem_budget_bytes: int = 0):
+        L = load_library()
+        cfg = ServerConfig(k, max_batch_queries, max_inflight, 0, mem_budget_bytes)
+        h = ctypes.c_void_p()
+        st = L.nw_server_create(dictionary.handle, ctypes.byref(cfg), ctypes.byref(h))
+        if st != NW_OK:
+            raise NwError(st, (L.nw_server_last_error(None) or b"").decode())
+        self.handle = h
+        self.k = k
+        self.dictionary = dictionary  # keeps the dictionary alive
+
+    def _err(self, st):
+        raise NwError(st, (load_library().nw_server_last_error(self.handle) or b"").decode())
+
+    def submit(self, qcodes, qoffsets) -> int:
+        qcodes = np.ascontiguousarray(qcodes, dtype=np.uint8)
+        if qcodes.size == 0:
+            qcodes = np.zeros(1, np.uint8)
+        qoffsets = np.ascontiguousarray(qoffsets, dtype=np.uint32)
+        rid = ctypes.c_uint64(0)
+        st = load_library().nw_server_submit(self.handle, ctypes.c_void_p(qcodes.ctypes.data),
+                                             ctypes.c_void_p(qoffsets.ctypes.data), qoffsets.size - 1,
+                                             ctypes.byref(rid))
+        if st != NW_OK:
+            self._err(st)
+        self._pending_nq = getattr(self, "_pending_nq", {})
+        self._pending_nq[rid.value] = qoffsets.size - 1
+        return rid.value
+
+    def wait(self, request_id: int, timeout_ms: int = -1):
+        """(idx[nq, k] uint32, score[nq, k] int16, info dict) or None if still pending."""
+        nq = self._pending_nq[request_id]
+        idx = np.empty((nq, self.k), dtype=np.uint32)
+        sc = np.empty((nq, self.k), dtype=np.int16)
+        info = RequestInfo()
+        st = load_library().nw_server_wait(self.handle, request_id, timeout_ms, ctypes.c_void_p(idx.ctypes.data),
+                                           ctypes.c_void_p(sc.ctypes.data), ctypes.byref(info))
+        if st == NW_EBUSY:
+            return None
+        del self._pending_nq[request_id]
+        if st != NW_OK:
+            self._err(st)
+        return idx, sc, {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().nw_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
