@@ -194,6 +194,53 @@ nw_status nw_score_pairs(nw_dict *dict, const uint32_t *i, const uint32_t *j, si
 nw_status nw_query(nw_dict *dict, const uint8_t *qcodes, const uint32_t *qoffsets, uint32_t nq,
                    uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score, uint32_t flags);
 
+/* ---- batches of independent dictionaries ----
+ *
+ * Many dictionaries of uneven size, length range, alphabet and scoring (each
+ * the paper's problem on its own word list, Sections 4-5) reduced to per-word
+ * top-k lists in one CUDA-graph launch.  nw_batch_create loads every
+ * dictionary, plans all their pairs together (one alignment launch per longer
+ * length covering every dictionary), optionally autotunes the tile shape (A
+ * words per task) of each launch by timing candidates on the batch itself,
+ * and captures the whole reduction -- list resets, alignment launches, list
+ * finalisation -- into a CUDA graph.  nw_batch_run replays the graph and
+ * copies each dictionary's lists out.  Results equal nw_all_pairs_topk run on
+ * each dictionary alone.  The batch uses the context's stream and memory
+ * budget; the context must outlive it. */
+typedef struct nw_batch nw_batch;
+
+typedef struct {
+    const uint8_t *codes;      /* CSR words as in nw_load_dictionary */
+    const uint32_t *offsets;
+    uint32_t n;
+    uint32_t alphabet;
+    nw_scoring scoring;
+} nw_batch_dict;
+
+#define NW_BATCH_AUTOTUNE 0x10u /* nw_batch_create flag: time tile-shape candidates per launch */
+
+typedef struct {
+    uint32_t ndicts;
+    uint32_t launches;                          /* alignment launches in the graph */
+    uint64_t pairs, cells;                      /* over all dictionaries */
+    double tune_ms;                             /* time spent autotuning */
+    uint32_t words_per_task[NW_MAX_WORD_LEN + 1]; /* chosen A words per task by longer length (0: none) */
+} nw_batch_info;
+
+/* flags: NW_DEVICE_PTRS (the dictionaries' buffers are device pointers),
+ * NW_BATCH_AUTOTUNE.  k in [1, NW_MAX_K]. */
+nw_status nw_batch_create(nw_ctx *ctx, const nw_batch_dict *dicts, uint32_t ndicts, uint32_t k, uint32_t flags,
+                          nw_batch **out);
+
+/* Runs the graph.  nbr_idx[d] / nbr_score[d] receive dictionary d's n*k
+ * lists (ranked as nw_all_pairs_topk); host buffers, or device buffers with
+ * NW_DEVICE_PTRS. */
+nw_status nw_batch_run(nw_batch *batch, uint32_t *const *nbr_idx, int16_t *const *nbr_score, uint32_t flags);
+
+nw_status nw_batch_info_get(const nw_batch *batch, nw_batch_info *out);
+
+void nw_batch_free(nw_batch *batch);
+
 /* ---- serving: continuous batching of query requests ----
  *
  * A query service over one device-resident dictionary (Section 6's finding of

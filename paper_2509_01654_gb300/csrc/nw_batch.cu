@@ -1,0 +1,332 @@
+// nw_batch.cu -- nw_batch_*: many independent dictionaries reduced to per-word
+// top-k lists in one CUDA-graph launch.
+//
+// Every dictionary is loaded as usual (its own word set, scoring and score
+// bounds).  The pair plans of all dictionaries are merged by longer length:
+// the launch for length LB walks the LB segments of every dictionary, each
+// segment tagged with its dictionary, and the kernel (epilogue
+// kEpiBatchLists) reads that dictionary's word set, lists and scoring per
+// task.  The A-chunk size of each launch is a tile-shape parameter that the
+// autotuner picks by timing candidates on the batch.  The whole reduction is
+// captured once into a CUDA graph and replayed by nw_batch_run.
+#include <chrono>
+
+#include "nw_host.h"
+
+struct nw_batch {
+  nw_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;  // the batch's own stream (capture needs a non-legacy stream)
+  std::vector<nw_dict*> dicts;
+  uint32_t k = 0;
+  uint32_t ta_by_lb[kBuckets] = {0};
+  Plan plan;
+  std::vector<size_t> list_off;  // first list (word) of each dictionary in the combined arrays
+  size_t nlists = 0;
+  DevBuf d_segs, d_terms, d_slots, d_thr, d_small, d_out_idx, d_out_score;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double tune_ms = 0;
+};
+
+namespace {
+
+constexpr uint32_t kTaCandidates[] = {64, 128, 256, 512, 1024};
+
+// The segments of every dictionary whose longer length is LB, with A chunks of
+// `ta` words, appended as one launch (task0 rebased, dictionary tagged).
+void append_launch(const nw_batch* B, int LB, uint32_t ta, Plan& out) {
+  LaunchPlan lp;
+  lp.LB = LB;
+  lp.role = 0;
+  lp.ta = ta;
+  lp.seg_first = (uint32_t)out.segs.size();
+  uint64_t task = 0;
+  for (size_t d = 0; d < B->dicts.size(); ++d) {
+    Plan p;
+    plan_all_pairs(B->dicts[d]->ws.bk, ta, p);
+    for (const LaunchPlan& q : p.launches) {
+      if (q.LB != LB) continue;
+      for (uint32_t s = 0; s < q.nsegs; ++s) {
+        Seg g = p.segs[q.seg_first + s];
+        g.task0 += task;
+        g.dict = (uint32_t)d;
+        out.segs.push_back(g);
+      }
+      task += q.ntasks;
+      lp.pairs += q.pairs;
+      lp.cells += q.cells;
+    }
+  }
+  lp.nsegs = (uint32_t)out.segs.size() - lp.seg_first;
+  lp.ntasks = task;
+  if (lp.nsegs) {
+    out.pairs += lp.pairs;
+    out.cells += lp.cells;
+    out.launches.push_back(lp);
+  }
+}
+
+DpParams batch_params(nw_batch* B) {
+  DpParams P{};
+  P.TA = kDefaultTA;
+  P.mode = kModeLists;
+  P.k = B->k;
+  P.hist_mode = kHistNone;
+  P.stats = reinterpret_cast<unsigned long long*>(B->d_small.as<char>() + 8);
+  P.err = B->d_small.as<uint32_t>();
+  P.terms = B->d_terms.as<DictTerms>();
+  return P;
+}
+
+nw_status upload_plan(nw_batch* B, const Plan& plan) {
+  nw_ctx* c = B->ctx;
+  NW_TRY(ctx_ensure(c, B->d_segs, sizeof(Seg) * std::max<size_t>(1, plan.segs.size()), "batch segments"));
+  if (!plan.segs.empty())
+    NW_CK(cudaMemcpyAsync(B->d_segs.p, plan.segs.data(), sizeof(Seg) * plan.segs.size(), cudaMemcpyHostToDevice,
+                          B->stream));
+  return NW_OK;
+}
+
+// List resets and the alignment launches of `plan` on the context's stream.
+nw_status issue_lists(nw_batch* B, const Plan& plan) {
+  nw_ctx* c = B->ctx;
+  cudaStream_t s = B->stream;
+  NW_CK(cudaMemsetAsync(B->d_small.p, 0, B->d_small.bytes, s));
+  NW_CK(cudaMemsetAsync(B->d_slots.p, 0, sizeof(uint32_t) * B->nlists * B->k, s));
+  NW_CK(cudaMemsetAsync(B->d_thr.p, 0, sizeof(uint32_t) * B->nlists, s));
+  const DpParams P = batch_params(B);
+  SideView none{nullptr, nullptr, nullptr};
+  const uint32_t* a_enc[3] = {nullptr, nullptr, nullptr};
+  const uint4* b_rec[3] = {nullptr, nullptr, nullptr};
+  const SideView* views[3] = {&none, &none, &none};
+  const bool saved = c->profiling;
+  c->profiling = false;
+  Timer tm{c};
+  RunOut ro;
+  const nw_status st = run_plan(c, s, plan, B->d_segs.as<Seg>(), P,
+                                reinterpret_cast<unsigned long long*>(B->d_small.as<char>() + 64), 0, 1, tm, ro,
+                                a_enc, views, b_rec, views);
+  c->profiling = saved;
+  return st;
+}
+
+nw_status issue_finalize(nw_batch* B) {
+  nw_ctx* c = B->ctx;
+  for (size_t d = 0; d < B->dicts.size(); ++d) {
+    const nw_dict* D = B->dicts[d];
+    const uint32_t n = D->ws.n;
+    if (n == 0) continue;
+    const uint32_t ib = index_bits(std::max<uint32_t>(n, 2));
+    NW_CK(launch_finalize(B->d_slots.as<uint32_t>() + B->list_off[d] * B->k, n, B->k, D->ws.perm.as<uint32_t>(),
+                          ib, (uint32_t)(((uint64_t)1 << ib) - 1), D->score_lo - 1,
+                          B->d_out_idx.as<uint32_t>() + B->list_off[d] * B->k,
+                          B->d_out_score.as<int16_t>() + B->list_off[d] * B->k, B->stream));
+  }
+  return NW_OK;
+}
+
+// Times each launch length with each A-chunk candidate and keeps the fastest.
+nw_status autotune(nw_batch* B) {
+  nw_ctx* c = B->ctx;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaEvent_t e0, e1;
+  NW_CK(cudaEventCreate(&e0));
+  NW_CK(cudaEventCreate(&e1));
+  struct EvFree {
+    cudaEvent_t a, b;
+    ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } evfree{e0, e1};
+  for (int LB = 0; LB < kBuckets; ++LB) {
+    float best = 0;
+    uint32_t best_ta = 0;
+    for (uint32_t ta : kTaCandidates) {
+      Plan p;
+      append_launch(B, LB, ta, p);
+      if (p.launches.empty()) break;
+      NW_TRY(upload_plan(B, p));
+      float ms_min = 0;
+      for (int rep = 0; rep < 2; ++rep) {
+        NW_CK(cudaEventRecord(e0, B->stream));
+        NW_TRY(issue_lists(B, p));
+        NW_CK(cudaEventRecord(e1, B->stream));
+        NW_CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        NW_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep == 0 || ms < ms_min) ms_min = ms;
+      }
+      if (best_ta == 0 || ms_min < best) {
+        best = ms_min;
+        best_ta = ta;
+      }
+    }
+    if (best_ta) B->ta_by_lb[LB] = best_ta;  // lengths without pairs keep the default
+  }
+  B->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return NW_OK;
+}
+
+nw_status check_flags(nw_ctx* c, cudaStream_t stream, const uint32_t* d_err) {
+  uint32_t err = 0;
+  NW_CK(cudaMemcpyAsync(&err, d_err, sizeof err, cudaMemcpyDeviceToHost, stream));
+  NW_CK(cudaStreamSynchronize(stream));
+  if (err & kErrRetry) return set_err(c, NW_ETIMEOUT, "a neighbour-list update exceeded its retry bound");
+  if (err) return set_err(c, NW_EINVAL, "device-side error flag %u", err);
+  return NW_OK;
+}
+
+nw_status create_impl(nw_batch* B, const nw_batch_dict* dicts, uint32_t ndicts, uint32_t flags) {
+  nw_ctx* c = B->ctx;
+  for (uint32_t d = 0; d < ndicts; ++d) {
+    nw_dict* D = nullptr;
+    const nw_status st = nw_load_dictionary(c, dicts[d].codes, dicts[d].offsets, dicts[d].n, dicts[d].alphabet,
+                                            &dicts[d].scoring, flags & NW_DEVICE_PTRS, &D);
+    if (st != NW_OK) return st;
+    B->dicts.push_back(D);
+    const uint32_t ib = index_bits(std::max<uint32_t>(D->ws.n, 2));
+    if (D->score_lo < INT16_MIN + 1 || D->score_hi > INT16_MAX ||
+        (uint64_t)(D->score_hi - (D->score_lo - 1)) >= (1ull << (32 - ib)))
+      return set_err(c, NW_ERANGE, "dictionary %u: scores [%d, %d] do not fit the list keys", d, D->score_lo,
+                     D->score_hi);
+    B->list_off.push_back(B->nlists);
+    B->nlists += D->ws.n;
+  }
+  const size_t L = std::max<size_t>(1, B->nlists);
+  NW_TRY(ctx_alloc(c, B->d_slots, sizeof(uint32_t) * L * B->k, "batch list slots"));
+  NW_TRY(ctx_alloc(c, B->d_thr, sizeof(uint32_t) * L, "batch list bounds"));
+  NW_TRY(ctx_alloc(c, B->d_out_idx, sizeof(uint32_t) * L * B->k, "batch output indices"));
+  NW_TRY(ctx_alloc(c, B->d_out_score, sizeof(int16_t) * L * B->k, "batch output scores"));
+  NW_TRY(ctx_alloc(c, B->d_small, 64 + sizeof(unsigned long long) * (kBuckets + 2), "batch counters"));
+  std::vector<DictTerms> terms(std::max<size_t>(1, B->dicts.size()));
+  for (size_t d = 0; d < B->dicts.size(); ++d) {
+    const nw_dict* D = B->dicts[d];
+    const uint32_t ib = index_bits(std::max<uint32_t>(D->ws.n, 2));
+    DictTerms& T = terms[d];
+    T.a_enc = D->ws.a_enc.as<uint32_t>();
+    T.b_rec = D->ws.b_rec.as<uint4>();
+    T.perm = D->ws.perm.as<uint32_t>();
+    T.slots = B->d_slots.as<uint32_t>() + B->list_off[d] * B->k;
+    T.thr = B->d_thr.as<uint32_t>() + B->list_off[d];
+    T.C1 = D->ss.C1;
+    T.C2 = D->ss.C2;
+    T.match = D->sc.match;
+    T.mismatch = D->sc.mismatch;
+    T.gap = D->sc.gap;
+    T.key_lo = D->score_lo - 1;
+    T.ib = ib;
+    T.imask = (uint32_t)(((uint64_t)1 << ib) - 1);
+  }
+  NW_TRY(ctx_alloc(c, B->d_terms, sizeof(DictTerms) * terms.size(), "batch terms"));
+  NW_CK(cudaMemcpyAsync(B->d_terms.p, terms.data(), sizeof(DictTerms) * terms.size(), cudaMemcpyHostToDevice,
+                        B->stream));
+
+  for (int LB = 0; LB < kBuckets; ++LB) B->ta_by_lb[LB] = kDefaultTA;
+  if (flags & NW_BATCH_AUTOTUNE) NW_TRY(autotune(B));
+  B->plan = Plan{};
+  for (int LB = 0; LB < kBuckets; ++LB) append_launch(B, LB, B->ta_by_lb[LB], B->plan);
+  for (int LB = 0; LB < kBuckets; ++LB) {
+    bool present = false;
+    for (const LaunchPlan& lp : B->plan.launches) present |= lp.LB == LB;
+    if (!present) B->ta_by_lb[LB] = 0;
+  }
+  NW_TRY(upload_plan(B, B->plan));
+  // one uncaptured run sets the kernels' shared-memory attributes
+  NW_TRY(issue_lists(B, B->plan));
+  NW_TRY(issue_finalize(B));
+  NW_TRY(check_flags(c, B->stream, B->d_small.as<uint32_t>()));
+
+  NW_CK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+  nw_status st = issue_lists(B, B->plan);
+  if (st == NW_OK) st = issue_finalize(B);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
+  if (st != NW_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+  B->graph = g;
+  NW_CK(cudaGraphInstantiate(&B->exec, B->graph, 0));
+  return NW_OK;
+}
+
+void destroy_impl(nw_batch* B) {
+  nw_ctx* c = B->ctx;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (DevBuf* b : {&B->d_segs, &B->d_terms, &B->d_slots, &B->d_thr, &B->d_small, &B->d_out_idx, &B->d_out_score})
+    ctx_free(c, *b);
+  for (nw_dict* D : B->dicts) nw_dict_free(D);
+  if (B->stream) cudaStreamDestroy(B->stream);
+  delete B;
+}
+
+}  // namespace
+
+extern "C" {
+
+nw_status nw_batch_create(nw_ctx* ctx, const nw_batch_dict* dicts, uint32_t ndicts, uint32_t k, uint32_t flags,
+                          nw_batch** out) {
+  if (!ctx || !out) return NW_EINVAL;
+  *out = nullptr;
+  if (!dicts && ndicts) return set_err(ctx, NW_EINVAL, "null dictionary array");
+  if (k == 0 || k > NW_MAX_K) return set_err(ctx, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
+  nw_batch* B = new nw_batch();
+  B->ctx = ctx;
+  B->k = k;
+  nw_status st = NW_OK;
+  if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess)
+    st = cuda_fail(ctx, cudaGetLastError(), "cudaStreamCreateWithFlags");
+  if (st == NW_OK) st = create_impl(B, dicts, ndicts, flags);
+  if (st != NW_OK) {
+    const std::string msg = ctx->err;
+    destroy_impl(B);
+    ctx->err = msg;
+    return st;
+  }
+  *out = B;
+  return NW_OK;
+}
+
+nw_status nw_batch_run(nw_batch* B, uint32_t* const* nbr_idx, int16_t* const* nbr_score, uint32_t flags) {
+  if (!B) return NW_EINVAL;
+  nw_ctx* c = B->ctx;
+  NW_ENTER(c);
+  if (!nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null output arrays");
+  const bool dev = flags & NW_DEVICE_PTRS;
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  NW_CK(cudaGraphLaunch(B->exec, B->stream));
+  for (size_t d = 0; d < B->dicts.size(); ++d) {
+    const size_t cnt = (size_t)B->dicts[d]->ws.n * B->k;
+    if (!cnt) continue;
+    if (!nbr_idx[d] || !nbr_score[d]) return set_err(c, NW_EINVAL, "null output for dictionary %zu", d);
+    NW_CK(cudaMemcpyAsync(nbr_idx[d], B->d_out_idx.as<uint32_t>() + B->list_off[d] * B->k, sizeof(uint32_t) * cnt,
+                          kind, B->stream));
+    NW_CK(cudaMemcpyAsync(nbr_score[d], B->d_out_score.as<int16_t>() + B->list_off[d] * B->k,
+                          sizeof(int16_t) * cnt, kind, B->stream));
+  }
+  if ((flags & NW_ASYNC) && dev) return NW_OK;
+  return check_flags(c, B->stream, B->d_small.as<uint32_t>());
+}
+
+nw_status nw_batch_info_get(const nw_batch* B, nw_batch_info* out) {
+  if (!B || !out) return NW_EINVAL;
+  nw_batch_info i{};
+  i.ndicts = (uint32_t)B->dicts.size();
+  i.launches = (uint32_t)B->plan.launches.size();
+  i.pairs = B->plan.pairs;
+  i.cells = B->plan.cells;
+  i.tune_ms = B->tune_ms;
+  for (int L = 0; L < kBuckets; ++L) i.words_per_task[L] = B->ta_by_lb[L];
+  *out = i;
+  return NW_OK;
+}
+
+void nw_batch_free(nw_batch* B) {
+  if (!B) return;
+  cudaSetDevice(B->ctx->device);
+  destroy_impl(B);
+}
+
+}  // extern "C"

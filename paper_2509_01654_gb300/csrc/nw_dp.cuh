@@ -217,23 +217,37 @@ __device__ __forceinline__ int g_threshold(uint32_t thr_key, uint32_t ib, int32_
 // the optimum from below, and no alignment beats the diagonal one with every
 // diagonal column a match from above (for gap <= 0; with gap > 0 the all-gap
 // alignment is the larger).
-__device__ __forceinline__ void pair_score_bounds(const DpParams& P, int la, int lb, int& lo, int& hi) {
-  const int allgap = (la + lb) * P.gap;
-  const int diag_lo = la * P.mismatch + (lb - la) * P.gap;
-  const int diag_hi = la * P.match + (lb - la) * P.gap;
+__device__ __forceinline__ void pair_score_bounds(int match, int mismatch, int gap, int la, int lb, int& lo,
+                                                  int& hi) {
+  const int allgap = (la + lb) * gap;
+  const int diag_lo = la * mismatch + (lb - la) * gap;
+  const int diag_hi = la * match + (lb - la) * gap;
   lo = allgap > diag_lo ? allgap : diag_lo;
   hi = allgap > diag_hi ? allgap : diag_hi;
 }
 
+// Word sets, lists and scoring of one task: the kernel parameters, or in a
+// batched launch the terms of the segment's dictionary.
+struct TaskTerms {
+  const uint32_t* a_enc;
+  const uint4* b_rec;
+  SideView A, B;
+  uint32_t C1, C2;
+  int32_t match, mismatch, gap, key_lo;
+  uint32_t ib, imask;
+};
+
 // The all-pairs kernel.  EPI selects the per-pair epilogue at compile time:
 // kEpiMatrix writes the int8 upper triangle, kEpiLists updates neighbour lists
 // (and a shared or global histogram), kEpiListsLaneHist updates lists and the
-// per-lane shared histogram columns.
+// per-lane shared histogram columns, kEpiBatchLists updates lists of the
+// segment's dictionary in a launch spanning many dictionaries.
 template <int LB, int EPI>
 __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const DpParams P) {
   extern __shared__ uint32_t s_dyn[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  constexpr bool kLists = EPI != kEpiMatrix;
   const bool smem_hist = EPI == kEpiListsLaneHist || (EPI == kEpiLists && P.hist_mode == kHistSmem);
   const uint32_t wstride = EPI == kEpiListsLaneHist ? P.nbins * 32u : (smem_hist ? P.nbins : 0u);
   uint32_t* wh = s_dyn + (size_t)wib * wstride;
@@ -247,8 +261,6 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
   }
   uint64_t wpairs = 0;
   uint32_t inserts = 0;
-  const bool listsA = EPI != kEpiMatrix && P.A.slots != nullptr;
-  const bool listsB = EPI != kEpiMatrix && P.B.slots != nullptr;
 
   for (;;) {
     unsigned long long t = 0;
@@ -258,21 +270,31 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
 
     const Seg S = P.segs[find_seg(P.segs, P.nsegs, t)];
     const TaskGeom g = task_geom(S, t, P.TA);
+    TaskTerms T;
+    if constexpr (EPI == kEpiBatchLists) {
+      const DictTerms& D = P.terms[S.dict];
+      T = TaskTerms{D.a_enc, D.b_rec, SideView{D.perm, D.slots, D.thr}, SideView{D.perm, D.slots, D.thr},
+                    D.C1, D.C2, D.match, D.mismatch, D.gap, D.key_lo, D.ib, D.imask};
+    } else {
+      T = TaskTerms{P.a_enc, P.b_rec, P.A, P.B, P.C1, P.C2, P.match, P.mismatch, P.gap, P.key_lo, P.ib, P.imask};
+    }
+    const bool listsA = kLists && T.A.slots != nullptr;
+    const bool listsB = kLists && T.B.slots != nullptr;
     const uint32_t blo = g.b0 + 2u * lane;
     const uint32_t bhi = blo + 1u;
     const bool vlo = blo < g.bend;
     const bool vhi = bhi < g.bend;
     const bool check = g.tri && g.a1 > g.b0;  // the task straddles the diagonal: test a < b
     const int la = S.la;
-    const int pconst = P.gap * (la + LB);  // score = G + pconst
+    const int pconst = T.gap * (la + LB);  // score = G + pconst
     const int hoff = pconst - P.hist_lo;   // histogram bin = G + hoff
 
     // every bin this task can produce lies inside the histogram (proven
     // bounds); checked once here instead of per pair
-    bool hist_on = EPI != kEpiMatrix && P.hist_mode != kHistNone;
+    bool hist_on = (EPI == kEpiLists || EPI == kEpiListsLaneHist) && P.hist_mode != kHistNone;
     if (hist_on) {
       int lo, hi;
-      pair_score_bounds(P, la, LB, lo, hi);
+      pair_score_bounds(T.match, T.mismatch, T.gap, la, LB, lo, hi);
       if (lo < P.hist_lo || hi - P.hist_lo >= (int)P.nbins) {
         if (lane == 0) atomicOr(P.err, kErrHistRange);
         hist_on = false;
@@ -284,16 +306,16 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
     if constexpr (LB > 0) {
 #pragma unroll
       for (int j = 0; j < LB; ++j) brow.v[j] = 0xffffffffu;
-      if (vlo) load_brow<LB>(P.b_rec + S.brec_base + (size_t)(g.cb * (kWarpB / 2) + lane) * (ceil4(LB) / 4), brow);
+      if (vlo) load_brow<LB>(T.b_rec + S.brec_base + (size_t)(g.cb * (kWarpB / 2) + lane) * (ceil4(LB) / 4), brow);
     }
-    const uint32_t ob_lo = vlo ? __ldg(P.B.perm + blo) : 0u;
-    const uint32_t ob_hi = vhi ? __ldg(P.B.perm + bhi) : 0u;
+    const uint32_t ob_lo = vlo ? __ldg(T.B.perm + blo) : 0u;
+    const uint32_t ob_hi = vhi ? __ldg(T.B.perm + bhi) : 0u;
     // B-side lists: cached smallest keys and their G-space candidate bounds
     uint32_t thrB_lo = 0u, thrB_hi = 0u;
     int tB_lo = INT_MAX, tB_hi = INT_MAX;
     if (listsB) {
-      if (vlo) { thrB_lo = __ldcg(P.B.thr + blo); tB_lo = g_threshold(thrB_lo, P.ib, P.key_lo, pconst); }
-      if (vhi) { thrB_hi = __ldcg(P.B.thr + bhi); tB_hi = g_threshold(thrB_hi, P.ib, P.key_lo, pconst); }
+      if (vlo) { thrB_lo = __ldcg(T.B.thr + blo); tB_lo = g_threshold(thrB_lo, T.ib, T.key_lo, pconst); }
+      if (vhi) { thrB_hi = __ldcg(T.B.thr + bhi); tB_hi = g_threshold(thrB_hi, T.ib, T.key_lo, pconst); }
     }
 
     for (uint32_t c0 = g.a0; c0 < g.a1; c0 += 32u) {
@@ -303,12 +325,12 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
       const uint32_t nA = g.a1 - c0 < 32u ? g.a1 - c0 : 32u;
       const uint32_t my_a = c0 + (uint32_t)lane;
       const bool have = (uint32_t)lane < nA;
-      const uint32_t my_orig = (EPI == kEpiMatrix && have) ? __ldg(P.A.perm + my_a) : 0u;
-      const uint32_t my_thr = (listsA && have) ? __ldcg(P.A.thr + my_a) : 0u;
-      const int my_tA = listsA ? g_threshold(my_thr, P.ib, P.key_lo, pconst) : INT_MAX;
+      const uint32_t my_orig = (EPI == kEpiMatrix && have) ? __ldg(T.A.perm + my_a) : 0u;
+      const uint32_t my_thr = (listsA && have) ? __ldcg(T.A.thr + my_a) : 0u;
+      const int my_tA = listsA ? g_threshold(my_thr, T.ib, T.key_lo, pconst) : INT_MAX;
       __syncwarp();
       if (have) {
-        const uint32_t* src = P.a_enc + S.aenc_base + (size_t)(my_a - S.a_beg) * (uint32_t)la;
+        const uint32_t* src = T.a_enc + S.aenc_base + (size_t)(my_a - S.a_beg) * (uint32_t)la;
         for (int i = 0; i < la; ++i) sA[32 * i + lane] = __ldg(src + i);
         sT[lane] = my_thr;
       }
@@ -316,7 +338,7 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
 
       for (uint32_t w = 0; w < nA; ++w) {
         const uint32_t a = c0 + w;
-        const uint32_t res = dp_word_staged<LB>(sA + w, la, brow, P.C1, P.C2);
+        const uint32_t res = dp_word_staged<LB>(sA + w, la, brow, T.C1, T.C2);
         const int g_lo = (int)(res & 0xffffu);  // G >= 0
         const int g_hi = (int)(res >> 16);
         bool ok_lo = vlo, ok_hi = vhi;
@@ -351,35 +373,35 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
           const bool c_lo = ok_lo && g_lo >= min(tB_lo, tA);
           const bool c_hi = ok_hi && g_hi >= min(tB_hi, tA);
           if (c_lo || c_hi) {
-            const uint32_t oa = __ldg(P.A.perm + a);
+            const uint32_t oa = __ldg(T.A.perm + a);
             const uint32_t thrA = sT[w];
-            uint32_t* rowA = listsA ? P.A.slots + (size_t)a * P.k : nullptr;
+            uint32_t* rowA = listsA ? T.A.slots + (size_t)a * P.k : nullptr;
             if (c_lo) {
-              const uint32_t s = (uint32_t)(g_lo + pconst - P.key_lo);
+              const uint32_t s = (uint32_t)(g_lo + pconst - T.key_lo);
               if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
-                const uint32_t key = (s << P.ib) | (P.imask - oa);
+                const uint32_t key = (s << T.ib) | (T.imask - oa);
                 if (key > thrB_lo) {
-                  const uint32_t nm = list_offer(P.B.slots + (size_t)blo * P.k, P.B.thr + blo, P.k, key, P.err, inserts);
-                  if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_threshold(nm, P.ib, P.key_lo, pconst); }
+                  const uint32_t nm = list_offer(T.B.slots + (size_t)blo * P.k, T.B.thr + blo, P.k, key, P.err, inserts);
+                  if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_threshold(nm, T.ib, T.key_lo, pconst); }
                 }
               }
               if (g_lo >= tA) {  // the A word takes the lane's word as a neighbour
-                const uint32_t key = (s << P.ib) | (P.imask - ob_lo);
-                if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
+                const uint32_t key = (s << T.ib) | (T.imask - ob_lo);
+                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts);
               }
             }
             if (c_hi) {
-              const uint32_t s = (uint32_t)(g_hi + pconst - P.key_lo);
+              const uint32_t s = (uint32_t)(g_hi + pconst - T.key_lo);
               if (g_hi >= tB_hi) {
-                const uint32_t key = (s << P.ib) | (P.imask - oa);
+                const uint32_t key = (s << T.ib) | (T.imask - oa);
                 if (key > thrB_hi) {
-                  const uint32_t nm = list_offer(P.B.slots + (size_t)bhi * P.k, P.B.thr + bhi, P.k, key, P.err, inserts);
-                  if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_threshold(nm, P.ib, P.key_lo, pconst); }
+                  const uint32_t nm = list_offer(T.B.slots + (size_t)bhi * P.k, T.B.thr + bhi, P.k, key, P.err, inserts);
+                  if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_threshold(nm, T.ib, T.key_lo, pconst); }
                 }
               }
               if (g_hi >= tA) {
-                const uint32_t key = (s << P.ib) | (P.imask - ob_hi);
-                if (key > thrA) list_offer(rowA, P.A.thr + a, P.k, key, P.err, inserts);
+                const uint32_t key = (s << T.ib) | (T.imask - ob_hi);
+                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts);
               }
             }
           }

@@ -45,6 +45,7 @@ struct WordSet {
 struct LaunchPlan {
   int LB = 0;
   int role = 0;  // 0: A and B from one set; 1: A = queries, B = dictionary; 2: A = dictionary, B = queries
+  uint32_t ta = 0;  // A words per task of this launch (0: the launch parameters' TA)
   uint32_t seg_first = 0, nsegs = 0;
   uint64_t ntasks = 0;
   uint64_t pairs = 0, cells = 0;
@@ -265,6 +266,8 @@ void order_launches(Plan& p) {
 // then shorter A lengths in order of growing length difference.
 void plan_all_pairs(const Buckets& bk, uint32_t TA, Plan& out) {
   out = Plan{};
+  if (TA == 0) TA = kDefaultTA;
+  TA = (TA + 1) & ~1u;  // A chunks start B chunks of the same bucket: keep them even
   for (int LB = 0; LB < kBuckets; ++LB) {
     const uint32_t nB = bk.count[LB];
     if (nB == 0) continue;
@@ -526,6 +529,7 @@ nw_status run_plan(nw_ctx* c, cudaStream_t stream, const Plan& plan, const Seg* 
     DpParams P = base;
     P.segs = d_segs + lp.seg_first;
     P.nsegs = lp.nsegs;
+    if (lp.ta) P.TA = lp.ta;
     P.task_lo = lo;
     P.task_hi = hi;
     P.counter = counters + li;
@@ -534,7 +538,9 @@ nw_status run_plan(nw_ctx* c, cudaStream_t stream, const Plan& plan, const Seg* 
     P.b_rec = b_rec_by_role[lp.role];
     P.B = *B_by_role[lp.role];
     const size_t smem = hist_smem_bytes(P.hist_mode, P.nbins) + dp_stage_bytes(lp.LB);
-    const int epi = P.mode == kModeMatrix ? kEpiMatrix : (P.hist_mode == kHistLane ? kEpiListsLaneHist : kEpiLists);
+    const int epi = P.terms ? kEpiBatchLists
+                            : (P.mode == kModeMatrix ? kEpiMatrix
+                                                     : (P.hist_mode == kHistLane ? kEpiListsLaneHist : kEpiLists));
     const void* fn = dp_kernel(lp.LB, epi);
     if (!fn) return set_err(c, NW_EINVAL, "no kernel for length %d", lp.LB);
     NW_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

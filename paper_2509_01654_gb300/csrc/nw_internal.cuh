@@ -65,7 +65,22 @@ struct Seg {
   uint16_t la;
   uint16_t tri;
   uint32_t nca;         // A chunks (tasks = nca * ceil((b_end - b_beg) / kWarpB))
+  uint32_t dict;        // dictionary of the segment in a batched launch (else 0)
   uint64_t task0;       // first task of the segment within its launch
+};
+
+// Per-dictionary terms of a batched launch: the word set, its lists and its
+// scoring constants (one entry per dictionary, indexed by Seg::dict).
+struct DictTerms {
+  const uint32_t* a_enc;
+  const uint4* b_rec;
+  const uint32_t* perm;
+  uint32_t* slots;
+  uint32_t* thr;
+  uint32_t C1, C2;
+  int32_t match, mismatch, gap;
+  int32_t key_lo;
+  uint32_t ib, imask;
 };
 
 struct TaskGeom {
@@ -124,8 +139,9 @@ __host__ __device__ constexpr size_t dp_stage_bytes(int LB) {
   return (size_t)kWarpsPerBlock * 32u * (size_t)(LB + 1) * sizeof(uint32_t);
 }
 
-// per-pair epilogue of the all-pairs kernel (a template parameter)
-enum { kEpiMatrix = 0, kEpiLists = 1, kEpiListsLaneHist = 2, kEpiKinds = 3 };
+// per-pair epilogue of the all-pairs kernel (a template parameter);
+// kEpiBatchLists takes word sets, lists and scoring per task from DpParams::terms
+enum { kEpiMatrix = 0, kEpiLists = 1, kEpiListsLaneHist = 2, kEpiBatchLists = 3, kEpiKinds = 4 };
 
 // Histogram accumulation mode for `nbins` bins and the dynamic shared memory
 // it needs per block: per-lane columns while they fit in 48 KiB, else one
@@ -163,6 +179,7 @@ struct DpParams {
   uint32_t nbins;
   unsigned long long* stats;      // [0] list inserts
   uint32_t* err;
+  const DictTerms* terms;         // batched launches: per-dictionary terms (device), else null
 };
 
 // Scoring constants of the shifted recurrence (see the kernel).

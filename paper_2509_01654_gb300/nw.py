@@ -32,7 +32,9 @@ EXPORTED = [
     "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
     "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc", "nw_all_pairs_topk_noalloc",
     "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
+    "nw_batch_create", "nw_batch_run", "nw_batch_info_get", "nw_batch_free",
 ]
+NW_BATCH_AUTOTUNE = 0x10
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -77,6 +79,17 @@ class RequestInfo(ctypes.Structure):
                 ("inflight_at_start", ctypes.c_uint32)]
 
 
+class BatchDict(ctypes.Structure):
+    _fields_ = [("codes", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n", ctypes.c_uint32),
+                ("alphabet", ctypes.c_uint32), ("scoring", Scoring)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("ndicts", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("pairs", ctypes.c_uint64),
+                ("cells", ctypes.c_uint64), ("tune_ms", ctypes.c_double),
+                ("words_per_task", ctypes.c_uint32 * (MAX_WORD_LEN + 1))]
+
+
 _lib = None
 
 
@@ -117,6 +130,11 @@ def load_library(path: str = LIB_PATH):
     L.nw_server_last_error.restype = ctypes.c_char_p
     L.nw_server_destroy.argtypes = [vp]
     L.nw_server_destroy.restype = None
+    L.nw_batch_create.argtypes = [vp, ctypes.POINTER(BatchDict), u32, u32, u32, ctypes.POINTER(vp)]
+    L.nw_batch_run.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), u32]
+    L.nw_batch_info_get.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    L.nw_batch_free.argtypes = [vp]
+    L.nw_batch_free.restype = None
     _lib = L
     return L
 
@@ -379,6 +397,61 @@ def debug_enumerate_pairs(lengths, shard: int = 0, nshards: int = 1):
     if st != NW_OK:
         raise NwError(st, "nw_debug_enumerate_pairs failed")
     return a[:cnt.value], b[:cnt.value]
+
+
+class Batch:
+    """nw_batch_*: many dictionaries reduced to top-k lists in one CUDA-graph launch.
+    `dicts`: [(codes, offsets, alphabet, (match, mismatch, gap)), ...] as host numpy arrays."""
+
+    def __init__(self, ctx: Context, dicts, k: int = 10, autotune: bool = True):
+        L = load_library()
+        arrs, specs = [], []
+        for codes, offsets, alphabet, scoring in dicts:
+            codes = np.ascontiguousarray(codes, dtype=np.uint8)
+            if codes.size == 0:
+                codes = np.zeros(1, np.uint8)
+            offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+            arrs.append((codes, offsets))
+            specs.append(BatchDict(codes.ctypes.data, offsets.ctypes.data, offsets.size - 1, alphabet,
+                                   Scoring(*scoring)))
+        arr = (BatchDict * max(1, len(specs)))(*specs)
+        h = ctypes.c_void_p()
+        st = L.nw_batch_create(ctx.handle, arr, len(specs), k, NW_BATCH_AUTOTUNE if autotune else 0,
+                               ctypes.byref(h))
+        _check(ctx.handle, st)
+        self.handle = h
+        self.ctx = ctx
+        self.k = k
+        self.sizes = [o.size - 1 for _, o in arrs]
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(self.ctx.handle, load_library().nw_batch_info_get(self.handle, ctypes.byref(i)))
+        out = {f: getattr(i, f) for f, _ in BatchInfo._fields_ if f != "words_per_task"}
+        out["words_per_task"] = list(i.words_per_task)
+        return out
+
+    def run(self, outputs=None):
+        """One graph launch; returns [(idx[n, k] uint32, score[n, k] int16), ...] (host) or fills
+        `outputs` (same structure, numpy or CUDA torch tensors)."""
+        if outputs is None:
+            outputs = [(np.empty((n, self.k), np.uint32), np.empty((n, self.k), np.int16)) for n in self.sizes]
+        ip = (ctypes.c_void_p * max(1, len(outputs)))(*[_ptr(o[0])[0] for o in outputs])
+        sp = (ctypes.c_void_p * max(1, len(outputs)))(*[_ptr(o[1])[0] for o in outputs])
+        flags = _flags(*[b for o in outputs for b in o])
+        _check(self.ctx.handle, load_library().nw_batch_run(self.handle, ip, sp, flags))
+        return outputs
+
+    def free(self):
+        if getattr(self, "handle", None) and getattr(self.ctx, "handle", None):
+            load_library().nw_batch_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class Server:
