@@ -30,11 +30,19 @@ struct nw_batch {
 
 namespace {
 
-constexpr uint32_t kTaCandidates[] = {64, 128, 256, 512, 1024};
+constexpr uint32_t kTaCandidates[] = {64, 128, 256};
 
-// The segments of every dictionary whose longer length is LB, with A chunks of
-// `ta` words, appended as one launch (task0 rebased, dictionary tagged).
-void append_launch(const nw_batch* B, int LB, uint32_t ta, Plan& out) {
+// Every dictionary's own plan with A chunks of `ta` words.
+std::vector<Plan> dict_plans(const nw_batch* B, uint32_t ta) {
+  std::vector<Plan> plans(B->dicts.size());
+  for (size_t d = 0; d < B->dicts.size(); ++d) plan_all_pairs(B->dicts[d]->ws.bk, ta, plans[d]);
+  return plans;
+}
+
+// The segments of every dictionary whose longer length is LB, taken from the
+// dictionaries' plans made with A chunks of `ta` words, appended as one
+// launch (task0 rebased, dictionary tagged).
+void append_launch(const nw_batch* B, const std::vector<Plan>& plans, int LB, uint32_t ta, Plan& out) {
   LaunchPlan lp;
   lp.LB = LB;
   lp.role = 0;
@@ -42,8 +50,7 @@ void append_launch(const nw_batch* B, int LB, uint32_t ta, Plan& out) {
   lp.seg_first = (uint32_t)out.segs.size();
   uint64_t task = 0;
   for (size_t d = 0; d < B->dicts.size(); ++d) {
-    Plan p;
-    plan_all_pairs(B->dicts[d]->ws.bk, ta, p);
+    const Plan& p = plans[d];
     for (const LaunchPlan& q : p.launches) {
       if (q.LB != LB) continue;
       for (uint32_t s = 0; s < q.nsegs; ++s) {
@@ -87,8 +94,9 @@ nw_status upload_plan(nw_batch* B, const Plan& plan) {
   return NW_OK;
 }
 
-// List resets and the alignment launches of `plan` on the context's stream.
-nw_status issue_lists(nw_batch* B, const Plan& plan) {
+// List resets and the alignment launches of `plan` (shard `shard` of
+// `nshards` of each launch's tasks) on the batch's stream.
+nw_status issue_lists(nw_batch* B, const Plan& plan, uint32_t shard = 0, uint32_t nshards = 1) {
   nw_ctx* c = B->ctx;
   cudaStream_t s = B->stream;
   NW_CK(cudaMemsetAsync(B->d_small.p, 0, B->d_small.bytes, s));
@@ -104,7 +112,8 @@ nw_status issue_lists(nw_batch* B, const Plan& plan) {
   Timer tm{c};
   RunOut ro;
   const nw_status st = run_plan(c, s, plan, B->d_segs.as<Seg>(), P,
-                                reinterpret_cast<unsigned long long*>(B->d_small.as<char>() + 64), 0, 1, tm, ro,
+                                reinterpret_cast<unsigned long long*>(B->d_small.as<char>() + 64), shard, nshards,
+                                tm, ro,
                                 a_enc, views, b_rec, views);
   c->profiling = saved;
   return st;
@@ -136,26 +145,30 @@ nw_status autotune(nw_batch* B) {
     cudaEvent_t a, b;
     ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } evfree{e0, e1};
+  std::vector<std::vector<Plan>> plans;
+  for (uint32_t ta : kTaCandidates) plans.push_back(dict_plans(B, ta));
   for (int LB = 0; LB < kBuckets; ++LB) {
     float best = 0;
     uint32_t best_ta = 0;
-    for (uint32_t ta : kTaCandidates) {
+    bool warm = false;
+    for (size_t ci = 0; ci < sizeof(kTaCandidates) / sizeof(kTaCandidates[0]); ++ci) {
+      const uint32_t ta = kTaCandidates[ci];
       Plan p;
-      append_launch(B, LB, ta, p);
+      append_launch(B, plans[ci], LB, ta, p);
       if (p.launches.empty()) break;
       NW_TRY(upload_plan(B, p));
-      float ms_min = 0;
-      for (int rep = 0; rep < 2; ++rep) {
-        NW_CK(cudaEventRecord(e0, B->stream));
+      if (!warm) {  // the kernel's first launch pays its set-up; keep it out of the timings
         NW_TRY(issue_lists(B, p));
-        NW_CK(cudaEventRecord(e1, B->stream));
-        NW_CK(cudaEventSynchronize(e1));
-        float ms = 0;
-        NW_CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (rep == 0 || ms < ms_min) ms_min = ms;
+        warm = true;
       }
-      if (best_ta == 0 || ms_min < best) {
-        best = ms_min;
+      NW_CK(cudaEventRecord(e0, B->stream));
+      NW_TRY(issue_lists(B, p));
+      NW_CK(cudaEventRecord(e1, B->stream));
+      NW_CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      NW_CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (best_ta == 0 || ms < best) {
+        best = ms;
         best_ta = ta;
       }
     }
@@ -222,7 +235,17 @@ nw_status create_impl(nw_batch* B, const nw_batch_dict* dicts, uint32_t ndicts, 
   for (int LB = 0; LB < kBuckets; ++LB) B->ta_by_lb[LB] = kDefaultTA;
   if (flags & NW_BATCH_AUTOTUNE) NW_TRY(autotune(B));
   B->plan = Plan{};
-  for (int LB = 0; LB < kBuckets; ++LB) append_launch(B, LB, B->ta_by_lb[LB], B->plan);
+  {
+    std::vector<uint32_t> tas;  // the distinct chunk sizes chosen, each planned once
+    for (int LB = 0; LB < kBuckets; ++LB)
+      if (std::find(tas.begin(), tas.end(), B->ta_by_lb[LB]) == tas.end()) tas.push_back(B->ta_by_lb[LB]);
+    std::vector<std::vector<Plan>> plans;
+    for (uint32_t ta : tas) plans.push_back(dict_plans(B, ta));
+    for (int LB = 0; LB < kBuckets; ++LB) {
+      const size_t ci = std::find(tas.begin(), tas.end(), B->ta_by_lb[LB]) - tas.begin();
+      append_launch(B, plans[ci], LB, B->ta_by_lb[LB], B->plan);
+    }
+  }
   for (int LB = 0; LB < kBuckets; ++LB) {
     bool present = false;
     for (const LaunchPlan& lp : B->plan.launches) present |= lp.LB == LB;
