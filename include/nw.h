@@ -61,6 +61,7 @@ typedef enum {
 /* call flags */
 #define NW_DEVICE_PTRS 0x1u /* buffer arguments are device pointers */
 #define NW_ASYNC 0x2u       /* with NW_DEVICE_PTRS: do not wait for the stream before returning */
+#define NW_RANK_NORMALISED 0x4u /* nw_all_pairs_topk: rank neighbours by s / max(len) (Section 5) */
 
 /* Similarity and gap values (Algorithm 1, Section 2): similarity(a, b) is
  * `match` when a == b and `mismatch` otherwise; `gap` (the paper's p, normally
@@ -149,6 +150,16 @@ void nw_dict_free(nw_dict *dict);
  * outside [-128, 127]. */
 nw_status nw_all_pairs_matrix(nw_dict *dict, int8_t *out, uint32_t flags);
 
+/* The same int8 row-major upper triangle for dictionaries whose matrix does
+ * not fit in device memory (Section 5's 107,000-word limit, and its proposal
+ * to copy intermediate results back and continue): the n(n-1)/2 entries are
+ * produced in consecutive chunks of at most chunk_bytes through one device
+ * buffer of that size and copied into the host buffer `out` chunk by chunk.
+ * Every chunk rescores all pairs and keeps its own entries, so the work grows
+ * with the number of chunks.  Host `out` only (NW_DEVICE_PTRS is refused when
+ * chunking is needed); chunk_bytes >= n(n-1)/2 is nw_all_pairs_matrix. */
+nw_status nw_all_pairs_matrix_chunked(nw_dict *dict, int8_t *out, uint64_t chunk_bytes, uint32_t flags);
+
 /* Scores every pair i < j once and reduces on the device to, for every word,
  * its k best neighbours over all other words (higher score first, lower
  * original index first on equal scores) -- the per-word ego-network lists of
@@ -158,7 +169,17 @@ nw_status nw_all_pairs_matrix(nw_dict *dict, int8_t *out, uint32_t flags);
  *   hist: NULL, or nbins int64 counts; hist[b] counts pairs scoring
  *         *hist_lo + b.  nbins must be >= nw_dict_info.nbins (else NW_ERANGE).
  *   hist_lo: receives the score of bin 0 (may be NULL when hist is NULL).
- * k in [1, NW_MAX_K].  NW_EINVAL if n < 2. */
+ * k in [1, NW_MAX_K].  NW_EINVAL if n < 2.
+ * With NW_RANK_NORMALISED in `flags` the lists hold the k best neighbours by
+ * the length-normalised weight s / max(len_i, len_j) of Section 5 (two empty
+ * words: s / 1), compared exactly as fractions; equal weights rank the lower
+ * original index first.  nbr_score still receives the raw score s (the
+ * paper's displayed weight is 100 * s / max(len_i, len_j)) and the histogram
+ * still counts raw scores.  NW_ERANGE if the distinct weights and the index
+ * bits of n do not fit 32-bit list keys (for match 1, mismatch -1, gap -1 and
+ * words of up to 40 symbols there are under 1,000 weights, so any n up to
+ * 2^20 fits).  The flag is accepted by this call only: the shard variant,
+ * the no-allocation variant, queries and batches give NW_EINVAL. */
 nw_status nw_all_pairs_topk(nw_dict *dict, uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score,
                             int64_t *hist, int32_t *hist_lo, uint32_t nbins, uint32_t flags);
 
@@ -358,6 +379,19 @@ nw_status nw_measure_int_rates(nw_ctx *ctx, double ms_target, nw_int_rates *out)
 nw_status nw_debug_enumerate_pairs(const uint32_t *lengths, uint32_t n, uint32_t shard,
                                    uint32_t nshards, uint32_t *a, uint32_t *b, uint64_t cap,
                                    uint64_t *count);
+
+/* Host-only: the tables behind NW_RANK_NORMALISED for scores [lo, hi].
+ * *nranks receives the number of distinct weights s/m (rank 0 = smallest);
+ * when it is <= cap_ranks, also writes
+ *   rank[(s - lo) * (NW_MAX_WORD_LEN + 1) + m]: rank of s/m for longer length
+ *       m (m = 0: s/1) where s is reachable for m, else 0;
+ *   smin[r * (NW_MAX_WORD_LEN + 1) + m]: smallest reachable s whose s/m has
+ *       rank >= r, else INT16_MAX;
+ *   frac[2r], frac[2r + 1]: rank r's weight in lowest terms.
+ * rank holds (hi - lo + 1) * (NW_MAX_WORD_LEN + 1) entries.  NW_EINVAL for
+ * lo > hi or null pointers; NW_ERANGE when *nranks > cap_ranks. */
+nw_status nw_debug_norm_tables(const nw_scoring *scoring, int32_t lo, int32_t hi, uint16_t *rank,
+                               int16_t *smin, int16_t *frac, uint32_t cap_ranks, uint32_t *nranks);
 
 /* Test hook: the `countdown`-th device allocation of the context from now on
  * fails as if the device were out of memory (0 disables).  Host-side only. */

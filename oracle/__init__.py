@@ -49,6 +49,8 @@ def lib():
         L.nwo_topk_rows.argtypes = [u8p, u32p, ctypes.c_uint32, u32p, ctypes.c_uint32, ctypes.c_uint32,
                                     ci, ci, ci, u32p, i32p, ci]
         L.nwo_topk_rows.restype = ci
+        L.nwo_topk_rows_normalised.argtypes = L.nwo_topk_rows.argtypes
+        L.nwo_topk_rows_normalised.restype = ci
         L.nwo_query_topk.argtypes = [u8p, u32p, ctypes.c_uint32, u8p, u32p, ctypes.c_uint32,
                                      ctypes.c_uint32, ci, ci, ci, u32p, i32p, ci]
         L.nwo_query_topk.restype = ci
@@ -119,6 +121,25 @@ def topk_rows(words, rows, k, scoring, nthreads=None):
                              _p(idx, ctypes.c_uint32), _p(sc, ctypes.c_int32), nthreads or default_threads())
     if rc != 0:
         raise RuntimeError(f"nwo_topk_rows failed: {rc}")
+    return idx, sc
+
+
+def topk_rows_normalised(words, rows, k, scoring, nthreads=None):
+    """(idx, raw score) of shape (len(rows), k), ranked by the Section 5 weight
+    s / max(len(A), len(B)) compared as exact fractions (lower index first on
+    equal weights)."""
+    rows = _u32(rows)
+    idx = np.zeros((rows.size, k), dtype=np.uint32)
+    sc = np.zeros((rows.size, k), dtype=np.int32)
+    if rows.size == 0:
+        return idx, sc
+    rc = lib().nwo_topk_rows_normalised(_p(_u8(words.codes), ctypes.c_uint8),
+                                        _p(_u32(words.offsets), ctypes.c_uint32), words.n,
+                                        _p(rows, ctypes.c_uint32), rows.size, k, *scoring,
+                                        _p(idx, ctypes.c_uint32), _p(sc, ctypes.c_int32),
+                                        nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"nwo_topk_rows_normalised failed: {rc}")
     return idx, sc
 
 

@@ -22,6 +22,8 @@
  *     higher score first and lower index on equal scores; the first k kept.
  *     Edges are undirected (Section 4.1), so word i's neighbours come from
  *     both halves of the matrix; self pairs are excluded.
+ *   - nwo_topk_rows_normalised: the same lists ranked by Section 5's
+ *     length-normalised weight s / max(len(A), len(B)), compared exactly.
  *   - nwo_histogram: one bin per integer score, each unordered pair counted
  *     once (the edge-weight histogram of Section 5).
  *   - nwo_score_pairs: the scores of an explicit list of pairs.
@@ -244,6 +246,71 @@ int nwo_topk_rows(const uint8_t *codes, const uint32_t *offsets, uint32_t n, con
     J.rows = rows; J.nrows = nrows; J.k = k;
     J.top_idx = out_idx; J.top_score = out_score;
     return run_threads(&J, topk_rows_worker);
+}
+
+/* Section 5's length normalisation: a pair's weight is s / max(len(A),
+ * len(B)) (times 100 for display, which does not change the order).  Two empty
+ * words have weight s / 1.  Weights are compared exactly, as fractions with
+ * positive denominators: s1/m1 > s2/m2  <=>  s1*m2 > s2*m1. */
+static int ranks_before_norm(int32_t s1, int32_t m1, uint32_t j1, int32_t s2, int32_t m2, uint32_t j2) {
+    int64_t l = (int64_t)s1 * m2, r = (int64_t)s2 * m1;
+    return l > r || (l == r && j1 < j2);
+}
+
+static void topk_rows_norm_worker(job_t *J, int tid) {
+    int32_t *H = matrix_buffer(J->maxlen, J->maxlen);
+    int32_t *den = (int32_t *)malloc(sizeof(int32_t) * J->k);
+    if (!H || !den) { free(H); free(den); return; }
+    for (uint32_t r = (uint32_t)tid; r < J->nrows; r += (uint32_t)J->nthreads) {
+        uint32_t i = J->rows[r];
+        const uint8_t *A = J->codes + J->offsets[i];
+        int la = (int)(J->offsets[i + 1] - J->offsets[i]);
+        uint32_t *idx = J->top_idx + (size_t)r * J->k;
+        int32_t *sc = J->top_score + (size_t)r * J->k;
+        uint32_t cnt = 0;
+        for (uint32_t j = 0; j < J->n; ++j) {
+            if (j == i) continue;
+            const uint8_t *B = J->codes + J->offsets[j];
+            int lb = (int)(J->offsets[j + 1] - J->offsets[j]);
+            int32_t s = score_with(H, A, la, B, lb, J->match, J->mismatch, J->gap);
+            int32_t m = la > lb ? la : lb;
+            if (m == 0) m = 1;
+            /* insertion into the ordered list, as keep_best but by weight */
+            if (cnt == J->k && !ranks_before_norm(s, m, j, sc[J->k - 1], den[J->k - 1], idx[J->k - 1])) continue;
+            uint32_t pos = cnt < J->k ? cnt : J->k - 1;
+            while (pos > 0 && ranks_before_norm(s, m, j, sc[pos - 1], den[pos - 1], idx[pos - 1])) {
+                sc[pos] = sc[pos - 1];
+                den[pos] = den[pos - 1];
+                idx[pos] = idx[pos - 1];
+                --pos;
+            }
+            sc[pos] = s;
+            den[pos] = m;
+            idx[pos] = j;
+            if (cnt < J->k) ++cnt;
+        }
+        for (uint32_t c = cnt; c < J->k; ++c) { idx[c] = UINT32_MAX; sc[c] = INT32_MIN; }
+    }
+    free(den);
+    free(H);
+}
+
+/* As nwo_topk_rows, ranked by the normalised weight (ties: lower index);
+ * out_score holds the raw scores s. */
+int nwo_topk_rows_normalised(const uint8_t *codes, const uint32_t *offsets, uint32_t n, const uint32_t *rows,
+                             uint32_t nrows, uint32_t k, int match, int mismatch, int gap,
+                             uint32_t *out_idx, int32_t *out_score, int nthreads) {
+    if (!codes || !offsets || !rows || !out_idx || !out_score || k == 0) return NWO_EINVAL;
+    for (uint32_t r = 0; r < nrows; ++r) if (rows[r] >= n) return NWO_EINVAL;
+    job_t J;
+    memset(&J, 0, sizeof J);
+    J.codes = codes; J.offsets = offsets; J.n = n;
+    J.match = match; J.mismatch = mismatch; J.gap = gap;
+    J.nthreads = nthreads < 1 ? 1 : nthreads;
+    J.maxlen = max_length(offsets, n);
+    J.rows = rows; J.nrows = nrows; J.k = k;
+    J.top_idx = out_idx; J.top_score = out_score;
+    return run_threads(&J, topk_rows_norm_worker);
 }
 
 static void query_worker(job_t *J, int tid) {

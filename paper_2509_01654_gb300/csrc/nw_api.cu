@@ -62,6 +62,7 @@ void nw_destroy(nw_ctx* c) {
   ctx_free(c, c->ws_mat);
   ctx_free(c, c->ws_pairs);
   ctx_free(c, c->ws_segs);
+  ctx_free(c, c->ws_norm);
   for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -157,10 +158,15 @@ void nw_dict_free(nw_dict* d) {
   delete d;
 }
 
-nw_status nw_all_pairs_matrix(nw_dict* d, int8_t* out, uint32_t flags) {
-  if (!d) return NW_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// The int8 matrix, written directly (chunk_bytes == 0 or >= the matrix) or in
+// chunks of chunk_bytes of the row-major order: every pass scores all pairs
+// and keeps the entries of one chunk, which is then copied to the host.
+nw_status matrix_impl(nw_dict* d, int8_t* out, uint64_t chunk_bytes, uint32_t flags) {
   nw_ctx* c = d->ctx;
-  NW_ENTER(c);
   const uint32_t n = d->ws.n;
   if (!out) return set_err(c, NW_EINVAL, "null output pointer");
   if (n < 2) return set_err(c, NW_EINVAL, "the dictionary needs at least 2 words (has %u)", n);
@@ -168,10 +174,13 @@ nw_status nw_all_pairs_matrix(nw_dict* d, int8_t* out, uint32_t flags) {
     return set_err(c, NW_ERANGE, "scores of this dictionary span [%d, %d], outside int8", d->score_lo, d->score_hi);
   const bool dev = flags & NW_DEVICE_PTRS;
   const uint64_t E = (uint64_t)n * (n - 1) / 2;
+  const bool chunked = chunk_bytes > 0 && chunk_bytes < E;
+  if (chunked && dev) return set_err(c, NW_EINVAL, "chunked output goes to host memory (no NW_DEVICE_PTRS)");
   cudaStream_t s = c->stream;
   int8_t* dst = out;
+  const uint64_t step = chunked ? chunk_bytes : E;
   if (!dev) {
-    NW_TRY(ctx_ensure(c, c->ws_mat, E, "score matrix"));
+    NW_TRY(ctx_ensure(c, c->ws_mat, step, "score matrix"));
     dst = c->ws_mat.as<int8_t>();
   }
   NW_TRY(ctx_ensure(c, c->ws_small, 64 + sizeof(unsigned long long) * (d->plan.launches.size() + 1), "task counters"));
@@ -181,26 +190,35 @@ nw_status nw_all_pairs_matrix(nw_dict* d, int8_t* out, uint32_t flags) {
   cudaEvent_t e0 = nullptr;
   tm.begin(false, e0);
   NW_CK(cudaMemsetAsync(c->ws_small.p, 0, c->ws_small.bytes, s));
-  DpParams base{};
-  base.TA = kDefaultTA;
-  base.C1 = d->ss.C1;
-  base.C2 = d->ss.C2;
-  base.match = d->sc.match;
-  base.mismatch = d->sc.mismatch;
-  base.gap = d->sc.gap;
-  base.mode = kModeMatrix;
-  base.mat = dst;
-  base.n = n;
-  base.hist_mode = kHistNone;
-  base.err = d_err;
-  SideView side{d->ws.perm.as<uint32_t>(), nullptr, nullptr};
-  const uint32_t* a_enc[3] = {d->ws.a_enc.as<uint32_t>(), nullptr, nullptr};
-  const uint4* b_rec[3] = {d->ws.b_rec.as<uint4>(), nullptr, nullptr};
-  const SideView* views[3] = {&side, nullptr, nullptr};
   RunOut ro;
-  NW_TRY(run_plan(c, c->stream, d->plan, d->d_segs.as<Seg>(), base, d_counters, 0, 1, tm, ro, a_enc, views,
-                  b_rec, views));
-  if (!dev) NW_CK(cudaMemcpyAsync(out, dst, E, cudaMemcpyDeviceToHost, s));
+  for (uint64_t lo = 0; lo < E; lo += step) {
+    const uint64_t hi = std::min(E, lo + step);
+    if (lo > 0) NW_CK(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * d->plan.launches.size(), s));
+    DpParams base{};
+    base.TA = kDefaultTA;
+    base.C1 = d->ss.C1;
+    base.C2 = d->ss.C2;
+    base.match = d->sc.match;
+    base.mismatch = d->sc.mismatch;
+    base.gap = d->sc.gap;
+    base.mode = kModeMatrix;
+    base.mat = dst - lo;  // entry `off` of the chunk [lo, hi) lands at dst[off - lo]
+    base.n = n;
+    base.mat_lo = lo;
+    base.mat_hi = hi;
+    base.hist_mode = kHistNone;
+    base.err = d_err;
+    SideView side{d->ws.perm.as<uint32_t>(), nullptr, nullptr};
+    const uint32_t* a_enc[3] = {d->ws.a_enc.as<uint32_t>(), nullptr, nullptr};
+    const uint4* b_rec[3] = {d->ws.b_rec.as<uint4>(), nullptr, nullptr};
+    const SideView* views[3] = {&side, nullptr, nullptr};
+    NW_TRY(run_plan(c, c->stream, d->plan, d->d_segs.as<Seg>(), base, d_counters, 0, 1, tm, ro, a_enc, views,
+                    b_rec, views));
+    if (!dev) {
+      NW_CK(cudaMemcpyAsync(out + lo, dst, hi - lo, cudaMemcpyDeviceToHost, s));
+      if (chunked) NW_CK(cudaStreamSynchronize(s));  // the chunk buffer is reused
+    }
+  }
   tm.mark(c->profiling ? tm.get() : nullptr);
   if ((flags & NW_ASYNC) && dev) return NW_OK;
   NW_TRY(check_device_flags(c, d_err));
@@ -213,6 +231,23 @@ nw_status nw_all_pairs_matrix(nw_dict* d, int8_t* out, uint32_t flags) {
     c->prof.list_inserts = 0;
   }
   return NW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nw_status nw_all_pairs_matrix(nw_dict* d, int8_t* out, uint32_t flags) {
+  if (!d) return NW_EINVAL;
+  NW_ENTER(d->ctx);
+  return matrix_impl(d, out, 0, flags);
+}
+
+nw_status nw_all_pairs_matrix_chunked(nw_dict* d, int8_t* out, uint64_t chunk_bytes, uint32_t flags) {
+  if (!d) return NW_EINVAL;
+  NW_ENTER(d->ctx);
+  if (chunk_bytes == 0) return set_err(d->ctx, NW_EINVAL, "chunk_bytes must be positive");
+  return matrix_impl(d, out, chunk_bytes, flags);
 }
 
 nw_status nw_all_pairs_topk(nw_dict* d, uint32_t k, uint32_t* nbr_idx, int16_t* nbr_score, int64_t* hist,
@@ -330,6 +365,7 @@ nw_status nw_query(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, 
   if (!d) return NW_EINVAL;
   nw_ctx* c = d->ctx;
   NW_ENTER(c);
+  if (flags & NW_RANK_NORMALISED) return set_err(c, NW_EINVAL, "queries rank by raw score only");
   if (nq == 0) return NW_OK;
   if (!qoffsets || !nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null pointer argument");
   if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
@@ -496,6 +532,19 @@ nw_status nw_measure_int_rates(nw_ctx* c, double ms_target, nw_int_rates* out) {
   return NW_OK;
 }
 
+nw_status nw_debug_norm_tables(const nw_scoring* sc, int32_t lo, int32_t hi, uint16_t* rank, int16_t* smin,
+                               int16_t* frac, uint32_t cap_ranks, uint32_t* nranks) {
+  if (!sc || !rank || !smin || !frac || !nranks || lo > hi || lo < INT16_MIN || hi > INT16_MAX) return NW_EINVAL;
+  NormTables t;
+  build_norm_tables(*sc, lo, hi, t);
+  *nranks = t.nranks;
+  if (t.nranks > cap_ranks) return NW_ERANGE;
+  std::copy(t.rank.begin(), t.rank.end(), rank);
+  std::copy(t.smin.begin(), t.smin.end(), smin);
+  std::copy(t.frac.begin(), t.frac.end(), frac);
+  return NW_OK;
+}
+
 nw_status nw_debug_enumerate_pairs(const uint32_t* lengths, uint32_t n, uint32_t shard, uint32_t nshards, uint32_t* a,
                                    uint32_t* b, uint64_t cap, uint64_t* count) {
   if (!lengths || !count || nshards == 0 || shard >= nshards) return NW_EINVAL;
@@ -557,6 +606,8 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
   NW_ENTER(c);
   if (!(flags & NW_DEVICE_PTRS))
     return set_err(c, NW_EINVAL, "the no-allocation variant needs device output buffers (NW_DEVICE_PTRS)");
+  if (flags & NW_RANK_NORMALISED)
+    return set_err(c, NW_EINVAL, "the no-allocation variant ranks by raw score only");
   const uint32_t n = d->ws.n;
   if (n < 2) return set_err(c, NW_EINVAL, "the dictionary needs at least 2 words (has %u)", n);
   if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);

@@ -294,6 +294,7 @@ nw_status nw_batch_create(nw_ctx* ctx, const nw_batch_dict* dicts, uint32_t ndic
   *out = nullptr;
   if (!dicts && ndicts) return set_err(ctx, NW_EINVAL, "null dictionary array");
   if (k == 0 || k > NW_MAX_K) return set_err(ctx, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  if (flags & NW_RANK_NORMALISED) return set_err(ctx, NW_EINVAL, "batches rank by raw score only");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cudaSetDevice");
   nw_batch* B = new nw_batch();
   B->ctx = ctx;
@@ -317,6 +318,7 @@ nw_status nw_batch_run(nw_batch* B, uint32_t* const* nbr_idx, int16_t* const* nb
   nw_ctx* c = B->ctx;
   NW_ENTER(c);
   if (!nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null output arrays");
+  if (flags & NW_RANK_NORMALISED) return set_err(c, NW_EINVAL, "batches rank by raw score only");
   const bool dev = flags & NW_DEVICE_PTRS;
   const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   NW_CK(cudaGraphLaunch(B->exec, B->stream));

@@ -206,12 +206,6 @@ __device__ __forceinline__ void hist_flush(const DpParams& P, uint32_t* wh, int 
   __syncwarp();
 }
 
-// G-space candidate threshold of a list whose smallest key is >= thr_key:
-// a pair can enter the list only if its packed G value reaches this bound.
-__device__ __forceinline__ int g_threshold(uint32_t thr_key, uint32_t ib, int32_t key_lo, int pconst) {
-  return thr_key == 0u ? INT_MIN : (int)(thr_key >> ib) + key_lo - pconst;
-}
-
 // Lowest and highest score any pair of lengths la <= lb can reach: the
 // all-gap alignment and the alignment with min(la, lb) diagonal columns bound
 // the optimum from below, and no alignment beats the diagonal one with every
@@ -236,6 +230,28 @@ struct TaskTerms {
   int32_t match, mismatch, gap, key_lo;
   uint32_t ib, imask;
 };
+
+// List key of a pair with score s whose longer word has m symbols: the raw
+// score, or the rank of s/m in the normalised ranking, above the partner's
+// reversed index (higher key = better neighbour).
+__device__ __forceinline__ uint32_t list_key(const DpParams& P, const TaskTerms& T, int s, int m,
+                                             uint32_t partner) {
+  const uint32_t v = P.norm_rank ? (uint32_t)P.norm_rank[(s - P.norm_lo) * kBuckets + m] + 1u
+                                 : (uint32_t)(s - T.key_lo);
+  return (v << T.ib) | (T.imask - partner);
+}
+
+// G-space candidate bound of a list whose smallest key is >= thr_key, for
+// pairs whose longer word has m symbols: a pair can enter the list only if its
+// G value (score - pconst) reaches this bound.  With raw keys that is the
+// threshold's own score; with normalised keys, the smallest score whose s/m
+// has the threshold's rank (a lower rank makes a key below any key of that
+// rank, whatever the partner).
+__device__ __forceinline__ int g_bound(const DpParams& P, const TaskTerms& T, uint32_t thr_key, int m, int pconst) {
+  if (thr_key == 0u) return INT_MIN;
+  if (P.norm_rank) return (int)P.norm_smin[((thr_key >> T.ib) - 1u) * kBuckets + m] - pconst;
+  return (int)(thr_key >> T.ib) + T.key_lo - pconst;
+}
 
 // The all-pairs kernel.  EPI selects the per-pair epilogue at compile time:
 // kEpiMatrix writes the int8 upper triangle, kEpiLists updates neighbour lists
@@ -314,8 +330,8 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
     uint32_t thrB_lo = 0u, thrB_hi = 0u;
     int tB_lo = INT_MAX, tB_hi = INT_MAX;
     if (listsB) {
-      if (vlo) { thrB_lo = __ldcg(T.B.thr + blo); tB_lo = g_threshold(thrB_lo, T.ib, T.key_lo, pconst); }
-      if (vhi) { thrB_hi = __ldcg(T.B.thr + bhi); tB_hi = g_threshold(thrB_hi, T.ib, T.key_lo, pconst); }
+      if (vlo) { thrB_lo = __ldcg(T.B.thr + blo); tB_lo = g_bound(P, T, thrB_lo, LB, pconst); }
+      if (vhi) { thrB_hi = __ldcg(T.B.thr + bhi); tB_hi = g_bound(P, T, thrB_hi, LB, pconst); }
     }
 
     for (uint32_t c0 = g.a0; c0 < g.a1; c0 += 32u) {
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
       const bool have = (uint32_t)lane < nA;
       const uint32_t my_orig = (EPI == kEpiMatrix && have) ? __ldg(T.A.perm + my_a) : 0u;
       const uint32_t my_thr = (listsA && have) ? __ldcg(T.A.thr + my_a) : 0u;
-      const int my_tA = listsA ? g_threshold(my_thr, T.ib, T.key_lo, pconst) : INT_MAX;
+      const int my_tA = listsA ? g_bound(P, T, my_thr, LB, pconst) : INT_MAX;
       __syncwarp();
       if (have) {
         const uint32_t* src = T.a_enc + S.aenc_base + (size_t)(my_a - S.a_beg) * (uint32_t)la;
@@ -351,11 +367,13 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
           const uint32_t oa = __shfl_sync(0xffffffffu, my_orig, (int)w);
           if (ok_lo) {
             const uint64_t i = oa < ob_lo ? oa : ob_lo, j = oa < ob_lo ? ob_lo : oa;
-            P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_lo + pconst);
+            const uint64_t off = upper_offset(i, j, P.n);
+            if (off >= P.mat_lo && off < P.mat_hi) P.mat[off] = (int8_t)(g_lo + pconst);
           }
           if (ok_hi) {
             const uint64_t i = oa < ob_hi ? oa : ob_hi, j = oa < ob_hi ? ob_hi : oa;
-            P.mat[upper_offset(i, j, P.n)] = (int8_t)(g_hi + pconst);
+            const uint64_t off = upper_offset(i, j, P.n);
+            if (off >= P.mat_lo && off < P.mat_hi) P.mat[off] = (int8_t)(g_hi + pconst);
           }
         } else {
           if (hist_on) {
@@ -377,30 +395,30 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
             const uint32_t thrA = sT[w];
             uint32_t* rowA = listsA ? T.A.slots + (size_t)a * P.k : nullptr;
             if (c_lo) {
-              const uint32_t s = (uint32_t)(g_lo + pconst - T.key_lo);
+              const int s = g_lo + pconst;
               if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
-                const uint32_t key = (s << T.ib) | (T.imask - oa);
+                const uint32_t key = list_key(P, T, s, LB, oa);
                 if (key > thrB_lo) {
                   const uint32_t nm = list_offer(T.B.slots + (size_t)blo * P.k, T.B.thr + blo, P.k, key, P.err, inserts);
-                  if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_threshold(nm, T.ib, T.key_lo, pconst); }
+                  if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_bound(P, T, nm, LB, pconst); }
                 }
               }
               if (g_lo >= tA) {  // the A word takes the lane's word as a neighbour
-                const uint32_t key = (s << T.ib) | (T.imask - ob_lo);
+                const uint32_t key = list_key(P, T, s, LB, ob_lo);
                 if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts);
               }
             }
             if (c_hi) {
-              const uint32_t s = (uint32_t)(g_hi + pconst - T.key_lo);
+              const int s = g_hi + pconst;
               if (g_hi >= tB_hi) {
-                const uint32_t key = (s << T.ib) | (T.imask - oa);
+                const uint32_t key = list_key(P, T, s, LB, oa);
                 if (key > thrB_hi) {
                   const uint32_t nm = list_offer(T.B.slots + (size_t)bhi * P.k, T.B.thr + bhi, P.k, key, P.err, inserts);
-                  if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_threshold(nm, T.ib, T.key_lo, pconst); }
+                  if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_bound(P, T, nm, LB, pconst); }
                 }
               }
               if (g_hi >= tA) {
-                const uint32_t key = (s << T.ib) | (T.imask - ob_hi);
+                const uint32_t key = list_key(P, T, s, LB, ob_hi);
                 if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts);
               }
             }

@@ -9,12 +9,14 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "nw.h"
@@ -72,7 +74,7 @@ struct nw_ctx {
   std::set<nw_dict*> dicts;
   std::atomic<int> busy{0};
   // grow-only workspace
-  DevBuf ws_slots, ws_thr, ws_hist, ws_small, ws_out_idx, ws_out_score, ws_mat, ws_pairs, ws_segs;
+  DevBuf ws_slots, ws_thr, ws_hist, ws_small, ws_out_idx, ws_out_score, ws_mat, ws_pairs, ws_segs, ws_norm;
   std::vector<cudaEvent_t> events;
 };
 
@@ -355,6 +357,73 @@ uint32_t index_bits(uint32_t n) {
   return b;
 }
 
+// Tables of the length-normalised ranking (Section 5 divides each score by
+// the longer word's length).  Every value s/m that a pair whose longer word
+// has m symbols can reach (s within that length's score bounds and within
+// [lo, hi]) is ranked ascending by exact integer cross-multiplication; equal
+// fractions share a rank.  Two empty words (m = 0) rank as s/1.
+struct NormTables {
+  int32_t lo = 0;              // score of row 0 of `rank`
+  uint32_t nranks = 0;
+  std::vector<uint16_t> rank;  // [(s - lo) * kBuckets + m]: rank of s/m (0 where s is out of reach for m)
+  std::vector<int16_t> smin;   // [r * kBuckets + m]: smallest reachable s whose s/m has rank >= r, else above reach
+  std::vector<int16_t> frac;   // [2r], [2r + 1]: numerator and denominator of rank r in lowest terms
+};
+
+void build_norm_tables(const nw_scoring& sc, int32_t lo, int32_t hi, NormTables& t) {
+  int flo[kBuckets], fhi[kBuckets];
+  std::vector<std::pair<int32_t, int32_t>> fr;  // reduced (numerator, denominator)
+  for (int m = 0; m < kBuckets; ++m) {
+    flo[m] = INT32_MAX;
+    fhi[m] = INT32_MIN;
+    for (int la = 0; la <= m; ++la) {
+      int a, b;
+      pair_bounds(sc, la, m, a, b);
+      flo[m] = std::min(flo[m], a);
+      fhi[m] = std::max(fhi[m], b);
+    }
+    flo[m] = std::max(flo[m], lo);
+    fhi[m] = std::min(fhi[m], hi);
+    const int32_t den = m > 0 ? m : 1;
+    for (int s = flo[m]; s <= fhi[m]; ++s) {
+      int32_t g = std::abs(s), h = den;
+      while (h) { const int32_t r = g % h; g = h; h = r; }
+      fr.push_back({s / g, den / g});
+    }
+  }
+  auto less = [](const std::pair<int32_t, int32_t>& x, const std::pair<int32_t, int32_t>& y) {
+    return (int64_t)x.first * y.second < (int64_t)y.first * x.second;
+  };
+  std::sort(fr.begin(), fr.end(), less);
+  fr.erase(std::unique(fr.begin(), fr.end()), fr.end());  // reduced fractions are equal iff their parts are
+  t.lo = lo;
+  t.nranks = (uint32_t)fr.size();
+  t.rank.assign((size_t)(hi - lo + 1) * kBuckets, 0);
+  t.frac.resize(2 * fr.size());
+  for (size_t r = 0; r < fr.size(); ++r) {
+    t.frac[2 * r] = (int16_t)fr[r].first;
+    t.frac[2 * r + 1] = (int16_t)fr[r].second;
+  }
+  for (int m = 0; m < kBuckets; ++m) {
+    const int32_t den = m > 0 ? m : 1;
+    for (int s = flo[m]; s <= fhi[m]; ++s) {
+      const auto it = std::lower_bound(fr.begin(), fr.end(), std::make_pair((int32_t)s, den), less);
+      t.rank[(size_t)(s - lo) * kBuckets + m] = (uint16_t)(it - fr.begin());
+    }
+  }
+  // rank grows with s at fixed m, so the smallest s reaching rank r is found
+  // by one sweep per length; above reach, the bound no G value attains
+  t.smin.assign((size_t)fr.size() * kBuckets, INT16_MAX);
+  for (int m = 0; m < kBuckets; ++m) {
+    int s = flo[m];
+    for (uint32_t r = 0; r < t.nranks; ++r) {
+      while (s <= fhi[m] && t.rank[(size_t)(s - lo) * kBuckets + m] < r) ++s;
+      if (s > fhi[m]) break;
+      t.smin[(size_t)r * kBuckets + m] = (int16_t)s;
+    }
+  }
+}
+
 void free_wordset(nw_ctx* c, WordSet& w) {
   ctx_free(c, w.perm);
   ctx_free(c, w.rank);
@@ -587,9 +656,19 @@ nw_status topk_impl(nw_dict* d, uint32_t shard, uint32_t nshards, uint32_t k, ui
     return set_err(c, NW_ERANGE, "scores [%d, %d] do not fit int16", d->score_lo, d->score_hi);
   const uint32_t ib = index_bits(n);
   const int32_t key_lo = d->score_lo - 1;
-  if ((uint64_t)(d->score_hi - key_lo) >= (1ull << (32 - ib)))
+  const bool norm = flags & NW_RANK_NORMALISED;
+  if (norm && nshards != 1)
+    return set_err(c, NW_EINVAL, "the normalised ranking is not available for shards (lists merge by raw score)");
+  NormTables nt;
+  if (norm) {
+    build_norm_tables(d->sc, d->score_lo, d->score_hi, nt);
+    if (nt.nranks > 65535u || (uint64_t)nt.nranks >= (1ull << (32 - ib)))
+      return set_err(c, NW_ERANGE, "%u normalised score values with %u words do not fit 32-bit list keys", nt.nranks,
+                     n);
+  } else if ((uint64_t)(d->score_hi - key_lo) >= (1ull << (32 - ib))) {
     return set_err(c, NW_ERANGE, "score range %d..%d with %u words does not fit 32-bit list keys", d->score_lo,
                    d->score_hi, n);
+  }
   const bool dev = flags & NW_DEVICE_PTRS;
   cudaStream_t s = c->stream;
   const size_t nlaunch = d->plan.launches.size();
@@ -636,6 +715,24 @@ nw_status topk_impl(nw_dict* d, uint32_t shard, uint32_t nshards, uint32_t k, ui
   base.nbins = hist ? need_bins : 0;
   base.stats = d_stats;
   base.err = d_err;
+  const int16_t* d_frac = nullptr;
+  if (norm) {
+    // one upload of the three tables, each at a 256-byte aligned offset
+    const size_t rank_b = nt.rank.size() * sizeof(uint16_t), smin_b = nt.smin.size() * sizeof(int16_t);
+    const size_t o_smin = (rank_b + 255) & ~(size_t)255, o_frac = (o_smin + smin_b + 255) & ~(size_t)255;
+    const size_t total = o_frac + nt.frac.size() * sizeof(int16_t);
+    NW_TRY(ctx_ensure(c, c->ws_norm, total, "normalised ranking tables"));
+    std::vector<char> h(total, 0);
+    std::memcpy(h.data(), nt.rank.data(), rank_b);
+    std::memcpy(h.data() + o_smin, nt.smin.data(), smin_b);
+    std::memcpy(h.data() + o_frac, nt.frac.data(), nt.frac.size() * sizeof(int16_t));
+    NW_CK(cudaMemcpyAsync(c->ws_norm.p, h.data(), total, cudaMemcpyHostToDevice, s));
+    NW_CK(cudaStreamSynchronize(s));  // the staging vector goes out of scope
+    base.norm_rank = c->ws_norm.as<uint16_t>();
+    base.norm_smin = reinterpret_cast<const int16_t*>(c->ws_norm.as<char>() + o_smin);
+    base.norm_lo = nt.lo;
+    d_frac = reinterpret_cast<const int16_t*>(c->ws_norm.as<char>() + o_frac);
+  }
   SideView side{d->ws.perm.as<uint32_t>(), c->ws_slots.as<uint32_t>(), c->ws_thr.as<uint32_t>()};
   const uint32_t* a_enc[3] = {d->ws.a_enc.as<uint32_t>(), nullptr, nullptr};
   const uint4* b_rec[3] = {d->ws.b_rec.as<uint4>(), nullptr, nullptr};
@@ -646,7 +743,7 @@ nw_status topk_impl(nw_dict* d, uint32_t shard, uint32_t nshards, uint32_t k, ui
   cudaEvent_t e_fin = nullptr;
   tm.begin(false, e_fin);
   NW_CK(launch_finalize(c->ws_slots.as<uint32_t>(), n, k, d->ws.perm.as<uint32_t>(), ib, base.imask, key_lo,
-                        out_idx, out_score, s));
+                        out_idx, out_score, s, d_frac, d->ws.slen.as<uint8_t>(), d->ws.rank.as<uint32_t>()));
   tm.end(false, e_fin);
   if (hist && dev) NW_CK(cudaMemcpyAsync(hist, c->ws_hist.p, sizeof(int64_t) * need_bins, cudaMemcpyDeviceToDevice, s));
   if (!dev) {

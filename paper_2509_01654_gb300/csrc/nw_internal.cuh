@@ -169,8 +169,9 @@ struct DpParams {
   uint32_t C1, C2;                // packed (s'_m + 1) and max(s'_x, 0), see the kernel
   int32_t match, mismatch, gap;
   int32_t mode;
-  int8_t* mat;                    // matrix mode: row-major upper triangle
+  int8_t* mat;                    // matrix mode: row-major upper triangle, entries [mat_lo, mat_hi) stored
   uint64_t n;
+  uint64_t mat_lo, mat_hi;        // (mat points at the buffer holding entry mat_lo, minus mat_lo)
   uint32_t k, ib, imask;          // list key = ((s - key_lo) << ib) | (imask - partner)
   int32_t key_lo;
   int32_t hist_mode;
@@ -180,6 +181,12 @@ struct DpParams {
   unsigned long long* stats;      // [0] list inserts
   uint32_t* err;
   const DictTerms* terms;         // batched launches: per-dictionary terms (device), else null
+  // length-normalised ranking (null = raw scores): rank of s / max(la, lb) at
+  // norm_rank[(s - norm_lo) * kBuckets + m], and the smallest s reaching rank r
+  // for longer length m at norm_smin[r * kBuckets + m]
+  const uint16_t* norm_rank;
+  const int16_t* norm_smin;
+  int32_t norm_lo;
 };
 
 // Scoring constants of the shifted recurrence (see the kernel).

@@ -137,7 +137,8 @@ cudaError_t launch_ingest_encode(const uint8_t* codes, const uint32_t* offsets, 
 __global__ void finalize_kernel(const uint32_t* __restrict__ slots, uint32_t nlists, uint32_t k,
                                 const uint32_t* __restrict__ perm, uint32_t ib, uint32_t imask,
                                 int32_t key_lo, uint32_t* __restrict__ out_idx,
-                                int16_t* __restrict__ out_score) {
+                                int16_t* __restrict__ out_score, const int16_t* __restrict__ norm_frac,
+                                const uint8_t* __restrict__ slen, const uint32_t* __restrict__ rank) {
   const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nlists) return;
   uint32_t keys[NW_MAX_K];
@@ -155,19 +156,30 @@ __global__ void finalize_kernel(const uint32_t* __restrict__ slots, uint32_t nli
       out_idx[o + r] = 0xffffffffu;
       out_score[o + r] = INT16_MIN;
     } else {
-      out_idx[o + r] = imask - (key & imask);
-      out_score[o + r] = (int16_t)((int32_t)(key >> ib) + key_lo);
+      const uint32_t partner = imask - (key & imask);
+      out_idx[o + r] = partner;
+      if (norm_frac) {
+        const uint32_t q = (key >> ib) - 1u;
+        uint32_t m = slen[w];
+        const uint32_t mp = slen[rank[partner]];
+        m = m > mp ? m : mp;
+        m = m > 0u ? m : 1u;
+        out_score[o + r] = (int16_t)(norm_frac[2 * q] * (int32_t)(m / (uint32_t)norm_frac[2 * q + 1]));
+      } else {
+        out_score[o + r] = (int16_t)((int32_t)(key >> ib) + key_lo);
+      }
     }
   }
 }
 
 cudaError_t launch_finalize(const uint32_t* slots, uint32_t nlists, uint32_t k, const uint32_t* perm,
                             uint32_t ib, uint32_t imask, int32_t key_lo, uint32_t* out_idx,
-                            int16_t* out_score, cudaStream_t s) {
+                            int16_t* out_score, cudaStream_t s, const int16_t* norm_frac, const uint8_t* slen,
+                            const uint32_t* rank) {
   if (nlists == 0) return cudaSuccess;
   const uint32_t blk = 128;
   finalize_kernel<<<(nlists + blk - 1) / blk, blk, 0, s>>>(slots, nlists, k, perm, ib, imask, key_lo,
-                                                           out_idx, out_score);
+                                                           out_idx, out_score, norm_frac, slen, rank);
   return cudaGetLastError();
 }
 

@@ -26,10 +26,14 @@ cudaError_t launch_ingest_encode(const uint8_t* codes, const uint32_t* offsets, 
                                  uint32_t* b_rec, uint32_t* brec_w, cudaStream_t s);
 constexpr uint32_t kIngestBlock = 256;
 
-// lists -> ranked (index, score) rows
+// lists -> ranked (index, score) rows.  With norm_frac (normalised ranking),
+// a key carries the rank r of s/m, whose reduced fraction is norm_frac[2r] /
+// norm_frac[2r+1]; the raw score is rebuilt from m = the longer length of the
+// pair (slen by sorted position, rank maps the partner to its position).
 cudaError_t launch_finalize(const uint32_t* slots, uint32_t nlists, uint32_t k, const uint32_t* perm,
                             uint32_t ib, uint32_t imask, int32_t key_lo, uint32_t* out_idx,
-                            int16_t* out_score, cudaStream_t s);
+                            int16_t* out_score, cudaStream_t s, const int16_t* norm_frac = nullptr,
+                            const uint8_t* slen = nullptr, const uint32_t* rank = nullptr);
 
 // explicit pairs of one encoded set
 struct PairsParams {

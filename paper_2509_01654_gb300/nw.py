@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "NW_OK", -1: "NW_EINVAL", -2: "NW_ENOMEM", -3: "NW_ERANGE", -
                 -5: "NW_ETIMEOUT", -6: "NW_EBUSY"}
 NW_DEVICE_PTRS = 0x1
 NW_ASYNC = 0x2
+NW_RANK_NORMALISED = 0x4
 MAX_WORD_LEN = 40
 MAX_K = 128
 MISSING_IDX = 0xFFFFFFFF
@@ -32,7 +33,8 @@ EXPORTED = [
     "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
     "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc", "nw_all_pairs_topk_noalloc",
     "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
-    "nw_batch_create", "nw_batch_run", "nw_batch_info_get", "nw_batch_free",
+    "nw_batch_create", "nw_batch_run", "nw_batch_info_get", "nw_batch_free", "nw_all_pairs_matrix_chunked",
+    "nw_debug_norm_tables",
 ]
 NW_BATCH_AUTOTUNE = 0x10
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -114,6 +116,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_dict_free.argtypes = [vp]
     L.nw_dict_free.restype = None
     L.nw_all_pairs_matrix.argtypes = [vp, vp, u32]
+    L.nw_all_pairs_matrix_chunked.argtypes = [vp, vp, u64, u32]
     L.nw_all_pairs_topk.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_all_pairs_topk_shard.argtypes = [vp, u32, u32, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_topk_merge.argtypes = [u32, u32, u32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
@@ -122,6 +125,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_measure_int_rates.argtypes = [vp, ctypes.c_double, ctypes.POINTER(IntRates)]
     L.nw_debug_enumerate_pairs.argtypes = [vp, u32, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
     L.nw_debug_fail_alloc.argtypes = [vp, u32]
+    L.nw_debug_norm_tables.argtypes = [ctypes.POINTER(Scoring), i32, i32, vp, vp, vp, u32, ctypes.POINTER(u32)]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.nw_server_submit.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u64)]
@@ -284,8 +288,20 @@ class Dictionary:
         _check(self.ctx.handle, load_library().nw_all_pairs_matrix(self.handle, _ptr(out)[0], _flags(out, async_=async_)))
         return out
 
-    def all_pairs_topk(self, k: int, nbr_idx=None, nbr_score=None, hist=True, shard=None, async_: bool = False):
-        """(idx[n, k] uint32, score[n, k] int16, hist int64 or None, hist_lo)."""
+    def all_pairs_matrix_chunked(self, chunk_bytes: int, out=None):
+        """The int8 upper triangle through a device buffer of chunk_bytes (host output)."""
+        E = self.n * (self.n - 1) // 2
+        if out is None:
+            out = np.empty(E, dtype=np.int8)
+        _check(self.ctx.handle, load_library().nw_all_pairs_matrix_chunked(self.handle, _ptr(out)[0], chunk_bytes, 0))
+        return out
+
+    def all_pairs_topk(self, k: int, nbr_idx=None, nbr_score=None, hist=True, shard=None, async_: bool = False,
+                       normalised: bool = False):
+        """(idx[n, k] uint32, score[n, k] int16, hist int64 or None, hist_lo).
+
+        normalised=True ranks neighbours by s / max(len_i, len_j) (Section 5);
+        scores stay raw."""
         n = self.n
         if nbr_idx is None:
             nbr_idx = _empty_like_kind(None, (n, k), np.uint32, None)
@@ -301,7 +317,7 @@ class Dictionary:
             nbins = int(h.shape[0])
         lo = ctypes.c_int32(0)
         L = load_library()
-        flags = _flags(nbr_idx, nbr_score, h, async_=async_)
+        flags = _flags(nbr_idx, nbr_score, h, async_=async_) | (NW_RANK_NORMALISED if normalised else 0)
         if shard is None:
             st = L.nw_all_pairs_topk(self.handle, k, _ptr(nbr_idx)[0], _ptr(nbr_score)[0], _ptr(h)[0],
                                      ctypes.byref(lo), nbins, flags)
@@ -397,6 +413,29 @@ def debug_enumerate_pairs(lengths, shard: int = 0, nshards: int = 1):
     if st != NW_OK:
         raise NwError(st, "nw_debug_enumerate_pairs failed")
     return a[:cnt.value], b[:cnt.value]
+
+
+def debug_norm_tables(scoring, lo: int, hi: int):
+    """(rank[hi-lo+1, 41] uint16, smin[R, 41] int16, frac[R, 2] int16) of NW_RANK_NORMALISED."""
+    L = load_library()
+    sc = Scoring(*scoring)
+    nr = ctypes.c_uint32(0)
+    nb = MAX_WORD_LEN + 1
+    rank = np.zeros((hi - lo + 1, nb), dtype=np.uint16)
+    z = np.zeros(1, dtype=np.int16)
+    st = L.nw_debug_norm_tables(ctypes.byref(sc), lo, hi, ctypes.c_void_p(rank.ctypes.data),
+                                ctypes.c_void_p(z.ctypes.data), ctypes.c_void_p(z.ctypes.data), 0, ctypes.byref(nr))
+    if st not in (NW_OK, NW_ERANGE):
+        raise NwError(st, "nw_debug_norm_tables failed")
+    R = nr.value
+    smin = np.zeros((max(R, 1), nb), dtype=np.int16)
+    frac = np.zeros((max(R, 1), 2), dtype=np.int16)
+    st = L.nw_debug_norm_tables(ctypes.byref(sc), lo, hi, ctypes.c_void_p(rank.ctypes.data),
+                                ctypes.c_void_p(smin.ctypes.data), ctypes.c_void_p(frac.ctypes.data), R,
+                                ctypes.byref(nr))
+    if st != NW_OK:
+        raise NwError(st, "nw_debug_norm_tables failed")
+    return rank, smin[:R], frac[:R]
 
 
 class Batch:

@@ -119,6 +119,17 @@ class WordList:
     def word(self, i: int) -> np.ndarray:
         return self.codes[int(self.offsets[i]):int(self.offsets[i + 1])]
 
+    @classmethod
+    def from_lists(cls, words, alphabet: int = 0) -> "WordList":
+        """Words given as lists of codes; alphabet defaults to the largest code + 1."""
+        lens = [len(w) for w in words]
+        offs = np.zeros(len(words) + 1, dtype=np.int64)
+        np.cumsum(lens, out=offs[1:])
+        flat = [int(c) for w in words for c in w]
+        codes = np.array(flat, dtype=np.uint8)
+        alphabet = alphabet or (max(flat) + 1 if flat else 1)
+        return cls(codes, offs.astype(np.uint32), alphabet)
+
     def subset(self, idx) -> "WordList":
         idx = np.asarray(idx, dtype=np.int64)
         lens = self.lengths[idx]

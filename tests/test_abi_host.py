@@ -123,3 +123,42 @@ def test_calls_fail_loudly_without_gpu(lib):
         nw.Context(0)
     assert e.value.status in (nw.NW_ECUDA, nw.NW_EINVAL)
     assert str(e.value)
+
+
+def _reach(sc, m):
+    """Score interval a pair whose longer word has m symbols can reach: between
+    the all-gap alignment and the diagonal alignments of the shorter word."""
+    match, mismatch, gap = sc
+    lo, hi = None, None
+    for la in range(0, m + 1):
+        allgap = (la + m) * gap
+        a = max(allgap, la * min(match, mismatch) + (m - la) * gap)
+        b = max(allgap, la * max(match, mismatch) + (m - la) * gap)
+        lo = a if lo is None else min(lo, a)
+        hi = b if hi is None else max(hi, b)
+    return lo, hi
+
+
+@pytest.mark.parametrize("sc,lo,hi", [((1, -1, -1), -40, 40), ((2, -3, -1), -80, 80), ((1, 0, 0), 0, 40),
+                                      ((3, -2, -2), -80, 120)])
+def test_normalised_rank_tables(lib, sc, lo, hi):
+    from fractions import Fraction
+    rank, smin, frac = nw.debug_norm_tables(sc, lo, hi)
+    R = frac.shape[0]
+    vals = [Fraction(int(frac[r, 0]), int(frac[r, 1])) for r in range(R)]
+    assert all(int(frac[r, 1]) > 0 for r in range(R))
+    assert all(vals[r] < vals[r + 1] for r in range(R - 1))  # strictly ascending, one rank per value
+    seen = set()
+    for m in range(nw.MAX_WORD_LEN + 1):
+        a, b = _reach(sc, m)
+        a, b = max(a, lo), min(b, hi)
+        for s in range(a, b + 1):
+            r = int(rank[s - lo, m])
+            assert vals[r] == Fraction(s, max(m, 1))
+            # stored in lowest terms
+            assert Fraction(int(frac[r, 0]), int(frac[r, 1])).denominator == int(frac[r, 1])
+            seen.add(r)
+        for r in range(R):
+            reach = [s for s in range(a, b + 1) if int(rank[s - lo, m]) >= r]
+            assert int(smin[r, m]) == (min(reach) if reach else 32767)
+    assert seen == set(range(R))  # every rank is some reachable weight

@@ -316,6 +316,57 @@ def test_topk_score_multiset_invariant_under_permutation(oracle_mod):
     assert np.array_equal(s1, s2[inv])
 
 
+def normalised_topk_by_fractions(M, lens, i, k):
+    """Word i's k best partners by Fraction(s, max(len_i, len_j) or 1), lower index first on ties."""
+    cand = [j for j in range(M.shape[0]) if j != i]
+    key = lambda j: (-Fraction(int(M[i, j]), max(lens[i], lens[j], 1)), j)
+    best = sorted(cand, key=key)[:k]
+    return np.array(best, dtype=np.int64), np.array([M[i, j] for j in best], dtype=np.int64)
+
+
+@pytest.mark.parametrize("sc", [(1, -1, -1), (2, -3, -1)])
+def test_topk_rows_normalised_against_fraction_sort(oracle_mod, sc):
+    # lengths 0 .. 9 (empty words included) with a small alphabet, so equal
+    # weights with different (s, m) -- 2/4 and 3/6 -- occur
+    w = synth.make_words(140, 4, 1.0, 4.0, 2.5, 0, 9, seed=23)
+    M = full_matrix(oracle_mod, w, sc)
+    lens = [len(w.word(i)) for i in range(w.n)]
+    k = 9
+    idx, score = oracle_mod.topk_rows_normalised(w, np.arange(w.n), k, sc)
+    _, raw_score = oracle_mod.topk_rows(w, np.arange(w.n), k, sc)
+    for i in range(w.n):
+        ej, es = normalised_topk_by_fractions(M, lens, i, k)
+        assert np.array_equal(idx[i].astype(np.int64), ej) and np.array_equal(score[i].astype(np.int64), es)
+    # the normalised order is not the raw one on this set
+    assert not np.array_equal(score, raw_score)
+
+
+def test_topk_rows_normalised_worked_cases(oracle_mod):
+    # Section 5's example: for puisant, epuisant (400/6) ranks above paysans (300/5)
+    g = read_golden("puisant_paysans_epuisant.txt")
+    names = ("puisant", "paysans", "epuisant")
+    w = synth.WordList.from_lists([ints(g[k][0]) for k in names])
+    sc = tuple(ints(g["scoring"][0]))
+    idx, score = oracle_mod.topk_rows_normalised(w, [0], 2, sc)
+    assert idx[0].tolist() == [2, 1] and score[0].tolist() == [4, 3]
+    # raw and normalised orders disagree: "ab" against a 12-symbol word that
+    # contains it (2 matches, 10 gaps: -8, weight -8/12) and against "cd"
+    # (2 mismatches: -2, weight -2/2); by raw score "cd" comes first, by
+    # weight the long word does; a length other than the longer one would
+    # put "cd" first as well
+    w2 = synth.WordList.from_lists([[1, 2], [4, 5], [1, 2] + [3] * 10])
+    s = (1, -1, -1)
+    assert brute_force([1, 2], [1, 2] + [3] * 10, s) == -8 and brute_force([1, 2], [4, 5], s) == -2
+    ri, rs = oracle_mod.topk_rows(w2, [0], 2, s)
+    ni, ns = oracle_mod.topk_rows_normalised(w2, [0], 2, s)
+    assert ri[0].tolist() == [1, 2] and rs[0].tolist() == [-2, -8]
+    assert ni[0].tolist() == [2, 1] and ns[0].tolist() == [-8, -2]
+    # two empty words have weight s / 1 = 0: above any negative weight, below any positive one
+    w3 = synth.WordList.from_lists([[], [], [7], [1, 2]])
+    ni, ns = oracle_mod.topk_rows_normalised(w3, [0], 3, s)
+    assert ni[0].tolist() == [1, 2, 3] and ns[0].tolist() == [0, -1, -2]
+
+
 def test_query_topk_against_lexsort(oracle_mod):
     d = synth.make_words(180, 6, 1.0, 5.0, 2.0, 1, 9, seed=31)
     q = synth.make_uniform_length_words(25, 6, 1.0, 0, 9, seed=32)
