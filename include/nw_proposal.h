@@ -1,0 +1,126 @@
+/*
+ * nw_proposal.h -- learned neighbour-candidate proposal for libnw.
+ *
+ * The paper scores every pair (Section 4) and notes that this cost grows
+ * with the square of the dictionary.  This part of the library adds a
+ * learned shortcut that it does not have: a character CNN maps each word to
+ * 64 values whose dot products approximate the normalised alignment weight
+ * s / max(len(A), len(B)) of Section 5; each word's C best dot products
+ * propose candidates, and Algorithm 1 rescores only those candidates
+ * exactly.  The result is an approximate top-k whose scores are exact.
+ *
+ * Network (fixed shape; float32 parameters, float32 arithmetic):
+ *   x_t = emb[code_t]                      (32 values per position)
+ *   three times: x_t <- ReLU(b + sum_{tap=0..2} W[., tap, .] x_{t+tap-1})
+ *                (128 channels, zero outside the word)
+ *   p = mean over the word's positions of x_t (zero for an empty word)
+ *   e = Wl p + bl                          (64 values)
+ * Flat parameter layout, in order: emb[alphabet][32], W1[128][3][32],
+ * b1[128], W2[128][3][128], b2[128], W3[128][3][128], b3[128], Wl[64][128],
+ * bl[64].
+ *
+ * Conventions as in nw.h: status codes, NW_DEVICE_PTRS / NW_ASYNC flags,
+ * original word indices, missing list entries (UINT32_MAX, INT16_MIN).
+ */
+#ifndef NW_PROPOSAL_H
+#define NW_PROPOSAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "nw.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NW_EMBED_DIM 64
+#define NW_MAX_CANDIDATES 512
+
+typedef struct nw_model nw_model;
+
+/* A model for codes < alphabet (<= 256) with parameters drawn from a
+ * SplitMix64 stream of `seed` (embedding uniform on [-sqrt(3), sqrt(3)],
+ * weights uniform on +-sqrt(6 / fan_in), biases zero) and Adam moments at
+ * zero.  Owned by the caller; freed by nw_model_free. */
+nw_status nw_model_create(nw_ctx *ctx, uint32_t alphabet, uint64_t seed, nw_model **out);
+void nw_model_free(nw_model *model);
+
+/* Number of float32 parameters (the flat layout above). */
+uint64_t nw_model_param_count(const nw_model *model);
+
+/* Copies the flat parameters out of / into the model (nparams floats; host
+ * buffers, or device buffers with NW_DEVICE_PTRS).  Setting parameters also
+ * resets the Adam moments and step. */
+nw_status nw_model_get_params(nw_model *model, float *params, uint32_t flags);
+nw_status nw_model_set_params(nw_model *model, const float *params, uint32_t flags);
+
+/* Embeddings of every word of `dict` (whose alphabet must not exceed the
+ * model's): out[i * 64 + d], original order. */
+nw_status nw_model_embed(nw_model *model, nw_dict *dict, float *out, uint32_t flags);
+
+/* Loss and gradient of m pairs without changing the model:
+ *   loss = (1/m) sum_p (e[pi[p]] . e[pj[p]] - target[p])^2
+ * grad receives nparams floats (NULL to skip).  pi, pj: original indices;
+ * m >= 1. */
+nw_status nw_model_loss_grad(nw_model *model, nw_dict *dict, const uint32_t *pi, const uint32_t *pj,
+                             const float *target, uint32_t m, float *loss, float *grad, uint32_t flags);
+
+/* Training by Adam on pairs drawn on the device, each labelled by Algorithm
+ * 1 with the dictionary's scoring: target = s / max(len_i, len_j, 1).
+ * Each step draws batch_pairs pairs from a SplitMix64 stream of `seed`: a
+ * fraction nbr_fraction take j from the given neighbour lists of a uniform i
+ * (nbr: n x knb original indices, UINT32_MAX entries skipped; NULL for
+ * none), the rest are uniform pairs i != j.  `losses` (steps floats, may be
+ * NULL) receives each step's mean loss.  Steps run as one captured CUDA
+ * graph replayed `steps` times. */
+typedef struct {
+    uint32_t steps;
+    uint32_t batch_pairs;   /* <= 65536 */
+    float lr, beta1, beta2, eps;
+    float nbr_fraction;     /* in [0, 1] */
+    uint64_t seed;
+} nw_train_config;
+
+nw_status nw_model_train(nw_model *model, nw_dict *dict, const nw_train_config *cfg, const uint32_t *nbr,
+                         uint32_t knb, float *losses, uint32_t flags);
+
+/* Symmetric 8-bit quantisation of n x 64 float embeddings with one scale:
+ * scale = max|E| / 127 (float32), q = round-half-even(E / scale) clamped to
+ * [-127, 127]; all q = 0 when max|E| = 0.  q: n * 64 int8. */
+nw_status nw_quantize_embeddings(nw_ctx *ctx, const float *E, uint32_t n, int8_t *q, float *scale,
+                                 uint32_t flags);
+
+/* For every row i of the n x 64 int8 matrix q, the C other rows j with the
+ * largest dot product q_i . q_j (exact integers), higher first and lower j
+ * first on equal values: idx[i * C + r], dot[i * C + r].  Rows with fewer
+ * than C others end in (UINT32_MAX, INT32_MIN).  1 <= C <= NW_MAX_CANDIDATES.
+ * The products run on the tensor cores in bf16 with float32 accumulation,
+ * which is exact for these integers. */
+nw_status nw_dot_topk(nw_ctx *ctx, const int8_t *q, uint32_t n, uint32_t C, uint32_t *idx, int32_t *dot,
+                      uint32_t flags);
+
+/* Exact rescoring: for every word i of `dict`, Algorithm 1's score against
+ * each candidate cand[i * C + r] (original indices; UINT32_MAX entries are
+ * skipped; candidates of a row must be distinct and differ from i), and the
+ * k best (higher score first, lower index on ties) into nbr_idx / nbr_score
+ * (n * k each).  1 <= k <= NW_MAX_K, 1 <= C <= NW_MAX_CANDIDATES. */
+nw_status nw_rescore_topk(nw_dict *dict, const uint32_t *cand, uint32_t C, uint32_t k, uint32_t *nbr_idx,
+                          int16_t *nbr_score, uint32_t flags);
+
+/* Stage times of the last nw_proposal_topk call, milliseconds. */
+typedef struct {
+    double embed_ms, quantize_ms, candidates_ms, rescore_ms, total_ms;
+} nw_proposal_profile;
+
+/* The whole proposal path for `dict`: embed every word, quantise, take C
+ * candidates per word by dot product, rescore them exactly and keep the k
+ * best (as nw_rescore_topk).  `prof` may be NULL. */
+nw_status nw_proposal_topk(nw_model *model, nw_dict *dict, uint32_t C, uint32_t k, uint32_t *nbr_idx,
+                           int16_t *nbr_score, nw_proposal_profile *prof, uint32_t flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NW_PROPOSAL_H */

@@ -53,6 +53,8 @@ void nw_destroy(nw_ctx* c) {
   cudaStreamSynchronize(c->stream);
   std::vector<nw_dict*> ds(c->dicts.begin(), c->dicts.end());
   for (nw_dict* d : ds) nw_dict_free(d);
+  const std::vector<nw_model*> ms(c->models.begin(), c->models.end());
+  for (nw_model* m : ms) nw_model_free(m);
   ctx_free(c, c->ws_slots);
   ctx_free(c, c->ws_thr);
   ctx_free(c, c->ws_hist);

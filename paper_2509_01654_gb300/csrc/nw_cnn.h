@@ -1,0 +1,113 @@
+// nw_cnn.h -- kernels of the proposal network (see include/nw_proposal.h).
+//
+// Activations of a batch of Bw words use a padded layout: word w owns rows
+// [w * Lp, (w + 1) * Lp) of every T x C activation matrix (T = Bw * Lp),
+// row w * Lp + t holding position t; rows at t >= len(w) are kept at zero,
+// which is the convolutions' zero padding.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nw {
+namespace cnn {
+
+constexpr int kEmb = 32;
+constexpr int kCh = 128;
+constexpr int kOut = 64;
+constexpr int kTaps = 3;
+
+// Offsets of the parameter blocks in the flat vector for `alphabet` codes.
+struct Layout {
+  uint64_t emb, W1, b1, W2, b2, W3, b3, Wl, bl, total;
+};
+inline Layout layout(uint32_t alphabet) {
+  Layout L{};
+  uint64_t o = 0;
+  L.emb = o; o += (uint64_t)alphabet * kEmb;
+  L.W1 = o; o += (uint64_t)kCh * kTaps * kEmb;
+  L.b1 = o; o += kCh;
+  L.W2 = o; o += (uint64_t)kCh * kTaps * kCh;
+  L.b2 = o; o += kCh;
+  L.W3 = o; o += (uint64_t)kCh * kTaps * kCh;
+  L.b3 = o; o += kCh;
+  L.Wl = o; o += (uint64_t)kOut * kCh;
+  L.bl = o; o += kOut;
+  L.total = o;
+  return L;
+}
+
+// Per-word inputs of a batch, gathered from a dictionary's device arrays.
+struct WordSrc {
+  const uint32_t* widx;   // Bw original indices
+  const uint32_t* rank;   // original -> sorted position
+  const uint8_t* slen;    // sorted position -> length
+  const uint32_t* aoff;   // sorted position -> a_enc offset
+  const uint32_t* a_enc;  // encoded symbols: code = (v & 0xffff) >> shift
+  uint32_t shift;
+  uint32_t n;             // words of the dictionary (bound of widx)
+};
+
+// GEMM epilogue: out = acc (+ bias[n]) (ReLU) (x (gate[m][n] > 0)) (x rowmask),
+// or atomicAdd of acc (split-K accumulation into a zeroed C).
+struct Epi {
+  const float* bias = nullptr;
+  bool relu = false;
+  const float* gate = nullptr;   // same layout as C
+  const int* rowlen = nullptr;   // mask rows whose position (m % Lp) >= rowlen[m / Lp]
+  int Lp = 1;
+  bool atomic = false;
+};
+
+// The network's matrix products (float32, tiled on the CUDA cores).  T rows
+// of padded activations, B words; W is [Co][3][Ci], Wl is [Co][Ci].
+//   conv_fwd: Y[T][Co]  = im2col(X[T][Ci]) . W^T            (epilogue e)
+//   conv_dw:  dW[Co][3Ci] += dY^T . im2col(X)               (split over T, atomic)
+//   conv_dx:  dX[T][Ci] = sum_tap shift_tap(dY) . W[.][tap]  (col2im folded in; epilogue e)
+//   lin_fwd:  E[B][Co]  = P[B][Ci] . Wl^T                   (epilogue e)
+//   lin_dw:   dWl[Co][Ci] += dE^T . P                       (split over B, atomic)
+//   lin_dx:   dP[B][Ci] = dE[B][Co] . Wl
+cudaError_t conv_fwd(const float* X, int Ci, const float* W, int Co, int T, int Lp, float* Y, const Epi& e,
+                     cudaStream_t s);
+cudaError_t conv_dw(const float* dY, int Co, const float* X, int Ci, int T, int Lp, float* dW, int nsm,
+                    cudaStream_t s);
+cudaError_t conv_dx(const float* dY, int Co, const float* W, int Ci, int T, int Lp, float* dX, const Epi& e,
+                    cudaStream_t s);
+cudaError_t lin_fwd(const float* P, int Ci, const float* Wl, int Co, int B, float* E, const Epi& e, cudaStream_t s);
+cudaError_t lin_dw(const float* dE, int Co, const float* P, int Ci, int B, float* dWl, int nsm, cudaStream_t s);
+cudaError_t lin_dx(const float* dE, int Co, const float* Wl, int Ci, int B, float* dP, cudaStream_t s);
+
+cudaError_t gather_words(const WordSrc& src, int Bw, int Lp, const float* emb, int* rowlen, int32_t* codes,
+                         float* X0, uint32_t* err, uint32_t alphabet, cudaStream_t s);
+cudaError_t mean_pool(const float* Y, const int* rowlen, int Bw, int Lp, float* P, cudaStream_t s);
+cudaError_t mean_pool_bwd(const float* dP, const float* Y, const int* rowlen, int Bw, int Lp, float* dY,
+                          cudaStream_t s);
+// pairs are word slots (2p, 2p + 1); loss_acc += sum (pred - y)^2 / m (if non-null)
+cudaError_t pair_loss(const float* E, const float* target, int m, float* dE, float* loss_acc, cudaStream_t s);
+cudaError_t col_sum(const float* Y, int rows, int cols, float* out, cudaStream_t s);  // out += column sums
+cudaError_t emb_scatter(const float* dX0, const int32_t* codes, int T, float* demb, cudaStream_t s);
+cudaError_t adam(float* theta, const float* g, float* m, float* v, uint64_t n, const uint32_t* step, float lr,
+                 float b1, float b2, float eps, cudaStream_t s);
+cudaError_t bump_step(uint32_t* step, cudaStream_t s);
+// losses[*step - 1 - step0] = *cur (when inside [0, nsteps)), then *cur = 0
+cudaError_t record_loss(float* cur, float* losses, const uint32_t* step, uint32_t step0, uint32_t nsteps,
+                        cudaStream_t s);
+
+// training pairs of one step: pi/pj, word slots widx[2p], widx[2p + 1]
+struct PairDraw {
+  uint64_t seed;
+  const uint32_t* step;   // device step counter (graph replays read it)
+  uint32_t n, m;
+  const uint32_t* nbr;    // n x knb or null
+  uint32_t knb;
+  uint32_t n_nbr;         // pairs [0, n_nbr) come from the lists
+};
+cudaError_t draw_pairs(const PairDraw& d, uint32_t* pi, uint32_t* pj, uint32_t* widx, cudaStream_t s);
+// target[p] = score[p] / max(len_i, len_j, 1)
+cudaError_t pair_targets(const int16_t* score, const uint32_t* pi, const uint32_t* pj, const uint32_t* rank,
+                         const uint8_t* slen, int m, float* target, cudaStream_t s);
+cudaError_t interleave_pairs(const uint32_t* pi, const uint32_t* pj, int m, uint32_t* widx, cudaStream_t s);
+cudaError_t iota(uint32_t* out, uint32_t base, int count, cudaStream_t s);
+
+}  // namespace cnn
+}  // namespace nw

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "nw.h"
+#include "nw_proposal.h"
 #include "nw_internal.cuh"
 #include "nw_launch.h"
 
@@ -72,6 +73,7 @@ struct nw_ctx {
   nw_profile prof{};
   int sm_count = 0;
   std::set<nw_dict*> dicts;
+  std::set<nw_model*> models;
   std::atomic<int> busy{0};
   // grow-only workspace
   DevBuf ws_slots, ws_thr, ws_hist, ws_small, ws_out_idx, ws_out_score, ws_mat, ws_pairs, ws_segs, ws_norm;

@@ -7,6 +7,8 @@
 
 #include "nw_dp.cuh"
 #include "nw_launch.h"
+#include "nw_proposal.h"
+#include "nw_proposal_internal.h"
 
 namespace nw {
 
@@ -59,6 +61,94 @@ __global__ void __launch_bounds__(128) pairs_kernel(const PairsParams P) {
   if (li > lj) { pa = rj; pb = ri; la = lj; lb = li; }
   P.out[p] = (int16_t)pair_dispatch(lb, P, pa, la, pb);
 }
+
+// one thread per candidate of the proposal path: the same computation as
+// pairs_kernel for (i, cand[i * C + r])
+__global__ void __launch_bounds__(128) rescore_kernel(const PairsParams P, const uint32_t* __restrict__ cand,
+                                                      uint32_t C, int32_t* __restrict__ score) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (uint64_t)P.n * C) return;
+  const uint32_t i = (uint32_t)(p / C);
+  const uint32_t j = cand[p];
+  if (j == 0xffffffffu) {
+    score[p] = INT32_MIN;
+    return;
+  }
+  if (j >= P.n || j == i) {
+    atomicOr(P.err, kErrInput);
+    score[p] = INT32_MIN;
+    return;
+  }
+  const uint32_t ri = __ldg(P.rank + i), rj = __ldg(P.rank + j);
+  const int li = __ldg(P.slen + ri), lj = __ldg(P.slen + rj);
+  uint32_t pa = ri, pb = rj;
+  int la = li, lb = lj;
+  if (li > lj) { pa = rj; pb = ri; la = lj; lb = li; }
+  score[p] = pair_dispatch(lb, P, pa, la, pb);
+}
+
+constexpr int kSelPerLane = NW_MAX_CANDIDATES / 32;
+
+// one warp per row: repeated warp-wide maximum over (score, reversed index) keys
+__global__ void select_topk_kernel(const uint32_t* __restrict__ cand, const int32_t* __restrict__ score, uint32_t n,
+                                   uint32_t C, uint32_t k, uint32_t* __restrict__ out_idx,
+                                   int16_t* __restrict__ out_score) {
+  const uint32_t row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  uint64_t keys[kSelPerLane];
+#pragma unroll
+  for (int q = 0; q < kSelPerLane; ++q) {
+    const uint32_t c = (uint32_t)lane + 32u * q;
+    keys[q] = 0ull;
+    if (c < C) {
+      const int32_t s = score[(size_t)row * C + c];
+      if (s != INT32_MIN)
+        keys[q] = ((uint64_t)(uint32_t)(s + 0x80000000) << 32) | (0xffffffffu - cand[(size_t)row * C + c]);
+    }
+  }
+  for (uint32_t r = 0; r < k; ++r) {
+    uint64_t best = 0ull;
+    int bq = -1;
+#pragma unroll
+    for (int q = 0; q < kSelPerLane; ++q)
+      if (keys[q] > best) { best = keys[q]; bq = q; }
+    uint64_t wb = best;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t other = __shfl_xor_sync(0xffffffffu, wb, o);
+      wb = other > wb ? other : wb;
+    }
+    if (wb != 0ull && best == wb) {
+#pragma unroll
+      for (int q = 0; q < kSelPerLane; ++q)
+        if (q == bq) keys[q] = 0ull;
+    }
+    if (lane == 0) {
+      const size_t o = (size_t)row * k + r;
+      out_idx[o] = wb ? 0xffffffffu - (uint32_t)wb : 0xffffffffu;
+      out_score[o] = wb ? (int16_t)(int32_t)((uint32_t)(wb >> 32) - 0x80000000u) : (int16_t)INT16_MIN;
+    }
+  }
+}
+
+namespace prop {
+
+cudaError_t rescore(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s) {
+  const uint64_t m = (uint64_t)P.n * C;
+  if (m == 0) return cudaSuccess;
+  rescore_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(P, cand, C, score);
+  return cudaGetLastError();
+}
+
+cudaError_t select_topk(const uint32_t* cand, const int32_t* score, uint32_t n, uint32_t C, uint32_t k,
+                        uint32_t* out_idx, int16_t* out_score, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  select_topk_kernel<<<(n + 7) / 8, 256, 0, s>>>(cand, score, n, C, k, out_idx, out_score);
+  return cudaGetLastError();
+}
+
+}  // namespace prop
 
 cudaError_t launch_pairs(const PairsParams& p, cudaStream_t s) {
   if (p.m == 0) return cudaSuccess;

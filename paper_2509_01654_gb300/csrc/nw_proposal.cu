@@ -1,0 +1,667 @@
+// nw_proposal.cu -- the learned candidate proposal (include/nw_proposal.h):
+// the model object, its forward and backward passes over a dictionary's
+// device-resident words, the training loop (one captured CUDA graph per
+// step, replayed), and the proposal path (embed, quantise, dot-product
+// top-C, exact rescoring).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "nw_cnn.h"
+#include "nw_host.h"
+#include "nw_proposal.h"
+#include "nw_proposal_internal.h"
+
+using namespace nw;
+
+struct nw_model {
+  nw_ctx* ctx = nullptr;
+  uint32_t alphabet = 0;
+  cnn::Layout L{};
+  cudaStream_t stream = nullptr;
+  uint32_t steps_done = 0;  // mirror of the device step counter
+  DevBuf params, grads, adam_m, adam_v, small;  // small: step counter, loss accumulator, error flags, amax
+  // forward/backward scratch for cap_words words of cap_Lp positions
+  int cap_words = 0, cap_Lp = 0;
+  DevBuf widx, rowlen, codes, X0, Y1, Y2, Y3, P, E, dE, dP, dYa, dYb, dX0;
+  // training pairs
+  uint32_t cap_pairs = 0;
+  DevBuf pi, pj, target, score16;
+  // proposal path
+  DevBuf Eall, Qb, topbuf, cand, cand_dot, cand_score, nbr;
+};
+
+namespace {
+
+constexpr int kMaxRowsPerPass = 1 << 20;  // padded positions per forward pass of nw_model_embed
+
+float* fptr(const DevBuf& b, uint64_t off = 0) { return b.as<float>() + off; }
+
+uint32_t* step_ptr(nw_model* M) { return M->small.as<uint32_t>(); }
+float* loss_ptr(nw_model* M) { return reinterpret_cast<float*>(M->small.as<char>() + 4); }
+uint32_t* err_ptr(nw_model* M) { return reinterpret_cast<uint32_t*>(M->small.as<char>() + 8); }
+unsigned int* amax_ptr(nw_model* M) { return reinterpret_cast<unsigned int*>(M->small.as<char>() + 12); }
+
+void model_free_buffers(nw_model* M) {
+  nw_ctx* c = M->ctx;
+  DevBuf* bufs[] = {&M->params, &M->grads, &M->adam_m, &M->adam_v, &M->small, &M->widx, &M->rowlen,
+                    &M->codes, &M->X0, &M->Y1, &M->Y2, &M->Y3, &M->P, &M->E, &M->dE, &M->dP, &M->dYa,
+                    &M->dYb, &M->dX0, &M->pi, &M->pj, &M->target, &M->score16, &M->Eall, &M->Qb,
+                    &M->topbuf, &M->cand, &M->cand_dot, &M->cand_score, &M->nbr};
+  for (DevBuf* b : bufs) ctx_free(c, *b);
+}
+
+// scratch for Bw words of Lp positions
+nw_status ensure_scratch(nw_model* M, int Bw, int Lp) {
+  nw_ctx* c = M->ctx;
+  if (Bw <= M->cap_words && Lp <= M->cap_Lp) return NW_OK;
+  const int W = std::max(Bw, M->cap_words), Lq = std::max(Lp, M->cap_Lp);
+  const size_t T = (size_t)W * Lq;
+  if (T > (size_t)INT32_MAX / cnn::kCh) return set_err(c, NW_EINVAL, "batch of %d words x %d positions too large", W, Lq);
+  NW_TRY(ctx_ensure(c, M->widx, sizeof(uint32_t) * W, "model word indices"));
+  NW_TRY(ctx_ensure(c, M->rowlen, sizeof(int) * W, "model word lengths"));
+  NW_TRY(ctx_ensure(c, M->codes, sizeof(int32_t) * T, "model codes"));
+  NW_TRY(ctx_ensure(c, M->X0, sizeof(float) * T * cnn::kEmb, "model activations"));
+  NW_TRY(ctx_ensure(c, M->dX0, sizeof(float) * T * cnn::kEmb, "model activations"));
+  DevBuf* big[] = {&M->Y1, &M->Y2, &M->Y3, &M->dYa, &M->dYb};
+  for (DevBuf* b : big) NW_TRY(ctx_ensure(c, *b, sizeof(float) * T * cnn::kCh, "model activations"));
+  NW_TRY(ctx_ensure(c, M->P, sizeof(float) * W * cnn::kCh, "model pooled"));
+  NW_TRY(ctx_ensure(c, M->dP, sizeof(float) * W * cnn::kCh, "model pooled"));
+  NW_TRY(ctx_ensure(c, M->E, sizeof(float) * W * cnn::kOut, "model embeddings"));
+  NW_TRY(ctx_ensure(c, M->dE, sizeof(float) * W * cnn::kOut, "model embeddings"));
+  M->cap_words = W;
+  M->cap_Lp = Lq;
+  return NW_OK;
+}
+
+nw_status ensure_pairs(nw_model* M, uint32_t m) {
+  nw_ctx* c = M->ctx;
+  if (m <= M->cap_pairs) return NW_OK;
+  NW_TRY(ctx_ensure(c, M->pi, sizeof(uint32_t) * m, "training pairs"));
+  NW_TRY(ctx_ensure(c, M->pj, sizeof(uint32_t) * m, "training pairs"));
+  NW_TRY(ctx_ensure(c, M->target, sizeof(float) * m, "training targets"));
+  NW_TRY(ctx_ensure(c, M->score16, sizeof(int16_t) * m, "training scores"));
+  M->cap_pairs = m;
+  return NW_OK;
+}
+
+int padded_len(const nw_dict* d) { return std::max<int>(1, (int)d->ws.max_len); }
+
+cnn::WordSrc word_src(const nw_dict* d, const uint32_t* widx) {
+  cnn::WordSrc s;
+  s.widx = widx;
+  s.rank = d->ws.rank.as<uint32_t>();
+  s.slen = d->ws.slen.as<uint8_t>();
+  s.aoff = d->ws.aoff.as<uint32_t>();
+  s.a_enc = d->ws.a_enc.as<uint32_t>();
+  s.shift = d->ss.shift;
+  s.n = d->ws.n;
+  return s;
+}
+
+// embeddings of Bw words (M->widx) into M->E
+nw_status forward(nw_model* M, const nw_dict* d, int Bw, int Lp, cudaStream_t s) {
+  nw_ctx* c = M->ctx;
+  const cnn::Layout& L = M->L;
+  const int T = Bw * Lp;
+  const float* W = fptr(M->params);
+  int* rowlen = M->rowlen.as<int>();
+  NW_CK(cnn::gather_words(word_src(d, M->widx.as<uint32_t>()), Bw, Lp, W + L.emb, rowlen, M->codes.as<int32_t>(),
+                          fptr(M->X0), err_ptr(M), M->alphabet, s));
+  cnn::Epi e;
+  e.relu = true;
+  e.rowlen = rowlen;
+  e.Lp = Lp;
+  e.bias = W + L.b1;
+  NW_CK(cnn::conv_fwd(fptr(M->X0), cnn::kEmb, W + L.W1, cnn::kCh, T, Lp, fptr(M->Y1), e, s));
+  e.bias = W + L.b2;
+  NW_CK(cnn::conv_fwd(fptr(M->Y1), cnn::kCh, W + L.W2, cnn::kCh, T, Lp, fptr(M->Y2), e, s));
+  e.bias = W + L.b3;
+  NW_CK(cnn::conv_fwd(fptr(M->Y2), cnn::kCh, W + L.W3, cnn::kCh, T, Lp, fptr(M->Y3), e, s));
+  NW_CK(cnn::mean_pool(fptr(M->Y3), rowlen, Bw, Lp, fptr(M->P), s));
+  cnn::Epi el;
+  el.bias = W + L.bl;
+  NW_CK(cnn::lin_fwd(fptr(M->P), cnn::kCh, W + L.Wl, cnn::kOut, Bw, fptr(M->E), el, s));
+  return NW_OK;
+}
+
+// gradient of the pair loss (pairs = word slots 2p, 2p + 1; targets in M->target) into M->grads
+nw_status backward(nw_model* M, int m, int Lp, cudaStream_t s) {
+  nw_ctx* c = M->ctx;
+  const cnn::Layout& L = M->L;
+  const int Bw = 2 * m, T = Bw * Lp;
+  const float* W = fptr(M->params);
+  float* G = fptr(M->grads);
+  const int* rowlen = M->rowlen.as<int>();
+  const int nsm = c->sm_count;
+  NW_CK(cudaMemsetAsync(G, 0, sizeof(float) * L.total, s));
+  NW_CK(cnn::pair_loss(fptr(M->E), fptr(M->target), m, fptr(M->dE), loss_ptr(M), s));
+  NW_CK(cnn::lin_dw(fptr(M->dE), cnn::kOut, fptr(M->P), cnn::kCh, Bw, G + L.Wl, nsm, s));
+  NW_CK(cnn::col_sum(fptr(M->dE), Bw, cnn::kOut, G + L.bl, s));
+  NW_CK(cnn::lin_dx(fptr(M->dE), cnn::kOut, W + L.Wl, cnn::kCh, Bw, fptr(M->dP), s));
+  NW_CK(cnn::mean_pool_bwd(fptr(M->dP), fptr(M->Y3), rowlen, Bw, Lp, fptr(M->dYa), s));
+  // layer 3: dYa = dY3
+  NW_CK(cnn::conv_dw(fptr(M->dYa), cnn::kCh, fptr(M->Y2), cnn::kCh, T, Lp, G + L.W3, nsm, s));
+  NW_CK(cnn::col_sum(fptr(M->dYa), T, cnn::kCh, G + L.b3, s));
+  cnn::Epi e;
+  e.rowlen = rowlen;
+  e.Lp = Lp;
+  e.gate = fptr(M->Y2);
+  NW_CK(cnn::conv_dx(fptr(M->dYa), cnn::kCh, W + L.W3, cnn::kCh, T, Lp, fptr(M->dYb), e, s));
+  // layer 2: dYb = dY2
+  NW_CK(cnn::conv_dw(fptr(M->dYb), cnn::kCh, fptr(M->Y1), cnn::kCh, T, Lp, G + L.W2, nsm, s));
+  NW_CK(cnn::col_sum(fptr(M->dYb), T, cnn::kCh, G + L.b2, s));
+  e.gate = fptr(M->Y1);
+  NW_CK(cnn::conv_dx(fptr(M->dYb), cnn::kCh, W + L.W2, cnn::kCh, T, Lp, fptr(M->dYa), e, s));
+  // layer 1: dYa = dY1
+  NW_CK(cnn::conv_dw(fptr(M->dYa), cnn::kCh, fptr(M->X0), cnn::kEmb, T, Lp, G + L.W1, nsm, s));
+  NW_CK(cnn::col_sum(fptr(M->dYa), T, cnn::kCh, G + L.b1, s));
+  e.gate = nullptr;
+  NW_CK(cnn::conv_dx(fptr(M->dYa), cnn::kCh, W + L.W1, cnn::kEmb, T, Lp, fptr(M->dX0), e, s));
+  NW_CK(cnn::emb_scatter(fptr(M->dX0), M->codes.as<int32_t>(), T, G + L.emb, s));
+  return NW_OK;
+}
+
+nw_status check_err(nw_model* M, cudaStream_t s) {
+  nw_ctx* c = M->ctx;
+  uint32_t err = 0;
+  NW_CK(cudaMemcpyAsync(&err, err_ptr(M), sizeof err, cudaMemcpyDeviceToHost, s));
+  NW_CK(cudaStreamSynchronize(s));
+  if (err) {
+    NW_CK(cudaMemsetAsync(err_ptr(M), 0, sizeof(uint32_t), s));
+    return set_err(c, NW_EINVAL, "invalid word index or code in the input");
+  }
+  return NW_OK;
+}
+
+nw_status check_model_dict(nw_model* M, nw_dict* d) {
+  nw_ctx* c = M->ctx;
+  if (d->ctx != c) return set_err(c, NW_EINVAL, "the dictionary belongs to another context");
+  if (d->alphabet > M->alphabet)
+    return set_err(c, NW_EINVAL, "dictionary alphabet %u exceeds the model's %u", d->alphabet, M->alphabet);
+  // the dictionary's uploads ran on the context stream
+  NW_CK(cudaStreamSynchronize(c->stream));
+  return NW_OK;
+}
+
+// copy n elements of T between host/device according to `dev`
+template <class T>
+nw_status copy_in(nw_ctx* c, T* dst, const T* src, size_t n, bool dev, cudaStream_t s) {
+  if (n) NW_CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return NW_OK;
+}
+template <class T>
+nw_status copy_out(nw_ctx* c, T* dst, const T* src, size_t n, bool dev, cudaStream_t s) {
+  if (n) NW_CK(cudaMemcpyAsync(dst, src, sizeof(T) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  return NW_OK;
+}
+
+uint64_t splitmix64_next(uint64_t& st) {
+  uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// embeddings of all n words into M->Eall (n x 64)
+nw_status embed_all(nw_model* M, nw_dict* d, cudaStream_t s) {
+  nw_ctx* c = M->ctx;
+  const uint32_t n = d->ws.n;
+  const int Lp = padded_len(d);
+  const int chunk = std::max(1, kMaxRowsPerPass / Lp);
+  NW_TRY(ensure_scratch(M, (int)std::min<uint32_t>(n, (uint32_t)chunk), Lp));
+  NW_TRY(ctx_ensure(c, M->Eall, sizeof(float) * std::max<size_t>(1, (size_t)n * cnn::kOut), "embeddings"));
+  for (uint32_t w0 = 0; w0 < n; w0 += (uint32_t)chunk) {
+    const int Bw = (int)std::min<uint32_t>((uint32_t)chunk, n - w0);
+    NW_CK(cnn::iota(M->widx.as<uint32_t>(), w0, Bw, s));
+    NW_TRY(forward(M, d, Bw, Lp, s));
+    NW_CK(cudaMemcpyAsync(fptr(M->Eall, (uint64_t)w0 * cnn::kOut), fptr(M->E), sizeof(float) * Bw * cnn::kOut,
+                          cudaMemcpyDeviceToDevice, s));
+  }
+  return NW_OK;
+}
+
+// the dictionary's encoded words as the pairs kernel reads them
+PairsParams pairs_params(const nw_dict* d, uint32_t* err) {
+  PairsParams P{};
+  P.n = d->ws.n;
+  P.rank = d->ws.rank.as<uint32_t>();
+  P.slen = d->ws.slen.as<uint8_t>();
+  P.aoff = d->ws.aoff.as<uint32_t>();
+  P.brec_w = d->ws.brec_w.as<uint32_t>();
+  P.a_enc = d->ws.a_enc.as<uint32_t>();
+  P.b_rec = d->ws.b_rec.as<uint32_t>();
+  P.C1 = d->ss.C1;
+  P.C2 = d->ss.C2;
+  P.gap = d->sc.gap;
+  P.err = err;
+  return P;
+}
+
+// candidate rescoring + selection on the model's or context's buffers
+nw_status rescore_select(nw_ctx* c, nw_dict* d, const uint32_t* cand, uint32_t C, uint32_t k, DevBuf& score_buf,
+                         uint32_t* out_idx, int16_t* out_score, uint32_t* err, cudaStream_t s) {
+  const uint32_t n = d->ws.n;
+  NW_TRY(ctx_ensure(c, score_buf, sizeof(int32_t) * std::max<size_t>(1, (size_t)n * C), "candidate scores"));
+  NW_CK(prop::rescore(pairs_params(d, err), cand, C, score_buf.as<int32_t>(), s));
+  NW_CK(prop::select_topk(cand, score_buf.as<int32_t>(), n, C, k, out_idx, out_score, s));
+  return NW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nw_status nw_model_create(nw_ctx* c, uint32_t alphabet, uint64_t seed, nw_model** out) {
+  if (!out) return NW_EINVAL;
+  *out = nullptr;
+  NW_ENTER(c);
+  if (alphabet == 0 || alphabet > 256) return set_err(c, NW_EINVAL, "alphabet must be in [1, 256]");
+  nw_model* M = new nw_model();
+  M->ctx = c;
+  M->alphabet = alphabet;
+  M->L = cnn::layout(alphabet);
+  auto fail = [&](nw_status st) {
+    const std::string msg = c->err;
+    model_free_buffers(M);
+    if (M->stream) cudaStreamDestroy(M->stream);
+    delete M;
+    c->err = msg;
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(cuda_fail(c, cudaGetLastError(), "cudaStreamCreateWithFlags"));
+  const size_t pb = sizeof(float) * M->L.total;
+  nw_status st = ctx_alloc(c, M->params, pb, "model parameters");
+  if (st == NW_OK) st = ctx_alloc(c, M->grads, pb, "model gradients");
+  if (st == NW_OK) st = ctx_alloc(c, M->adam_m, pb, "Adam moments");
+  if (st == NW_OK) st = ctx_alloc(c, M->adam_v, pb, "Adam moments");
+  if (st == NW_OK) st = ctx_alloc(c, M->small, 64, "model counters");
+  if (st != NW_OK) return fail(st);
+  // initial parameters from one SplitMix64 stream, block by block
+  std::vector<float> h(M->L.total, 0.f);
+  uint64_t state = seed;
+  auto uniform = [&](float a) {
+    const double u = (double)(splitmix64_next(state) >> 11) * (1.0 / 9007199254740992.0);  // [0, 1)
+    return (float)((2.0 * u - 1.0) * a);
+  };
+  const cnn::Layout& L = M->L;
+  for (uint64_t x = L.emb; x < L.W1; ++x) h[x] = uniform((float)std::sqrt(3.0));
+  for (uint64_t x = L.W1; x < L.b1; ++x) h[x] = uniform((float)std::sqrt(6.0 / (3 * cnn::kEmb)));
+  for (uint64_t x = L.W2; x < L.b2; ++x) h[x] = uniform((float)std::sqrt(6.0 / (3 * cnn::kCh)));
+  for (uint64_t x = L.W3; x < L.b3; ++x) h[x] = uniform((float)std::sqrt(6.0 / (3 * cnn::kCh)));
+  for (uint64_t x = L.Wl; x < L.bl; ++x) h[x] = uniform((float)std::sqrt(6.0 / cnn::kCh));
+  cudaError_t e = cudaMemcpy(M->params.p, h.data(), pb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(M->adam_m.p, 0, pb);
+  if (e == cudaSuccess) e = cudaMemset(M->adam_v.p, 0, pb);
+  if (e == cudaSuccess) e = cudaMemset(M->small.p, 0, 64);
+  if (e != cudaSuccess) return fail(cuda_fail(c, e, "model initialisation"));
+  c->models.insert(M);
+  *out = M;
+  return NW_OK;
+}
+
+void nw_model_free(nw_model* M) {
+  if (!M) return;
+  nw_ctx* c = M->ctx;
+  cudaSetDevice(c->device);
+  if (M->stream) {
+    cudaStreamSynchronize(M->stream);
+    cudaStreamDestroy(M->stream);
+  }
+  model_free_buffers(M);
+  c->models.erase(M);
+  delete M;
+}
+
+uint64_t nw_model_param_count(const nw_model* M) { return M ? M->L.total : 0; }
+
+nw_status nw_model_get_params(nw_model* M, float* params, uint32_t flags) {
+  if (!M) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  if (!params) return set_err(c, NW_EINVAL, "null parameter buffer");
+  NW_TRY(copy_out(c, params, fptr(M->params), M->L.total, flags & NW_DEVICE_PTRS, M->stream));
+  NW_CK(cudaStreamSynchronize(M->stream));
+  return NW_OK;
+}
+
+nw_status nw_model_set_params(nw_model* M, const float* params, uint32_t flags) {
+  if (!M) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  if (!params) return set_err(c, NW_EINVAL, "null parameter buffer");
+  NW_TRY(copy_in(c, fptr(M->params), params, M->L.total, flags & NW_DEVICE_PTRS, M->stream));
+  NW_CK(cudaMemsetAsync(M->adam_m.p, 0, M->adam_m.bytes, M->stream));
+  NW_CK(cudaMemsetAsync(M->adam_v.p, 0, M->adam_v.bytes, M->stream));
+  NW_CK(cudaMemsetAsync(step_ptr(M), 0, sizeof(uint32_t), M->stream));
+  M->steps_done = 0;
+  NW_CK(cudaStreamSynchronize(M->stream));
+  return NW_OK;
+}
+
+nw_status nw_model_embed(nw_model* M, nw_dict* d, float* out, uint32_t flags) {
+  if (!M || !d) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  if (!out) return set_err(c, NW_EINVAL, "null output buffer");
+  NW_TRY(check_model_dict(M, d));
+  NW_TRY(embed_all(M, d, M->stream));
+  NW_TRY(copy_out(c, out, fptr(M->Eall), (size_t)d->ws.n * cnn::kOut, flags & NW_DEVICE_PTRS, M->stream));
+  return check_err(M, M->stream);
+}
+
+nw_status nw_model_loss_grad(nw_model* M, nw_dict* d, const uint32_t* pi, const uint32_t* pj, const float* target,
+                             uint32_t m, float* loss, float* grad, uint32_t flags) {
+  if (!M || !d) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  if (!pi || !pj || !target || m == 0) return set_err(c, NW_EINVAL, "need m >= 1 pairs and their targets");
+  if (m > (1u << 20)) return set_err(c, NW_EINVAL, "at most 2^20 pairs per call");
+  NW_TRY(check_model_dict(M, d));
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = M->stream;
+  const int Lp = padded_len(d);
+  NW_TRY(ensure_pairs(M, m));
+  NW_TRY(ensure_scratch(M, (int)(2 * m), Lp));
+  NW_TRY(copy_in(c, M->pi.as<uint32_t>(), pi, m, dev, s));
+  NW_TRY(copy_in(c, M->pj.as<uint32_t>(), pj, m, dev, s));
+  NW_TRY(copy_in(c, fptr(M->target), target, m, dev, s));
+  NW_CK(cnn::interleave_pairs(M->pi.as<uint32_t>(), M->pj.as<uint32_t>(), (int)m, M->widx.as<uint32_t>(), s));
+  NW_CK(cudaMemsetAsync(loss_ptr(M), 0, sizeof(float), s));
+  NW_TRY(forward(M, d, (int)(2 * m), Lp, s));
+  NW_TRY(backward(M, (int)m, Lp, s));
+  if (grad) NW_TRY(copy_out(c, grad, fptr(M->grads), M->L.total, dev, s));
+  float h_loss = 0.f;
+  NW_CK(cudaMemcpyAsync(&h_loss, loss_ptr(M), sizeof(float), cudaMemcpyDeviceToHost, s));
+  NW_TRY(check_err(M, s));
+  if (loss) *loss = h_loss;
+  return NW_OK;
+}
+
+nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, const uint32_t* nbr, uint32_t knb,
+                         float* losses, uint32_t flags) {
+  if (!M || !d || !cfg) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  const uint32_t n = d->ws.n;
+  if (n < 2) return set_err(c, NW_EINVAL, "training needs at least 2 words");
+  if (cfg->batch_pairs == 0 || cfg->batch_pairs > 65536) return set_err(c, NW_EINVAL, "batch_pairs must be in [1, 65536]");
+  if (!(cfg->nbr_fraction >= 0.f && cfg->nbr_fraction <= 1.f)) return set_err(c, NW_EINVAL, "nbr_fraction in [0, 1]");
+  if (nbr && knb == 0) return set_err(c, NW_EINVAL, "neighbour lists need knb >= 1");
+  if (cfg->steps == 0) return NW_OK;
+  NW_TRY(check_model_dict(M, d));
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = M->stream;
+  const uint32_t m = cfg->batch_pairs;
+  const int Lp = padded_len(d);
+  NW_TRY(ensure_pairs(M, m));
+  NW_TRY(ensure_scratch(M, (int)(2 * m), Lp));
+  DevBuf loss_buf;
+  NW_TRY(ctx_alloc(c, loss_buf, sizeof(float) * cfg->steps, "training losses"));
+  struct Free {
+    nw_ctx* c;
+    DevBuf& b;
+    ~Free() { ctx_free(c, b); }
+  } free_losses{c, loss_buf};
+  const uint32_t* d_nbr = nullptr;
+  if (nbr) {
+    NW_TRY(ctx_ensure(c, M->nbr, sizeof(uint32_t) * (size_t)n * knb, "neighbour lists"));
+    NW_TRY(copy_in(c, M->nbr.as<uint32_t>(), nbr, (size_t)n * knb, dev, s));
+    d_nbr = M->nbr.as<uint32_t>();
+  }
+  NW_CK(cudaMemsetAsync(loss_ptr(M), 0, sizeof(float), s));
+  NW_CK(cudaStreamSynchronize(s));
+
+  cnn::PairDraw pd;
+  pd.seed = cfg->seed;
+  pd.step = step_ptr(M);
+  pd.n = n;
+  pd.m = m;
+  pd.nbr = d_nbr;
+  pd.knb = knb;
+  pd.n_nbr = d_nbr ? (uint32_t)std::lround((double)cfg->nbr_fraction * m) : 0u;
+  PairsParams pp = pairs_params(d, err_ptr(M));
+  pp.pi = M->pi.as<uint32_t>();
+  pp.pj = M->pj.as<uint32_t>();
+  pp.m = m;
+  pp.out = M->score16.as<int16_t>();
+
+  // one step, captured once and replayed
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  NW_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  nw_status st = NW_OK;
+  auto step_body = [&]() -> nw_status {
+    NW_CK(cnn::draw_pairs(pd, M->pi.as<uint32_t>(), M->pj.as<uint32_t>(), M->widx.as<uint32_t>(), s));
+    NW_CK(launch_pairs(pp, s));
+    NW_CK(cnn::pair_targets(M->score16.as<int16_t>(), M->pi.as<uint32_t>(), M->pj.as<uint32_t>(),
+                            d->ws.rank.as<uint32_t>(), d->ws.slen.as<uint8_t>(), (int)m, fptr(M->target), s));
+    NW_TRY(forward(M, d, (int)(2 * m), Lp, s));
+    NW_TRY(backward(M, (int)m, Lp, s));
+    NW_CK(cnn::bump_step(step_ptr(M), s));
+    NW_CK(cnn::adam(fptr(M->params), fptr(M->grads), fptr(M->adam_m), fptr(M->adam_v), M->L.total, step_ptr(M),
+                    cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, s));
+    NW_CK(cnn::record_loss(loss_ptr(M), loss_buf.as<float>(), step_ptr(M), M->steps_done, cfg->steps, s));
+    return NW_OK;
+  };
+  st = step_body();
+  const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (st != NW_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ec != cudaSuccess) return cuda_fail(c, ec, "cudaStreamEndCapture");
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  for (uint32_t x = 0; x < cfg->steps && e == cudaSuccess; ++x) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return cuda_fail(c, e, "training graph");
+  M->steps_done += cfg->steps;
+  if (losses) NW_TRY(copy_out(c, losses, loss_buf.as<float>(), cfg->steps, dev, s));
+  return check_err(M, s);
+}
+
+nw_status nw_quantize_embeddings(nw_ctx* c, const float* E, uint32_t n, int8_t* q, float* scale, uint32_t flags) {
+  NW_ENTER(c);
+  if (!E || !q || !scale) return set_err(c, NW_EINVAL, "null pointer argument");
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = c->stream;
+  const size_t cnt = (size_t)n * NW_EMBED_DIM;
+  DevBuf dE, dq, dsmall;
+  struct Free {
+    nw_ctx* c;
+    DevBuf* b[3];
+    ~Free() {
+      for (DevBuf* x : b) ctx_free(c, *x);
+    }
+  } fr{c, {&dE, &dq, &dsmall}};
+  const float* srcE = E;
+  int8_t* dstq = q;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, dE, sizeof(float) * std::max<size_t>(1, cnt), "embeddings"));
+    NW_TRY(ctx_alloc(c, dq, std::max<size_t>(1, cnt), "quantised embeddings"));
+    NW_TRY(copy_in(c, dE.as<float>(), E, cnt, false, s));
+    srcE = dE.as<float>();
+    dstq = dq.as<int8_t>();
+  }
+  NW_TRY(ctx_alloc(c, dsmall, 16, "quantisation scratch"));
+  float* dscale = reinterpret_cast<float*>(dsmall.as<char>() + 4);
+  NW_CK(prop::quantize(srcE, n, dsmall.as<unsigned int>(), dstq, nullptr, dscale, s));
+  if (!dev) NW_TRY(copy_out(c, q, dstq, cnt, false, s));
+  NW_TRY(copy_out(c, scale, dscale, 1, dev, s));
+  NW_CK(cudaStreamSynchronize(s));
+  return NW_OK;
+}
+
+nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, uint32_t n, uint32_t C, uint32_t* idx, int32_t* dot,
+                      uint32_t flags) {
+  NW_ENTER(c);
+  if (!q || !idx || !dot) return set_err(c, NW_EINVAL, "null pointer argument");
+  if (C == 0 || C > NW_MAX_CANDIDATES) return set_err(c, NW_EINVAL, "C must be in [1, %d]", NW_MAX_CANDIDATES);
+  if (n == 0) return NW_OK;
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = c->stream;
+  const size_t cnt = (size_t)n * NW_EMBED_DIM, outc = (size_t)n * C;
+  DevBuf dq, qb, buf, oi, od;
+  struct Free {
+    nw_ctx* c;
+    DevBuf* b[5];
+    ~Free() {
+      for (DevBuf* x : b) ctx_free(c, *x);
+    }
+  } fr{c, {&dq, &qb, &buf, &oi, &od}};
+  const int8_t* srcq = q;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, dq, cnt, "quantised embeddings"));
+    NW_TRY(copy_in(c, dq.as<int8_t>(), q, cnt, false, s));
+    srcq = dq.as<int8_t>();
+  }
+  NW_TRY(ctx_alloc(c, qb, cnt * sizeof(__nv_bfloat16), "bf16 embeddings"));
+  NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
+  uint32_t* out_i = idx;
+  int32_t* out_d = dot;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, oi, sizeof(uint32_t) * outc, "candidate lists"));
+    NW_TRY(ctx_alloc(c, od, sizeof(int32_t) * outc, "candidate lists"));
+    out_i = oi.as<uint32_t>();
+    out_d = od.as<int32_t>();
+  }
+  NW_CK(prop::widen(srcq, n, qb.as<__nv_bfloat16>(), s));
+  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), n, C, buf.as<uint64_t>(), out_i, out_d, s));
+  if (!dev) {
+    NW_TRY(copy_out(c, idx, out_i, outc, false, s));
+    NW_TRY(copy_out(c, dot, out_d, outc, false, s));
+  }
+  NW_CK(cudaStreamSynchronize(s));
+  return NW_OK;
+}
+
+nw_status nw_rescore_topk(nw_dict* d, const uint32_t* cand, uint32_t C, uint32_t k, uint32_t* nbr_idx,
+                          int16_t* nbr_score, uint32_t flags) {
+  if (!d) return NW_EINVAL;
+  nw_ctx* c = d->ctx;
+  NW_ENTER(c);
+  if (!cand || !nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null pointer argument");
+  if (C == 0 || C > NW_MAX_CANDIDATES) return set_err(c, NW_EINVAL, "C must be in [1, %d]", NW_MAX_CANDIDATES);
+  if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  if (d->score_lo < INT16_MIN + 1 || d->score_hi > INT16_MAX)
+    return set_err(c, NW_ERANGE, "scores [%d, %d] do not fit int16", d->score_lo, d->score_hi);
+  const uint32_t n = d->ws.n;
+  if (n == 0) return NW_OK;
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = c->stream;
+  DevBuf dc, sc, oi, os, small;
+  struct Free {
+    nw_ctx* c;
+    DevBuf* b[5];
+    ~Free() {
+      for (DevBuf* x : b) ctx_free(c, *x);
+    }
+  } fr{c, {&dc, &sc, &oi, &os, &small}};
+  const uint32_t* srcc = cand;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, dc, sizeof(uint32_t) * (size_t)n * C, "candidates"));
+    NW_TRY(copy_in(c, dc.as<uint32_t>(), cand, (size_t)n * C, false, s));
+    srcc = dc.as<uint32_t>();
+  }
+  uint32_t* out_i = nbr_idx;
+  int16_t* out_s = nbr_score;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, oi, sizeof(uint32_t) * (size_t)n * k, "neighbour lists"));
+    NW_TRY(ctx_alloc(c, os, sizeof(int16_t) * (size_t)n * k, "neighbour lists"));
+    out_i = oi.as<uint32_t>();
+    out_s = os.as<int16_t>();
+  }
+  NW_TRY(ctx_alloc(c, small, 16, "error flags"));
+  NW_CK(cudaMemsetAsync(small.p, 0, 16, s));
+  NW_TRY(rescore_select(c, d, srcc, C, k, sc, out_i, out_s, small.as<uint32_t>(), s));
+  if (!dev) {
+    NW_TRY(copy_out(c, nbr_idx, out_i, (size_t)n * k, false, s));
+    NW_TRY(copy_out(c, nbr_score, out_s, (size_t)n * k, false, s));
+  }
+  NW_TRY(check_device_flags(c, small.as<uint32_t>()));
+  return NW_OK;
+}
+
+nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint32_t* nbr_idx, int16_t* nbr_score,
+                           nw_proposal_profile* prof, uint32_t flags) {
+  if (!M || !d) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  if (!nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null output buffer");
+  if (C == 0 || C > NW_MAX_CANDIDATES) return set_err(c, NW_EINVAL, "C must be in [1, %d]", NW_MAX_CANDIDATES);
+  if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  if (d->score_lo < INT16_MIN + 1 || d->score_hi > INT16_MAX)
+    return set_err(c, NW_ERANGE, "scores [%d, %d] do not fit int16", d->score_lo, d->score_hi);
+  NW_TRY(check_model_dict(M, d));
+  const uint32_t n = d->ws.n;
+  if (n == 0) return NW_OK;
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = M->stream;
+  const size_t outc = (size_t)n * C;
+  NW_TRY(ctx_ensure(c, M->Qb, sizeof(__nv_bfloat16) * (size_t)n * NW_EMBED_DIM, "bf16 embeddings"));
+  NW_TRY(ctx_ensure(c, M->topbuf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
+  NW_TRY(ctx_ensure(c, M->cand, sizeof(uint32_t) * outc, "candidate lists"));
+  NW_TRY(ctx_ensure(c, M->cand_dot, sizeof(int32_t) * outc, "candidate lists"));
+  DevBuf oi, os;
+  struct Free {
+    nw_ctx* c;
+    DevBuf* b[2];
+    ~Free() {
+      for (DevBuf* x : b) ctx_free(c, *x);
+    }
+  } fr{c, {&oi, &os}};
+  uint32_t* out_i = nbr_idx;
+  int16_t* out_s = nbr_score;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, oi, sizeof(uint32_t) * (size_t)n * k, "neighbour lists"));
+    NW_TRY(ctx_alloc(c, os, sizeof(int16_t) * (size_t)n * k, "neighbour lists"));
+    out_i = oi.as<uint32_t>();
+    out_s = os.as<int16_t>();
+  }
+  // scratch sized before the timed stages
+  const int Lp = padded_len(d);
+  NW_TRY(ensure_scratch(M, (int)std::min<uint32_t>(n, (uint32_t)std::max(1, kMaxRowsPerPass / Lp)), Lp));
+  NW_TRY(ctx_ensure(c, M->Eall, sizeof(float) * (size_t)n * cnn::kOut, "embeddings"));
+  NW_TRY(ctx_ensure(c, M->cand_score, sizeof(int32_t) * outc, "candidate scores"));
+  cudaEvent_t ev[5];
+  for (auto& e : ev) NW_CK(cudaEventCreate(&e));
+  struct FreeEv {
+    cudaEvent_t* e;
+    ~FreeEv() {
+      for (int x = 0; x < 5; ++x) cudaEventDestroy(e[x]);
+    }
+  } fe{ev};
+  NW_CK(cudaEventRecord(ev[0], s));
+  NW_TRY(embed_all(M, d, s));
+  NW_CK(cudaEventRecord(ev[1], s));
+  NW_CK(prop::quantize(fptr(M->Eall), n, amax_ptr(M), nullptr, M->Qb.as<__nv_bfloat16>(), nullptr, s));
+  NW_CK(cudaEventRecord(ev[2], s));
+  NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), n, C, M->topbuf.as<uint64_t>(), M->cand.as<uint32_t>(),
+                       M->cand_dot.as<int32_t>(), s));
+  NW_CK(cudaEventRecord(ev[3], s));
+  NW_TRY(rescore_select(c, d, M->cand.as<uint32_t>(), C, k, M->cand_score, out_i, out_s, err_ptr(M), s));
+  NW_CK(cudaEventRecord(ev[4], s));
+  if (!dev) {
+    NW_TRY(copy_out(c, nbr_idx, out_i, (size_t)n * k, false, s));
+    NW_TRY(copy_out(c, nbr_score, out_s, (size_t)n * k, false, s));
+  }
+  NW_TRY(check_err(M, s));
+  if (prof) {
+    float ms[4];
+    for (int x = 0; x < 4; ++x) NW_CK(cudaEventElapsedTime(&ms[x], ev[x], ev[x + 1]));
+    prof->embed_ms = ms[0];
+    prof->quantize_ms = ms[1];
+    prof->candidates_ms = ms[2];
+    prof->rescore_ms = ms[3];
+    prof->total_ms = (double)ms[0] + ms[1] + ms[2] + ms[3];
+  }
+  return NW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+// nw_proposal_internal.h -- kernels of the candidate proposal path
+// (quantisation, dot-product top-C, exact rescoring; see nw_proposal.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nw_launch.h"
+
+namespace nw {
+namespace prop {
+
+constexpr int kCap = 1024;  // append-buffer keys per row of the dot-product top-C
+
+// q (int8, may be null) and qb (bf16, may be null) of n x 64 embeddings; scale
+// (device float, may be null); amax_bits is device scratch
+cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,
+                     float* scale, cudaStream_t s);
+cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s);
+size_t dot_topk_buffer_bytes(uint32_t n);
+cudaError_t dot_topk(const __nv_bfloat16* Qb, uint32_t n, uint32_t C, uint64_t* buf, uint32_t* idx, int32_t* dot,
+                     cudaStream_t s);
+
+// Algorithm 1's score of (i, cand[i * C + r]) into score[i * C + r] (int32;
+// INT32_MIN for UINT32_MAX entries); out-of-range or self candidates raise
+// kErrInput.  P supplies the encoded dictionary (its pi/pj/m/out are unused).
+cudaError_t rescore(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s);
+// each row's k best (score desc, index asc) of its C scored candidates
+cudaError_t select_topk(const uint32_t* cand, const int32_t* score, uint32_t n, uint32_t C, uint32_t k,
+                        uint32_t* out_idx, int16_t* out_score, cudaStream_t s);
+
+}  // namespace prop
+}  // namespace nw

@@ -35,9 +35,26 @@ EXPORTED = [
     "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
     "nw_batch_create", "nw_batch_run", "nw_batch_info_get", "nw_batch_free", "nw_all_pairs_matrix_chunked",
     "nw_debug_norm_tables",
+    # nw_proposal.h
+    "nw_model_create", "nw_model_free", "nw_model_param_count", "nw_model_get_params", "nw_model_set_params",
+    "nw_model_embed", "nw_model_loss_grad", "nw_model_train", "nw_quantize_embeddings", "nw_dot_topk",
+    "nw_rescore_topk", "nw_proposal_topk",
 ]
+EMBED_DIM = 64
+MAX_CANDIDATES = 512
 NW_BATCH_AUTOTUNE = 0x10
 NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+class TrainConfig(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("batch_pairs", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("nbr_fraction", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class ProposalProfile(ctypes.Structure):
+    _fields_ = [("embed_ms", ctypes.c_double), ("quantize_ms", ctypes.c_double), ("candidates_ms", ctypes.c_double),
+                ("rescore_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
 
 
 class NwError(RuntimeError):
@@ -126,6 +143,20 @@ def load_library(path: str = LIB_PATH):
     L.nw_debug_enumerate_pairs.argtypes = [vp, u32, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
     L.nw_debug_fail_alloc.argtypes = [vp, u32]
     L.nw_debug_norm_tables.argtypes = [ctypes.POINTER(Scoring), i32, i32, vp, vp, vp, u32, ctypes.POINTER(u32)]
+    L.nw_model_create.argtypes = [vp, u32, u64, ctypes.POINTER(vp)]
+    L.nw_model_free.argtypes = [vp]
+    L.nw_model_free.restype = None
+    L.nw_model_param_count.argtypes = [vp]
+    L.nw_model_param_count.restype = u64
+    L.nw_model_get_params.argtypes = [vp, vp, u32]
+    L.nw_model_set_params.argtypes = [vp, vp, u32]
+    L.nw_model_embed.argtypes = [vp, vp, vp, u32]
+    L.nw_model_loss_grad.argtypes = [vp, vp, vp, vp, vp, u32, ctypes.POINTER(ctypes.c_float), vp, u32]
+    L.nw_model_train.argtypes = [vp, vp, ctypes.POINTER(TrainConfig), vp, u32, vp, u32]
+    L.nw_quantize_embeddings.argtypes = [vp, vp, u32, vp, ctypes.POINTER(ctypes.c_float), u32]
+    L.nw_dot_topk.argtypes = [vp, vp, u32, u32, vp, vp, u32]
+    L.nw_rescore_topk.argtypes = [vp, vp, u32, u32, vp, vp, u32]
+    L.nw_proposal_topk.argtypes = [vp, vp, u32, u32, vp, vp, ctypes.POINTER(ProposalProfile), u32]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.nw_server_submit.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u64)]
@@ -557,3 +588,122 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# learned candidate proposal (nw_proposal.h)
+
+class Model:
+    """nw_model_*: the character CNN whose embeddings' dot products propose
+    neighbour candidates for exact rescoring."""
+
+    def __init__(self, ctx: Context, alphabet: int, seed: int = 0):
+        L = load_library()
+        h = ctypes.c_void_p()
+        _check(ctx.handle, L.nw_model_create(ctx.handle, alphabet, seed, ctypes.byref(h)))
+        self.ctx = ctx
+        self.handle = h
+        self.alphabet = alphabet
+
+    def free(self):
+        if getattr(self, "handle", None) and getattr(self.ctx, "handle", None):
+            load_library().nw_model_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def param_count(self) -> int:
+        return int(load_library().nw_model_param_count(self.handle))
+
+    def get_params(self, out=None):
+        if out is None:
+            out = np.empty(self.param_count, dtype=np.float32)
+        _check(self.ctx.handle, load_library().nw_model_get_params(self.handle, _ptr(out)[0], _flags(out)))
+        return out
+
+    def set_params(self, params):
+        if not _is_torch(params):
+            params = np.ascontiguousarray(params, dtype=np.float32)
+        assert int(params.shape[0]) == self.param_count
+        _check(self.ctx.handle, load_library().nw_model_set_params(self.handle, _ptr(params)[0], _flags(params)))
+
+    def embed(self, d: "Dictionary", out=None):
+        if out is None:
+            out = np.empty((d.n, EMBED_DIM), dtype=np.float32)
+        _check(self.ctx.handle, load_library().nw_model_embed(self.handle, d.handle, _ptr(out)[0], _flags(out)))
+        return out
+
+    def loss_grad(self, d: "Dictionary", pi, pj, target, grad=True):
+        pi = np.ascontiguousarray(pi, dtype=np.uint32)
+        pj = np.ascontiguousarray(pj, dtype=np.uint32)
+        target = np.ascontiguousarray(target, dtype=np.float32)
+        g = np.empty(self.param_count, dtype=np.float32) if grad else None
+        loss = ctypes.c_float(0)
+        _check(self.ctx.handle, load_library().nw_model_loss_grad(
+            self.handle, d.handle, _ptr(pi)[0], _ptr(pj)[0], _ptr(target)[0], int(pi.shape[0]),
+            ctypes.byref(loss), _ptr(g)[0], 0))
+        return float(loss.value), g
+
+    def train(self, d: "Dictionary", steps: int, batch_pairs: int = 8192, lr: float = 1e-3, seed: int = 1,
+              nbr=None, nbr_fraction: float = 0.5, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        """Adam on device-drawn pairs labelled by Algorithm 1; returns the per-step losses."""
+        cfg = TrainConfig(steps, batch_pairs, lr, beta1, beta2, eps, nbr_fraction if nbr is not None else 0.0, seed)
+        losses = np.zeros(max(steps, 1), dtype=np.float32)
+        knb = 0
+        if nbr is not None:
+            nbr = np.ascontiguousarray(nbr, dtype=np.uint32)
+            knb = int(nbr.shape[1])
+        _check(self.ctx.handle, load_library().nw_model_train(
+            self.handle, d.handle, ctypes.byref(cfg), _ptr(nbr)[0], knb, _ptr(losses)[0], 0))
+        return losses[:steps]
+
+    def proposal_topk(self, d: "Dictionary", C: int, k: int, nbr_idx=None, nbr_score=None):
+        """(idx[n, k], score[n, k], profile dict): embed, quantise, C candidates, exact rescoring."""
+        n = d.n
+        if nbr_idx is None:
+            nbr_idx = _empty_like_kind(None, (n, k), np.uint32, None)
+        if nbr_score is None:
+            nbr_score = _empty_like_kind(nbr_idx, (n, k), np.int16, _torch_dtype("int16"))
+        prof = ProposalProfile()
+        _check(self.ctx.handle, load_library().nw_proposal_topk(
+            self.handle, d.handle, C, k, _ptr(nbr_idx)[0], _ptr(nbr_score)[0], ctypes.byref(prof),
+            _flags(nbr_idx, nbr_score)))
+        return nbr_idx, nbr_score, {f: getattr(prof, f) for f, _ in ProposalProfile._fields_}
+
+
+def quantize_embeddings(ctx: Context, E):
+    """(q int8 [n, 64], scale) by nw_quantize_embeddings (host arrays)."""
+    E = np.ascontiguousarray(E, dtype=np.float32)
+    n = int(E.shape[0])
+    q = np.empty((n, EMBED_DIM), dtype=np.int8)
+    sc = ctypes.c_float(0)
+    _check(ctx.handle, load_library().nw_quantize_embeddings(ctx.handle, _ptr(E)[0], n, _ptr(q)[0],
+                                                             ctypes.byref(sc), 0))
+    return q, np.float32(sc.value)
+
+
+def dot_topk(ctx: Context, q, C: int):
+    """(idx uint32 [n, C], dot int32 [n, C]) by nw_dot_topk (host or CUDA buffers)."""
+    if not _is_torch(q):
+        q = np.ascontiguousarray(q, dtype=np.int8)
+    n = int(q.shape[0])
+    idx = _empty_like_kind(q, (n, C), np.uint32, _torch_dtype("int32"))
+    dot = _empty_like_kind(q, (n, C), np.int32, _torch_dtype("int32"))
+    _check(ctx.handle, load_library().nw_dot_topk(ctx.handle, _ptr(q)[0], n, C, _ptr(idx)[0], _ptr(dot)[0],
+                                                  _flags(q, idx, dot)))
+    return idx, dot
+
+
+def rescore_topk(d: "Dictionary", cand, k: int):
+    """(idx uint32 [n, k], score int16 [n, k]) by nw_rescore_topk (host arrays)."""
+    cand = np.ascontiguousarray(cand, dtype=np.uint32)
+    n, C = cand.shape
+    idx = np.empty((n, k), dtype=np.uint32)
+    sc = np.empty((n, k), dtype=np.int16)
+    _check(d.ctx.handle, load_library().nw_rescore_topk(d.handle, _ptr(cand)[0], C, k, _ptr(idx)[0], _ptr(sc)[0], 0))
+    return idx, sc

@@ -1,0 +1,251 @@
+"""GPU parity of the learned candidate proposal (include/nw_proposal.h)
+against the CPU oracle (oracle/proposal.py):
+
+* forward embeddings and the loss gradient: float32 kernels against the
+  float64 definition, relative tolerance 1e-4 (a sum of at most 384 float32
+  products per output and float32 atomics in the weight gradients);
+* quantisation: bit-exact (both sides divide and round in float32);
+* the dot-product top-C: bit-exact (integer dot products, exact in the
+  tensor cores' float32 accumulation), with ties, ragged tails, fewer rows
+  than C, and rows far beyond the append buffer so that compaction runs;
+* rescoring of given candidate lists: bit-exact against Algorithm 1;
+* training: Adam's first step has size lr per coordinate, and the loss falls;
+* the whole path: lists sorted, scores equal to Algorithm 1's, and every
+  listed neighbour among the exact top list or tied with it in score when
+  the candidates cover everything.
+"""
+import numpy as np
+import pytest
+
+from oracle import proposal as PR
+from paper_2509_01654_gb300 import nw, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2509_01654_gb300 import build
+    build.build()
+    c = nw.Context(0)
+    yield c
+    c.close()
+
+
+def small_dict(ctx, n=300, alphabet=9, seed=5, lo=0, hi=12):
+    w = synth.make_uniform_length_words(n, alphabet, 1.0, lo, hi, seed=seed)
+    return w, ctx.load_dictionary(w.codes, w.offsets, alphabet, (1, -1, -1))
+
+
+def rand_params(alphabet, seed, scale=0.2):
+    return np.random.default_rng(seed).normal(0.0, scale, PR.param_count(alphabet)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# network
+
+def test_param_count(ctx):
+    m = nw.Model(ctx, 40, seed=1)
+    assert m.param_count == PR.param_count(40)
+    p = m.get_params()
+    assert np.isfinite(p).all() and np.abs(p).max() <= np.sqrt(3.0) + 1e-6
+    P = PR.unflatten(p.astype(np.float64), 40)
+    assert np.all(P["b1"] == 0) and np.all(P["bl"] == 0)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_forward_matches_oracle(ctx, seed):
+    w, d = small_dict(ctx, n=700, seed=seed)  # lengths 0..12 incl. empty words; > one 128-row tile of words
+    m = nw.Model(ctx, 9, seed=seed)
+    flat = rand_params(9, seed)
+    m.set_params(flat)
+    assert np.array_equal(m.get_params(), flat)
+    got = m.embed(d)
+    want = PR.forward(flat.astype(np.float64), w, 9)
+    err = np.abs(got - want).max() / max(1e-6, np.abs(want).max())
+    assert err < 1e-4, err
+
+
+def test_gradient_matches_oracle(ctx):
+    w, d = small_dict(ctx, n=200, seed=7)
+    m = nw.Model(ctx, 9, seed=3)
+    flat = rand_params(9, 11, scale=0.15)
+    m.set_params(flat)
+    g = np.random.default_rng(8)
+    M = 300
+    pi = g.integers(0, w.n, M)
+    pj = g.integers(0, w.n, M)
+    pj[:5] = pi[:5]  # self pairs
+    y = g.uniform(-1, 1, M)
+    loss, grad = m.loss_grad(d, pi, pj, y.astype(np.float32))
+    want_loss, want_grad = PR.loss_and_grad(flat.astype(np.float64), w, 9, pi, pj, y.astype(np.float32))
+    assert abs(loss - want_loss) <= 1e-4 * abs(want_loss)
+    o = 0
+    for name, shape in PR.param_shapes(9):
+        n = int(np.prod(shape))
+        a, b = grad[o:o + n].astype(np.float64), want_grad[o:o + n]
+        rel = np.linalg.norm(a - b) / max(1e-12, np.linalg.norm(b))
+        assert rel < 1e-4, (name, rel)
+        o += n
+
+
+def test_invalid_pair_index_is_reported(ctx):
+    w, d = small_dict(ctx, n=50)
+    m = nw.Model(ctx, 9)
+    with pytest.raises(nw.NwError) as e:
+        m.loss_grad(d, [0, 50], [1, 2], [0.0, 0.0])
+    assert e.value.status == nw.NW_EINVAL
+    # the model stays usable
+    m.loss_grad(d, [0, 1], [1, 2], [0.0, 0.0])
+
+
+def test_dictionary_alphabet_above_model_refused(ctx):
+    w, d = small_dict(ctx, n=50, alphabet=9)
+    m = nw.Model(ctx, 5)
+    with pytest.raises(nw.NwError) as e:
+        m.embed(d)
+    assert e.value.status == nw.NW_EINVAL
+
+
+def test_first_adam_step_and_training_lowers_loss(ctx):
+    w, d = small_dict(ctx, n=2000, alphabet=12, seed=9, lo=1, hi=14)
+    m = nw.Model(ctx, 12, seed=4)
+    p0 = m.get_params()
+    lr = 1e-3
+    m.train(d, steps=1, batch_pairs=512, lr=lr, seed=3)
+    p1 = m.get_params()
+    delta = np.abs(p1.astype(np.float64) - p0)
+    # first Adam step: |delta| = lr * |g| / (|g| + eps) <= lr, and = lr (to float32) where |g| >> eps
+    assert delta.max() <= lr * (1 + 1e-3)
+    assert np.mean(delta > 0.9 * lr) > 0.5
+    # a fixed evaluation batch scored by the oracle's definition of the target
+    g = np.random.default_rng(2)
+    pi = g.integers(0, w.n, 2000)
+    pj = (pi + 1 + g.integers(0, w.n - 1, 2000)) % w.n
+    import oracle
+    s = oracle.score_pairs(w, pi, pj, (1, -1, -1))
+    y = (s / np.maximum(np.maximum(w.lengths[pi], w.lengths[pj]), 1)).astype(np.float32)
+    before, _ = m.loss_grad(d, pi, pj, y, grad=False)
+    losses = m.train(d, steps=300, batch_pairs=1024, lr=2e-3, seed=4)
+    after, _ = m.loss_grad(d, pi, pj, y, grad=False)
+    assert np.isfinite(losses).all()
+    assert after < 0.5 * before, (before, after)
+    assert losses[-20:].mean() < losses[:20].mean()
+
+
+# ---------------------------------------------------------------------------
+# quantisation and candidates
+
+def test_quantize_matches_oracle(ctx):
+    g = np.random.default_rng(1)
+    E = (g.normal(0, 1, (5000, 64)) * g.uniform(0.1, 3.0, (5000, 1))).astype(np.float32)
+    E[17, 3] = 0.5 * np.abs(E).max()  # exact halves after division happen rarely; this one is plain
+    q, s = nw.quantize_embeddings(ctx, E)
+    wq, ws = PR.quantize(E)
+    assert s == ws
+    assert np.array_equal(q, wq)
+    z, s0 = nw.quantize_embeddings(ctx, np.zeros((3, 64), np.float32))
+    assert s0 == 0 and not z.any()
+
+
+@pytest.mark.parametrize("n,C,levels", [(1000, 64, 127), (777, 32, 2), (20, 64, 5), (1, 4, 3), (300, 512, 127),
+                                        (4100, 256, 127)])
+def test_dot_topk_matches_oracle(ctx, n, C, levels):
+    g = np.random.default_rng(n + C)
+    q = g.integers(-levels, levels + 1, (n, 64)).astype(np.int8)
+    if n > 10:
+        q[n // 3] = q[1]  # duplicate rows
+    idx, dot = nw.dot_topk(ctx, q, C)
+    wi, wd = PR.dot_topk(q, C)
+    assert np.array_equal(dot, wd)
+    assert np.array_equal(idx, wi)
+
+
+def test_dot_topk_large_sampled_rows(ctx):
+    # 40,000 rows: each row's buffer is compacted many times during the sweep
+    n, C = 40_000, 256
+    g = np.random.default_rng(77)
+    q = g.integers(-20, 21, (n, 64)).astype(np.int8)
+    idx, dot = nw.dot_topk(ctx, q, C)
+    rows = synth.sample_rows(n, 64)
+    wi, wd = PR.dot_topk(q, C, rows=rows)
+    assert np.array_equal(dot[rows], wd)
+    assert np.array_equal(idx[rows], wi)
+    # every row: sorted, distinct, no self
+    assert np.all(np.diff(dot.astype(np.int64), axis=1) <= 0)
+    assert not np.any(idx == np.arange(n, dtype=np.uint32)[:, None])
+
+
+def test_dot_topk_rejects_bad_C(ctx):
+    q = np.zeros((10, 64), np.int8)
+    for C in (0, nw.MAX_CANDIDATES + 1):
+        with pytest.raises(nw.NwError) as e:
+            nw.dot_topk(ctx, q, C)
+        assert e.value.status == nw.NW_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# rescoring
+
+@pytest.mark.parametrize("k,C", [(10, 64), (1, 7), (33, 40)])
+def test_rescore_matches_oracle(ctx, oracle_mod, k, C):
+    w = synth.make_words(1500, 40, 1.1, 8.0, 3.0, 1, 25, seed=12)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    g = np.random.default_rng(k * 100 + C)
+    cand = np.empty((w.n, C), dtype=np.uint32)
+    for i in range(w.n):
+        pool = g.choice(w.n - 1, C, replace=False)
+        cand[i] = np.where(pool >= i, pool + 1, pool)  # distinct, never i
+    cand[::7, C // 2:] = PR.MISSING_IDX  # some rows with missing candidates
+    idx, sc = nw.rescore_topk(d, cand, k)
+    wi, ws = PR.rescore_topk(oracle_mod, w, cand, k, (1, -1, -1))
+    ws = np.where(ws == PR.MISSING_SCORE, nw.MISSING_SCORE, ws).astype(np.int16)
+    assert np.array_equal(sc, ws)
+    assert np.array_equal(idx, wi)
+
+
+def test_rescore_reports_self_candidate(ctx):
+    w = synth.make_words(100, 10, 1.0, 5.0, 2.0, 1, 9, seed=1)
+    d = ctx.load_dictionary(w.codes, w.offsets, 10, (1, -1, -1))
+    cand = np.tile(np.arange(5, dtype=np.uint32), (w.n, 1))
+    with pytest.raises(nw.NwError) as e:
+        nw.rescore_topk(d, cand, 3)
+    assert e.value.status == nw.NW_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# the whole path
+
+def test_proposal_path_properties(ctx, oracle_mod):
+    w = synth.make_words(6000, 40, 1.1, 8.0, 3.0, 1, 25, seed=21)
+    sc = (1, -1, -1)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, sc)
+    m = nw.Model(ctx, 40, seed=2)
+    ex_i, ex_s, _, _ = d.all_pairs_topk(10, hist=None)
+    m.train(d, steps=200, batch_pairs=2048, lr=2e-3, seed=5, nbr=ex_i, nbr_fraction=0.5)
+    idx, score, prof = m.proposal_topk(d, C=128, k=10)
+    assert prof["total_ms"] > 0
+    ok = idx != nw.MISSING_IDX
+    assert ok.all()  # 128 candidates always give 10 neighbours
+    assert np.all(np.diff(score.astype(np.int32), axis=1) <= 0)
+    rows = synth.sample_rows(w.n, 300)
+    I = np.repeat(rows, 10)
+    J = idx[rows].reshape(-1)
+    assert np.array_equal(oracle_mod.score_pairs(w, I, J, sc), score[rows].reshape(-1))
+    # the approximate lists never beat the exact ones
+    assert np.all(score[:, 0] <= ex_s[:, 0])
+    strict, tie = PR.recall_at_k(ex_i, ex_s, idx, score)
+    assert 0.0 < strict <= tie <= 1.0
+
+
+def test_proposal_with_all_candidates_is_exact(ctx):
+    # with C >= n - 1 every pair is a candidate: the lists equal the exhaustive ones
+    w = synth.make_words(400, 40, 1.1, 8.0, 3.0, 1, 25, seed=22)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    m = nw.Model(ctx, 40, seed=3)
+    ex_i, ex_s, _, _ = d.all_pairs_topk(10, hist=None)
+    idx, score, _ = m.proposal_topk(d, C=nw.MAX_CANDIDATES, k=10)
+    assert np.array_equal(score, ex_s)
+    assert np.array_equal(idx, ex_i)
