@@ -9,14 +9,22 @@ the CUDA path is checked against, written plainly:
 * ``forward``: codes -> embedding table (32) -> three 1-D convolutions of
   width 3 with 128 channels, zero padding, ReLU -> mean over the word's
   positions -> linear map to 64 values.  Plain PyTorch CPU ops in float64.
-* ``loss_and_grad``: squared error of the dot product of two words'
-  embeddings against the target s / max(len(A), len(B)) (Section 5's
-  normalised weight), averaged over the pairs; gradient by autograd.
+* ``predict``: the modelled similarity of two words.  The 64 outputs are
+  read as 63 features phi and one bias beta, and
+  pred(a, b) = phi_a . phi_b + beta_a + beta_b.  A raw alignment score
+  carries a -len(A) - len(B) term that no dot product of one embedding per
+  word can express (its Gram matrix is positive semi-definite); the two
+  biases carry it.
+* ``loss_and_grad``: squared error of pred against a target (the library
+  trains on Section 5's normalised weight s / max(len(A), len(B)) or on the
+  raw score times a constant), averaged over the pairs; gradient by autograd.
 * ``adam_update``: one Adam step (Kingma and Ba, 2015) with bias correction.
-* ``quantize``: symmetric 8-bit quantisation of the embeddings with one
-  scale, in float32 (the precision the library takes that decision in).
-* ``dot_topk``: each row's C best other rows by exact integer dot product of
-  the quantised embeddings, higher first, lower index on ties.
+* ``quantize``: symmetric 8-bit quantisation of the 63 features with one
+  scale, the bias in units of scale^2 (so that q_a . q_b + bias_b is the
+  quantised phi_a . phi_b + beta_b), in float32 (the precision the library
+  takes these decisions in).
+* ``dot_topk``: each row's C best other rows by the exact integer value
+  q_i . q_j + bias_j, higher first, lower index on ties.
 * ``rescore_topk``: the k best of each row's candidates by Algorithm 1's
   score (the oracle's C code), higher first, lower index on ties.
 * ``recall_at_k``: strict and tie-aware overlap of two sets of lists.
@@ -37,7 +45,9 @@ import numpy as np
 EMB = 32
 CH = 128
 OUT = 64
+FEAT = 63   # outputs 0..62 are features, output 63 is the bias
 TAPS = 3
+BIAS_LIMIT = 1 << 23
 
 MISSING_IDX = np.uint32(0xFFFFFFFF)
 MISSING_DOT = np.int32(-(2 ** 31))
@@ -101,9 +111,20 @@ def forward(flat, words, alphabet: int) -> np.ndarray:
         return _forward_t(P, words).numpy()
 
 
+def _predict_t(Ea, Eb):
+    return (Ea[:, :FEAT] * Eb[:, :FEAT]).sum(dim=1) + Ea[:, FEAT] + Eb[:, FEAT]
+
+
+def predict(Ea, Eb) -> np.ndarray:
+    """pred(a, b) = phi_a . phi_b + beta_a + beta_b for rows of two embedding arrays."""
+    Ea = np.asarray(Ea, dtype=np.float64)
+    Eb = np.asarray(Eb, dtype=np.float64)
+    return np.sum(Ea[:, :FEAT] * Eb[:, :FEAT], axis=1) + Ea[:, FEAT] + Eb[:, FEAT]
+
+
 def loss_and_grad(flat, words, alphabet: int, pi, pj, target):
     """(loss, gradient of the flat parameters): mean over pairs of
-    (E[pi] . E[pj] - target)^2."""
+    (pred(E[pi], E[pj]) - target)^2."""
     torch = _torch()
     flat_t = torch.tensor(np.asarray(flat, dtype=np.float64), requires_grad=True)
     P, o = {}, 0
@@ -115,7 +136,7 @@ def loss_and_grad(flat, words, alphabet: int, pi, pj, target):
     pi = torch.tensor(np.asarray(pi, dtype=np.int64))
     pj = torch.tensor(np.asarray(pj, dtype=np.int64))
     y = torch.tensor(np.asarray(target, dtype=np.float64))
-    pred = (E[pi] * E[pj]).sum(dim=1)
+    pred = _predict_t(E[pi], E[pj])
     loss = ((pred - y) ** 2).mean()
     loss.backward()
     return float(loss.item()), flat_t.grad.numpy().copy()
@@ -131,30 +152,41 @@ def adam_update(theta, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999,
 
 
 def quantize(E):
-    """(q int8 (n, 64), scale float32): scale = max|E| / 127, q = round-half-even(E / scale)
-    clamped to [-127, 127], all in float32; scale 0 gives q = 0."""
+    """(q int8 (n, 64), bias int32 (n,), scale float32), all in float32:
+    scale = max|phi| / 127 over the 63 features of all rows; q[:, :63] =
+    round-half-even(phi / scale) clamped to [-127, 127], q[:, 63] = 0;
+    bias = round-half-even(beta / (scale * scale)) clamped to +-2^23.  A zero
+    scale gives q = 0 and bias = 0."""
     E = np.asarray(E, dtype=np.float32)
-    amax = np.float32(np.max(np.abs(E))) if E.size else np.float32(0)
+    n = E.shape[0]
+    phi = E[:, :FEAT]
+    amax = np.float32(np.max(np.abs(phi))) if phi.size else np.float32(0)
     scale = np.float32(amax / np.float32(127.0))
+    q = np.zeros((n, OUT), dtype=np.int8)
+    bias = np.zeros(n, dtype=np.int32)
     if scale == 0:
-        return np.zeros(E.shape, dtype=np.int8), scale
-    q = np.rint(E / scale)
-    return np.clip(q, -127, 127).astype(np.int8), scale
+        return q, bias, scale
+    q[:, :FEAT] = np.clip(np.rint(phi / scale), -127, 127).astype(np.int8)
+    s2 = np.float32(scale * scale)
+    bias[:] = np.clip(np.rint(E[:, FEAT] / s2), -BIAS_LIMIT, BIAS_LIMIT).astype(np.int32)
+    return q, bias, scale
 
 
-def dot_topk(q, C: int, rows=None):
-    """(idx uint32 (r, C), dot int32 (r, C)): for each row i, the C rows j != i
-    with the largest exact dot(q_i, q_j), lower j first on ties; missing
-    entries (fewer than C other rows) are (MISSING_IDX, MISSING_DOT)."""
+def dot_topk(q, C: int, rows=None, bias=None):
+    """(idx uint32 (r, C), val int32 (r, C)): for each row i, the C rows j != i
+    with the largest exact q_i . q_j + bias_j (bias 0 when None), lower j
+    first on ties; missing entries (fewer than C other rows) are
+    (MISSING_IDX, MISSING_DOT)."""
     q = np.asarray(q, dtype=np.int64)
     n = q.shape[0]
+    b = np.zeros(n, dtype=np.int64) if bias is None else np.asarray(bias, dtype=np.int64)
     rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
     idx = np.full((rows.size, C), MISSING_IDX, dtype=np.uint32)
     dot = np.full((rows.size, C), MISSING_DOT, dtype=np.int32)
     jj = np.arange(n)
     for b0 in range(0, rows.size, 256):
         rb = rows[b0:b0 + 256]
-        D = q[rb] @ q.T  # exact in int64
+        D = q[rb] @ q.T + b[None, :]  # exact in int64
         for r, i in enumerate(rb):
             keep = jj != i
             order = np.lexsort((jj[keep], -D[r, keep]))[:C]

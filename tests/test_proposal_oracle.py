@@ -4,7 +4,8 @@
   forms for weights that make the network a (shifted) mean of embeddings;
 * the autograd gradient against central finite differences of the forward;
 * Adam's first step against its closed form -lr * g / (|g| + eps');
-* quantisation against hand-worked values;
+* quantisation against hand-worked values, and the quantised ranking value
+  against the float prediction;
 * the dot-product top-C against brute force on tiny inputs with ties;
 * rescoring against sorting by hand-listed scores; recall against hand cases.
 """
@@ -108,7 +109,7 @@ def test_forward_closed_form_shift_and_zero_padding():
 def test_gradient_against_finite_differences():
     w = synth.make_words(12, 5, 1.0, 4.0, 2.0, 0, 6, seed=12)
     A = 5
-    flat = rand_params(A, 2, scale=0.25)
+    flat = rand_params(A, 2, scale=0.1)  # a loss of order 1: finite differences stay above roundoff
     g = np.random.default_rng(4)
     pi = g.integers(0, w.n, 10)
     pj = g.integers(0, w.n, 10)
@@ -118,9 +119,10 @@ def test_gradient_against_finite_differences():
 
     def loss_at(theta):
         E = PR.forward(theta, w, A)
-        return np.mean((np.sum(E[pi] * E[pj], axis=1) - y) ** 2)
+        pred = np.array([E[a, :63] @ E[b, :63] + E[a, 63] + E[b, 63] for a, b in zip(pi, pj)])
+        return np.mean((pred - y) ** 2)
 
-    assert abs(loss - loss_at(flat)) < 1e-12
+    assert abs(loss - loss_at(flat)) < 1e-12 * max(1.0, loss)
     # every parameter block, a few coordinates each (coordinates with a
     # non-zero derivative included)
     h = 1e-6
@@ -153,31 +155,60 @@ def test_adam_first_step_closed_form():
 
 
 def test_quantize_hand_values():
-    # max |E| = 2.54 -> scale 0.02; -1.0 / 0.02 = -50, 0.011 / 0.02 = 0.55 -> 1, 1.9 / 0.02 = 95
-    E = np.array([[2.54, -1.0, 0.011, 0.0], [-2.54, 1.9, -0.009, 0.3]], dtype=np.float32)
-    q, s = PR.quantize(E)
+    # max |phi| = 2.54 -> scale 0.02; -1.0 / 0.02 = -50, 0.011 / 0.02 = 0.55 -> 1, 1.9 / 0.02 = 95;
+    # the bias column (63) is left out of the scale and counted in units of scale^2 = 0.0004
+    E = np.zeros((2, 64), dtype=np.float32)
+    E[0, :4] = [2.54, -1.0, 0.011, 0.0]
+    E[1, :4] = [-2.54, 1.9, -0.009, 0.3]
+    E[:, 63] = [1000.0, -0.002]  # far above max |phi|: does not move the scale
+    q, b, s = PR.quantize(E)
     assert abs(float(s) - 0.02) < 1e-9
-    assert q.tolist() == [[127, -50, 1, 0], [-127, 95, 0, 15]]
-    z, s0 = PR.quantize(np.zeros((3, 4), np.float32))
-    assert s0 == 0 and not z.any()
+    assert q[:, :4].tolist() == [[127, -50, 1, 0], [-127, 95, 0, 15]]
+    assert not q[:, 4:].any()
+    assert abs(int(b[0]) - 2_500_000) <= 1 and int(b[1]) == -5
+    z, zb, s0 = PR.quantize(np.zeros((3, 64), np.float32))
+    assert s0 == 0 and not z.any() and not zb.any()
+    # the bias saturates at 2^23
+    E[0, 63] = 1e6
+    assert int(PR.quantize(E)[1][0]) == 1 << 23
 
 
 def test_quantize_round_half_even():
-    # max 127 -> scale exactly 1, so E / scale is E itself
-    E = np.array([[127.0, 0.5, 1.5, 2.5, -0.5, -1.5, 3.49, -126.51]], dtype=np.float32)
-    q, s = PR.quantize(E)
+    # max 127 -> scale exactly 1, so phi / scale is phi itself and scale^2 = 1
+    E = np.zeros((1, 64), dtype=np.float32)
+    E[0, :8] = [127.0, 0.5, 1.5, 2.5, -0.5, -1.5, 3.49, -126.51]
+    E[0, 63] = 2.5
+    q, b, s = PR.quantize(E)
     assert s == 1.0
-    assert q.tolist() == [[127, 0, 2, 2, 0, -2, 3, -127]]
+    assert q[0, :8].tolist() == [127, 0, 2, 2, 0, -2, 3, -127]
+    assert int(b[0]) == 2
 
 
-def brute_dot_topk(q, C):
+def test_predict_matches_quantised_ranking_value():
+    # q_a . q_b + bias_b approximates (pred(a, b) - beta_a) / scale^2
+    g = np.random.default_rng(5)
+    E = g.normal(0, 1, (50, 64)).astype(np.float32)
+    q, b, s = PR.quantize(E)
+    s2 = float(s) ** 2
+    for a in range(5):
+        for c in range(5, 10):
+            exact = PR.predict(E[[a]], E[[c]])[0] - float(E[a, 63])
+            approx = (int(q[a].astype(np.int64) @ q[c].astype(np.int64)) + int(b[c])) * s2
+            # each quantised value is within scale/2 of its feature, the bias within scale^2/2
+            pa, pc = np.abs(E[a, :63].astype(np.float64)), np.abs(E[c, :63].astype(np.float64))
+            bound = np.sum(pa * s / 2 + pc * s / 2 + s2 / 4) + s2 / 2
+            assert abs(exact - approx) <= bound * (1 + 1e-6)
+
+
+def brute_dot_topk(q, C, bias=None):
     n = q.shape[0]
+    bias = np.zeros(n, np.int64) if bias is None else bias
     out_i, out_d = [], []
     for i in range(n):
         lst = []
         for j in range(n):
             if j != i:
-                lst.append((-int(np.dot(q[i].astype(np.int64), q[j].astype(np.int64))), j))
+                lst.append((-(int(np.dot(q[i].astype(np.int64), q[j].astype(np.int64))) + int(bias[j])), j))
         lst.sort()
         lst = lst[:C]
         out_i.append([j for _, j in lst] + [0xFFFFFFFF] * (C - len(lst)))
@@ -197,6 +228,11 @@ def test_dot_topk_brute_force(n, C, levels):
     r = np.array([0, n - 1])
     i2, d2 = PR.dot_topk(q, C, rows=r)
     assert np.array_equal(i2, bi[r]) and np.array_equal(d2, bd[r])
+    # with per-column biases (ties between bias and dot product included)
+    bias = g.integers(-3 * levels, 3 * levels + 1, n)
+    bi3, bd3 = brute_dot_topk(q, C, bias)
+    i3, d3 = PR.dot_topk(q, C, bias=bias)
+    assert np.array_equal(i3, bi3) and np.array_equal(d3, bd3)
 
 
 def test_rescore_topk_hand_case(oracle_mod):
