@@ -4,10 +4,13 @@
  * The paper scores every pair (Section 4) and notes that this cost grows
  * with the square of the dictionary.  This part of the library adds a
  * learned shortcut that it does not have: a character CNN maps each word to
- * 64 values whose dot products approximate the normalised alignment weight
- * s / max(len(A), len(B)) of Section 5; each word's C best dot products
- * propose candidates, and Algorithm 1 rescores only those candidates
- * exactly.  The result is an approximate top-k whose scores are exact.
+ * 64 values, read as 63 features phi and a bias beta, and models the
+ * similarity of two words as pred(a, b) = phi_a . phi_b + beta_a + beta_b
+ * (trained on Algorithm 1's raw score or on Section 5's normalised weight;
+ * the biases carry the -len(A) - len(B) part of a raw score, which no dot
+ * product of one embedding per word can express).  Each word's C best
+ * phi_a . phi_b + beta_b propose candidates, and Algorithm 1 rescores only
+ * those exactly.  The result is an approximate top-k whose scores are exact.
  *
  * Network (fixed shape; float32 parameters, float32 arithmetic):
  *   x_t = emb[code_t]                      (32 values per position)
@@ -41,8 +44,9 @@ typedef struct nw_model nw_model;
 
 /* A model for codes < alphabet (<= 256) with parameters drawn from a
  * SplitMix64 stream of `seed` (embedding uniform on [-sqrt(3), sqrt(3)],
- * weights uniform on +-sqrt(6 / fan_in), biases zero) and Adam moments at
- * zero.  Owned by the caller; freed by nw_model_free. */
+ * convolution weights uniform on +-sqrt(6 / fan_in), output weights on
+ * +-0.1 sqrt(6 / fan_in), biases zero) and Adam moments at zero.  Owned by
+ * the caller; freed by nw_model_free. */
 nw_status nw_model_create(nw_ctx *ctx, uint32_t alphabet, uint64_t seed, nw_model **out);
 void nw_model_free(nw_model *model);
 
@@ -60,7 +64,7 @@ nw_status nw_model_set_params(nw_model *model, const float *params, uint32_t fla
 nw_status nw_model_embed(nw_model *model, nw_dict *dict, float *out, uint32_t flags);
 
 /* Loss and gradient of m pairs without changing the model:
- *   loss = (1/m) sum_p (e[pi[p]] . e[pj[p]] - target[p])^2
+ *   loss = (1/m) sum_p (pred(pi[p], pj[p]) - target[p])^2
  * grad receives nparams floats (NULL to skip).  pi, pj: original indices;
  * m >= 1. */
 nw_status nw_model_loss_grad(nw_model *model, nw_dict *dict, const uint32_t *pi, const uint32_t *pj,
@@ -68,6 +72,7 @@ nw_status nw_model_loss_grad(nw_model *model, nw_dict *dict, const uint32_t *pi,
 
 /* Training by Adam on pairs drawn on the device, each labelled by Algorithm
  * 1 with the dictionary's scoring: target = s / max(len_i, len_j, 1).
+ * With raw_scale > 0 the target is s * raw_scale instead.
  * Each step draws batch_pairs pairs from a SplitMix64 stream of `seed`: a
  * fraction nbr_fraction take j from the given neighbour lists of a uniform i
  * (nbr: n x knb original indices, UINT32_MAX entries skipped; NULL for
@@ -79,26 +84,34 @@ typedef struct {
     uint32_t batch_pairs;   /* <= 65536 */
     float lr, beta1, beta2, eps;
     float nbr_fraction;     /* in [0, 1] */
+    float raw_scale;        /* > 0: target s * raw_scale; 0: s / max(len) */
+    float lr_final;         /* > 0: the rate falls linearly from lr to lr_final over the steps; 0: constant */
+    float clip_norm;        /* > 0: each step's gradient is scaled to norm <= clip_norm; 0: off */
     uint64_t seed;
 } nw_train_config;
 
 nw_status nw_model_train(nw_model *model, nw_dict *dict, const nw_train_config *cfg, const uint32_t *nbr,
                          uint32_t knb, float *losses, uint32_t flags);
 
-/* Symmetric 8-bit quantisation of n x 64 float embeddings with one scale:
- * scale = max|E| / 127 (float32), q = round-half-even(E / scale) clamped to
- * [-127, 127]; all q = 0 when max|E| = 0.  q: n * 64 int8. */
-nw_status nw_quantize_embeddings(nw_ctx *ctx, const float *E, uint32_t n, int8_t *q, float *scale,
-                                 uint32_t flags);
+/* Quantisation of n x 64 float embeddings, all arithmetic in float32:
+ * scale = max|phi| / 127 over the 63 features of every row,
+ * q[i][d] = round-half-even(phi[i][d] / scale) clamped to [-127, 127] for
+ * d < 63, q[i][63] = 0, and bias[i] = round-half-even(beta_i / (scale *
+ * scale)) clamped to +-2^23 (so q_a . q_b + bias_b is phi_a . phi_b + beta_b
+ * in units of scale^2).  All zero when scale is 0.  q: n * 64 int8; bias: n
+ * int32; scale: one float. */
+nw_status nw_quantize_embeddings(nw_ctx *ctx, const float *E, uint32_t n, int8_t *q, int32_t *bias,
+                                 float *scale, uint32_t flags);
 
 /* For every row i of the n x 64 int8 matrix q, the C other rows j with the
- * largest dot product q_i . q_j (exact integers), higher first and lower j
- * first on equal values: idx[i * C + r], dot[i * C + r].  Rows with fewer
- * than C others end in (UINT32_MAX, INT32_MIN).  1 <= C <= NW_MAX_CANDIDATES.
- * The products run on the tensor cores in bf16 with float32 accumulation,
- * which is exact for these integers. */
-nw_status nw_dot_topk(nw_ctx *ctx, const int8_t *q, uint32_t n, uint32_t C, uint32_t *idx, int32_t *dot,
-                      uint32_t flags);
+ * largest value q_i . q_j + bias[j] (exact integers; bias may be NULL for
+ * 0, |bias| <= 2^23), higher first and lower j first on equal values:
+ * idx[i * C + r], val[i * C + r].  Rows with fewer than C others end in
+ * (UINT32_MAX, INT32_MIN).  1 <= C <= NW_MAX_CANDIDATES.  The products run
+ * on the tensor cores in bf16 with float32 accumulation, which is exact for
+ * these integers. */
+nw_status nw_dot_topk(nw_ctx *ctx, const int8_t *q, const int32_t *bias, uint32_t n, uint32_t C, uint32_t *idx,
+                      int32_t *val, uint32_t flags);
 
 /* Exact rescoring: for every word i of `dict`, Algorithm 1's score against
  * each candidate cand[i * C + r] (original indices; UINT32_MAX entries are

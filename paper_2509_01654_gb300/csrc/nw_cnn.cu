@@ -1,6 +1,7 @@
 // nw_cnn.cu -- kernels of the proposal network: tiled float32 matrix products
-// whose operand loaders gather convolution windows directly from the padded
-// activations (no im2col buffer), and the elementwise steps around them.
+// whose operand loaders gather convolution windows directly from the packed
+// activations (no im2col buffer, no padding rows), and the elementwise steps
+// around them.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,28 +30,34 @@ struct DenseT {  // transpose of a row-major matrix
   __device__ __forceinline__ float at(int r, int c) const { return __ldg(p + (size_t)c * ld + r); }
 };
 
-// im2col of padded X[T][Ci]: (t, tap * Ci + ch) = X[t + tap - 1][ch] within t's word block
+// im2col of packed X[T][Ci]: (t, tap * Ci + ch) = X[t + tap - 1][ch] when
+// position pos(t) + tap - 1 lies inside t's word (rinfo: (pos << 8) | len)
 struct Im2col {
   const float* X;
-  int Ci, Lp;
+  const int* rinfo;
+  int Ci;
   static constexpr bool kColFast = true;
   __device__ __forceinline__ float at(int t, int k) const {
     const int tap = k / Ci, ch = k - tap * Ci;
-    const int pos = t % Lp + tap - 1;
-    if (pos < 0 || pos >= Lp) return 0.f;
+    const int info = __ldg(rinfo + t);
+    const int pos = (info >> 8) + tap - 1;
+    if (pos < 0 || pos >= (info & 255)) return 0.f;
     return __ldg(X + (size_t)(t + tap - 1) * Ci + ch);
   }
 };
 
-// shifted output gradient: (t, tap * Co + o) = dY[t - tap + 1][o] within t's word block
+// shifted output gradient: (t, tap * Co + o) = dY[t - tap + 1][o] when
+// position pos(t) - tap + 1 lies inside t's word
 struct Shift {
   const float* dY;
-  int Co, Lp;
+  const int* rinfo;
+  int Co;
   static constexpr bool kColFast = true;
   __device__ __forceinline__ float at(int t, int k) const {
     const int tap = k / Co, o = k - tap * Co;
-    const int pos = t % Lp - tap + 1;
-    if (pos < 0 || pos >= Lp) return 0.f;
+    const int info = __ldg(rinfo + t);
+    const int pos = (info >> 8) - tap + 1;
+    if (pos < 0 || pos >= (info & 255)) return 0.f;
     return __ldg(dY + (size_t)(t - tap + 1) * Co + o);
   }
 };
@@ -70,16 +77,20 @@ constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
 
 // C[M][N] = A[M][K] . B[K][N] over the K range of blockIdx.z: 128 x 128 tiles,
 // 8 x 8 outputs per thread (two 4 x 4 blocks 64 apart in each direction).
+// Mlim / Klim (device, may be null) lower M / K below the launch's bounds.
 template <class AV, class BV>
 __global__ void __launch_bounds__(NT) gemm_kernel(AV A, BV B, int M, int N, int K, int kchunk, float* C, int ldc,
-                                                  Epi e) {
+                                                  Epi e, const int* Mlim, const int* Klim) {
   __shared__ __align__(16) float As[BK][BM];
   __shared__ __align__(16) float Bs[BK][BN];
+  if (Mlim) M = min(M, *Mlim);
+  if (Klim) K = min(K, *Klim);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kb = blockIdx.z * kchunk;
   const int ke = min(K, kb + kchunk);
+  if (m0 >= M || (e.atomic && kb >= ke)) return;  // block-uniform
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -124,7 +135,6 @@ __global__ void __launch_bounds__(NT) gemm_kernel(AV A, BV B, int M, int N, int 
   for (int i = 0; i < 8; ++i) {
     const int m = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
     if (m >= M) continue;
-    const bool rowok = !e.rowlen || (m % e.Lp) < __ldg(e.rowlen + m / e.Lp);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int n = n0 + tx * 4 + (j & 3) + (j >> 2) * 64;
@@ -138,14 +148,14 @@ __global__ void __launch_bounds__(NT) gemm_kernel(AV A, BV B, int M, int N, int 
       if (e.bias) v += __ldg(e.bias + n);
       if (e.relu) v = fmaxf(v, 0.f);
       if (e.gate && !(__ldg(e.gate + (size_t)m * ldc + n) > 0.f)) v = 0.f;
-      if (!rowok) v = 0.f;
       *dst = v;
     }
   }
 }
 
 template <class AV, class BV>
-cudaError_t run_gemm(AV A, BV B, int M, int N, int K, float* C, int ldc, const Epi& e, int splits, cudaStream_t s) {
+cudaError_t run_gemm(AV A, BV B, int M, int N, int K, float* C, int ldc, const Epi& e, int splits, cudaStream_t s,
+                     const int* Mlim = nullptr, const int* Klim = nullptr) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   const int gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
   int kchunk = K;
@@ -156,7 +166,7 @@ cudaError_t run_gemm(AV A, BV B, int M, int N, int K, float* C, int ldc, const E
     gz = (K + kchunk - 1) / kchunk;
   }
   if (K <= 0) gz = 1;
-  gemm_kernel<AV, BV><<<dim3(gx, gy, gz), NT, 0, s>>>(A, B, M, N, K, kchunk, C, ldc, e);
+  gemm_kernel<AV, BV><<<dim3(gx, gy, gz), NT, 0, s>>>(A, B, M, N, K, kchunk, C, ldc, e, Mlim, Klim);
   return cudaGetLastError();
 }
 
@@ -171,60 +181,111 @@ int splits_for(int M, int N, int K, int nsm) {
 // ---------------------------------------------------------------------------
 // elementwise steps
 
-__global__ void word_len_kernel(WordSrc src, int Bw, int* rowlen, uint32_t* err) {
+__global__ void word_len_kernel(WordSrc src, int Bw, int* len, uint32_t* err) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= Bw) return;
   const uint32_t i = src.widx[w];
   if (i >= src.n) {
     atomicOr(err, kErrInput);
-    rowlen[w] = 0;
+    len[w] = 0;
     return;
   }
-  rowlen[w] = __ldg(src.slen + __ldg(src.rank + i));
+  len[w] = __ldg(src.slen + __ldg(src.rank + i));
 }
 
-// one warp per padded position: lane = embedding channel
-__global__ void gather_kernel(WordSrc src, int Bw, int Lp, const float* __restrict__ emb, const int* rowlen,
-                              int32_t* codes, float* X0, uint32_t* err, uint32_t alphabet) {
+constexpr int kScanThreads = 1024;
+
+// off = exclusive prefix sum of len (one block), T = the total (at most Tmax)
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(const int* len, int Bw, int* off, int* T, int Tmax,
+                                                            uint32_t* err) {
+  __shared__ int warp_sum[kScanThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (Bw + kScanThreads - 1) / kScanThreads;
+  const int w0 = min(Bw, tid * per), w1 = min(Bw, w0 + per);
+  int local = 0;
+  for (int w = w0; w < w1; ++w) local += len[w];
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int ws = warp_sum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, ws, o);
+      if (lane >= o) ws += t;
+    }
+    warp_sum[lane] = ws;  // inclusive over warps
+  }
+  __syncthreads();
+  int run = incl - local + (warp ? warp_sum[warp - 1] : 0);
+  for (int w = w0; w < w1; ++w) {
+    off[w] = run;
+    run += len[w];
+  }
+  if (tid == kScanThreads - 1) {
+    const int total = warp_sum[kScanThreads / 32 - 1];
+    if (total > Tmax) atomicOr(err, kErrInput);
+    *T = min(total, Tmax);
+  }
+}
+
+// per-row tables: thread per word (rows past Tmax are dropped)
+__global__ void fill_rows_kernel(const int* len, const int* off, int Bw, int Tmax, int* rinfo, int* rword) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Bw) return;
+  const int L = len[w], o = off[w];
+  for (int t = 0; t < L && o + t < Tmax; ++t) {
+    rinfo[o + t] = (t << 8) | L;
+    rword[o + t] = w;
+  }
+}
+
+// one warp per packed row: lane = embedding channel
+__global__ void gather_kernel(WordSrc src, const int* Tdev, int Tmax, const float* __restrict__ emb, const int* rinfo,
+                              const int* rword, int32_t* codes, float* X0, uint32_t* err, uint32_t alphabet) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (row >= Bw * Lp) return;
-  const int w = row / Lp, t = row - w * Lp;
-  int code = -1;
-  if (t < rowlen[w]) {
-    const uint32_t pos = __ldg(src.rank + src.widx[w]);
-    const uint32_t v = __ldg(src.a_enc + __ldg(src.aoff + pos) + t);
-    code = (int)((v & 0xffffu) >> src.shift);
-    if ((uint32_t)code >= alphabet) {
-      if (lane == 0) atomicOr(err, kErrInput);
-      code = -1;
-    }
+  if (row >= min(Tmax, *Tdev)) return;
+  const int w = rword[row], t = rinfo[row] >> 8;
+  const uint32_t pos = __ldg(src.rank + src.widx[w]);
+  const uint32_t v = __ldg(src.a_enc + __ldg(src.aoff + pos) + t);
+  int code = (int)((v & 0xffffu) >> src.shift);
+  if ((uint32_t)code >= alphabet) {
+    if (lane == 0) atomicOr(err, kErrInput);
+    code = -1;
   }
   if (lane == 0) codes[row] = code;
   X0[(size_t)row * kEmb + lane] = code >= 0 ? __ldg(emb + (size_t)code * kEmb + lane) : 0.f;
 }
 
-__global__ void pool_kernel(const float* __restrict__ Y, const int* rowlen, int Bw, int Lp, float* P) {
+// P[w] = mean of word w's rows (0 for an empty word)
+__global__ void pool_kernel(const float* __restrict__ Y, const int* len, const int* off, int Bw, int Tmax, float* P) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= Bw * kCh) return;
   const int w = x / kCh, ch = x - w * kCh;
-  const int L = rowlen[w];
+  const int o = off[w];
+  const int L = min(len[w], max(0, Tmax - o));  // rows past Tmax were never filled (an error already raised)
   float acc = 0.f;
-  for (int t = 0; t < L; ++t) acc += Y[((size_t)w * Lp + t) * kCh + ch];
+  for (int t = 0; t < L; ++t) acc += Y[((size_t)o + t) * kCh + ch];
   P[x] = L > 0 ? acc / (float)L : 0.f;
 }
 
-__global__ void pool_bwd_kernel(const float* __restrict__ dP, const float* __restrict__ Y, const int* rowlen,
-                                int Bw, int Lp, float* dY) {
+__global__ void pool_bwd_kernel(const float* __restrict__ dP, const float* __restrict__ Y, const int* len,
+                                const int* rword, const int* Tdev, int Tmax, float* dY) {
   const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= (size_t)Bw * Lp * kCh) return;
+  if (x >= (size_t)min(Tmax, *Tdev) * kCh) return;
   const int row = (int)(x / kCh), ch = (int)(x - (size_t)row * kCh);
-  const int w = row / Lp, t = row - w * Lp;
-  const int L = rowlen[w];
-  dY[x] = (t < L && Y[x] > 0.f) ? dP[(size_t)w * kCh + ch] / (float)L : 0.f;
+  const int w = rword[row];
+  dY[x] = Y[x] > 0.f ? dP[(size_t)w * kCh + ch] / (float)len[w] : 0.f;
 }
 
-// one warp per pair: lanes hold dimensions lane and lane + 32
+// one warp per pair: lanes hold dimensions lane and lane + 32.  The 64
+// outputs are 63 features and a bias (the last): pred = phi_a . phi_b + beta_a + beta_b
 __global__ void pair_loss_kernel(const float* __restrict__ E, const float* __restrict__ target, int m, float* dE,
                                  float* loss_acc) {
   const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -233,7 +294,8 @@ __global__ void pair_loss_kernel(const float* __restrict__ E, const float* __res
   const float* a = E + (size_t)(2 * p) * kOut;
   const float* b = E + (size_t)(2 * p + 1) * kOut;
   const float a0 = a[lane], a1 = a[lane + 32], b0 = b[lane], b1 = b[lane + 32];
-  float d = a0 * b0 + a1 * b1;
+  const bool bias_lane = lane == 31;  // holds output 63 as its second value
+  float d = a0 * b0 + (bias_lane ? a1 + b1 : a1 * b1);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
   const float diff = d - target[p];
@@ -241,38 +303,52 @@ __global__ void pair_loss_kernel(const float* __restrict__ E, const float* __res
   float* da = dE + (size_t)(2 * p) * kOut;
   float* db = dE + (size_t)(2 * p + 1) * kOut;
   da[lane] = g * b0;
-  da[lane + 32] = g * b1;
+  da[lane + 32] = bias_lane ? g : g * b1;
   db[lane] = g * a0;
-  db[lane + 32] = g * a1;
+  db[lane + 32] = bias_lane ? g : g * a1;
   if (lane == 0 && loss_acc) atomicAdd(loss_acc, diff * diff / (float)m);
 }
 
 constexpr int kColSumRows = 256;
 
-__global__ void col_sum_kernel(const float* __restrict__ Y, int rows, int cols, float* out) {
+__global__ void col_sum_kernel(const float* __restrict__ Y, int rows, const int* rows_dev, int cols, float* out) {
   const int c = threadIdx.x;
+  if (rows_dev) rows = min(rows, *rows_dev);
   const int r0 = blockIdx.x * kColSumRows;
   const int r1 = min(rows, r0 + kColSumRows);
-  if (c >= cols) return;
+  if (c >= cols || r0 >= r1) return;
   float acc = 0.f;
   for (int r = r0; r < r1; ++r) acc += Y[(size_t)r * cols + c];
   atomicAdd(out + c, acc);
 }
 
-__global__ void emb_scatter_kernel(const float* __restrict__ dX0, const int32_t* codes, int T, float* demb) {
+__global__ void emb_scatter_kernel(const float* __restrict__ dX0, const int32_t* codes, const int* Tdev, int Tmax,
+                                   float* demb) {
   const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= (size_t)T * kEmb) return;
+  if (x >= (size_t)min(Tmax, *Tdev) * kEmb) return;
   const int row = (int)(x / kEmb), ch = (int)(x - (size_t)row * kEmb);
   const int code = codes[row];
   if (code >= 0) atomicAdd(demb + (size_t)code * kEmb + ch, dX0[x]);
 }
 
+// Adam with bias correction; the gradient is scaled by min(1, clip / |g|)
+// when clip > 0 (|g|^2 in *sumsq), and the rate falls linearly from lr to
+// lr_final over the steps [step0, step0 + nsteps).
 __global__ void adam_kernel(float* theta, const float* __restrict__ g, float* m, float* v, uint64_t n,
-                            const uint32_t* step, float lr, float b1, float b2, float eps) {
+                            const uint32_t* step, AdamCfg c) {
   const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= n) return;
-  const float t = (float)*step;
-  const float gx = g[x];
+  const uint32_t st = *step;
+  const float t = (float)st;
+  const float frac = c.nsteps ? fminf(1.f, (float)(st - 1u - c.step0) / (float)c.nsteps) : 0.f;
+  const float lr = c.lr + (c.lr_final - c.lr) * frac;
+  const float b1 = c.b1, b2 = c.b2, eps = c.eps;
+  float gscale = 1.f;
+  if (c.clip > 0.f) {
+    const float norm = sqrtf(*c.sumsq);
+    if (norm > c.clip) gscale = c.clip / norm;
+  }
+  const float gx = g[x] * gscale;
   const float mx = b1 * m[x] + (1.f - b1) * gx;
   const float vx = b2 * v[x] + (1.f - b2) * gx * gx;
   m[x] = mx;
@@ -283,6 +359,15 @@ __global__ void adam_kernel(float* theta, const float* __restrict__ g, float* m,
 }
 
 __global__ void bump_kernel(uint32_t* step) { *step += 1u; }
+
+__global__ void sumsq_kernel(const float* __restrict__ g, uint64_t n, float* out) {
+  float acc = 0.f;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+    acc += g[x] * g[x];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
 
 __global__ void record_loss_kernel(float* cur, float* losses, const uint32_t* step, uint32_t step0,
                                    uint32_t nsteps) {
@@ -318,9 +403,13 @@ __global__ void draw_pairs_kernel(PairDraw d, uint32_t* pi, uint32_t* pj, uint32
 }
 
 __global__ void targets_kernel(const int16_t* score, const uint32_t* pi, const uint32_t* pj, const uint32_t* rank,
-                               const uint8_t* slen, int m, float* target) {
+                               const uint8_t* slen, int m, float raw_scale, float* target) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m) return;
+  if (raw_scale > 0.f) {
+    target[p] = (float)score[p] * raw_scale;
+    return;
+  }
   int L = max((int)slen[rank[pi[p]]], (int)slen[rank[pj[p]]]);
   L = L > 0 ? L : 1;
   target[p] = (float)score[p] / (float)L;
@@ -333,31 +422,38 @@ __global__ void interleave_kernel(const uint32_t* pi, const uint32_t* pj, int m,
   widx[2 * p + 1] = pj[p];
 }
 
-__global__ void iota_kernel(uint32_t* out, uint32_t base, int count) {
+__global__ void take_kernel(const uint32_t* src, uint32_t base, int count, uint32_t* out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < count) out[x] = base + (uint32_t)x;
+  if (x < count) out[x] = src[base + (uint32_t)x];
+}
+
+__global__ void scatter_rows_kernel(const float* __restrict__ E, const uint32_t* widx, int Bw, float* dst) {
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (size_t)Bw * kOut) return;
+  const size_t w = x / kOut;
+  dst[(size_t)widx[w] * kOut + (x - w * kOut)] = E[x];
 }
 
 inline unsigned blocks_for(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
-cudaError_t conv_fwd(const float* X, int Ci, const float* W, int Co, int T, int Lp, float* Y, const Epi& e,
+cudaError_t conv_fwd(const float* X, int Ci, const float* W, int Co, const Packed& pk, float* Y, const Epi& e,
                      cudaStream_t s) {
-  return run_gemm(Im2col{X, Ci, Lp}, DenseT{W, 3 * Ci}, T, Co, 3 * Ci, Y, Co, e, 1, s);
+  return run_gemm(Im2col{X, pk.rinfo, Ci}, DenseT{W, 3 * Ci}, pk.Tmax, Co, 3 * Ci, Y, Co, e, 1, s, pk.T);
 }
 
-cudaError_t conv_dw(const float* dY, int Co, const float* X, int Ci, int T, int Lp, float* dW, int nsm,
+cudaError_t conv_dw(const float* dY, int Co, const float* X, int Ci, const Packed& pk, float* dW, int nsm,
                     cudaStream_t s) {
   Epi e;
   e.atomic = true;
-  return run_gemm(DenseT{dY, Co}, Im2col{X, Ci, Lp}, Co, 3 * Ci, T, dW, 3 * Ci, e, splits_for(Co, 3 * Ci, T, nsm),
-                  s);
+  return run_gemm(DenseT{dY, Co}, Im2col{X, pk.rinfo, Ci}, Co, 3 * Ci, pk.Tmax, dW, 3 * Ci, e,
+                  splits_for(Co, 3 * Ci, pk.Tmax, nsm), s, nullptr, pk.T);
 }
 
-cudaError_t conv_dx(const float* dY, int Co, const float* W, int Ci, int T, int Lp, float* dX, const Epi& e,
+cudaError_t conv_dx(const float* dY, int Co, const float* W, int Ci, const Packed& pk, float* dX, const Epi& e,
                     cudaStream_t s) {
-  return run_gemm(Shift{dY, Co, Lp}, WTap{W, Co, Ci}, T, Ci, 3 * Co, dX, Ci, e, 1, s);
+  return run_gemm(Shift{dY, pk.rinfo, Co}, WTap{W, Co, Ci}, pk.Tmax, Ci, 3 * Co, dX, Ci, e, 1, s, pk.T);
 }
 
 cudaError_t lin_fwd(const float* P, int Ci, const float* Wl, int Co, int B, float* E, const Epi& e, cudaStream_t s) {
@@ -374,24 +470,26 @@ cudaError_t lin_dx(const float* dE, int Co, const float* Wl, int Ci, int B, floa
   return run_gemm(Dense{dE, Co}, Dense{Wl, Ci}, B, Ci, Co, dP, Ci, Epi{}, 1, s);
 }
 
-cudaError_t gather_words(const WordSrc& src, int Bw, int Lp, const float* emb, int* rowlen, int32_t* codes,
-                         float* X0, uint32_t* err, uint32_t alphabet, cudaStream_t s) {
-  if (Bw <= 0) return cudaSuccess;
-  word_len_kernel<<<blocks_for(Bw, 256), 256, 0, s>>>(src, Bw, rowlen, err);
-  gather_kernel<<<blocks_for((size_t)Bw * Lp, 8), 256, 0, s>>>(src, Bw, Lp, emb, rowlen, codes, X0, err, alphabet);
+cudaError_t pack_words(const WordSrc& src, int Bw, int Tmax, const float* emb, const PackBufs& b, float* X0,
+                       uint32_t* err, uint32_t alphabet, cudaStream_t s) {
+  if (Bw <= 0) return cudaMemsetAsync(b.T, 0, sizeof(int), s);
+  word_len_kernel<<<blocks_for(Bw, 256), 256, 0, s>>>(src, Bw, b.len, err);
+  scan_kernel<<<1, kScanThreads, 0, s>>>(b.len, Bw, b.off, b.T, Tmax, err);
+  fill_rows_kernel<<<blocks_for(Bw, 256), 256, 0, s>>>(b.len, b.off, Bw, Tmax, b.rinfo, b.rword);
+  gather_kernel<<<blocks_for((size_t)Tmax, 8), 256, 0, s>>>(src, b.T, Tmax, emb, b.rinfo, b.rword, b.codes, X0, err,
+                                                             alphabet);
   return cudaGetLastError();
 }
 
-cudaError_t mean_pool(const float* Y, const int* rowlen, int Bw, int Lp, float* P, cudaStream_t s) {
-  if (Bw <= 0) return cudaSuccess;
-  pool_kernel<<<blocks_for((size_t)Bw * kCh, 256), 256, 0, s>>>(Y, rowlen, Bw, Lp, P);
+cudaError_t mean_pool(const float* Y, const Packed& pk, float* P, cudaStream_t s) {
+  if (pk.Bw <= 0) return cudaSuccess;
+  pool_kernel<<<blocks_for((size_t)pk.Bw * kCh, 256), 256, 0, s>>>(Y, pk.len, pk.off, pk.Bw, pk.Tmax, P);
   return cudaGetLastError();
 }
 
-cudaError_t mean_pool_bwd(const float* dP, const float* Y, const int* rowlen, int Bw, int Lp, float* dY,
-                          cudaStream_t s) {
-  if (Bw <= 0) return cudaSuccess;
-  pool_bwd_kernel<<<blocks_for((size_t)Bw * Lp * kCh, 256), 256, 0, s>>>(dP, Y, rowlen, Bw, Lp, dY);
+cudaError_t mean_pool_bwd(const float* dP, const float* Y, const Packed& pk, float* dY, cudaStream_t s) {
+  if (pk.Tmax <= 0) return cudaSuccess;
+  pool_bwd_kernel<<<blocks_for((size_t)pk.Tmax * kCh, 256), 256, 0, s>>>(dP, Y, pk.len, pk.rword, pk.T, pk.Tmax, dY);
   return cudaGetLastError();
 }
 
@@ -401,21 +499,26 @@ cudaError_t pair_loss(const float* E, const float* target, int m, float* dE, flo
   return cudaGetLastError();
 }
 
-cudaError_t col_sum(const float* Y, int rows, int cols, float* out, cudaStream_t s) {
+cudaError_t col_sum(const float* Y, int rows, const int* rows_dev, int cols, float* out, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
-  col_sum_kernel<<<blocks_for(rows, kColSumRows), cols <= 64 ? 64 : 128, 0, s>>>(Y, rows, cols, out);
+  col_sum_kernel<<<blocks_for(rows, kColSumRows), cols <= 64 ? 64 : 128, 0, s>>>(Y, rows, rows_dev, cols, out);
   return cudaGetLastError();
 }
 
-cudaError_t emb_scatter(const float* dX0, const int32_t* codes, int T, float* demb, cudaStream_t s) {
-  if (T <= 0) return cudaSuccess;
-  emb_scatter_kernel<<<blocks_for((size_t)T * kEmb, 256), 256, 0, s>>>(dX0, codes, T, demb);
+cudaError_t emb_scatter(const float* dX0, const int32_t* codes, const Packed& pk, float* demb, cudaStream_t s) {
+  if (pk.Tmax <= 0) return cudaSuccess;
+  emb_scatter_kernel<<<blocks_for((size_t)pk.Tmax * kEmb, 256), 256, 0, s>>>(dX0, codes, pk.T, pk.Tmax, demb);
   return cudaGetLastError();
 }
 
-cudaError_t adam(float* theta, const float* g, float* m, float* v, uint64_t n, const uint32_t* step, float lr,
-                 float b1, float b2, float eps, cudaStream_t s) {
-  adam_kernel<<<blocks_for(n, 256), 256, 0, s>>>(theta, g, m, v, n, step, lr, b1, b2, eps);
+cudaError_t adam(float* theta, const float* g, float* m, float* v, uint64_t n, const uint32_t* step,
+                 const AdamCfg& c, cudaStream_t s) {
+  if (c.clip > 0.f) {
+    cudaError_t e = cudaMemsetAsync(c.sumsq, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    sumsq_kernel<<<256, 256, 0, s>>>(g, n, c.sumsq);
+  }
+  adam_kernel<<<blocks_for(n, 256), 256, 0, s>>>(theta, g, m, v, n, step, c);
   return cudaGetLastError();
 }
 
@@ -437,9 +540,9 @@ cudaError_t draw_pairs(const PairDraw& d, uint32_t* pi, uint32_t* pj, uint32_t* 
 }
 
 cudaError_t pair_targets(const int16_t* score, const uint32_t* pi, const uint32_t* pj, const uint32_t* rank,
-                         const uint8_t* slen, int m, float* target, cudaStream_t s) {
+                         const uint8_t* slen, int m, float raw_scale, float* target, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  targets_kernel<<<blocks_for(m, 256), 256, 0, s>>>(score, pi, pj, rank, slen, m, target);
+  targets_kernel<<<blocks_for(m, 256), 256, 0, s>>>(score, pi, pj, rank, slen, m, raw_scale, target);
   return cudaGetLastError();
 }
 
@@ -449,9 +552,15 @@ cudaError_t interleave_pairs(const uint32_t* pi, const uint32_t* pj, int m, uint
   return cudaGetLastError();
 }
 
-cudaError_t iota(uint32_t* out, uint32_t base, int count, cudaStream_t s) {
+cudaError_t take(const uint32_t* src, uint32_t base, int count, uint32_t* out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  iota_kernel<<<blocks_for(count, 256), 256, 0, s>>>(out, base, count);
+  take_kernel<<<blocks_for(count, 256), 256, 0, s>>>(src, base, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_rows(const float* E, const uint32_t* widx, int Bw, float* dst, cudaStream_t s) {
+  if (Bw <= 0) return cudaSuccess;
+  scatter_rows_kernel<<<blocks_for((size_t)Bw * kOut, 256), 256, 0, s>>>(E, widx, Bw, dst);
   return cudaGetLastError();
 }
 

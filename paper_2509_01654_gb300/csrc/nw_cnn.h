@@ -1,9 +1,4 @@
 // nw_cnn.h -- kernels of the proposal network (see include/nw_proposal.h).
-//
-// Activations of a batch of Bw words use a padded layout: word w owns rows
-// [w * Lp, (w + 1) * Lp) of every T x C activation matrix (T = Bw * Lp),
-// row w * Lp + t holding position t; rows at t >= len(w) are kept at zero,
-// which is the convolutions' zero padding.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -48,46 +43,77 @@ struct WordSrc {
   uint32_t n;             // words of the dictionary (bound of widx)
 };
 
-// GEMM epilogue: out = acc (+ bias[n]) (ReLU) (x (gate[m][n] > 0)) (x rowmask),
-// or atomicAdd of acc (split-K accumulation into a zeroed C).
+// A batch of Bw words in the packed layout: word w owns rows
+// [off[w], off[w] + len[w]) of every activation matrix, row off[w] + t
+// holding position t.  Grids are sized for Tmax rows; the actual row count T
+// lives in device memory (kernels stop there), so a step whose words are
+// drawn on the device can still be captured in a graph.
+struct Packed {
+  const int* len;    // Bw word lengths
+  const int* off;    // Bw first rows
+  const int* T;      // device: rows in use
+  const int* rinfo;  // per row: (position << 8) | word length
+  const int* rword;  // per row: word
+  int Bw, Tmax;
+};
+
+// GEMM epilogue: out = acc (+ bias[n]) (ReLU) (x (gate[m][n] > 0)), or
+// atomicAdd of acc (split-K accumulation into a zeroed C).
 struct Epi {
   const float* bias = nullptr;
   bool relu = false;
   const float* gate = nullptr;   // same layout as C
-  const int* rowlen = nullptr;   // mask rows whose position (m % Lp) >= rowlen[m / Lp]
-  int Lp = 1;
   bool atomic = false;
 };
 
-// The network's matrix products (float32, tiled on the CUDA cores).  T rows
-// of padded activations, B words; W is [Co][3][Ci], Wl is [Co][Ci].
+// The network's matrix products (float32, tiled on the CUDA cores).  W is
+// [Co][3][Ci], Wl is [Co][Ci]; activations of a packed batch have pk.T rows.
 //   conv_fwd: Y[T][Co]  = im2col(X[T][Ci]) . W^T            (epilogue e)
-//   conv_dw:  dW[Co][3Ci] += dY^T . im2col(X)               (split over T, atomic)
+//   conv_dw:  dW[Co][3Ci] += dY^T . im2col(X)               (split over rows, atomic)
 //   conv_dx:  dX[T][Ci] = sum_tap shift_tap(dY) . W[.][tap]  (col2im folded in; epilogue e)
 //   lin_fwd:  E[B][Co]  = P[B][Ci] . Wl^T                   (epilogue e)
 //   lin_dw:   dWl[Co][Ci] += dE^T . P                       (split over B, atomic)
 //   lin_dx:   dP[B][Ci] = dE[B][Co] . Wl
-cudaError_t conv_fwd(const float* X, int Ci, const float* W, int Co, int T, int Lp, float* Y, const Epi& e,
+// im2col(X) row t, column tap * Ci + c, is X[t + tap - 1][c] when position
+// pos(t) + tap - 1 lies inside t's word, else 0 (the zero padding).
+cudaError_t conv_fwd(const float* X, int Ci, const float* W, int Co, const Packed& pk, float* Y, const Epi& e,
                      cudaStream_t s);
-cudaError_t conv_dw(const float* dY, int Co, const float* X, int Ci, int T, int Lp, float* dW, int nsm,
+cudaError_t conv_dw(const float* dY, int Co, const float* X, int Ci, const Packed& pk, float* dW, int nsm,
                     cudaStream_t s);
-cudaError_t conv_dx(const float* dY, int Co, const float* W, int Ci, int T, int Lp, float* dX, const Epi& e,
+cudaError_t conv_dx(const float* dY, int Co, const float* W, int Ci, const Packed& pk, float* dX, const Epi& e,
                     cudaStream_t s);
 cudaError_t lin_fwd(const float* P, int Ci, const float* Wl, int Co, int B, float* E, const Epi& e, cudaStream_t s);
 cudaError_t lin_dw(const float* dE, int Co, const float* P, int Ci, int B, float* dWl, int nsm, cudaStream_t s);
 cudaError_t lin_dx(const float* dE, int Co, const float* Wl, int Ci, int B, float* dP, cudaStream_t s);
 
-cudaError_t gather_words(const WordSrc& src, int Bw, int Lp, const float* emb, int* rowlen, int32_t* codes,
-                         float* X0, uint32_t* err, uint32_t alphabet, cudaStream_t s);
-cudaError_t mean_pool(const float* Y, const int* rowlen, int Bw, int Lp, float* P, cudaStream_t s);
-cudaError_t mean_pool_bwd(const float* dP, const float* Y, const int* rowlen, int Bw, int Lp, float* dY,
-                          cudaStream_t s);
-// pairs are word slots (2p, 2p + 1); loss_acc += sum (pred - y)^2 / m (if non-null)
+// word lengths, row offsets and T of widx's words, the per-row tables, the
+// codes and the embedded input X0 (rows past Tmax raise kErrInput)
+struct PackBufs {
+  int* len;
+  int* off;
+  int* T;
+  int* rinfo;
+  int* rword;
+  int32_t* codes;
+};
+cudaError_t pack_words(const WordSrc& src, int Bw, int Tmax, const float* emb, const PackBufs& b, float* X0,
+                       uint32_t* err, uint32_t alphabet, cudaStream_t s);
+cudaError_t mean_pool(const float* Y, const Packed& pk, float* P, cudaStream_t s);
+cudaError_t mean_pool_bwd(const float* dP, const float* Y, const Packed& pk, float* dY, cudaStream_t s);
+// pairs are word slots (2p, 2p + 1), pred = phi . phi + beta + beta (outputs
+// 0..62 features, 63 bias); loss_acc += sum (pred - y)^2 / m (if non-null)
 cudaError_t pair_loss(const float* E, const float* target, int m, float* dE, float* loss_acc, cudaStream_t s);
-cudaError_t col_sum(const float* Y, int rows, int cols, float* out, cudaStream_t s);  // out += column sums
-cudaError_t emb_scatter(const float* dX0, const int32_t* codes, int T, float* demb, cudaStream_t s);
-cudaError_t adam(float* theta, const float* g, float* m, float* v, uint64_t n, const uint32_t* step, float lr,
-                 float b1, float b2, float eps, cudaStream_t s);
+// out += column sums of Y's first rows (rows: a host count, or the device count *rows_dev when non-null)
+cudaError_t col_sum(const float* Y, int rows, const int* rows_dev, int cols, float* out, cudaStream_t s);
+cudaError_t emb_scatter(const float* dX0, const int32_t* codes, const Packed& pk, float* demb, cudaStream_t s);
+struct AdamCfg {
+  float lr, lr_final, b1, b2, eps;
+  float clip;        // > 0: scale the gradient to norm <= clip
+  float* sumsq;      // device scratch for |g|^2
+  uint32_t step0, nsteps;  // the rate falls linearly over steps step0 + 1 .. step0 + nsteps
+};
+cudaError_t adam(float* theta, const float* g, float* m, float* v, uint64_t n, const uint32_t* step,
+                 const AdamCfg& c, cudaStream_t s);
 cudaError_t bump_step(uint32_t* step, cudaStream_t s);
 // losses[*step - 1 - step0] = *cur (when inside [0, nsteps)), then *cur = 0
 cudaError_t record_loss(float* cur, float* losses, const uint32_t* step, uint32_t step0, uint32_t nsteps,
@@ -103,11 +129,14 @@ struct PairDraw {
   uint32_t n_nbr;         // pairs [0, n_nbr) come from the lists
 };
 cudaError_t draw_pairs(const PairDraw& d, uint32_t* pi, uint32_t* pj, uint32_t* widx, cudaStream_t s);
-// target[p] = score[p] / max(len_i, len_j, 1)
+// target[p] = score[p] * raw_scale (raw_scale > 0), else score[p] / max(len_i, len_j, 1)
 cudaError_t pair_targets(const int16_t* score, const uint32_t* pi, const uint32_t* pj, const uint32_t* rank,
-                         const uint8_t* slen, int m, float* target, cudaStream_t s);
+                         const uint8_t* slen, int m, float raw_scale, float* target, cudaStream_t s);
 cudaError_t interleave_pairs(const uint32_t* pi, const uint32_t* pj, int m, uint32_t* widx, cudaStream_t s);
-cudaError_t iota(uint32_t* out, uint32_t base, int count, cudaStream_t s);
+// out[x] = src[base + x]
+cudaError_t take(const uint32_t* src, uint32_t base, int count, uint32_t* out, cudaStream_t s);
+// dst[widx[w] * 64 + d] = E[w * 64 + d]
+cudaError_t scatter_rows(const float* E, const uint32_t* widx, int Bw, float* dst, cudaStream_t s);
 
 }  // namespace cnn
 }  // namespace nw

@@ -23,19 +23,19 @@ struct nw_model {
   cudaStream_t stream = nullptr;
   uint32_t steps_done = 0;  // mirror of the device step counter
   DevBuf params, grads, adam_m, adam_v, small;  // small: step counter, loss accumulator, error flags, amax
-  // forward/backward scratch for cap_words words of cap_Lp positions
-  int cap_words = 0, cap_Lp = 0;
-  DevBuf widx, rowlen, codes, X0, Y1, Y2, Y3, P, E, dE, dP, dYa, dYb, dX0;
+  // forward/backward scratch for cap_words words packed into cap_rows rows
+  int cap_words = 0, cap_rows = 0;
+  DevBuf widx, len, off, rinfo, rword, codes, X0, Y1, Y2, Y3, P, E, dE, dP, dYa, dYb, dX0;
   // training pairs
   uint32_t cap_pairs = 0;
   DevBuf pi, pj, target, score16;
   // proposal path
-  DevBuf Eall, Qb, topbuf, cand, cand_dot, cand_score, nbr;
+  DevBuf Eall, Qb, qbias, topbuf, cand, cand_dot, cand_score, nbr;
 };
 
 namespace {
 
-constexpr int kMaxRowsPerPass = 1 << 20;  // padded positions per forward pass of nw_model_embed
+constexpr int kMaxRowsPerPass = 1 << 20;  // packed positions per forward pass of nw_model_embed
 
 float* fptr(const DevBuf& b, uint64_t off = 0) { return b.as<float>() + off; }
 
@@ -43,25 +43,31 @@ uint32_t* step_ptr(nw_model* M) { return M->small.as<uint32_t>(); }
 float* loss_ptr(nw_model* M) { return reinterpret_cast<float*>(M->small.as<char>() + 4); }
 uint32_t* err_ptr(nw_model* M) { return reinterpret_cast<uint32_t*>(M->small.as<char>() + 8); }
 unsigned int* amax_ptr(nw_model* M) { return reinterpret_cast<unsigned int*>(M->small.as<char>() + 12); }
+int* rows_ptr(nw_model* M) { return reinterpret_cast<int*>(M->small.as<char>() + 16); }
+float* sumsq_ptr(nw_model* M) { return reinterpret_cast<float*>(M->small.as<char>() + 20); }
 
 void model_free_buffers(nw_model* M) {
   nw_ctx* c = M->ctx;
-  DevBuf* bufs[] = {&M->params, &M->grads, &M->adam_m, &M->adam_v, &M->small, &M->widx, &M->rowlen,
-                    &M->codes, &M->X0, &M->Y1, &M->Y2, &M->Y3, &M->P, &M->E, &M->dE, &M->dP, &M->dYa,
+  DevBuf* bufs[] = {&M->params, &M->grads, &M->adam_m, &M->adam_v, &M->small, &M->widx, &M->len, &M->off,
+                    &M->rinfo, &M->rword, &M->codes, &M->X0, &M->Y1, &M->Y2, &M->Y3, &M->P, &M->E, &M->dE, &M->dP, &M->dYa,
                     &M->dYb, &M->dX0, &M->pi, &M->pj, &M->target, &M->score16, &M->Eall, &M->Qb,
-                    &M->topbuf, &M->cand, &M->cand_dot, &M->cand_score, &M->nbr};
+                    &M->qbias, &M->topbuf, &M->cand, &M->cand_dot, &M->cand_score, &M->nbr};
   for (DevBuf* b : bufs) ctx_free(c, *b);
 }
 
-// scratch for Bw words of Lp positions
-nw_status ensure_scratch(nw_model* M, int Bw, int Lp) {
+// scratch for Bw words packed into at most Tmax rows
+nw_status ensure_scratch(nw_model* M, int Bw, int Tmax) {
   nw_ctx* c = M->ctx;
-  if (Bw <= M->cap_words && Lp <= M->cap_Lp) return NW_OK;
-  const int W = std::max(Bw, M->cap_words), Lq = std::max(Lp, M->cap_Lp);
-  const size_t T = (size_t)W * Lq;
-  if (T > (size_t)INT32_MAX / cnn::kCh) return set_err(c, NW_EINVAL, "batch of %d words x %d positions too large", W, Lq);
+  if (Bw <= M->cap_words && Tmax <= M->cap_rows) return NW_OK;
+  const int W = std::max(Bw, M->cap_words);
+  const size_t T = (size_t)std::max(Tmax, M->cap_rows);
+  if (T > (size_t)INT32_MAX / cnn::kCh || W > (1 << 20))
+    return set_err(c, NW_EINVAL, "batch of %d words in %zu rows too large", W, T);
   NW_TRY(ctx_ensure(c, M->widx, sizeof(uint32_t) * W, "model word indices"));
-  NW_TRY(ctx_ensure(c, M->rowlen, sizeof(int) * W, "model word lengths"));
+  NW_TRY(ctx_ensure(c, M->len, sizeof(int) * W, "model word lengths"));
+  NW_TRY(ctx_ensure(c, M->off, sizeof(int) * W, "model word offsets"));
+  NW_TRY(ctx_ensure(c, M->rinfo, sizeof(int) * T, "model row tables"));
+  NW_TRY(ctx_ensure(c, M->rword, sizeof(int) * T, "model row tables"));
   NW_TRY(ctx_ensure(c, M->codes, sizeof(int32_t) * T, "model codes"));
   NW_TRY(ctx_ensure(c, M->X0, sizeof(float) * T * cnn::kEmb, "model activations"));
   NW_TRY(ctx_ensure(c, M->dX0, sizeof(float) * T * cnn::kEmb, "model activations"));
@@ -72,7 +78,7 @@ nw_status ensure_scratch(nw_model* M, int Bw, int Lp) {
   NW_TRY(ctx_ensure(c, M->E, sizeof(float) * W * cnn::kOut, "model embeddings"));
   NW_TRY(ctx_ensure(c, M->dE, sizeof(float) * W * cnn::kOut, "model embeddings"));
   M->cap_words = W;
-  M->cap_Lp = Lq;
+  M->cap_rows = (int)T;
   return NW_OK;
 }
 
@@ -87,7 +93,20 @@ nw_status ensure_pairs(nw_model* M, uint32_t m) {
   return NW_OK;
 }
 
-int padded_len(const nw_dict* d) { return std::max<int>(1, (int)d->ws.max_len); }
+// longest word of the dictionary (rows per word at most)
+int max_len(const nw_dict* d) { return std::max<int>(1, (int)d->ws.max_len); }
+
+cnn::Packed packed(nw_model* M, int Bw, int Tmax) {
+  cnn::Packed pk;
+  pk.len = M->len.as<int>();
+  pk.off = M->off.as<int>();
+  pk.T = rows_ptr(M);
+  pk.rinfo = M->rinfo.as<int>();
+  pk.rword = M->rword.as<int>();
+  pk.Bw = Bw;
+  pk.Tmax = Tmax;
+  return pk;
+}
 
 cnn::WordSrc word_src(const nw_dict* d, const uint32_t* widx) {
   cnn::WordSrc s;
@@ -101,26 +120,25 @@ cnn::WordSrc word_src(const nw_dict* d, const uint32_t* widx) {
   return s;
 }
 
-// embeddings of Bw words (M->widx) into M->E
-nw_status forward(nw_model* M, const nw_dict* d, int Bw, int Lp, cudaStream_t s) {
+// embeddings of Bw words (M->widx), packed into at most Tmax rows, into M->E
+nw_status forward(nw_model* M, const nw_dict* d, int Bw, int Tmax, cudaStream_t s) {
   nw_ctx* c = M->ctx;
   const cnn::Layout& L = M->L;
-  const int T = Bw * Lp;
   const float* W = fptr(M->params);
-  int* rowlen = M->rowlen.as<int>();
-  NW_CK(cnn::gather_words(word_src(d, M->widx.as<uint32_t>()), Bw, Lp, W + L.emb, rowlen, M->codes.as<int32_t>(),
-                          fptr(M->X0), err_ptr(M), M->alphabet, s));
+  const cnn::Packed pk = packed(M, Bw, Tmax);
+  cnn::PackBufs pb{M->len.as<int>(), M->off.as<int>(), rows_ptr(M), M->rinfo.as<int>(), M->rword.as<int>(),
+                   M->codes.as<int32_t>()};
+  NW_CK(cnn::pack_words(word_src(d, M->widx.as<uint32_t>()), Bw, Tmax, W + L.emb, pb, fptr(M->X0), err_ptr(M),
+                        M->alphabet, s));
   cnn::Epi e;
   e.relu = true;
-  e.rowlen = rowlen;
-  e.Lp = Lp;
   e.bias = W + L.b1;
-  NW_CK(cnn::conv_fwd(fptr(M->X0), cnn::kEmb, W + L.W1, cnn::kCh, T, Lp, fptr(M->Y1), e, s));
+  NW_CK(cnn::conv_fwd(fptr(M->X0), cnn::kEmb, W + L.W1, cnn::kCh, pk, fptr(M->Y1), e, s));
   e.bias = W + L.b2;
-  NW_CK(cnn::conv_fwd(fptr(M->Y1), cnn::kCh, W + L.W2, cnn::kCh, T, Lp, fptr(M->Y2), e, s));
+  NW_CK(cnn::conv_fwd(fptr(M->Y1), cnn::kCh, W + L.W2, cnn::kCh, pk, fptr(M->Y2), e, s));
   e.bias = W + L.b3;
-  NW_CK(cnn::conv_fwd(fptr(M->Y2), cnn::kCh, W + L.W3, cnn::kCh, T, Lp, fptr(M->Y3), e, s));
-  NW_CK(cnn::mean_pool(fptr(M->Y3), rowlen, Bw, Lp, fptr(M->P), s));
+  NW_CK(cnn::conv_fwd(fptr(M->Y2), cnn::kCh, W + L.W3, cnn::kCh, pk, fptr(M->Y3), e, s));
+  NW_CK(cnn::mean_pool(fptr(M->Y3), pk, fptr(M->P), s));
   cnn::Epi el;
   el.bias = W + L.bl;
   NW_CK(cnn::lin_fwd(fptr(M->P), cnn::kCh, W + L.Wl, cnn::kOut, Bw, fptr(M->E), el, s));
@@ -128,39 +146,37 @@ nw_status forward(nw_model* M, const nw_dict* d, int Bw, int Lp, cudaStream_t s)
 }
 
 // gradient of the pair loss (pairs = word slots 2p, 2p + 1; targets in M->target) into M->grads
-nw_status backward(nw_model* M, int m, int Lp, cudaStream_t s) {
+nw_status backward(nw_model* M, int m, int Tmax, cudaStream_t s) {
   nw_ctx* c = M->ctx;
   const cnn::Layout& L = M->L;
-  const int Bw = 2 * m, T = Bw * Lp;
+  const int Bw = 2 * m;
   const float* W = fptr(M->params);
   float* G = fptr(M->grads);
-  const int* rowlen = M->rowlen.as<int>();
+  const cnn::Packed pk = packed(M, Bw, Tmax);
   const int nsm = c->sm_count;
   NW_CK(cudaMemsetAsync(G, 0, sizeof(float) * L.total, s));
   NW_CK(cnn::pair_loss(fptr(M->E), fptr(M->target), m, fptr(M->dE), loss_ptr(M), s));
   NW_CK(cnn::lin_dw(fptr(M->dE), cnn::kOut, fptr(M->P), cnn::kCh, Bw, G + L.Wl, nsm, s));
-  NW_CK(cnn::col_sum(fptr(M->dE), Bw, cnn::kOut, G + L.bl, s));
+  NW_CK(cnn::col_sum(fptr(M->dE), Bw, nullptr, cnn::kOut, G + L.bl, s));
   NW_CK(cnn::lin_dx(fptr(M->dE), cnn::kOut, W + L.Wl, cnn::kCh, Bw, fptr(M->dP), s));
-  NW_CK(cnn::mean_pool_bwd(fptr(M->dP), fptr(M->Y3), rowlen, Bw, Lp, fptr(M->dYa), s));
+  NW_CK(cnn::mean_pool_bwd(fptr(M->dP), fptr(M->Y3), pk, fptr(M->dYa), s));
   // layer 3: dYa = dY3
-  NW_CK(cnn::conv_dw(fptr(M->dYa), cnn::kCh, fptr(M->Y2), cnn::kCh, T, Lp, G + L.W3, nsm, s));
-  NW_CK(cnn::col_sum(fptr(M->dYa), T, cnn::kCh, G + L.b3, s));
+  NW_CK(cnn::conv_dw(fptr(M->dYa), cnn::kCh, fptr(M->Y2), cnn::kCh, pk, G + L.W3, nsm, s));
+  NW_CK(cnn::col_sum(fptr(M->dYa), Tmax, pk.T, cnn::kCh, G + L.b3, s));
   cnn::Epi e;
-  e.rowlen = rowlen;
-  e.Lp = Lp;
   e.gate = fptr(M->Y2);
-  NW_CK(cnn::conv_dx(fptr(M->dYa), cnn::kCh, W + L.W3, cnn::kCh, T, Lp, fptr(M->dYb), e, s));
+  NW_CK(cnn::conv_dx(fptr(M->dYa), cnn::kCh, W + L.W3, cnn::kCh, pk, fptr(M->dYb), e, s));
   // layer 2: dYb = dY2
-  NW_CK(cnn::conv_dw(fptr(M->dYb), cnn::kCh, fptr(M->Y1), cnn::kCh, T, Lp, G + L.W2, nsm, s));
-  NW_CK(cnn::col_sum(fptr(M->dYb), T, cnn::kCh, G + L.b2, s));
+  NW_CK(cnn::conv_dw(fptr(M->dYb), cnn::kCh, fptr(M->Y1), cnn::kCh, pk, G + L.W2, nsm, s));
+  NW_CK(cnn::col_sum(fptr(M->dYb), Tmax, pk.T, cnn::kCh, G + L.b2, s));
   e.gate = fptr(M->Y1);
-  NW_CK(cnn::conv_dx(fptr(M->dYb), cnn::kCh, W + L.W2, cnn::kCh, T, Lp, fptr(M->dYa), e, s));
+  NW_CK(cnn::conv_dx(fptr(M->dYb), cnn::kCh, W + L.W2, cnn::kCh, pk, fptr(M->dYa), e, s));
   // layer 1: dYa = dY1
-  NW_CK(cnn::conv_dw(fptr(M->dYa), cnn::kCh, fptr(M->X0), cnn::kEmb, T, Lp, G + L.W1, nsm, s));
-  NW_CK(cnn::col_sum(fptr(M->dYa), T, cnn::kCh, G + L.b1, s));
+  NW_CK(cnn::conv_dw(fptr(M->dYa), cnn::kCh, fptr(M->X0), cnn::kEmb, pk, G + L.W1, nsm, s));
+  NW_CK(cnn::col_sum(fptr(M->dYa), Tmax, pk.T, cnn::kCh, G + L.b1, s));
   e.gate = nullptr;
-  NW_CK(cnn::conv_dx(fptr(M->dYa), cnn::kCh, W + L.W1, cnn::kEmb, T, Lp, fptr(M->dX0), e, s));
-  NW_CK(cnn::emb_scatter(fptr(M->dX0), M->codes.as<int32_t>(), T, G + L.emb, s));
+  NW_CK(cnn::conv_dx(fptr(M->dYa), cnn::kCh, W + L.W1, cnn::kEmb, pk, fptr(M->dX0), e, s));
+  NW_CK(cnn::emb_scatter(fptr(M->dX0), M->codes.as<int32_t>(), pk, G + L.emb, s));
   return NW_OK;
 }
 
@@ -205,20 +221,43 @@ uint64_t splitmix64_next(uint64_t& st) {
   return z ^ (z >> 31);
 }
 
-// embeddings of all n words into M->Eall (n x 64)
+// embeddings of all n words into M->Eall (n x 64): chunks of consecutive
+// sorted positions (words of similar length), each at most kMaxRowsPerPass
+// packed rows, scattered back to original order
 nw_status embed_all(nw_model* M, nw_dict* d, cudaStream_t s) {
   nw_ctx* c = M->ctx;
   const uint32_t n = d->ws.n;
-  const int Lp = padded_len(d);
-  const int chunk = std::max(1, kMaxRowsPerPass / Lp);
-  NW_TRY(ensure_scratch(M, (int)std::min<uint32_t>(n, (uint32_t)chunk), Lp));
+  const Buckets& bk = d->ws.bk;
+  // chunk boundaries on the host from the bucket table
+  std::vector<std::pair<uint32_t, uint32_t>> chunks;  // (first sorted position, words)
+  int max_words = 1;
+  {
+    uint32_t p0 = 0;
+    uint64_t rows = 0;
+    for (int Lb = 0; Lb < kBuckets; ++Lb) {
+      for (uint32_t k = 0; k < bk.count[Lb]; ++k) {
+        const uint32_t p = bk.start[Lb] + k;
+        if (rows + (uint64_t)Lb > (uint64_t)kMaxRowsPerPass || p - p0 >= (uint32_t)kMaxRowsPerPass) {
+          chunks.push_back({p0, p - p0});
+          max_words = std::max<int>(max_words, (int)(p - p0));
+          p0 = p;
+          rows = 0;
+        }
+        rows += (uint64_t)Lb;
+      }
+    }
+    if (n > p0) {
+      chunks.push_back({p0, n - p0});
+      max_words = std::max<int>(max_words, (int)(n - p0));
+    }
+  }
+  NW_TRY(ensure_scratch(M, max_words, kMaxRowsPerPass));
   NW_TRY(ctx_ensure(c, M->Eall, sizeof(float) * std::max<size_t>(1, (size_t)n * cnn::kOut), "embeddings"));
-  for (uint32_t w0 = 0; w0 < n; w0 += (uint32_t)chunk) {
-    const int Bw = (int)std::min<uint32_t>((uint32_t)chunk, n - w0);
-    NW_CK(cnn::iota(M->widx.as<uint32_t>(), w0, Bw, s));
-    NW_TRY(forward(M, d, Bw, Lp, s));
-    NW_CK(cudaMemcpyAsync(fptr(M->Eall, (uint64_t)w0 * cnn::kOut), fptr(M->E), sizeof(float) * Bw * cnn::kOut,
-                          cudaMemcpyDeviceToDevice, s));
+  for (const auto& ch : chunks) {
+    const int Bw = (int)ch.second;
+    NW_CK(cnn::take(d->ws.perm.as<uint32_t>(), ch.first, Bw, M->widx.as<uint32_t>(), s));
+    NW_TRY(forward(M, d, Bw, kMaxRowsPerPass, s));
+    NW_CK(cnn::scatter_rows(fptr(M->E), M->widx.as<uint32_t>(), Bw, fptr(M->Eall), s));
   }
   return NW_OK;
 }
@@ -292,7 +331,7 @@ nw_status nw_model_create(nw_ctx* c, uint32_t alphabet, uint64_t seed, nw_model*
   for (uint64_t x = L.W1; x < L.b1; ++x) h[x] = uniform((float)std::sqrt(6.0 / (3 * cnn::kEmb)));
   for (uint64_t x = L.W2; x < L.b2; ++x) h[x] = uniform((float)std::sqrt(6.0 / (3 * cnn::kCh)));
   for (uint64_t x = L.W3; x < L.b3; ++x) h[x] = uniform((float)std::sqrt(6.0 / (3 * cnn::kCh)));
-  for (uint64_t x = L.Wl; x < L.bl; ++x) h[x] = uniform((float)std::sqrt(6.0 / cnn::kCh));
+  for (uint64_t x = L.Wl; x < L.bl; ++x) h[x] = uniform((float)(0.1 * std::sqrt(6.0 / cnn::kCh)));
   cudaError_t e = cudaMemcpy(M->params.p, h.data(), pb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(M->adam_m.p, 0, pb);
   if (e == cudaSuccess) e = cudaMemset(M->adam_v.p, 0, pb);
@@ -363,16 +402,16 @@ nw_status nw_model_loss_grad(nw_model* M, nw_dict* d, const uint32_t* pi, const 
   NW_TRY(check_model_dict(M, d));
   const bool dev = flags & NW_DEVICE_PTRS;
   cudaStream_t s = M->stream;
-  const int Lp = padded_len(d);
+  const int Tmax = (int)(2 * m) * max_len(d);
   NW_TRY(ensure_pairs(M, m));
-  NW_TRY(ensure_scratch(M, (int)(2 * m), Lp));
+  NW_TRY(ensure_scratch(M, (int)(2 * m), Tmax));
   NW_TRY(copy_in(c, M->pi.as<uint32_t>(), pi, m, dev, s));
   NW_TRY(copy_in(c, M->pj.as<uint32_t>(), pj, m, dev, s));
   NW_TRY(copy_in(c, fptr(M->target), target, m, dev, s));
   NW_CK(cnn::interleave_pairs(M->pi.as<uint32_t>(), M->pj.as<uint32_t>(), (int)m, M->widx.as<uint32_t>(), s));
   NW_CK(cudaMemsetAsync(loss_ptr(M), 0, sizeof(float), s));
-  NW_TRY(forward(M, d, (int)(2 * m), Lp, s));
-  NW_TRY(backward(M, (int)m, Lp, s));
+  NW_TRY(forward(M, d, (int)(2 * m), Tmax, s));
+  NW_TRY(backward(M, (int)m, Tmax, s));
   if (grad) NW_TRY(copy_out(c, grad, fptr(M->grads), M->L.total, dev, s));
   float h_loss = 0.f;
   NW_CK(cudaMemcpyAsync(&h_loss, loss_ptr(M), sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -390,15 +429,17 @@ nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, co
   if (n < 2) return set_err(c, NW_EINVAL, "training needs at least 2 words");
   if (cfg->batch_pairs == 0 || cfg->batch_pairs > 65536) return set_err(c, NW_EINVAL, "batch_pairs must be in [1, 65536]");
   if (!(cfg->nbr_fraction >= 0.f && cfg->nbr_fraction <= 1.f)) return set_err(c, NW_EINVAL, "nbr_fraction in [0, 1]");
+  if (!(cfg->raw_scale >= 0.f)) return set_err(c, NW_EINVAL, "raw_scale must be >= 0");
+  if (!(cfg->clip_norm >= 0.f) || !(cfg->lr_final >= 0.f)) return set_err(c, NW_EINVAL, "clip_norm, lr_final >= 0");
   if (nbr && knb == 0) return set_err(c, NW_EINVAL, "neighbour lists need knb >= 1");
   if (cfg->steps == 0) return NW_OK;
   NW_TRY(check_model_dict(M, d));
   const bool dev = flags & NW_DEVICE_PTRS;
   cudaStream_t s = M->stream;
   const uint32_t m = cfg->batch_pairs;
-  const int Lp = padded_len(d);
+  const int Tmax = (int)(2 * m) * max_len(d);
   NW_TRY(ensure_pairs(M, m));
-  NW_TRY(ensure_scratch(M, (int)(2 * m), Lp));
+  NW_TRY(ensure_scratch(M, (int)(2 * m), Tmax));
   DevBuf loss_buf;
   NW_TRY(ctx_alloc(c, loss_buf, sizeof(float) * cfg->steps, "training losses"));
   struct Free {
@@ -429,6 +470,17 @@ nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, co
   pp.m = m;
   pp.out = M->score16.as<int16_t>();
 
+  cnn::AdamCfg ac;
+  ac.lr = cfg->lr;
+  ac.lr_final = cfg->lr_final > 0.f ? cfg->lr_final : cfg->lr;
+  ac.b1 = cfg->beta1;
+  ac.b2 = cfg->beta2;
+  ac.eps = cfg->eps;
+  ac.clip = cfg->clip_norm;
+  ac.sumsq = sumsq_ptr(M);
+  ac.step0 = M->steps_done;
+  ac.nsteps = cfg->steps;
+
   // one step, captured once and replayed
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -438,12 +490,13 @@ nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, co
     NW_CK(cnn::draw_pairs(pd, M->pi.as<uint32_t>(), M->pj.as<uint32_t>(), M->widx.as<uint32_t>(), s));
     NW_CK(launch_pairs(pp, s));
     NW_CK(cnn::pair_targets(M->score16.as<int16_t>(), M->pi.as<uint32_t>(), M->pj.as<uint32_t>(),
-                            d->ws.rank.as<uint32_t>(), d->ws.slen.as<uint8_t>(), (int)m, fptr(M->target), s));
-    NW_TRY(forward(M, d, (int)(2 * m), Lp, s));
-    NW_TRY(backward(M, (int)m, Lp, s));
+                            d->ws.rank.as<uint32_t>(), d->ws.slen.as<uint8_t>(), (int)m, cfg->raw_scale,
+                            fptr(M->target), s));
+    NW_TRY(forward(M, d, (int)(2 * m), Tmax, s));
+    NW_TRY(backward(M, (int)m, Tmax, s));
     NW_CK(cnn::bump_step(step_ptr(M), s));
     NW_CK(cnn::adam(fptr(M->params), fptr(M->grads), fptr(M->adam_m), fptr(M->adam_v), M->L.total, step_ptr(M),
-                    cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, s));
+                    ac, s));
     NW_CK(cnn::record_loss(loss_ptr(M), loss_buf.as<float>(), step_ptr(M), M->steps_done, cfg->steps, s));
     return NW_OK;
   };
@@ -466,76 +519,91 @@ nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, co
   return check_err(M, s);
 }
 
-nw_status nw_quantize_embeddings(nw_ctx* c, const float* E, uint32_t n, int8_t* q, float* scale, uint32_t flags) {
+nw_status nw_quantize_embeddings(nw_ctx* c, const float* E, uint32_t n, int8_t* q, int32_t* bias, float* scale,
+                                 uint32_t flags) {
   NW_ENTER(c);
-  if (!E || !q || !scale) return set_err(c, NW_EINVAL, "null pointer argument");
+  if (!E || !q || !bias || !scale) return set_err(c, NW_EINVAL, "null pointer argument");
   const bool dev = flags & NW_DEVICE_PTRS;
   cudaStream_t s = c->stream;
   const size_t cnt = (size_t)n * NW_EMBED_DIM;
-  DevBuf dE, dq, dsmall;
+  DevBuf dE, dq, db, dsmall;
   struct Free {
     nw_ctx* c;
-    DevBuf* b[3];
+    DevBuf* b[4];
     ~Free() {
       for (DevBuf* x : b) ctx_free(c, *x);
     }
-  } fr{c, {&dE, &dq, &dsmall}};
+  } fr{c, {&dE, &dq, &db, &dsmall}};
   const float* srcE = E;
   int8_t* dstq = q;
+  int32_t* dstb = bias;
   if (!dev) {
     NW_TRY(ctx_alloc(c, dE, sizeof(float) * std::max<size_t>(1, cnt), "embeddings"));
     NW_TRY(ctx_alloc(c, dq, std::max<size_t>(1, cnt), "quantised embeddings"));
+    NW_TRY(ctx_alloc(c, db, sizeof(int32_t) * std::max<size_t>(1, n), "quantised biases"));
     NW_TRY(copy_in(c, dE.as<float>(), E, cnt, false, s));
     srcE = dE.as<float>();
     dstq = dq.as<int8_t>();
+    dstb = db.as<int32_t>();
   }
   NW_TRY(ctx_alloc(c, dsmall, 16, "quantisation scratch"));
   float* dscale = reinterpret_cast<float*>(dsmall.as<char>() + 4);
-  NW_CK(prop::quantize(srcE, n, dsmall.as<unsigned int>(), dstq, nullptr, dscale, s));
-  if (!dev) NW_TRY(copy_out(c, q, dstq, cnt, false, s));
+  NW_CK(prop::quantize(srcE, n, dsmall.as<unsigned int>(), dstq, nullptr, dstb, dscale, s));
+  if (!dev) {
+    NW_TRY(copy_out(c, q, dstq, cnt, false, s));
+    NW_TRY(copy_out(c, bias, dstb, n, false, s));
+  }
   NW_TRY(copy_out(c, scale, dscale, 1, dev, s));
   NW_CK(cudaStreamSynchronize(s));
   return NW_OK;
 }
 
-nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, uint32_t n, uint32_t C, uint32_t* idx, int32_t* dot,
-                      uint32_t flags) {
+nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, const int32_t* bias, uint32_t n, uint32_t C, uint32_t* idx,
+                      int32_t* val, uint32_t flags) {
   NW_ENTER(c);
-  if (!q || !idx || !dot) return set_err(c, NW_EINVAL, "null pointer argument");
+  if (!q || !idx || !val) return set_err(c, NW_EINVAL, "null pointer argument");
   if (C == 0 || C > NW_MAX_CANDIDATES) return set_err(c, NW_EINVAL, "C must be in [1, %d]", NW_MAX_CANDIDATES);
   if (n == 0) return NW_OK;
   const bool dev = flags & NW_DEVICE_PTRS;
   cudaStream_t s = c->stream;
   const size_t cnt = (size_t)n * NW_EMBED_DIM, outc = (size_t)n * C;
-  DevBuf dq, qb, buf, oi, od;
+  DevBuf dq, db, qb, buf, oi, od;
   struct Free {
     nw_ctx* c;
-    DevBuf* b[5];
+    DevBuf* b[6];
     ~Free() {
       for (DevBuf* x : b) ctx_free(c, *x);
     }
-  } fr{c, {&dq, &qb, &buf, &oi, &od}};
+  } fr{c, {&dq, &db, &qb, &buf, &oi, &od}};
   const int8_t* srcq = q;
+  const int32_t* srcb = bias;
   if (!dev) {
     NW_TRY(ctx_alloc(c, dq, cnt, "quantised embeddings"));
     NW_TRY(copy_in(c, dq.as<int8_t>(), q, cnt, false, s));
     srcq = dq.as<int8_t>();
   }
+  // the kernel reads biases in 16-byte chunks: host or unaligned device biases are copied
+  if (bias && (!dev || (reinterpret_cast<uintptr_t>(bias) & 15u))) {
+    NW_TRY(ctx_alloc(c, db, sizeof(int32_t) * n, "biases"));
+    NW_CK(cudaMemcpyAsync(db.p, bias, sizeof(int32_t) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          s));
+    srcb = db.as<int32_t>();
+  }
   NW_TRY(ctx_alloc(c, qb, cnt * sizeof(__nv_bfloat16), "bf16 embeddings"));
   NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
   uint32_t* out_i = idx;
-  int32_t* out_d = dot;
+  int32_t* out_v = val;
   if (!dev) {
     NW_TRY(ctx_alloc(c, oi, sizeof(uint32_t) * outc, "candidate lists"));
     NW_TRY(ctx_alloc(c, od, sizeof(int32_t) * outc, "candidate lists"));
     out_i = oi.as<uint32_t>();
-    out_d = od.as<int32_t>();
+    out_v = od.as<int32_t>();
   }
   NW_CK(prop::widen(srcq, n, qb.as<__nv_bfloat16>(), s));
-  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), n, C, buf.as<uint64_t>(), out_i, out_d, s));
+  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), srcb, n, C, buf.as<uint64_t>(), out_i, out_v, s));
   if (!dev) {
     NW_TRY(copy_out(c, idx, out_i, outc, false, s));
-    NW_TRY(copy_out(c, dot, out_d, outc, false, s));
+    NW_TRY(copy_out(c, val, out_v, outc, false, s));
   }
   NW_CK(cudaStreamSynchronize(s));
   return NW_OK;
@@ -605,6 +673,7 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
   cudaStream_t s = M->stream;
   const size_t outc = (size_t)n * C;
   NW_TRY(ctx_ensure(c, M->Qb, sizeof(__nv_bfloat16) * (size_t)n * NW_EMBED_DIM, "bf16 embeddings"));
+  NW_TRY(ctx_ensure(c, M->qbias, sizeof(int32_t) * (size_t)n, "quantised biases"));
   NW_TRY(ctx_ensure(c, M->topbuf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
   NW_TRY(ctx_ensure(c, M->cand, sizeof(uint32_t) * outc, "candidate lists"));
   NW_TRY(ctx_ensure(c, M->cand_dot, sizeof(int32_t) * outc, "candidate lists"));
@@ -625,8 +694,6 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
     out_s = os.as<int16_t>();
   }
   // scratch sized before the timed stages
-  const int Lp = padded_len(d);
-  NW_TRY(ensure_scratch(M, (int)std::min<uint32_t>(n, (uint32_t)std::max(1, kMaxRowsPerPass / Lp)), Lp));
   NW_TRY(ctx_ensure(c, M->Eall, sizeof(float) * (size_t)n * cnn::kOut, "embeddings"));
   NW_TRY(ctx_ensure(c, M->cand_score, sizeof(int32_t) * outc, "candidate scores"));
   cudaEvent_t ev[5];
@@ -640,10 +707,11 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
   NW_CK(cudaEventRecord(ev[0], s));
   NW_TRY(embed_all(M, d, s));
   NW_CK(cudaEventRecord(ev[1], s));
-  NW_CK(prop::quantize(fptr(M->Eall), n, amax_ptr(M), nullptr, M->Qb.as<__nv_bfloat16>(), nullptr, s));
+  NW_CK(prop::quantize(fptr(M->Eall), n, amax_ptr(M), nullptr, M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(),
+                       nullptr, s));
   NW_CK(cudaEventRecord(ev[2], s));
-  NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), n, C, M->topbuf.as<uint64_t>(), M->cand.as<uint32_t>(),
-                       M->cand_dot.as<int32_t>(), s));
+  NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
+                       M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), s));
   NW_CK(cudaEventRecord(ev[3], s));
   NW_TRY(rescore_select(c, d, M->cand.as<uint32_t>(), C, k, M->cand_score, out_i, out_s, err_ptr(M), s));
   NW_CK(cudaEventRecord(ev[4], s));

@@ -11,16 +11,20 @@
 namespace nw {
 namespace prop {
 
-constexpr int kCap = 1024;  // append-buffer keys per row of the dot-product top-C
+constexpr int kCap = 2048;       // append-buffer keys per row of the dot-product top-C
+constexpr int kFeat = 63;        // embedding outputs 0..62 are features, 63 is the bias
+constexpr int kBiasLimit = 1 << 23;
 
-// q (int8, may be null) and qb (bf16, may be null) of n x 64 embeddings; scale
-// (device float, may be null); amax_bits is device scratch
+// Quantisation of n x 64 embeddings (see nw_quantize_embeddings): q (int8,
+// may be null), qb (bf16, may be null), bias (int32, may be null), scale
+// (device float, may be null); amax_bits is device scratch.
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,
-                     float* scale, cudaStream_t s);
+                     int32_t* bias, float* scale, cudaStream_t s);
 cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s);
 size_t dot_topk_buffer_bytes(uint32_t n);
-cudaError_t dot_topk(const __nv_bfloat16* Qb, uint32_t n, uint32_t C, uint64_t* buf, uint32_t* idx, int32_t* dot,
-                     cudaStream_t s);
+// each row's C best q_i . q_j + bias_j (bias may be null: 0)
+cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
+                     uint32_t* idx, int32_t* dot, cudaStream_t s);
 
 // Algorithm 1's score of (i, cand[i * C + r]) into score[i * C + r] (int32;
 // INT32_MIN for UINT32_MAX entries); out-of-range or self candidates raise

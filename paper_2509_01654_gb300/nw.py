@@ -49,7 +49,8 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 class TrainConfig(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_uint32), ("batch_pairs", ctypes.c_uint32), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("nbr_fraction", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("nbr_fraction", ctypes.c_float), ("raw_scale", ctypes.c_float), ("lr_final", ctypes.c_float),
+                ("clip_norm", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
 class ProposalProfile(ctypes.Structure):
@@ -153,8 +154,8 @@ def load_library(path: str = LIB_PATH):
     L.nw_model_embed.argtypes = [vp, vp, vp, u32]
     L.nw_model_loss_grad.argtypes = [vp, vp, vp, vp, vp, u32, ctypes.POINTER(ctypes.c_float), vp, u32]
     L.nw_model_train.argtypes = [vp, vp, ctypes.POINTER(TrainConfig), vp, u32, vp, u32]
-    L.nw_quantize_embeddings.argtypes = [vp, vp, u32, vp, ctypes.POINTER(ctypes.c_float), u32]
-    L.nw_dot_topk.argtypes = [vp, vp, u32, u32, vp, vp, u32]
+    L.nw_quantize_embeddings.argtypes = [vp, vp, u32, vp, vp, ctypes.POINTER(ctypes.c_float), u32]
+    L.nw_dot_topk.argtypes = [vp, vp, vp, u32, u32, vp, vp, u32]
     L.nw_rescore_topk.argtypes = [vp, vp, u32, u32, vp, vp, u32]
     L.nw_proposal_topk.argtypes = [vp, vp, u32, u32, vp, vp, ctypes.POINTER(ProposalProfile), u32]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
@@ -650,9 +651,13 @@ class Model:
         return float(loss.value), g
 
     def train(self, d: "Dictionary", steps: int, batch_pairs: int = 8192, lr: float = 1e-3, seed: int = 1,
-              nbr=None, nbr_fraction: float = 0.5, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
-        """Adam on device-drawn pairs labelled by Algorithm 1; returns the per-step losses."""
-        cfg = TrainConfig(steps, batch_pairs, lr, beta1, beta2, eps, nbr_fraction if nbr is not None else 0.0, seed)
+              nbr=None, nbr_fraction: float = 0.5, raw_scale: float = 0.0, lr_final: float = 0.0,
+              clip_norm: float = 0.0, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        """Adam on device-drawn pairs labelled by Algorithm 1; returns the per-step losses.
+        raw_scale > 0 trains on s * raw_scale, else on s / max(len); lr_final > 0 decays
+        the rate linearly to it; clip_norm > 0 clips the gradient norm."""
+        cfg = TrainConfig(steps, batch_pairs, lr, beta1, beta2, eps, nbr_fraction if nbr is not None else 0.0,
+                          raw_scale, lr_final, clip_norm, seed)
         losses = np.zeros(max(steps, 1), dtype=np.float32)
         knb = 0
         if nbr is not None:
@@ -677,26 +682,29 @@ class Model:
 
 
 def quantize_embeddings(ctx: Context, E):
-    """(q int8 [n, 64], scale) by nw_quantize_embeddings (host arrays)."""
+    """(q int8 [n, 64], bias int32 [n], scale) by nw_quantize_embeddings (host arrays)."""
     E = np.ascontiguousarray(E, dtype=np.float32)
     n = int(E.shape[0])
     q = np.empty((n, EMBED_DIM), dtype=np.int8)
+    b = np.empty(max(n, 1), dtype=np.int32)
     sc = ctypes.c_float(0)
-    _check(ctx.handle, load_library().nw_quantize_embeddings(ctx.handle, _ptr(E)[0], n, _ptr(q)[0],
+    _check(ctx.handle, load_library().nw_quantize_embeddings(ctx.handle, _ptr(E)[0], n, _ptr(q)[0], _ptr(b)[0],
                                                              ctypes.byref(sc), 0))
-    return q, np.float32(sc.value)
+    return q, b[:n], np.float32(sc.value)
 
 
-def dot_topk(ctx: Context, q, C: int):
-    """(idx uint32 [n, C], dot int32 [n, C]) by nw_dot_topk (host or CUDA buffers)."""
+def dot_topk(ctx: Context, q, C: int, bias=None):
+    """(idx uint32 [n, C], val int32 [n, C]) by nw_dot_topk (host or CUDA buffers)."""
     if not _is_torch(q):
         q = np.ascontiguousarray(q, dtype=np.int8)
+        if bias is not None:
+            bias = np.ascontiguousarray(bias, dtype=np.int32)
     n = int(q.shape[0])
     idx = _empty_like_kind(q, (n, C), np.uint32, _torch_dtype("int32"))
-    dot = _empty_like_kind(q, (n, C), np.int32, _torch_dtype("int32"))
-    _check(ctx.handle, load_library().nw_dot_topk(ctx.handle, _ptr(q)[0], n, C, _ptr(idx)[0], _ptr(dot)[0],
-                                                  _flags(q, idx, dot)))
-    return idx, dot
+    val = _empty_like_kind(q, (n, C), np.int32, _torch_dtype("int32"))
+    _check(ctx.handle, load_library().nw_dot_topk(ctx.handle, _ptr(q)[0], _ptr(bias)[0], n, C, _ptr(idx)[0],
+                                                  _ptr(val)[0], _flags(q, bias, idx, val)))
+    return idx, val
 
 
 def rescore_topk(d: "Dictionary", cand, k: int):

@@ -141,26 +141,50 @@ def test_first_adam_step_and_training_lowers_loss(ctx):
 def test_quantize_matches_oracle(ctx):
     g = np.random.default_rng(1)
     E = (g.normal(0, 1, (5000, 64)) * g.uniform(0.1, 3.0, (5000, 1))).astype(np.float32)
-    E[17, 3] = 0.5 * np.abs(E).max()  # exact halves after division happen rarely; this one is plain
-    q, s = nw.quantize_embeddings(ctx, E)
-    wq, ws = PR.quantize(E)
+    E[:, 63] = g.normal(-10, 5, 5000).astype(np.float32)  # biases on their own scale
+    E[17, 63] = 1e9  # saturates at 2^23
+    q, b, s = nw.quantize_embeddings(ctx, E)
+    wq, wb, ws = PR.quantize(E)
     assert s == ws
     assert np.array_equal(q, wq)
-    z, s0 = nw.quantize_embeddings(ctx, np.zeros((3, 64), np.float32))
-    assert s0 == 0 and not z.any()
+    assert np.array_equal(b, wb)
+    assert int(b[17]) == 1 << 23 and not q[:, 63].any()
+    z, zb, s0 = nw.quantize_embeddings(ctx, np.zeros((3, 64), np.float32))
+    assert s0 == 0 and not z.any() and not zb.any()
 
 
-@pytest.mark.parametrize("n,C,levels", [(1000, 64, 127), (777, 32, 2), (20, 64, 5), (1, 4, 3), (300, 512, 127),
-                                        (4100, 256, 127)])
-def test_dot_topk_matches_oracle(ctx, n, C, levels):
+@pytest.mark.parametrize("n,C,levels,bias_range", [(1000, 64, 127, 0), (777, 32, 2, 0), (20, 64, 5, 0),
+                                                   (1, 4, 3, 0), (300, 512, 127, 0), (4100, 256, 127, 0),
+                                                   (1000, 64, 127, 300_000), (777, 32, 2, 40), (301, 64, 127, -1)])
+def test_dot_topk_matches_oracle(ctx, n, C, levels, bias_range):
     g = np.random.default_rng(n + C)
     q = g.integers(-levels, levels + 1, (n, 64)).astype(np.int8)
     if n > 10:
         q[n // 3] = q[1]  # duplicate rows
-    idx, dot = nw.dot_topk(ctx, q, C)
-    wi, wd = PR.dot_topk(q, C)
+    bias = None
+    if bias_range > 0:
+        bias = g.integers(-bias_range, bias_range + 1, n).astype(np.int32)
+    elif bias_range < 0:  # the extremes: sums near 2^24 must stay exact
+        bias = g.choice(np.array([-(1 << 23), (1 << 23), 0, 1], np.int32), n)
+    idx, dot = nw.dot_topk(ctx, q, C, bias=bias)
+    wi, wd = PR.dot_topk(q, C, bias=bias)
     assert np.array_equal(dot, wd)
     assert np.array_equal(idx, wi)
+
+
+def test_dot_topk_device_buffers_and_unaligned_bias(ctx):
+    import torch
+    n, C = 700, 48
+    g = np.random.default_rng(3)
+    q = g.integers(-60, 61, (n, 64)).astype(np.int8)
+    bias = g.integers(-5000, 5001, n + 1).astype(np.int32)
+    wi, wd = PR.dot_topk(q, C, bias=bias[1:])
+    tq = torch.from_numpy(q).cuda()
+    tb = torch.from_numpy(bias).cuda()[1:]  # 4 bytes past an aligned start
+    assert tb.data_ptr() % 16 != 0
+    idx, dot = nw.dot_topk(ctx, tq, C, bias=tb)
+    assert np.array_equal(dot.cpu().numpy(), wd)
+    assert np.array_equal(idx.cpu().numpy().view(np.uint32), wi)
 
 
 def test_dot_topk_large_sampled_rows(ctx):
