@@ -321,6 +321,11 @@ def run_ours(args, rank, world, local_rank):
         }
         batch.free()
 
+    # the learned candidate proposal against the exhaustive lists of the timed leg
+    proposal_stats = None
+    if args.proposal_steps > 0 and rank == 0:
+        proposal_stats = proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, total_ms / args.steps, dev)
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, rows, dt, threads = oracle_sample(w, float(os.environ.get("NW_CPU_BASELINE_S", "15")))
@@ -352,8 +357,85 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "serving": serving_stats,
         "batched": batched_stats,
+        "proposal": proposal_stats,
     }
     print(json.dumps(line), flush=True)
+
+
+def recall_vs_exact(ex_i, ex_s, ap_i, ap_s):
+    """(strict, tie-aware) recall of approximate top-k lists against exact ones:
+    strict = shared neighbours / k; tie-aware also counts a neighbour whose
+    (exact) score reaches the exact k-th score."""
+    import numpy as np
+    ok = ex_i[:, -1] != 0xFFFFFFFF
+    e, a = ex_i[ok].astype(np.int64), ap_i[ok].astype(np.int64)
+    strict = (e[:, :, None] == a[:, None, :]).any(axis=1).sum(axis=1) / e.shape[1]
+    kth = ex_s[ok][:, -1].astype(np.int32)
+    tie = np.minimum((ap_s[ok].astype(np.int32) >= kth[:, None]).sum(axis=1), e.shape[1]) / e.shape[1]
+    return float(strict.mean()), float(tie.mean())
+
+
+def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_ms, dev):
+    import numpy as np
+    import torch
+    k = K_NEIGHBOURS
+    d = ctx.load_dictionary(codes_d, offs_d, 40, SCORING)
+    ex_i = idx_d.cpu().numpy().view(np.uint32)
+    ex_s = score_d.cpu().numpy()
+    n = w.n
+    out_i = torch.empty((n, k), dtype=torch.int32, device=dev)
+    out_s = torch.empty((n, k), dtype=torch.int16, device=dev)
+    train_cfg = dict(batch_pairs=8192, lr=1e-3, lr_final=1e-4, clip_norm=1.0, nbr_fraction=0.5, seed=1)
+
+    def evaluate(model, C, reps):
+        model.proposal_topk(d, C, k, nbr_idx=out_i, nbr_score=out_s)  # warm-up
+        profs, walls = [], []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, prof = model.proposal_topk(d, C, k, nbr_idx=out_i, nbr_score=out_s)
+            walls.append(1e3 * (time.perf_counter() - t0))
+            profs.append(prof)
+        strict, tie = recall_vs_exact(ex_i, ex_s, out_i.cpu().numpy().view(np.uint32), out_s.cpu().numpy())
+        med = {key: statistics.median(p[key] for p in profs) for key in profs[0]}
+        return {"ms": {key: round(v, 3) for key, v in med.items()}, "wall_ms": round(statistics.median(walls), 3),
+                "recall_at_10": round(strict, 4), "recall_at_10_tie_aware": round(tie, 4),
+                "speedup_vs_exhaustive": round(exhaustive_ms / med["total_ms"], 2)}
+
+    untrained = nw.Model(ctx, 40, seed=1)
+    ablation = {"untrained_C256": evaluate(untrained, 256, 1)}
+    untrained.free()
+    model = nw.Model(ctx, 40, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = model.train(d, steps=args.proposal_steps, nbr=ex_i, **train_cfg)
+    train_s = time.perf_counter() - t0
+    res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (128, 256)}
+    # candidates without a network: the C words nearest in length order (stable by index)
+    order = np.argsort(w.lengths, kind="stable")
+    pos = np.empty(n, dtype=np.int64)
+    pos[order] = np.arange(n)
+    C = 256
+    lo = np.clip(pos - C // 2, 0, n - C - 1)
+    win = lo[:, None] + np.arange(C + 1)[None, :]
+    win = win[win != pos[:, None]].reshape(n, C)
+    li, ls = nw.rescore_topk(d, order[win].astype(np.uint32), k)
+    st, tt = recall_vs_exact(ex_i, ex_s, li, ls)
+    ablation["length_window_C256"] = {"recall_at_10": round(st, 4), "recall_at_10_tie_aware": round(tt, 4)}
+    model.free()
+    d.free()
+    return {
+        "workload": (f"{n:,} words of the exhaustive workload; approximate top-{k} by the learned proposal "
+                     f"(embed, quantise, C candidates by exact integer dot product, exact rescoring) against "
+                     f"the exhaustive top-{k} lists of the timed leg"),
+        "train": {"steps": args.proposal_steps, "pairs": args.proposal_steps * train_cfg["batch_pairs"],
+                  "seconds": round(train_s, 2), "target": "s / max(len_i, len_j)",
+                  "loss_first_100": round(float(np.mean(losses[:100])), 5),
+                  "loss_last_100": round(float(np.mean(losses[-100:])), 5), **train_cfg},
+        "exhaustive_ms": round(exhaustive_ms, 3),
+        "by_candidates": res,
+        "ablation": ablation,
+    }
 
 
 def main():
@@ -369,6 +451,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrivals per second")
     ap.add_argument("--batched-dicts", type=int, default=64,
                     help="dictionaries of the batched-launch measurement (0 skips it)")
+    ap.add_argument("--proposal-steps", type=int, default=3000,
+                    help="training steps of the learned-proposal measurement (0 skips it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
