@@ -60,6 +60,20 @@ def lib():
         L.nwo_score_pairs.argtypes = [u8p, u32p, ctypes.c_uint32, u32p, u32p, ctypes.c_size_t,
                                       ci, ci, ci, i32p, ci]
         L.nwo_score_pairs.restype = ci
+        i32a = ctypes.POINTER(ctypes.c_int32)
+        L.nwo_score_sim.argtypes = [u8p, ci, u8p, ci, i32a, ci, ci]
+        L.nwo_score_sim.restype = ctypes.c_int32
+        L.nwo_all_pairs_sim.argtypes = [u8p, u32p, ctypes.c_uint32, i32a, ci, ci, i32p, ci]
+        L.nwo_all_pairs_sim.restype = ci
+        L.nwo_topk_rows_sim.argtypes = [u8p, u32p, ctypes.c_uint32, u32p, ctypes.c_uint32, ctypes.c_uint32,
+                                        i32a, ci, ci, u32p, i32p, ci]
+        L.nwo_topk_rows_sim.restype = ci
+        L.nwo_histogram_sim.argtypes = [u8p, u32p, ctypes.c_uint32, i32a, ci, ci, ctypes.c_int32,
+                                        ctypes.c_uint32, i64p, ci]
+        L.nwo_histogram_sim.restype = ctypes.c_int64
+        L.nwo_score_pairs_sim.argtypes = [u8p, u32p, ctypes.c_uint32, u32p, u32p, ctypes.c_size_t,
+                                          i32a, ci, ci, i32p, ci]
+        L.nwo_score_pairs_sim.restype = ci
         _lib = L
     return _lib
 
@@ -187,3 +201,79 @@ def upper_index(i, j, n):
     i = np.asarray(i, dtype=np.int64)
     j = np.asarray(j, dtype=np.int64)
     return i * (2 * n - i - 1) // 2 + (j - i - 1)
+
+
+# ---------------------------------------------------------------------------
+# a full similarity matrix: sim[a][b] replaces match / mismatch (Algorithm 1's
+# similarity step); gap as above
+
+def _sim(sim):
+    sim = np.ascontiguousarray(sim, dtype=np.int32)
+    assert sim.ndim == 2 and sim.shape[0] == sim.shape[1]
+    return sim, int(sim.shape[0])
+
+
+def score_sim(A, B, sim, gap) -> int:
+    sim, a = _sim(sim)
+    A = np.asarray(A, dtype=np.uint8)
+    B = np.asarray(B, dtype=np.uint8)
+    return int(lib().nwo_score_sim(_p(_u8(A), ctypes.c_uint8), len(A), _p(_u8(B), ctypes.c_uint8), len(B),
+                                   _p(sim, ctypes.c_int32), a, gap))
+
+
+def all_pairs_sim(words, sim, gap, nthreads=None) -> np.ndarray:
+    sim, a = _sim(sim)
+    n = words.n
+    out = np.zeros(max(1, n * (n - 1) // 2), dtype=np.int32)
+    rc = lib().nwo_all_pairs_sim(_p(_u8(words.codes), ctypes.c_uint8), _p(_u32(words.offsets), ctypes.c_uint32),
+                                 n, _p(sim, ctypes.c_int32), a, gap, _p(out, ctypes.c_int32),
+                                 nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"nwo_all_pairs_sim failed: {rc}")
+    return out[:n * (n - 1) // 2]
+
+
+def topk_rows_sim(words, rows, k, sim, gap, nthreads=None):
+    sim, a = _sim(sim)
+    rows = _u32(rows)
+    idx = np.zeros((rows.size, k), dtype=np.uint32)
+    sc = np.zeros((rows.size, k), dtype=np.int32)
+    if rows.size == 0:
+        return idx, sc
+    rc = lib().nwo_topk_rows_sim(_p(_u8(words.codes), ctypes.c_uint8), _p(_u32(words.offsets), ctypes.c_uint32),
+                                 words.n, _p(rows, ctypes.c_uint32), rows.size, k, _p(sim, ctypes.c_int32), a, gap,
+                                 _p(idx, ctypes.c_uint32), _p(sc, ctypes.c_int32), nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"nwo_topk_rows_sim failed: {rc}")
+    return idx, sc
+
+
+def histogram_sim(words, sim, gap, lo, nbins, nthreads=None) -> np.ndarray:
+    sim, a = _sim(sim)
+    h = np.zeros(nbins, dtype=np.int64)
+    bad = lib().nwo_histogram_sim(_p(_u8(words.codes), ctypes.c_uint8), _p(_u32(words.offsets), ctypes.c_uint32),
+                                  words.n, _p(sim, ctypes.c_int32), a, gap, lo, nbins, _p(h, ctypes.c_int64),
+                                  nthreads or default_threads())
+    if bad != 0:
+        raise RuntimeError(f"nwo_histogram_sim: {bad} scores outside the bins (or error)")
+    return h
+
+
+def score_pairs_sim(words, I, J, sim, gap, nthreads=None) -> np.ndarray:
+    sim, a = _sim(sim)
+    I, J = _u32(I), _u32(J)
+    out = np.zeros(max(1, I.size), dtype=np.int32)
+    rc = lib().nwo_score_pairs_sim(_p(_u8(words.codes), ctypes.c_uint8), _p(_u32(words.offsets), ctypes.c_uint32),
+                                   words.n, _p(I, ctypes.c_uint32), _p(J, ctypes.c_uint32), I.size,
+                                   _p(sim, ctypes.c_int32), a, gap, _p(out, ctypes.c_int32),
+                                   nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"nwo_score_pairs_sim failed: {rc}")
+    return out[:I.size]
+
+
+def match_mismatch_matrix(alphabet, match, mismatch) -> np.ndarray:
+    """The matrix of the scalar scoring: match on the diagonal, mismatch elsewhere."""
+    m = np.full((alphabet, alphabet), mismatch, dtype=np.int32)
+    np.fill_diagonal(m, match)
+    return m

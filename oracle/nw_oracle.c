@@ -27,6 +27,8 @@
  *   - nwo_histogram: one bin per integer score, each unordered pair counted
  *     once (the edge-weight histogram of Section 5).
  *   - nwo_score_pairs: the scores of an explicit list of pairs.
+ *   - the *_sim variants: the same with Algorithm 1's similarity read from a
+ *     full alphabet x alphabet matrix instead of match / mismatch.
  *
  * Pins: every function above is checked by the oracle's own tests against
  * the paper's worked examples, brute-force enumeration of alignments, the
@@ -71,6 +73,37 @@ static int32_t score_with(int32_t *buf, const uint8_t *A, int la, const uint8_t 
     return buf[la * (lb + 1) + lb];
 }
 
+/* Algorithm 1 with a full similarity matrix (its similarity(A[i-1], B[j-1])
+ * step read from sim[a * alphabet + b]; Section 2's matrix, which Section 6
+ * proposes to tune per phoneme pair). */
+int nwo_score_matrix_sim(const uint8_t *A, int la, const uint8_t *B, int lb, const int32_t *sim,
+                         int alphabet, int gap, int32_t *H) {
+    if (la < 0 || lb < 0 || H == NULL || sim == NULL) return NWO_EINVAL;
+    const int w = lb + 1;
+    for (int i = 0; i <= la; ++i) H[i * w + 0] = gap * i;
+    for (int j = 0; j <= lb; ++j) H[0 * w + j] = gap * j;
+    for (int i = 1; i <= la; ++i) {
+        for (int j = 1; j <= lb; ++j) {
+            int32_t cost = sim[(int)A[i - 1] * alphabet + (int)B[j - 1]];
+            int32_t match_score = H[(i - 1) * w + (j - 1)] + cost;
+            int32_t delete_score = H[(i - 1) * w + j] + gap;
+            int32_t insert_score = H[i * w + (j - 1)] + gap;
+            H[i * w + j] = max3(match_score, delete_score, insert_score);
+        }
+    }
+    return NWO_OK;
+}
+
+int32_t nwo_score_sim(const uint8_t *A, int la, const uint8_t *B, int lb, const int32_t *sim, int alphabet,
+                      int gap) {
+    int32_t *H = (int32_t *)malloc(sizeof(int32_t) * (size_t)(la + 1) * (size_t)(lb + 1));
+    if (!H) return INT32_MIN;
+    nwo_score_matrix_sim(A, la, B, lb, sim, alphabet, gap, H);
+    int32_t s = H[la * (lb + 1) + lb];
+    free(H);
+    return s;
+}
+
 int32_t nwo_score(const uint8_t *A, int la, const uint8_t *B, int lb, int match, int mismatch,
                   int gap) {
     int32_t *H = (int32_t *)malloc(sizeof(int32_t) * (size_t)(la + 1) * (size_t)(lb + 1));
@@ -106,7 +139,18 @@ typedef struct {
     int64_t *out_of_range;
     const uint32_t *pi, *pj;
     size_t npairs;
+    const int32_t *sim; /* NULL: match / mismatch; else alphabet x alphabet */
+    int alphabet;
 } job_t;
+
+/* a pair's score under the job's similarity */
+static int32_t score_job(const job_t *J, int32_t *H, const uint8_t *A, int la, const uint8_t *B, int lb) {
+    if (J->sim) {
+        nwo_score_matrix_sim(A, la, B, lb, J->sim, J->alphabet, J->gap, H);
+        return H[la * (lb + 1) + lb];
+    }
+    return score_with(H, A, la, B, lb, J->match, J->mismatch, J->gap);
+}
 
 typedef struct {
     job_t *job;
@@ -167,7 +211,7 @@ static void all_pairs_rows(job_t *J, int tid) {
             const uint8_t *B = J->codes + J->offsets[j];
             int lb = (int)(J->offsets[j + 1] - J->offsets[j]);
             J->all_out[row_start + (j - i - 1)] =
-                score_with(H, A, la, B, lb, J->match, J->mismatch, J->gap);
+                score_job(J, H, A, la, B, lb);
         }
     }
     free(H);
@@ -224,7 +268,7 @@ static void topk_rows_worker(job_t *J, int tid) {
             if (j == i) continue;
             const uint8_t *B = J->codes + J->offsets[j];
             int lb = (int)(J->offsets[j + 1] - J->offsets[j]);
-            int32_t s = score_with(H, A, la, B, lb, J->match, J->mismatch, J->gap);
+            int32_t s = score_job(J, H, A, la, B, lb);
             keep_best(idx, sc, J->k, &cnt, s, j);
         }
         for (uint32_t c = cnt; c < J->k; ++c) { idx[c] = UINT32_MAX; sc[c] = INT32_MIN; }
@@ -272,7 +316,7 @@ static void topk_rows_norm_worker(job_t *J, int tid) {
             if (j == i) continue;
             const uint8_t *B = J->codes + J->offsets[j];
             int lb = (int)(J->offsets[j + 1] - J->offsets[j]);
-            int32_t s = score_with(H, A, la, B, lb, J->match, J->mismatch, J->gap);
+            int32_t s = score_job(J, H, A, la, B, lb);
             int32_t m = la > lb ? la : lb;
             if (m == 0) m = 1;
             /* insertion into the ordered list, as keep_best but by weight */
@@ -326,7 +370,7 @@ static void query_worker(job_t *J, int tid) {
         for (uint32_t j = 0; j < J->n; ++j) {
             const uint8_t *B = J->codes + J->offsets[j];
             int lb = (int)(J->offsets[j + 1] - J->offsets[j]);
-            int32_t s = score_with(H, A, la, B, lb, J->match, J->mismatch, J->gap);
+            int32_t s = score_job(J, H, A, la, B, lb);
             keep_best(idx, sc, J->k, &cnt, s, j);
         }
         for (uint32_t c = cnt; c < J->k; ++c) { idx[c] = UINT32_MAX; sc[c] = INT32_MIN; }
@@ -368,7 +412,7 @@ static void histogram_rows(job_t *J, int tid) {
         for (uint32_t j = i + 1; j < J->n; ++j) {
             const uint8_t *B = J->codes + J->offsets[j];
             int lb = (int)(J->offsets[j + 1] - J->offsets[j]);
-            int64_t b = (int64_t)score_with(H, A, la, B, lb, J->match, J->mismatch, J->gap) -
+            int64_t b = (int64_t)score_job(J, H, A, la, B, lb) -
                         J->hist_lo;
             if (b < 0 || b >= (int64_t)J->nbins) ++bad; else ++hist[b];
         }
@@ -411,9 +455,8 @@ static void pairs_worker(job_t *J, int tid) {
     if (!H) return;
     for (size_t p = (size_t)tid; p < J->npairs; p += (size_t)J->nthreads) {
         uint32_t i = J->pi[p], j = J->pj[p];
-        J->all_out[p] = score_with(H, J->codes + J->offsets[i], (int)(J->offsets[i + 1] - J->offsets[i]),
-                                   J->codes + J->offsets[j], (int)(J->offsets[j + 1] - J->offsets[j]),
-                                   J->match, J->mismatch, J->gap);
+        J->all_out[p] = score_job(J, H, J->codes + J->offsets[i], (int)(J->offsets[i + 1] - J->offsets[i]),
+                                  J->codes + J->offsets[j], (int)(J->offsets[j + 1] - J->offsets[j]));
     }
     free(H);
 }
@@ -429,6 +472,81 @@ int nwo_score_pairs(const uint8_t *codes, const uint32_t *offsets, uint32_t n, c
     J.match = match; J.mismatch = mismatch; J.gap = gap;
     J.nthreads = nthreads < 1 ? 1 : nthreads;
     J.maxlen = max_length(offsets, n);
+    J.pi = pi; J.pj = pj; J.npairs = m; J.all_out = out;
+    return run_threads(&J, pairs_worker);
+}
+
+/* ------------------------------------------------------------------------ */
+/* the same reductions under a full similarity matrix                       */
+
+static int codes_below(const uint8_t *codes, const uint32_t *offsets, uint32_t n, int alphabet) {
+    for (uint32_t x = offsets[0]; x < offsets[n]; ++x)
+        if ((int)codes[x] >= alphabet) return 0;
+    return 1;
+}
+
+static void sim_job(job_t *J, const uint8_t *codes, const uint32_t *offsets, uint32_t n, const int32_t *sim,
+                    int alphabet, int gap, int nthreads) {
+    memset(J, 0, sizeof *J);
+    J->codes = codes; J->offsets = offsets; J->n = n;
+    J->gap = gap;
+    J->sim = sim; J->alphabet = alphabet;
+    J->nthreads = nthreads < 1 ? 1 : nthreads;
+    J->maxlen = max_length(offsets, n);
+}
+
+int nwo_all_pairs_sim(const uint8_t *codes, const uint32_t *offsets, uint32_t n, const int32_t *sim,
+                      int alphabet, int gap, int32_t *out, int nthreads) {
+    if (!codes || !offsets || !out || !sim || alphabet < 1) return NWO_EINVAL;
+    if (!codes_below(codes, offsets, n, alphabet)) return NWO_EINVAL;
+    job_t J;
+    sim_job(&J, codes, offsets, n, sim, alphabet, gap, nthreads);
+    J.all_out = out;
+    return run_threads(&J, all_pairs_rows);
+}
+
+int nwo_topk_rows_sim(const uint8_t *codes, const uint32_t *offsets, uint32_t n, const uint32_t *rows,
+                      uint32_t nrows, uint32_t k, const int32_t *sim, int alphabet, int gap,
+                      uint32_t *out_idx, int32_t *out_score, int nthreads) {
+    if (!codes || !offsets || !rows || !out_idx || !out_score || k == 0 || !sim || alphabet < 1) return NWO_EINVAL;
+    for (uint32_t r = 0; r < nrows; ++r) if (rows[r] >= n) return NWO_EINVAL;
+    if (!codes_below(codes, offsets, n, alphabet)) return NWO_EINVAL;
+    job_t J;
+    sim_job(&J, codes, offsets, n, sim, alphabet, gap, nthreads);
+    J.rows = rows; J.nrows = nrows; J.k = k;
+    J.top_idx = out_idx; J.top_score = out_score;
+    return run_threads(&J, topk_rows_worker);
+}
+
+int64_t nwo_histogram_sim(const uint8_t *codes, const uint32_t *offsets, uint32_t n, const int32_t *sim,
+                          int alphabet, int gap, int32_t lo, uint32_t nbins, int64_t *hist, int nthreads) {
+    if (!codes || !offsets || !hist || nbins == 0 || !sim || alphabet < 1) return NWO_EINVAL;
+    if (!codes_below(codes, offsets, n, alphabet)) return NWO_EINVAL;
+    job_t J;
+    sim_job(&J, codes, offsets, n, sim, alphabet, gap, nthreads);
+    J.hist_lo = lo; J.nbins = nbins;
+    J.hist_parts = (int64_t *)calloc((size_t)J.nthreads * nbins, sizeof(int64_t));
+    J.out_of_range = (int64_t *)calloc((size_t)J.nthreads, sizeof(int64_t));
+    if (!J.hist_parts || !J.out_of_range) { free(J.hist_parts); free(J.out_of_range); return NWO_ENOMEM; }
+    int rc = run_threads(&J, histogram_rows);
+    int64_t bad = 0;
+    memset(hist, 0, sizeof(int64_t) * nbins);
+    for (int t = 0; t < J.nthreads; ++t) {
+        bad += J.out_of_range[t];
+        for (uint32_t b = 0; b < nbins; ++b) hist[b] += J.hist_parts[(size_t)t * nbins + b];
+    }
+    free(J.hist_parts); free(J.out_of_range);
+    return rc == NWO_OK ? bad : rc;
+}
+
+int nwo_score_pairs_sim(const uint8_t *codes, const uint32_t *offsets, uint32_t n, const uint32_t *pi,
+                        const uint32_t *pj, size_t m, const int32_t *sim, int alphabet, int gap, int32_t *out,
+                        int nthreads) {
+    if (!codes || !offsets || (m && (!pi || !pj || !out)) || !sim || alphabet < 1) return NWO_EINVAL;
+    for (size_t p = 0; p < m; ++p) if (pi[p] >= n || pj[p] >= n) return NWO_EINVAL;
+    if (!codes_below(codes, offsets, n, alphabet)) return NWO_EINVAL;
+    job_t J;
+    sim_job(&J, codes, offsets, n, sim, alphabet, gap, nthreads);
     J.pi = pi; J.pj = pj; J.npairs = m; J.all_out = out;
     return run_threads(&J, pairs_worker);
 }

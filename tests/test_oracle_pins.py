@@ -410,3 +410,59 @@ def test_score_pairs_and_thread_count_independence(oracle_mod):
     a1 = oracle_mod.all_pairs(w, sc, nthreads=1)
     a4 = oracle_mod.all_pairs(w, sc, nthreads=5)
     assert np.array_equal(a1, a4)
+
+
+# ---------------------------------------------------------------------------
+# a full similarity matrix (Algorithm 1's similarity step read from a table)
+
+def column_score_sim(A, B, cols, sim, gap):
+    return sum(gap if (i is None or j is None) else int(sim[A[i]][B[j]]) for i, j in cols)
+
+
+def test_sim_matrix_hand_case(oracle_mod):
+    # two symbols that pay more for being swapped than kept: [0, 1] against [1, 0]
+    S = np.array([[1, 5], [5, 1]], dtype=np.int32)
+    # diagonal alignment 5 + 5 = 10; keeping one symbol in place costs gaps (e.g. 1 + 4 gaps = -3)
+    assert oracle_mod.score_sim([0, 1], [1, 0], S, -1) == 10
+    assert oracle_mod.score_sim([0, 1], [1, 0], S, -1) == max(
+        column_score_sim([0, 1], [1, 0], c, S, -1) for c in alignments(2, 2))
+    # all-gap alignment once every aligned pair costs more than two gaps
+    S2 = np.array([[-5, -5], [-5, -5]], dtype=np.int32)
+    assert oracle_mod.score_sim([0, 1, 1], [1, 0], S2, -1) == -5
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_sim_matrix_brute_force(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    a = 5
+    S = rng.integers(-4, 6, (a, a)).astype(np.int32)
+    S = (S + S.T) // 2  # symmetric, entries of both signs
+    gap = int(rng.integers(-3, 0))
+    for _ in range(25):
+        A = random_word(rng, 0, 5, a)
+        B = random_word(rng, 0, 5, a)
+        want = max(column_score_sim(A, B, c, S, gap) for c in alignments(len(A), len(B)))
+        assert oracle_mod.score_sim(A, B, S, gap) == want
+
+
+def test_sim_matrix_transpose(oracle_mod):
+    rng = np.random.default_rng(9)
+    S = rng.integers(-3, 4, (6, 6)).astype(np.int32)  # not symmetric
+    for _ in range(20):
+        A, B = random_word(rng, 0, 7, 6), random_word(rng, 0, 7, 6)
+        assert oracle_mod.score_sim(A, B, S, -2) == oracle_mod.score_sim(B, A, S.T, -2)
+
+
+@pytest.mark.parametrize("sc", [(1, -1, -1), (2, -3, -1), (1, 0, 0)])
+def test_sim_matrix_reduces_to_scalar_scoring(oracle_mod, sc):
+    w = synth.make_uniform_length_words(120, 7, 1.0, 0, 9, seed=17)
+    S = oracle_mod.match_mismatch_matrix(7, sc[0], sc[1])
+    assert np.array_equal(oracle_mod.all_pairs_sim(w, S, sc[2]), oracle_mod.all_pairs(w, sc))
+    rows = np.arange(w.n)
+    i1, s1 = oracle_mod.topk_rows_sim(w, rows, 8, S, sc[2])
+    i2, s2 = oracle_mod.topk_rows(w, rows, 8, sc)
+    assert np.array_equal(i1, i2) and np.array_equal(s1, s2)
+    lo, nb = -40, 120
+    assert np.array_equal(oracle_mod.histogram_sim(w, S, sc[2], lo, nb), oracle_mod.histogram(w, sc, lo, nb))
+    I, J = rows[:50], rows[::-1][:50]
+    assert np.array_equal(oracle_mod.score_pairs_sim(w, I, J, S, sc[2]), oracle_mod.score_pairs(w, I, J, sc))
