@@ -136,6 +136,20 @@ nw_status nw_load_dictionary(nw_ctx *ctx, const uint8_t *codes, const uint32_t *
                              uint32_t alphabet, const nw_scoring *scoring, uint32_t flags,
                              nw_dict **out);
 
+/* The same with Algorithm 1's similarity read from a full matrix (Section 2;
+ * Section 6 proposes per-phoneme coefficients): sim[a * alphabet + b] for
+ * codes a, b < alphabet <= 64, symmetric, |values| <= 1024, and a linear gap
+ * `gap`.  Every all-pairs call, nw_score_pairs, nw_query and the proposal
+ * path score such a dictionary with the matrix; the no-allocation variant,
+ * the query server and batches take match / mismatch dictionaries only
+ * (NW_EINVAL).  The kernels look each cell's term up in a 64 x 64 table of
+ * max(sim - 2 * gap, 0) in shared memory; NW_ERANGE if
+ * 40 * max(sim - 2 * gap) exceeds 32767.  Histogram bins and the int8 range
+ * check use the bounds of match = max(sim), mismatch = min(sim). */
+nw_status nw_load_dictionary_sim(nw_ctx *ctx, const uint8_t *codes, const uint32_t *offsets, uint32_t n,
+                                 uint32_t alphabet, const int32_t *sim, int32_t gap, uint32_t flags,
+                                 nw_dict **out);
+
 /* Fills `out` with facts about the dictionary. */
 nw_status nw_dict_info_get(const nw_dict *dict, nw_dict_info *out);
 

@@ -11,6 +11,70 @@ using namespace nw;
 // ===========================================================================
 // C ABI
 
+namespace {
+
+// A dictionary from validated scoring: `scoring` gives the gap and the score
+// bounds (match = the best and mismatch = the worst similarity), `tab` the
+// substitution table of a similarity-matrix dictionary (else null).
+nw_status load_impl(nw_ctx* c, const uint8_t* codes, const uint32_t* offsets, uint32_t n, uint32_t alphabet,
+                    const nw_scoring& sc, const ShiftedScoring& ss, const std::vector<uint16_t>* tab, uint32_t flags,
+                    nw_dict** out) {
+  const nw_scoring* scoring = &sc;
+  nw_dict* d = new nw_dict();
+  d->ctx = c;
+  d->sc = sc;
+  d->ss = ss;
+  d->alphabet = alphabet;
+  d->subst = tab != nullptr;
+  nw_status st = NW_OK;
+  if (tab) {
+    st = ctx_alloc(c, d->d_tab, kTabBytes, "substitution table");
+    if (st == NW_OK) {
+      cudaError_t e = cudaMemcpyAsync(d->d_tab.p, tab->data(), kTabBytes, cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "uploading the substitution table");
+    }
+  }
+  if (st == NW_OK) st = ingest(c, codes, offsets, n, alphabet, d->ss.shift, flags, d->ws);
+  if (st == NW_OK) {
+    // score bounds over the length pairs present
+    int lo = INT32_MAX, hi = INT32_MIN;
+    for (int La = 0; La < kBuckets; ++La) {
+      for (int Lb = La; Lb < kBuckets; ++Lb) {
+        const uint32_t na = d->ws.bk.count[La], nb = d->ws.bk.count[Lb];
+        if (!na || !nb || (La == Lb && na < 2)) continue;
+        int l, h;
+        pair_bounds(*scoring, La, Lb, l, h);
+        lo = std::min(lo, l);
+        hi = std::max(hi, h);
+      }
+    }
+    if (lo > hi) lo = hi = 0;  // fewer than two words
+    d->score_lo = lo;
+    d->score_hi = hi;
+    plan_all_pairs(d->ws.bk, kDefaultTA, d->plan);
+    st = ctx_alloc(c, d->d_segs, sizeof(Seg) * std::max<size_t>(1, d->plan.segs.size()), "segment plan");
+    if (st == NW_OK && !d->plan.segs.empty()) {
+      cudaError_t e = cudaMemcpyAsync(d->d_segs.p, d->plan.segs.data(), sizeof(Seg) * d->plan.segs.size(),
+                                      cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) st = cuda_fail(c, e, "uploading the segment plan");
+    }
+  }
+  if (st != NW_OK) {
+    free_wordset(c, d->ws);
+    ctx_free(c, d->d_segs);
+    ctx_free(c, d->d_tab);
+    delete d;
+    return st;
+  }
+  c->dicts.insert(d);
+  *out = d;
+  return NW_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 nw_status nw_create(nw_ctx** out, int device, size_t mem_budget_bytes, void* cuda_stream) {
@@ -90,47 +154,42 @@ nw_status nw_load_dictionary(nw_ctx* c, const uint8_t* codes, const uint32_t* of
   if (!out || !offsets || !scoring || (!codes && n)) return set_err(c, NW_EINVAL, "null pointer argument");
   *out = nullptr;
   if (alphabet == 0 || alphabet > 256) return set_err(c, NW_EINVAL, "alphabet must be in [1, 256]");
-  nw_dict* d = new nw_dict();
-  d->ctx = c;
-  d->sc = *scoring;
-  d->alphabet = alphabet;
-  nw_status st = make_shifted(c, *scoring, alphabet, d->ss);
-  if (st == NW_OK) st = ingest(c, codes, offsets, n, alphabet, d->ss.shift, flags, d->ws);
-  if (st == NW_OK) {
-    // score bounds over the length pairs present
-    int lo = INT32_MAX, hi = INT32_MIN;
-    for (int La = 0; La < kBuckets; ++La) {
-      for (int Lb = La; Lb < kBuckets; ++Lb) {
-        const uint32_t na = d->ws.bk.count[La], nb = d->ws.bk.count[Lb];
-        if (!na || !nb || (La == Lb && na < 2)) continue;
-        int l, h;
-        pair_bounds(*scoring, La, Lb, l, h);
-        lo = std::min(lo, l);
-        hi = std::max(hi, h);
-      }
-    }
-    if (lo > hi) lo = hi = 0;  // fewer than two words
-    d->score_lo = lo;
-    d->score_hi = hi;
-    plan_all_pairs(d->ws.bk, kDefaultTA, d->plan);
-    st = ctx_alloc(c, d->d_segs, sizeof(Seg) * std::max<size_t>(1, d->plan.segs.size()), "segment plan");
-    if (st == NW_OK && !d->plan.segs.empty()) {
-      cudaError_t e = cudaMemcpyAsync(d->d_segs.p, d->plan.segs.data(), sizeof(Seg) * d->plan.segs.size(),
-                                      cudaMemcpyHostToDevice, c->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-      if (e != cudaSuccess) st = cuda_fail(c, e, "uploading the segment plan");
-    }
-  }
-  if (st != NW_OK) {
-    free_wordset(c, d->ws);
-    ctx_free(c, d->d_segs);
-    delete d;
-    return st;
-  }
-  c->dicts.insert(d);
-  *out = d;
-  return NW_OK;
+  ShiftedScoring ss{};
+  NW_TRY(make_shifted(c, *scoring, alphabet, ss));
+  return load_impl(c, codes, offsets, n, alphabet, *scoring, ss, nullptr, flags, out);
 }
+
+nw_status nw_load_dictionary_sim(nw_ctx* c, const uint8_t* codes, const uint32_t* offsets, uint32_t n,
+                                 uint32_t alphabet, const int32_t* sim, int32_t gap, uint32_t flags, nw_dict** out) {
+  NW_ENTER(c);
+  if (!out || !offsets || !sim || (!codes && n)) return set_err(c, NW_EINVAL, "null pointer argument");
+  *out = nullptr;
+  if (alphabet == 0 || alphabet > (uint32_t)kTabDim)
+    return set_err(c, NW_EINVAL, "a similarity-matrix dictionary needs alphabet in [1, %d]", kTabDim);
+  if (std::abs(gap) > 1024) return set_err(c, NW_EINVAL, "gap must lie in [-1024, 1024]");
+  int smax = INT32_MIN, smin = INT32_MAX;
+  std::vector<uint16_t> tab((size_t)kTabDim * kTabDim, 0);
+  for (uint32_t a = 0; a < alphabet; ++a) {
+    for (uint32_t b = 0; b < alphabet; ++b) {
+      const int32_t v = sim[a * alphabet + b];
+      if (std::abs(v) > 1024) return set_err(c, NW_EINVAL, "similarity values must lie in [-1024, 1024]");
+      if (v != sim[b * alphabet + a]) return set_err(c, NW_EINVAL, "the similarity matrix must be symmetric");
+      smax = std::max(smax, v);
+      smin = std::min(smin, v);
+      const int32_t sp = std::max(v - 2 * gap, 0);
+      if ((int64_t)sp * kMaxLen > 32767)
+        return set_err(c, NW_ERANGE, "sim - 2*gap = %d is too large for 16-bit cells at length %d", sp, kMaxLen);
+      tab[(size_t)a * kTabDim + b] = (uint16_t)sp;
+    }
+  }
+  // the bounds of a match / mismatch scoring with match = max sim and mismatch
+  // = min sim hold for the matrix (the same two alignments bound the optimum)
+  const nw_scoring bounds{smax, smin, gap};
+  ShiftedScoring ss{};  // codes stay unshifted: the kernels look them up in the table
+  return load_impl(c, codes, offsets, n, alphabet, bounds, ss, &tab, flags, out);
+}
+
+
 
 nw_status nw_dict_info_get(const nw_dict* d, nw_dict_info* out) {
   if (!d || !out) return NW_EINVAL;
@@ -156,6 +215,7 @@ void nw_dict_free(nw_dict* d) {
   cudaStreamSynchronize(c->stream);
   free_wordset(c, d->ws);
   ctx_free(c, d->d_segs);
+  ctx_free(c, d->d_tab);
   c->dicts.erase(d);
   delete d;
 }
@@ -203,6 +263,7 @@ nw_status matrix_impl(nw_dict* d, int8_t* out, uint64_t chunk_bytes, uint32_t fl
     base.match = d->sc.match;
     base.mismatch = d->sc.mismatch;
     base.gap = d->sc.gap;
+    base.sim_tab = dict_tab(d);
     base.mode = kModeMatrix;
     base.mat = dst - lo;  // entry `off` of the chunk [lo, hi) lands at dst[off - lo]
     base.n = n;
@@ -341,6 +402,7 @@ nw_status nw_score_pairs(nw_dict* d, const uint32_t* i, const uint32_t* j, size_
   P.C1 = d->ss.C1;
   P.C2 = d->ss.C2;
   P.gap = d->sc.gap;
+  P.tab = dict_tab(d);
   P.out = dout;
   P.err = c->ws_small.as<uint32_t>();
   Timer tm{c};
@@ -429,6 +491,7 @@ nw_status nw_query(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, 
   base.match = d->sc.match;
   base.mismatch = d->sc.mismatch;
   base.gap = d->sc.gap;
+  base.sim_tab = dict_tab(d);
   base.mode = kModeLists;
   base.k = k;
   base.ib = ib;
@@ -610,6 +673,7 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
     return set_err(c, NW_EINVAL, "the no-allocation variant needs device output buffers (NW_DEVICE_PTRS)");
   if (flags & NW_RANK_NORMALISED)
     return set_err(c, NW_EINVAL, "the no-allocation variant ranks by raw score only");
+  if (d->subst) return set_err(c, NW_EINVAL, "the no-allocation variant takes match / mismatch dictionaries only");
   const uint32_t n = d->ws.n;
   if (n < 2) return set_err(c, NW_EINVAL, "the dictionary needs at least 2 words (has %u)", n);
   if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);

@@ -27,6 +27,11 @@
 // packed add never carries between halves (G + f <= s'_m * LB < 2^15).
 // Per two cells: one LOP3, one add and two DPX instructions; rows go two at
 // a time so the two rows' dependency chains interleave.
+//
+// Substitution-matrix scoring (TAB): the lane holds its B words' codes
+// (lo / hi halves) and the per-cell term is read from the table row of the A
+// symbol, f = s'+(a, b_lo) | s'+(a, b_hi) << 16 with s'+ = max(s', 0) (the
+// same argument as above makes the clamp exact and keeps the add carry-free).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,15 +46,34 @@ struct BRow {
   uint32_t v[LB > 0 ? LB : 1];
 };
 
+// the packed per-cell term of symbol pair column j
+template <int LB, bool TAB>
+__device__ __forceinline__ uint32_t cell_term(uint32_t a2, const BRow<LB>& b, int j, uint32_t C1, uint32_t C2,
+                                              const uint16_t* trow) {
+  if constexpr (TAB) {
+    const uint32_t bv = b.v[j];
+    return (uint32_t)trow[bv & 0xffffu] | ((uint32_t)trow[bv >> 16] << 16);
+  } else {
+    return __viaddmax_s16x2(a2 ^ b.v[j], C1, C2);
+  }
+}
+
+// the table row of A symbol a2 (codes stored unshifted in TAB dictionaries)
+template <bool TAB>
+__device__ __forceinline__ const uint16_t* tab_row(const uint16_t* tab, uint32_t a2) {
+  if constexpr (TAB) return tab + ((a2 & 0xffffu) * (uint32_t)kTabDim);
+  return nullptr;
+}
+
 // One row of the shifted recurrence: G[1..LB] of row i-1 becomes row i.
-template <int LB>
+template <int LB, bool TAB = false>
 __device__ __forceinline__ void dp_row(uint32_t (&G)[LB], uint32_t a2, const BRow<LB>& b, uint32_t C1,
-                                       uint32_t C2) {
+                                       uint32_t C2, const uint16_t* tab = nullptr) {
+  const uint16_t* trow = tab_row<TAB>(tab, a2);
   uint32_t diag = 0u, left = 0u;
 #pragma unroll
   for (int j = 0; j < LB; ++j) {
-    const uint32_t xt = a2 ^ b.v[j];
-    const uint32_t f = __viaddmax_s16x2(xt, C1, C2);
+    const uint32_t f = cell_term<LB, TAB>(a2, b, j, C1, C2, trow);
     const uint32_t up = G[j];
     const uint32_t h = __vimax3_s16x2(diag + f, up, left);
     diag = up;
@@ -60,13 +84,14 @@ __device__ __forceinline__ void dp_row(uint32_t (&G)[LB], uint32_t a2, const BRo
 
 // The first row (i = 1): diag and up are G[0][*] = 0 and f, left >= 0, so
 // the cell is max(f, left) and no row of zeros needs setting up.
-template <int LB>
+template <int LB, bool TAB = false>
 __device__ __forceinline__ void dp_row_first(uint32_t (&G)[LB], uint32_t a2, const BRow<LB>& b, uint32_t C1,
-                                             uint32_t C2) {
+                                             uint32_t C2, const uint16_t* tab = nullptr) {
+  const uint16_t* trow = tab_row<TAB>(tab, a2);
   uint32_t left = 0u;
 #pragma unroll
   for (int j = 0; j < LB; ++j) {
-    const uint32_t f = __viaddmax_s16x2(a2 ^ b.v[j], C1, C2);
+    const uint32_t f = cell_term<LB, TAB>(a2, b, j, C1, C2, trow);
     left = __vimax_s16x2_relu(f, left);
     G[j] = left;
   }
@@ -74,9 +99,10 @@ __device__ __forceinline__ void dp_row_first(uint32_t (&G)[LB], uint32_t a2, con
 
 // DP over the la rows of one A word against the lane's two B words; returns
 // the packed G[la][LB] (0 when la == 0 or LB == 0).
-template <int LB>
+template <int LB, bool TAB = false>
 __device__ __forceinline__ uint32_t dp_word(const uint32_t* __restrict__ arow, int la,
-                                            const BRow<LB>& b, uint32_t C1, uint32_t C2) {
+                                            const BRow<LB>& b, uint32_t C1, uint32_t C2,
+                                            const uint16_t* tab = nullptr) {
   if constexpr (LB == 0) {
     return 0u;
   } else {
@@ -88,10 +114,10 @@ __device__ __forceinline__ uint32_t dp_word(const uint32_t* __restrict__ arow, i
     for (; i + 1 < la; i += 2) {
       const uint32_t a0 = __ldg(arow + i);
       const uint32_t a1 = __ldg(arow + i + 1);
-      dp_row<LB>(G, a0, b, C1, C2);
-      dp_row<LB>(G, a1, b, C1, C2);
+      dp_row<LB, TAB>(G, a0, b, C1, C2, tab);
+      dp_row<LB, TAB>(G, a1, b, C1, C2, tab);
     }
-    if (i < la) dp_row<LB>(G, __ldg(arow + i), b, C1, C2);
+    if (i < la) dp_row<LB, TAB>(G, __ldg(arow + i), b, C1, C2, tab);
     return G[LB - 1];
   }
 }
@@ -99,24 +125,24 @@ __device__ __forceinline__ uint32_t dp_word(const uint32_t* __restrict__ arow, i
 // The same DP with the A word's symbols in shared memory, symbol i at
 // acol[32 * i] (the staging layout of the all-pairs kernel; every lane reads
 // the same address, so each load is a broadcast).
-template <int LB>
+template <int LB, bool TAB = false>
 __device__ __forceinline__ uint32_t dp_word_staged(const uint32_t* acol, int la, const BRow<LB>& b, uint32_t C1,
-                                                   uint32_t C2) {
+                                                   uint32_t C2, const uint16_t* tab = nullptr) {
   if constexpr (LB == 0) {
     return 0u;
   } else {
     if (la == 0) return 0u;
     uint32_t G[LB];
-    dp_row_first<LB>(G, acol[0], b, C1, C2);
+    dp_row_first<LB, TAB>(G, acol[0], b, C1, C2, tab);
     int i = 1;
 #pragma unroll 1
     for (; i + 1 < la; i += 2) {
       const uint32_t a0 = acol[32 * i];
       const uint32_t a1 = acol[32 * (i + 1)];
-      dp_row<LB>(G, a0, b, C1, C2);
-      dp_row<LB>(G, a1, b, C1, C2);
+      dp_row<LB, TAB>(G, a0, b, C1, C2, tab);
+      dp_row<LB, TAB>(G, a1, b, C1, C2, tab);
     }
-    if (i < la) dp_row<LB>(G, acol[32 * i], b, C1, C2);
+    if (i < la) dp_row<LB, TAB>(G, acol[32 * i], b, C1, C2, tab);
     return G[LB - 1];
   }
 }
@@ -253,12 +279,14 @@ __device__ __forceinline__ int g_bound(const DpParams& P, const TaskTerms& T, ui
   return (int)(thr_key >> T.ib) + T.key_lo - pconst;
 }
 
-// The all-pairs kernel.  EPI selects the per-pair epilogue at compile time:
+// The all-pairs kernel.  TAB selects substitution-matrix scoring (the table
+// is copied to shared memory after the staging area).  EPI selects the
+// per-pair epilogue at compile time:
 // kEpiMatrix writes the int8 upper triangle, kEpiLists updates neighbour lists
 // (and a shared or global histogram), kEpiListsLaneHist updates lists and the
 // per-lane shared histogram columns, kEpiBatchLists updates lists of the
 // segment's dictionary in a launch spanning many dictionaries.
-template <int LB, int EPI>
+template <int LB, int EPI, bool TAB = false>
 __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const DpParams P) {
   extern __shared__ uint32_t s_dyn[];
   const int lane = threadIdx.x & 31;
@@ -271,6 +299,15 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
   // followed by the 32 words' list bounds (raw keys) at sT[w]
   uint32_t* sA = s_dyn + (size_t)kWarpsPerBlock * wstride + (size_t)wib * 32u * (uint32_t)(LB + 1);
   uint32_t* sT = sA + 32u * (uint32_t)LB;
+  uint16_t* sTab = nullptr;
+  if constexpr (TAB) {
+    sTab = reinterpret_cast<uint16_t*>(s_dyn + (size_t)kWarpsPerBlock * wstride +
+                                       (size_t)kWarpsPerBlock * 32u * (uint32_t)(LB + 1));
+    const uint4* src = reinterpret_cast<const uint4*>(P.sim_tab);
+    uint4* dst = reinterpret_cast<uint4*>(sTab);
+    for (int q = threadIdx.x; q < (int)(kTabBytes / sizeof(uint4)); q += blockDim.x) dst[q] = __ldg(src + q);
+    __syncthreads();
+  }
   if (smem_hist) {
     for (uint32_t q = lane; q < wstride; q += 32) wh[q] = 0u;
     __syncwarp();
@@ -323,6 +360,13 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
 #pragma unroll
       for (int j = 0; j < LB; ++j) brow.v[j] = 0xffffffffu;
       if (vlo) load_brow<LB>(T.b_rec + S.brec_base + (size_t)(g.cb * (kWarpB / 2) + lane) * (ceil4(LB) / 4), brow);
+      if constexpr (TAB) {
+        // records hold ~code per half (unshifted codes): back to codes, and
+        // code 0 for halves without a word (their results are discarded)
+        const uint32_t keep = (vlo ? 0x0000ffffu : 0u) | (vhi ? 0xffff0000u : 0u);
+#pragma unroll
+        for (int j = 0; j < LB; ++j) brow.v[j] = ~brow.v[j] & keep;
+      }
     }
     const uint32_t ob_lo = vlo ? __ldg(T.B.perm + blo) : 0u;
     const uint32_t ob_hi = vhi ? __ldg(T.B.perm + bhi) : 0u;
@@ -354,7 +398,7 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
 
       for (uint32_t w = 0; w < nA; ++w) {
         const uint32_t a = c0 + w;
-        const uint32_t res = dp_word_staged<LB>(sA + w, la, brow, T.C1, T.C2);
+        const uint32_t res = dp_word_staged<LB, TAB>(sA + w, la, brow, T.C1, T.C2, sTab);
         const int g_lo = (int)(res & 0xffffu);  // G >= 0
         const int g_hi = (int)(res >> 16);
         bool ok_lo = vlo, ok_hi = vhi;

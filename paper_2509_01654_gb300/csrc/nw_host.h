@@ -89,6 +89,8 @@ struct nw_dict {
   int32_t score_lo = 0, score_hi = 0;
   Plan plan;
   DevBuf d_segs;
+  bool subst = false;  // scored with a full similarity matrix (d_tab)
+  DevBuf d_tab;        // kTabDim x kTabDim s'+ table
 };
 
 namespace {
@@ -203,6 +205,8 @@ nw_status make_shifted(nw_ctx* c, const nw_scoring& s, uint32_t alphabet, Shifte
   out.C2 = pack16(std::max(sx, 0));  // a negative mismatch term never wins (see nw_dp.cuh)
   return NW_OK;
 }
+
+const uint16_t* dict_tab(const nw_dict* d) { return d->subst ? d->d_tab.as<uint16_t>() : nullptr; }
 
 void pair_bounds(const nw_scoring& s, int la, int lb, int& lo, int& hi) {
   const int mn = std::min(la, lb), d = std::abs(la - lb);
@@ -608,11 +612,12 @@ nw_status run_plan(nw_ctx* c, cudaStream_t stream, const Plan& plan, const Seg* 
     P.A = *A_by_role[lp.role];
     P.b_rec = b_rec_by_role[lp.role];
     P.B = *B_by_role[lp.role];
-    const size_t smem = hist_smem_bytes(P.hist_mode, P.nbins) + dp_stage_bytes(lp.LB);
+    const bool tab = P.sim_tab != nullptr;
+    const size_t smem = hist_smem_bytes(P.hist_mode, P.nbins) + dp_stage_bytes(lp.LB) + (tab ? kTabBytes : 0);
     const int epi = P.terms ? kEpiBatchLists
                             : (P.mode == kModeMatrix ? kEpiMatrix
                                                      : (P.hist_mode == kHistLane ? kEpiListsLaneHist : kEpiLists));
-    const void* fn = dp_kernel(lp.LB, epi);
+    const void* fn = dp_kernel(lp.LB, epi, tab);
     if (!fn) return set_err(c, NW_EINVAL, "no kernel for length %d", lp.LB);
     NW_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
@@ -706,6 +711,7 @@ nw_status topk_impl(nw_dict* d, uint32_t shard, uint32_t nshards, uint32_t k, ui
   base.match = d->sc.match;
   base.mismatch = d->sc.mismatch;
   base.gap = d->sc.gap;
+  base.sim_tab = dict_tab(d);
   base.mode = kModeLists;
   base.k = k;
   base.ib = ib;

@@ -187,7 +187,17 @@ struct DpParams {
   const uint16_t* norm_rank;
   const int16_t* norm_smin;
   int32_t norm_lo;
+  // substitution-matrix scoring (null = match / mismatch): kTabDim x kTabDim
+  // table of s'+(a, b) = max(sim(a, b) - 2p, 0), copied to shared memory
+  const uint16_t* sim_tab;
 };
+
+// The substitution table of a dictionary scored with a full similarity
+// matrix: row a holds s'+(a, b) for b < kTabDim (zero past the alphabet).  A
+// row of 64 16-bit entries covers the 32 shared-memory banks once, so the 32
+// lanes' lookups into one row never conflict.
+constexpr int kTabDim = 64;
+constexpr size_t kTabBytes = (size_t)kTabDim * kTabDim * sizeof(uint16_t);
 
 // Scoring constants of the shifted recurrence (see the kernel).
 struct ShiftedScoring {

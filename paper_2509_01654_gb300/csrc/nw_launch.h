@@ -8,8 +8,9 @@
 
 namespace nw {
 
-// alignment kernel for the longer length LB (0 .. kMaxLen) and epilogue kind; nullptr if out of range
-const void* dp_kernel(int LB, int epi);
+// alignment kernel for the longer length LB (0 .. kMaxLen), epilogue kind and
+// scoring (tab: substitution table); nullptr if there is none
+const void* dp_kernel(int LB, int epi, bool tab = false);
 
 // ingest: stable bucketing by length and encoding of a word set
 cudaError_t launch_ingest_count(const uint8_t* codes, const uint32_t* offsets, uint32_t n,
@@ -51,6 +52,7 @@ struct PairsParams {
   int32_t gap;
   int16_t* out;
   uint32_t* err;
+  const uint16_t* tab;  // substitution table (device, kTabDim x kTabDim) or null
 };
 cudaError_t launch_pairs(const PairsParams& p, cudaStream_t s);
 

@@ -12,7 +12,7 @@
 
 namespace nw {
 
-template <int LB>
+template <int LB, bool TAB>
 __device__ __forceinline__ int pair_score(const PairsParams& P, uint32_t pa, int la, uint32_t pb) {
   BRow<LB> b;
   if constexpr (LB > 0) {
@@ -21,18 +21,20 @@ __device__ __forceinline__ int pair_score(const PairsParams& P, uint32_t pa, int
     const uint32_t* rec = P.b_rec + (w & ~3u);
 #pragma unroll
     for (int j = 0; j < LB; ++j) {
-      const uint32_t v = (__ldg(rec + j) >> sh) & 0xffffu;
+      uint32_t v = (__ldg(rec + j) >> sh) & 0xffffu;
+      if constexpr (TAB) v = ~v & 0xffffu;  // the code itself (unshifted)
       b.v[j] = v | (v << 16);
     }
   }
   const uint32_t* arow = P.a_enc + __ldg(P.aoff + pa);
-  const uint32_t res = dp_word<LB>(arow, la, b, P.C1, P.C2);
+  const uint32_t res = dp_word<LB, TAB>(arow, la, b, P.C1, P.C2, P.tab);
   return (int)(int16_t)(res & 0xffffu) + P.gap * (la + LB);
 }
 
-__device__ int pair_dispatch(int LB, const PairsParams& P, uint32_t pa, int la, uint32_t pb) {
+template <bool TAB>
+__device__ int pair_dispatch_t(int LB, const PairsParams& P, uint32_t pa, int la, uint32_t pb) {
   switch (LB) {
-#define NW_CASE(L) case L: return pair_score<L>(P, pa, la, pb);
+#define NW_CASE(L) case L: return pair_score<L, TAB>(P, pa, la, pb);
     NW_CASE(0) NW_CASE(1) NW_CASE(2) NW_CASE(3) NW_CASE(4) NW_CASE(5) NW_CASE(6) NW_CASE(7)
     NW_CASE(8) NW_CASE(9) NW_CASE(10) NW_CASE(11) NW_CASE(12) NW_CASE(13) NW_CASE(14)
     NW_CASE(15) NW_CASE(16) NW_CASE(17) NW_CASE(18) NW_CASE(19) NW_CASE(20) NW_CASE(21)
@@ -44,6 +46,10 @@ __device__ int pair_dispatch(int LB, const PairsParams& P, uint32_t pa, int la, 
   }
 }
 static_assert(kMaxLen == 40, "pair_dispatch lists every length up to kMaxLen");
+
+__device__ int pair_dispatch(int LB, const PairsParams& P, uint32_t pa, int la, uint32_t pb) {
+  return P.tab ? pair_dispatch_t<true>(LB, P, pa, la, pb) : pair_dispatch_t<false>(LB, P, pa, la, pb);
+}
 
 __global__ void __launch_bounds__(128) pairs_kernel(const PairsParams P) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;

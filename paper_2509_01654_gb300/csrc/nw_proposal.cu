@@ -275,6 +275,7 @@ PairsParams pairs_params(const nw_dict* d, uint32_t* err) {
   P.C1 = d->ss.C1;
   P.C2 = d->ss.C2;
   P.gap = d->sc.gap;
+  P.tab = dict_tab(d);
   P.err = err;
   return P;
 }

@@ -336,6 +336,7 @@ nw_status nw_server_create(nw_dict* dict, const nw_server_config* cfg, nw_server
   if (!out) return NW_EINVAL;
   *out = nullptr;
   if (!dict || !cfg) return set_err(nullptr, NW_EINVAL, "null argument");
+  if (dict->subst) return set_err(nullptr, NW_EINVAL, "the server takes match / mismatch dictionaries only");
   if (cfg->k == 0 || cfg->k > NW_MAX_K) return set_err(nullptr, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
   if (cfg->max_batch_queries == 0 || cfg->max_batch_queries > (1u << 20))
     return set_err(nullptr, NW_EINVAL, "max_batch_queries must be in [1, 2^20]");

@@ -34,7 +34,7 @@ EXPORTED = [
     "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc", "nw_all_pairs_topk_noalloc",
     "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
     "nw_batch_create", "nw_batch_run", "nw_batch_info_get", "nw_batch_free", "nw_all_pairs_matrix_chunked",
-    "nw_debug_norm_tables",
+    "nw_debug_norm_tables", "nw_load_dictionary_sim",
     # nw_proposal.h
     "nw_model_create", "nw_model_free", "nw_model_param_count", "nw_model_get_params", "nw_model_set_params",
     "nw_model_embed", "nw_model_loss_grad", "nw_model_train", "nw_quantize_embeddings", "nw_dot_topk",
@@ -131,6 +131,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_last_profile.argtypes = [vp, ctypes.POINTER(Profile)]
     L.nw_load_dictionary.argtypes = [vp, vp, vp, u32, u32, ctypes.POINTER(Scoring), u32, ctypes.POINTER(vp)]
     L.nw_dict_info_get.argtypes = [vp, ctypes.POINTER(DictInfo)]
+    L.nw_load_dictionary_sim.argtypes = [vp, vp, vp, u32, u32, vp, i32, u32, ctypes.POINTER(vp)]
     L.nw_dict_free.argtypes = [vp]
     L.nw_dict_free.restype = None
     L.nw_all_pairs_matrix.argtypes = [vp, vp, u32]
@@ -274,24 +275,37 @@ class Context:
     def load_dictionary(self, codes, offsets, alphabet: int, scoring) -> "Dictionary":
         return Dictionary(self, codes, offsets, alphabet, scoring)
 
+    def load_dictionary_sim(self, codes, offsets, alphabet: int, sim, gap: int) -> "Dictionary":
+        """A dictionary scored with a full similarity matrix (nw_load_dictionary_sim)."""
+        return Dictionary(self, codes, offsets, alphabet, sim=sim, gap=gap)
+
 
 class Dictionary:
     """nw_load_dictionary / nw_dict_free and the calls on a dictionary."""
 
-    def __init__(self, ctx: Context, codes, offsets, alphabet: int, scoring):
+    def __init__(self, ctx: Context, codes, offsets, alphabet: int, scoring=None, sim=None, gap=None):
+        """scoring = (match, mismatch, gap), or sim (alphabet x alphabet matrix) and gap."""
         L = load_library()
         self.ctx = ctx
-        self.scoring = tuple(int(v) for v in scoring)
         if not _is_torch(codes):
             codes = np.ascontiguousarray(codes, dtype=np.uint8)
             if codes.size == 0:
                 codes = np.zeros(1, np.uint8)
             offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
         n = (offsets.shape[0] if hasattr(offsets, "shape") else len(offsets)) - 1
-        sc = Scoring(*self.scoring)
         h = ctypes.c_void_p()
-        st = L.nw_load_dictionary(ctx.handle, _ptr(codes)[0], _ptr(offsets)[0], n, alphabet, ctypes.byref(sc),
-                                  _flags(codes, offsets), ctypes.byref(h))
+        if sim is not None:
+            self.scoring = None
+            self.sim = np.ascontiguousarray(sim, dtype=np.int32)
+            self.gap = int(gap)
+            st = L.nw_load_dictionary_sim(ctx.handle, _ptr(codes)[0], _ptr(offsets)[0], n, alphabet,
+                                          ctypes.c_void_p(self.sim.ctypes.data), self.gap, _flags(codes, offsets),
+                                          ctypes.byref(h))
+        else:
+            self.scoring = tuple(int(v) for v in scoring)
+            sc = Scoring(*self.scoring)
+            st = L.nw_load_dictionary(ctx.handle, _ptr(codes)[0], _ptr(offsets)[0], n, alphabet, ctypes.byref(sc),
+                                      _flags(codes, offsets), ctypes.byref(h))
         _check(ctx.handle, st)
         self.handle = h
         self.n = n

@@ -4,7 +4,11 @@
   the neighbour lists, against the oracle's exact-fraction ranking;
 * the int8 matrix produced in host-copied chunks (Section 5's proposal for
   dictionaries whose matrix exceeds device memory), against the oracle's
-  matrix and the one-shot device matrix."""
+  matrix and the one-shot device matrix;
+* dictionaries scored with a full similarity matrix (Algorithm 1's
+  similarity step from a table): lists, histogram, matrix, pairs, queries and
+  the normalised ranking against the oracle's matrix variants, the
+  match/mismatch matrix against the scalar oracle, and the refusals."""
 import numpy as np
 import pytest
 
@@ -133,3 +137,106 @@ def test_matrix_chunked_refuses_device_output(ctx):
     L = nw.load_library()
     assert L.nw_all_pairs_matrix_chunked(d.handle, out.data_ptr(), 1000, nw.NW_DEVICE_PTRS) == nw.NW_EINVAL
     assert L.nw_all_pairs_matrix_chunked(d.handle, out.data_ptr(), 0, nw.NW_DEVICE_PTRS) == nw.NW_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# full similarity matrix (nw_load_dictionary_sim)
+
+def sym_matrix(alphabet, lo, hi, seed):
+    g = np.random.default_rng(seed)
+    S = g.integers(lo, hi + 1, (alphabet, alphabet))
+    S = np.triu(S) + np.triu(S, 1).T
+    return S.astype(np.int32)
+
+
+@pytest.mark.parametrize("alphabet,lo,hi,gap,lens", [(20, -3, 4, -2, (0, 16)), (7, -2, 2, -1, (0, 9)),
+                                                     (64, -5, 9, -3, (1, 12)), (12, 0, 3, -1, (25, 40))])
+def test_sim_topk_histogram_matrix_pairs(ctx, oracle_mod, alphabet, lo, hi, gap, lens):
+    S = sym_matrix(alphabet, lo, hi, seed=alphabet)
+    np.fill_diagonal(S, hi + 2)  # identical symbols score highest, as in a phoneme similarity
+    w = synth.make_uniform_length_words(700, alphabet, 1.0, lens[0], lens[1], seed=alphabet + 1)
+    d = ctx.load_dictionary_sim(w.codes, w.offsets, alphabet, S, gap)
+    idx, score, h, hlo = d.all_pairs_topk(10)
+    oi, os_ = oracle_mod.topk_rows_sim(w, np.arange(w.n), 10, S, gap)
+    os_ = np.where(os_ == oracle_mod.MISSING_SCORE, nw.MISSING_SCORE, os_).astype(np.int16)
+    assert np.array_equal(score, os_) and np.array_equal(idx, oi)
+    assert np.array_equal(h, oracle_mod.histogram_sim(w, S, gap, hlo, h.size))
+    info = d.info()
+    if info["score_lo"] >= -128 and info["score_hi"] <= 127:
+        assert np.array_equal(d.all_pairs_matrix().astype(np.int32), oracle_mod.all_pairs_sim(w, S, gap))
+    g = np.random.default_rng(5)
+    I, J = g.integers(0, w.n, 3000), g.integers(0, w.n, 3000)
+    assert np.array_equal(d.score_pairs(I, J).astype(np.int32), oracle_mod.score_pairs_sim(w, I, J, S, gap))
+
+
+def test_sim_match_mismatch_matrix_equals_scalar_scoring(ctx, oracle_mod):
+    w = synth.make_words(1500, 40, 1.1, 8.0, 3.0, 1, 25, seed=2)
+    S = oracle_mod.match_mismatch_matrix(40, 1, -1)
+    d = ctx.load_dictionary_sim(w.codes, w.offsets, 40, S, -1)
+    idx, score, h, hlo = d.all_pairs_topk(10)
+    oi, os_ = oracle_mod.topk_rows(w, np.arange(w.n), 10, (1, -1, -1))
+    assert np.array_equal(score, os_.astype(np.int16)) and np.array_equal(idx, oi)
+    assert np.array_equal(h, oracle_mod.histogram(w, (1, -1, -1), hlo, h.size))
+
+
+def test_sim_query_and_normalised(ctx, oracle_mod):
+    alphabet, gap = 30, -2
+    S = sym_matrix(alphabet, -2, 3, seed=7)
+    np.fill_diagonal(S, 5)
+    w = synth.make_uniform_length_words(900, alphabet, 1.0, 1, 14, seed=8)
+    q = synth.make_uniform_length_words(40, alphabet, 1.0, 0, 14, seed=9)
+    d = ctx.load_dictionary_sim(w.codes, w.offsets, alphabet, S, gap)
+    qi, qs = d.query(q.codes, q.offsets, 10)
+    for a in range(q.n):
+        row = np.array([oracle_mod.score_sim(q.word(a), w.word(j), S, gap) for j in range(w.n)])
+        order = np.lexsort((np.arange(w.n), -row))[:10]
+        assert np.array_equal(qi[a], order) and np.array_equal(qs[a].astype(np.int64), row[order])
+    # the normalised ranking over matrix scores: lists ordered by s / max(len), ties by index
+    ni, ns, _, _ = d.all_pairs_topk(10, hist=None, normalised=True)
+    lens = w.lengths
+    M = np.zeros((w.n, w.n), dtype=np.int64)
+    iu = np.triu_indices(w.n, 1)
+    M[iu] = oracle_mod.all_pairs_sim(w, S, gap)
+    M = M + M.T
+    from fractions import Fraction
+    for i in range(0, w.n, 61):
+        cand = [j for j in range(w.n) if j != i]
+        best = sorted(cand, key=lambda j: (-Fraction(int(M[i, j]), max(lens[i], lens[j], 1)), j))[:10]
+        assert ni[i].tolist() == best and ns[i].tolist() == [int(M[i, j]) for j in best]
+
+
+def test_sim_dictionary_refusals(ctx):
+    w = synth.make_uniform_length_words(50, 10, 1.0, 1, 8, seed=3)
+    S = sym_matrix(10, -2, 3, seed=1)
+    bad = S.copy()
+    bad[0, 1] += 1  # not symmetric
+    for args in [(w.codes, w.offsets, 10, bad, -1), (w.codes, w.offsets, 65, np.zeros((65, 65), np.int32), -1),
+                 (w.codes, w.offsets, 10, S * 400, -1)]:
+        with pytest.raises(nw.NwError) as e:
+            ctx.load_dictionary_sim(*args)
+        assert e.value.status in (nw.NW_EINVAL, nw.NW_ERANGE)
+    d = ctx.load_dictionary_sim(w.codes, w.offsets, 10, S, -1)
+    with pytest.raises(nw.NwError) as e:
+        nw.Server(d, k=5, max_batch_queries=64, max_inflight=1)
+    assert e.value.status == nw.NW_EINVAL
+    import torch
+    ti = torch.empty((w.n, 5), dtype=torch.int32, device="cuda")
+    ts = torch.empty((w.n, 5), dtype=torch.int16, device="cuda")
+    with pytest.raises(nw.NwError) as e:
+        d.all_pairs_topk_noalloc(5, ti, ts)
+    assert e.value.status == nw.NW_EINVAL
+
+
+def test_sim_large_sampled_rows(ctx, oracle_mod):
+    # 60,000 words of the exhaustive mix under a phoneme-like matrix: near
+    # codes (adjacent in the code order) are similar
+    alphabet = 40
+    a = np.arange(alphabet)
+    S = np.where(a[:, None] == a[None, :], 3, np.where(np.abs(a[:, None] - a[None, :]) <= 2, 1, -2)).astype(np.int32)
+    w = synth.exhaustive_words(60_000)
+    d = ctx.load_dictionary_sim(w.codes, w.offsets, alphabet, S, -2)
+    idx, score, h, hlo = d.all_pairs_topk(10)
+    assert h.sum() == w.n * (w.n - 1) // 2
+    rows = synth.sample_rows(w.n, 200)
+    oi, os_ = oracle_mod.topk_rows_sim(w, rows, 10, S, -2)
+    assert np.array_equal(score[rows], os_.astype(np.int16)) and np.array_equal(idx[rows], oi)
