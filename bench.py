@@ -321,6 +321,11 @@ def run_ours(args, rank, world, local_rank):
         }
         batch.free()
 
+    # method variants on the same 600k words: a full similarity matrix and the normalised ranking
+    variants_stats = None
+    if args.variants and rank == 0:
+        variants_stats = variants_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, hist_d, info, flush)
+
     # the learned candidate proposal against the exhaustive lists of the timed leg
     proposal_stats = None
     if args.proposal_steps > 0 and rank == 0:
@@ -357,9 +362,61 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "serving": serving_stats,
         "batched": batched_stats,
+        "variants": variants_stats,
         "proposal": proposal_stats,
     }
     print(json.dumps(line), flush=True)
+
+
+def phoneme_like_matrix(alphabet):
+    """A similarity table of the shape Section 6 suggests: 3 for equal codes,
+    1 for codes within 2 of each other (similar sounds), -2 otherwise."""
+    import numpy as np
+    a = np.arange(alphabet)
+    d = np.abs(a[:, None] - a[None, :])
+    return np.where(d == 0, 3, np.where(d <= 2, 1, -2)).astype(np.int32)
+
+
+def variants_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, hist_d, info, flush):
+    import torch
+    k = K_NEIGHBOURS
+    cells = info["cells"]
+
+    def timed(fn, reps):
+        fn()  # warm-up
+        ts = []
+        for _ in range(reps):
+            flush.fill_(len(ts))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    reps = max(2, args.steps)
+    out = {}
+    # own output buffers: the timed leg's lists stay the exhaustive reference of the proposal leg
+    idx_d, score_d, hist_d = torch.empty_like(idx_d), torch.empty_like(score_d), torch.empty_like(hist_d)
+    S = phoneme_like_matrix(40)
+    ds = ctx.load_dictionary_sim(codes_d, offs_d, 40, S, -2)
+    hist_s = torch.empty(ds.info()["nbins"], dtype=hist_d.dtype, device=hist_d.device)
+    ms = timed(lambda: ds.all_pairs_topk(k, nbr_idx=idx_d, nbr_score=score_d, hist=hist_s), reps)
+    out["substitution_matrix"] = {
+        "workload": f"{w.n:,} words, top-{k} + histogram, 40 x 40 similarity table (3 equal, 1 within 2 codes, "
+                    f"-2 otherwise), gap -2",
+        "ms_per_step": round(ms, 2), "gcups": round(cells / (ms / 1e3) / 1e9, 1),
+        "pairs_per_s": info["pairs"] / (ms / 1e3)}
+    ds.free()
+    d = ctx.load_dictionary(codes_d, offs_d, 40, SCORING)
+    ms = timed(lambda: d.all_pairs_topk(k, nbr_idx=idx_d, nbr_score=score_d, hist=None, normalised=True), reps)
+    out["normalised_ranking"] = {
+        "workload": f"{w.n:,} words, top-{k} by s / max(len), match 1, mismatch -1, gap -1",
+        "ms_per_step": round(ms, 2), "gcups": round(cells / (ms / 1e3) / 1e9, 1)}
+    d.free()
+    return out
 
 
 def recall_vs_exact(ex_i, ex_s, ap_i, ap_s):
@@ -451,6 +508,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrivals per second")
     ap.add_argument("--batched-dicts", type=int, default=64,
                     help="dictionaries of the batched-launch measurement (0 skips it)")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the substitution-matrix and normalised-ranking measurements")
     ap.add_argument("--proposal-steps", type=int, default=3000,
                     help="training steps of the learned-proposal measurement (0 skips it)")
     args = ap.parse_args()
