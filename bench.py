@@ -39,7 +39,11 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM traffic of the alignment kernel from the ncu capture summarised in
 # profiles/ (bytes per launch, averaged over the launches of one step), valid
 # only for the kernel source it was measured on.
-TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) of one step's alignment launches on the 600k
+# workload, from ncu dram__bytes_read.sum + dram__bytes_write.sum (one pass,
+# profiles/traffic_exhaustive_600k_words.md); valid while the kernel sources
+# hash to kernel_sha
+TRAFFIC = {"kernel_sha": "b50e01893571cc54", "bytes_per_step": 442.5e6}
 
 
 def kernel_sha() -> str:
@@ -278,7 +282,7 @@ def run_ours(args, rank, world, local_rank):
     c_min = 3.0  # packed instructions per two cells in the fewest-instruction cell update
     peak = 2.0 * rates["viaddmax_s16x2"] / c_min / 1e9
     sha = kernel_sha()
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == sha else None
+    traffic = TRAFFIC["bytes_per_step"] if TRAFFIC["kernel_sha"] == sha and args.n == 600_000 else None
 
     # the serving form of the same dictionary: open-loop Poisson load on the query server
     serving_stats = None
@@ -347,6 +351,7 @@ def run_ours(args, rank, world, local_rank):
         "dp_kernel_ms_per_step": dp_avg_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
                      "frac": achieved / peak, "traffic": traffic,
+                     "traffic_basis": "DRAM bytes of one step's alignment launches (all 22), ncu, 600k words",
                      "peak_basis": f"2 cells x measured __viaddmax_s16x2 rate ({rates['viaddmax_s16x2']:.4g}/s, "
                                    f"{rates['sm_count']} SMs at {rates['sm_clock_mhz']:.0f} MHz) / {c_min:g} "
                                    f"packed instructions per cell pair; cell-mix microbenchmark "
