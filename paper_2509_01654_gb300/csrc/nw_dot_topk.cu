@@ -15,12 +15,16 @@
 // columns' biases.  Each row keeps an append buffer of kCap keys in global
 // memory and a threshold; a value enters when it beats the threshold (a row
 // group's maximum is tested first, so most tiles cost one compare per value
-// and no branch).  When a row holds more than 4C keys (or its buffer could
-// overflow during the next tile), its warp finds the row's C-th best key by
-// an 8-pass radix select (8 bits per pass), keeps the C keys at or above it
-// and raises the threshold to that key's value.  Later columns
-// have higher indices, so a later value equal to the threshold never
-// displaces a kept key: the comparison is strict and the lists are exact.
+// and no branch).  A row's values in a tile belong to the four lanes of one
+// quad, so its key count lives in their registers and appends take slots by
+// a prefix sum over the quad, with no atomics.  When a row holds more than
+// 2C keys (or its buffer could overflow during the next tile), its warp
+// raises the row's threshold to the lower edge t of the value-histogram bin
+// that holds the C-th best key and drops the keys below t (an exact 8-pass
+// radix select when that bin is crowded).  Later columns have higher
+// indices, so a later value equal to the C-th best never displaces a kept
+// key: the comparison is strict, and the final pass, an exact select and
+// sort of each row's buffer, gives exact lists.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <float.h>
@@ -44,21 +48,30 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kSel = NW_MAX_CANDIDATES;  // per-warp gather/sort area (keys)
 
 // dynamic shared memory layout (bytes)
-constexpr int kStages = 3;                              // B tiles in flight (one barrier per tile)
-constexpr int kSmemB = kStages * kTileCols * kRowBytes; // 24 KiB
-constexpr int kSmemBias = kStages * kTileCols * 4;      // their biases (float)
-constexpr int kSmemSort = kWarps * kSel * 8;            // 32 KiB (A staging at start)
-constexpr int kSmemHist = kWarps * 256 * 4;             // radix histograms
+constexpr int kStages = 6;                               // column tiles in flight
+constexpr int kTileBytes = kTileCols * kRowBytes;        // 8 KiB per tile
+constexpr int kTileBiasBytes = kTileCols * 4;            // its biases (float)
+constexpr int kSmemB = kStages * kTileBytes;
+constexpr int kSmemBias = kStages * kTileBiasBytes;
+constexpr int kSmemSort = kWarps * kSel * 8;             // 32 KiB (A staging at start)
+constexpr int kSmemHist = kWarps * 256 * 4;              // radix histograms
 constexpr int kSmemCnt = kRowsPerCta * 4;
 constexpr int kSmemThr = kRowsPerCta * 4;
+constexpr int kSmemBars = 2 * kStages * 8 + 16;          // full / empty mbarriers, next tile to issue
 constexpr int kOffBias = kSmemB;
 constexpr int kOffSort = kOffBias + kSmemBias;
 constexpr int kOffHist = kOffSort + kSmemSort;
 constexpr int kOffCnt = kOffHist + kSmemHist;
 constexpr int kOffThr = kOffCnt + kSmemCnt;
-constexpr int kSmemTotal = kOffThr + kSmemThr;
+constexpr int kOffBars = kOffThr + kSmemThr;
+constexpr int kSmemTotal = kOffBars + kSmemBars;
+static_assert(kSmemTotal <= 113 * 1024, "two CTAs per SM");
+// a pipeline wait gives up after this many SM clock cycles (about a second)
+constexpr long long kWaitCycles = 2000000000ll;
 static_assert(kRowsPerCta * kRowBytes <= kSmemSort, "A staging fits the sort area");
 static_assert(kCap - kTileCols > NW_MAX_CANDIDATES, "a compaction leaves room for a tile");
+static_assert(kTileCols == 64, "a row's own column is found by i >> 6");
+static_assert(kSel * 8 >= 32 * 32 * 4, "a warp's sort area stages 32 values per lane");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -73,6 +86,47 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// ---- mbarriers and bulk copies
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+// whether the barrier's phase of this parity has completed (never blocks)
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// waits for the phase of this parity to complete; false once kWaitCycles have passed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+// global -> shared, 16-byte aligned addresses, bytes a multiple of 16; counted on bar
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
@@ -126,6 +180,50 @@ __device__ void warp_bitonic_desc(uint64_t* s, int size, int lane) {
   }
 }
 
+// A warp's 256-bin histogram scanned from the top bin down: the bin in which
+// the running count reaches need (1 <= need <= total), and the count of the
+// bins above it.
+__device__ __forceinline__ void hist_find_desc(const unsigned* hist, unsigned need, int lane, int& bin,
+                                               unsigned& before) {
+  // lane l holds bins 255 - 8l .. 248 - 8l (descending order)
+  unsigned c[8], tot = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    c[q] = hist[255 - 8 * lane - q];
+    tot += c[q];
+  }
+  unsigned incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const unsigned excl = incl - tot;
+  const bool mine = excl < need && need <= incl;
+  const unsigned ball = __ballot_sync(0xffffffffu, mine);
+  const int src = __ffs(ball) - 1;
+  int b = 0;
+  unsigned bef = 0;
+  if (mine) {
+    unsigned acc = excl;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (acc + c[q] >= need) {
+        b = 255 - 8 * lane - q;
+        bef = acc;
+        break;
+      }
+      acc += c[q];
+    }
+  }
+  bin = __shfl_sync(0xffffffffu, b, src);
+  before = __shfl_sync(0xffffffffu, bef, src);
+}
+
+// Row-buffer passes read kBatch keys per lane before using any of them, so
+// their loads are in flight together.
+constexpr int kBatch = 8;
+
 // The r-th largest (1-based) of the cnt distinct keys buf[0, cnt), r <= cnt:
 // one 8-bit digit per pass from the top, counting only keys that share the
 // digits found so far.
@@ -137,44 +235,21 @@ __device__ uint64_t warp_select_kth(const uint64_t* buf, int cnt, int r, unsigne
     const uint64_t hmask = byte == 7 ? 0ull : (~0ull << (sh + 8));
     for (int b = lane; b < 256; b += 32) hist[b] = 0u;
     __syncwarp();
-    for (int i = lane; i < cnt; i += 32) {
-      const uint64_t k = buf[i];
-      if ((k & hmask) == prefix) atomicAdd(&hist[(uint32_t)(k >> sh) & 255u], 1u);
+    for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
+      uint64_t k[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = i0 + 32 * u + lane;
+        k[u] = i < cnt ? buf[i] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        if (i0 + 32 * u + lane < cnt && (k[u] & hmask) == prefix) atomicAdd(&hist[(uint32_t)(k[u] >> sh) & 255u], 1u);
     }
     __syncwarp();
-    // lane l holds bins 255 - 8l .. 248 - 8l (descending digit order)
-    unsigned c[8], tot = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      c[q] = hist[255 - 8 * lane - q];
-      tot += c[q];
-    }
-    unsigned incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const unsigned excl = incl - tot;
-    const bool mine = excl < need && need <= incl;
-    const unsigned ball = __ballot_sync(0xffffffffu, mine);
-    const int src = __ffs(ball) - 1;
-    int bin = 0;
-    unsigned before = 0;
-    if (mine) {
-      unsigned acc = excl;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (acc + c[q] >= need) {
-          bin = 255 - 8 * lane - q;
-          before = acc;
-          break;
-        }
-        acc += c[q];
-      }
-    }
-    bin = __shfl_sync(0xffffffffu, bin, src);
-    before = __shfl_sync(0xffffffffu, before, src);
+    int bin;
+    unsigned before;
+    hist_find_desc(hist, need, lane, bin, before);
     prefix |= (uint64_t)bin << sh;
     need -= before;
     __syncwarp();
@@ -185,16 +260,106 @@ __device__ uint64_t warp_select_kth(const uint64_t* buf, int cnt, int r, unsigne
 // Copies the keys >= kmin of buf[0, cnt) into s (in any order); returns how many.
 __device__ int warp_gather_ge(const uint64_t* buf, int cnt, uint64_t kmin, uint64_t* s, int lane) {
   int base = 0;
-  for (int i0 = 0; i0 < cnt; i0 += 32) {
-    const int i = i0 + lane;
-    const uint64_t k = i < cnt ? buf[i] : 0ull;
-    const bool keep = i < cnt && k >= kmin;
-    const unsigned ball = __ballot_sync(0xffffffffu, keep);
-    if (keep) s[base + __popc(ball & ((1u << lane) - 1u))] = k;
-    base += __popc(ball);
+  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
+    uint64_t k[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + 32 * u + lane;
+      k[u] = i < cnt ? buf[i] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const bool keep = i0 + 32 * u + lane < cnt && k[u] >= kmin;
+      const unsigned ball = __ballot_sync(0xffffffffu, keep);
+      if (keep) s[base + __popc(ball & ((1u << lane) - 1u))] = k[u];
+      base += __popc(ball);
+    }
   }
   __syncwarp();
   return base;
+}
+
+// Smallest and largest value among the keys buf[0, cnt), cnt >= 1.
+__device__ void warp_value_range(const uint64_t* buf, int cnt, int lane, int& lo, int& hi) {
+  int mn = INT32_MAX, mx = INT32_MIN;
+  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
+    uint64_t k[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + 32 * u + lane;
+      k[u] = i < cnt ? buf[i] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+      if (i0 + 32 * u + lane < cnt) {
+        mn = min(mn, key_val(k[u]));
+        mx = max(mx, key_val(k[u]));
+      }
+  }
+  lo = __reduce_min_sync(0xffffffffu, mn);
+  hi = __reduce_max_sync(0xffffffffu, mx);
+}
+
+// hist[b] = number of keys of buf[0, cnt) with (value - lo) >> sh == b; every
+// value lies in [lo, lo + (256 << sh)).
+__device__ void warp_value_hist(const uint64_t* buf, int cnt, int lo, int sh, unsigned* hist, int lane) {
+  for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+  __syncwarp();
+  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
+    uint64_t k[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + 32 * u + lane;
+      k[u] = i < cnt ? buf[i] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+      if (i0 + 32 * u + lane < cnt) atomicAdd(&hist[(uint32_t)(key_val(k[u]) - lo) >> sh], 1u);
+  }
+  __syncwarp();
+}
+
+// Keeps the keys of buf[0, cnt) whose value is >= t at the front of buf, in
+// their order; returns how many.  A batch's writes land below the end of the
+// batch, which its lanes have already read.
+__device__ int warp_keep_value_ge(uint64_t* buf, int cnt, int t, int lane) {
+  int base = 0;
+  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
+    uint64_t k[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + 32 * u + lane;
+      k[u] = i < cnt ? buf[i] : 0ull;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const bool keep = i0 + 32 * u + lane < cnt && key_val(k[u]) >= t;
+      const unsigned ball = __ballot_sync(0xffffffffu, keep);
+      if (keep) buf[base + __popc(ball & ((1u << lane) - 1u))] = k[u];
+      base += __popc(ball);
+    }
+    __syncwarp();
+  }
+  return base;
+}
+
+// Bits k (value k = 2 nb + e of a lane's row group: column 8 nb + 2 t4 + e of
+// the tile) whose column j is a real column other than the row i itself; a
+// row past n has none.
+__device__ __forceinline__ uint32_t valid_cols(uint32_t i, uint32_t tile, uint32_t n, int t4) {
+  if (i >= n) return 0u;
+  const uint32_t j0 = tile * kTileCols;
+  uint32_t v = 0xffffu;
+  if (j0 + kTileCols > n || (i >> 6) == tile) {
+    v = 0u;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t j = j0 + (uint32_t)((k >> 1) * 8 + 2 * t4 + (k & 1));
+      if (j < n && j != i) v |= 1u << k;
+    }
+  }
+  return v;
 }
 
 __device__ __forceinline__ int pow2_at_least(int x) {
@@ -207,7 +372,8 @@ __device__ __forceinline__ int pow2_at_least(int x) {
 // a multiple of kTileCols entries
 __global__ void __launch_bounds__(kThreads, 2)
     dot_topk_kernel(const __nv_bfloat16* __restrict__ Q, const float* __restrict__ biasf, uint32_t n, uint32_t C,
-                    uint64_t* __restrict__ buf, uint32_t* __restrict__ out_idx, int32_t* __restrict__ out_val) {
+                    uint64_t* __restrict__ buf, uint32_t* __restrict__ out_idx, int32_t* __restrict__ out_val,
+                    uint32_t* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* sB = smem;
   float* sBias = reinterpret_cast<float*>(smem + kOffBias);
@@ -216,21 +382,43 @@ __global__ void __launch_bounds__(kThreads, 2)
   int* sCnt = reinterpret_cast<int*>(smem + kOffCnt);
   float* sThr = reinterpret_cast<float*>(smem + kOffThr);
 
+  const uint32_t barFull = smem_u32(smem + kOffBars), barEmpty = barFull + 8 * kStages;
+  uint32_t* sNext = reinterpret_cast<uint32_t*>(smem + kOffBars + 16 * kStages);
+
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t row0 = blockIdx.x * (uint32_t)kRowsPerCta;
   const unsigned char* Qb = reinterpret_cast<const unsigned char*>(Q);
+  const uint32_t ntiles = (n + kTileCols - 1) / kTileCols, npad = ntiles * kTileCols;
 
-  // stage the CTA's 256 rows (zero past n) into the sort area, swizzled
+  // column tile u into ring stage u % kStages: its rows (already swizzled and
+  // zero-padded in global memory) and biases, counted on the stage's full barrier
+  auto issue = [&](uint32_t u) {
+    const uint32_t st = u % kStages;
+    mbar_expect_tx(barFull + 8 * st, kTileBytes + kTileBiasBytes);
+    bulk_g2s(smem_u32(sB + st * kTileBytes), Qb + (size_t)u * kTileBytes, kTileBytes, barFull + 8 * st);
+    bulk_g2s(smem_u32(sBias + st * kTileCols), biasf + (size_t)u * kTileCols, kTileBiasBytes, barFull + 8 * st);
+  };
+
+  // stage the CTA's 256 rows (zero past the padded rows) into the sort area
   unsigned char* sA = reinterpret_cast<unsigned char*>(sSort);
   for (int x = tid; x < kRowsPerCta * 8; x += kThreads) {
-    const int r = x >> 3, c = x & 7;
-    const uint32_t g = row0 + (uint32_t)r;
-    cp_async16(smem_u32(sA + swz(r, c)), Qb + (size_t)(g < n ? g : 0) * kRowBytes + c * 16, g < n);
+    const uint32_t g = row0 + (uint32_t)(x >> 3);
+    cp_async16(smem_u32(sA + x * 16), Qb + (size_t)(g < npad ? g : 0) * kRowBytes + (x & 7) * 16, g < npad);
   }
   cp_async_commit();
   for (int r = tid; r < kRowsPerCta; r += kThreads) {
     sCnt[r] = 0;
     sThr[r] = -FLT_MAX;
+  }
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(barFull + 8 * st, 1);
+      mbar_init(barEmpty + 8 * st, kWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const uint32_t first = min(ntiles, (uint32_t)kStages);
+    for (uint32_t u = 0; u < first; ++u) issue(u);
+    *sNext = first;
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -249,37 +437,39 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const int g = lane >> 2, t4 = lane & 3;
   float thr[2][2];
+  int cnt[2][2];  // keys in the row's buffer (same in the row's four lanes)
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) thr[s][h] = -FLT_MAX;
-
-  const uint32_t ntiles = (n + kTileCols - 1) / kTileCols;
-  auto load_tile = [&](uint32_t tile, int b) {
-    unsigned char* dst = sB + b * (kTileCols * kRowBytes);
-    for (int x = tid; x < kTileCols * 8; x += kThreads) {
-      const int r = x >> 3, c = x & 7;
-      const uint32_t j = tile * kTileCols + (uint32_t)r;
-      cp_async16(smem_u32(dst + swz(r, c)), Qb + (size_t)(j < n ? j : 0) * kRowBytes + c * 16, j < n);
+    for (int h = 0; h < 2; ++h) {
+      thr[s][h] = -FLT_MAX;
+      cnt[s][h] = 0;
     }
-    if (tid < kTileCols / 4)
-      cp_async16(smem_u32(sBias + b * kTileCols + tid * 4), biasf + (size_t)tile * kTileCols + tid * 4, true);
-  };
-#pragma unroll
-  for (int st = 0; st < kStages - 1; ++st) {
-    if ((uint32_t)st < ntiles) load_tile((uint32_t)st, st);
-    cp_async_commit();
-  }
 
   uint64_t* sMine = sSort + warp * kSel;
   unsigned* hMine = sHist + warp * 256;
-  const int trigger = min(kCap - kTileCols, 4 * (int)C);
+  const int trigger = min(kCap - kTileCols, 2 * (int)C);
+  const unsigned keep_limit = (C + (unsigned)trigger) / 2;  // a compaction frees at least this much
+  // Warps sweep the ring at their own pace.  A stage is released by each
+  // warp once its products are taken, and refilled by whichever warp finds it
+  // free first (the next tile to issue is claimed with a compare-and-swap), so
+  // a warp may run up to kStages tiles ahead of the CTA's slowest.
   for (uint32_t tile = 0; tile < ntiles; ++tile) {
     const int b = (int)(tile % kStages);
-    cp_async_wait<kStages - 2>();  // this tile's group has landed
-    __syncthreads();               // ... for every thread; and every warp is done with tile - 1
-    if (tile + kStages - 1 < ntiles) load_tile(tile + kStages - 1, (int)((tile + kStages - 1) % kStages));
-    cp_async_commit();
+    if (lane == 0) {
+      for (;;) {
+        const uint32_t u = *reinterpret_cast<volatile uint32_t*>(sNext);
+        if (u >= ntiles || u >= tile + kStages) break;
+        // stage u % kStages last held tile u - kStages: free once every warp released it
+        if (!mbar_test(barEmpty + 8 * (u % kStages), ((u / kStages) + 1) & 1)) break;
+        if (atomicCAS(sNext, u, u + 1) == u) issue(u);
+      }
+    }
+    const bool landed = mbar_wait(barFull + 8 * b, (tile / kStages) & 1);
+    if (__any_sync(0xffffffffu, !landed)) {
+      if (lane == 0) atomicOr(err, kErrWait);
+      break;
+    }
 
     const unsigned char* tB = sB + b * (kTileCols * kRowBytes);
     const float* tBias = sBias + b * kTileCols;
@@ -310,6 +500,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
 
+    __syncwarp();
+    if (lane == 0) mbar_arrive(barEmpty + 8 * b);
+
     // epilogue: the maximum of each (slab, half) row group against its row's
     // threshold; only groups that beat it look at their values one by one
     bool gh[2][2];
@@ -323,57 +516,131 @@ __global__ void __launch_bounds__(kThreads, 2)
         gh[s][h] = m > thr[s][h];
       }
     if (__any_sync(0xffffffffu, gh[0][0] | gh[0][1] | gh[1][0] | gh[1][1])) {
-      const uint32_t j0 = tile * kTileCols + 2u * (uint32_t)t4;
+      // A row's 16 x 4 values of this tile sit in the four lanes of one quad,
+      // and no other warp appends to it: the quad's lanes take consecutive
+      // slots by a prefix sum of their hit counts, with no atomics.  Hits are
+      // found as a bit mask, then read back from this lane's staging slots.
+      float* stage = reinterpret_cast<float*>(sMine) + lane * 32;
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < 2; ++s) {
+        uint32_t m[2] = {0u, 0u};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          if (!gh[s][h]) continue;
-          const int lr = warp * kRowsPerWarp + s * 16 + h * 8 + g;
-          const uint32_t i = row0 + (uint32_t)lr;
+          if (gh[s][h]) {
 #pragma unroll
-          for (int nb = 0; nb < 8; ++nb)
+            for (int nb = 0; nb < 8; ++nb)
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const float v = acc[s][nb][2 * h + e];
-              if (v > thr[s][h]) {
-                const uint32_t j = j0 + (uint32_t)(nb * 8 + e);
-                if (i < n && j < n && j != i) {
-                  const int slot = atomicAdd(&sCnt[lr], 1);
-                  buf[(size_t)i * kCap + slot] = make_key((int)v, j);
-                }
-              }
-            }
+              for (int e = 0; e < 2; ++e)
+                if (acc[s][nb][2 * h + e] > thr[s][h]) m[h] |= 1u << (2 * nb + e);
+            const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
+            if (m[h] != 0u) m[h] &= valid_cols(i, tile, n, t4);
+          }
         }
+        uint32_t pos[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int hc = __popc(m[h]);
+          int incl = hc;
+#pragma unroll
+          for (int o = 1; o < 4; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o, 4);
+            if (t4 >= o) incl += t;
+          }
+          pos[h] = (uint32_t)(cnt[s][h] + incl - hc);
+          cnt[s][h] += __shfl_sync(0xffffffffu, incl, 3, 4);
+        }
+        if ((m[0] | m[1]) != 0u) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int nb = 0; nb < 8; ++nb)
+              *reinterpret_cast<float2*>(stage + h * 16 + 2 * nb) =
+                  make_float2(acc[s][nb][2 * h], acc[s][nb][2 * h + 1]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
+            uint64_t* rb = buf + (size_t)i * kCap;
+            uint32_t mm = m[h], slot = pos[h];
+            while (mm != 0u) {
+              const int k = __ffs(mm) - 1;
+              mm &= mm - 1u;
+              const uint32_t j = tile * kTileCols + (uint32_t)((k >> 1) * 8 + 2 * t4 + (k & 1));
+              rb[slot++] = make_key((int)stage[h * 16 + k], j);
+            }
+          }
+        }
+      }
     }
     __syncwarp();
 
-    // rows of this warp holding more than `trigger` keys: compacting at 4C
+    // rows of this warp holding more than `trigger` keys: compacting at 2C
     // (or when the buffer could overflow during the next tile) keeps the
     // thresholds close to the running C-th best value
-    unsigned full = __ballot_sync(0xffffffffu, sCnt[warp * kRowsPerWarp + lane] > trigger);
-    if (full) {
+    if (__any_sync(0xffffffffu, (cnt[0][0] > trigger) | (cnt[0][1] > trigger) | (cnt[1][0] > trigger) |
+                                    (cnt[1][1] > trigger))) {
+      if (t4 == 0) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g] = cnt[s][h];
+      }
+      __syncwarp();
+      unsigned full = __ballot_sync(0xffffffffu, sCnt[warp * kRowsPerWarp + lane] > trigger);
       while (full) {
         const int l = __ffs(full) - 1;
         full &= full - 1;
         const int lr = warp * kRowsPerWarp + l;
         uint64_t* rb = buf + (size_t)(row0 + (uint32_t)lr) * kCap;
-        const uint64_t kth = warp_select_kth(rb, sCnt[lr], (int)C, hMine, lane);
-        const int kept = warp_gather_ge(rb, sCnt[lr], kth, sMine, lane);  // == C
-        for (int x = lane; x < kept; x += 32) rb[x] = sMine[x];
+        const int c = sCnt[lr];
+        // A threshold t at or below the C-th best value is enough here (the
+        // final pass selects exactly): t is the lower edge of the 256-bin
+        // value-histogram bin holding the C-th best key, and the keys with
+        // value >= t stay.  A later value that can still enter the row's top
+        // C beats the C-th best key now, hence t.  A crowded bin falls back
+        // to the exact C-th key.
+        int lo, hi;
+        warp_value_range(rb, c, lane, lo, hi);
+        const unsigned span = (unsigned)(hi - lo);
+        const int sh = span < 256u ? 0 : 24 - __clz((int)span);
+        warp_value_hist(rb, c, lo, sh, hMine, lane);
+        int bin;
+        unsigned above;
+        hist_find_desc(hMine, C, lane, bin, above);
+        const unsigned keep = above + hMine[bin];
+        __syncwarp();
+        int kept, t;
+        if (keep <= keep_limit) {
+          t = lo + (bin << sh);
+          kept = warp_keep_value_ge(rb, c, t, lane);  // == keep
+        } else {
+          const uint64_t kth = warp_select_kth(rb, c, (int)C, hMine, lane);
+          kept = warp_gather_ge(rb, c, kth, sMine, lane);  // == C
+          for (int x = lane; x < kept; x += 32) rb[x] = sMine[x];
+          t = key_val(kth);
+        }
         if (lane == 0) {
           sCnt[lr] = kept;
-          sThr[lr] = (float)key_val(kth);
+          sThr[lr] = (float)t;
         }
         __syncwarp();
       }
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) thr[s][h] = sThr[warp * kRowsPerWarp + s * 16 + h * 8 + g];
+        for (int h = 0; h < 2; ++h) {
+          thr[s][h] = sThr[warp * kRowsPerWarp + s * 16 + h * 8 + g];
+          cnt[s][h] = sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g];
+        }
+      __syncwarp();
     }
   }
-  cp_async_wait<0>();
+  if (t4 == 0) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g] = cnt[s][h];
+  }
+  __syncwarp();
 
   // final lists: the C best keys of each row, sorted
   for (int l = 0; l < kRowsPerWarp; ++l) {
@@ -395,6 +662,18 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncwarp();
   }
+
+  // every issued copy has landed before the CTA's shared memory is released
+  // (all of them were consumed, unless a wait ran out)
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t issued = *sNext;
+    for (uint32_t u = issued > (uint32_t)kStages ? issued - kStages : 0u; u < issued; ++u)
+      if (!mbar_wait(barFull + 8 * (u % kStages), (u / kStages) & 1)) {
+        atomicOr(err, kErrWait);
+        break;
+      }
+  }
 }
 
 __global__ void absmax_kernel(const float* __restrict__ E, uint32_t n, unsigned int* amax_bits) {
@@ -409,32 +688,45 @@ __global__ void absmax_kernel(const float* __restrict__ E, uint32_t n, unsigned 
   if ((threadIdx.x & 31) == 0) atomicMax(amax_bits, __float_as_uint(m));  // non-negative floats order as integers
 }
 
-__global__ void quantize_kernel(const float* __restrict__ E, uint32_t n, const unsigned int* amax_bits, int8_t* q,
-                                __nv_bfloat16* qb, int32_t* bias, float* scale_out) {
+// Element (r, c) of the bf16 rows the candidate kernel reads: rows padded
+// with zeros to a whole number of column tiles, and the 16-byte chunks of row
+// r permuted by r & 7, the shared-memory swizzle its tiles are copied into.
+__device__ __forceinline__ size_t swz_index(size_t r, int c) {
+  return r * kDim + (size_t)((((c >> 3) ^ (int)(r & 7)) << 3) | (c & 7));
+}
+
+// one thread per (row, value) of the padded rows: the quantised values
+// (row-major int8, optional), their bf16 copy (optional) and the biases
+__global__ void quantize_kernel(const float* __restrict__ E, uint32_t n, uint32_t npad, const unsigned int* amax_bits,
+                                int8_t* q, __nv_bfloat16* qb, int32_t* bias, float* scale_out) {
   const float scale = __uint_as_float(*amax_bits) / 127.0f;
   const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x == 0 && scale_out) *scale_out = scale;
-  if (x >= (size_t)n * kDim) return;
+  if (x >= (size_t)npad * kDim) return;
   const size_t r = x / kDim;
   const int c = (int)(x - r * kDim);
   float v = 0.f;
-  if (c < kFeat) {
-    if (scale > 0.f) v = fminf(fmaxf(rintf(E[x] / scale), -127.f), 127.f);
-  } else if (bias) {
-    int32_t bv = 0;
-    if (scale > 0.f) {
-      const float s2 = scale * scale;
-      bv = (int32_t)fminf(fmaxf(rintf(E[x] / s2), -(float)kBiasLimit), (float)kBiasLimit);
+  if (r < n) {
+    if (c < kFeat) {
+      if (scale > 0.f) v = fminf(fmaxf(rintf(E[x] / scale), -127.f), 127.f);
+    } else if (bias) {
+      int32_t bv = 0;
+      if (scale > 0.f) {
+        const float s2 = scale * scale;
+        bv = (int32_t)fminf(fmaxf(rintf(E[x] / s2), -(float)kBiasLimit), (float)kBiasLimit);
+      }
+      bias[r] = bv;
     }
-    bias[r] = bv;
+    if (q) q[x] = (int8_t)v;
   }
-  if (q) q[x] = (int8_t)v;
-  if (qb) qb[x] = __float2bfloat16_rn(v);
+  if (qb) qb[swz_index(r, c)] = __float2bfloat16_rn(v);
 }
 
-__global__ void widen_kernel(const int8_t* __restrict__ q, size_t count, __nv_bfloat16* qb) {
+__global__ void widen_kernel(const int8_t* __restrict__ q, uint32_t n, uint32_t npad, __nv_bfloat16* qb) {
   const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < count) qb[x] = __float2bfloat16_rn((float)q[x]);
+  if (x >= (size_t)npad * kDim) return;
+  const size_t r = x / kDim;
+  qb[swz_index(r, (int)(x - r * kDim))] = __float2bfloat16_rn(r < n ? (float)q[x] : 0.f);
 }
 
 __global__ void bias_float_kernel(const int32_t* __restrict__ bias, uint32_t n, uint32_t npad, float* biasf) {
@@ -446,36 +738,44 @@ size_t bias_pad(uint32_t n) { return ((size_t)n + kTileCols - 1) / kTileCols * k
 
 }  // namespace
 
-size_t dot_topk_buffer_bytes(uint32_t n) { return (size_t)n * kCap * sizeof(uint64_t) + bias_pad(n) * sizeof(float); }
+size_t dot_topk_qb_bytes(uint32_t n) { return bias_pad(n) * kRowBytes; }
+
+size_t dot_topk_buffer_bytes(uint32_t n) {
+  return (size_t)n * kCap * sizeof(uint64_t) + bias_pad(n) * sizeof(float) + 16;
+}
+
+uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t n) {
+  return reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(buf + (size_t)n * kCap) + bias_pad(n));
+}
 
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
-                     uint32_t* idx, int32_t* val, cudaStream_t s) {
+                     uint32_t* idx, int32_t* val, uint32_t* err, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(dot_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
   if (e != cudaSuccess) return e;
-  float* biasf = reinterpret_cast<float*>(buf + (size_t)n * kCap);  // after the append buffers
+  float* biasf = reinterpret_cast<float*>(buf + (size_t)n * kCap);  // after the append buffers (16-byte aligned)
   const uint32_t npad = (uint32_t)bias_pad(n);
   bias_float_kernel<<<(npad + 255) / 256, 256, 0, s>>>(bias, n, npad, biasf);
   const unsigned grid = (n + kRowsPerCta - 1) / kRowsPerCta;
-  dot_topk_kernel<<<grid, kThreads, kSmemTotal, s>>>(Qb, biasf, n, C, buf, idx, val);
+  dot_topk_kernel<<<grid, kThreads, kSmemTotal, s>>>(Qb, biasf, n, C, buf, idx, val, err);
   return cudaGetLastError();
 }
 
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,
                      int32_t* bias, float* scale, cudaStream_t s) {
-  const size_t count = (size_t)n * kDim;
+  const size_t count = (size_t)bias_pad(n) * kDim;
   cudaError_t e = cudaMemsetAsync(amax_bits, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  if (count) absmax_kernel<<<1024, 256, 0, s>>>(E, n, amax_bits);
-  quantize_kernel<<<(unsigned)((count + 255) / 256 + (count == 0)), 256, 0, s>>>(E, n, amax_bits, q, qb, bias,
-                                                                                   scale);
+  if (n) absmax_kernel<<<1024, 256, 0, s>>>(E, n, amax_bits);
+  quantize_kernel<<<(unsigned)((count + 255) / 256 + (count == 0)), 256, 0, s>>>(E, n, (uint32_t)bias_pad(n),
+                                                                                   amax_bits, q, qb, bias, scale);
   return cudaGetLastError();
 }
 
 cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s) {
-  const size_t count = (size_t)n * kDim;
+  const size_t count = (size_t)bias_pad(n) * kDim;
   if (!count) return cudaSuccess;
-  widen_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(q, count, qb);
+  widen_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(q, n, (uint32_t)bias_pad(n), qb);
   return cudaGetLastError();
 }
 

@@ -642,6 +642,7 @@ nw_status check_device_flags(nw_ctx* c, const uint32_t* d_small) {
   NW_CK(cudaMemcpyAsync(&err, d_small, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
   NW_CK(cudaStreamSynchronize(c->stream));
   if (err & kErrRetry) return set_err(c, NW_ETIMEOUT, "a neighbour-list update exceeded its retry bound");
+  if (err & kErrWait) return set_err(c, NW_ETIMEOUT, "a pipeline wait on the device ran out");
   if (err & kErrInput) return set_err(c, NW_EINVAL, "invalid word index in the input (outputs may be partially written)");
   if (err & kErrHistRange) return set_err(c, NW_ERANGE, "a score fell outside the histogram range");
   return NW_OK;

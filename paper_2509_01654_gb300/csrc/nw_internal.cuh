@@ -42,6 +42,7 @@ constexpr int kInsertMaxIters = 1 << 20;
 constexpr uint32_t kErrRetry = 1u;      // a list insertion exceeded its retry bound
 constexpr uint32_t kErrHistRange = 2u;  // a score fell outside the histogram bins
 constexpr uint32_t kErrInput = 4u;      // invalid input seen on the device (code/length/index)
+constexpr uint32_t kErrWait = 8u;       // a pipeline wait ran out (the kernel stopped early)
 
 __host__ __device__ constexpr int ceil4(int x) { return (x + 3) & ~3; }
 

@@ -187,6 +187,7 @@ nw_status check_err(nw_model* M, cudaStream_t s) {
   NW_CK(cudaStreamSynchronize(s));
   if (err) {
     NW_CK(cudaMemsetAsync(err_ptr(M), 0, sizeof(uint32_t), s));
+    if (err & kErrWait) return set_err(c, NW_ETIMEOUT, "a pipeline wait on the device ran out");
     return set_err(c, NW_EINVAL, "invalid word index or code in the input");
   }
   return NW_OK;
@@ -590,7 +591,7 @@ nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, const int32_t* bias, uint32_t 
                           s));
     srcb = db.as<int32_t>();
   }
-  NW_TRY(ctx_alloc(c, qb, cnt * sizeof(__nv_bfloat16), "bf16 embeddings"));
+  NW_TRY(ctx_alloc(c, qb, prop::dot_topk_qb_bytes(n), "bf16 embeddings"));
   NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
   uint32_t* out_i = idx;
   int32_t* out_v = val;
@@ -600,8 +601,11 @@ nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, const int32_t* bias, uint32_t 
     out_i = oi.as<uint32_t>();
     out_v = od.as<int32_t>();
   }
+  uint32_t* derr = prop::dot_topk_err_word(buf.as<uint64_t>(), n);
+  NW_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
   NW_CK(prop::widen(srcq, n, qb.as<__nv_bfloat16>(), s));
-  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), srcb, n, C, buf.as<uint64_t>(), out_i, out_v, s));
+  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), srcb, n, C, buf.as<uint64_t>(), out_i, out_v, derr, s));
+  NW_TRY(check_device_flags(c, derr));
   if (!dev) {
     NW_TRY(copy_out(c, idx, out_i, outc, false, s));
     NW_TRY(copy_out(c, val, out_v, outc, false, s));
@@ -673,7 +677,7 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
   const bool dev = flags & NW_DEVICE_PTRS;
   cudaStream_t s = M->stream;
   const size_t outc = (size_t)n * C;
-  NW_TRY(ctx_ensure(c, M->Qb, sizeof(__nv_bfloat16) * (size_t)n * NW_EMBED_DIM, "bf16 embeddings"));
+  NW_TRY(ctx_ensure(c, M->Qb, prop::dot_topk_qb_bytes(n), "bf16 embeddings"));
   NW_TRY(ctx_ensure(c, M->qbias, sizeof(int32_t) * (size_t)n, "quantised biases"));
   NW_TRY(ctx_ensure(c, M->topbuf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
   NW_TRY(ctx_ensure(c, M->cand, sizeof(uint32_t) * outc, "candidate lists"));
@@ -712,7 +716,7 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
                        nullptr, s));
   NW_CK(cudaEventRecord(ev[2], s));
   NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
-                       M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), s));
+                       M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s));
   NW_CK(cudaEventRecord(ev[3], s));
   NW_TRY(rescore_select(c, d, M->cand.as<uint32_t>(), C, k, M->cand_score, out_i, out_s, err_ptr(M), s));
   NW_CK(cudaEventRecord(ev[4], s));

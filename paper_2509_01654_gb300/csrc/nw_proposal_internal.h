@@ -16,15 +16,23 @@ constexpr int kFeat = 63;        // embedding outputs 0..62 are features, 63 is 
 constexpr int kBiasLimit = 1 << 23;
 
 // Quantisation of n x 64 embeddings (see nw_quantize_embeddings): q (int8,
-// may be null), qb (bf16, may be null), bias (int32, may be null), scale
+// row-major, may be null), qb (the candidate kernel's bf16 rows,
+// dot_topk_qb_bytes(n), may be null), bias (int32, may be null), scale
 // (device float, may be null); amax_bits is device scratch.
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,
                      int32_t* bias, float* scale, cudaStream_t s);
+// int8 rows (row-major) -> the candidate kernel's bf16 rows
 cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s);
+// bf16 rows: zero-padded to whole 64-row tiles, 16-byte chunks of row r
+// permuted by r & 7
+size_t dot_topk_qb_bytes(uint32_t n);
 size_t dot_topk_buffer_bytes(uint32_t n);
-// each row's C best q_i . q_j + bias_j (bias may be null: 0)
+// the device error word inside a dot_topk buffer (zero it before a launch)
+uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t n);
+// each row's C best q_i . q_j + bias_j (bias may be null: 0); a pipeline
+// wait that runs out sets kErrWait in *err
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
-                     uint32_t* idx, int32_t* dot, cudaStream_t s);
+                     uint32_t* idx, int32_t* dot, uint32_t* err, cudaStream_t s);
 
 // Algorithm 1's score of (i, cand[i * C + r]) into score[i * C + r] (int32;
 // INT32_MIN for UINT32_MAX entries); out-of-range or self candidates raise

@@ -202,6 +202,30 @@ def test_dot_topk_large_sampled_rows(ctx):
     assert not np.any(idx == np.arange(n, dtype=np.uint32)[:, None])
 
 
+@pytest.mark.parametrize("kind", ["constant", "two_values", "narrow", "wide"])
+def test_dot_topk_compaction_value_spreads(ctx, kind):
+    # C = 16 compacts every 64 keys.  Constant values put every key in one
+    # histogram bin (the exact select runs); two values, a narrow and a wide
+    # spread exercise the histogram threshold with few and many keys per bin.
+    n, C = 3000, 16
+    g = np.random.default_rng(5)
+    q = np.zeros((n, 64), np.int8)
+    bias = None
+    if kind == "two_values":
+        q[:, 0] = g.integers(0, 2, n)
+        q[:, 1] = 1
+    elif kind == "narrow":
+        q[:, :4] = g.integers(-3, 4, (n, 4))
+    elif kind == "wide":
+        q = g.integers(-127, 128, (n, 64)).astype(np.int8)
+        bias = g.integers(-(1 << 22), 1 << 22, n).astype(np.int32)
+    idx, dot = nw.dot_topk(ctx, q, C, bias=bias)
+    rows = np.unique(np.concatenate([synth.sample_rows(n, 96), [0, 1, n - 2, n - 1]])).astype(np.int64)
+    wi, wd = PR.dot_topk(q, C, rows=rows, bias=bias)
+    assert np.array_equal(dot[rows], wd)
+    assert np.array_equal(idx[rows], wi)
+
+
 def test_dot_topk_rejects_bad_C(ctx):
     q = np.zeros((10, 64), np.int8)
     for C in (0, nw.MAX_CANDIDATES + 1):
