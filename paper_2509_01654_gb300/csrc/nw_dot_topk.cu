@@ -510,10 +510,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        float m = fmaxf(acc[s][0][2 * h], acc[s][0][2 * h + 1]);
+        float m[8];  // a tree of maxima: depth 4 instead of a chain of 15
 #pragma unroll
-        for (int nb = 1; nb < 8; ++nb) m = fmaxf(m, fmaxf(acc[s][nb][2 * h], acc[s][nb][2 * h + 1]));
-        gh[s][h] = m > thr[s][h];
+        for (int nb = 0; nb < 8; ++nb) m[nb] = fmaxf(acc[s][nb][2 * h], acc[s][nb][2 * h + 1]);
+#pragma unroll
+        for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+          for (int x = 0; x < w; ++x) m[x] = fmaxf(m[x], m[x + w]);
+        gh[s][h] = m[0] > thr[s][h];
       }
     if (__any_sync(0xffffffffu, gh[0][0] | gh[0][1] | gh[1][0] | gh[1][1])) {
       // A row's 16 x 4 values of this tile sit in the four lanes of one quad,
@@ -527,11 +531,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (gh[s][h]) {
+            uint32_t part[4] = {0u, 0u, 0u, 0u};  // independent partial masks
 #pragma unroll
             for (int nb = 0; nb < 8; ++nb)
 #pragma unroll
               for (int e = 0; e < 2; ++e)
-                if (acc[s][nb][2 * h + e] > thr[s][h]) m[h] |= 1u << (2 * nb + e);
+                if (acc[s][nb][2 * h + e] > thr[s][h]) part[nb & 3] |= 1u << (2 * nb + e);
+            m[h] = (part[0] | part[1]) | (part[2] | part[3]);
             const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
             if (m[h] != 0u) m[h] &= valid_cols(i, tile, n, t4);
           }
