@@ -9,6 +9,13 @@ the CUDA path is checked against, written plainly:
 * ``forward``: codes -> embedding table (32) -> three 1-D convolutions of
   width 3 with 128 channels, zero padding, ReLU -> mean over the word's
   positions -> linear map to 64 values.  Plain PyTorch CPU ops in float64.
+  With ``bf16=True`` every matrix product takes its two operands rounded
+  to bfloat16 (through float32, nearest even), the precision the
+  network's weights and products are specified in (BF16 operands,
+  float32 accumulation); the products themselves stay exact in float64.
+  In ``loss_and_grad`` the gradient products round their operands the
+  same way (the output gradient and the saved input or weight); bias
+  gradients are sums of the unrounded output gradient.
 * ``predict``: the modelled similarity of two words.  The 64 outputs are
   read as 63 features phi and one bias beta, and
   pred(a, b) = phi_a . phi_b + beta_a + beta_b.  A raw alignment score
@@ -79,9 +86,64 @@ def _torch():
     return torch
 
 
-def _forward_t(P, words):
+def _bf16(x):
+    """x (float64 tensor) rounded to float32, then to bfloat16 (nearest
+    even), returned as float64."""
+    torch = _torch()
+    return x.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+_FUNCS = {}
+
+
+def _bf16_funcs():
+    """autograd functions of a convolution and of the linear map whose
+    forward and gradient products take bf16-rounded operands."""
+    if _FUNCS:
+        return _FUNCS["conv"], _FUNCS["lin"]
+    torch = _torch()
+    F = torch.nn.functional
+
+    class Conv(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, W, b):  # x (n, C, L), W (o, tap, c)
+            xr, Wr = _bf16(x), _bf16(W)
+            ctx.save_for_backward(xr, Wr)
+            return F.conv1d(xr, Wr.permute(0, 2, 1), b, padding=1)
+
+        @staticmethod
+        def backward(ctx, gy):
+            xr, Wr = ctx.saved_tensors
+            gr = _bf16(gy)
+            w_oct = Wr.permute(0, 2, 1)
+            gx = torch.nn.grad.conv1d_input(xr.shape, w_oct, gr, padding=1)
+            gw = torch.nn.grad.conv1d_weight(xr, w_oct.shape, gr, padding=1).permute(0, 2, 1)
+            return gx, gw, gy.sum(dim=(0, 2))
+
+    class Lin(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, p, W, b):  # p (n, Ci), W (Co, Ci)
+            pr, Wr = _bf16(p), _bf16(W)
+            ctx.save_for_backward(pr, Wr)
+            return pr @ Wr.T + b
+
+        @staticmethod
+        def backward(ctx, ge):
+            pr, Wr = ctx.saved_tensors
+            gr = _bf16(ge)
+            return gr @ Wr, gr.T @ pr, ge.sum(dim=0)
+
+    _FUNCS["conv"], _FUNCS["lin"] = Conv, Lin
+    return Conv, Lin
+
+
+def _forward_t(P, words, bf16=False):
     """Embeddings (n, 64) as a float64 torch tensor; P holds torch tensors."""
     torch = _torch()
+    conv = lin = None
+    if bf16:
+        Conv, Lin = _bf16_funcs()
+        conv, lin = Conv.apply, Lin.apply
     n = words.n
     lens = torch.tensor(words.lengths, dtype=torch.int64)
     Lp = max(1, int(lens.max().item()) if n else 1)
@@ -96,19 +158,21 @@ def _forward_t(P, words):
     for W, b in ((P["W1"], P["b1"]), (P["W2"], P["b2"]), (P["W3"], P["b3"])):
         # W[o][tap][c] with tap 0 reading x[t - 1]: conv1d's weight[o][c][tap]
         # with padding 1 computes sum_tap weight[o][c][tap] * x[t + tap - 1]
-        y = torch.nn.functional.conv1d(x, W.permute(0, 2, 1), b, padding=1)
+        y = conv(x, W, b) if bf16 else torch.nn.functional.conv1d(x, W.permute(0, 2, 1), b, padding=1)
         x = torch.relu(y) * mask[:, None, :]  # positions past the word are zero input to the next layer
     denom = lens.clamp(min=1).to(torch.float64)
     pooled = x.sum(dim=2) / denom[:, None]                                # (n, 128); empty word -> 0
+    if bf16:
+        return lin(pooled, P["Wl"], P["bl"])
     return pooled @ P["Wl"].T + P["bl"]
 
 
-def forward(flat, words, alphabet: int) -> np.ndarray:
+def forward(flat, words, alphabet: int, bf16: bool = False) -> np.ndarray:
     """float64 embeddings (n, 64) of every word for the flat parameters."""
     torch = _torch()
     P = {k: torch.tensor(np.asarray(v, dtype=np.float64)) for k, v in unflatten(np.asarray(flat), alphabet).items()}
     with torch.no_grad():
-        return _forward_t(P, words).numpy()
+        return _forward_t(P, words, bf16).numpy()
 
 
 def _predict_t(Ea, Eb):
@@ -122,7 +186,7 @@ def predict(Ea, Eb) -> np.ndarray:
     return np.sum(Ea[:, :FEAT] * Eb[:, :FEAT], axis=1) + Ea[:, FEAT] + Eb[:, FEAT]
 
 
-def loss_and_grad(flat, words, alphabet: int, pi, pj, target):
+def loss_and_grad(flat, words, alphabet: int, pi, pj, target, bf16: bool = False):
     """(loss, gradient of the flat parameters): mean over pairs of
     (pred(E[pi], E[pj]) - target)^2."""
     torch = _torch()
@@ -132,7 +196,7 @@ def loss_and_grad(flat, words, alphabet: int, pi, pj, target):
         n = int(np.prod(shape))
         P[name] = flat_t[o:o + n].reshape(shape)
         o += n
-    E = _forward_t(P, words)
+    E = _forward_t(P, words, bf16)
     pi = torch.tensor(np.asarray(pi, dtype=np.int64))
     pj = torch.tensor(np.asarray(pj, dtype=np.int64))
     y = torch.tensor(np.asarray(target, dtype=np.float64))

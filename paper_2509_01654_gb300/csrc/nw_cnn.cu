@@ -1,7 +1,8 @@
-// nw_cnn.cu -- kernels of the proposal network: tiled float32 matrix products
-// whose operand loaders gather convolution windows directly from the packed
+// nw_cnn.cu -- kernels of the proposal network: bf16 tensor-core matrix
+// products (float32 accumulation) whose operand loaders gather convolution windows directly from the packed
 // activations (no im2col buffer, no padding rows), and the elementwise steps
 // around them.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,13 +15,18 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // operand views: element (r, c) of a logical matrix.  kColFast: consecutive
-// c are adjacent in memory (the tile loader then walks c fastest).
+// c are adjacent in memory (the tile loader then walks c fastest).  A view
+// whose pairs (c, c + 1) (at2c) or (r, r + 1) (at2r) are adjacent reads
+// them with one 8-byte load; channel counts are powers of two.
 
 struct Dense {  // row-major
   const float* p;
   int ld;
   static constexpr bool kColFast = true;
   __device__ __forceinline__ float at(int r, int c) const { return __ldg(p + (size_t)r * ld + c); }
+  __device__ __forceinline__ float2 at2c(int r, int c) const {
+    return __ldg(reinterpret_cast<const float2*>(p + (size_t)r * ld + c));
+  }
 };
 
 struct DenseT {  // transpose of a row-major matrix
@@ -28,6 +34,9 @@ struct DenseT {  // transpose of a row-major matrix
   int ld;
   static constexpr bool kColFast = false;
   __device__ __forceinline__ float at(int r, int c) const { return __ldg(p + (size_t)c * ld + r); }
+  __device__ __forceinline__ float2 at2r(int r, int c) const {
+    return __ldg(reinterpret_cast<const float2*>(p + (size_t)c * ld + r));
+  }
 };
 
 // im2col of packed X[T][Ci]: (t, tap * Ci + ch) = X[t + tap - 1][ch] when
@@ -35,14 +44,22 @@ struct DenseT {  // transpose of a row-major matrix
 struct Im2col {
   const float* X;
   const int* rinfo;
-  int Ci;
+  int lg;  // log2 Ci
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ float at(int t, int k) const {
-    const int tap = k / Ci, ch = k - tap * Ci;
+  __device__ __forceinline__ const float* row(int t, int k) const {
+    const int tap = k >> lg;
     const int info = __ldg(rinfo + t);
     const int pos = (info >> 8) + tap - 1;
-    if (pos < 0 || pos >= (info & 255)) return 0.f;
-    return __ldg(X + (size_t)(t + tap - 1) * Ci + ch);
+    if (pos < 0 || pos >= (info & 255)) return nullptr;
+    return X + ((size_t)(t + tap - 1) << lg) + (k & ((1 << lg) - 1));
+  }
+  __device__ __forceinline__ float at(int t, int k) const {
+    const float* q = row(t, k);
+    return q ? __ldg(q) : 0.f;
+  }
+  __device__ __forceinline__ float2 at2c(int t, int k) const {  // k even: one tap
+    const float* q = row(t, k);
+    return q ? __ldg(reinterpret_cast<const float2*>(q)) : make_float2(0.f, 0.f);
   }
 };
 
@@ -51,106 +68,216 @@ struct Im2col {
 struct Shift {
   const float* dY;
   const int* rinfo;
-  int Co;
+  int lg;  // log2 Co
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ float at(int t, int k) const {
-    const int tap = k / Co, o = k - tap * Co;
+  __device__ __forceinline__ const float* row(int t, int k) const {
+    const int tap = k >> lg;
     const int info = __ldg(rinfo + t);
     const int pos = (info >> 8) - tap + 1;
-    if (pos < 0 || pos >= (info & 255)) return 0.f;
-    return __ldg(dY + (size_t)(t - tap + 1) * Co + o);
+    if (pos < 0 || pos >= (info & 255)) return nullptr;
+    return dY + ((size_t)(t - tap + 1) << lg) + (k & ((1 << lg) - 1));
+  }
+  __device__ __forceinline__ float at(int t, int k) const {
+    const float* q = row(t, k);
+    return q ? __ldg(q) : 0.f;
+  }
+  __device__ __forceinline__ float2 at2c(int t, int k) const {
+    const float* q = row(t, k);
+    return q ? __ldg(reinterpret_cast<const float2*>(q)) : make_float2(0.f, 0.f);
   }
 };
 
 // W[Co][3][Ci] read as the (tap * Co + o, ch) matrix of the input gradient
 struct WTap {
   const float* W;
-  int Co, Ci;
+  int lgCo, Ci;
   static constexpr bool kColFast = true;
   __device__ __forceinline__ float at(int k, int ch) const {
-    const int tap = k / Co, o = k - tap * Co;
+    const int tap = k >> lgCo, o = k & ((1 << lgCo) - 1);
     return __ldg(W + ((size_t)o * 3 + tap) * Ci + ch);
+  }
+  __device__ __forceinline__ float2 at2c(int k, int ch) const {
+    const int tap = k >> lgCo, o = k & ((1 << lgCo) - 1);
+    return __ldg(reinterpret_cast<const float2*>(W + ((size_t)o * 3 + tap) * Ci + ch));
   }
 };
 
-constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
+// bf16 tensor-core tiles: 128 x 128 outputs per block of 8 warps (2 x 4,
+// 64 x 32 each, m16n8k16 products with float32 accumulation), K in steps of
+// 32 through two shared buffers.  Operands are rounded to bf16 (nearest
+// even) as they are staged; a shared row holds 32 values plus 8 of padding,
+// so the eight 16-byte rows of an ldmatrix fall in distinct banks.
+constexpr int BM = 128, BN = 128, BK = 32, NT = 256;
+constexpr int LDS = BK + 8;
 
-// C[M][N] = A[M][K] . B[K][N] over the K range of blockIdx.z: 128 x 128 tiles,
-// 8 x 8 outputs per thread (two 4 x 4 blocks 64 apart in each direction).
-// Mlim / Klim (device, may be null) lower M / K below the launch's bounds.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // lo in the low half
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void ldsm_x4(const void* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// thread tid's 8 pairs of a 128 x 32 tile: (row, k pair); the fast index
+// follows the view's memory order so that a warp's loads are contiguous
+template <bool kFastK>
+__device__ __forceinline__ void tile_pair(int x, int& row, int& kp) {
+  if (kFastK) {
+    row = x >> 4;
+    kp = x & 15;
+  } else {
+    row = x & 127;
+    kp = x >> 7;
+  }
+}
+
+// A[m][k] values of k-tile k0 as bf16 pairs (zero outside M x [.., ke))
+template <class AV>
+__device__ __forceinline__ void load_a(const AV& A, int m0, int k0, int M, int ke, int tid, uint32_t (&r)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int mm, kp;
+    tile_pair<AV::kColFast>(tid + q * NT, mm, kp);
+    const int gm = m0 + mm, gk = k0 + 2 * kp;
+    float2 v = make_float2(0.f, 0.f);
+    if (gm < M) {
+      if constexpr (AV::kColFast) {
+        if (gk + 1 < ke) v = A.at2c(gm, gk);
+        else if (gk < ke) v.x = A.at(gm, gk);
+      } else {
+        if (gk < ke) v.x = A.at(gm, gk);
+        if (gk + 1 < ke) v.y = A.at(gm, gk + 1);
+      }
+    }
+    r[q] = pack_bf16(v.x, v.y);
+  }
+}
+
+// B[k][n] values of k-tile k0 as bf16 pairs along k, for the [n][k] tile
+template <class BV>
+__device__ __forceinline__ void load_b(const BV& B, int n0, int k0, int N, int ke, int tid, uint32_t (&r)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int nn, kp;
+    tile_pair<!BV::kColFast>(tid + q * NT, nn, kp);
+    const int gn = n0 + nn, gk = k0 + 2 * kp;
+    float2 v = make_float2(0.f, 0.f);
+    if (gn < N) {
+      if constexpr (!BV::kColFast) {
+        if (gk + 1 < ke) v = B.at2r(gk, gn);
+        else if (gk < ke) v.x = B.at(gk, gn);
+      } else {
+        if (gk < ke) v.x = B.at(gk, gn);
+        if (gk + 1 < ke) v.y = B.at(gk + 1, gn);
+      }
+    }
+    r[q] = pack_bf16(v.x, v.y);
+  }
+}
+
+// C[M][N] = A[M][K] . B[K][N] over the K range of blockIdx.z.  Mlim / Klim
+// (device, may be null) lower M / K below the launch's bounds.
 template <class AV, class BV>
 __global__ void __launch_bounds__(NT) gemm_kernel(AV A, BV B, int M, int N, int K, int kchunk, float* C, int ldc,
                                                   Epi e, const int* Mlim, const int* Klim) {
-  __shared__ __align__(16) float As[BK][BM];
-  __shared__ __align__(16) float Bs[BK][BN];
+  __shared__ __align__(16) uint32_t As[2][BM][LDS / 2];
+  __shared__ __align__(16) uint32_t Bs[2][BN][LDS / 2];
   if (Mlim) M = min(M, *Mlim);
   if (Klim) K = min(K, *Klim);
-  const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, t4 = lane & 3;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kb = blockIdx.z * kchunk;
   const int ke = min(K, kb + kchunk);
   if (m0 >= M || (e.atomic && kb >= ke)) return;  // block-uniform
-  float acc[8][8];
+  float acc[4][4][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int x = 0; x < 4; ++x) acc[i][j][x] = 0.f;
 
+  uint32_t ra[8], rb[8];
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int mm, kp;
+      tile_pair<AV::kColFast>(tid + q * NT, mm, kp);
+      As[buf][mm][kp] = ra[q];
+      int nn, kq;
+      tile_pair<!BV::kColFast>(tid + q * NT, nn, kq);
+      Bs[buf][nn][kq] = rb[q];
+    }
+  };
+  load_a(A, m0, kb, M, ke, tid, ra);
+  load_b(B, n0, kb, N, ke, tid, rb);
+  stage(0);
+  __syncthreads();
+  int buf = 0;
   for (int k0 = kb; k0 < ke; k0 += BK) {
-#pragma unroll
-    for (int q = 0; q < (BM * BK) / NT; ++q) {
-      const int x = tid + q * NT;
-      int mm, kk;
-      if constexpr (AV::kColFast) { mm = x / BK; kk = x % BK; } else { kk = x / BM; mm = x % BM; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < ke) ? A.at(gm, gk) : 0.f;
+    const bool more = k0 + BK < ke;
+    if (more) {
+      load_a(A, m0, k0 + BK, M, ke, tid, ra);
+      load_b(B, n0, k0 + BK, N, ke, tid, rb);
     }
 #pragma unroll
-    for (int q = 0; q < (BN * BK) / NT; ++q) {
-      const int x = tid + q * NT;
-      int kk, nn;
-      if constexpr (BV::kColFast) { kk = x / BN; nn = x % BN; } else { nn = x / BK; kk = x % BK; }
-      const int gk = k0 + kk, gn = n0 + nn;
-      Bs[kk][nn] = (gk < ke && gn < N) ? B.at(gk, gn) : 0.f;
+    for (int ks = 0; ks < 2; ++ks) {
+      uint32_t af[4][4], bfr[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+        ldsm_x4(&As[buf][wm * 64 + mi * 16 + (lane & 15)][ks * 8 + (lane >> 4) * 4], af[mi][0], af[mi][1],
+                af[mi][2], af[mi][3]);
+#pragma unroll
+      for (int np = 0; np < 2; ++np)
+        ldsm_x4(&Bs[buf][wn * 32 + (2 * np + (lane >> 4)) * 8 + (lane & 7)][ks * 8 + ((lane >> 3) & 1) * 4],
+                bfr[2 * np][0], bfr[2 * np][1], bfr[2 * np + 1][0], bfr[2 * np + 1][1]);
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni][0], bfr[ni][1]);
     }
+    if (more) stage(buf ^ 1);
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 4 + 64]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4 + 64]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+    buf ^= 1;
   }
 
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int m = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
-    if (m >= M) continue;
+  for (int mi = 0; mi < 4; ++mi)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int n = n0 + tx * 4 + (j & 3) + (j >> 2) * 64;
-      if (n >= N) continue;
-      float* dst = C + (size_t)m * ldc + n;
-      float v = acc[i][j];
-      if (e.atomic) {
-        atomicAdd(dst, v);
-        continue;
-      }
-      if (e.bias) v += __ldg(e.bias + n);
-      if (e.relu) v = fmaxf(v, 0.f);
-      if (e.gate && !(__ldg(e.gate + (size_t)m * ldc + n) > 0.f)) v = 0.f;
-      *dst = v;
+    for (int rr = 0; rr < 2; ++rr) {
+      const int m = m0 + wm * 64 + mi * 16 + g + 8 * rr;
+      if (m >= M) continue;
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+        for (int ee = 0; ee < 2; ++ee) {
+          const int n = n0 + wn * 32 + ni * 8 + 2 * t4 + ee;
+          if (n >= N) continue;
+          float* dst = C + (size_t)m * ldc + n;
+          float v = acc[mi][ni][2 * rr + ee];
+          if (e.atomic) {
+            atomicAdd(dst, v);
+            continue;
+          }
+          if (e.bias) v += __ldg(e.bias + n);
+          if (e.relu) v = fmaxf(v, 0.f);
+          if (e.gate && !(__ldg(e.gate + (size_t)m * ldc + n) > 0.f)) v = 0.f;
+          *dst = v;
+        }
     }
-  }
 }
 
 template <class AV, class BV>
@@ -436,24 +563,32 @@ __global__ void scatter_rows_kernel(const float* __restrict__ E, const uint32_t*
 
 inline unsigned blocks_for(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
+// log2 of a channel count (32 or 128: the views index taps by shifts)
+inline int log2_ch(int c) {
+  int l = 0;
+  while ((1 << l) < c) ++l;
+  return l;
+}
+
 }  // namespace
 
 cudaError_t conv_fwd(const float* X, int Ci, const float* W, int Co, const Packed& pk, float* Y, const Epi& e,
                      cudaStream_t s) {
-  return run_gemm(Im2col{X, pk.rinfo, Ci}, DenseT{W, 3 * Ci}, pk.Tmax, Co, 3 * Ci, Y, Co, e, 1, s, pk.T);
+  return run_gemm(Im2col{X, pk.rinfo, log2_ch(Ci)}, DenseT{W, 3 * Ci}, pk.Tmax, Co, 3 * Ci, Y, Co, e, 1, s, pk.T);
 }
 
 cudaError_t conv_dw(const float* dY, int Co, const float* X, int Ci, const Packed& pk, float* dW, int nsm,
                     cudaStream_t s) {
   Epi e;
   e.atomic = true;
-  return run_gemm(DenseT{dY, Co}, Im2col{X, pk.rinfo, Ci}, Co, 3 * Ci, pk.Tmax, dW, 3 * Ci, e,
+  return run_gemm(DenseT{dY, Co}, Im2col{X, pk.rinfo, log2_ch(Ci)}, Co, 3 * Ci, pk.Tmax, dW, 3 * Ci, e,
                   splits_for(Co, 3 * Ci, pk.Tmax, nsm), s, nullptr, pk.T);
 }
 
 cudaError_t conv_dx(const float* dY, int Co, const float* W, int Ci, const Packed& pk, float* dX, const Epi& e,
                     cudaStream_t s) {
-  return run_gemm(Shift{dY, pk.rinfo, Co}, WTap{W, Co, Ci}, pk.Tmax, Ci, 3 * Co, dX, Ci, e, 1, s, pk.T);
+  return run_gemm(Shift{dY, pk.rinfo, log2_ch(Co)}, WTap{W, log2_ch(Co), Ci}, pk.Tmax, Ci, 3 * Co, dX, Ci, e, 1, s,
+                  pk.T);
 }
 
 cudaError_t lin_fwd(const float* P, int Ci, const float* Wl, int Co, int B, float* E, const Epi& e, cudaStream_t s) {

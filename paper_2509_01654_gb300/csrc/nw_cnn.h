@@ -66,8 +66,10 @@ struct Epi {
   bool atomic = false;
 };
 
-// The network's matrix products (float32, tiled on the CUDA cores).  W is
-// [Co][3][Ci], Wl is [Co][Ci]; activations of a packed batch have pk.T rows.
+// The network's matrix products: bf16 tensor-core tiles, operands rounded
+// to bf16 (nearest even) as they are loaded, float32 accumulation.  W is
+// [Co][3][Ci], Wl is [Co][Ci]; Ci and Co of a convolution are powers of
+// two; activations of a packed batch have pk.T rows.
 //   conv_fwd: Y[T][Co]  = im2col(X[T][Ci]) . W^T            (epilogue e)
 //   conv_dw:  dW[Co][3Ci] += dY^T . im2col(X)               (split over rows, atomic)
 //   conv_dx:  dX[T][Ci] = sum_tap shift_tap(dY) . W[.][tap]  (col2im folded in; epilogue e)

@@ -1,9 +1,12 @@
 """GPU parity of the learned candidate proposal (include/nw_proposal.h)
 against the CPU oracle (oracle/proposal.py):
 
-* forward embeddings and the loss gradient: float32 kernels against the
-  float64 definition, relative tolerance 1e-4 (a sum of at most 384 float32
-  products per output and float32 atomics in the weight gradients);
+* forward embeddings and the loss gradient: the bf16 tensor-core products
+  against the oracle's bf16 mode (the same operands rounded the same way,
+  exact products), relative tolerance 1e-3: float32 accumulation of at most
+  384 products per output, float32 atomics in the weight gradients, and the
+  rare operand that float32 and float64 round to different bf16 neighbours;
+  and against the float64 definition within the rounding's few percent;
 * quantisation: bit-exact (both sides divide and round in float32);
 * the dot-product top-C: bit-exact (integer dot products, exact in the
   tensor cores' float32 accumulation), with ties, ragged tails, fewer rows
@@ -63,9 +66,11 @@ def test_forward_matches_oracle(ctx, seed):
     m.set_params(flat)
     assert np.array_equal(m.get_params(), flat)
     got = m.embed(d)
-    want = PR.forward(flat.astype(np.float64), w, 9)
+    want = PR.forward(flat.astype(np.float64), w, 9, bf16=True)
     err = np.abs(got - want).max() / max(1e-6, np.abs(want).max())
-    assert err < 1e-4, err
+    assert err < 1e-3, err
+    exact = PR.forward(flat.astype(np.float64), w, 9)
+    assert np.abs(got - exact).max() / np.abs(exact).max() < 3e-2
 
 
 def test_gradient_matches_oracle(ctx):
@@ -80,14 +85,17 @@ def test_gradient_matches_oracle(ctx):
     pj[:5] = pi[:5]  # self pairs
     y = g.uniform(-1, 1, M)
     loss, grad = m.loss_grad(d, pi, pj, y.astype(np.float32))
-    want_loss, want_grad = PR.loss_and_grad(flat.astype(np.float64), w, 9, pi, pj, y.astype(np.float32))
-    assert abs(loss - want_loss) <= 1e-4 * abs(want_loss)
+    want_loss, want_grad = PR.loss_and_grad(flat.astype(np.float64), w, 9, pi, pj, y.astype(np.float32), bf16=True)
+    assert abs(loss - want_loss) <= 1e-3 * abs(want_loss)
+    _, exact_grad = PR.loss_and_grad(flat.astype(np.float64), w, 9, pi, pj, y.astype(np.float32))
     o = 0
     for name, shape in PR.param_shapes(9):
         n = int(np.prod(shape))
         a, b = grad[o:o + n].astype(np.float64), want_grad[o:o + n]
         rel = np.linalg.norm(a - b) / max(1e-12, np.linalg.norm(b))
-        assert rel < 1e-4, (name, rel)
+        assert rel < 1e-3, (name, rel)
+        c = exact_grad[o:o + n]
+        assert np.linalg.norm(a - c) / max(1e-12, np.linalg.norm(c)) < 5e-2, name
         o += n
 
 

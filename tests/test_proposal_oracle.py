@@ -142,6 +142,58 @@ def test_gradient_against_finite_differences():
     assert checked >= 18
 
 
+def test_bf16_rounding_is_nearest_even():
+    import torch
+    u = 2.0 ** -8  # half the spacing of bfloat16 just above 1
+    # ties go to the even neighbour; 65,280 = 255 * 2^8 has 8 significant bits
+    x = torch.tensor([1 + u, 1 + 3 * u, -(1 + u), 1 + 1.5 * u, 3.0, 65280.0, 65408.0], dtype=torch.float64)
+    want = [1.0, 1 + 4 * u, -1.0, 1 + 2 * u, 3.0, 65280.0, 65536.0]
+    assert PR._bf16(x).tolist() == want
+
+
+def test_bf16_products_match_autograd_on_representable_operands():
+    # On operands bfloat16 holds exactly the rounding is the identity, so
+    # the bf16 functions' forward and hand-written gradients must equal the
+    # plain operations and their autograd gradients.
+    import torch
+    F = torch.nn.functional
+    Conv, Lin = PR._bf16_funcs()
+    g = np.random.default_rng(4)
+
+    def rep(*shape):  # multiples of 1/16 in [-2, 2]: exact in bfloat16
+        return torch.tensor(g.integers(-32, 33, shape) / 16.0, dtype=torch.float64)
+
+    x, W, b = rep(3, 5, 7), rep(4, 3, 5), rep(4)
+    gy = rep(3, 4, 7)
+    args = [t.clone().requires_grad_(True) for t in (x, W, b)]
+    Conv.apply(*args).backward(gy)
+    ref = [t.clone().requires_grad_(True) for t in (x, W, b)]
+    F.conv1d(ref[0], ref[1].permute(0, 2, 1), ref[2], padding=1).backward(gy)
+    assert torch.equal(Conv.apply(x, W, b), F.conv1d(x, W.permute(0, 2, 1), b, padding=1))
+    for a, r in zip(args, ref):
+        assert torch.allclose(a.grad, r.grad, rtol=0, atol=1e-12)
+
+    p, Wl, bl, ge = rep(6, 5), rep(3, 5), rep(3), rep(6, 3)
+    args = [t.clone().requires_grad_(True) for t in (p, Wl, bl)]
+    Lin.apply(*args).backward(ge)
+    ref = [t.clone().requires_grad_(True) for t in (p, Wl, bl)]
+    (ref[0] @ ref[1].T + ref[2]).backward(ge)
+    for a, r in zip(args, ref):
+        assert torch.allclose(a.grad, r.grad, rtol=0, atol=1e-12)
+
+
+def test_bf16_forward_within_rounding_of_float64():
+    # each product's operands carry a relative error of at most 2^-8 after
+    # rounding; through three convolutions and the linear map the outputs
+    # stay within a few percent of the float64 definition
+    w = synth.make_uniform_length_words(60, 9, 1.0, 0, 12, seed=8)
+    flat = np.random.default_rng(9).normal(0.0, 0.2, PR.param_count(9))
+    a = PR.forward(flat, w, 9)
+    b = PR.forward(flat, w, 9, bf16=True)
+    rel = np.abs(a - b).max() / np.abs(a).max()
+    assert 0 < rel < 3e-2, rel
+
+
 def test_adam_first_step_closed_form():
     g = np.array([0.5, -2.0, 1e-3, 0.0])
     th = np.array([1.0, 1.0, 1.0, 1.0])
