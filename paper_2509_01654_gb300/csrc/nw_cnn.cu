@@ -14,18 +14,17 @@ namespace cnn {
 namespace {
 
 // ---------------------------------------------------------------------------
-// operand views: element (r, c) of a logical matrix.  kColFast: consecutive
-// c are adjacent in memory (the tile loader then walks c fastest).  A view
-// whose pairs (c, c + 1) (at2c) or (r, r + 1) (at2r) are adjacent reads
-// them with one 8-byte load; channel counts are powers of two.
+// operand views: element (r, c) of a logical matrix, read four at a time
+// along the view's contiguous axis: kColFast views give (r, c .. c + 3),
+// the others (r .. r + 3, c).  Contiguous extents are multiples of four and
+// rows start 16-byte aligned; channel counts are powers of two.
 
 struct Dense {  // row-major
   const float* p;
   int ld;
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ float at(int r, int c) const { return __ldg(p + (size_t)r * ld + c); }
-  __device__ __forceinline__ float2 at2c(int r, int c) const {
-    return __ldg(reinterpret_cast<const float2*>(p + (size_t)r * ld + c));
+  __device__ __forceinline__ float4 vec4(int r, int c) const {
+    return __ldg(reinterpret_cast<const float4*>(p + (size_t)r * ld + c));
   }
 };
 
@@ -33,9 +32,8 @@ struct DenseT {  // transpose of a row-major matrix
   const float* p;
   int ld;
   static constexpr bool kColFast = false;
-  __device__ __forceinline__ float at(int r, int c) const { return __ldg(p + (size_t)c * ld + r); }
-  __device__ __forceinline__ float2 at2r(int r, int c) const {
-    return __ldg(reinterpret_cast<const float2*>(p + (size_t)c * ld + r));
+  __device__ __forceinline__ float4 vec4(int r, int c) const {
+    return __ldg(reinterpret_cast<const float4*>(p + (size_t)c * ld + r));
   }
 };
 
@@ -46,20 +44,12 @@ struct Im2col {
   const int* rinfo;
   int lg;  // log2 Ci
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ const float* row(int t, int k) const {
+  __device__ __forceinline__ float4 vec4(int t, int k) const {
     const int tap = k >> lg;
     const int info = __ldg(rinfo + t);
     const int pos = (info >> 8) + tap - 1;
-    if (pos < 0 || pos >= (info & 255)) return nullptr;
-    return X + ((size_t)(t + tap - 1) << lg) + (k & ((1 << lg) - 1));
-  }
-  __device__ __forceinline__ float at(int t, int k) const {
-    const float* q = row(t, k);
-    return q ? __ldg(q) : 0.f;
-  }
-  __device__ __forceinline__ float2 at2c(int t, int k) const {  // k even: one tap
-    const float* q = row(t, k);
-    return q ? __ldg(reinterpret_cast<const float2*>(q)) : make_float2(0.f, 0.f);
+    if (pos < 0 || pos >= (info & 255)) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return __ldg(reinterpret_cast<const float4*>(X + ((size_t)(t + tap - 1) << lg) + (k & ((1 << lg) - 1))));
   }
 };
 
@@ -70,20 +60,12 @@ struct Shift {
   const int* rinfo;
   int lg;  // log2 Co
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ const float* row(int t, int k) const {
+  __device__ __forceinline__ float4 vec4(int t, int k) const {
     const int tap = k >> lg;
     const int info = __ldg(rinfo + t);
     const int pos = (info >> 8) - tap + 1;
-    if (pos < 0 || pos >= (info & 255)) return nullptr;
-    return dY + ((size_t)(t - tap + 1) << lg) + (k & ((1 << lg) - 1));
-  }
-  __device__ __forceinline__ float at(int t, int k) const {
-    const float* q = row(t, k);
-    return q ? __ldg(q) : 0.f;
-  }
-  __device__ __forceinline__ float2 at2c(int t, int k) const {
-    const float* q = row(t, k);
-    return q ? __ldg(reinterpret_cast<const float2*>(q)) : make_float2(0.f, 0.f);
+    if (pos < 0 || pos >= (info & 255)) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return __ldg(reinterpret_cast<const float4*>(dY + ((size_t)(t - tap + 1) << lg) + (k & ((1 << lg) - 1))));
   }
 };
 
@@ -92,32 +74,39 @@ struct WTap {
   const float* W;
   int lgCo, Ci;
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ float at(int k, int ch) const {
+  __device__ __forceinline__ float4 vec4(int k, int ch) const {
     const int tap = k >> lgCo, o = k & ((1 << lgCo) - 1);
-    return __ldg(W + ((size_t)o * 3 + tap) * Ci + ch);
-  }
-  __device__ __forceinline__ float2 at2c(int k, int ch) const {
-    const int tap = k >> lgCo, o = k & ((1 << lgCo) - 1);
-    return __ldg(reinterpret_cast<const float2*>(W + ((size_t)o * 3 + tap) * Ci + ch));
+    return __ldg(reinterpret_cast<const float4*>(W + ((size_t)o * 3 + tap) * Ci + ch));
   }
 };
 
 // bf16 tensor-core tiles: 128 x 128 outputs per block of 8 warps (2 x 4,
 // 64 x 32 each, m16n8k16 products with float32 accumulation), K in steps of
-// 32 through two shared buffers.  Operands are rounded to bf16 (nearest
-// even) as they are staged; a shared row holds 32 values plus 8 of padding,
-// so the eight 16-byte rows of an ldmatrix fall in distinct banks.
+// 32 through two shared buffers.  Each operand tile is staged in its
+// memory's orientation -- [m][k] / [n][k] when K is the contiguous axis,
+// [k][m] / [k][n] otherwise (read back with ldmatrix .trans) -- by 16-byte
+// loads rounded to bf16 (nearest even).  Shared rows are padded (40 or 136
+// values) so that the eight 16-byte rows of an ldmatrix fall in distinct
+// banks.
 constexpr int BM = 128, BN = 128, BK = 32, NT = 256;
-constexpr int LDS = BK + 8;
+constexpr int LDK = BK + 8;    // row of a [m][k] tile
+constexpr int LDM = BM + 8;    // row of a [k][m] tile
+constexpr int kTileHalfs = BM * LDK > BK * LDM ? BM * LDK : BK * LDM;
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // lo in the low half
-  return *reinterpret_cast<const uint32_t*>(&v);
+__device__ __forceinline__ uint2 pack4_bf16(float4 v) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
 }
 
 __device__ __forceinline__ void ldsm_x4(const void* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(const void* p, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                : "r"(a));
 }
@@ -130,70 +119,36 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// thread tid's 8 pairs of a 128 x 32 tile: (row, k pair); the fast index
-// follows the view's memory order so that a warp's loads are contiguous
-template <bool kFastK>
-__device__ __forceinline__ void tile_pair(int x, int& row, int& kp) {
-  if (kFastK) {
-    row = x >> 4;
-    kp = x & 15;
-  } else {
-    row = x & 127;
-    kp = x >> 7;
-  }
-}
-
-// A[m][k] values of k-tile k0 as bf16 pairs (zero outside M x [.., ke))
-template <class AV>
-__device__ __forceinline__ void load_a(const AV& A, int m0, int k0, int M, int ke, int tid, uint32_t (&r)[8]) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    int mm, kp;
-    tile_pair<AV::kColFast>(tid + q * NT, mm, kp);
-    const int gm = m0 + mm, gk = k0 + 2 * kp;
-    float2 v = make_float2(0.f, 0.f);
-    if (gm < M) {
-      if constexpr (AV::kColFast) {
-        if (gk + 1 < ke) v = A.at2c(gm, gk);
-        else if (gk < ke) v.x = A.at(gm, gk);
-      } else {
-        if (gk < ke) v.x = A.at(gm, gk);
-        if (gk + 1 < ke) v.y = A.at(gm, gk + 1);
-      }
+// One operand's 128 x 32 tile (outer index o over 128, k over 32).  KFast:
+// the memory is contiguous along k (vectors (o, k .. k + 3)), staged [o][k];
+// else along o (vectors (o .. o + 3, k)), staged [k][o].  Thread tid holds
+// vectors tid + 256 q, q < 4.  at(o, k) is the view's vec4 at logical
+// (outer, k) for A, (k, outer) for B.
+template <bool KFast>
+struct TileMap {
+  __device__ __forceinline__ static void pos(int x, int& o, int& k) {
+    if (KFast) {
+      o = x >> 3;
+      k = (x & 7) * 4;
+    } else {
+      k = x >> 5;
+      o = (x & 31) * 4;
     }
-    r[q] = pack_bf16(v.x, v.y);
   }
-}
-
-// B[k][n] values of k-tile k0 as bf16 pairs along k, for the [n][k] tile
-template <class BV>
-__device__ __forceinline__ void load_b(const BV& B, int n0, int k0, int N, int ke, int tid, uint32_t (&r)[8]) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    int nn, kp;
-    tile_pair<!BV::kColFast>(tid + q * NT, nn, kp);
-    const int gn = n0 + nn, gk = k0 + 2 * kp;
-    float2 v = make_float2(0.f, 0.f);
-    if (gn < N) {
-      if constexpr (!BV::kColFast) {
-        if (gk + 1 < ke) v = B.at2r(gk, gn);
-        else if (gk < ke) v.x = B.at(gk, gn);
-      } else {
-        if (gk < ke) v.x = B.at(gk, gn);
-        if (gk + 1 < ke) v.y = B.at(gk + 1, gn);
-      }
-    }
-    r[q] = pack_bf16(v.x, v.y);
-  }
-}
+  __device__ __forceinline__ static int off(int o, int k) { return KFast ? o * LDK + k : k * LDM + o; }
+};
 
 // C[M][N] = A[M][K] . B[K][N] over the K range of blockIdx.z.  Mlim / Klim
 // (device, may be null) lower M / K below the launch's bounds.
 template <class AV, class BV>
 __global__ void __launch_bounds__(NT) gemm_kernel(AV A, BV B, int M, int N, int K, int kchunk, float* C, int ldc,
                                                   Epi e, const int* Mlim, const int* Klim) {
-  __shared__ __align__(16) uint32_t As[2][BM][LDS / 2];
-  __shared__ __align__(16) uint32_t Bs[2][BN][LDS / 2];
+  constexpr bool kAK = AV::kColFast;   // A contiguous along k
+  constexpr bool kBK = !BV::kColFast;  // B contiguous along k
+  using MA = TileMap<kAK>;
+  using MB = TileMap<kBK>;
+  __shared__ __align__(16) __nv_bfloat16 As[2][kTileHalfs];
+  __shared__ __align__(16) __nv_bfloat16 Bs[2][kTileHalfs];
   if (Mlim) M = min(M, *Mlim);
   if (Klim) K = min(K, *Klim);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -210,40 +165,58 @@ __global__ void __launch_bounds__(NT) gemm_kernel(AV A, BV B, int M, int N, int 
 #pragma unroll
       for (int x = 0; x < 4; ++x) acc[i][j][x] = 0.f;
 
-  uint32_t ra[8], rb[8];
-  auto stage = [&](int buf) {
+  float4 ra[4], rb[4];
+  auto load = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int mm, kp;
-      tile_pair<AV::kColFast>(tid + q * NT, mm, kp);
-      As[buf][mm][kp] = ra[q];
-      int nn, kq;
-      tile_pair<!BV::kColFast>(tid + q * NT, nn, kq);
-      Bs[buf][nn][kq] = rb[q];
+    for (int q = 0; q < 4; ++q) {
+      int o, k;
+      MA::pos(tid + q * NT, o, k);
+      ra[q] = (m0 + o < M && k0 + k < ke) ? A.vec4(m0 + o, k0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      MB::pos(tid + q * NT, o, k);
+      rb[q] = (n0 + o < N && k0 + k < ke) ? B.vec4(k0 + k, n0 + o) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
-  load_a(A, m0, kb, M, ke, tid, ra);
-  load_b(B, n0, kb, N, ke, tid, rb);
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int o, k;
+      MA::pos(tid + q * NT, o, k);
+      *reinterpret_cast<uint2*>(&As[buf][MA::off(o, k)]) = pack4_bf16(ra[q]);
+      MB::pos(tid + q * NT, o, k);
+      *reinterpret_cast<uint2*>(&Bs[buf][MB::off(o, k)]) = pack4_bf16(rb[q]);
+    }
+  };
+  load(kb);
   stage(0);
   __syncthreads();
   int buf = 0;
+  const int q8 = lane >> 3, r8 = lane & 7;
   for (int k0 = kb; k0 < ke; k0 += BK) {
     const bool more = k0 + BK < ke;
-    if (more) {
-      load_a(A, m0, k0 + BK, M, ke, tid, ra);
-      load_b(B, n0, k0 + BK, N, ke, tid, rb);
-    }
+    if (more) load(k0 + BK);
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
       uint32_t af[4][4], bfr[4][2];
 #pragma unroll
-      for (int mi = 0; mi < 4; ++mi)
-        ldsm_x4(&As[buf][wm * 64 + mi * 16 + (lane & 15)][ks * 8 + (lane >> 4) * 4], af[mi][0], af[mi][1],
-                af[mi][2], af[mi][3]);
+      for (int mi = 0; mi < 4; ++mi) {
+        const int mb = wm * 64 + mi * 16;
+        if (kAK)
+          ldsm_x4(&As[buf][MA::off(mb + (lane & 15), ks * 16 + (lane >> 4) * 8)], af[mi][0], af[mi][1], af[mi][2],
+                  af[mi][3]);
+        else
+          ldsm_x4_t(&As[buf][MA::off(mb + ((q8 & 1) << 3), ks * 16 + r8 + ((q8 >> 1) << 3))], af[mi][0], af[mi][1],
+                    af[mi][2], af[mi][3]);
+      }
 #pragma unroll
-      for (int np = 0; np < 2; ++np)
-        ldsm_x4(&Bs[buf][wn * 32 + (2 * np + (lane >> 4)) * 8 + (lane & 7)][ks * 8 + ((lane >> 3) & 1) * 4],
-                bfr[2 * np][0], bfr[2 * np][1], bfr[2 * np + 1][0], bfr[2 * np + 1][1]);
+      for (int np = 0; np < 2; ++np) {
+        const int nb = wn * 32 + np * 16;
+        if (kBK)
+          ldsm_x4(&Bs[buf][MB::off(nb + (lane >> 4) * 8 + r8, ks * 16 + ((lane >> 3) & 1) * 8)], bfr[2 * np][0],
+                  bfr[2 * np][1], bfr[2 * np + 1][0], bfr[2 * np + 1][1]);
+        else
+          ldsm_x4_t(&Bs[buf][MB::off(nb + ((q8 >> 1) << 3), ks * 16 + r8 + ((q8 & 1) << 3))], bfr[2 * np][0],
+                    bfr[2 * np][1], bfr[2 * np + 1][0], bfr[2 * np + 1][1]);
+      }
 #pragma unroll
       for (int mi = 0; mi < 4; ++mi)
 #pragma unroll
@@ -284,6 +257,8 @@ template <class AV, class BV>
 cudaError_t run_gemm(AV A, BV B, int M, int N, int K, float* C, int ldc, const Epi& e, int splits, cudaStream_t s,
                      const int* Mlim = nullptr, const int* Klim = nullptr) {
   if (M <= 0 || N <= 0) return cudaSuccess;
+  // the operands are read in 16-byte vectors along their contiguous axes
+  if ((AV::kColFast ? K : M) % 4 != 0 || (BV::kColFast ? N : K) % 4 != 0) return cudaErrorInvalidValue;
   const int gx = (N + BN - 1) / BN, gy = (M + BM - 1) / BM;
   int kchunk = K;
   int gz = 1;
