@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20
 # workload, from ncu dram__bytes_read.sum + dram__bytes_write.sum (one pass,
 # profiles/traffic_exhaustive_600k_words.md); valid while the kernel sources
 # hash to kernel_sha
-TRAFFIC = {"kernel_sha": "b50e01893571cc54", "bytes_per_step": 442.5e6}
+TRAFFIC = {"kernel_sha": "ac55343567321b45", "bytes_per_step": 441.9e6}
 
 
 def kernel_sha() -> str:
@@ -472,7 +472,7 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
     t0 = time.perf_counter()
     losses = model.train(d, steps=args.proposal_steps, nbr=ex_i, **train_cfg)
     train_s = time.perf_counter() - t0
-    res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (128, 256)}
+    res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (256, 512)}
     # candidates without a network: the C words nearest in length order (stable by index)
     order = np.argsort(w.lengths, kind="stable")
     pos = np.empty(n, dtype=np.int64)
@@ -515,7 +515,7 @@ def main():
                     help="dictionaries of the batched-launch measurement (0 skips it)")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the substitution-matrix and normalised-ranking measurements")
-    ap.add_argument("--proposal-steps", type=int, default=3000,
+    ap.add_argument("--proposal-steps", type=int, default=20000,
                     help="training steps of the learned-proposal measurement (0 skips it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
