@@ -113,6 +113,14 @@ nw_status nw_quantize_embeddings(nw_ctx *ctx, const float *E, uint32_t n, int8_t
 nw_status nw_dot_topk(nw_ctx *ctx, const int8_t *q, const int32_t *bias, uint32_t n, uint32_t C, uint32_t *idx,
                       int32_t *val, uint32_t flags);
 
+/* Rectangular form: for every row i of qa (na x 64 int8), the C rows j of
+ * qb (nb x 64 int8) with the largest q_a[i] . q_b[j] + bias[j] (bias: nb
+ * int32 or NULL for 0), higher first and lower j first on equal values; no
+ * row is skipped (qa and qb are different sets).  Rows with fewer than C
+ * columns end in (UINT32_MAX, INT32_MIN).  Same arithmetic as nw_dot_topk. */
+nw_status nw_dot_topk_cross(nw_ctx *ctx, const int8_t *qa, uint32_t na, const int8_t *qb, const int32_t *bias,
+                            uint32_t nb, uint32_t C, uint32_t *idx, int32_t *val, uint32_t flags);
+
 /* Exact rescoring: for every word i of `dict`, Algorithm 1's score against
  * each candidate cand[i * C + r] (original indices; UINT32_MAX entries are
  * skipped; candidates of a row must be distinct and differ from i), and the
@@ -131,6 +139,22 @@ typedef struct {
  * best (as nw_rescore_topk).  `prof` may be NULL. */
 nw_status nw_proposal_topk(nw_model *model, nw_dict *dict, uint32_t C, uint32_t k, uint32_t *nbr_idx,
                            int16_t *nbr_score, nw_proposal_profile *prof, uint32_t flags);
+
+/* Queries through the proposal: the nq query words (codes and offsets as
+ * nw_query) get their k best words of `dict` (raw score, higher first, lower
+ * index on ties; UINT32_MAX / INT16_MIN past the candidates).  The
+ * dictionary's embeddings are quantised once and kept on the device while
+ * neither the dictionary nor the model's parameters change; each call
+ * embeds the queries, quantises them on the dictionary's scale (features
+ * beyond it clamp to +-127), takes each query's C dictionary words with the
+ * largest q_query . q_j + bias_j, and rescores those exactly (Algorithm 1).
+ * The scores are exact; the lists equal nw_query's when C >= the
+ * dictionary's size.  1 <= C <= NW_MAX_CANDIDATES, 1 <= k <= NW_MAX_K;
+ * NW_ERANGE when query scores may not fit int16; NW_RANK_NORMALISED is
+ * refused. */
+nw_status nw_proposal_query(nw_model *model, nw_dict *dict, const uint8_t *qcodes, const uint32_t *qoffsets,
+                            uint32_t nq, uint32_t C, uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score,
+                            uint32_t flags);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,8 @@ the CUDA path is checked against, written plainly:
   takes these decisions in).
 * ``dot_topk``: each row's C best other rows by the exact integer value
   q_i . q_j + bias_j, higher first, lower index on ties.
+* ``dot_topk_cross``: the same over two sets: each row of one set's C best
+  rows of the other (no row skipped).
 * ``rescore_topk``: the k best of each row's candidates by Algorithm 1's
   score (the oracle's C code), higher first, lower index on ties.
 * ``recall_at_k``: strict and tie-aware overlap of two sets of lists.
@@ -257,6 +259,30 @@ def dot_topk(q, C: int, rows=None, bias=None):
             sel = jj[keep][order]
             idx[b0 + r, :sel.size] = sel
             dot[b0 + r, :sel.size] = D[r, sel]
+    return idx, dot
+
+
+def dot_topk_cross(qa, qb, C: int, bias=None, rows=None):
+    """(idx uint32 (r, C), val int32 (r, C)): for each row i of qa, the C
+    rows j of qb with the largest exact qa_i . qb_j + bias_j (bias 0 when
+    None), lower j first on ties; every j is eligible (qa and qb are two
+    sets); missing entries (qb has fewer than C rows) are
+    (MISSING_IDX, MISSING_DOT)."""
+    qa = np.asarray(qa, dtype=np.int64)
+    qb = np.asarray(qb, dtype=np.int64).reshape(-1, OUT)
+    nb = qb.shape[0]
+    b = np.zeros(nb, dtype=np.int64) if bias is None else np.asarray(bias, dtype=np.int64)
+    rows = np.arange(qa.shape[0]) if rows is None else np.asarray(rows, dtype=np.int64)
+    idx = np.full((rows.size, C), MISSING_IDX, dtype=np.uint32)
+    dot = np.full((rows.size, C), MISSING_DOT, dtype=np.int32)
+    jj = np.arange(nb)
+    for b0 in range(0, rows.size, 256):
+        rb = rows[b0:b0 + 256]
+        D = qa[rb] @ qb.T + b[None, :]  # exact in int64
+        for r in range(rb.size):
+            order = np.lexsort((jj, -D[r]))[:C]
+            idx[b0 + r, :order.size] = order
+            dot[b0 + r, :order.size] = D[r, order]
     return idx, dot
 
 

@@ -20,7 +20,9 @@ nw_status load_impl(nw_ctx* c, const uint8_t* codes, const uint32_t* offsets, ui
                     const nw_scoring& sc, const ShiftedScoring& ss, const std::vector<uint16_t>* tab, uint32_t flags,
                     nw_dict** out) {
   const nw_scoring* scoring = &sc;
+  static std::atomic<uint64_t> next_serial{1};
   nw_dict* d = new nw_dict();
+  d->serial = next_serial.fetch_add(1);
   d->ctx = c;
   d->sc = sc;
   d->ss = ss;

@@ -345,18 +345,19 @@ __device__ int warp_keep_value_ge(uint64_t* buf, int cnt, int t, int lane) {
 }
 
 // Bits k (value k = 2 nb + e of a lane's row group: column 8 nb + 2 t4 + e of
-// the tile) whose column j is a real column other than the row i itself; a
-// row past n has none.
-__device__ __forceinline__ uint32_t valid_cols(uint32_t i, uint32_t tile, uint32_t n, int t4) {
-  if (i >= n) return 0u;
+// the tile) whose column j is a real column (j < nB) other than the row i
+// itself when rows and columns are one set (self); a row past nA has none.
+__device__ __forceinline__ uint32_t valid_cols(uint32_t i, uint32_t tile, uint32_t nA, uint32_t nB, bool self,
+                                               int t4) {
+  if (i >= nA) return 0u;
   const uint32_t j0 = tile * kTileCols;
   uint32_t v = 0xffffu;
-  if (j0 + kTileCols > n || (i >> 6) == tile) {
+  if (j0 + kTileCols > nB || (self && (i >> 6) == tile)) {
     v = 0u;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const uint32_t j = j0 + (uint32_t)((k >> 1) * 8 + 2 * t4 + (k & 1));
-      if (j < n && j != i) v |= 1u << k;
+      if (j < nB && !(self && j == i)) v |= 1u << k;
     }
   }
   return v;
@@ -368,12 +369,29 @@ __device__ __forceinline__ int pow2_at_least(int x) {
   return p;
 }
 
-// biasf: the columns' biases as floats (exact: |bias| <= 2^23), zero-padded to
-// a multiple of kTileCols entries
-__global__ void __launch_bounds__(kThreads, 2)
-    dot_topk_kernel(const __nv_bfloat16* __restrict__ Q, const float* __restrict__ biasf, uint32_t n, uint32_t C,
-                    uint64_t* __restrict__ buf, uint32_t* __restrict__ out_idx, int32_t* __restrict__ out_val,
-                    uint32_t* __restrict__ err) {
+// One launch: rows QA[0, nA) against columns QB[0, nB) (both in the padded,
+// swizzled bf16 layout); biasf holds the columns' biases as floats (exact:
+// |bias| <= 2^23), zero-padded to a multiple of kTileCols entries.  self:
+// rows and columns are one set, and row i skips column i.
+struct DotArgs {
+  const __nv_bfloat16* QA;
+  const __nv_bfloat16* QB;
+  const float* biasf;
+  uint32_t nA, nB, C;
+  bool self;
+  uint64_t* buf;  // nA x kCap keys
+  uint32_t* out_idx;
+  int32_t* out_val;
+  uint32_t* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) {
+  const float* __restrict__ biasf = P.biasf;
+  const uint32_t C = P.C;
+  uint64_t* __restrict__ buf = P.buf;
+  uint32_t* __restrict__ out_idx = P.out_idx;
+  int32_t* __restrict__ out_val = P.out_val;
+  uint32_t* __restrict__ err = P.err;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* sB = smem;
   float* sBias = reinterpret_cast<float*>(smem + kOffBias);
@@ -387,8 +405,10 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t row0 = blockIdx.x * (uint32_t)kRowsPerCta;
-  const unsigned char* Qb = reinterpret_cast<const unsigned char*>(Q);
-  const uint32_t ntiles = (n + kTileCols - 1) / kTileCols, npad = ntiles * kTileCols;
+  const unsigned char* Qa = reinterpret_cast<const unsigned char*>(P.QA);
+  const unsigned char* Qb = reinterpret_cast<const unsigned char*>(P.QB);
+  const uint32_t ntiles = (P.nB + kTileCols - 1) / kTileCols;
+  const uint32_t npadA = (P.nA + kTileCols - 1) / kTileCols * kTileCols;
 
   // column tile u into ring stage u % kStages: its rows (already swizzled and
   // zero-padded in global memory) and biases, counted on the stage's full barrier
@@ -403,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   unsigned char* sA = reinterpret_cast<unsigned char*>(sSort);
   for (int x = tid; x < kRowsPerCta * 8; x += kThreads) {
     const uint32_t g = row0 + (uint32_t)(x >> 3);
-    cp_async16(smem_u32(sA + x * 16), Qb + (size_t)(g < npad ? g : 0) * kRowBytes + (x & 7) * 16, g < npad);
+    cp_async16(smem_u32(sA + x * 16), Qa + (size_t)(g < npadA ? g : 0) * kRowBytes + (x & 7) * 16, g < npadA);
   }
   cp_async_commit();
   for (int r = tid; r < kRowsPerCta; r += kThreads) {
@@ -539,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 if (acc[s][nb][2 * h + e] > thr[s][h]) part[nb & 3] |= 1u << (2 * nb + e);
             m[h] = (part[0] | part[1]) | (part[2] | part[3]);
             const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
-            if (m[h] != 0u) m[h] &= valid_cols(i, tile, n, t4);
+            if (m[h] != 0u) m[h] &= valid_cols(i, tile, P.nA, P.nB, P.self, t4);
           }
         }
         uint32_t pos[2];
@@ -652,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int l = 0; l < kRowsPerWarp; ++l) {
     const int lr = warp * kRowsPerWarp + l;
     const uint32_t i = row0 + (uint32_t)lr;
-    if (i >= n) break;
+    if (i >= P.nA) break;
     const int cnt = sCnt[lr];
     const uint64_t* rb = buf + (size_t)i * kCap;
     const uint64_t kmin = cnt > (int)C ? warp_select_kth(rb, cnt, (int)C, hMine, lane) : 1ull;
@@ -746,33 +766,52 @@ size_t bias_pad(uint32_t n) { return ((size_t)n + kTileCols - 1) / kTileCols * k
 
 size_t dot_topk_qb_bytes(uint32_t n) { return bias_pad(n) * kRowBytes; }
 
-size_t dot_topk_buffer_bytes(uint32_t n) {
-  return (size_t)n * kCap * sizeof(uint64_t) + bias_pad(n) * sizeof(float) + 16;
+size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB) {
+  return (size_t)nA * kCap * sizeof(uint64_t) + bias_pad(nB) * sizeof(float) + 16;
 }
 
-uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t n) {
-  return reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(buf + (size_t)n * kCap) + bias_pad(n));
+uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB) {
+  return reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(buf + (size_t)nA * kCap) + bias_pad(nB));
+}
+
+cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
+                          uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* val,
+                          uint32_t* err, cudaStream_t s) {
+  if (nA == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(dot_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
+  if (e != cudaSuccess) return e;
+  DotArgs P;
+  P.QA = QA;
+  P.QB = QB;
+  P.biasf = reinterpret_cast<float*>(buf + (size_t)nA * kCap);  // after the append buffers (16-byte aligned)
+  P.nA = nA;
+  P.nB = nB;
+  P.C = C;
+  P.self = self;
+  P.buf = buf;
+  P.out_idx = idx;
+  P.out_val = val;
+  P.err = err;
+  const uint32_t npad = (uint32_t)bias_pad(nB);
+  bias_float_kernel<<<(npad + 255) / 256 + (npad == 0), 256, 0, s>>>(biasB, nB, npad, const_cast<float*>(P.biasf));
+  const unsigned grid = (nA + kRowsPerCta - 1) / kRowsPerCta;
+  dot_topk_kernel<<<grid, kThreads, kSmemTotal, s>>>(P);
+  return cudaGetLastError();
 }
 
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
                      uint32_t* idx, int32_t* val, uint32_t* err, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(dot_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
-  if (e != cudaSuccess) return e;
-  float* biasf = reinterpret_cast<float*>(buf + (size_t)n * kCap);  // after the append buffers (16-byte aligned)
-  const uint32_t npad = (uint32_t)bias_pad(n);
-  bias_float_kernel<<<(npad + 255) / 256, 256, 0, s>>>(bias, n, npad, biasf);
-  const unsigned grid = (n + kRowsPerCta - 1) / kRowsPerCta;
-  dot_topk_kernel<<<grid, kThreads, kSmemTotal, s>>>(Qb, biasf, n, C, buf, idx, val, err);
-  return cudaGetLastError();
+  return dot_topk_rect(Qb, n, Qb, bias, n, C, true, buf, idx, val, err, s);
 }
 
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,
-                     int32_t* bias, float* scale, cudaStream_t s) {
+                     int32_t* bias, float* scale, cudaStream_t s, bool given_scale) {
   const size_t count = (size_t)bias_pad(n) * kDim;
-  cudaError_t e = cudaMemsetAsync(amax_bits, 0, sizeof(unsigned int), s);
-  if (e != cudaSuccess) return e;
-  if (n) absmax_kernel<<<1024, 256, 0, s>>>(E, n, amax_bits);
+  if (!given_scale) {
+    cudaError_t e = cudaMemsetAsync(amax_bits, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    if (n) absmax_kernel<<<1024, 256, 0, s>>>(E, n, amax_bits);
+  }
   quantize_kernel<<<(unsigned)((count + 255) / 256 + (count == 0)), 256, 0, s>>>(E, n, (uint32_t)bias_pad(n),
                                                                                    amax_bits, q, qb, bias, scale);
   return cudaGetLastError();

@@ -91,6 +91,7 @@ struct nw_dict {
   DevBuf d_segs;
   bool subst = false;  // scored with a full similarity matrix (d_tab)
   DevBuf d_tab;        // kTabDim x kTabDim s'+ table
+  uint64_t serial = 0;  // unique per loaded dictionary (caches keyed on it)
 };
 
 namespace {

@@ -93,6 +93,29 @@ __global__ void __launch_bounds__(128) rescore_kernel(const PairsParams P, const
   score[p] = pair_dispatch(lb, P, pa, la, pb);
 }
 
+// one thread per candidate of a query: Algorithm 1 between query i of set
+// Q and dictionary word cand[i * C + r] of set D, the shorter word streamed
+// (QD: query streamed, dictionary word in registers; DQ: the reverse)
+__global__ void __launch_bounds__(128) cross_rescore_kernel(const prop::CrossParams X, const uint32_t* __restrict__ cand,
+                                                            uint32_t C, int32_t* __restrict__ score) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (uint64_t)X.nq * C) return;
+  const uint32_t i = (uint32_t)(p / C);
+  const uint32_t j = cand[p];
+  if (j == 0xffffffffu) {
+    score[p] = INT32_MIN;
+    return;
+  }
+  if (j >= X.nd) {
+    atomicOr(X.QD.err, kErrInput);
+    score[p] = INT32_MIN;
+    return;
+  }
+  const uint32_t ri = __ldg(X.q_rank + i), rj = __ldg(X.d_rank + j);
+  const int li = __ldg(X.q_slen + ri), lj = __ldg(X.d_slen + rj);
+  score[p] = li <= lj ? pair_dispatch(lj, X.QD, ri, li, rj) : pair_dispatch(li, X.DQ, rj, lj, ri);
+}
+
 constexpr int kSelPerLane = NW_MAX_CANDIDATES / 32;
 
 // one warp per row: repeated warp-wide maximum over (score, reversed index) keys
@@ -144,6 +167,13 @@ cudaError_t rescore(const PairsParams& P, const uint32_t* cand, uint32_t C, int3
   const uint64_t m = (uint64_t)P.n * C;
   if (m == 0) return cudaSuccess;
   rescore_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(P, cand, C, score);
+  return cudaGetLastError();
+}
+
+cudaError_t cross_rescore(const CrossParams& X, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s) {
+  const uint64_t m = (uint64_t)X.nq * C;
+  if (m == 0) return cudaSuccess;
+  cross_rescore_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(X, cand, C, score);
   return cudaGetLastError();
 }
 

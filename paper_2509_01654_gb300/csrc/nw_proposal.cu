@@ -31,6 +31,10 @@ struct nw_model {
   DevBuf pi, pj, target, score16;
   // proposal path
   DevBuf Eall, Qb, qbias, topbuf, cand, cand_dot, cand_score, nbr;
+  // queries against a dictionary: its quantised rows, kept while the
+  // dictionary (serial) and the parameters (gen) are unchanged
+  uint64_t gen = 1, prep_serial = 0, prep_gen = 0;
+  DevBuf dQb, dqbias, prep_small, qQb, qcand, qcand_dot, qscore, qbuf;
 };
 
 namespace {
@@ -51,7 +55,8 @@ void model_free_buffers(nw_model* M) {
   DevBuf* bufs[] = {&M->params, &M->grads, &M->adam_m, &M->adam_v, &M->small, &M->widx, &M->len, &M->off,
                     &M->rinfo, &M->rword, &M->codes, &M->X0, &M->Y1, &M->Y2, &M->Y3, &M->P, &M->E, &M->dE, &M->dP, &M->dYa,
                     &M->dYb, &M->dX0, &M->pi, &M->pj, &M->target, &M->score16, &M->Eall, &M->Qb,
-                    &M->qbias, &M->topbuf, &M->cand, &M->cand_dot, &M->cand_score, &M->nbr};
+                    &M->qbias, &M->topbuf, &M->cand, &M->cand_dot, &M->cand_score, &M->nbr,
+                    &M->dQb, &M->dqbias, &M->prep_small, &M->qQb, &M->qcand, &M->qcand_dot, &M->qscore, &M->qbuf};
   for (DevBuf* b : bufs) ctx_free(c, *b);
 }
 
@@ -108,28 +113,28 @@ cnn::Packed packed(nw_model* M, int Bw, int Tmax) {
   return pk;
 }
 
-cnn::WordSrc word_src(const nw_dict* d, const uint32_t* widx) {
+cnn::WordSrc word_src(const WordSet& ws, uint32_t shift, const uint32_t* widx) {
   cnn::WordSrc s;
   s.widx = widx;
-  s.rank = d->ws.rank.as<uint32_t>();
-  s.slen = d->ws.slen.as<uint8_t>();
-  s.aoff = d->ws.aoff.as<uint32_t>();
-  s.a_enc = d->ws.a_enc.as<uint32_t>();
-  s.shift = d->ss.shift;
-  s.n = d->ws.n;
+  s.rank = ws.rank.as<uint32_t>();
+  s.slen = ws.slen.as<uint8_t>();
+  s.aoff = ws.aoff.as<uint32_t>();
+  s.a_enc = ws.a_enc.as<uint32_t>();
+  s.shift = shift;
+  s.n = ws.n;
   return s;
 }
 
-// embeddings of Bw words (M->widx), packed into at most Tmax rows, into M->E
-nw_status forward(nw_model* M, const nw_dict* d, int Bw, int Tmax, cudaStream_t s) {
+// embeddings of Bw words of `ws` (M->widx), packed into at most Tmax rows, into M->E
+nw_status forward(nw_model* M, const WordSet& ws, uint32_t shift, int Bw, int Tmax, cudaStream_t s) {
   nw_ctx* c = M->ctx;
   const cnn::Layout& L = M->L;
   const float* W = fptr(M->params);
   const cnn::Packed pk = packed(M, Bw, Tmax);
   cnn::PackBufs pb{M->len.as<int>(), M->off.as<int>(), rows_ptr(M), M->rinfo.as<int>(), M->rword.as<int>(),
                    M->codes.as<int32_t>()};
-  NW_CK(cnn::pack_words(word_src(d, M->widx.as<uint32_t>()), Bw, Tmax, W + L.emb, pb, fptr(M->X0), err_ptr(M),
-                        M->alphabet, s));
+  NW_CK(cnn::pack_words(word_src(ws, shift, M->widx.as<uint32_t>()), Bw, Tmax, W + L.emb, pb, fptr(M->X0),
+                        err_ptr(M), M->alphabet, s));
   cnn::Epi e;
   e.relu = true;
   e.bias = W + L.b1;
@@ -143,6 +148,10 @@ nw_status forward(nw_model* M, const nw_dict* d, int Bw, int Tmax, cudaStream_t 
   el.bias = W + L.bl;
   NW_CK(cnn::lin_fwd(fptr(M->P), cnn::kCh, W + L.Wl, cnn::kOut, Bw, fptr(M->E), el, s));
   return NW_OK;
+}
+
+nw_status forward(nw_model* M, const nw_dict* d, int Bw, int Tmax, cudaStream_t s) {
+  return forward(M, d->ws, d->ss.shift, Bw, Tmax, s);
 }
 
 // gradient of the pair loss (pairs = word slots 2p, 2p + 1; targets in M->target) into M->grads
@@ -225,10 +234,10 @@ uint64_t splitmix64_next(uint64_t& st) {
 // embeddings of all n words into M->Eall (n x 64): chunks of consecutive
 // sorted positions (words of similar length), each at most kMaxRowsPerPass
 // packed rows, scattered back to original order
-nw_status embed_all(nw_model* M, nw_dict* d, cudaStream_t s) {
+nw_status embed_all(nw_model* M, const WordSet& ws, uint32_t shift, cudaStream_t s) {
   nw_ctx* c = M->ctx;
-  const uint32_t n = d->ws.n;
-  const Buckets& bk = d->ws.bk;
+  const uint32_t n = ws.n;
+  const Buckets& bk = ws.bk;
   // chunk boundaries on the host from the bucket table
   std::vector<std::pair<uint32_t, uint32_t>> chunks;  // (first sorted position, words)
   int max_words = 1;
@@ -256,12 +265,14 @@ nw_status embed_all(nw_model* M, nw_dict* d, cudaStream_t s) {
   NW_TRY(ctx_ensure(c, M->Eall, sizeof(float) * std::max<size_t>(1, (size_t)n * cnn::kOut), "embeddings"));
   for (const auto& ch : chunks) {
     const int Bw = (int)ch.second;
-    NW_CK(cnn::take(d->ws.perm.as<uint32_t>(), ch.first, Bw, M->widx.as<uint32_t>(), s));
-    NW_TRY(forward(M, d, Bw, kMaxRowsPerPass, s));
+    NW_CK(cnn::take(ws.perm.as<uint32_t>(), ch.first, Bw, M->widx.as<uint32_t>(), s));
+    NW_TRY(forward(M, ws, shift, Bw, kMaxRowsPerPass, s));
     NW_CK(cnn::scatter_rows(fptr(M->E), M->widx.as<uint32_t>(), Bw, fptr(M->Eall), s));
   }
   return NW_OK;
 }
+
+nw_status embed_all(nw_model* M, nw_dict* d, cudaStream_t s) { return embed_all(M, d->ws, d->ss.shift, s); }
 
 // the dictionary's encoded words as the pairs kernel reads them
 PairsParams pairs_params(const nw_dict* d, uint32_t* err) {
@@ -379,6 +390,7 @@ nw_status nw_model_set_params(nw_model* M, const float* params, uint32_t flags) 
   NW_CK(cudaMemsetAsync(M->adam_v.p, 0, M->adam_v.bytes, M->stream));
   NW_CK(cudaMemsetAsync(step_ptr(M), 0, sizeof(uint32_t), M->stream));
   M->steps_done = 0;
+  ++M->gen;
   NW_CK(cudaStreamSynchronize(M->stream));
   return NW_OK;
 }
@@ -435,6 +447,7 @@ nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, co
   if (!(cfg->clip_norm >= 0.f) || !(cfg->lr_final >= 0.f)) return set_err(c, NW_EINVAL, "clip_norm, lr_final >= 0");
   if (nbr && knb == 0) return set_err(c, NW_EINVAL, "neighbour lists need knb >= 1");
   if (cfg->steps == 0) return NW_OK;
+  ++M->gen;  // the parameters change from here on
   NW_TRY(check_model_dict(M, d));
   const bool dev = flags & NW_DEVICE_PTRS;
   cudaStream_t s = M->stream;
@@ -658,6 +671,176 @@ nw_status nw_rescore_topk(nw_dict* d, const uint32_t* cand, uint32_t C, uint32_t
     NW_TRY(copy_out(c, nbr_score, out_s, (size_t)n * k, false, s));
   }
   NW_TRY(check_device_flags(c, small.as<uint32_t>()));
+  return NW_OK;
+}
+
+nw_status nw_dot_topk_cross(nw_ctx* c, const int8_t* qa, uint32_t na, const int8_t* qb, const int32_t* bias,
+                           uint32_t nb, uint32_t C, uint32_t* idx, int32_t* val, uint32_t flags) {
+  NW_ENTER(c);
+  if (!qa || !idx || !val || (nb && !qb)) return set_err(c, NW_EINVAL, "null pointer argument");
+  if (C == 0 || C > NW_MAX_CANDIDATES) return set_err(c, NW_EINVAL, "C must be in [1, %d]", NW_MAX_CANDIDATES);
+  if (na == 0) return NW_OK;
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = c->stream;
+  const size_t outc = (size_t)na * C;
+  DevBuf dqa, dqb, db, qab, qbb, buf, oi, od;
+  struct Free {
+    nw_ctx* c;
+    DevBuf* b[8];
+    ~Free() {
+      for (DevBuf* x : b) ctx_free(c, *x);
+    }
+  } fr{c, {&dqa, &dqb, &db, &qab, &qbb, &buf, &oi, &od}};
+  const int8_t* sa = qa;
+  const int8_t* sb = qb;
+  const int32_t* sbias = bias;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, dqa, (size_t)na * NW_EMBED_DIM, "quantised rows"));
+    NW_TRY(copy_in(c, dqa.as<int8_t>(), qa, (size_t)na * NW_EMBED_DIM, false, s));
+    sa = dqa.as<int8_t>();
+    if (nb) {
+      NW_TRY(ctx_alloc(c, dqb, (size_t)nb * NW_EMBED_DIM, "quantised columns"));
+      NW_TRY(copy_in(c, dqb.as<int8_t>(), qb, (size_t)nb * NW_EMBED_DIM, false, s));
+      sb = dqb.as<int8_t>();
+    }
+  }
+  // the kernel reads biases in 16-byte chunks: host or unaligned device biases are copied
+  if (bias && nb && (!dev || (reinterpret_cast<uintptr_t>(bias) & 15u))) {
+    NW_TRY(ctx_alloc(c, db, sizeof(int32_t) * nb, "biases"));
+    NW_CK(cudaMemcpyAsync(db.p, bias, sizeof(int32_t) * nb, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          s));
+    sbias = db.as<int32_t>();
+  }
+  NW_TRY(ctx_alloc(c, qab, prop::dot_topk_qb_bytes(na), "bf16 rows"));
+  NW_TRY(ctx_alloc(c, qbb, std::max<size_t>(128, prop::dot_topk_qb_bytes(nb)), "bf16 columns"));
+  NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(na, nb), "candidate buffers"));
+  uint32_t* out_i = idx;
+  int32_t* out_v = val;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, oi, sizeof(uint32_t) * outc, "candidate lists"));
+    NW_TRY(ctx_alloc(c, od, sizeof(int32_t) * outc, "candidate lists"));
+    out_i = oi.as<uint32_t>();
+    out_v = od.as<int32_t>();
+  }
+  uint32_t* derr = prop::dot_topk_err_word(buf.as<uint64_t>(), na, nb);
+  NW_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
+  NW_CK(prop::widen(sa, na, qab.as<__nv_bfloat16>(), s));
+  NW_CK(prop::widen(sb, nb, qbb.as<__nv_bfloat16>(), s));
+  NW_CK(prop::dot_topk_rect(qab.as<__nv_bfloat16>(), na, qbb.as<__nv_bfloat16>(), sbias, nb, C, false,
+                            buf.as<uint64_t>(), out_i, out_v, derr, s));
+  NW_TRY(check_device_flags(c, derr));
+  if (!dev) {
+    NW_TRY(copy_out(c, idx, out_i, outc, false, s));
+    NW_TRY(copy_out(c, val, out_v, outc, false, s));
+  }
+  NW_CK(cudaStreamSynchronize(s));
+  return NW_OK;
+}
+
+nw_status nw_proposal_query(nw_model* M, nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, uint32_t nq,
+                            uint32_t C, uint32_t k, uint32_t* nbr_idx, int16_t* nbr_score, uint32_t flags) {
+  if (!M || !d) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  if (flags & NW_RANK_NORMALISED) return set_err(c, NW_EINVAL, "queries rank by raw score only");
+  if (nq == 0) return NW_OK;
+  if (!qoffsets || !nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null pointer argument");
+  if (C == 0 || C > NW_MAX_CANDIDATES) return set_err(c, NW_EINVAL, "C must be in [1, %d]", NW_MAX_CANDIDATES);
+  if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  NW_TRY(check_model_dict(M, d));
+  const uint32_t n = d->ws.n;
+  const bool dev = flags & NW_DEVICE_PTRS;
+  cudaStream_t s = M->stream;
+
+  WordSet q;
+  struct QFree {
+    nw_ctx* c;
+    WordSet& q;
+    ~QFree() { free_wordset(c, q); }
+  } qfree{c, q};
+  NW_TRY(ingest(c, qcodes, qoffsets, nq, d->alphabet, d->ss.shift, flags & NW_DEVICE_PTRS, q));
+  int lo = INT32_MAX, hi = INT32_MIN;
+  for (int La = 0; La < kBuckets; ++La)
+    for (int Lb = 0; Lb < kBuckets; ++Lb) {
+      if (!q.bk.count[La] || !d->ws.bk.count[Lb]) continue;
+      int l, h;
+      pair_bounds(d->sc, La, Lb, l, h);
+      lo = std::min(lo, l);
+      hi = std::max(hi, h);
+    }
+  if (n == 0) lo = hi = 0;
+  if (lo < INT16_MIN + 1 || hi > INT16_MAX) return set_err(c, NW_ERANGE, "query scores do not fit int16");
+  NW_CK(cudaStreamSynchronize(c->stream));  // the query words were uploaded on the context stream
+
+  // the dictionary's quantised rows, kept until the dictionary or the parameters change
+  unsigned int* amax = M->prep_small.p ? M->prep_small.as<unsigned int>() : nullptr;
+  if (M->prep_serial != d->serial || M->prep_gen != M->gen) {
+    M->prep_serial = 0;
+    NW_TRY(ctx_ensure(c, M->dQb, std::max<size_t>(128, prop::dot_topk_qb_bytes(n)), "dictionary bf16 rows"));
+    NW_TRY(ctx_ensure(c, M->dqbias, sizeof(int32_t) * std::max<size_t>(1, n), "dictionary biases"));
+    NW_TRY(ctx_ensure(c, M->prep_small, 16, "dictionary scale"));
+    amax = M->prep_small.as<unsigned int>();
+    NW_TRY(embed_all(M, d, s));
+    NW_CK(prop::quantize(fptr(M->Eall), n, amax, nullptr, M->dQb.as<__nv_bfloat16>(), M->dqbias.as<int32_t>(),
+                         nullptr, s));
+    M->prep_serial = d->serial;
+    M->prep_gen = M->gen;
+  }
+  // the queries, quantised on the dictionary's scale
+  NW_TRY(embed_all(M, q, d->ss.shift, s));
+  NW_TRY(ctx_ensure(c, M->qQb, prop::dot_topk_qb_bytes(nq), "query bf16 rows"));
+  NW_CK(prop::quantize(fptr(M->Eall), nq, amax, nullptr, M->qQb.as<__nv_bfloat16>(), nullptr, nullptr, s, true));
+
+  const size_t outc = (size_t)nq * C;
+  NW_TRY(ctx_ensure(c, M->qbuf, prop::dot_topk_buffer_bytes(nq, n), "candidate buffers"));
+  NW_TRY(ctx_ensure(c, M->qcand, sizeof(uint32_t) * outc, "candidate lists"));
+  NW_TRY(ctx_ensure(c, M->qcand_dot, sizeof(int32_t) * outc, "candidate lists"));
+  NW_TRY(ctx_ensure(c, M->qscore, sizeof(int32_t) * outc, "candidate scores"));
+  uint32_t* derr = prop::dot_topk_err_word(M->qbuf.as<uint64_t>(), nq, n);
+  NW_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
+  NW_CK(prop::dot_topk_rect(M->qQb.as<__nv_bfloat16>(), nq, M->dQb.as<__nv_bfloat16>(), M->dqbias.as<int32_t>(), n,
+                            C, false, M->qbuf.as<uint64_t>(), M->qcand.as<uint32_t>(), M->qcand_dot.as<int32_t>(),
+                            derr, s));
+  NW_CK(cudaStreamSynchronize(s));
+  NW_TRY(check_device_flags(c, derr));
+
+  // exact rescoring of (query, candidate) and the k best
+  prop::CrossParams X{};
+  X.QD = pairs_params(d, err_ptr(M));
+  X.QD.aoff = q.aoff.as<uint32_t>();
+  X.QD.a_enc = q.a_enc.as<uint32_t>();
+  X.DQ = pairs_params(d, err_ptr(M));
+  X.DQ.brec_w = q.brec_w.as<uint32_t>();
+  X.DQ.b_rec = q.b_rec.as<uint32_t>();
+  X.q_rank = q.rank.as<uint32_t>();
+  X.q_slen = q.slen.as<uint8_t>();
+  X.d_rank = d->ws.rank.as<uint32_t>();
+  X.d_slen = d->ws.slen.as<uint8_t>();
+  X.nq = nq;
+  X.nd = n;
+  DevBuf oi, os;
+  struct Free {
+    nw_ctx* c;
+    DevBuf* b[2];
+    ~Free() {
+      for (DevBuf* x : b) ctx_free(c, *x);
+    }
+  } fr{c, {&oi, &os}};
+  uint32_t* out_i = nbr_idx;
+  int16_t* out_s = nbr_score;
+  if (!dev) {
+    NW_TRY(ctx_alloc(c, oi, sizeof(uint32_t) * (size_t)nq * k, "neighbour lists"));
+    NW_TRY(ctx_alloc(c, os, sizeof(int16_t) * (size_t)nq * k, "neighbour lists"));
+    out_i = oi.as<uint32_t>();
+    out_s = os.as<int16_t>();
+  }
+  NW_CK(prop::cross_rescore(X, M->qcand.as<uint32_t>(), C, M->qscore.as<int32_t>(), s));
+  NW_CK(prop::select_topk(M->qcand.as<uint32_t>(), M->qscore.as<int32_t>(), nq, C, k, out_i, out_s, s));
+  if (!dev) {
+    NW_TRY(copy_out(c, nbr_idx, out_i, (size_t)nq * k, false, s));
+    NW_TRY(copy_out(c, nbr_score, out_s, (size_t)nq * k, false, s));
+  }
+  NW_TRY(check_err(M, s));
   return NW_OK;
 }
 

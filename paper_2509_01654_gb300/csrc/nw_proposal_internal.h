@@ -18,26 +18,52 @@ constexpr int kBiasLimit = 1 << 23;
 // Quantisation of n x 64 embeddings (see nw_quantize_embeddings): q (int8,
 // row-major, may be null), qb (the candidate kernel's bf16 rows,
 // dot_topk_qb_bytes(n), may be null), bias (int32, may be null), scale
-// (device float, may be null); amax_bits is device scratch.
+// (device float, may be null); amax_bits is device scratch.  given_scale:
+// *amax_bits already holds the largest |feature| to scale by (another set's,
+// e.g. the dictionary's for its queries; larger features clamp to +-127).
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,
-                     int32_t* bias, float* scale, cudaStream_t s);
+                     int32_t* bias, float* scale, cudaStream_t s, bool given_scale = false);
 // int8 rows (row-major) -> the candidate kernel's bf16 rows
 cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s);
 // bf16 rows: zero-padded to whole 64-row tiles, 16-byte chunks of row r
 // permuted by r & 7
 size_t dot_topk_qb_bytes(uint32_t n);
-size_t dot_topk_buffer_bytes(uint32_t n);
+// scratch of a launch over nA rows and nB columns
+size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB);
+inline size_t dot_topk_buffer_bytes(uint32_t n) { return dot_topk_buffer_bytes(n, n); }
 // the device error word inside a dot_topk buffer (zero it before a launch)
-uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t n);
-// each row's C best q_i . q_j + bias_j (bias may be null: 0); a pipeline
-// wait that runs out sets kErrWait in *err
+uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB);
+inline uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t n) { return dot_topk_err_word(buf, n, n); }
+// each row's C best q_i . q_j + bias_j over the other rows (bias may be
+// null: 0); a pipeline wait that runs out sets kErrWait in *err
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
                      uint32_t* idx, int32_t* dot, uint32_t* err, cudaStream_t s);
+// each row i of QA's C best QA_i . QB_j + biasB_j over all nB columns (self:
+// the two are one set and column i is skipped)
+cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
+                          uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* dot,
+                          uint32_t* err, cudaStream_t s);
 
 // Algorithm 1's score of (i, cand[i * C + r]) into score[i * C + r] (int32;
 // INT32_MIN for UINT32_MAX entries); out-of-range or self candidates raise
 // kErrInput.  P supplies the encoded dictionary (its pi/pj/m/out are unused).
 cudaError_t rescore(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s);
+// Words of a query set Q against a dictionary D for cross_rescore: QD reads
+// its streamed (A) words from Q and its register (B) words from D, DQ the
+// reverse; both carry D's scoring.  Ranks and lengths of either set map
+// original indices to sorted positions.
+struct CrossParams {
+  PairsParams QD, DQ;
+  const uint32_t* q_rank;
+  const uint8_t* q_slen;
+  const uint32_t* d_rank;
+  const uint8_t* d_slen;
+  uint32_t nq, nd;
+};
+// Algorithm 1's score of (query i, dictionary word cand[i * C + r]) into
+// score[i * C + r] (INT32_MIN for UINT32_MAX entries; out-of-range
+// candidates raise kErrInput)
+cudaError_t cross_rescore(const CrossParams& X, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s);
 // each row's k best (score desc, index asc) of its C scored candidates
 cudaError_t select_topk(const uint32_t* cand, const int32_t* score, uint32_t n, uint32_t C, uint32_t k,
                         uint32_t* out_idx, int16_t* out_score, cudaStream_t s);

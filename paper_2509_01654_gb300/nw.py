@@ -38,7 +38,7 @@ EXPORTED = [
     # nw_proposal.h
     "nw_model_create", "nw_model_free", "nw_model_param_count", "nw_model_get_params", "nw_model_set_params",
     "nw_model_embed", "nw_model_loss_grad", "nw_model_train", "nw_quantize_embeddings", "nw_dot_topk",
-    "nw_rescore_topk", "nw_proposal_topk",
+    "nw_rescore_topk", "nw_proposal_topk", "nw_dot_topk_cross", "nw_proposal_query",
 ]
 EMBED_DIM = 64
 MAX_CANDIDATES = 512
@@ -159,6 +159,8 @@ def load_library(path: str = LIB_PATH):
     L.nw_dot_topk.argtypes = [vp, vp, vp, u32, u32, vp, vp, u32]
     L.nw_rescore_topk.argtypes = [vp, vp, u32, u32, vp, vp, u32]
     L.nw_proposal_topk.argtypes = [vp, vp, u32, u32, vp, vp, ctypes.POINTER(ProposalProfile), u32]
+    L.nw_dot_topk_cross.argtypes = [vp, vp, u32, vp, vp, u32, u32, vp, vp, u32]
+    L.nw_proposal_query.argtypes = [vp, vp, vp, vp, u32, u32, u32, vp, vp, u32]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.nw_server_submit.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u64)]
@@ -681,6 +683,25 @@ class Model:
             self.handle, d.handle, ctypes.byref(cfg), _ptr(nbr)[0], knb, _ptr(losses)[0], 0))
         return losses[:steps]
 
+    def query(self, d: "Dictionary", qcodes, qoffsets, C: int, k: int, nbr_idx=None, nbr_score=None):
+        """(idx[nq, k], score[nq, k]) by nw_proposal_query: the query words' k best
+        dictionary words among C proposed candidates, scored exactly."""
+        if not _is_torch(qoffsets):
+            qcodes = np.ascontiguousarray(qcodes, dtype=np.uint8)
+            if qcodes.size == 0:
+                qcodes = np.zeros(1, np.uint8)
+            qoffsets = np.ascontiguousarray(qoffsets, dtype=np.uint32)
+        nq = int(qoffsets.shape[0]) - 1
+        if nbr_idx is None:
+            nbr_idx = _empty_like_kind(qoffsets if _is_torch(qoffsets) else None, (nq, k), np.uint32,
+                                       _torch_dtype("int32"))
+        if nbr_score is None:
+            nbr_score = _empty_like_kind(nbr_idx, (nq, k), np.int16, _torch_dtype("int16"))
+        _check(self.ctx.handle, load_library().nw_proposal_query(
+            self.handle, d.handle, _ptr(qcodes)[0], _ptr(qoffsets)[0], nq, C, k, _ptr(nbr_idx)[0],
+            _ptr(nbr_score)[0], _flags(qcodes, qoffsets, nbr_idx, nbr_score)))
+        return nbr_idx, nbr_score
+
     def proposal_topk(self, d: "Dictionary", C: int, k: int, nbr_idx=None, nbr_score=None):
         """(idx[n, k], score[n, k], profile dict): embed, quantise, C candidates, exact rescoring."""
         n = d.n
@@ -718,6 +739,21 @@ def dot_topk(ctx: Context, q, C: int, bias=None):
     val = _empty_like_kind(q, (n, C), np.int32, _torch_dtype("int32"))
     _check(ctx.handle, load_library().nw_dot_topk(ctx.handle, _ptr(q)[0], _ptr(bias)[0], n, C, _ptr(idx)[0],
                                                   _ptr(val)[0], _flags(q, bias, idx, val)))
+    return idx, val
+
+
+def dot_topk_cross(ctx: Context, qa, qb, C: int, bias=None):
+    """(idx uint32 [na, C], val int32 [na, C]) by nw_dot_topk_cross (host or CUDA buffers)."""
+    if not _is_torch(qa):
+        qa = np.ascontiguousarray(qa, dtype=np.int8)
+        qb = np.ascontiguousarray(qb, dtype=np.int8)
+        if bias is not None:
+            bias = np.ascontiguousarray(bias, dtype=np.int32)
+    na, nb = int(qa.shape[0]), int(qb.shape[0])
+    idx = _empty_like_kind(qa, (na, C), np.uint32, _torch_dtype("int32"))
+    val = _empty_like_kind(qa, (na, C), np.int32, _torch_dtype("int32"))
+    _check(ctx.handle, load_library().nw_dot_topk_cross(ctx.handle, _ptr(qa)[0], na, _ptr(qb)[0], _ptr(bias)[0], nb,
+                                                        C, _ptr(idx)[0], _ptr(val)[0], _flags(qa, qb, bias, idx, val)))
     return idx, val
 
 

@@ -305,3 +305,105 @@ def test_proposal_with_all_candidates_is_exact(ctx):
     idx, score, _ = m.proposal_topk(d, C=nw.MAX_CANDIDATES, k=10)
     assert np.array_equal(score, ex_s)
     assert np.array_equal(idx, ex_i)
+
+
+# ---------------------------------------------------------------------------
+# queries through the proposal (rectangular candidates, cross rescoring)
+
+@pytest.mark.parametrize("na,nb,C,levels,bias_range", [(300, 1000, 64, 127, 0), (257, 777, 32, 2, 40),
+                                                       (5, 40, 64, 5, 0), (70, 130, 16, 127, 300_000),
+                                                       (1000, 20_000, 128, 20, 0)])
+def test_dot_topk_cross_matches_oracle(ctx, na, nb, C, levels, bias_range):
+    # ragged row and column tails, ties (duplicate columns, few levels),
+    # fewer columns than C, and 20,000 columns (compaction) on sampled rows
+    g = np.random.default_rng(na + nb + C)
+    qa = g.integers(-levels, levels + 1, (na, 64)).astype(np.int8)
+    qb = g.integers(-levels, levels + 1, (nb, 64)).astype(np.int8)
+    if nb > 10:
+        qb[nb // 2] = qb[1]
+    bias = g.integers(-bias_range, bias_range + 1, nb).astype(np.int32) if bias_range else None
+    idx, val = nw.dot_topk_cross(ctx, qa, qb, C, bias=bias)
+    rows = np.arange(na) if na * nb <= 2_000_000 else synth.sample_rows(na, 64).astype(np.int64)
+    wi, wv = PR.dot_topk_cross(qa, qb, C, bias=bias, rows=rows)
+    assert np.array_equal(val[rows], wv)
+    assert np.array_equal(idx[rows], wi)
+
+
+def test_dot_topk_cross_without_columns(ctx):
+    qa = np.ones((3, 64), np.int8)
+    idx, val = nw.dot_topk_cross(ctx, qa, np.zeros((0, 64), np.int8), 4)
+    assert np.all(idx == 0xFFFFFFFF) and np.all(val == np.iinfo(np.int32).min)
+
+
+def query_set(n, alphabet, seed, lo=0, hi=14):
+    return synth.make_uniform_length_words(n, alphabet, 1.0, lo, hi, seed=seed)
+
+
+def test_proposal_query_with_every_candidate_equals_exhaustive(ctx):
+    # C >= the dictionary's size: every word is rescored, so the lists are
+    # the exhaustive query lists, ties included
+    w, d = small_dict(ctx, n=300, seed=21, lo=0, hi=12)
+    q = query_set(70, 9, seed=22)
+    m = nw.Model(ctx, 9, seed=2)
+    idx, sc = m.query(d, q.codes, q.offsets, C=300, k=10)
+    wi, ws = d.query(q.codes, q.offsets, 10)
+    assert np.array_equal(idx, wi) and np.array_equal(sc, ws)
+    import oracle
+    oi, osc = oracle.query_topk(q, w, 10, (1, -1, -1))
+    assert np.array_equal(idx, oi) and np.array_equal(sc.astype(np.int32), osc)
+
+
+def test_proposal_query_scores_exact_and_sorted(ctx):
+    import oracle
+    w, d = small_dict(ctx, n=3000, alphabet=12, seed=23, lo=1, hi=14)
+    m = nw.Model(ctx, 12, seed=3)
+    m.train(d, steps=150, batch_pairs=2048, lr=2e-3, seed=5)
+    q = query_set(200, 12, seed=24, lo=1, hi=16)
+    idx, sc = m.query(d, q.codes, q.offsets, C=64, k=10)
+    assert idx.shape == (200, 10) and not np.any(idx == 0xFFFFFFFF)
+    for r in range(q.n):
+        assert len(set(idx[r].tolist())) == 10
+        want = [oracle.score(q.word(r), w.word(int(j)), (1, -1, -1)) for j in idx[r]]
+        assert sc[r].astype(np.int64).tolist() == want
+        key = [(-int(s), int(j)) for s, j in zip(sc[r], idx[r])]
+        assert key == sorted(key)
+    # the exact top-10 score is an upper bound of every listed score
+    oi, osc = oracle.query_topk(q, w, 10, (1, -1, -1))
+    assert np.all(sc.astype(np.int32) <= osc)
+
+
+def test_proposal_query_cache_follows_parameters_and_dictionary(ctx):
+    w1, d1 = small_dict(ctx, n=400, seed=31, lo=1, hi=12)
+    w2, d2 = small_dict(ctx, n=500, seed=32, lo=1, hi=12)
+    q = query_set(50, 9, seed=33, lo=1, hi=12)
+    a = nw.Model(ctx, 9, seed=4)
+    b = nw.Model(ctx, 9, seed=5)
+    ra = a.query(d1, q.codes, q.offsets, C=16, k=5)
+    rb = b.query(d1, q.codes, q.offsets, C=16, k=5)
+    # new parameters: the cached dictionary rows are rebuilt
+    a.set_params(b.get_params())
+    ra2 = a.query(d1, q.codes, q.offsets, C=16, k=5)
+    assert np.array_equal(ra2[0], rb[0]) and np.array_equal(ra2[1], rb[1])
+    # another dictionary: the same as a fresh model's
+    r2 = a.query(d2, q.codes, q.offsets, C=16, k=5)
+    c = nw.Model(ctx, 9, seed=5)
+    r2c = c.query(d2, q.codes, q.offsets, C=16, k=5)
+    assert np.array_equal(r2[0], r2c[0]) and np.array_equal(r2[1], r2c[1])
+    assert ra[0].shape == (50, 5)
+
+
+def test_proposal_query_refusals(ctx):
+    w, d = small_dict(ctx, n=50)
+    q = query_set(4, 9, seed=1, lo=1, hi=5)
+    m = nw.Model(ctx, 9)
+    for C, k in ((0, 5), (nw.MAX_CANDIDATES + 1, 5), (16, 0)):
+        with pytest.raises(nw.NwError) as e:
+            m.query(d, q.codes, q.offsets, C=C, k=k)
+        assert e.value.status == nw.NW_EINVAL
+    bad = q.codes.copy()
+    bad[0] = 9  # a code past the alphabet
+    with pytest.raises(nw.NwError) as e:
+        m.query(d, bad, q.offsets, C=8, k=3)
+    assert e.value.status == nw.NW_EINVAL
+    m.query(d, q.codes, q.offsets, C=8, k=3)  # still usable
+

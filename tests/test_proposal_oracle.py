@@ -287,6 +287,39 @@ def test_dot_topk_brute_force(n, C, levels):
     assert np.array_equal(i3, bi3) and np.array_equal(d3, bd3)
 
 
+def test_dot_topk_cross_hand_case():
+    # values qa_i . qb_j + bias_j worked by hand
+    qa = np.zeros((2, 64), np.int8)
+    qb = np.zeros((4, 64), np.int8)
+    qa[0, :2] = (1, 0)
+    qa[1, :2] = (0, 1)
+    qb[:, :2] = [(2, 0), (1, 1), (0, 3), (1, 1)]
+    bias = np.array([0, 1, -1, 1], np.int32)
+    # row 0: (2, 2, -1, 2) -> j 0, 1, 3 tie at 2 (lower j first), then 2
+    # row 1: (0, 2, 2, 2) -> j 1, 2, 3 tie at 2, then 0
+    idx, val = PR.dot_topk_cross(qa, qb, 3, bias=bias)
+    assert idx.tolist() == [[0, 1, 3], [1, 2, 3]]
+    assert val.tolist() == [[2, 2, 2], [2, 2, 2]]
+    idx, val = PR.dot_topk_cross(qa, qb, 6, bias=bias)  # more than nb: missing tail
+    assert idx[0, 4:].tolist() == [PR.MISSING_IDX] * 2 and val[1, 4:].tolist() == [PR.MISSING_DOT] * 2
+    assert idx[0, :4].tolist() == [0, 1, 3, 2] and val[1, :4].tolist() == [2, 2, 2, 0]
+
+
+@pytest.mark.parametrize("n,C", [(40, 5), (33, 31), (9, 12)])
+def test_dot_topk_cross_with_itself_is_dot_topk_plus_self(n, C):
+    # rows against their own set: dropping column i from the C + 1 best
+    # gives the C best other rows
+    g = np.random.default_rng(n)
+    q = g.integers(-2, 3, (n, 64)).astype(np.int8)
+    bias = g.integers(-3, 4, n).astype(np.int32)
+    ci, cv = PR.dot_topk_cross(q, q, C + 1, bias=bias)
+    wi, wv = PR.dot_topk(q, C, bias=bias)
+    for i in range(n):
+        keep = ci[i] != i
+        got_i, got_v = ci[i][keep][:C], cv[i][keep][:C]
+        assert np.array_equal(got_i, wi[i]) and np.array_equal(got_v, wv[i])
+
+
 def test_rescore_topk_hand_case(oracle_mod):
     w = synth.WordList.from_lists([[1, 2, 3], [1, 2, 3], [1, 2], [4, 5, 6], [1, 2, 4]])
     sc = (1, -1, -1)
