@@ -473,6 +473,7 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
     losses = model.train(d, steps=args.proposal_steps, nbr=ex_i, **train_cfg)
     train_s = time.perf_counter() - t0
     res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (256, 512)}
+    queries = proposal_queries(args, model, d, k, recall_vs_exact)
     # candidates without a network: the C words nearest in length order (stable by index)
     order = np.argsort(w.lengths, kind="stable")
     pos = np.empty(n, dtype=np.int64)
@@ -496,8 +497,50 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
                   "loss_last_100": round(float(np.mean(losses[-100:])), 5), **train_cfg},
         "exhaustive_ms": round(exhaustive_ms, 3),
         "by_candidates": res,
+        "queries": queries,
         "ablation": ablation,
     }
+
+
+def proposal_queries(args, model, d, k, recall):
+    """A batch of serving-style query words (lengths U[1, 30]) against the
+    dictionary: exhaustive nw_query against nw_proposal_query, host buffers
+    both ways (each call copies its queries in and its lists out)."""
+    import numpy as np
+    import torch
+    from paper_2509_01654_gb300 import synth
+    q = synth.serving_queries(4096, seed=11)
+    reps = max(3, args.steps)
+
+    def timed(fn):
+        fn()  # warm-up (the proposal's first call also quantises the dictionary)
+        ts = []
+        out = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return statistics.median(ts), out
+
+    ex_ms, (ex_i, ex_s) = timed(lambda: d.query(q.codes, q.offsets, k))
+    out = {"workload": f"{q.n} query words, lengths U[1,30], against the dictionary; top-{k}",
+           "exhaustive_ms": round(ex_ms, 3), "exhaustive_queries_per_s": round(q.n / ex_ms * 1e3, 1)}
+    for C in (256, 512):
+        ms, (pi, ps) = timed(lambda: model.query(d, q.codes, q.offsets, C, k))
+        st, tt = recall(np.asarray(ex_i).view(np.uint32), np.asarray(ex_s), np.asarray(pi).view(np.uint32),
+                        np.asarray(ps))
+        by_len = {}
+        lens = np.asarray(q.lengths)
+        for lo, hi in ((1, 10), (11, 20), (21, 25), (26, 30)):  # the dictionary's words are at most 25 long
+            sel = (lens >= lo) & (lens <= hi)
+            _, t_sel = recall(np.asarray(ex_i).view(np.uint32)[sel], np.asarray(ex_s)[sel],
+                              np.asarray(pi).view(np.uint32)[sel], np.asarray(ps)[sel])
+            by_len[f"{lo}-{hi}"] = round(t_sel, 4)
+        out[str(C)] = {"ms": round(ms, 3), "queries_per_s": round(q.n / ms * 1e3, 1), "recall_at_10": round(st, 4),
+                       "recall_at_10_tie_aware": round(tt, 4), "tie_aware_by_query_length": by_len,
+                       "speedup_vs_exhaustive": round(ex_ms / ms, 2)}
+    return out
 
 
 def main():

@@ -26,6 +26,7 @@
 // key: the comparison is strict, and the final pass, an exact select and
 // sort of each row's buffer, gives exact lists.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <float.h>
 #include <stdint.h>
@@ -373,18 +374,24 @@ __device__ __forceinline__ int pow2_at_least(int x) {
 // swizzled bf16 layout); biasf holds the columns' biases as floats (exact:
 // |bias| <= 2^23), zero-padded to a multiple of kTileCols entries.  self:
 // rows and columns are one set, and row i skips column i.
+// With splits > 1, CTA (x, y) sweeps only the column tiles [y * tps, (y +
+// 1) * tps) and writes its rows' C best keys, sorted, to part (a merge
+// kernel then takes each row's C best of its splits' lists).
 struct DotArgs {
   const __nv_bfloat16* QA;
   const __nv_bfloat16* QB;
   const float* biasf;
   uint32_t nA, nB, C;
   bool self;
-  uint64_t* buf;  // nA x kCap keys
+  uint32_t splits, tps;
+  uint64_t* buf;   // (nA x splits) x kCap keys
+  uint64_t* part;  // (nA x splits) x C keys when splits > 1
   uint32_t* out_idx;
   int32_t* out_val;
   uint32_t* err;
 };
 
+template <bool kSplit, bool kSelf>
 __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) {
   const float* __restrict__ biasf = P.biasf;
   const uint32_t C = P.C;
@@ -407,7 +414,13 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
   const uint32_t row0 = blockIdx.x * (uint32_t)kRowsPerCta;
   const unsigned char* Qa = reinterpret_cast<const unsigned char*>(P.QA);
   const unsigned char* Qb = reinterpret_cast<const unsigned char*>(P.QB);
-  const uint32_t ntiles = (P.nB + kTileCols - 1) / kTileCols;
+  // this CTA's column tiles: global tiles tlo + [0, ntiles)
+  const uint32_t ys = kSplit ? blockIdx.y : 0u;
+  const uint32_t tall = (P.nB + kTileCols - 1) / kTileCols;
+  const uint32_t tlo = kSplit ? min(tall, ys * P.tps) : 0u;
+  const uint32_t ntiles = kSplit ? min(tall - tlo, P.tps) : tall;
+  // row i's append buffer
+  auto row_buf = [&](uint32_t i) { return buf + (kSplit ? (size_t)i * P.splits + ys : (size_t)i) * kCap; };
   const uint32_t npadA = (P.nA + kTileCols - 1) / kTileCols * kTileCols;
 
   // column tile u into ring stage u % kStages: its rows (already swizzled and
@@ -415,8 +428,9 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
   auto issue = [&](uint32_t u) {
     const uint32_t st = u % kStages;
     mbar_expect_tx(barFull + 8 * st, kTileBytes + kTileBiasBytes);
-    bulk_g2s(smem_u32(sB + st * kTileBytes), Qb + (size_t)u * kTileBytes, kTileBytes, barFull + 8 * st);
-    bulk_g2s(smem_u32(sBias + st * kTileCols), biasf + (size_t)u * kTileCols, kTileBiasBytes, barFull + 8 * st);
+    bulk_g2s(smem_u32(sB + st * kTileBytes), Qb + (size_t)(tlo + u) * kTileBytes, kTileBytes, barFull + 8 * st);
+    bulk_g2s(smem_u32(sBias + st * kTileCols), biasf + (size_t)(tlo + u) * kTileCols, kTileBiasBytes,
+             barFull + 8 * st);
   };
 
   // stage the CTA's 256 rows (zero past the padded rows) into the sort area
@@ -559,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
                 if (acc[s][nb][2 * h + e] > thr[s][h]) part[nb & 3] |= 1u << (2 * nb + e);
             m[h] = (part[0] | part[1]) | (part[2] | part[3]);
             const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
-            if (m[h] != 0u) m[h] &= valid_cols(i, tile, P.nA, P.nB, P.self, t4);
+            if (m[h] != 0u) m[h] &= valid_cols(i, tlo + tile, P.nA, P.nB, kSelf, t4);
           }
         }
         uint32_t pos[2];
@@ -585,12 +599,12 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
-            uint64_t* rb = buf + (size_t)i * kCap;
+            uint64_t* rb = row_buf(i);
             uint32_t mm = m[h], slot = pos[h];
             while (mm != 0u) {
               const int k = __ffs(mm) - 1;
               mm &= mm - 1u;
-              const uint32_t j = tile * kTileCols + (uint32_t)((k >> 1) * 8 + 2 * t4 + (k & 1));
+              const uint32_t j = (tlo + tile) * kTileCols + (uint32_t)((k >> 1) * 8 + 2 * t4 + (k & 1));
               rb[slot++] = make_key((int)stage[h * 16 + k], j);
             }
           }
@@ -616,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
         const int l = __ffs(full) - 1;
         full &= full - 1;
         const int lr = warp * kRowsPerWarp + l;
-        uint64_t* rb = buf + (size_t)(row0 + (uint32_t)lr) * kCap;
+        uint64_t* rb = row_buf(row0 + (uint32_t)lr);
         const int c = sCnt[lr];
         // A threshold t at or below the C-th best value is enough here (the
         // final pass selects exactly): t is the lower edge of the 256-bin
@@ -674,17 +688,22 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
     const uint32_t i = row0 + (uint32_t)lr;
     if (i >= P.nA) break;
     const int cnt = sCnt[lr];
-    const uint64_t* rb = buf + (size_t)i * kCap;
+    const uint64_t* rb = row_buf(i);
     const uint64_t kmin = cnt > (int)C ? warp_select_kth(rb, cnt, (int)C, hMine, lane) : 1ull;
     const int kept = warp_gather_ge(rb, cnt, kmin, sMine, lane);
     const int size = pow2_at_least(kept);
     for (int x = kept + lane; x < size; x += 32) sMine[x] = 0ull;
     __syncwarp();
     warp_bitonic_desc(sMine, size, lane);
-    for (uint32_t x = lane; x < C; x += 32) {
-      const bool have = (int)x < kept;
-      out_idx[(size_t)i * C + x] = have ? key_idx(sMine[x]) : 0xffffffffu;
-      out_val[(size_t)i * C + x] = have ? key_val(sMine[x]) : INT32_MIN;
+    if (kSplit) {
+      uint64_t* dst = P.part + ((size_t)i * P.splits + ys) * C;
+      for (uint32_t x = lane; x < C; x += 32) dst[x] = (int)x < kept ? sMine[x] : 0ull;
+    } else {
+      for (uint32_t x = lane; x < C; x += 32) {
+        const bool have = (int)x < kept;
+        out_idx[(size_t)i * C + x] = have ? key_idx(sMine[x]) : 0xffffffffu;
+        out_val[(size_t)i * C + x] = have ? key_val(sMine[x]) : INT32_MIN;
+      }
     }
     __syncwarp();
   }
@@ -699,6 +718,34 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
         atomicOr(err, kErrWait);
         break;
       }
+  }
+}
+
+// one warp per row: the C best of the row's splits' sorted lists (S x C
+// keys, 0 for missing) by the exact select, then sorted
+constexpr int kMergeWarps = 8;
+__global__ void __launch_bounds__(kMergeWarps * 32)
+    merge_splits_kernel(const uint64_t* __restrict__ part, uint32_t nA, uint32_t S, uint32_t C,
+                        uint32_t* __restrict__ out_idx, int32_t* __restrict__ out_val) {
+  __shared__ unsigned hist[kMergeWarps][256];
+  __shared__ uint64_t keep[kMergeWarps][kSel];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t i = blockIdx.x * kMergeWarps + warp;
+  if (i >= nA) return;  // warp-uniform
+  const uint64_t* keys = part + (size_t)i * S * C;
+  const int cnt = (int)(S * C);
+  // missing entries are key 0, below every real key: select among all of them
+  const uint64_t kth = warp_select_kth(keys, cnt, (int)C, hist[warp], lane);
+  const uint64_t kmin = kth ? kth : 1ull;
+  const int kept = warp_gather_ge(keys, cnt, kmin, keep[warp], lane);  // <= C
+  const int size = pow2_at_least(kept);
+  for (int x = kept + lane; x < size; x += 32) keep[warp][x] = 0ull;
+  __syncwarp();
+  warp_bitonic_desc(keep[warp], size, lane);
+  for (uint32_t x = lane; x < C; x += 32) {
+    const bool have = (int)x < kept;
+    out_idx[(size_t)i * C + x] = have ? key_idx(keep[warp][x]) : 0xffffffffu;
+    out_val[(size_t)i * C + x] = have ? key_val(keep[warp][x]) : INT32_MIN;
   }
 }
 
@@ -766,36 +813,59 @@ size_t bias_pad(uint32_t n) { return ((size_t)n + kTileCols - 1) / kTileCols * k
 
 size_t dot_topk_qb_bytes(uint32_t n) { return bias_pad(n) * kRowBytes; }
 
-size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB) {
-  return (size_t)nA * kCap * sizeof(uint64_t) + bias_pad(nB) * sizeof(float) + 16;
+// column splits of a launch over nA rows and nB columns: enough CTAs for
+// two per SM when the row blocks alone are fewer, each split at least 8
+// tiles of 64 columns
+uint32_t dot_topk_splits(uint32_t nA, uint32_t nB) {
+  const uint32_t blocks = (nA + kRowsPerCta - 1) / kRowsPerCta;
+  const uint32_t tiles = (nB + kTileCols - 1) / kTileCols;
+  const uint32_t want = (2u * 152u + blocks - 1) / std::max(blocks, 1u);
+  return std::max(1u, std::min(want, tiles / 8));
+}
+
+size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB, uint32_t C) {
+  const size_t S = dot_topk_splits(nA, nB);
+  return (size_t)nA * S * kCap * sizeof(uint64_t) + bias_pad(nB) * sizeof(float) + 16 +
+         (S > 1 ? (size_t)nA * S * C * sizeof(uint64_t) : 0);
 }
 
 uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB) {
-  return reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(buf + (size_t)nA * kCap) + bias_pad(nB));
+  const size_t S = dot_topk_splits(nA, nB);
+  return reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(buf + (size_t)nA * S * kCap) + bias_pad(nB));
 }
 
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* val,
                           uint32_t* err, cudaStream_t s) {
   if (nA == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(dot_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
+  const uint32_t S = dot_topk_splits(nA, nB);
+  const auto kernel = S > 1 ? (self ? dot_topk_kernel<true, true> : dot_topk_kernel<true, false>)
+                             : (self ? dot_topk_kernel<false, true> : dot_topk_kernel<false, false>);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
   if (e != cudaSuccess) return e;
+  const uint32_t tiles = (nB + kTileCols - 1) / kTileCols;
   DotArgs P;
   P.QA = QA;
   P.QB = QB;
-  P.biasf = reinterpret_cast<float*>(buf + (size_t)nA * kCap);  // after the append buffers (16-byte aligned)
+  P.biasf = reinterpret_cast<float*>(buf + (size_t)nA * S * kCap);  // after the append buffers (16-byte aligned)
   P.nA = nA;
   P.nB = nB;
   P.C = C;
   P.self = self;
+  P.splits = S;
+  P.tps = (tiles + S - 1) / S;
   P.buf = buf;
+  // the split lists follow the buffer's own error-word slot (err itself may live elsewhere)
+  P.part = S > 1 ? reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(dot_topk_err_word(buf, nA, nB)) + 16) : nullptr;
   P.out_idx = idx;
   P.out_val = val;
   P.err = err;
   const uint32_t npad = (uint32_t)bias_pad(nB);
   bias_float_kernel<<<(npad + 255) / 256 + (npad == 0), 256, 0, s>>>(biasB, nB, npad, const_cast<float*>(P.biasf));
-  const unsigned grid = (nA + kRowsPerCta - 1) / kRowsPerCta;
-  dot_topk_kernel<<<grid, kThreads, kSmemTotal, s>>>(P);
+  const dim3 grid((nA + kRowsPerCta - 1) / kRowsPerCta, S);
+  kernel<<<grid, kThreads, kSmemTotal, s>>>(P);
+  if (S > 1)
+    merge_splits_kernel<<<(nA + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(P.part, nA, S, C, idx, val);
   return cudaGetLastError();
 }
 

@@ -605,7 +605,7 @@ nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, const int32_t* bias, uint32_t 
     srcb = db.as<int32_t>();
   }
   NW_TRY(ctx_alloc(c, qb, prop::dot_topk_qb_bytes(n), "bf16 embeddings"));
-  NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
+  NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(n, C), "candidate buffers"));
   uint32_t* out_i = idx;
   int32_t* out_v = val;
   if (!dev) {
@@ -713,7 +713,7 @@ nw_status nw_dot_topk_cross(nw_ctx* c, const int8_t* qa, uint32_t na, const int8
   }
   NW_TRY(ctx_alloc(c, qab, prop::dot_topk_qb_bytes(na), "bf16 rows"));
   NW_TRY(ctx_alloc(c, qbb, std::max<size_t>(128, prop::dot_topk_qb_bytes(nb)), "bf16 columns"));
-  NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(na, nb), "candidate buffers"));
+  NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(na, nb, C), "candidate buffers"));
   uint32_t* out_i = idx;
   int32_t* out_v = val;
   if (!dev) {
@@ -792,7 +792,7 @@ nw_status nw_proposal_query(nw_model* M, nw_dict* d, const uint8_t* qcodes, cons
   NW_CK(prop::quantize(fptr(M->Eall), nq, amax, nullptr, M->qQb.as<__nv_bfloat16>(), nullptr, nullptr, s, true));
 
   const size_t outc = (size_t)nq * C;
-  NW_TRY(ctx_ensure(c, M->qbuf, prop::dot_topk_buffer_bytes(nq, n), "candidate buffers"));
+  NW_TRY(ctx_ensure(c, M->qbuf, prop::dot_topk_buffer_bytes(nq, n, C), "candidate buffers"));
   NW_TRY(ctx_ensure(c, M->qcand, sizeof(uint32_t) * outc, "candidate lists"));
   NW_TRY(ctx_ensure(c, M->qcand_dot, sizeof(int32_t) * outc, "candidate lists"));
   NW_TRY(ctx_ensure(c, M->qscore, sizeof(int32_t) * outc, "candidate scores"));
@@ -862,7 +862,7 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
   const size_t outc = (size_t)n * C;
   NW_TRY(ctx_ensure(c, M->Qb, prop::dot_topk_qb_bytes(n), "bf16 embeddings"));
   NW_TRY(ctx_ensure(c, M->qbias, sizeof(int32_t) * (size_t)n, "quantised biases"));
-  NW_TRY(ctx_ensure(c, M->topbuf, prop::dot_topk_buffer_bytes(n), "candidate buffers"));
+  NW_TRY(ctx_ensure(c, M->topbuf, prop::dot_topk_buffer_bytes(n, C), "candidate buffers"));
   NW_TRY(ctx_ensure(c, M->cand, sizeof(uint32_t) * outc, "candidate lists"));
   NW_TRY(ctx_ensure(c, M->cand_dot, sizeof(int32_t) * outc, "candidate lists"));
   DevBuf oi, os;

@@ -28,9 +28,11 @@ cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s
 // bf16 rows: zero-padded to whole 64-row tiles, 16-byte chunks of row r
 // permuted by r & 7
 size_t dot_topk_qb_bytes(uint32_t n);
-// scratch of a launch over nA rows and nB columns
-size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB);
-inline size_t dot_topk_buffer_bytes(uint32_t n) { return dot_topk_buffer_bytes(n, n); }
+// scratch of a launch over nA rows, nB columns and C candidates (the err
+// word must follow the returned layout: use dot_topk_err_word)
+uint32_t dot_topk_splits(uint32_t nA, uint32_t nB);
+size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB, uint32_t C);
+inline size_t dot_topk_buffer_bytes(uint32_t n, uint32_t C) { return dot_topk_buffer_bytes(n, n, C); }
 // the device error word inside a dot_topk buffer (zero it before a launch)
 uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB);
 inline uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t n) { return dot_topk_err_word(buf, n, n); }
