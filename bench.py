@@ -540,6 +540,15 @@ def proposal_queries(args, model, d, k, recall):
         out[str(C)] = {"ms": round(ms, 3), "queries_per_s": round(q.n / ms * 1e3, 1), "recall_at_10": round(st, 4),
                        "recall_at_10_tie_aware": round(tt, 4), "tie_aware_by_query_length": by_len,
                        "speedup_vs_exhaustive": round(ex_ms / ms, 2)}
+    if args.serving_requests > 0:
+        # the serving leg's open-loop load, answered through the proposal
+        from paper_2509_01654_gb300 import nw, serving
+        with nw.Server(d, k=k, max_batch_queries=8192, proposal=(model, 256)) as srv:
+            ps = serving.run_load(srv, synth.serving_queries(200_000), n_requests=args.serving_requests,
+                                  rate_hz=args.serving_rate, max_batch=4096)
+        ps["workload"] = ("the serving leg's load (Poisson arrivals, request sizes log-uniform on [1, 4096]) on the "
+                          "proposal server, C = 256")
+        out["serving"] = ps
     return out
 
 

@@ -156,6 +156,20 @@ nw_status nw_proposal_query(nw_model *model, nw_dict *dict, const uint8_t *qcode
                             uint32_t nq, uint32_t C, uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score,
                             uint32_t flags);
 
+/* A query server (nw_server_submit / nw_server_wait / nw_server_destroy of
+ * nw.h) that answers through the proposal: each GPU batch holds every queued
+ * request that fits cfg->max_batch_queries and runs as
+ * nw_proposal_query(model, dict, ..., C, cfg->k); requests arriving while a
+ * batch runs join the next one (one batch at a time: the candidate search of
+ * a batch already spreads over every SM).  A request's lists equal
+ * nw_proposal_query's for its words alone (a word's embedding, candidates and
+ * scores do not depend on the rest of its batch).  cfg->max_inflight and
+ * mem_budget_bytes are not used: memory comes from the model's context.  The
+ * model and the dictionary must share a context and outlive the server, and
+ * the model must not be used by other calls while the server runs. */
+nw_status nw_server_create_proposal(nw_dict *dict, nw_model *model, uint32_t C, const nw_server_config *cfg,
+                                    nw_server **out);
+
 #ifdef __cplusplus
 }
 #endif

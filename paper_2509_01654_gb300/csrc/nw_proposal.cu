@@ -304,6 +304,12 @@ nw_status rescore_select(nw_ctx* c, nw_dict* d, const uint32_t* cand, uint32_t C
 
 }  // namespace
 
+namespace nw {
+namespace prop {
+nw_ctx* model_ctx(const nw_model* M) { return M->ctx; }
+}  // namespace prop
+}  // namespace nw
+
 extern "C" {
 
 nw_status nw_model_create(nw_ctx* c, uint32_t alphabet, uint64_t seed, nw_model** out) {

@@ -8,8 +8,14 @@
 
 #include "nw_launch.h"
 
+struct nw_ctx;
+struct nw_model;
+
 namespace nw {
 namespace prop {
+
+// the context a model was created on (its allocations, stream and error text)
+nw_ctx* model_ctx(const nw_model* M);
 
 constexpr int kCap = 2048;       // append-buffer keys per row of the dot-product top-C
 constexpr int kFeat = 63;        // embedding outputs 0..62 are features, 63 is the bias

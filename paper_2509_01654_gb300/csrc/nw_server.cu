@@ -11,6 +11,11 @@
 // memory budget.  While batches run, new requests keep queueing and are
 // admitted the moment a slot frees, so their GPU work overlaps the running
 // batches'.
+//
+// A proposal server (nw_server_create_proposal) runs each batch through the
+// learned proposal instead: one batch at a time (its candidate search spreads
+// over every SM), holding every queued request that fits, answered by
+// nw_proposal_query on the model's stream.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -20,6 +25,8 @@
 #include <unordered_map>
 
 #include "nw_host.h"
+#include "nw_proposal.h"
+#include "nw_proposal_internal.h"
 
 namespace {
 
@@ -74,6 +81,8 @@ constexpr size_t kMaxSegs = 2u * kBuckets * kBuckets;  // plan_query makes at mo
 
 struct nw_server {
   nw_dict* dict = nullptr;
+  nw_model* model = nullptr;  // proposal mode: batches go through nw_proposal_query
+  uint32_t C = 0;
   nw_ctx ictx;  // the server's own context: device, SM count, budget accounting, error text
   nw_server_config cfg{};
   std::vector<std::unique_ptr<Slot>> slots;
@@ -263,7 +272,78 @@ void retire(nw_server* S, Slot& s) {
   S->cv_done.notify_all();
 }
 
+// Proposal mode: each batch is every queued request that fits
+// max_batch_queries, answered synchronously by nw_proposal_query; requests
+// arriving meanwhile wait for the next batch.
+void worker_proposal(nw_server* S) {
+  cudaSetDevice(S->ictx.device);
+  const uint32_t Q = S->cfg.max_batch_queries, k = S->cfg.k;
+  std::vector<uint8_t> codes;
+  std::vector<uint32_t> offsets, idx;
+  std::vector<int16_t> score;
+  std::unique_lock<std::mutex> lock(S->mu);
+  while (!S->stop) {
+    if (S->queue.empty()) {
+      S->cv.wait_for(lock, std::chrono::milliseconds(2));
+      continue;
+    }
+    std::vector<Request*> batch;
+    uint32_t nq = 0;
+    while (!S->queue.empty() && nq + S->queue.front()->nq <= Q) {
+      batch.push_back(S->queue.front());
+      nq += S->queue.front()->nq;
+      S->queue.pop_front();
+    }
+    const double t0 = now_s();
+    for (Request* r : batch) {
+      r->state = 1;
+      r->info.start_s = t0;
+      r->info.batch_queries = nq;
+      r->info.batch_requests = (uint32_t)batch.size();
+      r->info.inflight_at_start = 0;
+    }
+    lock.unlock();
+    codes.clear();
+    offsets.assign(1, 0u);
+    for (Request* r : batch) {
+      const uint32_t base = (uint32_t)codes.size();
+      codes.insert(codes.end(), r->codes.begin(), r->codes.end());
+      for (uint32_t q = 0; q < r->nq; ++q) offsets.push_back(base + r->offsets[q + 1]);
+    }
+    if (codes.empty()) codes.push_back(0);
+    idx.resize((size_t)nq * k);
+    score.resize((size_t)nq * k);
+    const nw_status st =
+        nw_proposal_query(S->model, S->dict, codes.data(), offsets.data(), nq, S->C, k, idx.data(), score.data(), 0);
+    lock.lock();
+    if (st != NW_OK) S->err = nw::prop::model_ctx(S->model)->err;
+    const double t1 = now_s();
+    uint32_t first = 0;
+    for (Request* r : batch) {
+      if (st == NW_OK) {
+        r->idx.assign(idx.begin() + (size_t)first * k, idx.begin() + (size_t)(first + r->nq) * k);
+        r->score.assign(score.begin() + (size_t)first * k, score.begin() + (size_t)(first + r->nq) * k);
+      }
+      first += r->nq;
+      r->status = st;
+      r->state = 2;
+      r->info.done_s = t1;
+    }
+    S->cv_done.notify_all();
+  }
+  for (Request* r : S->queue) {
+    r->status = NW_EINVAL;
+    r->state = 2;
+  }
+  S->queue.clear();
+  S->cv_done.notify_all();
+}
+
 void worker_main(nw_server* S) {
+  if (S->model) {
+    worker_proposal(S);
+    return;
+  }
   cudaSetDevice(S->ictx.device);
   const uint32_t Q = S->cfg.max_batch_queries;
   std::unique_lock<std::mutex> lock(S->mu);
@@ -371,6 +451,29 @@ nw_status nw_server_create(nw_dict* dict, const nw_server_config* cfg, nw_server
     }
     S->slots.push_back(std::move(sp));
   }
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return NW_OK;
+}
+
+nw_status nw_server_create_proposal(nw_dict* dict, nw_model* model, uint32_t C, const nw_server_config* cfg,
+                                    nw_server** out) {
+  if (!out) return NW_EINVAL;
+  *out = nullptr;
+  if (!dict || !model || !cfg) return set_err(nullptr, NW_EINVAL, "null argument");
+  if (nw::prop::model_ctx(model) != dict->ctx)
+    return set_err(nullptr, NW_EINVAL, "the model and the dictionary belong to different contexts");
+  if (C == 0 || C > NW_MAX_CANDIDATES) return set_err(nullptr, NW_EINVAL, "C must be in [1, %d]", NW_MAX_CANDIDATES);
+  if (cfg->k == 0 || cfg->k > NW_MAX_K) return set_err(nullptr, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  if (cfg->max_batch_queries == 0 || cfg->max_batch_queries > (1u << 20))
+    return set_err(nullptr, NW_EINVAL, "max_batch_queries must be in [1, 2^20]");
+  nw_server* S = new nw_server();
+  S->dict = dict;
+  S->model = model;
+  S->C = C;
+  S->cfg = *cfg;
+  S->ictx.device = dict->ctx->device;
+  S->ictx.sm_count = dict->ctx->sm_count;
   S->worker = std::thread(worker_main, S);
   *out = S;
   return NW_OK;

@@ -38,7 +38,7 @@ EXPORTED = [
     # nw_proposal.h
     "nw_model_create", "nw_model_free", "nw_model_param_count", "nw_model_get_params", "nw_model_set_params",
     "nw_model_embed", "nw_model_loss_grad", "nw_model_train", "nw_quantize_embeddings", "nw_dot_topk",
-    "nw_rescore_topk", "nw_proposal_topk", "nw_dot_topk_cross", "nw_proposal_query",
+    "nw_rescore_topk", "nw_proposal_topk", "nw_dot_topk_cross", "nw_proposal_query", "nw_server_create_proposal",
 ]
 EMBED_DIM = 64
 MAX_CANDIDATES = 512
@@ -161,6 +161,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_proposal_topk.argtypes = [vp, vp, u32, u32, vp, vp, ctypes.POINTER(ProposalProfile), u32]
     L.nw_dot_topk_cross.argtypes = [vp, vp, u32, vp, vp, u32, u32, vp, vp, u32]
     L.nw_proposal_query.argtypes = [vp, vp, vp, vp, u32, u32, u32, vp, vp, u32]
+    L.nw_server_create_proposal.argtypes = [vp, vp, u32, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.nw_server_submit.argtypes = [vp, vp, vp, u32, ctypes.POINTER(u64)]
@@ -545,11 +546,18 @@ class Server:
     """nw_server_*: continuous-batching query service over a loaded dictionary."""
 
     def __init__(self, dictionary: "Dictionary", k: int = 10, max_batch_queries: int = 8192, max_inflight: int = 4,
-                 mem_budget_bytes: int = 0):
+                 mem_budget_bytes: int = 0, proposal=None):
+        """proposal=(model, C): answer through the learned proposal
+        (nw_server_create_proposal) instead of exhaustively."""
         L = load_library()
         cfg = ServerConfig(k, max_batch_queries, max_inflight, 0, mem_budget_bytes)
         h = ctypes.c_void_p()
-        st = L.nw_server_create(dictionary.handle, ctypes.byref(cfg), ctypes.byref(h))
+        if proposal is None:
+            st = L.nw_server_create(dictionary.handle, ctypes.byref(cfg), ctypes.byref(h))
+        else:
+            model, C = proposal
+            st = L.nw_server_create_proposal(dictionary.handle, model.handle, C, ctypes.byref(cfg), ctypes.byref(h))
+            self.model = model  # keeps the model alive
         if st != NW_OK:
             raise NwError(st, (L.nw_server_last_error(None) or b"").decode())
         self.handle = h

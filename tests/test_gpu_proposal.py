@@ -407,3 +407,40 @@ def test_proposal_query_refusals(ctx):
     assert e.value.status == nw.NW_EINVAL
     m.query(d, q.codes, q.offsets, C=8, k=3)  # still usable
 
+
+def test_proposal_server_results_equal_the_call_alone(ctx):
+    # requests of mixed sizes batched by the proposal server: each request's
+    # lists equal the proposal query of its words alone (bit for bit)
+    w, d = small_dict(ctx, n=2000, alphabet=12, seed=41, lo=1, hi=14)
+    m = nw.Model(ctx, 12, seed=6)
+    m.train(d, steps=100, batch_pairs=2048, lr=2e-3, seed=2)
+    g = np.random.default_rng(7)
+    reqs = [query_set(int(g.integers(1, 60)), 12, seed=100 + i, lo=0, hi=16) for i in range(16)]
+    alone = [m.query(d, q.codes, q.offsets, C=32, k=7) for q in reqs]
+    with nw.Server(d, k=7, max_batch_queries=160, proposal=(m, 32)) as srv:
+        ids = [srv.submit(q.codes, q.offsets) for q in reqs]
+        shared = 0
+        for rid, (wi, ws) in zip(ids, alone):
+            idx, sc, info = srv.wait(rid)
+            assert np.array_equal(idx, wi) and np.array_equal(sc, ws)
+            shared += info["batch_requests"] > 1
+        assert shared > 0  # some batches carried several requests
+
+
+def test_proposal_server_refusals(ctx):
+    w, d = small_dict(ctx, n=100)
+    m = nw.Model(ctx, 9)
+    for C in (0, nw.MAX_CANDIDATES + 1):
+        with pytest.raises(nw.NwError) as e:
+            nw.Server(d, k=5, proposal=(m, C))
+        assert e.value.status == nw.NW_EINVAL
+    other = nw.Context(0)
+    try:
+        m2 = nw.Model(other, 9)
+        with pytest.raises(nw.NwError) as e:
+            nw.Server(d, k=5, proposal=(m2, 8))
+        assert e.value.status == nw.NW_EINVAL
+        m2.free()
+    finally:
+        other.close()
+
