@@ -68,31 +68,6 @@ __global__ void __launch_bounds__(128) pairs_kernel(const PairsParams P) {
   P.out[p] = (int16_t)pair_dispatch(lb, P, pa, la, pb);
 }
 
-// one thread per candidate of the proposal path: the same computation as
-// pairs_kernel for (i, cand[i * C + r])
-__global__ void __launch_bounds__(128) rescore_kernel(const PairsParams P, const uint32_t* __restrict__ cand,
-                                                      uint32_t C, int32_t* __restrict__ score) {
-  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (uint64_t)P.n * C) return;
-  const uint32_t i = (uint32_t)(p / C);
-  const uint32_t j = cand[p];
-  if (j == 0xffffffffu) {
-    score[p] = INT32_MIN;
-    return;
-  }
-  if (j >= P.n || j == i) {
-    atomicOr(P.err, kErrInput);
-    score[p] = INT32_MIN;
-    return;
-  }
-  const uint32_t ri = __ldg(P.rank + i), rj = __ldg(P.rank + j);
-  const int li = __ldg(P.slen + ri), lj = __ldg(P.slen + rj);
-  uint32_t pa = ri, pb = rj;
-  int la = li, lb = lj;
-  if (li > lj) { pa = rj; pb = ri; la = lj; lb = li; }
-  score[p] = pair_dispatch(lb, P, pa, la, pb);
-}
-
 // one thread per candidate of a query: Algorithm 1 between query i of set
 // Q and dictionary word cand[i * C + r] of set D, the shorter word streamed
 // (QD: query streamed, dictionary word in registers; DQ: the reverse)
@@ -162,13 +137,6 @@ __global__ void select_topk_kernel(const uint32_t* __restrict__ cand, const int3
 }
 
 namespace prop {
-
-cudaError_t rescore(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s) {
-  const uint64_t m = (uint64_t)P.n * C;
-  if (m == 0) return cudaSuccess;
-  rescore_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(P, cand, C, score);
-  return cudaGetLastError();
-}
 
 cudaError_t cross_rescore(const CrossParams& X, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s) {
   const uint64_t m = (uint64_t)X.nq * C;

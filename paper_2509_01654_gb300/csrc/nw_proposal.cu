@@ -296,9 +296,12 @@ PairsParams pairs_params(const nw_dict* d, uint32_t* err) {
 nw_status rescore_select(nw_ctx* c, nw_dict* d, const uint32_t* cand, uint32_t C, uint32_t k, DevBuf& score_buf,
                          uint32_t* out_idx, int16_t* out_score, uint32_t* err, cudaStream_t s) {
   const uint32_t n = d->ws.n;
-  NW_TRY(ctx_ensure(c, score_buf, sizeof(int32_t) * std::max<size_t>(1, (size_t)n * C), "candidate scores"));
-  NW_CK(prop::rescore(pairs_params(d, err), cand, C, score_buf.as<int32_t>(), s));
-  NW_CK(prop::select_topk(cand, score_buf.as<int32_t>(), n, C, k, out_idx, out_score, s));
+  // scores, then the length-sorted candidates they belong to and the work lists
+  NW_TRY(ctx_ensure(c, score_buf, prop::rescore_scratch_bytes(n, C), "candidate scores"));
+  int32_t* score = score_buf.as<int32_t>();
+  uint32_t* sorted = nullptr;
+  NW_CK(prop::rescore_sorted(pairs_params(d, err), cand, C, score, &sorted, s));
+  NW_CK(prop::select_topk(sorted, score, n, C, k, out_idx, out_score, s));
   return NW_OK;
 }
 

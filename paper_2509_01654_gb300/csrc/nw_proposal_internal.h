@@ -52,10 +52,17 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* dot,
                           uint32_t* err, cudaStream_t s);
 
-// Algorithm 1's score of (i, cand[i * C + r]) into score[i * C + r] (int32;
-// INT32_MIN for UINT32_MAX entries); out-of-range or self candidates raise
-// kErrInput.  P supplies the encoded dictionary (its pi/pj/m/out are unused).
-cudaError_t rescore(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score, cudaStream_t s);
+// Algorithm 1's scores of every row i against its candidates cand[i * C +
+// r] (UINT32_MAX entries score INT32_MIN; out-of-range or self candidates
+// raise kErrInput; P supplies the encoded dictionary, its pi/pj/m/out
+// unused), two candidates per thread: each row's candidates are first
+// reordered by length (*sorted_out, n * C), and score[i * C + r] is the
+// score of (*sorted_out)[i * C + r].  score points at the start of a region
+// of rescore_scratch_bytes(n, C) (the scores, then the reordered candidates
+// and the work lists grouped by DP width).
+size_t rescore_scratch_bytes(uint32_t n, uint32_t C);
+cudaError_t rescore_sorted(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score,
+                           uint32_t** sorted_out, cudaStream_t s);
 // Words of a query set Q against a dictionary D for cross_rescore: QD reads
 // its streamed (A) words from Q and its register (B) words from D, DQ the
 // reverse; both carry D's scoring.  Ranks and lengths of either set map
