@@ -41,7 +41,10 @@ namespace {
 
 constexpr int kDim = 64;                 // values per row (bf16)
 constexpr int kRowBytes = kDim * 2;      // 128
+// 32 rows (two 16-row slabs) per warp: 16 rows with three CTAs per SM measured 5% slower
 constexpr int kRowsPerWarp = 32;
+constexpr int kSlabs = kRowsPerWarp / 16;
+constexpr int kCtasPerSm = kSlabs == 2 ? 2 : 3;
 constexpr int kWarps = 8;
 constexpr int kRowsPerCta = kRowsPerWarp * kWarps;  // 256
 constexpr int kTileCols = 64;
@@ -49,7 +52,7 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kSel = NW_MAX_CANDIDATES;  // per-warp gather/sort area (keys)
 
 // dynamic shared memory layout (bytes)
-constexpr int kStages = 6;                               // column tiles in flight
+constexpr int kStages = kSlabs == 2 ? 6 : 4;             // column tiles in flight
 constexpr int kTileBytes = kTileCols * kRowBytes;        // 8 KiB per tile
 constexpr int kTileBiasBytes = kTileCols * 4;            // its biases (float)
 constexpr int kSmemB = kStages * kTileBytes;
@@ -66,7 +69,7 @@ constexpr int kOffCnt = kOffHist + kSmemHist;
 constexpr int kOffThr = kOffCnt + kSmemCnt;
 constexpr int kOffBars = kOffThr + kSmemThr;
 constexpr int kSmemTotal = kOffBars + kSmemBars;
-static_assert(kSmemTotal <= 113 * 1024, "two CTAs per SM");
+static_assert(kSmemTotal * kCtasPerSm <= 224 * 1024, "kCtasPerSm CTAs per SM");
 // a pipeline wait gives up after this many SM clock cycles (about a second)
 constexpr long long kWaitCycles = 2000000000ll;
 static_assert(kRowsPerCta * kRowBytes <= kSmemSort, "A staging fits the sort area");
@@ -392,7 +395,7 @@ struct DotArgs {
 };
 
 template <bool kSplit, bool kSelf>
-__global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) dot_topk_kernel(const DotArgs P) {
   const float* __restrict__ biasf = P.biasf;
   const uint32_t C = P.C;
   uint64_t* __restrict__ buf = P.buf;
@@ -458,9 +461,9 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
   __syncthreads();
 
   // A fragments: slab s (16 rows), k-step ks
-  uint32_t afr[2][4][4];
+  uint32_t afr[kSlabs][4][4];
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < kSlabs; ++s)
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks) {
       const int r = warp * kRowsPerWarp + s * 16 + (lane & 15);
@@ -470,10 +473,10 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
   __syncthreads();  // the sort area is free from here on
 
   const int g = lane >> 2, t4 = lane & 3;
-  float thr[2][2];
-  int cnt[2][2];  // keys in the row's buffer (same in the row's four lanes)
+  float thr[kSlabs][2];
+  int cnt[kSlabs][2];  // keys in the row's buffer (same in the row's four lanes)
 #pragma unroll
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < kSlabs; ++s)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       thr[s][h] = -FLT_MAX;
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
 
     const unsigned char* tB = sB + b * (kTileCols * kRowBytes);
     const float* tBias = sBias + b * kTileCols;
-    float acc[2][8][4];
+    float acc[kSlabs][8][4];
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks) {
 #pragma unroll
@@ -520,13 +523,13 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
           const float2 c0 = *reinterpret_cast<const float2*>(tBias + nb * 8 + 2 * t4);
           const float2 c1 = *reinterpret_cast<const float2*>(tBias + (nb + 1) * 8 + 2 * t4);
 #pragma unroll
-          for (int s = 0; s < 2; ++s) {
+          for (int s = 0; s < kSlabs; ++s) {
             mma_bf16_init(acc[s][nb], afr[s][0], b0, b1, c0.x, c0.y);
             mma_bf16_init(acc[s][nb + 1], afr[s][0], b2, b3, c1.x, c1.y);
           }
         } else {
 #pragma unroll
-          for (int s = 0; s < 2; ++s) {
+          for (int s = 0; s < kSlabs; ++s) {
             mma_bf16(acc[s][nb], afr[s][ks], b0, b1);
             mma_bf16(acc[s][nb + 1], afr[s][ks], b2, b3);
           }
@@ -539,9 +542,9 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
 
     // epilogue: the maximum of each (slab, half) row group against its row's
     // threshold; only groups that beat it look at their values one by one
-    bool gh[2][2];
+    bool gh[kSlabs][2];
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < kSlabs; ++s)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float m[8];  // a tree of maxima: depth 4 instead of a chain of 15
@@ -553,14 +556,17 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
           for (int x = 0; x < w; ++x) m[x] = fmaxf(m[x], m[x + w]);
         gh[s][h] = m[0] > thr[s][h];
       }
-    if (__any_sync(0xffffffffu, gh[0][0] | gh[0][1] | gh[1][0] | gh[1][1])) {
+    bool any_hit = false;
+#pragma unroll
+    for (int s = 0; s < kSlabs; ++s) any_hit |= gh[s][0] | gh[s][1];
+    if (__any_sync(0xffffffffu, any_hit)) {
       // A row's 16 x 4 values of this tile sit in the four lanes of one quad,
       // and no other warp appends to it: the quad's lanes take consecutive
       // slots by a prefix sum of their hit counts, with no atomics.  Hits are
       // found as a bit mask, then read back from this lane's staging slots.
       float* stage = reinterpret_cast<float*>(sMine) + lane * 32;
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
+      for (int s = 0; s < kSlabs; ++s) {
         uint32_t m[2] = {0u, 0u};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -616,16 +622,18 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
     // rows of this warp holding more than `trigger` keys: compacting at 2C
     // (or when the buffer could overflow during the next tile) keeps the
     // thresholds close to the running C-th best value
-    if (__any_sync(0xffffffffu, (cnt[0][0] > trigger) | (cnt[0][1] > trigger) | (cnt[1][0] > trigger) |
-                                    (cnt[1][1] > trigger))) {
+    bool over = false;
+#pragma unroll
+    for (int s = 0; s < kSlabs; ++s) over |= (cnt[s][0] > trigger) | (cnt[s][1] > trigger);
+    if (__any_sync(0xffffffffu, over)) {
       if (t4 == 0) {
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < kSlabs; ++s)
 #pragma unroll
           for (int h = 0; h < 2; ++h) sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g] = cnt[s][h];
       }
       __syncwarp();
-      unsigned full = __ballot_sync(0xffffffffu, sCnt[warp * kRowsPerWarp + lane] > trigger);
+      unsigned full = __ballot_sync(0xffffffffu, lane < kRowsPerWarp && sCnt[warp * kRowsPerWarp + lane] > trigger);
       while (full) {
         const int l = __ffs(full) - 1;
         full &= full - 1;
@@ -665,7 +673,7 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
         __syncwarp();
       }
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < kSlabs; ++s)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           thr[s][h] = sThr[warp * kRowsPerWarp + s * 16 + h * 8 + g];
@@ -676,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 2) dot_topk_kernel(const DotArgs P) 
   }
   if (t4 == 0) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < kSlabs; ++s)
 #pragma unroll
       for (int h = 0; h < 2; ++h) sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g] = cnt[s][h];
   }
