@@ -122,39 +122,6 @@ __device__ __forceinline__ uint32_t dp_word(const uint32_t* __restrict__ arow, i
   }
 }
 
-// Two alignments in the int16 halves: the low half's B word has l0 symbols
-// and the high half's l1 (both <= LB; columns past a word's end only extend
-// its DP to the right and do not change its earlier columns).  Returns the
-// low half's cell at column l0 and the high half's at column l1 (0 for an
-// empty word).
-template <int LB, bool TAB = false>
-__device__ __forceinline__ uint32_t dp_word2(const uint32_t* __restrict__ arow, int la, const BRow<LB>& b,
-                                             uint32_t C1, uint32_t C2, const uint16_t* tab, int l0, int l1) {
-  if constexpr (LB == 0) {
-    return 0u;
-  } else {
-    uint32_t G[LB];
-#pragma unroll
-    for (int j = 0; j < LB; ++j) G[j] = 0u;
-    int i = 0;
-#pragma unroll 1
-    for (; i + 1 < la; i += 2) {
-      const uint32_t a0 = __ldg(arow + i);
-      const uint32_t a1 = __ldg(arow + i + 1);
-      dp_row<LB, TAB>(G, a0, b, C1, C2, tab);
-      dp_row<LB, TAB>(G, a1, b, C1, C2, tab);
-    }
-    if (i < la) dp_row<LB, TAB>(G, __ldg(arow + i), b, C1, C2, tab);
-    uint32_t lo = 0u, hi = 0u;
-#pragma unroll
-    for (int j = 0; j < LB; ++j) {
-      if (j == l0 - 1) lo = G[j] & 0xffffu;
-      if (j == l1 - 1) hi = G[j] >> 16;
-    }
-    return lo | (hi << 16);
-  }
-}
-
 // The same DP with the A word's symbols in shared memory, symbol i at
 // acol[32 * i] (the staging layout of the all-pairs kernel; every lane reads
 // the same address, so each load is a broadcast).
