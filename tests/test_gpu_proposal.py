@@ -262,6 +262,55 @@ def test_rescore_matches_oracle(ctx, oracle_mod, k, C):
     assert np.array_equal(idx, wi)
 
 
+@pytest.mark.parametrize("C", [7, 32, 129])
+def test_rescore_with_a_similarity_matrix(ctx, oracle_mod, C):
+    # the paired rescoring's table variant: scores from a full similarity
+    # matrix, candidates of mixed lengths, odd C (one unpaired entry per row)
+    alphabet, gap, k = 24, -2, 6
+    g = np.random.default_rng(C)
+    S = g.integers(-3, 4, (alphabet, alphabet))
+    S = (np.triu(S) + np.triu(S, 1).T).astype(np.int32)
+    np.fill_diagonal(S, 6)
+    w = synth.make_uniform_length_words(900, alphabet, 1.0, 0, 20, seed=C + 3)
+    d = ctx.load_dictionary_sim(w.codes, w.offsets, alphabet, S, gap)
+    cand = np.empty((w.n, C), dtype=np.uint32)
+    for i in range(w.n):
+        pool = g.choice(w.n - 1, C, replace=False)
+        cand[i] = np.where(pool >= i, pool + 1, pool)
+    cand[::5, C // 3:] = PR.MISSING_IDX
+    idx, sc = nw.rescore_topk(d, cand, k)
+    I = np.repeat(np.arange(w.n), C)
+    J = cand.reshape(-1).astype(np.int64)
+    ok = J != PR.MISSING_IDX
+    full = np.full(I.size, np.iinfo(np.int64).min, dtype=np.int64)
+    full[ok] = oracle_mod.score_pairs_sim(w, I[ok], J[ok], S, gap)
+    full = full.reshape(w.n, C)
+    for i in range(w.n):
+        v = cand[i] != PR.MISSING_IDX
+        j, s_ = cand[i][v].astype(np.int64), full[i][v]
+        order = np.lexsort((j, -s_))[:k]
+        assert np.array_equal(idx[i, :order.size], j[order])
+        assert np.array_equal(sc[i, :order.size].astype(np.int64), s_[order])
+        assert np.all(idx[i, order.size:] == PR.MISSING_IDX)
+
+
+def test_proposal_query_with_a_similarity_matrix(ctx):
+    # cross rescoring's table variant: with every word a candidate the lists
+    # equal the exhaustive query's over matrix scores
+    alphabet, gap = 30, -2
+    g = np.random.default_rng(9)
+    S = g.integers(-2, 4, (alphabet, alphabet))
+    S = (np.triu(S) + np.triu(S, 1).T).astype(np.int32)
+    np.fill_diagonal(S, 5)
+    w = synth.make_uniform_length_words(400, alphabet, 1.0, 1, 14, seed=10)
+    q = query_set(60, alphabet, seed=11, lo=0, hi=16)
+    d = ctx.load_dictionary_sim(w.codes, w.offsets, alphabet, S, gap)
+    m = nw.Model(ctx, alphabet, seed=3)
+    idx, sc = m.query(d, q.codes, q.offsets, C=400, k=8)
+    wi, ws = d.query(q.codes, q.offsets, 8)
+    assert np.array_equal(idx, wi) and np.array_equal(sc, ws)
+
+
 def test_rescore_reports_self_candidate(ctx):
     w = synth.make_words(100, 10, 1.0, 5.0, 2.0, 1, 9, seed=1)
     d = ctx.load_dictionary(w.codes, w.offsets, 10, (1, -1, -1))
