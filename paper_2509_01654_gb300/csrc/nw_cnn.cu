@@ -141,7 +141,7 @@ struct TileMap {
 // C[M][N] = A[M][K] . B[K][N] over the K range of blockIdx.z.  Mlim / Klim
 // (device, may be null) lower M / K below the launch's bounds.
 template <class AV, class BV>
-__global__ void __launch_bounds__(NT) gemm_kernel(AV A, BV B, int M, int N, int K, int kchunk, float* C, int ldc,
+__global__ void __launch_bounds__(NT, 2) gemm_kernel(AV A, BV B, int M, int N, int K, int kchunk, float* C, int ldc,
                                                   Epi e, const int* Mlim, const int* Klim) {
   constexpr bool kAK = AV::kColFast;   // A contiguous along k
   constexpr bool kBK = !BV::kColFast;  // B contiguous along k
