@@ -165,8 +165,10 @@ nw_status nw_proposal_query(nw_model *model, nw_dict *dict, const uint8_t *qcode
  * nw_proposal_query's for its words alone (a word's embedding, candidates and
  * scores do not depend on the rest of its batch).  cfg->max_inflight and
  * mem_budget_bytes are not used: memory comes from the model's context.  The
- * model and the dictionary must share a context and outlive the server, and
- * the model must not be used by other calls while the server runs. */
+ * model and the dictionary must share a context and outlive the server.  The
+ * batches use that context: a call of the caller's that holds it meanwhile
+ * delays the next batch (retried for up to about 10 s, then NW_EBUSY), and
+ * the model's parameters must not change while the server runs. */
 nw_status nw_server_create_proposal(nw_dict *dict, nw_model *model, uint32_t C, const nw_server_config *cfg,
                                     nw_server **out);
 

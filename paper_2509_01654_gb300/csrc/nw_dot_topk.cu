@@ -821,13 +821,20 @@ size_t bias_pad(uint32_t n) { return ((size_t)n + kTileCols - 1) / kTileCols * k
 
 size_t dot_topk_qb_bytes(uint32_t n) { return bias_pad(n) * kRowBytes; }
 
-// column splits of a launch over nA rows and nB columns: enough CTAs for
-// two per SM when the row blocks alone are fewer, each split at least 8
-// tiles of 64 columns
+// column splits of a launch over nA rows and nB columns on the current
+// device: enough CTAs for kCtasPerSm per SM when the row blocks alone are
+// fewer, each split at least 8 tiles of 64 columns
 uint32_t dot_topk_splits(uint32_t nA, uint32_t nB) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 152;
+  }
   const uint32_t blocks = (nA + kRowsPerCta - 1) / kRowsPerCta;
   const uint32_t tiles = (nB + kTileCols - 1) / kTileCols;
-  const uint32_t want = (2u * 152u + blocks - 1) / std::max(blocks, 1u);
+  const uint32_t slots = (uint32_t)kCtasPerSm * (uint32_t)sms;
+  const uint32_t want = (slots + blocks - 1) / std::max(blocks, 1u);
   return std::max(1u, std::min(want, tiles / 8));
 }
 

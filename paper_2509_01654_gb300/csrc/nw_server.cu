@@ -313,8 +313,13 @@ void worker_proposal(nw_server* S) {
     if (codes.empty()) codes.push_back(0);
     idx.resize((size_t)nq * k);
     score.resize((size_t)nq * k);
-    const nw_status st =
-        nw_proposal_query(S->model, S->dict, codes.data(), offsets.data(), nq, S->C, k, idx.data(), score.data(), 0);
+    // a call of the user's on the model's context holds it busy: retry for up to ~10 s
+    nw_status st = NW_EBUSY;
+    for (int attempt = 0; attempt < 10000 && st == NW_EBUSY; ++attempt) {
+      st = nw_proposal_query(S->model, S->dict, codes.data(), offsets.data(), nq, S->C, k, idx.data(), score.data(),
+                             0);
+      if (st == NW_EBUSY) std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
     lock.lock();
     if (st != NW_OK) S->err = nw::prop::model_ctx(S->model)->err;
     const double t1 = now_s();
