@@ -342,6 +342,11 @@ def run_ours(args, rank, world, local_rank):
                "sample": f"top-{k} of {rows} sampled words against all {n:,} words ({rows * (n - 1):,} pairs) "
                          f"in {dt:.1f} s; full (la+1)x(lb+1) int32 matrix per pair"}
 
+    # issue width implied by the measured rate at the SM clock nvidia-smi reported under load
+    lanes_note = ""
+    if clocks and clocks.get("sm_mhz"):
+        lanes = rates["viaddmax_s16x2"] / (rates["sm_count"] * clocks["sm_mhz"] * 1e6)
+        lanes_note = f", {lanes:.1f} lanes/clk/SM at the {clocks['sm_mhz']:.0f} MHz median SM clock under load"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -352,8 +357,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
                      "frac": achieved / peak, "traffic": traffic,
                      "traffic_basis": "DRAM bytes of one step's alignment launches (all 22), ncu, 600k words",
-                     "peak_basis": f"2 cells x measured __viaddmax_s16x2 rate ({rates['viaddmax_s16x2']:.4g}/s, "
-                                   f"{rates['sm_count']} SMs at {rates['sm_clock_mhz']:.0f} MHz) / {c_min:g} "
+                     "peak_basis": f"2 cells x measured __viaddmax_s16x2 rate ({rates['viaddmax_s16x2']:.4g}/s "
+                                   f"over {rates['sm_count']} SMs{lanes_note}) / {c_min:g} "
                                    f"packed instructions per cell pair; cell-mix microbenchmark "
                                    f"{2 * rates['nw_cell_mix'] / 1e9:.0f} GCUPS",
                      "rates_per_s": {key: rates[key] for key in ("viaddmax_s16x2", "vimax3_s16x2",
@@ -458,10 +463,18 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
             _, _, prof = model.proposal_topk(d, C, k, nbr_idx=out_i, nbr_score=out_s)
             walls.append(1e3 * (time.perf_counter() - t0))
             profs.append(prof)
-        strict, tie = recall_vs_exact(ex_i, ex_s, out_i.cpu().numpy().view(np.uint32), out_s.cpu().numpy())
+        ap_i, ap_s = out_i.cpu().numpy().view(np.uint32), out_s.cpu().numpy()
+        strict, tie = recall_vs_exact(ex_i, ex_s, ap_i, ap_s)
+        by_len = {}
+        lens = w.lengths
+        for lo, hi in ((1, 4), (5, 8), (9, 12), (13, 16), (17, 25)):
+            sel = (lens >= lo) & (lens <= hi)
+            if sel.any():
+                by_len[f"{lo}-{hi}"] = round(recall_vs_exact(ex_i[sel], ex_s[sel], ap_i[sel], ap_s[sel])[1], 4)
         med = {key: statistics.median(p[key] for p in profs) for key in profs[0]}
         return {"ms": {key: round(v, 3) for key, v in med.items()}, "wall_ms": round(statistics.median(walls), 3),
                 "recall_at_10": round(strict, 4), "recall_at_10_tie_aware": round(tie, 4),
+                "tie_aware_by_word_length": by_len,
                 "speedup_vs_exhaustive": round(exhaustive_ms / med["total_ms"], 2)}
 
     untrained = nw.Model(ctx, 40, seed=1)
@@ -472,7 +485,7 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
     t0 = time.perf_counter()
     losses = model.train(d, steps=args.proposal_steps, nbr=ex_i, **train_cfg)
     train_s = time.perf_counter() - t0
-    res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (256, 512)}
+    res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (256, 384, 512)}
     queries = proposal_queries(args, model, d, k, recall_vs_exact)
     # candidates without a network: the C words nearest in length order (stable by index)
     order = np.argsort(w.lengths, kind="stable")

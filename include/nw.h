@@ -377,7 +377,10 @@ typedef struct {
     double iadd3;           /* three-input 32-bit add */
     double lop3;            /* three-input 32-bit logic op */
     double nw_cell_mix;     /* the alignment kernel's per-cell instruction mix, in packed cells/s */
-    double sm_clock_mhz;    /* SM clock seen by the benchmark (clock64 cycles / event time) */
+    double sm_clock_mhz;    /* clock64 cycles per microsecond of event time, averaged over the
+                             * benchmarks; on a GB300 this reads well below the SM clock that
+                             * nvidia-smi reports under the same load, so issue widths are best
+                             * derived from the rates and nvidia-smi's clock */
     uint32_t sm_count;
     uint32_t pad_;
 } nw_int_rates;

@@ -13,6 +13,9 @@ against the CPU oracle (oracle/proposal.py):
   than C, and rows far beyond the append buffer so that compaction runs;
 * rescoring of given candidate lists: bit-exact against Algorithm 1;
 * training: Adam's first step has size lr per coordinate, and the loss falls;
+* what training gains: at the same candidate budget the trained network's
+  lists reach the exact neighbours far more often than the untrained
+  network's or than candidates taken without a network (a length window);
 * the whole path: lists sorted, scores equal to Algorithm 1's, and every
   listed neighbour among the exact top list or tied with it in score when
   the candidates cover everything.
@@ -343,6 +346,38 @@ def test_proposal_path_properties(ctx, oracle_mod):
     assert np.all(score[:, 0] <= ex_s[:, 0])
     strict, tie = PR.recall_at_k(ex_i, ex_s, idx, score)
     assert 0.0 < strict <= tie <= 1.0
+
+
+def test_trained_network_beats_the_proposal_without_it(ctx):
+    # The same candidate budget three ways, each rescored exactly: the trained
+    # network, the same network untrained, and no network at all (the C words
+    # nearest in length order). Only the trained network finds the neighbours.
+    w = synth.make_words(20000, 40, 1.1, 8.0, 3.0, 1, 25, seed=23)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    ex_i, ex_s, _, _ = d.all_pairs_topk(10, hist=None)
+    C = 128
+    untrained = nw.Model(ctx, 40, seed=6)
+    ui, us, _ = untrained.proposal_topk(d, C=C, k=10)
+    untrained.free()
+    order = np.argsort(w.lengths, kind="stable")
+    pos = np.empty(w.n, dtype=np.int64)
+    pos[order] = np.arange(w.n)
+    lo = np.clip(pos - C // 2, 0, w.n - C - 1)
+    win = lo[:, None] + np.arange(C + 1)[None, :]
+    win = win[win != pos[:, None]].reshape(w.n, C)
+    li, ls = nw.rescore_topk(d, order[win].astype(np.uint32), 10)
+    m = nw.Model(ctx, 40, seed=6)
+    m.train(d, steps=1000, batch_pairs=2048, lr=2e-3, lr_final=2e-4, clip_norm=1.0, seed=7, nbr=ex_i,
+            nbr_fraction=0.5)
+    ti, ts, _ = m.proposal_topk(d, C=C, k=10)
+    m.free()
+    _, r_untrained = PR.recall_at_k(ex_i, ex_s, ui, us)
+    _, r_window = PR.recall_at_k(ex_i, ex_s, li, ls)
+    _, r_trained = PR.recall_at_k(ex_i, ex_s, ti, ts)
+    print(f"tie-aware recall@10 at C={C}: trained {r_trained:.3f}, untrained {r_untrained:.3f}, "
+          f"length window {r_window:.3f}")
+    assert r_trained >= 0.5
+    assert r_trained >= max(r_untrained, r_window) + 0.3
 
 
 def test_proposal_with_all_candidates_is_exact(ctx):
