@@ -229,19 +229,22 @@ nw_status nw_score_pairs(nw_dict *dict, const uint32_t *i, const uint32_t *j, si
 nw_status nw_query(nw_dict *dict, const uint8_t *qcodes, const uint32_t *qoffsets, uint32_t nq,
                    uint32_t k, uint32_t *nbr_idx, int16_t *nbr_score, uint32_t flags);
 
-/* ---- batches of independent dictionaries ----
+/* ---- batches of independent dictionaries and query sets ----
  *
  * Many dictionaries of uneven size, length range, alphabet and scoring (each
  * the paper's problem on its own word list, Sections 4-5) reduced to per-word
- * top-k lists in one CUDA-graph launch.  nw_batch_create loads every
- * dictionary, plans all their pairs together (one alignment launch per longer
- * length covering every dictionary), optionally autotunes the tile shape (A
- * words per task) of each launch by timing candidates on the batch itself,
- * and captures the whole reduction -- list resets, alignment launches, list
- * finalisation -- into a CUDA graph.  nw_batch_run replays the graph and
- * copies each dictionary's lists out.  Results equal nw_all_pairs_topk run on
- * each dictionary alone.  The batch uses the context's stream and memory
- * budget; the context must outlive it. */
+ * top-k lists in one CUDA-graph launch.  Each dictionary may bring a query
+ * set of its own size and lengths (Section 6's search for similar-sounding
+ * words, nw_query), answered in the same launch.  nw_batch_create loads every
+ * dictionary and query set, plans all their pairs together (one alignment
+ * launch per longer length covering every dictionary and query set),
+ * optionally autotunes the tile shape (A words per task) of each launch by
+ * timing candidates on the batch itself, and captures the whole reduction --
+ * list resets, alignment launches, list finalisation -- into a CUDA graph.
+ * nw_batch_run / nw_batch_run_queries replay the graph and copy the lists
+ * out.  Results equal nw_all_pairs_topk run on each dictionary alone and
+ * nw_query run on each query set alone.  The batch uses the context's stream
+ * and memory budget; the context must outlive it. */
 typedef struct nw_batch nw_batch;
 
 typedef struct {
@@ -250,6 +253,13 @@ typedef struct {
     uint32_t n;
     uint32_t alphabet;
     nw_scoring scoring;
+    /* optional query set against this dictionary (nq = 0: none), CSR as in
+     * nw_query; copied at creation like the dictionary */
+    const uint8_t *qcodes;
+    const uint32_t *qoffsets;
+    uint32_t nq;
+    uint32_t queries_only;     /* nonzero: only the query set is answered; the
+                                * dictionary's own lists are not computed */
 } nw_batch_dict;
 
 #define NW_BATCH_AUTOTUNE 0x10u /* nw_batch_create flag: time tile-shape candidates per launch */
@@ -257,20 +267,33 @@ typedef struct {
 typedef struct {
     uint32_t ndicts;
     uint32_t launches;                          /* alignment launches in the graph */
-    uint64_t pairs, cells;                      /* over all dictionaries */
+    uint64_t pairs, cells;                      /* over all dictionaries and query sets */
     double tune_ms;                             /* time spent autotuning */
     uint32_t words_per_task[NW_MAX_WORD_LEN + 1]; /* chosen A words per task by longer length (0: none) */
+    uint32_t query_words;                       /* words of all query sets */
+    uint64_t query_pairs, query_cells;          /* the part of pairs / cells from query sets */
 } nw_batch_info;
 
-/* flags: NW_DEVICE_PTRS (the dictionaries' buffers are device pointers),
- * NW_BATCH_AUTOTUNE.  k in [1, NW_MAX_K]. */
+/* flags: NW_DEVICE_PTRS (the dictionaries' and query sets' buffers are
+ * device pointers), NW_BATCH_AUTOTUNE.  k in [1, NW_MAX_K].  Errors as
+ * nw_load_dictionary and nw_query: NW_EINVAL for a code >= the dictionary's
+ * alphabet (query codes included) or a null query array with nq > 0,
+ * NW_ERANGE when a dictionary's or query set's scores do not fit the list
+ * keys. */
 nw_status nw_batch_create(nw_ctx *ctx, const nw_batch_dict *dicts, uint32_t ndicts, uint32_t k, uint32_t flags,
                           nw_batch **out);
 
 /* Runs the graph.  nbr_idx[d] / nbr_score[d] receive dictionary d's n*k
  * lists (ranked as nw_all_pairs_topk); host buffers, or device buffers with
- * NW_DEVICE_PTRS. */
+ * NW_DEVICE_PTRS.  Entries of queries_only dictionaries are not read (may be
+ * NULL).  Query lists are computed but not copied out. */
 nw_status nw_batch_run(nw_batch *batch, uint32_t *const *nbr_idx, int16_t *const *nbr_score, uint32_t flags);
+
+/* nw_batch_run that also copies dictionary d's query lists, nq*k each and
+ * ranked as nw_query, to qnbr_idx[d] / qnbr_score[d] (entries of dictionaries
+ * without queries are not read).  Same buffer convention and flags. */
+nw_status nw_batch_run_queries(nw_batch *batch, uint32_t *const *nbr_idx, int16_t *const *nbr_score,
+                               uint32_t *const *qnbr_idx, int16_t *const *qnbr_score, uint32_t flags);
 
 nw_status nw_batch_info_get(const nw_batch *batch, nw_batch_info *out);
 

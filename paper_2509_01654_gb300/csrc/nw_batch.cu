@@ -1,14 +1,17 @@
-// nw_batch.cu -- nw_batch_*: many independent dictionaries reduced to per-word
-// top-k lists in one CUDA-graph launch.
+// nw_batch.cu -- nw_batch_*: many independent dictionaries, each with an
+// optional query set, reduced to top-k lists in one CUDA-graph launch.
 //
 // Every dictionary is loaded as usual (its own word set, scoring and score
-// bounds).  The pair plans of all dictionaries are merged by longer length:
-// the launch for length LB walks the LB segments of every dictionary, each
-// segment tagged with its dictionary, and the kernel (epilogue
-// kEpiBatchLists) reads that dictionary's word set, lists and scoring per
-// task.  The A-chunk size of each launch is a tile-shape parameter that the
-// autotuner picks by timing candidates on the batch.  The whole reduction is
-// captured once into a CUDA graph and replayed by nw_batch_run.
+// bounds), and its query set is ingested with the dictionary's alphabet and
+// code shift.  The pair plans of all dictionaries and query sets are merged
+// by longer length: the launch for length LB walks the LB segments of every
+// dictionary and query set, each segment tagged with its terms (3d for
+// dictionary d's own pairs, 3d + 1 for its queries as A words, 3d + 2 for its
+// queries as B words), and the kernel (epilogue kEpiBatchLists) reads those
+// terms' word sets, lists and scoring per task.  The A-chunk size of each
+// launch is a tile-shape parameter that the autotuner picks by timing
+// candidates on the batch.  The whole reduction is captured once into a CUDA
+// graph and replayed by nw_batch_run / nw_batch_run_queries.
 #include <chrono>
 
 #include "nw_host.h"
@@ -17,11 +20,17 @@ struct nw_batch {
   nw_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;  // the batch's own stream (capture needs a non-legacy stream)
   std::vector<nw_dict*> dicts;
+  std::vector<WordSet> qsets;     // each dictionary's query set (n = 0: none)
+  std::vector<uint8_t> self;      // 1: the dictionary's own lists are computed
   uint32_t k = 0;
   uint32_t ta_by_lb[kBuckets] = {0};
   Plan plan;
-  std::vector<size_t> list_off;  // first list (word) of each dictionary in the combined arrays
+  std::vector<size_t> list_off;   // first list of each dictionary's own lists in the combined arrays
+  std::vector<size_t> qlist_off;  // first list of each query set in the combined arrays
+  std::vector<int32_t> q_key_lo;  // list-key offset of each query set (its lowest score - 1)
   size_t nlists = 0;
+  uint32_t query_words = 0;
+  uint64_t query_pairs = 0, query_cells = 0;
   DevBuf d_segs, d_terms, d_slots, d_thr, d_small, d_out_idx, d_out_score;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -32,17 +41,31 @@ namespace {
 
 constexpr uint32_t kTaCandidates[] = {64, 128, 256};
 
-// Every dictionary's own plan with A chunks of `ta` words.
-std::vector<Plan> dict_plans(const nw_batch* B, uint32_t ta) {
-  std::vector<Plan> plans(B->dicts.size());
-  for (size_t d = 0; d < B->dicts.size(); ++d) plan_all_pairs(B->dicts[d]->ws.bk, ta, plans[d]);
-  return plans;
+// Terms of dictionary d's own pairs (role 0) and of its query set as A words
+// (role 1) or B words (role 2).
+uint32_t term_index(size_t d, int role) { return (uint32_t)(3 * d + role); }
+
+// Every dictionary's own plan and every query set's plan (launches of roles 1
+// and 2), made with A chunks of `ta` words.
+struct DictPlans {
+  std::vector<Plan> self, query;
+};
+
+DictPlans dict_plans(const nw_batch* B, uint32_t ta) {
+  DictPlans p;
+  p.self.resize(B->dicts.size());
+  p.query.resize(B->dicts.size());
+  for (size_t d = 0; d < B->dicts.size(); ++d) {
+    if (B->self[d]) plan_all_pairs(B->dicts[d]->ws.bk, ta, p.self[d]);
+    if (B->qsets[d].n) plan_query(B->qsets[d].bk, B->dicts[d]->ws.bk, ta, p.query[d]);
+  }
+  return p;
 }
 
-// The segments of every dictionary whose longer length is LB, taken from the
-// dictionaries' plans made with A chunks of `ta` words, appended as one
-// launch (task0 rebased, dictionary tagged).
-void append_launch(const nw_batch* B, const std::vector<Plan>& plans, int LB, uint32_t ta, Plan& out) {
+// The segments of every dictionary and query set whose longer length is LB,
+// taken from plans made with A chunks of `ta` words, appended as one launch
+// (task0 rebased, terms tagged).
+void append_launch(const nw_batch* B, const DictPlans& plans, int LB, uint32_t ta, Plan& out) {
   LaunchPlan lp;
   lp.LB = LB;
   lp.role = 0;
@@ -50,18 +73,19 @@ void append_launch(const nw_batch* B, const std::vector<Plan>& plans, int LB, ui
   lp.seg_first = (uint32_t)out.segs.size();
   uint64_t task = 0;
   for (size_t d = 0; d < B->dicts.size(); ++d) {
-    const Plan& p = plans[d];
-    for (const LaunchPlan& q : p.launches) {
-      if (q.LB != LB) continue;
-      for (uint32_t s = 0; s < q.nsegs; ++s) {
-        Seg g = p.segs[q.seg_first + s];
-        g.task0 += task;
-        g.dict = (uint32_t)d;
-        out.segs.push_back(g);
+    for (const Plan* p : {&plans.self[d], &plans.query[d]}) {
+      for (const LaunchPlan& q : p->launches) {
+        if (q.LB != LB) continue;
+        for (uint32_t s = 0; s < q.nsegs; ++s) {
+          Seg g = p->segs[q.seg_first + s];
+          g.task0 += task;
+          g.dict = term_index(d, q.role);
+          out.segs.push_back(g);
+        }
+        task += q.ntasks;
+        lp.pairs += q.pairs;
+        lp.cells += q.cells;
       }
-      task += q.ntasks;
-      lp.pairs += q.pairs;
-      lp.cells += q.cells;
     }
   }
   lp.nsegs = (uint32_t)out.segs.size() - lp.seg_first;
@@ -124,12 +148,19 @@ nw_status issue_finalize(nw_batch* B) {
   for (size_t d = 0; d < B->dicts.size(); ++d) {
     const nw_dict* D = B->dicts[d];
     const uint32_t n = D->ws.n;
-    if (n == 0) continue;
     const uint32_t ib = index_bits(std::max<uint32_t>(n, 2));
-    NW_CK(launch_finalize(B->d_slots.as<uint32_t>() + B->list_off[d] * B->k, n, B->k, D->ws.perm.as<uint32_t>(),
-                          ib, (uint32_t)(((uint64_t)1 << ib) - 1), D->score_lo - 1,
-                          B->d_out_idx.as<uint32_t>() + B->list_off[d] * B->k,
-                          B->d_out_score.as<int16_t>() + B->list_off[d] * B->k, B->stream));
+    const uint32_t imask = (uint32_t)(((uint64_t)1 << ib) - 1);
+    if (B->self[d] && n) {
+      NW_CK(launch_finalize(B->d_slots.as<uint32_t>() + B->list_off[d] * B->k, n, B->k, D->ws.perm.as<uint32_t>(),
+                            ib, imask, D->score_lo - 1, B->d_out_idx.as<uint32_t>() + B->list_off[d] * B->k,
+                            B->d_out_score.as<int16_t>() + B->list_off[d] * B->k, B->stream));
+    }
+    const WordSet& Q = B->qsets[d];
+    if (Q.n) {  // query lists name dictionary words, as nw_query's do
+      NW_CK(launch_finalize(B->d_slots.as<uint32_t>() + B->qlist_off[d] * B->k, Q.n, B->k, Q.perm.as<uint32_t>(),
+                            ib, imask, B->q_key_lo[d], B->d_out_idx.as<uint32_t>() + B->qlist_off[d] * B->k,
+                            B->d_out_score.as<int16_t>() + B->qlist_off[d] * B->k, B->stream));
+    }
   }
   return NW_OK;
 }
@@ -145,7 +176,7 @@ nw_status autotune(nw_batch* B) {
     cudaEvent_t a, b;
     ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } evfree{e0, e1};
-  std::vector<std::vector<Plan>> plans;
+  std::vector<DictPlans> plans;
   for (uint32_t ta : kTaCandidates) plans.push_back(dict_plans(B, ta));
   for (int LB = 0; LB < kBuckets; ++LB) {
     float best = 0;
@@ -195,13 +226,42 @@ nw_status create_impl(nw_batch* B, const nw_batch_dict* dicts, uint32_t ndicts, 
                                             &dicts[d].scoring, flags & NW_DEVICE_PTRS, &D);
     if (st != NW_OK) return st;
     B->dicts.push_back(D);
+    B->qsets.emplace_back();
+    B->self.push_back(dicts[d].queries_only ? 0 : 1);
     const uint32_t ib = index_bits(std::max<uint32_t>(D->ws.n, 2));
-    if (D->score_lo < INT16_MIN + 1 || D->score_hi > INT16_MAX ||
-        (uint64_t)(D->score_hi - (D->score_lo - 1)) >= (1ull << (32 - ib)))
+    if (B->self[d] && (D->score_lo < INT16_MIN + 1 || D->score_hi > INT16_MAX ||
+                       (uint64_t)(D->score_hi - (D->score_lo - 1)) >= (1ull << (32 - ib))))
       return set_err(c, NW_ERANGE, "dictionary %u: scores [%d, %d] do not fit the list keys", d, D->score_lo,
                      D->score_hi);
     B->list_off.push_back(B->nlists);
-    B->nlists += D->ws.n;
+    if (B->self[d]) B->nlists += D->ws.n;
+    // the query set: ingested with the dictionary's alphabet and code shift;
+    // its list keys span the scores of the (query length, dictionary length)
+    // pairs present, as in nw_query
+    int32_t key_lo = 0;
+    if (dicts[d].nq) {
+      if (!dicts[d].qoffsets) return set_err(c, NW_EINVAL, "dictionary %u: null query offsets", d);
+      NW_TRY(ingest(c, dicts[d].qcodes, dicts[d].qoffsets, dicts[d].nq, D->alphabet, D->ss.shift,
+                    flags & NW_DEVICE_PTRS, B->qsets[d]));
+      const WordSet& Q = B->qsets[d];
+      int lo = INT32_MAX, hi = INT32_MIN;
+      for (int La = 0; La < kBuckets; ++La)
+        for (int Lb = 0; Lb < kBuckets; ++Lb) {
+          if (!Q.bk.count[La] || !D->ws.bk.count[Lb]) continue;
+          int l, h;
+          pair_bounds(D->sc, La, Lb, l, h);
+          lo = std::min(lo, l);
+          hi = std::max(hi, h);
+        }
+      if (D->ws.n == 0) lo = hi = 0;
+      if (lo < INT16_MIN + 1 || hi > INT16_MAX || (uint64_t)(hi - (lo - 1)) >= (1ull << (32 - ib)))
+        return set_err(c, NW_ERANGE, "query set %u: scores [%d, %d] do not fit the list keys", d, lo, hi);
+      key_lo = lo - 1;
+      B->query_words += Q.n;
+    }
+    B->q_key_lo.push_back(key_lo);
+    B->qlist_off.push_back(B->nlists);
+    B->nlists += B->qsets[d].n;
   }
   const size_t L = std::max<size_t>(1, B->nlists);
   NW_TRY(ctx_alloc(c, B->d_slots, sizeof(uint32_t) * L * B->k, "batch list slots"));
@@ -209,24 +269,37 @@ nw_status create_impl(nw_batch* B, const nw_batch_dict* dicts, uint32_t ndicts, 
   NW_TRY(ctx_alloc(c, B->d_out_idx, sizeof(uint32_t) * L * B->k, "batch output indices"));
   NW_TRY(ctx_alloc(c, B->d_out_score, sizeof(int16_t) * L * B->k, "batch output scores"));
   NW_TRY(ctx_alloc(c, B->d_small, 64 + sizeof(unsigned long long) * (kBuckets + 2), "batch counters"));
-  std::vector<DictTerms> terms(std::max<size_t>(1, B->dicts.size()));
+  std::vector<DictTerms> terms(std::max<size_t>(1, 3 * B->dicts.size()));
   for (size_t d = 0; d < B->dicts.size(); ++d) {
     const nw_dict* D = B->dicts[d];
+    const WordSet& Q = B->qsets[d];
     const uint32_t ib = index_bits(std::max<uint32_t>(D->ws.n, 2));
-    DictTerms& T = terms[d];
-    T.a_enc = D->ws.a_enc.as<uint32_t>();
-    T.b_rec = D->ws.b_rec.as<uint4>();
-    T.perm = D->ws.perm.as<uint32_t>();
-    T.slots = B->d_slots.as<uint32_t>() + B->list_off[d] * B->k;
-    T.thr = B->d_thr.as<uint32_t>() + B->list_off[d];
-    T.C1 = D->ss.C1;
-    T.C2 = D->ss.C2;
-    T.match = D->sc.match;
-    T.mismatch = D->sc.mismatch;
-    T.gap = D->sc.gap;
-    T.key_lo = D->score_lo - 1;
-    T.ib = ib;
-    T.imask = (uint32_t)(((uint64_t)1 << ib) - 1);
+    const SideView dict_side{D->ws.perm.as<uint32_t>(), B->d_slots.as<uint32_t>() + B->list_off[d] * B->k,
+                             B->d_thr.as<uint32_t>() + B->list_off[d]};
+    const SideView dict_nolists{D->ws.perm.as<uint32_t>(), nullptr, nullptr};
+    const SideView query_side{Q.perm.as<uint32_t>(), B->d_slots.as<uint32_t>() + B->qlist_off[d] * B->k,
+                              B->d_thr.as<uint32_t>() + B->qlist_off[d]};
+    for (int role = 0; role < 3; ++role) {
+      DictTerms& T = terms[term_index(d, role)];
+      T.a_enc = role == 1 ? Q.a_enc.as<uint32_t>() : D->ws.a_enc.as<uint32_t>();
+      T.b_rec = role == 2 ? Q.b_rec.as<uint4>() : D->ws.b_rec.as<uint4>();
+      T.A = role == 0 ? dict_side : (role == 1 ? query_side : dict_nolists);
+      T.B = role == 0 ? dict_side : (role == 1 ? dict_nolists : query_side);
+      T.C1 = D->ss.C1;
+      T.C2 = D->ss.C2;
+      T.match = D->sc.match;
+      T.mismatch = D->sc.mismatch;
+      T.gap = D->sc.gap;
+      T.key_lo = role == 0 ? D->score_lo - 1 : B->q_key_lo[d];
+      T.ib = ib;
+      T.imask = (uint32_t)(((uint64_t)1 << ib) - 1);
+    }
+    if (Q.n) {
+      Plan qp;
+      plan_query(Q.bk, D->ws.bk, kDefaultTA, qp);
+      B->query_pairs += qp.pairs;
+      B->query_cells += qp.cells;
+    }
   }
   NW_TRY(ctx_alloc(c, B->d_terms, sizeof(DictTerms) * terms.size(), "batch terms"));
   NW_CK(cudaMemcpyAsync(B->d_terms.p, terms.data(), sizeof(DictTerms) * terms.size(), cudaMemcpyHostToDevice,
@@ -239,7 +312,7 @@ nw_status create_impl(nw_batch* B, const nw_batch_dict* dicts, uint32_t ndicts, 
     std::vector<uint32_t> tas;  // the distinct chunk sizes chosen, each planned once
     for (int LB = 0; LB < kBuckets; ++LB)
       if (std::find(tas.begin(), tas.end(), B->ta_by_lb[LB]) == tas.end()) tas.push_back(B->ta_by_lb[LB]);
-    std::vector<std::vector<Plan>> plans;
+    std::vector<DictPlans> plans;
     for (uint32_t ta : tas) plans.push_back(dict_plans(B, ta));
     for (int LB = 0; LB < kBuckets; ++LB) {
       const size_t ci = std::find(tas.begin(), tas.end(), B->ta_by_lb[LB]) - tas.begin();
@@ -279,6 +352,7 @@ void destroy_impl(nw_batch* B) {
   if (B->graph) cudaGraphDestroy(B->graph);
   for (DevBuf* b : {&B->d_segs, &B->d_terms, &B->d_slots, &B->d_thr, &B->d_small, &B->d_out_idx, &B->d_out_score})
     ctx_free(c, *b);
+  for (WordSet& Q : B->qsets) free_wordset(c, Q);
   for (nw_dict* D : B->dicts) nw_dict_free(D);
   if (B->stream) cudaStreamDestroy(B->stream);
   delete B;
@@ -313,26 +387,42 @@ nw_status nw_batch_create(nw_ctx* ctx, const nw_batch_dict* dicts, uint32_t ndic
   return NW_OK;
 }
 
-nw_status nw_batch_run(nw_batch* B, uint32_t* const* nbr_idx, int16_t* const* nbr_score, uint32_t flags) {
+nw_status nw_batch_run_queries(nw_batch* B, uint32_t* const* nbr_idx, int16_t* const* nbr_score,
+                               uint32_t* const* qnbr_idx, int16_t* const* qnbr_score, uint32_t flags) {
   if (!B) return NW_EINVAL;
   nw_ctx* c = B->ctx;
   NW_ENTER(c);
-  if (!nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null output arrays");
   if (flags & NW_RANK_NORMALISED) return set_err(c, NW_EINVAL, "batches rank by raw score only");
+  const bool want_q = qnbr_idx || qnbr_score;
+  if (want_q && (!qnbr_idx || !qnbr_score)) return set_err(c, NW_EINVAL, "null query output arrays");
+  // every buffer the copies need, checked before the graph runs
+  for (size_t d = 0; d < B->dicts.size(); ++d) {
+    if (B->self[d] && B->dicts[d]->ws.n &&
+        (!nbr_idx || !nbr_score || !nbr_idx[d] || !nbr_score[d]))
+      return set_err(c, NW_EINVAL, "null output for dictionary %zu", d);
+    if (want_q && B->qsets[d].n && (!qnbr_idx[d] || !qnbr_score[d]))
+      return set_err(c, NW_EINVAL, "null query output for dictionary %zu", d);
+  }
   const bool dev = flags & NW_DEVICE_PTRS;
   const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   NW_CK(cudaGraphLaunch(B->exec, B->stream));
+  auto copy_out = [&](uint32_t* idx, int16_t* score, size_t first, size_t lists) -> nw_status {
+    const size_t cnt = lists * B->k;
+    NW_CK(cudaMemcpyAsync(idx, B->d_out_idx.as<uint32_t>() + first * B->k, sizeof(uint32_t) * cnt, kind, B->stream));
+    NW_CK(cudaMemcpyAsync(score, B->d_out_score.as<int16_t>() + first * B->k, sizeof(int16_t) * cnt, kind,
+                          B->stream));
+    return NW_OK;
+  };
   for (size_t d = 0; d < B->dicts.size(); ++d) {
-    const size_t cnt = (size_t)B->dicts[d]->ws.n * B->k;
-    if (!cnt) continue;
-    if (!nbr_idx[d] || !nbr_score[d]) return set_err(c, NW_EINVAL, "null output for dictionary %zu", d);
-    NW_CK(cudaMemcpyAsync(nbr_idx[d], B->d_out_idx.as<uint32_t>() + B->list_off[d] * B->k, sizeof(uint32_t) * cnt,
-                          kind, B->stream));
-    NW_CK(cudaMemcpyAsync(nbr_score[d], B->d_out_score.as<int16_t>() + B->list_off[d] * B->k,
-                          sizeof(int16_t) * cnt, kind, B->stream));
+    if (B->self[d] && B->dicts[d]->ws.n) NW_TRY(copy_out(nbr_idx[d], nbr_score[d], B->list_off[d], B->dicts[d]->ws.n));
+    if (want_q && B->qsets[d].n) NW_TRY(copy_out(qnbr_idx[d], qnbr_score[d], B->qlist_off[d], B->qsets[d].n));
   }
   if ((flags & NW_ASYNC) && dev) return NW_OK;
   return check_flags(c, B->stream, B->d_small.as<uint32_t>());
+}
+
+nw_status nw_batch_run(nw_batch* B, uint32_t* const* nbr_idx, int16_t* const* nbr_score, uint32_t flags) {
+  return nw_batch_run_queries(B, nbr_idx, nbr_score, nullptr, nullptr, flags);
 }
 
 nw_status nw_batch_info_get(const nw_batch* B, nw_batch_info* out) {
@@ -344,6 +434,9 @@ nw_status nw_batch_info_get(const nw_batch* B, nw_batch_info* out) {
   i.cells = B->plan.cells;
   i.tune_ms = B->tune_ms;
   for (int L = 0; L < kBuckets; ++L) i.words_per_task[L] = B->ta_by_lb[L];
+  i.query_words = B->query_words;
+  i.query_pairs = B->query_pairs;
+  i.query_cells = B->query_cells;
   *out = i;
   return NW_OK;
 }

@@ -247,7 +247,7 @@ __device__ __forceinline__ void pair_score_bounds(int match, int mismatch, int g
 }
 
 // Word sets, lists and scoring of one task: the kernel parameters, or in a
-// batched launch the terms of the segment's dictionary.
+// batched launch the terms of the segment (its dictionary or query set).
 struct TaskTerms {
   const uint32_t* a_enc;
   const uint4* b_rec;
@@ -284,8 +284,9 @@ __device__ __forceinline__ int g_bound(const DpParams& P, const TaskTerms& T, ui
 // per-pair epilogue at compile time:
 // kEpiMatrix writes the int8 upper triangle, kEpiLists updates neighbour lists
 // (and a shared or global histogram), kEpiListsLaneHist updates lists and the
-// per-lane shared histogram columns, kEpiBatchLists updates lists of the
-// segment's dictionary in a launch spanning many dictionaries.
+// per-lane shared histogram columns, kEpiBatchLists updates the lists named
+// by the segment's terms (a dictionary's own lists, or a query set's lists
+// against a dictionary) in a launch spanning many dictionaries.
 template <int LB, int EPI, bool TAB = false>
 __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const DpParams P) {
   extern __shared__ uint32_t s_dyn[];
@@ -326,8 +327,7 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
     TaskTerms T;
     if constexpr (EPI == kEpiBatchLists) {
       const DictTerms& D = P.terms[S.dict];
-      T = TaskTerms{D.a_enc, D.b_rec, SideView{D.perm, D.slots, D.thr}, SideView{D.perm, D.slots, D.thr},
-                    D.C1, D.C2, D.match, D.mismatch, D.gap, D.key_lo, D.ib, D.imask};
+      T = TaskTerms{D.a_enc, D.b_rec, D.A, D.B, D.C1, D.C2, D.match, D.mismatch, D.gap, D.key_lo, D.ib, D.imask};
     } else {
       T = TaskTerms{P.a_enc, P.b_rec, P.A, P.B, P.C1, P.C2, P.match, P.mismatch, P.gap, P.key_lo, P.ib, P.imask};
     }

@@ -66,18 +66,26 @@ struct Seg {
   uint16_t la;
   uint16_t tri;
   uint32_t nca;         // A chunks (tasks = nca * ceil((b_end - b_beg) / kWarpB))
-  uint32_t dict;        // dictionary of the segment in a batched launch (else 0)
+  uint32_t dict;        // terms of the segment in a batched launch (else 0)
   uint64_t task0;       // first task of the segment within its launch
 };
 
-// Per-dictionary terms of a batched launch: the word set, its lists and its
-// scoring constants (one entry per dictionary, indexed by Seg::dict).
+// One side of a launch: the word set providing A (or B) words.
+struct SideView {
+  const uint32_t* perm;   // sorted position -> original index of the set
+  uint32_t* slots;        // k list slots per word (sorted position), or null
+  uint32_t* thr;          // per-word lower bound of the k-th best key, or null
+};
+
+// Terms of one kind of segment in a batched launch (indexed by Seg::dict):
+// the A and B word sets with their lists and the scoring constants.  A
+// dictionary's own pairs take A = B = the dictionary with its lists; a query
+// set against a dictionary takes the query words on one side (with the
+// queries' lists) and the dictionary on the other (no lists).
 struct DictTerms {
   const uint32_t* a_enc;
   const uint4* b_rec;
-  const uint32_t* perm;
-  uint32_t* slots;
-  uint32_t* thr;
+  SideView A, B;
   uint32_t C1, C2;
   int32_t match, mismatch, gap;
   int32_t key_lo;
@@ -118,13 +126,6 @@ __host__ __device__ __forceinline__ TaskGeom task_geom(const Seg& S, uint64_t t,
 __host__ __device__ __forceinline__ bool pair_valid(const TaskGeom& g, uint32_t a, uint32_t b) {
   return b < g.bend && (!g.tri || a < b);
 }
-
-// One side of a launch: the word set providing A (or B) words.
-struct SideView {
-  const uint32_t* perm;   // sorted position -> original index of the set
-  uint32_t* slots;        // k list slots per word (sorted position), or null
-  uint32_t* thr;          // per-word lower bound of the k-th best key, or null
-};
 
 enum { kModeMatrix = 0, kModeLists = 1 };
 enum { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2, kHistLane = 3 };

@@ -33,7 +33,7 @@ EXPORTED = [
     "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
     "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc", "nw_all_pairs_topk_noalloc",
     "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
-    "nw_batch_create", "nw_batch_run", "nw_batch_info_get", "nw_batch_free", "nw_all_pairs_matrix_chunked",
+    "nw_batch_create", "nw_batch_run", "nw_batch_run_queries", "nw_batch_info_get", "nw_batch_free", "nw_all_pairs_matrix_chunked",
     "nw_debug_norm_tables", "nw_load_dictionary_sim",
     # nw_proposal.h
     "nw_model_create", "nw_model_free", "nw_model_param_count", "nw_model_get_params", "nw_model_set_params",
@@ -101,13 +101,15 @@ class RequestInfo(ctypes.Structure):
 
 class BatchDict(ctypes.Structure):
     _fields_ = [("codes", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n", ctypes.c_uint32),
-                ("alphabet", ctypes.c_uint32), ("scoring", Scoring)]
+                ("alphabet", ctypes.c_uint32), ("scoring", Scoring), ("qcodes", ctypes.c_void_p),
+                ("qoffsets", ctypes.c_void_p), ("nq", ctypes.c_uint32), ("queries_only", ctypes.c_uint32)]
 
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("ndicts", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("pairs", ctypes.c_uint64),
                 ("cells", ctypes.c_uint64), ("tune_ms", ctypes.c_double),
-                ("words_per_task", ctypes.c_uint32 * (MAX_WORD_LEN + 1))]
+                ("words_per_task", ctypes.c_uint32 * (MAX_WORD_LEN + 1)), ("query_words", ctypes.c_uint32),
+                ("query_pairs", ctypes.c_uint64), ("query_cells", ctypes.c_uint64)]
 
 
 _lib = None
@@ -172,6 +174,8 @@ def load_library(path: str = LIB_PATH):
     L.nw_server_destroy.restype = None
     L.nw_batch_create.argtypes = [vp, ctypes.POINTER(BatchDict), u32, u32, u32, ctypes.POINTER(vp)]
     L.nw_batch_run.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), u32]
+    L.nw_batch_run_queries.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), u32]
     L.nw_batch_info_get.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     L.nw_batch_free.argtypes = [vp]
     L.nw_batch_free.restype = None
@@ -488,20 +492,35 @@ def debug_norm_tables(scoring, lo: int, hi: int):
 
 
 class Batch:
-    """nw_batch_*: many dictionaries reduced to top-k lists in one CUDA-graph launch.
-    `dicts`: [(codes, offsets, alphabet, (match, mismatch, gap)), ...] as host numpy arrays."""
+    """nw_batch_*: many dictionaries, each with an optional query set, reduced to top-k
+    lists in one CUDA-graph launch.  `dicts`: [(codes, offsets, alphabet, (match, mismatch,
+    gap)[, (qcodes, qoffsets)[, queries_only]]), ...] as host numpy arrays."""
 
     def __init__(self, ctx: Context, dicts, k: int = 10, autotune: bool = True):
         L = load_library()
         arrs, specs = [], []
-        for codes, offsets, alphabet, scoring in dicts:
+
+        def csr(codes, offsets):
             codes = np.ascontiguousarray(codes, dtype=np.uint8)
             if codes.size == 0:
                 codes = np.zeros(1, np.uint8)
-            offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
-            arrs.append((codes, offsets))
+            return codes, np.ascontiguousarray(offsets, dtype=np.uint32)
+
+        self.sizes, self.qsizes, self.self_lists = [], [], []
+        for entry in dicts:
+            codes, offsets, alphabet, scoring = entry[:4]
+            queries = entry[4] if len(entry) > 4 else None
+            only = bool(entry[5]) if len(entry) > 5 else False
+            codes, offsets = csr(codes, offsets)
+            q = csr(*queries) if queries is not None else (None, None)
+            arrs.append((codes, offsets, q))
+            nq = q[1].size - 1 if q[1] is not None else 0
             specs.append(BatchDict(codes.ctypes.data, offsets.ctypes.data, offsets.size - 1, alphabet,
-                                   Scoring(*scoring)))
+                                   Scoring(*scoring), q[0].ctypes.data if nq else None,
+                                   q[1].ctypes.data if q[1] is not None else None, nq, int(only)))
+            self.sizes.append(offsets.size - 1)
+            self.qsizes.append(nq)
+            self.self_lists.append(not only)
         arr = (BatchDict * max(1, len(specs)))(*specs)
         h = ctypes.c_void_p()
         st = L.nw_batch_create(ctx.handle, arr, len(specs), k, NW_BATCH_AUTOTUNE if autotune else 0,
@@ -510,7 +529,6 @@ class Batch:
         self.handle = h
         self.ctx = ctx
         self.k = k
-        self.sizes = [o.size - 1 for _, o in arrs]
 
     def info(self) -> dict:
         i = BatchInfo()
@@ -519,16 +537,36 @@ class Batch:
         out["words_per_task"] = list(i.words_per_task)
         return out
 
+    def _host_lists(self, sizes):
+        return [(np.empty((n, self.k), np.uint32), np.empty((n, self.k), np.int16)) for n in sizes]
+
     def run(self, outputs=None):
         """One graph launch; returns [(idx[n, k] uint32, score[n, k] int16), ...] (host) or fills
         `outputs` (same structure, numpy or CUDA torch tensors)."""
         if outputs is None:
-            outputs = [(np.empty((n, self.k), np.uint32), np.empty((n, self.k), np.int16)) for n in self.sizes]
+            outputs = self._host_lists(self.sizes)
         ip = (ctypes.c_void_p * max(1, len(outputs)))(*[_ptr(o[0])[0] for o in outputs])
         sp = (ctypes.c_void_p * max(1, len(outputs)))(*[_ptr(o[1])[0] for o in outputs])
         flags = _flags(*[b for o in outputs for b in o])
         _check(self.ctx.handle, load_library().nw_batch_run(self.handle, ip, sp, flags))
         return outputs
+
+    def run_queries(self, outputs=None, query_outputs=None):
+        """One graph launch by nw_batch_run_queries; returns (outputs, query_outputs): each
+        dictionary's lists and each query set's lists [(idx[nq, k] uint32, score[nq, k] int16), ...]
+        (host arrays unless buffers are given; all buffers host or all CUDA tensors)."""
+        if outputs is None:
+            outputs = self._host_lists(self.sizes)
+        if query_outputs is None:
+            query_outputs = self._host_lists(self.qsizes)
+        n = max(1, len(outputs))
+        ip = (ctypes.c_void_p * n)(*[_ptr(o[0])[0] for o in outputs])
+        sp = (ctypes.c_void_p * n)(*[_ptr(o[1])[0] for o in outputs])
+        qip = (ctypes.c_void_p * n)(*[_ptr(o[0])[0] for o in query_outputs])
+        qsp = (ctypes.c_void_p * n)(*[_ptr(o[1])[0] for o in query_outputs])
+        flags = _flags(*[b for o in list(outputs) + list(query_outputs) for b in o])
+        _check(self.ctx.handle, load_library().nw_batch_run_queries(self.handle, ip, sp, qip, qsp, flags))
+        return outputs, query_outputs
 
     def free(self):
         if getattr(self, "handle", None) and getattr(self.ctx, "handle", None):

@@ -224,3 +224,16 @@ def batched_dictionaries(count: int = 64, size_lo: int = 1000, size_hi: int = 50
                                       length_stream=STREAM_LENGTH, code_stream=STREAM_CODE)
         out.append(BatchedDict(w, (match, mismatch, gap)))
     return out
+
+
+def batched_query_sets(dicts: list, size_lo: int = 1, size_hi: int = 4096, seed: int = 3) -> list:
+    """One query set per dictionary of `batched_dictionaries(seed=seed)`: sizes
+    floor(exp U(ln lo, ln hi)), lengths uniform on [1, 40], the dictionary's
+    alphabet with Zipf(1.0) codes (query streams of the dictionary's seed)."""
+    out = []
+    for d, x in enumerate(dicts):
+        sd = seed + d
+        u = uniform01(sd, STREAM_MISC, 1, start=5)  # after the dictionary's five draws
+        size = int(math.floor(math.exp(math.log(size_lo) + u[0] * (math.log(size_hi) - math.log(size_lo)))))
+        out.append(make_uniform_length_words(size, x.words.alphabet, 1.0, 1, 40, seed=sd))
+    return out

@@ -1,9 +1,11 @@
-"""Batches of independent dictionaries in one CUDA-graph launch.
+"""Batches of independent dictionaries and query sets in one CUDA-graph launch.
 
 Each dictionary has its own size, length range (up to 40), alphabet (40..120)
-and scoring; the batched lists must equal, bit for bit, the lists of each
-dictionary reduced alone and the oracle's, whatever tile shapes the autotuner
-picked, on every replay of the graph."""
+and scoring, and may bring a query set of its own size and lengths; the
+batched lists must equal, bit for bit, the lists of each dictionary reduced
+alone (nw_all_pairs_topk), of each query set answered alone (nw_query) and the
+oracle's, whatever tile shapes the autotuner picked, on every replay of the
+graph."""
 import numpy as np
 import pytest
 
@@ -67,3 +69,66 @@ def test_batch_device_outputs_and_fixed_tiles(ctx, dicts):
     for (hi, hs), (di, ds) in zip(host, dev):
         assert np.array_equal(hi, di.cpu().numpy().view(np.uint32)) and np.array_equal(hs, ds.cpu().numpy())
     b1.free()
+
+
+def test_batch_with_query_sets_equals_each_call_alone(ctx, dicts, oracle_mod):
+    import torch
+    qsets = synth.batched_query_sets(dicts, size_lo=1, size_hi=700, seed=30)
+    # dictionary 2 brings no queries; dictionary 5 asks only for its queries
+    entries = []
+    for i, (d, q) in enumerate(zip(dicts, qsets)):
+        e = (d.words.codes, d.words.offsets, d.words.alphabet, d.scoring)
+        if i == 2:
+            entries.append(e)
+        else:
+            entries.append(e + ((q.codes, q.offsets), i == 5))
+    batch = nw.Batch(ctx, entries, k=K)
+    info = batch.info()
+    nq = [0 if i == 2 else q.n for i, q in enumerate(qsets)]
+    assert info["query_words"] == sum(nq)
+    assert info["query_pairs"] == sum(a * d.words.n for a, d in zip(nq, dicts))
+    own = sum(d.words.n * (d.words.n - 1) // 2 for i, d in enumerate(dicts) if i != 5)
+    assert info["pairs"] == own + info["query_pairs"]
+    first, qfirst = batch.run_queries()
+    second, qsecond = batch.run_queries()
+    for i, (d, q) in enumerate(zip(dicts, qsets)):
+        alone = ctx.load_dictionary(d.words.codes, d.words.offsets, d.words.alphabet, d.scoring)
+        if i != 5:
+            ai, asc, _, _ = alone.all_pairs_topk(K, hist=None)
+            assert np.array_equal(first[i][0], ai) and np.array_equal(first[i][1], asc), i
+            assert np.array_equal(second[i][0], ai) and np.array_equal(second[i][1], asc), i
+        if i != 2:
+            qi, qs = alone.query(q.codes, q.offsets, K)
+            assert qfirst[i][0].shape == (q.n, K)
+            assert np.array_equal(qfirst[i][0], qi) and np.array_equal(qfirst[i][1], qs), i
+            assert np.array_equal(qsecond[i][0], qi) and np.array_equal(qsecond[i][1], qs), i
+        alone.free()
+    # the oracle on the three smallest query sets
+    for i in [j for j in np.argsort(nq) if nq[j]][:3]:
+        oi, os_ = oracle_mod.query_topk(qsets[i], dicts[i].words, K, dicts[i].scoring)
+        assert np.array_equal(qfirst[i][0], oi) and np.array_equal(qfirst[i][1].astype(np.int32), os_), i
+    # device buffers give the same lists
+    dev = [(torch.empty((d.words.n, K), dtype=torch.int32, device="cuda"),
+            torch.empty((d.words.n, K), dtype=torch.int16, device="cuda")) for d in dicts]
+    qdev = [(torch.empty((n, K), dtype=torch.int32, device="cuda"),
+             torch.empty((n, K), dtype=torch.int16, device="cuda")) for n in nq]
+    batch.run_queries(dev, qdev)
+    for i in range(len(dicts)):
+        if i != 5:
+            assert np.array_equal(dev[i][0].cpu().numpy().view(np.uint32), first[i][0])
+        assert np.array_equal(qdev[i][0].cpu().numpy().view(np.uint32), qfirst[i][0])
+        assert np.array_equal(qdev[i][1].cpu().numpy(), qfirst[i][1])
+    # the plain run still gives the dictionaries' lists
+    plain = batch.run()
+    assert all(np.array_equal(plain[i][0], first[i][0]) for i in range(len(dicts)) if i != 5)
+    batch.free()
+
+
+def test_batch_query_set_refusals(ctx, dicts):
+    d = dicts[0]
+    q = synth.batched_query_sets(dicts[:1], size_lo=5, size_hi=6, seed=30)[0]
+    bad = q.codes.copy()
+    bad[0] = d.words.alphabet  # a code outside the dictionary's alphabet
+    with pytest.raises(nw.NwError) as e:
+        nw.Batch(ctx, [(d.words.codes, d.words.offsets, d.words.alphabet, d.scoring, (bad, q.offsets))], k=K)
+    assert e.value.status == nw.NW_EINVAL

@@ -62,3 +62,17 @@ def test_batched_dictionaries_shapes():
         assert 100 <= d.words.n <= 400
         assert d.words.lengths.min() >= 1 and d.words.lengths.max() <= 40
         assert 40 <= d.words.alphabet <= 120 and d.words.codes.max() < d.words.alphabet
+
+
+def test_batched_query_sets_shapes():
+    ds = synth.batched_dictionaries(count=6, size_lo=100, size_hi=400)
+    qs = synth.batched_query_sets(ds, size_lo=1, size_hi=300)
+    assert len(qs) == len(ds)
+    for d, q in zip(ds, qs):
+        assert 1 <= q.n <= 300
+        assert q.lengths.min() >= 1 and q.lengths.max() <= 40
+        assert q.alphabet == d.words.alphabet and q.codes.max() < q.alphabet
+    # deterministic, and not a copy of the dictionaries' own words
+    again = synth.batched_query_sets(ds, size_lo=1, size_hi=300)
+    assert all(np.array_equal(a.codes, b.codes) and np.array_equal(a.offsets, b.offsets) for a, b in zip(qs, again))
+    assert len({q.n for q in qs}) > 1
