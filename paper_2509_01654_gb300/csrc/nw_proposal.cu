@@ -300,7 +300,7 @@ nw_status rescore_select(nw_ctx* c, nw_dict* d, const uint32_t* cand, uint32_t C
   NW_TRY(ctx_ensure(c, score_buf, prop::rescore_scratch_bytes(n, C), "candidate scores"));
   int32_t* score = score_buf.as<int32_t>();
   uint32_t* sorted = nullptr;
-  NW_CK(prop::rescore_sorted(pairs_params(d, err), cand, C, score, &sorted, s));
+  NW_CK(prop::rescore_sorted(pairs_params(d, err), cand, C, (int)d->ws.max_len, score, &sorted, s));
   NW_CK(prop::select_topk(sorted, score, n, C, k, out_idx, out_score, s));
   return NW_OK;
 }

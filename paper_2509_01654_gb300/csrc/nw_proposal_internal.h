@@ -59,9 +59,10 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
 // reordered by length (*sorted_out, n * C), and score[i * C + r] is the
 // score of (*sorted_out)[i * C + r].  score points at the start of a region
 // of rescore_scratch_bytes(n, C) (the scores, then the reordered candidates
-// and the work lists grouped by DP width).
+// and the work lists grouped by DP width).  max_len: the dictionary's
+// longest word (the widest DP; one launch per width up to it).
 size_t rescore_scratch_bytes(uint32_t n, uint32_t C);
-cudaError_t rescore_sorted(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score,
+cudaError_t rescore_sorted(const PairsParams& P, const uint32_t* cand, uint32_t C, int max_len, int32_t* score,
                            uint32_t** sorted_out, cudaStream_t s);
 // Words of a query set Q against a dictionary D for cross_rescore: QD reads
 // its streamed (A) words from Q and its register (B) words from D, DQ the

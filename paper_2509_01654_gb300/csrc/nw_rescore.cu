@@ -2,6 +2,7 @@
 // each row's candidates are reordered by length, and consecutive entries
 // share one thread's int16 halves (the row's word streamed, both candidates
 // in registers), so neither half of the packed DP idles.
+#include <algorithm>
 #include <climits>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -188,8 +189,77 @@ __global__ void __launch_bounds__(kBinThreads) scatter_widths_kernel(const Pairs
   if (p < m) items[base[w] + local] = p;
 }
 
+// Scores of pair item p (two consecutive entries of a row's length-sorted
+// candidates) with DP width LB >= both candidates' lengths.
+template <int LB, bool TAB>
+__device__ __forceinline__ void rescore_item(const PairsParams& P, const uint32_t* __restrict__ cs, uint32_t C,
+                                             uint64_t p, int32_t* __restrict__ score) {
+  const uint32_t Ch = (C + 1) / 2;
+  const uint32_t i = (uint32_t)(p / Ch), r = (uint32_t)(p - (uint64_t)i * Ch);
+  const size_t o = (size_t)i * C + 2 * r;
+  const bool two = 2 * r + 1 < C;
+  const uint32_t j0 = cs[o], j1 = two ? cs[o + 1] : 0xffffffffu;
+  bool ok0 = j0 != 0xffffffffu, ok1 = j1 != 0xffffffffu;
+  if (ok0 && (j0 >= P.n || j0 == i)) {
+    atomicOr(P.err, kErrInput);
+    ok0 = false;
+  }
+  if (ok1 && (j1 >= P.n || j1 == i)) {
+    atomicOr(P.err, kErrInput);
+    ok1 = false;
+  }
+  int s0 = INT32_MIN, s1 = INT32_MIN;
+  if (ok0 || ok1) {
+    const uint32_t ri = __ldg(P.rank + i);
+    const int la = __ldg(P.slen + ri);
+    const uint32_t rb0 = ok0 ? __ldg(P.rank + j0) : 0u, rb1 = ok1 ? __ldg(P.rank + j1) : 0u;
+    const int l0 = ok0 ? __ldg(P.slen + rb0) : 0, l1 = ok1 ? __ldg(P.slen + rb1) : 0;
+    const int2 t = pair2_score<LB, TAB>(P, ri, la, ok0, rb0, l0, ok1, rb1, l1);
+    if (ok0) s0 = t.x;
+    if (ok1) s1 = t.y;
+  }
+  score[o] = s0;
+  if (two) score[o + 1] = s1;
+}
+
+// The pair items of DP width LB: items[ends[LB - 1] .. ends[LB]) after the
+// grouping by width (ends[w] = first item past width w).  One launch per
+// width, so that each kernel's registers follow its own width (a single
+// kernel switching over every width is held to the widest case's registers
+// and occupancy).  The table variant keeps a table row pointer and code
+// halves live and gets twice the registers per thread.
+template <bool TAB>
+constexpr int rescore_min_blocks(int LB) { return TAB ? dp_min_blocks(LB) : 2 * dp_min_blocks(LB); }
+
+template <int LB, bool TAB>
+__global__ void __launch_bounds__(128, rescore_min_blocks<TAB>(LB)) rescore_width_kernel(
+    const PairsParams P, const uint32_t* __restrict__ cs, uint32_t C, const uint32_t* __restrict__ items,
+    const unsigned* __restrict__ ends, int32_t* __restrict__ score) {
+  const uint32_t beg = LB == 0 ? 0u : ends[LB - 1], end = ends[LB];
+  for (uint32_t t = beg + blockIdx.x * blockDim.x + threadIdx.x; t < end; t += gridDim.x * blockDim.x)
+    rescore_item<LB, TAB>(P, cs, C, items[t], score);
+}
+
+template <bool TAB>
+cudaError_t launch_rescore_width(int LB, unsigned grid, const PairsParams& P, const uint32_t* cs, uint32_t C,
+                                 const uint32_t* items, const unsigned* ends, int32_t* score, cudaStream_t s) {
+  switch (LB) {
+#define NW_CASE(L) \
+  case L: rescore_width_kernel<L, TAB><<<grid, 128, 0, s>>>(P, cs, C, items, ends, score); break;
+    NW_CASE(0) NW_CASE(1) NW_CASE(2) NW_CASE(3) NW_CASE(4) NW_CASE(5) NW_CASE(6) NW_CASE(7)
+    NW_CASE(8) NW_CASE(9) NW_CASE(10) NW_CASE(11) NW_CASE(12) NW_CASE(13) NW_CASE(14)
+    NW_CASE(15) NW_CASE(16) NW_CASE(17) NW_CASE(18) NW_CASE(19) NW_CASE(20) NW_CASE(21)
+    NW_CASE(22) NW_CASE(23) NW_CASE(24) NW_CASE(25) NW_CASE(26) NW_CASE(27) NW_CASE(28)
+    NW_CASE(29) NW_CASE(30) NW_CASE(31) NW_CASE(32) NW_CASE(33) NW_CASE(34) NW_CASE(35)
+    NW_CASE(36) NW_CASE(37) NW_CASE(38) NW_CASE(39) NW_CASE(40)
+#undef NW_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // one thread per two consecutive entries of a row's length-sorted candidates
-// (work item items[t], or t itself when items is null)
+// (work item t; used when the items are too many to group by width)
 __global__ void __launch_bounds__(128) rescore2_kernel(const PairsParams P, const uint32_t* __restrict__ cs, uint32_t C,
                                                        const uint32_t* __restrict__ items, uint64_t m,
                                                        int32_t* __restrict__ score) {
@@ -234,7 +304,7 @@ size_t rescore_scratch_bytes(uint32_t n, uint32_t C) {
   return ((size_t)n * C * 2 + m) * sizeof(uint32_t) + 256;
 }
 
-cudaError_t rescore_sorted(const PairsParams& P, const uint32_t* cand, uint32_t C, int32_t* score,
+cudaError_t rescore_sorted(const PairsParams& P, const uint32_t* cand, uint32_t C, int max_len, int32_t* score,
                            uint32_t** sorted_out, cudaStream_t s) {
   uint32_t* sorted = reinterpret_cast<uint32_t*>(score + (size_t)P.n * C);
   *sorted_out = sorted;
@@ -251,6 +321,25 @@ cudaError_t rescore_sorted(const PairsParams& P, const uint32_t* cand, uint32_t 
     count_widths_kernel<<<blocks, kBinThreads, 0, s>>>(P, sorted, C, (uint32_t)m, bins);
     scan_widths_kernel<<<1, 1, 0, s>>>(bins);
     scatter_widths_kernel<<<blocks, kBinThreads, 0, s>>>(P, sorted, C, (uint32_t)m, bins, items);
+    // the scatter left bins[w] at the end of width w's items: one launch per
+    // width up to the dictionary's longest word, each a grid of resident blocks
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaGetLastError();
+    }
+    const int top = max_len < 0 ? 0 : (max_len > kMaxLen ? kMaxLen : max_len);
+    for (int LB = 0; LB <= top; ++LB) {
+      const uint64_t cap = (uint64_t)sms * (uint64_t)(P.tab ? rescore_min_blocks<true>(LB)
+                                                            : rescore_min_blocks<false>(LB));
+      const unsigned grid = (unsigned)std::min<uint64_t>(cap, (m + 127) / 128);
+      e = P.tab ? launch_rescore_width<true>(LB, grid, P, sorted, C, items, bins, score, s)
+                : launch_rescore_width<false>(LB, grid, P, sorted, C, items, bins, score, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   rescore2_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(P, sorted, C, items, m, score);
   return cudaGetLastError();
