@@ -6,7 +6,9 @@ shard's pairs plus that shard's score histogram.  The full result is the
 k best of the union of all ranks' lists (``nw_topk_merge``, associative and
 order-independent because neighbour keys are totally ordered) and the sum of
 the histograms.  This module moves the partial results with torch.distributed
-(NCCL between GPUs, gloo on CPU) and merges them on the host.
+(NCCL between GPUs, gloo on CPU) and merges them on the host.  The same
+shards make a long exhaustive run resumable: ``topk_with_checkpoints`` saves
+each finished shard and, after an interruption, scores only the missing ones.
 """
 from __future__ import annotations
 
@@ -47,3 +49,59 @@ def allreduce_histogram(hist, group=None):
     t = _as_tensor(hist).clone()
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# checkpoint / resume of a long exhaustive run
+
+def _workload_tag(d, k: int, nshards: int, hist: bool, fingerprint: str) -> str:
+    i = d.info()
+    keys = ("n", "alphabet", "min_len", "max_len", "score_lo", "score_hi", "pairs", "cells")
+    return "|".join([f"{key}={i[key]}" for key in keys] + [f"k={k}", f"nshards={nshards}", f"hist={int(hist)}",
+                                                          f"fingerprint={fingerprint}"])
+
+
+def topk_with_checkpoints(d, k: int, nshards: int, ckpt_dir: str, hist: bool = True, fingerprint: str = "",
+                          after_shard=None):
+    """The exhaustive top-k lists (and histogram) of dictionary `d`, computed as
+    `nshards` shards (``nw_all_pairs_topk_shard``) with each finished shard
+    saved to `ckpt_dir`.  A run that stops between shards (a crash, a
+    preemption) is resumed by calling this again with the same arguments: the
+    saved shards are read back and only the missing ones are scored.  The
+    result is exactly that of one ``nw_all_pairs_topk`` call: every pair lies
+    in one shard, the histograms add up, and the merge of the partial lists is
+    exact and order-independent.
+
+    `fingerprint` (e.g. a hash of the word list) is stored with each shard, as
+    are the dictionary's size, lengths, score range and pair counts; a shard
+    saved for another workload is refused.  `after_shard(g)` is called after
+    shard g is saved.  Returns (idx uint32 [n, k], score int16 [n, k], hist
+    int64 or None, hist_lo)."""
+    import os
+
+    if nshards < 1:
+        raise ValueError("nshards must be >= 1")
+    os.makedirs(ckpt_dir, exist_ok=True)
+    tag = _workload_tag(d, k, nshards, hist, fingerprint)
+    parts, total, lo = [], None, 0
+    for g in range(nshards):
+        path = os.path.join(ckpt_dir, f"shard{g:05d}-of-{nshards:05d}.npz")
+        if os.path.exists(path):
+            with np.load(path) as z:
+                if str(z["tag"]) != tag:
+                    raise ValueError(f"{path} was saved for another workload")
+                idx, score, lo = z["idx"], z["score"], int(z["hist_lo"])
+                h = z["hist"] if hist else None
+        else:
+            idx, score, h, lo = d.all_pairs_topk(k, hist=hist, shard=(g, nshards))
+            tmp = path + ".partial.npz"
+            np.savez(tmp, tag=np.array(tag), idx=idx, score=score, hist_lo=np.array(lo),
+                     hist=h if hist else np.zeros(0, np.int64))
+            os.replace(tmp, path)  # a shard file is complete or absent
+            if after_shard is not None:
+                after_shard(g)
+        parts.append((idx, score))
+        if hist:
+            total = h.astype(np.int64).copy() if total is None else total + h
+    idx, score = nw.topk_merge(parts, k)
+    return idx, score, total, lo

@@ -183,6 +183,40 @@ def test_shards_merge_to_full_result(ctx, oracle_mod, G):
     assert np.array_equal(hsum, full[2])
 
 
+def test_interrupted_run_resumes_from_checkpoints(ctx, oracle_mod, tmp_path):
+    # a run that stops after its third shard (an exception raised on the host
+    # between shards) resumes from the saved shards and scores only the rest
+    from paper_2509_01654_gb300 import dist
+    w = synth.make_words(1500, 40, 1.1, 8.0, 3.0, 1, 25, seed=8)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    full = d.all_pairs_topk(10)
+    done = []
+
+    def stop_after_third(g):
+        done.append(g)
+        if g == 2:
+            raise RuntimeError("interrupted")
+
+    ck = str(tmp_path / "ck")
+    with pytest.raises(RuntimeError):
+        dist.topk_with_checkpoints(d, 10, 5, ck, fingerprint="seed8", after_shard=stop_after_third)
+    assert done == [0, 1, 2]
+    done.clear()
+    idx, score, hist, lo = dist.topk_with_checkpoints(d, 10, 5, ck, fingerprint="seed8", after_shard=done.append)
+    assert done == [3, 4]
+    assert np.array_equal(idx, full[0]) and np.array_equal(score, full[1])
+    assert np.array_equal(hist, full[2]) and lo == full[3]
+    # everything saved: a third call scores nothing and gives the same result
+    done.clear()
+    again = dist.topk_with_checkpoints(d, 10, 5, ck, fingerprint="seed8", after_shard=done.append)
+    assert done == [] and np.array_equal(again[0], idx) and np.array_equal(again[2], hist)
+    # shards saved for another workload are refused
+    with pytest.raises(ValueError):
+        dist.topk_with_checkpoints(d, 10, 5, ck, fingerprint="other words")
+    oi, os_ = oracle_mod.topk_rows(w, np.arange(0, w.n, 7), 10, (1, -1, -1))
+    assert np.array_equal(idx[::7], oi) and np.array_equal(score[::7].astype(np.int32), os_)
+
+
 def test_score_pairs(ctx, oracle_mod):
     w = synth.make_uniform_length_words(500, 30, 1.0, 0, 40, seed=10)
     sc = (2, -1, -2)
