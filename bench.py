@@ -54,6 +54,23 @@ def kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def tensor_roofline(flops: float, ms: float, peaks_path: str = os.path.join(ROOT, "MEASURED_PEAKS.json")) -> dict:
+    """Roofline of a bf16 tensor-core contraction: `flops` algorithmic FLOPs in
+    `ms` milliseconds against the measured bf16 burst peak of MEASURED_PEAKS.json,
+    or the 1,900 TFLOP/s fallback when that file is absent."""
+    peak, basis = 1900.0, "fallback bf16 dense burst (1,900 TFLOP/s)"
+    try:
+        with open(peaks_path) as f:
+            v = float(json.load(f)["bf16_tflops"])
+        if v > 0:
+            peak, basis = v, "measured bf16 burst (MEASURED_PEAKS.json bf16_tflops)"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_basis": basis}
+
+
 def workload_config(n, w, info):
     return {
         "workload": f"exhaustive all-pairs NW, {n:,} synthetic words (lengths round(N(8,3)) on [1,25], "
@@ -545,6 +562,9 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
                   "loss_last_100": round(float(np.mean(losses[-100:])), 5), **train_cfg},
         "exhaustive_ms": round(exhaustive_ms, 3),
         "by_candidates": res,
+        # the candidate kernel: 2 n^2 d FLOP of bf16 products (d = 64) per launch
+        "candidates_roofline": {str(C): tensor_roofline(2.0 * n * n * 64, r["ms"]["candidates_ms"])
+                                for C, r in res.items()},
         "queries": queries,
         "ablation": ablation,
     }
