@@ -118,6 +118,31 @@ def test_topk_heavy_ties(ctx, oracle_mod):
     check_topk(oracle_mod, d, w, (1, -1, -1), 10)
 
 
+def test_all_equal_words(ctx, oracle_mod):
+    # one bucket, every pair identical: every score is len * match, each list
+    # is the lowest other indices, the histogram has one non-empty bin
+    word = [3, 1, 4, 1, 5, 9, 2, 6, 5]
+    w = synth.WordList.from_lists([word] * 300, alphabet=10)
+    sc = (1, -1, -1)
+    d = ctx.load_dictionary(w.codes, w.offsets, 10, sc)
+    idx, score, h, lo = check_topk(oracle_mod, d, w, sc, 10)
+    assert np.all(score == len(word))
+    for i in (0, 5, 299):
+        assert list(idx[i]) == [j for j in range(11) if j != i][:10]
+    assert h[len(word) - lo] == w.n * (w.n - 1) // 2 and h.sum() == h[len(word) - lo]
+    assert np.all(d.all_pairs_matrix() == len(word))
+
+
+def test_single_length_bucket(ctx, oracle_mod):
+    # every word of one length: one bucket, only same-length (triangular) tasks
+    w = synth.make_uniform_length_words(900, 6, 1.0, 12, 12, seed=12)
+    sc = (2, -1, -2)
+    d = ctx.load_dictionary(w.codes, w.offsets, 6, sc)
+    _, _, h, lo = check_topk(oracle_mod, d, w, sc, 10)
+    assert np.array_equal(h, oracle_mod.histogram(w, sc, lo, h.size))
+    assert np.array_equal(d.all_pairs_matrix().astype(np.int32), oracle_mod.all_pairs(w, sc))
+
+
 def test_topk_empty_words(ctx, oracle_mod):
     w = synth.make_uniform_length_words(400, 5, 1.0, 0, 6, seed=8)
     assert (w.lengths == 0).sum() > 10
