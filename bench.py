@@ -141,11 +141,15 @@ def oracle_sample(w, rows_target_s: float, min_rows: int = 8, max_rows: int = 50
     from paper_2509_01654_gb300 import synth
 
     threads = oracle.default_threads()
-    probe = synth.sample_rows(w.n, min_rows, seed=7)
+    min_rows = max(min_rows, threads)  # the probe keeps every thread busy, as the sample does
+    # a first call warms the threads and the word arrays; the second, on four
+    # rows per thread, sets the sample size for about rows_target_s of work
+    oracle.topk_rows(w, synth.sample_rows(w.n, min_rows, seed=8), K_NEIGHBOURS, SCORING, nthreads=threads)
+    probe = synth.sample_rows(w.n, 4 * min_rows, seed=7)
     t0 = time.perf_counter()
     oracle.topk_rows(w, probe, K_NEIGHBOURS, SCORING, nthreads=threads)
     dt = time.perf_counter() - t0
-    rows = int(max(min_rows, min(max_rows, min_rows * rows_target_s / max(dt, 1e-3))))
+    rows = int(max(min_rows, min(max_rows, probe.size * rows_target_s / max(dt, 1e-3))))
     rows -= rows % threads if rows > threads else 0
     sample = synth.sample_rows(w.n, rows, seed=6)
     t0 = time.perf_counter()
