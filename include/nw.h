@@ -420,6 +420,17 @@ nw_status nw_debug_enumerate_pairs(const uint32_t *lengths, uint32_t n, uint32_t
                                    uint32_t nshards, uint32_t *a, uint32_t *b, uint64_t cap,
                                    uint64_t *count);
 
+/* Host-only: the (query, dictionary word) pairs that nw_query's kernels
+ * would score for query words of lengths q_lengths[0..nq) against dictionary
+ * words of lengths d_lengths[0..nd), with `ta` A words per task (0 = the
+ * default; batches use 64, 128 or 256), as original-index pairs (q[p], d[p]).
+ * Writes at most `cap` pairs and sets *count to the total.  Runs the same
+ * query planner and task-to-pair mapping as the kernels, on the CPU, so tests
+ * can check that every (query, word) pair is covered exactly once. */
+nw_status nw_debug_enumerate_query_pairs(const uint32_t *q_lengths, uint32_t nq, const uint32_t *d_lengths,
+                                         uint32_t nd, uint32_t ta, uint32_t *q, uint32_t *d, uint64_t cap,
+                                         uint64_t *count);
+
 /* Host-only: the tables behind NW_RANK_NORMALISED for scores [lo, hi].
  * *nranks receives the number of distinct weights s/m (rank 0 = smallest);
  * when it is <= cap_ranks, also writes

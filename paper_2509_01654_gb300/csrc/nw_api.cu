@@ -652,6 +652,53 @@ nw_status nw_debug_enumerate_pairs(const uint32_t* lengths, uint32_t n, uint32_t
   return NW_OK;
 }
 
+nw_status nw_debug_enumerate_query_pairs(const uint32_t* q_lengths, uint32_t nq, const uint32_t* d_lengths,
+                                         uint32_t nd, uint32_t ta, uint32_t* q, uint32_t* d, uint64_t cap,
+                                         uint64_t* count) {
+  if (!q_lengths || !d_lengths || !count) return NW_EINVAL;
+  if (cap && (!q || !d)) return NW_EINVAL;
+  // each set bucketed by length as ingest does (stable), then planned as nw_query plans it
+  auto bucket = [](const uint32_t* len, uint32_t n, Buckets& bk, std::vector<uint32_t>& perm) -> bool {
+    bk = Buckets{};
+    for (uint32_t i = 0; i < n; ++i) {
+      if (len[i] > (uint32_t)kMaxLen) return false;
+      ++bk.count[len[i]];
+    }
+    fill_buckets(bk);
+    perm.assign(n, 0);
+    std::vector<uint32_t> fill(kBuckets, 0);
+    for (uint32_t i = 0; i < n; ++i) perm[bk.start[len[i]] + fill[len[i]]++] = i;
+    return true;
+  };
+  Buckets qb, db;
+  std::vector<uint32_t> qperm, dperm;
+  if (!bucket(q_lengths, nq, qb, qperm) || !bucket(d_lengths, nd, db, dperm)) return NW_EINVAL;
+  const uint32_t TA = ta ? ta : kDefaultTA;
+  Plan plan;
+  plan_query(qb, db, TA, plan);
+  uint64_t cnt = 0;
+  for (const LaunchPlan& lp : plan.launches) {
+    const Seg* segs = plan.segs.data() + lp.seg_first;
+    for (uint64_t t = 0; t < lp.ntasks; ++t) {
+      const Seg& S = segs[find_seg(segs, lp.nsegs, t)];
+      const TaskGeom g = task_geom(S, t, TA);
+      for (uint32_t x = g.a0; x < g.a1; ++x) {
+        for (uint32_t y = g.b0; y < g.bend; ++y) {
+          if (!pair_valid(g, x, y)) continue;
+          // role 1: queries are the A words; role 2: queries are the B words
+          if (cnt < cap) {
+            q[cnt] = lp.role == 1 ? qperm[x] : qperm[y];
+            d[cnt] = lp.role == 1 ? dperm[y] : dperm[x];
+          }
+          ++cnt;
+        }
+      }
+    }
+  }
+  *count = cnt;
+  return NW_OK;
+}
+
 nw_status nw_debug_fail_alloc(nw_ctx* c, uint32_t countdown) {
   if (!c) return NW_EINVAL;
   c->fail_countdown = countdown;

@@ -31,7 +31,8 @@ EXPORTED = [
     "nw_create", "nw_destroy", "nw_last_error", "nw_set_profiling", "nw_last_profile",
     "nw_load_dictionary", "nw_dict_info_get", "nw_dict_free", "nw_all_pairs_matrix",
     "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
-    "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_fail_alloc", "nw_all_pairs_topk_noalloc",
+    "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_enumerate_query_pairs", "nw_debug_fail_alloc",
+    "nw_all_pairs_topk_noalloc",
     "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
     "nw_batch_create", "nw_batch_run", "nw_batch_run_queries", "nw_batch_info_get", "nw_batch_free", "nw_all_pairs_matrix_chunked",
     "nw_debug_norm_tables", "nw_load_dictionary_sim",
@@ -145,6 +146,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_query.argtypes = [vp, vp, vp, u32, u32, vp, vp, u32]
     L.nw_measure_int_rates.argtypes = [vp, ctypes.c_double, ctypes.POINTER(IntRates)]
     L.nw_debug_enumerate_pairs.argtypes = [vp, u32, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
+    L.nw_debug_enumerate_query_pairs.argtypes = [vp, u32, vp, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
     L.nw_debug_fail_alloc.argtypes = [vp, u32]
     L.nw_debug_norm_tables.argtypes = [ctypes.POINTER(Scoring), i32, i32, vp, vp, vp, u32, ctypes.POINTER(u32)]
     L.nw_model_create.argtypes = [vp, u32, u64, ctypes.POINTER(vp)]
@@ -446,6 +448,27 @@ def topk_merge(parts, k: int):
     if st != NW_OK:
         raise NwError(st, "nw_topk_merge failed")
     return oi, os_
+
+
+def debug_enumerate_query_pairs(q_lengths, d_lengths, ta: int = 0):
+    """The (query, dictionary word) original-index pairs nw_query's kernels would score."""
+    L = load_library()
+    ql = np.ascontiguousarray(q_lengths, dtype=np.uint32)
+    dl = np.ascontiguousarray(d_lengths, dtype=np.uint32)
+    qp = ql if ql.size else np.zeros(1, np.uint32)
+    dp = dl if dl.size else np.zeros(1, np.uint32)
+    cnt = ctypes.c_uint64()
+    st = L.nw_debug_enumerate_query_pairs(qp.ctypes.data, ql.size, dp.ctypes.data, dl.size, ta, None, None, 0,
+                                          ctypes.byref(cnt))
+    if st != NW_OK:
+        raise NwError(st, "nw_debug_enumerate_query_pairs failed")
+    q = np.empty(max(1, cnt.value), dtype=np.uint32)
+    d = np.empty(max(1, cnt.value), dtype=np.uint32)
+    st = L.nw_debug_enumerate_query_pairs(qp.ctypes.data, ql.size, dp.ctypes.data, dl.size, ta, q.ctypes.data,
+                                          d.ctypes.data, cnt.value, ctypes.byref(cnt))
+    if st != NW_OK:
+        raise NwError(st, "nw_debug_enumerate_query_pairs failed")
+    return q[:cnt.value], d[:cnt.value]
 
 
 def debug_enumerate_pairs(lengths, shard: int = 0, nshards: int = 1):

@@ -84,6 +84,27 @@ def test_planner_degenerate_sizes(lib):
         assert as_set(a, b)[1] == all_unordered(len(L))
 
 
+@pytest.mark.parametrize("case,ta", [("mixed", 0), ("mixed", 64), ("ragged_big", 128), ("long_queries", 256),
+                                     ("with_empty", 0), ("no_queries", 0)])
+def test_query_planner_covers_each_pair_once(lib, case, ta):
+    # nw_query and the batched query sets: every (query, word) pair exactly once
+    rng = np.random.default_rng(len(case) + ta)
+    if case == "mixed":
+        Q, D = rng.integers(1, 12, 70), rng.integers(1, 12, 300)
+    elif case == "ragged_big":
+        Q, D = synth.serving_queries(257).lengths, synth.exhaustive_words(1100).lengths
+    elif case == "long_queries":
+        Q, D = rng.integers(26, 41, 90), rng.integers(1, 26, 400)   # queries longer than every word
+    elif case == "with_empty":
+        Q, D = rng.integers(0, 4, 40), rng.integers(0, 4, 130)
+    else:
+        Q, D = np.zeros(0, np.int64), rng.integers(1, 9, 50)
+    q, d = nw.debug_enumerate_query_pairs(Q, D, ta)
+    pairs = list(zip(q.tolist(), d.tolist()))
+    assert len(pairs) == len(set(pairs)) == Q.size * D.size
+    assert set(pairs) == {(i, j) for i in range(Q.size) for j in range(D.size)}
+
+
 def test_topk_merge_matches_full_lists(lib, oracle_mod):
     w = synth.make_words(90, 5, 1.0, 4.0, 2.0, 1, 8, seed=12)
     sc = (1, -1, -1)
