@@ -125,6 +125,7 @@ def test_batch_with_query_sets_equals_each_call_alone(ctx, dicts, oracle_mod):
 
 
 def test_batch_query_set_refusals(ctx, dicts):
+    import ctypes
     d = dicts[0]
     q = synth.batched_query_sets(dicts[:1], size_lo=5, size_hi=6, seed=30)[0]
     bad = q.codes.copy()
@@ -132,3 +133,18 @@ def test_batch_query_set_refusals(ctx, dicts):
     with pytest.raises(nw.NwError) as e:
         nw.Batch(ctx, [(d.words.codes, d.words.offsets, d.words.alphabet, d.scoring, (bad, q.offsets))], k=K)
     assert e.value.status == nw.NW_EINVAL
+    # a queries-only batch needs no dictionary outputs; its query outputs are required
+    b = nw.Batch(ctx, [(d.words.codes, d.words.offsets, d.words.alphabet, d.scoring, (q.codes, q.offsets), True)],
+                 k=K, autotune=False)
+    L = nw.load_library()
+    qi = np.empty((q.n, K), np.uint32)
+    qs = np.empty((q.n, K), np.int16)
+    P = ctypes.c_void_p * 1
+    st = L.nw_batch_run_queries(b.handle, None, None, P(qi.ctypes.data), P(qs.ctypes.data), 0)
+    assert st == nw.NW_OK
+    alone = ctx.load_dictionary(d.words.codes, d.words.offsets, d.words.alphabet, d.scoring)
+    ai, asc = alone.query(q.codes, q.offsets, K)
+    assert np.array_equal(qi, ai) and np.array_equal(qs, asc)
+    st = L.nw_batch_run_queries(b.handle, None, None, P(None), P(None), 0)
+    assert st == nw.NW_EINVAL
+    b.free()
