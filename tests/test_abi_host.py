@@ -184,3 +184,39 @@ def test_normalised_rank_tables(lib, sc, lo, hi):
             reach = [s for s in range(a, b + 1) if int(rank[s - lo, m]) >= r]
             assert int(smin[r, m]) == (min(reach) if reach else 32767)
     assert seen == set(range(R))  # every rank is some reachable weight
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "nw.h"
+#include "nw_proposal.h"
+int main(void) {
+  nw_ctx *ctx = NULL;
+  nw_status st = nw_create(&ctx, 0, 0, NULL);
+  if (st == NW_OK) { nw_destroy(ctx); return 0; }
+  const char *msg = nw_last_error(NULL);
+  printf("%d %s\n", (int)st, msg ? msg : "");
+  return msg && msg[0] ? 3 : 4;
+}
+"""
+
+
+def test_headers_are_plain_c_and_link(lib, tmp_path):
+    # the boundary is a C ABI: both headers compile as strict C99 and a C
+    # program links against libnw and calls it (no GPU: a clean error status)
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text(C_PROGRAM)
+    libdir = os.path.dirname(nw.LIB_PATH)
+    exe = tmp_path / "t"
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc,
+                        str(src), "-L", libdir, "-lnw", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert run.returncode in (0, 3), run.stdout + run.stderr
