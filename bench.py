@@ -36,13 +36,10 @@ SCORING = (1, -1, -1)
 K_NEIGHBOURS = 10
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM traffic of the alignment kernel from the ncu capture summarised in
-# profiles/ (bytes per launch, averaged over the launches of one step), valid
-# only for the kernel source it was measured on.
 # DRAM bytes (read + write) of one step's alignment launches on the 600k
-# workload, from ncu dram__bytes_read.sum + dram__bytes_write.sum (one pass,
-# profiles/traffic_exhaustive_600k_words.md); valid while the kernel sources
-# hash to kernel_sha
+# workload, from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
+# (summarised under profiles/); valid only while the kernel sources hash to
+# kernel_sha, and reported as null otherwise
 TRAFFIC = {"kernel_sha": "9b17614b2a258dd0", "bytes_per_step": 440.0e6}
 
 

@@ -379,6 +379,13 @@ void nw_server_destroy(nw_server *srv);
  *     call's contents; each call clears what must start at zero.  Calls whose
  *     GPU work overlaps (other contexts or streams on the same device) race on
  *     the array and give wrong results: serialise them.
+ *   - With NW_ASYNC the call returns before its kernels finish, so it cannot
+ *     report a device-side failure (a bound that ran out, a score outside the
+ *     histogram) itself.  Such a failure is kept in the array and the next
+ *     synchronous call of this entry point on the same device reports it
+ *     (NW_ETIMEOUT / NW_ERANGE / NW_EINVAL, message naming the earlier
+ *     NW_ASYNC call) after computing its own, valid, outputs; then it clears
+ *     it.  An NW_ASYNC call never clears it.
  *   - The array occupies device memory on every GPU that loads the library
  *     until the process exits. */
 #define NW_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -447,6 +454,25 @@ nw_status nw_debug_norm_tables(const nw_scoring *scoring, int32_t lo, int32_t hi
 /* Test hook: the `countdown`-th device allocation of the context from now on
  * fails as if the device were out of memory (0 disables).  Host-side only. */
 nw_status nw_debug_fail_alloc(nw_ctx *ctx, uint32_t countdown);
+
+/* Test hook for the device-side bounds (failure detection without a GPU
+ * fault).  Later calls on the context use:
+ *   insert_iters  >= 0: neighbour-list insertions of the alignment kernels
+ *                 give up after this many compare-and-swap rounds (0: at the
+ *                 first offer) and the call returns NW_ETIMEOUT; < 0 restores
+ *                 the kernel's own bound (2^20 rounds);
+ *   wait_cycles   >= 0: every pipeline wait of the candidate kernel
+ *                 (nw_dot_topk, nw_dot_topk_cross, the proposal calls) gives
+ *                 up after this many SM clock cycles; < 0 restores its own
+ *                 bound (2e9 cycles, about a second);
+ *   withhold_tile != UINT32_MAX: the candidate kernel's producer never issues
+ *                 the bulk copy of this column tile (of 64 columns), so every
+ *                 wait for it runs out with no copy in flight; the kernel
+ *                 still waits (bounded) for the copies it did issue before it
+ *                 exits.  The call returns NW_ETIMEOUT.
+ * The context stays usable: a later call with the defaults restored is
+ * correct.  Host-side only; NW_EINVAL for a null context. */
+nw_status nw_debug_set_bounds(nw_ctx *ctx, int32_t insert_iters, int64_t wait_cycles, uint32_t withhold_tile);
 
 #ifdef __cplusplus
 }

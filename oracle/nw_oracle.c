@@ -141,7 +141,12 @@ typedef struct {
     size_t npairs;
     const int32_t *sim; /* NULL: match / mismatch; else alphabet x alphabet */
     int alphabet;
+    int failed; /* set by a worker whose scratch allocation failed */
 } job_t;
+
+/* a worker that could not allocate its scratch marks the job failed, so the
+ * call reports NWO_ENOMEM instead of returning with rows unwritten */
+static void worker_failed(job_t *J) { __atomic_store_n(&J->failed, 1, __ATOMIC_RELAXED); }
 
 /* a pair's score under the job's similarity */
 static int32_t score_job(const job_t *J, int32_t *H, const uint8_t *A, int la, const uint8_t *B, int lb) {
@@ -180,7 +185,7 @@ static int run_threads(job_t *job, void (*fn)(job_t *, int)) {
         else fn(job, t); /* a thread that could not start: do its share here */
     }
     free(th); free(ws);
-    return NWO_OK;
+    return __atomic_load_n(&job->failed, __ATOMIC_RELAXED) ? NWO_ENOMEM : NWO_OK;
 }
 
 static int max_length(const uint32_t *offsets, uint32_t n) {
@@ -201,7 +206,7 @@ static int32_t *matrix_buffer(int la_max, int lb_max) {
 
 static void all_pairs_rows(job_t *J, int tid) {
     int32_t *H = matrix_buffer(J->maxlen, J->maxlen);
-    if (!H) return;
+    if (!H) { worker_failed(J); return; }
     const uint64_t n = J->n;
     for (uint64_t i = (uint64_t)tid; i + 1 < n; i += (uint64_t)J->nthreads) {
         const uint8_t *A = J->codes + J->offsets[i];
@@ -256,7 +261,7 @@ static void keep_best(uint32_t *idx, int32_t *sc, uint32_t k, uint32_t *cnt, int
 
 static void topk_rows_worker(job_t *J, int tid) {
     int32_t *H = matrix_buffer(J->maxlen, J->maxlen);
-    if (!H) return;
+    if (!H) { worker_failed(J); return; }
     for (uint32_t r = (uint32_t)tid; r < J->nrows; r += (uint32_t)J->nthreads) {
         uint32_t i = J->rows[r];
         const uint8_t *A = J->codes + J->offsets[i];
@@ -304,7 +309,7 @@ static int ranks_before_norm(int32_t s1, int32_t m1, uint32_t j1, int32_t s2, in
 static void topk_rows_norm_worker(job_t *J, int tid) {
     int32_t *H = matrix_buffer(J->maxlen, J->maxlen);
     int32_t *den = (int32_t *)malloc(sizeof(int32_t) * J->k);
-    if (!H || !den) { free(H); free(den); return; }
+    if (!H || !den) { free(H); free(den); worker_failed(J); return; }
     for (uint32_t r = (uint32_t)tid; r < J->nrows; r += (uint32_t)J->nthreads) {
         uint32_t i = J->rows[r];
         const uint8_t *A = J->codes + J->offsets[i];
@@ -360,7 +365,7 @@ int nwo_topk_rows_normalised(const uint8_t *codes, const uint32_t *offsets, uint
 static void query_worker(job_t *J, int tid) {
     int m = J->maxlen > J->qmaxlen ? J->maxlen : J->qmaxlen;
     int32_t *H = matrix_buffer(m, m);
-    if (!H) return;
+    if (!H) { worker_failed(J); return; }
     for (uint32_t q = (uint32_t)tid; q < J->nrows; q += (uint32_t)J->nthreads) {
         const uint8_t *A = J->qcodes + J->qoffsets[q];
         int la = (int)(J->qoffsets[q + 1] - J->qoffsets[q]);
@@ -403,7 +408,7 @@ int nwo_query_topk(const uint8_t *qcodes, const uint32_t *qoffsets, uint32_t nq,
 
 static void histogram_rows(job_t *J, int tid) {
     int32_t *H = matrix_buffer(J->maxlen, J->maxlen);
-    if (!H) return;
+    if (!H) { worker_failed(J); return; }
     int64_t *hist = J->hist_parts + (size_t)tid * J->nbins;
     int64_t bad = 0;
     for (uint32_t i = (uint32_t)tid; i + 1 < J->n; i += (uint32_t)J->nthreads) {
@@ -452,7 +457,7 @@ int64_t nwo_histogram(const uint8_t *codes, const uint32_t *offsets, uint32_t n,
 
 static void pairs_worker(job_t *J, int tid) {
     int32_t *H = matrix_buffer(J->maxlen, J->maxlen);
-    if (!H) return;
+    if (!H) { worker_failed(J); return; }
     for (size_t p = (size_t)tid; p < J->npairs; p += (size_t)J->nthreads) {
         uint32_t i = J->pi[p], j = J->pj[p];
         J->all_out[p] = score_job(J, H, J->codes + J->offsets[i], (int)(J->offsets[i + 1] - J->offsets[i]),

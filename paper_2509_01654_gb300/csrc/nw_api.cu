@@ -705,6 +705,14 @@ nw_status nw_debug_fail_alloc(nw_ctx* c, uint32_t countdown) {
   return NW_OK;
 }
 
+nw_status nw_debug_set_bounds(nw_ctx* c, int32_t insert_iters, int64_t wait_cycles, uint32_t withhold_tile) {
+  if (!c) return NW_EINVAL;
+  c->dbg_insert_iters = insert_iters < 0 ? -1 : insert_iters;
+  c->dbg_wait_cycles = wait_cycles < 0 ? -1 : wait_cycles;
+  c->dbg_withhold_tile = withhold_tile;
+  return NW_OK;
+}
+
 }  // extern "C"
 
 // ===========================================================================
@@ -757,7 +765,13 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
     return set_err(c, NW_ERANGE, "%u words with k = %u need %zu bytes of scratch; the static region holds %zu", n, k,
                    need, cap);
   char* sb = static_cast<char*>(base);
+  // two error words: a synchronous call clears and reads word 0; an NW_ASYNC
+  // call cannot read its flag, so its kernels raise word 1 instead, which is
+  // never cleared by an NW_ASYNC call and is reported (then cleared) by the
+  // next synchronous call
+  const bool async = flags & NW_ASYNC;
   uint32_t* d_err = reinterpret_cast<uint32_t*>(sb);
+  uint32_t* d_err_async = d_err + 1;
   unsigned long long* d_stats = reinterpret_cast<unsigned long long*>(sb + 8);
   unsigned long long* d_counters = reinterpret_cast<unsigned long long*>(sb + 64);
   uint32_t* d_thr = reinterpret_cast<uint32_t*>(sb + off_thr);
@@ -774,7 +788,8 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
     ~Restore() { c->profiling = v; }
   } restore{c, saved_profiling};
 
-  NW_CK(cudaMemsetAsync(sb, 0, off_thr, s));
+  if (!async) NW_CK(cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s));
+  NW_CK(cudaMemsetAsync(sb + 8, 0, off_thr - 8, s));
   NW_CK(cudaMemsetAsync(d_thr, 0, sizeof(uint32_t) * (size_t)n, s));
   NW_CK(cudaMemsetAsync(d_slots, 0, sizeof(uint32_t) * (size_t)n * k, s));
   if (hist) NW_CK(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * need_bins, s));
@@ -796,7 +811,7 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
   P.hist_lo = d->score_lo;
   P.nbins = hist ? need_bins : 0;
   P.stats = d_stats;
-  P.err = d_err;
+  P.err = async ? d_err_async : d_err;
   SideView side{d->ws.perm.as<uint32_t>(), d_slots, d_thr};
   const uint32_t* a_enc[3] = {d->ws.a_enc.as<uint32_t>(), nullptr, nullptr};
   const uint4* b_rec[3] = {d->ws.b_rec.as<uint4>(), nullptr, nullptr};
@@ -811,8 +826,26 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
     if (nbins > need_bins) NW_CK(cudaMemsetAsync(hist + need_bins, 0, sizeof(int64_t) * (nbins - need_bins), s));
     if (hist_lo) *hist_lo = d->score_lo;
   }
-  if (flags & NW_ASYNC) return NW_OK;
-  return check_device_flags(c, d_err);
+  if (async) return NW_OK;
+  uint32_t words[2] = {0u, 0u};
+  NW_CK(cudaMemcpyAsync(words, d_err, sizeof words, cudaMemcpyDeviceToHost, s));
+  NW_CK(cudaStreamSynchronize(s));
+  if (words[0]) return check_device_flags(c, d_err);
+  if (words[1]) {
+    NW_CK(cudaMemsetAsync(d_err_async, 0, sizeof(uint32_t), s));
+    NW_CK(cudaStreamSynchronize(s));
+    const char* what = (words[1] & (kErrRetry | kErrWait)) ? "a device-side bound ran out"
+                       : (words[1] & kErrHistRange)        ? "a score fell outside the histogram range"
+                                                           : "invalid input seen on the device";
+    const nw_status st = (words[1] & (kErrRetry | kErrWait)) ? NW_ETIMEOUT
+                         : (words[1] & kErrHistRange)        ? NW_ERANGE
+                                                             : NW_EINVAL;
+    return set_err(c, st,
+                   "an earlier NW_ASYNC call of nw_all_pairs_topk_noalloc on this device failed (%s); its outputs "
+                   "are not valid; this call's outputs are",
+                   what);
+  }
+  return NW_OK;
 }
 
 }  // namespace nw

@@ -112,8 +112,8 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0u;
 }
-// waits for the phase of this parity to complete; false once kWaitCycles have passed
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// waits for the phase of this parity to complete; false once `limit` SM clock cycles have passed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t ok;
@@ -123,7 +123,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 // global -> shared, 16-byte aligned addresses, bytes a multiple of 16; counted on bar
@@ -392,6 +392,8 @@ struct DotArgs {
   uint32_t* out_idx;
   int32_t* out_val;
   uint32_t* err;
+  long long wait_cycles;  // bound of every pipeline wait (SM clock cycles)
+  uint32_t withhold;      // debug: a column tile never issued (UINT32_MAX: none)
 };
 
 template <bool kSplit, bool kSelf>
@@ -429,6 +431,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) dot_topk_kernel(const Do
   // column tile u into ring stage u % kStages: its rows (already swizzled and
   // zero-padded in global memory) and biases, counted on the stage's full barrier
   auto issue = [&](uint32_t u) {
+    if (u == P.withhold) return;  // debug: its waits run out with nothing in flight
     const uint32_t st = u % kStages;
     mbar_expect_tx(barFull + 8 * st, kTileBytes + kTileBiasBytes);
     bulk_g2s(smem_u32(sB + st * kTileBytes), Qb + (size_t)(tlo + u) * kTileBytes, kTileBytes, barFull + 8 * st);
@@ -502,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) dot_topk_kernel(const Do
         if (atomicCAS(sNext, u, u + 1) == u) issue(u);
       }
     }
-    const bool landed = mbar_wait(barFull + 8 * b, (tile / kStages) & 1);
+    const bool landed = mbar_wait(barFull + 8 * b, (tile / kStages) & 1, P.wait_cycles);
     if (__any_sync(0xffffffffu, !landed)) {
       if (lane == 0) atomicOr(err, kErrWait);
       break;
@@ -717,15 +720,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) dot_topk_kernel(const Do
   }
 
   // every issued copy has landed before the CTA's shared memory is released
-  // (all of them were consumed, unless a wait ran out)
+  // (all of them were consumed, unless a wait ran out); each wait is bounded
   __syncthreads();
   if (tid == 0) {
     const uint32_t issued = *sNext;
-    for (uint32_t u = issued > (uint32_t)kStages ? issued - kStages : 0u; u < issued; ++u)
-      if (!mbar_wait(barFull + 8 * (u % kStages), (u / kStages) & 1)) {
+    for (uint32_t u = issued > (uint32_t)kStages ? issued - kStages : 0u; u < issued; ++u) {
+      if (u == P.withhold) continue;
+      if (!mbar_wait(barFull + 8 * (u % kStages), (u / kStages) & 1, P.wait_cycles)) {
         atomicOr(err, kErrWait);
         break;
       }
+    }
   }
 }
 
@@ -851,7 +856,7 @@ uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB) {
 
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* val,
-                          uint32_t* err, cudaStream_t s) {
+                          uint32_t* err, cudaStream_t s, DotDebug dbg) {
   if (nA == 0) return cudaSuccess;
   const uint32_t S = dot_topk_splits(nA, nB);
   const auto kernel = S > 1 ? (self ? dot_topk_kernel<true, true> : dot_topk_kernel<true, false>)
@@ -875,6 +880,8 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
   P.out_idx = idx;
   P.out_val = val;
   P.err = err;
+  P.wait_cycles = dbg.wait_cycles >= 0 ? dbg.wait_cycles : kWaitCycles;
+  P.withhold = dbg.withhold;
   const uint32_t npad = (uint32_t)bias_pad(nB);
   bias_float_kernel<<<(npad + 255) / 256 + (npad == 0), 256, 0, s>>>(biasB, nB, npad, const_cast<float*>(P.biasf));
   const dim3 grid((nA + kRowsPerCta - 1) / kRowsPerCta, S);
@@ -885,8 +892,8 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
 }
 
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
-                     uint32_t* idx, int32_t* val, uint32_t* err, cudaStream_t s) {
-  return dot_topk_rect(Qb, n, Qb, bias, n, C, true, buf, idx, val, err, s);
+                     uint32_t* idx, int32_t* val, uint32_t* err, cudaStream_t s, DotDebug dbg) {
+  return dot_topk_rect(Qb, n, Qb, bias, n, C, true, buf, idx, val, err, s, dbg);
 }
 
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,

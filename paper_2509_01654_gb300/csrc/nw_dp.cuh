@@ -170,8 +170,8 @@ __device__ __forceinline__ void load_brow(const uint4* __restrict__ rec, BRow<LB
 // Returns a lower bound of the list's current smallest key and raises it in
 // *thr.
 __device__ __forceinline__ uint32_t list_offer(uint32_t* row, uint32_t* thr, uint32_t k,
-                                               uint32_t key, uint32_t* err, uint32_t& inserts) {
-  for (int it = 0; it < kInsertMaxIters; ++it) {
+                                               uint32_t key, uint32_t* err, uint32_t& inserts, int max_iters) {
+  for (int it = 0; it < max_iters; ++it) {
     uint32_t m1 = 0xffffffffu, m2 = 0xffffffffu, mi = 0;
     for (uint32_t s = 0; s < k; ++s) {
       const uint32_t v = __ldcg(row + s);
@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
   }
   uint64_t wpairs = 0;
   uint32_t inserts = 0;
+  const int max_iters = P.dbg_insert_limit ? (int)(P.dbg_insert_limit - 1u) : kInsertMaxIters;
 
   for (;;) {
     unsigned long long t = 0;
@@ -443,13 +444,13 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
               if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
                 const uint32_t key = list_key(P, T, s, LB, oa);
                 if (key > thrB_lo) {
-                  const uint32_t nm = list_offer(T.B.slots + (size_t)blo * P.k, T.B.thr + blo, P.k, key, P.err, inserts);
+                  const uint32_t nm = list_offer(T.B.slots + (size_t)blo * P.k, T.B.thr + blo, P.k, key, P.err, inserts, max_iters);
                   if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_bound(P, T, nm, LB, pconst); }
                 }
               }
               if (g_lo >= tA) {  // the A word takes the lane's word as a neighbour
                 const uint32_t key = list_key(P, T, s, LB, ob_lo);
-                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts);
+                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
               }
             }
             if (c_hi) {
@@ -457,13 +458,13 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
               if (g_hi >= tB_hi) {
                 const uint32_t key = list_key(P, T, s, LB, oa);
                 if (key > thrB_hi) {
-                  const uint32_t nm = list_offer(T.B.slots + (size_t)bhi * P.k, T.B.thr + bhi, P.k, key, P.err, inserts);
+                  const uint32_t nm = list_offer(T.B.slots + (size_t)bhi * P.k, T.B.thr + bhi, P.k, key, P.err, inserts, max_iters);
                   if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_bound(P, T, nm, LB, pconst); }
                 }
               }
               if (g_hi >= tA) {
                 const uint32_t key = list_key(P, T, s, LB, ob_hi);
-                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts);
+                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
               }
             }
           }

@@ -69,6 +69,13 @@ struct nw_ctx {
   bool own_stream = false;
   size_t budget = 0, used = 0;
   uint32_t fail_countdown = 0;
+  // debug bounds (nw_debug_set_bounds): list-insertion retries (-1 = the
+  // kernel's own bound), pipeline wait cycles (-1 = the kernel's own bound),
+  // and a column tile the candidate kernel's producer never issues (UINT32_MAX
+  // = none)
+  int32_t dbg_insert_iters = -1;
+  int64_t dbg_wait_cycles = -1;
+  uint32_t dbg_withhold_tile = UINT32_MAX;
   std::string err;
   bool profiling = false;
   nw_profile prof{};
@@ -613,6 +620,7 @@ nw_status run_plan(nw_ctx* c, cudaStream_t stream, const Plan& plan, const Seg* 
     const uint64_t lo = lp.ntasks * shard / nshards, hi = lp.ntasks * (shard + 1) / nshards;
     if (lo >= hi) continue;
     DpParams P = base;
+    P.dbg_insert_limit = c->dbg_insert_iters >= 0 ? (uint32_t)c->dbg_insert_iters + 1u : 0u;
     P.segs = d_segs + lp.seg_first;
     P.nsegs = lp.nsegs;
     if (lp.ta) P.TA = lp.ta;

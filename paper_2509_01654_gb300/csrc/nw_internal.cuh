@@ -192,6 +192,9 @@ struct DpParams {
   // substitution-matrix scoring (null = match / mismatch): kTabDim x kTabDim
   // table of s'+(a, b) = max(sim(a, b) - 2p, 0), copied to shared memory
   const uint16_t* sim_tab;
+  // debug setting: 0 = list insertions retry up to kInsertMaxIters times;
+  // otherwise they give up after dbg_insert_limit - 1 tries (NW_ETIMEOUT)
+  uint32_t dbg_insert_limit;
 };
 
 // The substitution table of a dictionary scored with a full similarity

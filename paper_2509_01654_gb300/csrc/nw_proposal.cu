@@ -39,6 +39,14 @@ struct nw_model {
 
 namespace {
 
+// the context's debug bounds for the candidate kernel (nw_debug_set_bounds)
+prop::DotDebug dot_debug(const nw_ctx* c) {
+  prop::DotDebug d;
+  d.wait_cycles = c->dbg_wait_cycles;
+  d.withhold = c->dbg_withhold_tile;
+  return d;
+}
+
 constexpr int kMaxRowsPerPass = 1 << 20;  // packed positions per forward pass of nw_model_embed
 
 float* fptr(const DevBuf& b, uint64_t off = 0) { return b.as<float>() + off; }
@@ -626,7 +634,7 @@ nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, const int32_t* bias, uint32_t 
   uint32_t* derr = prop::dot_topk_err_word(buf.as<uint64_t>(), n);
   NW_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
   NW_CK(prop::widen(srcq, n, qb.as<__nv_bfloat16>(), s));
-  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), srcb, n, C, buf.as<uint64_t>(), out_i, out_v, derr, s));
+  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), srcb, n, C, buf.as<uint64_t>(), out_i, out_v, derr, s, dot_debug(c)));
   NW_TRY(check_device_flags(c, derr));
   if (!dev) {
     NW_TRY(copy_out(c, idx, out_i, outc, false, s));
@@ -736,7 +744,7 @@ nw_status nw_dot_topk_cross(nw_ctx* c, const int8_t* qa, uint32_t na, const int8
   NW_CK(prop::widen(sa, na, qab.as<__nv_bfloat16>(), s));
   NW_CK(prop::widen(sb, nb, qbb.as<__nv_bfloat16>(), s));
   NW_CK(prop::dot_topk_rect(qab.as<__nv_bfloat16>(), na, qbb.as<__nv_bfloat16>(), sbias, nb, C, false,
-                            buf.as<uint64_t>(), out_i, out_v, derr, s));
+                            buf.as<uint64_t>(), out_i, out_v, derr, s, dot_debug(c)));
   NW_TRY(check_device_flags(c, derr));
   if (!dev) {
     NW_TRY(copy_out(c, idx, out_i, outc, false, s));
@@ -809,7 +817,7 @@ nw_status nw_proposal_query(nw_model* M, nw_dict* d, const uint8_t* qcodes, cons
   NW_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
   NW_CK(prop::dot_topk_rect(M->qQb.as<__nv_bfloat16>(), nq, M->dQb.as<__nv_bfloat16>(), M->dqbias.as<int32_t>(), n,
                             C, false, M->qbuf.as<uint64_t>(), M->qcand.as<uint32_t>(), M->qcand_dot.as<int32_t>(),
-                            derr, s));
+                            derr, s, dot_debug(c)));
   NW_CK(cudaStreamSynchronize(s));
   NW_TRY(check_device_flags(c, derr));
 
@@ -908,7 +916,7 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
                        nullptr, s));
   NW_CK(cudaEventRecord(ev[2], s));
   NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
-                       M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s));
+                       M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s, dot_debug(c)));
   NW_CK(cudaEventRecord(ev[3], s));
   NW_TRY(rescore_select(c, d, M->cand.as<uint32_t>(), C, k, M->cand_score, out_i, out_s, err_ptr(M), s));
   NW_CK(cudaEventRecord(ev[4], s));

@@ -42,15 +42,23 @@ inline size_t dot_topk_buffer_bytes(uint32_t n, uint32_t C) { return dot_topk_bu
 // the device error word inside a dot_topk buffer (zero it before a launch)
 uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB);
 inline uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t n) { return dot_topk_err_word(buf, n, n); }
+// debug settings of the candidate kernel: wait_cycles < 0 keeps the kernel's
+// own bound on a pipeline wait; withhold names a column tile the producer
+// never issues (UINT32_MAX: none), so that the waits for it run out with no
+// copy in flight
+struct DotDebug {
+  long long wait_cycles = -1;
+  uint32_t withhold = 0xffffffffu;
+};
 // each row's C best q_i . q_j + bias_j over the other rows (bias may be
 // null: 0); a pipeline wait that runs out sets kErrWait in *err
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
-                     uint32_t* idx, int32_t* dot, uint32_t* err, cudaStream_t s);
+                     uint32_t* idx, int32_t* dot, uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{});
 // each row i of QA's C best QA_i . QB_j + biasB_j over all nB columns (self:
 // the two are one set and column i is skipped)
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* dot,
-                          uint32_t* err, cudaStream_t s);
+                          uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{});
 
 // Algorithm 1's scores of every row i against its candidates cand[i * C +
 // r] (UINT32_MAX entries score INT32_MIN; out-of-range or self candidates

@@ -32,6 +32,7 @@ EXPORTED = [
     "nw_load_dictionary", "nw_dict_info_get", "nw_dict_free", "nw_all_pairs_matrix",
     "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
     "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_enumerate_query_pairs", "nw_debug_fail_alloc",
+    "nw_debug_set_bounds",
     "nw_all_pairs_topk_noalloc",
     "nw_server_create", "nw_server_submit", "nw_server_wait", "nw_server_last_error", "nw_server_destroy",
     "nw_batch_create", "nw_batch_run", "nw_batch_run_queries", "nw_batch_info_get", "nw_batch_free", "nw_all_pairs_matrix_chunked",
@@ -148,6 +149,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_debug_enumerate_pairs.argtypes = [vp, u32, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
     L.nw_debug_enumerate_query_pairs.argtypes = [vp, u32, vp, u32, u32, vp, vp, u64, ctypes.POINTER(u64)]
     L.nw_debug_fail_alloc.argtypes = [vp, u32]
+    L.nw_debug_set_bounds.argtypes = [vp, i32, ctypes.c_int64, u32]
     L.nw_debug_norm_tables.argtypes = [ctypes.POINTER(Scoring), i32, i32, vp, vp, vp, u32, ctypes.POINTER(u32)]
     L.nw_model_create.argtypes = [vp, u32, u64, ctypes.POINTER(vp)]
     L.nw_model_free.argtypes = [vp]
@@ -280,6 +282,10 @@ class Context:
 
     def debug_fail_alloc(self, countdown: int):
         _check(self.handle, load_library().nw_debug_fail_alloc(self.handle, countdown))
+
+    def debug_set_bounds(self, insert_iters: int = -1, wait_cycles: int = -1, withhold_tile: int = 0xFFFFFFFF):
+        """Device-side bounds for tests (nw_debug_set_bounds); no arguments restores the defaults."""
+        _check(self.handle, load_library().nw_debug_set_bounds(self.handle, insert_iters, wait_cycles, withhold_tile))
 
     def load_dictionary(self, codes, offsets, alphabet: int, scoring) -> "Dictionary":
         return Dictionary(self, codes, offsets, alphabet, scoring)

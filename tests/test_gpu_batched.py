@@ -148,3 +148,25 @@ def test_batch_query_set_refusals(ctx, dicts):
     st = L.nw_batch_run_queries(b.handle, None, None, P(None), P(None), 0)
     assert st == nw.NW_EINVAL
     b.free()
+
+
+def test_benchmarked_64_dictionary_batch_against_oracle_sampled_rows(ctx, oracle_mod):
+    """The benchmarked batched workload itself: 64 dictionaries of 1k..50k
+    words, lengths 1..40, alphabets 40..120 and per-dictionary scoring, in one
+    autotuned batch.  64 seeded sampled rows of every dictionary (its first and
+    last words included) equal the oracle's top-10 with that dictionary's
+    scoring, bit for bit, on two replays of the graph."""
+    dicts = synth.batched_dictionaries(64)
+    batch = nw.Batch(ctx, [(d.words.codes, d.words.offsets, d.words.alphabet, d.scoring) for d in dicts], k=K)
+    first = batch.run()
+    second = batch.run()
+    assert len(first) == 64
+    for di, (d, (idx, sc), (idx2, sc2)) in enumerate(zip(dicts, first, second)):
+        n = d.words.n
+        assert idx.shape == (n, K)
+        assert np.array_equal(idx, idx2) and np.array_equal(sc, sc2)
+        rows = np.unique(np.concatenate([synth.sample_rows(n, 64, seed=100 + di), [0, n - 1]])).astype(np.uint32)
+        oi, os_ = oracle_mod.topk_rows(d.words, rows, K, d.scoring)
+        assert np.array_equal(idx[rows], oi), (di, d.scoring)
+        assert np.array_equal(sc[rows].astype(np.int32), os_), (di, d.scoring)
+    batch.free()

@@ -102,6 +102,95 @@ def test_gradient_matches_oracle(ctx):
         o += n
 
 
+# Element-wise tolerance against the oracle's bf16 mode.  Both sides round
+# the same operands to bf16 and multiply them exactly; they differ only in
+# the float32 accumulation of each product (at most 384 terms: K = 3 taps x
+# 128 channels), whose error is at most 384 * 2^-24 ~ 2.3e-5 of the sum of
+# the terms' magnitudes.  That difference is far below one bf16 unit
+# (2^-8..2^-7 relative), but when an intermediate value (a ReLU activation, a
+# pooled feature, a back-propagated gradient) sits within it of a bf16
+# rounding boundary the two sides round it to neighbouring bf16 values, and
+# every later product sees operands one bf16 unit apart.  An output is a sum
+# of many terms, a few of them moved by one unit, so its error is bounded by a
+# few units of 2^-8 of its largest terms: RTOL = 2^-6 of the element, and an
+# absolute floor ATOL = 2^-6 x the rms of the tensor for elements that are
+# small because their terms cancel.  A wrong element (a bad conv tap, a bias
+# row, a missing position) is off by far more than either.
+RTOL = 2.0 ** -6
+
+
+def assert_elementwise(got, want, what):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    atol = RTOL * float(np.sqrt(np.mean(want * want)))
+    bad = np.abs(got - want) > atol + RTOL * np.abs(want)
+    assert not bad.any(), (what, int(bad.sum()), bad.size, float(np.abs(got - want).max()), atol)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_forward_elementwise_product_shapes(ctx, seed):
+    """Alphabet 40 and lengths 0..25, the exhaustive workload's shapes."""
+    w = synth.make_uniform_length_words(1500, 40, 1.1, 0, 25, seed=seed)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    m = nw.Model(ctx, 40, seed=seed)
+    flat = rand_params(40, seed, scale=0.15)
+    m.set_params(flat)
+    got = m.embed(d)
+    want = PR.forward(flat.astype(np.float64), w, 40, bf16=True)
+    for c in range(64):
+        assert_elementwise(got[:, c], want[:, c], f"output {c}")
+    assert_elementwise(got, want, "all outputs")
+
+
+def test_forward_across_a_chunk_boundary(ctx):
+    """Embedding passes take at most 2^20 packed positions; words on both
+    sides of the first chunk boundary (sorted by length, then index) match the
+    oracle element by element."""
+    n = 120_000
+    w = synth.make_uniform_length_words(n, 40, 1.1, 0, 25, seed=21)
+    assert int(w.lengths.sum()) > (1 << 20)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    m = nw.Model(ctx, 40, seed=2)
+    flat = rand_params(40, 5, scale=0.15)
+    m.set_params(flat)
+    got = m.embed(d)
+    order = np.lexsort((np.arange(n), w.lengths))  # sorted positions
+    rows = np.cumsum(w.lengths[order])
+    p = int(np.searchsorted(rows, 1 << 20, side="right"))  # first word of the second chunk
+    near = order[max(0, p - 150):p + 150]
+    pick = np.unique(np.concatenate([near, synth.sample_rows(n, 300, seed=6)]))
+    sub = w.subset(pick)
+    want = PR.forward(flat.astype(np.float64), sub, 40, bf16=True)
+    assert_elementwise(got[pick], want, "embeddings near the chunk boundary")
+
+
+def test_gradient_elementwise_product_shapes(ctx):
+    w = synth.make_uniform_length_words(600, 40, 1.1, 0, 25, seed=13)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    m = nw.Model(ctx, 40, seed=5)
+    flat = rand_params(40, 17, scale=0.15)
+    m.set_params(flat)
+    g = np.random.default_rng(19)
+    M = 700
+    pi = g.integers(0, w.n, M)
+    pj = g.integers(0, w.n, M)
+    pj[:7] = pi[:7]  # self pairs
+    y = g.uniform(-1, 1, M).astype(np.float32)
+    loss, grad = m.loss_grad(d, pi, pj, y)
+    want_loss, want_grad = PR.loss_and_grad(flat.astype(np.float64), w, 40, pi, pj, y, bf16=True)
+    assert abs(loss - want_loss) <= RTOL * abs(want_loss)
+    o = 0
+    for name, shape in PR.param_shapes(40):
+        size = int(np.prod(shape))
+        a, b = grad[o:o + size].reshape(shape), want_grad[o:o + size].reshape(shape)
+        assert_elementwise(a, b, name)
+        if len(shape) > 1:  # each row / output channel on its own scale
+            for r in range(shape[0]):
+                if np.any(b[r] != 0):
+                    assert_elementwise(a[r], b[r], f"{name}[{r}]")
+        o += size
+
+
 def test_invalid_pair_index_is_reported(ctx):
     w, d = small_dict(ctx, n=50)
     m = nw.Model(ctx, 9)

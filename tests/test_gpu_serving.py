@@ -60,6 +60,25 @@ def test_server_results_equal_alone_and_in_the_mix(ctx, oracle_mod):
     assert np.array_equal(si, oi) and np.array_equal(ss.astype(np.int32), os_)
 
 
+def test_batches_overlap_on_the_device_and_results_stay_exact(ctx):
+    """Requests submitted back to back, each filling a batch, are admitted
+    while earlier batches are still on the GPU (their start sees another batch
+    in flight), and each result equals the call made alone."""
+    w = synth.exhaustive_words(200_000)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)
+    pool = synth.serving_queries(12_000)
+    reqs = [pool.subset(np.arange(i * 2000, (i + 1) * 2000)) for i in range(6)]
+    with nw.Server(d, k=10, max_batch_queries=2000, max_inflight=3) as srv:
+        ids = [srv.submit(r.codes, r.offsets) for r in reqs]
+        out = [srv.wait(i) for i in ids]
+    overlapped = [info["inflight_at_start"] for _, _, info in out]
+    assert max(overlapped) >= 1, overlapped
+    assert all(info["batch_requests"] == 1 for _, _, info in out)
+    for r, (idx, sc, info) in zip(reqs, out):
+        alone_i, alone_s = d.query(r.codes, r.offsets, 10)
+        assert np.array_equal(idx, alone_i) and np.array_equal(sc, alone_s)
+
+
 def test_server_load_reports_latency(ctx):
     w = synth.exhaustive_words(20_000)
     d = ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)

@@ -466,3 +466,54 @@ def test_sim_matrix_reduces_to_scalar_scoring(oracle_mod, sc):
     assert np.array_equal(oracle_mod.histogram_sim(w, S, sc[2], lo, nb), oracle_mod.histogram(w, sc, lo, nb))
     I, J = rows[:50], rows[::-1][:50]
     assert np.array_equal(oracle_mod.score_pairs_sim(w, I, J, S, sc[2]), oracle_mod.score_pairs(w, I, J, sc))
+
+
+_ENOMEM_CHILD = r"""
+import resource, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_2509_01654_gb300 import synth
+oracle.lib()
+# one word of 20,000 symbols: each worker's full score matrix needs 1.6 GB,
+# more than the address space left to this process
+codes = np.zeros(20_000 + 6, np.uint8)
+offsets = np.array([0, 20_000, 20_002, 20_004, 20_006], np.uint32)
+w = synth.WordList(codes, offsets, 1)
+vm = 0
+for line in open("/proc/self/status"):
+    if line.startswith("VmSize:"):
+        vm = int(line.split()[1]) * 1024
+resource.setrlimit(resource.RLIMIT_AS, (vm + (384 << 20), vm + (384 << 20)))
+sc = (1, -1, -1)
+failed = []
+for name, call in [
+    ("topk_rows", lambda: oracle.topk_rows(w, [0, 1, 2, 3], 2, sc, nthreads=2)),
+    ("topk_rows_normalised", lambda: oracle.topk_rows_normalised(w, [0, 1], 2, sc, nthreads=2)),
+    ("all_pairs", lambda: oracle.all_pairs(w, sc, nthreads=2)),
+    ("histogram", lambda: oracle.histogram(w, sc, -40_000, 80_001, nthreads=2)),
+    ("score_pairs", lambda: oracle.score_pairs(w, [0, 1], [1, 2], sc, nthreads=2)),
+    ("query_topk", lambda: oracle.query_topk(w, w, 2, sc, nthreads=2)),
+]:
+    try:
+        call()
+    except RuntimeError as e:
+        if "-2" in str(e) or "error" in str(e):
+            failed.append(name)
+print(",".join(failed))
+"""
+
+
+def test_worker_allocation_failure_is_reported_not_silent(oracle_mod):
+    """A worker that cannot allocate its score matrix must make the call fail
+    (NWO_ENOMEM) rather than return with rows unwritten."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _ENOMEM_CHILD, root], capture_output=True, text=True, timeout=120,
+                       cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = set(r.stdout.strip().split(","))
+    assert got == {"topk_rows", "topk_rows_normalised", "all_pairs", "histogram", "score_pairs", "query_topk"}, (
+        r.stdout, r.stderr[-2000:])

@@ -80,3 +80,58 @@ def test_noalloc_refuses_what_it_cannot_hold(ctx):
     with pytest.raises(nw.NwError) as e:
         db.all_pairs_topk_noalloc(k, ti, ts)
     assert e.value.status == nw.NW_ERANGE and "scratch" in str(e.value)
+
+
+def test_noalloc_reaches_no_allocator(ctx):
+    """With the context's next device allocation armed to fail, the
+    no-allocation entry point still runs and matches, and the armed failure
+    is still pending afterwards (the next allocating call trips it): the
+    entry point never reached the allocator."""
+    import torch
+    w = synth.make_words(3000, 40, 1.1, 8.0, 3.0, 1, 25, seed=5)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)
+    k = 10
+    want_idx, want_score, want_hist, want_lo = d.all_pairs_topk(k)
+    nbins = d.info()["nbins"]
+    ti = torch.empty((w.n, k), dtype=torch.int32, device="cuda")
+    ts = torch.empty((w.n, k), dtype=torch.int16, device="cuda")
+    th = torch.empty((nbins,), dtype=torch.int64, device="cuda")
+    ctx.debug_fail_alloc(1)
+    try:
+        assert d.all_pairs_topk_noalloc(k, ti, ts, th) == want_lo
+        with pytest.raises(nw.NwError) as e:  # loading a dictionary allocates
+            ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)
+        assert e.value.status == nw.NW_ENOMEM and "injected" in str(e.value)
+    finally:
+        ctx.debug_fail_alloc(0)
+    assert np.array_equal(ti.cpu().numpy().view(np.uint32), want_idx)
+    assert np.array_equal(ts.cpu().numpy(), want_score)
+    assert np.array_equal(th.cpu().numpy(), want_hist)
+
+
+def test_noalloc_async_failure_is_reported_by_the_next_synchronous_call(ctx):
+    """An NW_ASYNC call returns before its kernels finish and cannot report a
+    device-side failure itself; the next synchronous call does, after
+    computing its own valid outputs, and clears it."""
+    import torch
+    w = synth.make_words(2500, 40, 1.1, 8.0, 3.0, 1, 25, seed=6)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)
+    k = 10
+    want_idx, want_score, _, _ = d.all_pairs_topk(k, hist=None)
+    ti = torch.empty((w.n, k), dtype=torch.int32, device="cuda")
+    ts = torch.empty((w.n, k), dtype=torch.int16, device="cuda")
+    ctx.debug_set_bounds(insert_iters=0)  # every list insertion gives up at once
+    try:
+        d.all_pairs_topk_noalloc(k, ti, ts, async_=True)  # returns NW_OK: nothing read back
+    finally:
+        ctx.debug_set_bounds()
+    torch.cuda.synchronize()
+    with pytest.raises(nw.NwError) as e:
+        d.all_pairs_topk_noalloc(k, ti, ts)
+    assert e.value.status == nw.NW_ETIMEOUT and "NW_ASYNC" in str(e.value)
+    # that synchronous call's own outputs are valid
+    assert np.array_equal(ti.cpu().numpy().view(np.uint32), want_idx)
+    assert np.array_equal(ts.cpu().numpy(), want_score)
+    # and the report is not repeated
+    d.all_pairs_topk_noalloc(k, ti, ts)
+    assert np.array_equal(ti.cpu().numpy().view(np.uint32), want_idx)
