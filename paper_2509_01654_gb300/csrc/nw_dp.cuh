@@ -135,12 +135,25 @@ __device__ __forceinline__ uint32_t dp_word_staged(const uint32_t* acol, int la,
     uint32_t G[LB];
     dp_row_first<LB, TAB>(G, acol[0], b, C1, C2, tab);
     int i = 1;
+    // four rows per iteration: their dependency chains interleave as a
+    // wavefront, and the loop control is paid once per four rows
 #pragma unroll 1
-    for (; i + 1 < la; i += 2) {
+    for (; i + 3 < la; i += 4) {
+      const uint32_t a0 = acol[32 * i];
+      const uint32_t a1 = acol[32 * (i + 1)];
+      const uint32_t a2 = acol[32 * (i + 2)];
+      const uint32_t a3 = acol[32 * (i + 3)];
+      dp_row<LB, TAB>(G, a0, b, C1, C2, tab);
+      dp_row<LB, TAB>(G, a1, b, C1, C2, tab);
+      dp_row<LB, TAB>(G, a2, b, C1, C2, tab);
+      dp_row<LB, TAB>(G, a3, b, C1, C2, tab);
+    }
+    if (i + 1 < la) {
       const uint32_t a0 = acol[32 * i];
       const uint32_t a1 = acol[32 * (i + 1)];
       dp_row<LB, TAB>(G, a0, b, C1, C2, tab);
       dp_row<LB, TAB>(G, a1, b, C1, C2, tab);
+      i += 2;
     }
     if (i < la) dp_row<LB, TAB>(G, acol[32 * i], b, C1, C2, tab);
     return G[LB - 1];
@@ -279,6 +292,19 @@ __device__ __forceinline__ int g_bound(const DpParams& P, const TaskTerms& T, ui
   return (int)(thr_key >> T.ib) + T.key_lo - pconst;
 }
 
+// Packed candidate prefilter.  A G-space bound t (a pair is a candidate for
+// a list when G >= t) is held as 1 - t, clamped so that t = 0 admits every G
+// (G >= 0) and t = 0x7fff none (G <= 819 * 40 < 0x7fff: the host bounds
+// s'_m * NW_MAX_WORD_LEN by 32767).  For the lane's two results packed in res,
+// viaddmax_relu(res, 1 - t, 0) is non-zero in a half exactly when G >= t there.
+__device__ __forceinline__ uint32_t neg_bound16(int t) {
+  const int c = t < 0 ? 0 : (t > 0x7fff ? 0x7fff : t);
+  return (uint32_t)(1 - c) & 0xffffu;
+}
+__device__ __forceinline__ uint32_t neg_bound2(int t_lo, int t_hi) {
+  return neg_bound16(t_lo) | (neg_bound16(t_hi) << 16);
+}
+
 // The all-pairs kernel.  TAB selects substitution-matrix scoring (the table
 // is copied to shared memory after the staging area).  EPI selects the
 // per-pair epilogue at compile time:
@@ -378,6 +404,9 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
       if (vlo) { thrB_lo = __ldcg(T.B.thr + blo); tB_lo = g_bound(P, T, thrB_lo, LB, pconst); }
       if (vhi) { thrB_hi = __ldcg(T.B.thr + bhi); tB_hi = g_bound(P, T, thrB_hi, LB, pconst); }
     }
+    // packed form of the B bounds for the prefilter, and the halves holding a word
+    uint32_t nB2 = neg_bound2(tB_lo, tB_hi);
+    const uint32_t okmask = (vlo ? 0x0000ffffu : 0u) | (vhi ? 0xffff0000u : 0u);
 
     for (uint32_t c0 = g.a0; c0 < g.a1; c0 += 32u) {
       // Stage 32 A words: lane l copies word c0 + l (la symbols) and its list
@@ -389,6 +418,7 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
       const uint32_t my_orig = (EPI == kEpiMatrix && have) ? __ldg(T.A.perm + my_a) : 0u;
       const uint32_t my_thr = (listsA && have) ? __ldcg(T.A.thr + my_a) : 0u;
       const int my_tA = listsA ? g_bound(P, T, my_thr, LB, pconst) : INT_MAX;
+      const uint32_t my_nA2 = neg_bound2(my_tA, my_tA);
       __syncwarp();
       if (have) {
         const uint32_t* src = T.a_enc + S.aenc_base + (size_t)(my_a - S.a_beg) * (uint32_t)la;
@@ -423,48 +453,63 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
         } else {
           if (hist_on) {
             if constexpr (EPI == kEpiListsLaneHist) {
-              if (ok_lo) atomicAdd(hcol + 32 * g_lo, 1u);
-              if (ok_hi) atomicAdd(hcol + 32 * g_hi, 1u);
+              // lane columns are private to their lane: plain increments
+              if (ok_lo) hcol[32 * g_lo] += 1u;
+              if (ok_hi) hcol[32 * g_hi] += 1u;
             } else {
               if (ok_lo) hist_add(P, wh, lane, g_lo + hoff);
               if (ok_hi) hist_add(P, wh, lane, g_hi + hoff);
             }
           }
-          // One compare per half against the lower of the two lists' bounds;
-          // exact keys are formed only for the rare candidates.
-          const int tA = __shfl_sync(0xffffffffu, my_tA, (int)w);
-          const bool c_lo = ok_lo && g_lo >= min(tB_lo, tA);
-          const bool c_hi = ok_hi && g_hi >= min(tB_hi, tA);
-          if (c_lo || c_hi) {
-            const uint32_t oa = __ldg(T.A.perm + a);
+          // Both halves tested at once against the lower of the two lists'
+          // bounds (packed prefilter, exact: see neg_bound16); tasks on the
+          // diagonal, which must also test a < b, skip it.  Exact keys are
+          // formed only for the rare candidates.
+          const uint32_t nA2 = __shfl_sync(0xffffffffu, my_nA2, (int)w);
+          const bool pre = check || (__viaddmax_s16x2_relu(res, __vmaxs2(nB2, nA2), 0u) & okmask) != 0u;
+          if (pre) {
             const uint32_t thrA = sT[w];
-            uint32_t* rowA = listsA ? T.A.slots + (size_t)a * P.k : nullptr;
-            if (c_lo) {
-              const int s = g_lo + pconst;
-              if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
-                const uint32_t key = list_key(P, T, s, LB, oa);
-                if (key > thrB_lo) {
-                  const uint32_t nm = list_offer(T.B.slots + (size_t)blo * P.k, T.B.thr + blo, P.k, key, P.err, inserts, max_iters);
-                  if (nm > thrB_lo) { thrB_lo = nm; tB_lo = g_bound(P, T, nm, LB, pconst); }
+            const int tA = listsA ? g_bound(P, T, thrA, LB, pconst) : INT_MAX;
+            const bool c_lo = ok_lo && g_lo >= min(tB_lo, tA);
+            const bool c_hi = ok_hi && g_hi >= min(tB_hi, tA);
+            if (c_lo || c_hi) {
+              const uint32_t oa = __ldg(T.A.perm + a);
+              uint32_t* rowA = listsA ? T.A.slots + (size_t)a * P.k : nullptr;
+              if (c_lo) {
+                const int s = g_lo + pconst;
+                if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
+                  const uint32_t key = list_key(P, T, s, LB, oa);
+                  if (key > thrB_lo) {
+                    const uint32_t nm = list_offer(T.B.slots + (size_t)blo * P.k, T.B.thr + blo, P.k, key, P.err, inserts, max_iters);
+                    if (nm > thrB_lo) {
+                      thrB_lo = nm;
+                      tB_lo = g_bound(P, T, nm, LB, pconst);
+                      nB2 = neg_bound2(tB_lo, tB_hi);
+                    }
+                  }
+                }
+                if (g_lo >= tA) {  // the A word takes the lane's word as a neighbour
+                  const uint32_t key = list_key(P, T, s, LB, ob_lo);
+                  if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
                 }
               }
-              if (g_lo >= tA) {  // the A word takes the lane's word as a neighbour
-                const uint32_t key = list_key(P, T, s, LB, ob_lo);
-                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
-              }
-            }
-            if (c_hi) {
-              const int s = g_hi + pconst;
-              if (g_hi >= tB_hi) {
-                const uint32_t key = list_key(P, T, s, LB, oa);
-                if (key > thrB_hi) {
-                  const uint32_t nm = list_offer(T.B.slots + (size_t)bhi * P.k, T.B.thr + bhi, P.k, key, P.err, inserts, max_iters);
-                  if (nm > thrB_hi) { thrB_hi = nm; tB_hi = g_bound(P, T, nm, LB, pconst); }
+              if (c_hi) {
+                const int s = g_hi + pconst;
+                if (g_hi >= tB_hi) {
+                  const uint32_t key = list_key(P, T, s, LB, oa);
+                  if (key > thrB_hi) {
+                    const uint32_t nm = list_offer(T.B.slots + (size_t)bhi * P.k, T.B.thr + bhi, P.k, key, P.err, inserts, max_iters);
+                    if (nm > thrB_hi) {
+                      thrB_hi = nm;
+                      tB_hi = g_bound(P, T, nm, LB, pconst);
+                      nB2 = neg_bound2(tB_lo, tB_hi);
+                    }
+                  }
                 }
-              }
-              if (g_hi >= tA) {
-                const uint32_t key = list_key(P, T, s, LB, ob_hi);
-                if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
+                if (g_hi >= tA) {
+                  const uint32_t key = list_key(P, T, s, LB, ob_hi);
+                  if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
+                }
               }
             }
           }
