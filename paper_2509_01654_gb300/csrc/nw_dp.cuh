@@ -206,6 +206,14 @@ __device__ __forceinline__ uint32_t list_offer(uint32_t* row, uint32_t* thr, uin
   return 0xffffffffu;
 }
 
+// global -> shared 4-byte asynchronous copy (cp.async.ca; 4-byte aligned)
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t upper_offset(uint64_t i, uint64_t j, uint64_t n) {
   // pair (i, j), i < j, in the row-major upper triangle: S(i-1) + (j - i - 1)
   return i * (2 * n - i - 1) / 2 + (j - i - 1);
@@ -421,10 +429,12 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
       const uint32_t my_nA2 = neg_bound2(my_tA, my_tA);
       __syncwarp();
       if (have) {
+        // asynchronous 4-byte copies: the word's symbol loads are in flight together
         const uint32_t* src = T.a_enc + S.aenc_base + (size_t)(my_a - S.a_beg) * (uint32_t)la;
-        for (int i = 0; i < la; ++i) sA[32 * i + lane] = __ldg(src + i);
+        for (int i = 0; i < la; ++i) cp_async4(sA + 32 * i + lane, src + i);
         sT[lane] = my_thr;
       }
+      cp_async_wait_all();
       __syncwarp();
 
       for (uint32_t w = 0; w < nA; ++w) {
