@@ -1,30 +1,42 @@
-// nw_dot_topk.cu -- candidate proposal by quantised embedding products.
+// nw_dot_topk.cu -- candidate proposal by quantised embedding products, on the
+// fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
 //
-// Features are quantised to integers in [-127, 127] and stored as bf16, which
-// holds them exactly; a product of two is at most 16,129, a sum of 64 at most
-// 1,032,256, and a per-column bias is an integer of magnitude <= 2^23, so
-// every partial sum stays below 2^24 and the tensor cores' float32
-// accumulation gives the exact integer q_i . q_j + bias_j in any order.  The
-// top-C selection is then an exact, deterministic function of the integers
-// (ties: lower index).
+// Exactness.  Features are quantised to integers in [-127, 127] (exact in
+// bf16) and a column's bias b (|b| <= 2^23) is split into three bf16-exact
+// digits, b = b2 * 2^16 + b1 * 2^8 + b0 with b0, b1 in [0, 256) and b2 in
+// [-128, 128]; a row carries the matching weights (2^16, 2^8, 1).  The products
+// of one output are then integers, and so is every partial sum (|.| < 2^24), so
+// the tensor cores' float32 accumulation gives q_i . q_j + b_j exactly, in any
+// order, and the top-C selection is an exact, deterministic function of the
+// integers (ties: lower column index first).
 //
-// dot_topk_kernel: a CTA owns 256 rows (8 warps x 32 rows, A fragments held
-// in registers for the whole sweep) and sweeps every column in tiles of 64:
-// a three-stage cp.async ring into swizzled shared memory (one barrier per
-// tile), ldmatrix, bf16 m16n8k16 mma.sync whose first k-step starts from the
-// columns' biases.  Each row keeps an append buffer of kCap keys in global
-// memory and a threshold; a value enters when it beats the threshold (a row
-// group's maximum is tested first, so most tiles cost one compare per value
-// and no branch).  A row's values in a tile belong to the four lanes of one
-// quad, so its key count lives in their registers and appends take slots by
-// a prefix sum over the quad, with no atomics.  When a row holds more than
-// 2C keys (or its buffer could overflow during the next tile), its warp
-// raises the row's threshold to the lower edge t of the value-histogram bin
-// that holds the C-th best key and drops the keys below t (an exact 8-pass
-// radix select when that bin is crowded).  Later columns have higher
-// indices, so a later value equal to the C-th best never displaces a kept
-// key: the comparison is strict, and the final pass, an exact select and
-// sort of each row's buffer, gives exact lists.
+// dot_topk_kernel: a CTA owns 128 rows (the 128 lanes of tensor memory) and
+// sweeps column tiles of 256.  Ten warps with fixed roles:
+//   * a producer thread streams each tile (256 rows of 128 B, already in the
+//     128-byte-swizzled K-major layout, plus 8 KiB of bias digits) into a
+//     four-stage shared-memory ring with cp.async.bulk, counted on mbarriers;
+//   * an MMA thread issues, per tile, four tcgen05.mma (M = 128, N = 256,
+//     K = 16, bf16 -> f32) over the 64 features and a fifth over the bias
+//     digits into one of two 256-column accumulators, then commits the stage
+//     back to the producer and the accumulator to the epilogue;
+//   * four epilogue warps, one thread per row, read the accumulator with
+//     tcgen05.ld (32 columns at a time, the next load in flight while the
+//     current values are tested), release it, and append every value that
+//     reaches the row's threshold to one of the row's two global buffers;
+//   * four compactor warps, one per epilogue warp: when a row's active
+//     buffer passes its trigger, the epilogue thread hands the buffer over and
+//     keeps appending to the other one; the compactor raises the row's
+//     threshold to a value at or below the C-th best key in the handed buffer
+//     and drops the keys below it, off the path of the tensor pipe.
+// A key is appended when its value is >= the threshold, so the column order
+// does not matter: a CTA starts at its own diagonal tile (similar words sit
+// near each other in the length-sorted order, so thresholds rise early), and
+// every key of the final top C is always kept (each threshold is at most the
+// C-th best value among keys already seen).  A final pass selects each row's
+// C best keys from its two buffers exactly and sorts them.  Every wait is
+// bounded and sets kErrWait when it runs out; the CTA then stops, waits
+// (bounded) for the copies and products it issued, frees its tensor memory
+// and returns.
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cuda_runtime.h>
@@ -39,58 +51,66 @@ namespace nw {
 namespace prop {
 namespace {
 
-constexpr int kDim = 64;                 // values per row (bf16)
-constexpr int kRowBytes = kDim * 2;      // 128
-// 32 rows (two 16-row slabs) per warp: 16 rows with three CTAs per SM measured 5% slower
-constexpr int kRowsPerWarp = 32;
-constexpr int kSlabs = kRowsPerWarp / 16;
-constexpr int kCtasPerSm = kSlabs == 2 ? 2 : 3;
-constexpr int kWarps = 8;
-constexpr int kRowsPerCta = kRowsPerWarp * kWarps;  // 256
-constexpr int kTileCols = 64;
+constexpr int kDim = 64;                  // values per row (bf16)
+constexpr int kRowBytes = kDim * 2;       // 128
+constexpr int kRows = 128;                // rows per CTA = tensor-memory lanes
+constexpr int kTileN = 256;               // columns per tile (MMA N)
+constexpr int kExtK = 16;                 // bias-digit K (one MMA K-step)
+constexpr int kStages = 3;
+constexpr int kMainBytes = kTileN * kRowBytes;          // 32 KiB
+constexpr int kExtBytes = kTileN * kExtK * 2;           // 8 KiB
+constexpr int kStageBytes = kMainBytes + kExtBytes;     // 40 KiB
+constexpr int kAMainBytes = kRows * kRowBytes;          // 16 KiB
+constexpr int kAExtBytes = kRows * kExtK * 2;           // 4 KiB
+constexpr int kEpiWarps = 4;                            // warps 0..3
+constexpr int kProducerWarp = 4;
+constexpr int kMmaWarp = 5;
+constexpr int kCompWarps = 4;                           // warps 6..9
+constexpr int kWarps = kEpiWarps + 2 + kCompWarps;
 constexpr int kThreads = kWarps * 32;
-constexpr int kSel = NW_MAX_CANDIDATES;  // per-warp gather/sort area (keys)
+constexpr int kSel = NW_MAX_CANDIDATES;                 // per-warp gather/sort area (keys)
+constexpr uint32_t kTmemCols = 2 * kTileN;              // two accumulators
 
-// dynamic shared memory layout (bytes)
-constexpr int kStages = kSlabs == 2 ? 6 : 4;             // column tiles in flight
-constexpr int kTileBytes = kTileCols * kRowBytes;        // 8 KiB per tile
-constexpr int kTileBiasBytes = kTileCols * 4;            // its biases (float)
-constexpr int kSmemB = kStages * kTileBytes;
-constexpr int kSmemBias = kStages * kTileBiasBytes;
-constexpr int kSmemSort = kWarps * kSel * 8;             // 32 KiB (A staging at start)
-constexpr int kSmemHist = kWarps * 256 * 4;              // radix histograms
-constexpr int kSmemCnt = kRowsPerCta * 4;
-constexpr int kSmemThr = kRowsPerCta * 4;
-constexpr int kSmemBars = 2 * kStages * 8 + 16;          // full / empty mbarriers, next tile to issue
-constexpr int kOffBias = kSmemB;
-constexpr int kOffSort = kOffBias + kSmemBias;
-constexpr int kOffHist = kOffSort + kSmemSort;
-constexpr int kOffCnt = kOffHist + kSmemHist;
-constexpr int kOffThr = kOffCnt + kSmemCnt;
-constexpr int kOffBars = kOffThr + kSmemThr;
-constexpr int kSmemTotal = kOffBars + kSmemBars;
-static_assert(kSmemTotal * kCtasPerSm <= 224 * 1024, "kCtasPerSm CTAs per SM");
+// dynamic shared memory (bytes from a 1024-aligned base)
+constexpr int kOffAMain = 0;
+constexpr int kOffAExt = kOffAMain + kAMainBytes;
+constexpr int kOffStages = kOffAExt + kAExtBytes;
+// compactor warps: a 256-bin histogram each and one staging area for the
+// handed-over keys and the kept keys of the row's other buffer, split into
+// kCompWarps areas of 1,536 keys (hand-overs of up to 1,024 keys, C <= 256) or
+// two of 3,072 (hand-overs of up to 2,048 keys, larger C: two compactors, each
+// serving two epilogue warps)
+constexpr int kStageKeysTotal = 6144;
+constexpr int kOffCompHist = kOffStages + kStages * kStageBytes;
+constexpr int kOffCompKeys = kOffCompHist + kCompWarps * 1024;
+// epilogue: each thread's 32 values of a chunk with hits, staged so that the
+// hits can be read by index (row stride 36 floats: conflict-free 16-byte stores)
+constexpr int kValStride = 36;
+constexpr int kOffVals = kOffCompKeys + kStageKeysTotal * 8;
+constexpr int kOffRow = kOffVals + kRows * kValStride * 4;
+constexpr int kFinalBytes = 256 * 4 + kSel * 8;        // final pass: histogram + sort area per warp
+// row state: threshold, kept counts of the two buffers, hand-over request, final state
+constexpr int kOffThr = kOffRow;
+constexpr int kOffKept = kOffThr + kRows * 4;
+constexpr int kOffReq = kOffKept + kRows * 8;
+constexpr int kOffFin = kOffReq + kRows * 4;
+constexpr int kOffMisc = kOffFin + kRows * 4;          // request masks, done flags, tmem address
+constexpr int kOffBars = kOffMisc + 64;
+constexpr int kNumBars = 2 * kStages + 4 + 1;          // full, empty, acc full x2, acc empty x2, A loaded
+constexpr int kSmemUsed = kOffBars + kNumBars * 8;
+constexpr int kSmemTotal = kSmemUsed + 1024;           // slack for aligning the base
+static_assert(kSmemTotal <= 227 * 1024, "one CTA per SM");
+// the final pass reuses the stage ring: per warp a histogram and a sort area
+static_assert(kWarps * kFinalBytes <= kStages * kStageBytes, "final-pass scratch fits the ring");
+static_assert(kCap >= 2 * NW_MAX_CANDIDATES + kTileN, "a buffer holds a compaction's keys and a tile");
 // a pipeline wait gives up after this many SM clock cycles (about a second)
 constexpr long long kWaitCycles = 2000000000ll;
-static_assert(kRowsPerCta * kRowBytes <= kSmemSort, "A staging fits the sort area");
-static_assert(kCap - kTileCols > NW_MAX_CANDIDATES, "a compaction leaves room for a tile");
-static_assert(kTileCols == 64, "a row's own column is found by i >> 6");
-static_assert(kSel * 8 >= 32 * 32 * 4, "a warp's sort area stages 32 values per lane");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// 16-byte chunk c of row r in a swizzled [rows][8 chunks] tile
-__device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * kRowBytes + ((c ^ (r & 7)) << 4)); }
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n));
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---- mbarriers and bulk copies
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -101,16 +121,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-// whether the barrier's phase of this parity has completed (never blocks)
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0u;
 }
 // waits for the phase of this parity to complete; false once `limit` SM clock cycles have passed
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
@@ -133,28 +143,64 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
+// ---- tensor memory and tcgen05
+// shared-memory matrix descriptor: start, leading and stride byte offsets,
+// descriptor version 1, layout (0: no swizzle, 2: 128-byte swizzle)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46) | ((uint64_t)layout << 61);
+}
+// instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+// arrives on bar once every tcgen05 operation this thread issued has completed
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+// 32 consecutive accumulator columns of this thread's lane (no wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+// waits for this thread's outstanding tcgen05.ld; the registers are tied to
+// the wait so that no use of them is scheduled before it
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                 "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]),
+                 "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]),
+                 "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+               :
+               : "memory");
 }
 
-// d = a . b + (c0, c1, c0, c1): the first k-step, accumulating onto the columns' biases
-__device__ __forceinline__ void mma_bf16_init(float* d, const uint32_t* a, uint32_t b0, uint32_t b1, float c0,
-                                              float c1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%10, %11, %10, %11};\n"
-      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1));
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;\n" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
 }
 
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// Byte offset of element (row r, k) of a K = 16 bf16 tile in the canonical
+// K-major layout without swizzle: 8-row x 16-byte core matrices, the two K
+// halves 128 bytes apart, 8-row groups 256 bytes apart.
+__host__ __device__ __forceinline__ uint32_t ext_offset(uint32_t r, uint32_t k) {
+  return (r >> 3) * 256u + (k >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
 }
 
 // key: higher value first, then lower index; 0 sorts below every real key
@@ -323,414 +369,457 @@ __device__ void warp_value_hist(const uint64_t* buf, int cnt, int lo, int sh, un
   __syncwarp();
 }
 
-// Keeps the keys of buf[0, cnt) whose value is >= t at the front of buf, in
-// their order; returns how many.  A batch's writes land below the end of the
-// batch, which its lanes have already read.
-__device__ int warp_keep_value_ge(uint64_t* buf, int cnt, int t, int lane) {
-  int base = 0;
-  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
-    uint64_t k[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int i = i0 + 32 * u + lane;
-      k[u] = i < cnt ? buf[i] : 0ull;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const bool keep = i0 + 32 * u + lane < cnt && key_val(k[u]) >= t;
-      const unsigned ball = __ballot_sync(0xffffffffu, keep);
-      if (keep) buf[base + __popc(ball & ((1u << lane) - 1u))] = k[u];
-      base += __popc(ball);
-    }
-    __syncwarp();
-  }
-  return base;
-}
-
-// Bits k (value k = 2 nb + e of a lane's row group: column 8 nb + 2 t4 + e of
-// the tile) whose column j is a real column (j < nB) other than the row i
-// itself when rows and columns are one set (self); a row past nA has none.
-__device__ __forceinline__ uint32_t valid_cols(uint32_t i, uint32_t tile, uint32_t nA, uint32_t nB, bool self,
-                                               int t4) {
-  if (i >= nA) return 0u;
-  const uint32_t j0 = tile * kTileCols;
-  uint32_t v = 0xffffu;
-  if (j0 + kTileCols > nB || (self && (i >> 6) == tile)) {
-    v = 0u;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const uint32_t j = j0 + (uint32_t)((k >> 1) * 8 + 2 * t4 + (k & 1));
-      if (j < nB && !(self && j == i)) v |= 1u << k;
-    }
-  }
-  return v;
-}
-
 __device__ __forceinline__ int pow2_at_least(int x) {
   int p = 32;
   while (p < x) p <<= 1;
   return p;
 }
 
-// One launch: rows QA[0, nA) against columns QB[0, nB) (both in the padded,
-// swizzled bf16 layout); biasf holds the columns' biases as floats (exact:
-// |bias| <= 2^23), zero-padded to a multiple of kTileCols entries.  self:
-// rows and columns are one set, and row i skips column i.
-// With splits > 1, CTA (x, y) sweeps only the column tiles [y * tps, (y +
-// 1) * tps) and writes its rows' C best keys, sorted, to part (a merge
-// kernel then takes each row's C best of its splits' lists).
+
+// One launch: rows QA[0, nA) against columns QB[0, nB) (both bf16, zero-padded
+// to whole 256-row tiles, 16-byte chunks of row r permuted by r & 7: the
+// 128-byte-swizzled K-major layout); ext holds the columns' bias digits in the
+// K = 16 layout of ext_offset.  self: rows and columns are one set, and row i
+// skips column i.  With splits > 1, CTA (x, y) sweeps only the column tiles
+// [y * tps, (y + 1) * tps) and writes its rows' C best keys, sorted, to part
+// (a merge kernel then takes each row's C best of its splits' lists).
 struct DotArgs {
   const __nv_bfloat16* QA;
   const __nv_bfloat16* QB;
-  const float* biasf;
+  const unsigned char* ext;
   uint32_t nA, nB, C;
-  bool self;
   uint32_t splits, tps;
-  uint64_t* buf;   // (nA x splits) x kCap keys
+  uint64_t* buf;   // (nA x splits) x 2 buffers x kCap keys
   uint64_t* part;  // (nA x splits) x C keys when splits > 1
   uint32_t* out_idx;
   int32_t* out_val;
   uint32_t* err;
-  long long wait_cycles;  // bound of every pipeline wait (SM clock cycles)
+  const uint32_t* order;  // column tiles in sweep order (each split sweeps a contiguous part)
+  long long wait_cycles;  // bound of every wait (SM clock cycles)
   uint32_t withhold;      // debug: a column tile never issued (UINT32_MAX: none)
 };
 
-template <bool kSplit, bool kSelf>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) dot_topk_kernel(const DotArgs P) {
-  const float* __restrict__ biasf = P.biasf;
-  const uint32_t C = P.C;
-  uint64_t* __restrict__ buf = P.buf;
-  uint32_t* __restrict__ out_idx = P.out_idx;
-  int32_t* __restrict__ out_val = P.out_val;
-  uint32_t* __restrict__ err = P.err;
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* sB = smem;
-  float* sBias = reinterpret_cast<float*>(smem + kOffBias);
-  uint64_t* sSort = reinterpret_cast<uint64_t*>(smem + kOffSort);
-  unsigned* sHist = reinterpret_cast<unsigned*>(smem + kOffHist);
-  int* sCnt = reinterpret_cast<int*>(smem + kOffCnt);
-  float* sThr = reinterpret_cast<float*>(smem + kOffThr);
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) { return *reinterpret_cast<const volatile uint32_t*>(p); }
 
-  const uint32_t barFull = smem_u32(smem + kOffBars), barEmpty = barFull + 8 * kStages;
-  uint32_t* sNext = reinterpret_cast<uint32_t*>(smem + kOffBars + 16 * kStages);
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t row0 = blockIdx.x * (uint32_t)kRowsPerCta;
-  const unsigned char* Qa = reinterpret_cast<const unsigned char*>(P.QA);
-  const unsigned char* Qb = reinterpret_cast<const unsigned char*>(P.QB);
-  // this CTA's column tiles: global tiles tlo + [0, ntiles)
-  const uint32_t ys = kSplit ? blockIdx.y : 0u;
-  const uint32_t tall = (P.nB + kTileCols - 1) / kTileCols;
-  const uint32_t tlo = kSplit ? min(tall, ys * P.tps) : 0u;
-  const uint32_t ntiles = kSplit ? min(tall - tlo, P.tps) : tall;
-  // row i's append buffer
-  auto row_buf = [&](uint32_t i) { return buf + (kSplit ? (size_t)i * P.splits + ys : (size_t)i) * kCap; };
-  const uint32_t npadA = (P.nA + kTileCols - 1) / kTileCols * kTileCols;
-
-  // column tile u into ring stage u % kStages: its rows (already swizzled and
-  // zero-padded in global memory) and biases, counted on the stage's full barrier
-  auto issue = [&](uint32_t u) {
-    if (u == P.withhold) return;  // debug: its waits run out with nothing in flight
-    const uint32_t st = u % kStages;
-    mbar_expect_tx(barFull + 8 * st, kTileBytes + kTileBiasBytes);
-    bulk_g2s(smem_u32(sB + st * kTileBytes), Qb + (size_t)(tlo + u) * kTileBytes, kTileBytes, barFull + 8 * st);
-    bulk_g2s(smem_u32(sBias + st * kTileCols), biasf + (size_t)(tlo + u) * kTileCols, kTileBiasBytes,
-             barFull + 8 * st);
-  };
-
-  // stage the CTA's 256 rows (zero past the padded rows) into the sort area
-  unsigned char* sA = reinterpret_cast<unsigned char*>(sSort);
-  for (int x = tid; x < kRowsPerCta * 8; x += kThreads) {
-    const uint32_t g = row0 + (uint32_t)(x >> 3);
-    cp_async16(smem_u32(sA + x * 16), Qa + (size_t)(g < npadA ? g : 0) * kRowBytes + (x & 7) * 16, g < npadA);
+// Copies the keys of src[0, cnt) whose value is >= t to dst (in their order);
+// returns how many.
+__device__ int warp_keep_value_ge_to(const uint64_t* src, int cnt, int t, uint64_t* dst, int lane) {
+  int base = 0;
+  for (int i0 = 0; i0 < cnt; i0 += 32) {
+    const int i = i0 + lane;
+    const uint64_t k = i < cnt ? src[i] : 0ull;
+    const bool keep = i < cnt && key_val(k) >= t;
+    const unsigned ball = __ballot_sync(0xffffffffu, keep);
+    if (keep) dst[base + __popc(ball & ((1u << lane) - 1u))] = k;
+    base += __popc(ball);
   }
-  cp_async_commit();
-  for (int r = tid; r < kRowsPerCta; r += kThreads) {
-    sCnt[r] = 0;
-    sThr[r] = -FLT_MAX;
-  }
-  if (tid == 0) {
-    for (int st = 0; st < kStages; ++st) {
-      mbar_init(barFull + 8 * st, 1);
-      mbar_init(barEmpty + 8 * st, kWarps);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    const uint32_t first = min(ntiles, (uint32_t)kStages);
-    for (uint32_t u = 0; u < first; ++u) issue(u);
-    *sNext = first;
-  }
-  cp_async_wait<0>();
-  __syncthreads();
+  return base;
+}
 
-  // A fragments: slab s (16 rows), k-step ks
-  uint32_t afr[kSlabs][4][4];
-#pragma unroll
-  for (int s = 0; s < kSlabs; ++s)
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const int r = warp * kRowsPerWarp + s * 16 + (lane & 15);
-      const int c = 2 * ks + (lane >> 4);
-      ldmatrix_x4(smem_u32(sA + swz(r, c)), afr[s][ks][0], afr[s][ks][1], afr[s][ks][2], afr[s][ks][3]);
-    }
-  __syncthreads();  // the sort area is free from here on
-
-  const int g = lane >> 2, t4 = lane & 3;
-  float thr[kSlabs][2];
-  int cnt[kSlabs][2];  // keys in the row's buffer (same in the row's four lanes)
-#pragma unroll
-  for (int s = 0; s < kSlabs; ++s)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      thr[s][h] = -FLT_MAX;
-      cnt[s][h] = 0;
-    }
-
-  uint64_t* sMine = sSort + warp * kSel;
-  unsigned* hMine = sHist + warp * 256;
-  const int trigger = min(kCap - kTileCols, 2 * (int)C);
-  const unsigned keep_limit = (C + (unsigned)trigger) / 2;  // a compaction frees at least this much
-  // Warps sweep the ring at their own pace.  A stage is released by each
-  // warp once its products are taken, and refilled by whichever warp finds it
-  // free first (the next tile to issue is claimed with a compare-and-swap), so
-  // a warp may run up to kStages tiles ahead of the CTA's slowest.
-  for (uint32_t tile = 0; tile < ntiles; ++tile) {
-    const int b = (int)(tile % kStages);
-    if (lane == 0) {
-      for (;;) {
-        const uint32_t u = *reinterpret_cast<volatile uint32_t*>(sNext);
-        if (u >= ntiles || u >= tile + kStages) break;
-        // stage u % kStages last held tile u - kStages: free once every warp released it
-        if (!mbar_test(barEmpty + 8 * (u % kStages), ((u / kStages) + 1) & 1)) break;
-        if (atomicCAS(sNext, u, u + 1) == u) issue(u);
-      }
-    }
-    const bool landed = mbar_wait(barFull + 8 * b, (tile / kStages) & 1, P.wait_cycles);
-    if (__any_sync(0xffffffffu, !landed)) {
-      if (lane == 0) atomicOr(err, kErrWait);
-      break;
-    }
-
-    const unsigned char* tB = sB + b * (kTileCols * kRowBytes);
-    const float* tBias = sBias + b * kTileCols;
-    float acc[kSlabs][8][4];
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-#pragma unroll
-      for (int nb = 0; nb < 8; nb += 2) {
-        const int r = 8 * (nb + (lane >> 4)) + (lane & 7);
-        const int c = 2 * ks + ((lane >> 3) & 1);
-        uint32_t b0, b1, b2, b3;
-        ldmatrix_x4(smem_u32(tB + swz(r, c)), b0, b1, b2, b3);
-        if (ks == 0) {
-          const float2 c0 = *reinterpret_cast<const float2*>(tBias + nb * 8 + 2 * t4);
-          const float2 c1 = *reinterpret_cast<const float2*>(tBias + (nb + 1) * 8 + 2 * t4);
-#pragma unroll
-          for (int s = 0; s < kSlabs; ++s) {
-            mma_bf16_init(acc[s][nb], afr[s][0], b0, b1, c0.x, c0.y);
-            mma_bf16_init(acc[s][nb + 1], afr[s][0], b2, b3, c1.x, c1.y);
-          }
-        } else {
-#pragma unroll
-          for (int s = 0; s < kSlabs; ++s) {
-            mma_bf16(acc[s][nb], afr[s][ks], b0, b1);
-            mma_bf16(acc[s][nb + 1], afr[s][ks], b2, b3);
-          }
-        }
-      }
-    }
-
-    __syncwarp();
-    if (lane == 0) mbar_arrive(barEmpty + 8 * b);
-
-    // epilogue: the maximum of each (slab, half) row group against its row's
-    // threshold; only groups that beat it look at their values one by one
-    bool gh[kSlabs][2];
-#pragma unroll
-    for (int s = 0; s < kSlabs; ++s)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float m[8];  // a tree of maxima: depth 4 instead of a chain of 15
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) m[nb] = fmaxf(acc[s][nb][2 * h], acc[s][nb][2 * h + 1]);
-#pragma unroll
-        for (int w = 4; w > 0; w >>= 1)
-#pragma unroll
-          for (int x = 0; x < w; ++x) m[x] = fmaxf(m[x], m[x + w]);
-        gh[s][h] = m[0] > thr[s][h];
-      }
-    bool any_hit = false;
-#pragma unroll
-    for (int s = 0; s < kSlabs; ++s) any_hit |= gh[s][0] | gh[s][1];
-    if (__any_sync(0xffffffffu, any_hit)) {
-      // A row's 16 x 4 values of this tile sit in the four lanes of one quad,
-      // and no other warp appends to it: the quad's lanes take consecutive
-      // slots by a prefix sum of their hit counts, with no atomics.  Hits are
-      // found as a bit mask, then read back from this lane's staging slots.
-      float* stage = reinterpret_cast<float*>(sMine) + lane * 32;
-#pragma unroll
-      for (int s = 0; s < kSlabs; ++s) {
-        uint32_t m[2] = {0u, 0u};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (gh[s][h]) {
-            uint32_t part[4] = {0u, 0u, 0u, 0u};  // independent partial masks
-#pragma unroll
-            for (int nb = 0; nb < 8; ++nb)
-#pragma unroll
-              for (int e = 0; e < 2; ++e)
-                if (acc[s][nb][2 * h + e] > thr[s][h]) part[nb & 3] |= 1u << (2 * nb + e);
-            m[h] = (part[0] | part[1]) | (part[2] | part[3]);
-            const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
-            if (m[h] != 0u) m[h] &= valid_cols(i, tlo + tile, P.nA, P.nB, kSelf, t4);
-          }
-        }
-        uint32_t pos[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int hc = __popc(m[h]);
-          int incl = hc;
-#pragma unroll
-          for (int o = 1; o < 4; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o, 4);
-            if (t4 >= o) incl += t;
-          }
-          pos[h] = (uint32_t)(cnt[s][h] + incl - hc);
-          cnt[s][h] += __shfl_sync(0xffffffffu, incl, 3, 4);
-        }
-        if ((m[0] | m[1]) != 0u) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int nb = 0; nb < 8; ++nb)
-              *reinterpret_cast<float2*>(stage + h * 16 + 2 * nb) =
-                  make_float2(acc[s][nb][2 * h], acc[s][nb][2 * h + 1]);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t i = row0 + (uint32_t)(warp * kRowsPerWarp + s * 16 + h * 8 + g);
-            uint64_t* rb = row_buf(i);
-            uint32_t mm = m[h], slot = pos[h];
-            while (mm != 0u) {
-              const int k = __ffs(mm) - 1;
-              mm &= mm - 1u;
-              const uint32_t j = (tlo + tile) * kTileCols + (uint32_t)((k >> 1) * 8 + 2 * t4 + (k & 1));
-              rb[slot++] = make_key((int)stage[h * 16 + k], j);
-            }
-          }
-        }
-      }
-    }
-    __syncwarp();
-
-    // rows of this warp holding more than `trigger` keys: compacting at 2C
-    // (or when the buffer could overflow during the next tile) keeps the
-    // thresholds close to the running C-th best value
-    bool over = false;
-#pragma unroll
-    for (int s = 0; s < kSlabs; ++s) over |= (cnt[s][0] > trigger) | (cnt[s][1] > trigger);
-    if (__any_sync(0xffffffffu, over)) {
-      if (t4 == 0) {
-#pragma unroll
-        for (int s = 0; s < kSlabs; ++s)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g] = cnt[s][h];
-      }
-      __syncwarp();
-      unsigned full = __ballot_sync(0xffffffffu, lane < kRowsPerWarp && sCnt[warp * kRowsPerWarp + lane] > trigger);
-      while (full) {
-        const int l = __ffs(full) - 1;
-        full &= full - 1;
-        const int lr = warp * kRowsPerWarp + l;
-        uint64_t* rb = row_buf(row0 + (uint32_t)lr);
-        const int c = sCnt[lr];
-        // A threshold t at or below the C-th best value is enough here (the
-        // final pass selects exactly): t is the lower edge of the 256-bin
-        // value-histogram bin holding the C-th best key, and the keys with
-        // value >= t stay.  A later value that can still enter the row's top
-        // C beats the C-th best key now, hence t.  A crowded bin falls back
-        // to the exact C-th key.
-        int lo, hi;
-        warp_value_range(rb, c, lane, lo, hi);
-        const unsigned span = (unsigned)(hi - lo);
-        const int sh = span < 256u ? 0 : 24 - __clz((int)span);
-        warp_value_hist(rb, c, lo, sh, hMine, lane);
-        int bin;
-        unsigned above;
-        hist_find_desc(hMine, C, lane, bin, above);
-        const unsigned keep = above + hMine[bin];
-        __syncwarp();
-        int kept, t;
-        if (keep <= keep_limit) {
-          t = lo + (bin << sh);
-          kept = warp_keep_value_ge(rb, c, t, lane);  // == keep
-        } else {
-          const uint64_t kth = warp_select_kth(rb, c, (int)C, hMine, lane);
-          kept = warp_gather_ge(rb, c, kth, sMine, lane);  // == C
-          for (int x = lane; x < kept; x += 32) rb[x] = sMine[x];
-          t = key_val(kth);
-        }
-        if (lane == 0) {
-          sCnt[lr] = kept;
-          sThr[lr] = (float)t;
-        }
-        __syncwarp();
-      }
-#pragma unroll
-      for (int s = 0; s < kSlabs; ++s)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          thr[s][h] = sThr[warp * kRowsPerWarp + s * 16 + h * 8 + g];
-          cnt[s][h] = sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g];
-        }
-      __syncwarp();
-    }
-  }
-  if (t4 == 0) {
-#pragma unroll
-    for (int s = 0; s < kSlabs; ++s)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) sCnt[warp * kRowsPerWarp + s * 16 + h * 8 + g] = cnt[s][h];
+// A warp compacts one handed-over buffer keys[0, c) (C < c <= the hand-over
+// cap).  The keys, and the kept keys other[0, co) of the row's other buffer
+// (a prefix the epilogue no longer writes), are staged into shared memory
+// with one round of asynchronous copies; every pass runs there.  The
+// threshold t is at or below the C-th best value of the two together (the
+// lower edge of the 256-bin value-histogram bin holding it, or the exact C-th
+// key when that bin is crowded), so it is at or below the row's C-th best
+// value so far; the handed-over keys that reach it are written back to the
+// front of their buffer.  Returns the number kept there.
+__device__ int compact_buffer(uint64_t* keys, int c, const uint64_t* other, int co, uint32_t C, unsigned keep_limit,
+                              unsigned* hist, uint64_t* stage, int lane, int& t) {
+  for (int x = lane; x < c; x += 32) cp_async8(stage + x, keys + x);
+  for (int x = lane; x < co; x += 32) cp_async8(stage + c + x, other + x);
+  cp_async_wait_all();
+  __syncwarp();
+  const int n = c + co;
+  int lo, hi;
+  warp_value_range(stage, n, lane, lo, hi);
+  const unsigned span = (unsigned)(hi - lo);
+  const int sh = span < 256u ? 0 : 24 - __clz((int)span);
+  warp_value_hist(stage, n, lo, sh, hist, lane);
+  int bin;
+  unsigned above;
+  hist_find_desc(hist, C, lane, bin, above);
+  const unsigned keep = above + hist[bin];
+  __syncwarp();
+  int kept;
+  if (keep <= keep_limit) {
+    t = lo + (bin << sh);
+    kept = warp_keep_value_ge_to(stage, c, t, keys, lane);
+  } else {
+    const uint64_t kth = warp_select_kth(stage, n, (int)C, hist, lane);
+    kept = warp_gather_ge(stage, c, kth, keys, lane);
+    t = key_val(kth);
   }
   __syncwarp();
+  return kept;
+}
 
-  // final lists: the C best keys of each row, sorted
-  for (int l = 0; l < kRowsPerWarp; ++l) {
-    const int lr = warp * kRowsPerWarp + l;
-    const uint32_t i = row0 + (uint32_t)lr;
-    if (i >= P.nA) break;
-    const int cnt = sCnt[lr];
-    const uint64_t* rb = row_buf(i);
-    const uint64_t kmin = cnt > (int)C ? warp_select_kth(rb, cnt, (int)C, hMine, lane) : 1ull;
-    const int kept = warp_gather_ge(rb, cnt, kmin, sMine, lane);
-    const int size = pow2_at_least(kept);
-    for (int x = kept + lane; x < size; x += 32) sMine[x] = 0ull;
+template <bool kSplit, bool kSelf>
+__global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t C = P.C;
+  uint32_t* __restrict__ err = P.err;
+  const long long wait_lim = P.wait_cycles;
+
+  float* sThr = reinterpret_cast<float*>(smem + kOffThr);
+  int* sKept = reinterpret_cast<int*>(smem + kOffKept);          // [row][buffer]
+  uint32_t* sReq = reinterpret_cast<uint32_t*>(smem + kOffReq);  // buffer | count << 1 of a hand-over
+  uint32_t* sFin = reinterpret_cast<uint32_t*>(smem + kOffFin);  // active buffer | count << 1 at the end
+  uint32_t* sMisc = reinterpret_cast<uint32_t*>(smem + kOffMisc);
+  uint32_t* sMask = sMisc;      // [4]: rows of each epilogue warp awaiting compaction
+  uint32_t* sDone = sMisc + 4;  // epilogue warps that finished their sweep
+  uint32_t* sTmem = sMisc + 5;  // tensor-memory base (written by tcgen05.alloc)
+  const uint32_t bar0 = smem_u32(smem + kOffBars);
+  auto full_bar = [&](uint32_t s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](uint32_t s) { return bar0 + 8u * (kStages + s); };
+  auto accf_bar = [&](uint32_t b) { return bar0 + 8u * (2 * kStages + b); };
+  auto acce_bar = [&](uint32_t b) { return bar0 + 8u * (2 * kStages + 2 + b); };
+  const uint32_t a_bar = bar0 + 8u * (2 * kStages + 4);
+
+  const uint32_t row0 = blockIdx.x * (uint32_t)kRows;
+  const uint32_t ys = kSplit ? blockIdx.y : 0u;
+  const uint32_t tall = (P.nB + kTileN - 1) / kTileN;
+  const uint32_t tlo = kSplit ? min(tall, ys * P.tps) : 0u;
+  const uint32_t ntiles = kSplit ? min(tall - tlo, P.tps) : tall;
+  auto tile_of = [&](uint32_t u) { return __ldg(P.order + tlo + u); };
+  auto row_buf = [&](uint32_t i, uint32_t b) { return P.buf + (((size_t)i * P.splits + ys) * 2 + b) * kCap; };
+  // compactors and their staging capacity (keys a hand-over may carry)
+  const int ncomp = C <= 256u ? kCompWarps : 2;
+  const int stage_keys = kStageKeysTotal / ncomp * 2 / 3;  // keys a hand-over may carry
+  const int trigger = min(stage_keys - kTileN, 3 * (int)C);
+  const unsigned keep_limit = (C + (unsigned)trigger) / 2;  // a compaction frees at least this much
+
+  // ---- set-up: row state, the rows' bias-digit weights (2^16, 2^8, 1),
+  // barriers, tensor memory
+  for (int r = tid; r < kRows; r += kThreads) {
+    sThr[r] = -FLT_MAX;
+    sKept[2 * r] = 0;
+    sKept[2 * r + 1] = 0;
+    sReq[r] = 0u;
+    sFin[r] = 0u;
+  }
+  if (tid < 5) sMisc[tid] = 0u;
+  for (int x = tid; x < kRows * kExtK; x += kThreads) {
+    const uint32_t r = (uint32_t)x / kExtK, k = (uint32_t)x % kExtK;
+    const float w = k == 0 ? 65536.f : (k == 1 ? 256.f : (k == 2 ? 1.f : 0.f));
+    *reinterpret_cast<__nv_bfloat16*>(smem + kOffAExt + ext_offset(r, k)) = __float2bfloat16_rn(w);
+  }
+  if (tid == 0) {
+    for (uint32_t s = 0; s < (uint32_t)kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (uint32_t b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), kEpiWarps);
+    }
+    mbar_init(a_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(sTmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the weights above, for the tensor cores
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *sTmem;
+
+  if (warp == kProducerWarp) {
+    // ---- producer: the CTA's rows once, then the column tiles into the ring
+    if (lane == 0) {
+      mbar_expect_tx(a_bar, kAMainBytes);
+      bulk_g2s(smem_u32(smem + kOffAMain), reinterpret_cast<const unsigned char*>(P.QA) + (size_t)row0 * kRowBytes,
+               kAMainBytes, a_bar);
+      uint32_t u = 0;
+      for (; u < ntiles; ++u) {
+        const uint32_t s = u % kStages;
+        // stage s last held tile u - kStages: free once its products are done
+        if (u >= (uint32_t)kStages && !mbar_wait(empty_bar(s), ((u / kStages) - 1u) & 1u, wait_lim)) {
+          atomicOr(err, kErrWait);
+          break;
+        }
+        if (u == P.withhold) continue;  // debug: never issued; the waits for it run out
+        const uint32_t t = tile_of(u);
+        unsigned char* st = smem + kOffStages + s * kStageBytes;
+        mbar_expect_tx(full_bar(s), kStageBytes);
+        bulk_g2s(smem_u32(st), reinterpret_cast<const unsigned char*>(P.QB) + (size_t)t * kMainBytes, kMainBytes,
+                 full_bar(s));
+        bulk_g2s(smem_u32(st + kMainBytes), P.ext + (size_t)t * kExtBytes, kExtBytes, full_bar(s));
+      }
+      // every copy issued has landed before the CTA's shared memory is reused (bounded)
+      if (!mbar_wait(a_bar, 0u, wait_lim)) atomicOr(err, kErrWait);
+      for (uint32_t v = u > (uint32_t)kStages ? u - kStages : 0u; v < u; ++v) {
+        if (v == P.withhold) continue;
+        if (!mbar_wait(full_bar(v % kStages), (v / kStages) & 1u, wait_lim)) {
+          atomicOr(err, kErrWait);
+          break;
+        }
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---- one thread issues the products of each tile into accumulator u & 1
+    if (lane == 0) {
+      bool ok = mbar_wait(a_bar, 0u, wait_lim);
+      if (!ok) atomicOr(err, kErrWait);
+      const uint32_t a_main = smem_u32(smem + kOffAMain), a_ext = smem_u32(smem + kOffAExt);
+      uint32_t u = 0;
+      for (; ok && u < ntiles; ++u) {
+        const uint32_t s = u % kStages, b = u & 1u;
+        if (!mbar_wait(full_bar(s), (u / kStages) & 1u, wait_lim)) {
+          atomicOr(err, kErrWait);
+          break;
+        }
+        if (u >= 2 && !mbar_wait(acce_bar(b), ((u >> 1) - 1u) & 1u, wait_lim)) {
+          atomicOr(err, kErrWait);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + kOffStages + s * kStageBytes);
+        const uint32_t d = tbase + b * (uint32_t)kTileN;
+#pragma unroll
+        for (uint32_t ks = 0; ks < 4; ++ks)
+          tc_mma(d, smem_desc(a_main + 32u * ks, 16u, 1024u, 2u), smem_desc(st + 32u * ks, 16u, 1024u, 2u),
+                 ks > 0 ? 1u : 0u);
+        tc_mma(d, smem_desc(a_ext, 128u, 256u, 0u), smem_desc(st + kMainBytes, 128u, 256u, 0u), 1u);
+        tc_commit(empty_bar(s));
+        tc_commit(accf_bar(b));
+      }
+      // the products issued have completed before tensor memory is freed
+      if (u > 0 && !mbar_wait(accf_bar((u - 1u) & 1u), ((u - 1u) >> 1) & 1u, wait_lim)) atomicOr(err, kErrWait);
+    }
+  } else if (warp < kEpiWarps) {
+    // ---- epilogue: thread = row (tensor-memory lane 32 * warp + lane)
+    const int r = warp * 32 + lane;
+    const uint32_t i = row0 + (uint32_t)r;
+    bool live = i < P.nA;
+    uint32_t act = 0;  // the buffer being appended to
+    int cnt = 0;
+    uint64_t* rb = live ? row_buf(i, 0) : nullptr;
+    float thr = -FLT_MAX;
+    const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+    const uint32_t bit = 1u << lane;
+
+    float* sv = reinterpret_cast<float*>(smem + kOffVals) + r * kValStride;
+    // values of one 32-column chunk (column colbase + k in v[k]) that reach
+    // the threshold are appended.  The chunk's maximum is tested first; a
+    // thread whose maximum passes builds its hit mask with two instructions
+    // per value (the sign bit of x - thr: values and threshold are integers,
+    // so the difference has the exact sign, and it is +0 when they are equal)
+    // and reads the hits back from shared memory, so the work beyond the test
+    // follows the number of hits.
+    auto process = [&](const uint32_t (&v)[32], uint32_t colbase) {
+      float m[11];
+#pragma unroll
+      for (int x = 0; x < 10; ++x)
+        m[x] = fmax3(__uint_as_float(v[3 * x]), __uint_as_float(v[3 * x + 1]), __uint_as_float(v[3 * x + 2]));
+      m[10] = fmaxf(__uint_as_float(v[30]), __uint_as_float(v[31]));
+      const float m2 = fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmax3(m[6], m[7], m[8]));
+      const float mx = fmax3(m2, m[9], m[10]);
+      if (live && mx >= thr) {
+        uint32_t miss = 0u;  // bit k: x_k < thr
+#pragma unroll
+        for (int k = 31; k >= 0; --k) miss = __funnelshift_l(__float_as_uint(__uint_as_float(v[k]) - thr), miss, 1);
+        uint32_t hit = ~miss;
+        if (colbase + 32u > P.nB || (kSelf && i - colbase < 32u)) {
+          uint32_t valid = 0u;
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const uint32_t j = colbase + (uint32_t)k;
+            if (j < P.nB && !(kSelf && j == i)) valid |= 1u << k;
+          }
+          hit &= valid;
+        }
+        if (hit) {
+#pragma unroll
+          for (int q4 = 0; q4 < 8; ++q4)
+            *reinterpret_cast<uint4*>(sv + 4 * q4) = make_uint4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+          do {
+            const int k = __ffs(hit) - 1;
+            hit &= hit - 1u;
+            rb[cnt++] = make_key(__float2int_rn(sv[k]), colbase + (uint32_t)k);
+          } while (hit);
+        }
+      }
+    };
+
+    for (uint32_t u = 0; u < ntiles; ++u) {
+      const uint32_t b = u & 1u;
+      const bool got = mbar_wait(accf_bar(b), (u >> 1) & 1u, wait_lim);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) atomicOr(err, kErrWait);
+        break;
+      }
+      tc_fence_after();
+      thr = fmaxf(thr, *reinterpret_cast<volatile float*>(sThr + r));
+      const uint32_t col0 = tile_of(u) * (uint32_t)kTileN;
+      const uint32_t tcol = lane_base + b * (uint32_t)kTileN;
+      uint32_t va[32], vb[32];
+      tmem_ld32(tcol, va);
+      tmem_wait(va);
+#pragma unroll
+      for (int c = 0; c < kTileN / 32; c += 2) {
+        tmem_ld32(tcol + 32u * (uint32_t)(c + 1), vb);
+        process(va, col0 + 32u * (uint32_t)c);
+        tmem_wait(vb);
+        if (c + 2 < kTileN / 32) {
+          tmem_ld32(tcol + 32u * (uint32_t)(c + 2), va);
+        } else {  // every column of the accumulator is in registers: release it
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce_bar(b));
+        }
+        process(vb, col0 + 32u * (uint32_t)(c + 1));
+        if (c + 2 < kTileN / 32) tmem_wait(va);
+      }
+      // a full buffer goes to the compactor, unless it still holds the other one
+      if (live && cnt > trigger) {
+        bool pending = (ld_volatile(sMask + warp) & bit) != 0u;
+        if (pending && cnt > stage_keys - kTileN) {  // a hand-over must fit the staging area: wait (bounded)
+          const long long t0 = clock64();
+          while (pending && clock64() - t0 <= wait_lim) pending = (ld_volatile(sMask + warp) & bit) != 0u;
+          if (pending) {
+            atomicOr(err, kErrWait);
+            live = false;
+          }
+        }
+        if (live && !pending) {
+          sReq[r] = act | ((uint32_t)cnt << 1);
+          __threadfence_block();
+          atomicOr(sMask + warp, bit);
+          act ^= 1u;
+          cnt = (int)ld_volatile(reinterpret_cast<const uint32_t*>(sKept + 2 * r + act));
+          rb = row_buf(i, act);
+        }
+      }
+      __syncwarp();
+    }
+    // the last hand-over completes before the final state is published
+    if (live) {
+      const long long t0 = clock64();
+      bool pending = true;
+      while ((pending = (ld_volatile(sMask + warp) & bit) != 0u) && clock64() - t0 <= wait_lim) {
+      }
+      if (pending) atomicOr(err, kErrWait);
+    }
+    sFin[r] = act | ((uint32_t)cnt << 1);
+    __threadfence_block();
     __syncwarp();
-    warp_bitonic_desc(sMine, size, lane);
+    if (lane == 0) atomicOr(sDone, 1u << warp);
+  } else if (warp >= kEpiWarps + 2) {
+    // ---- compactor q serves the rows of epilogue warps [q * per, (q + 1) * per)
+    const int q = warp - (kEpiWarps + 2);
+    if (q < ncomp) {
+      const int per = kEpiWarps / ncomp;
+      const uint32_t served = ((1u << per) - 1u) << (q * per);
+      unsigned* hist = reinterpret_cast<unsigned*>(smem + kOffCompHist + q * 1024);
+      uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kOffCompKeys) + (size_t)q * (kStageKeysTotal / ncomp);
+      long long t0 = clock64();
+      for (;;) {
+        uint32_t done = 0u;  // requests: bit (epilogue warp * 32 + lane) of a 64-bit mask
+        uint64_t m = 0ull;
+        if (lane == 0) {
+          done = ld_volatile(sDone) & served;
+          for (int e = 0; e < per; ++e) m |= (uint64_t)ld_volatile(sMask + q * per + e) << (32 * e);
+          if (m == 0ull && done == served)  // a last request raced with the done flags
+            for (int e = 0; e < per; ++e) m |= (uint64_t)ld_volatile(sMask + q * per + e) << (32 * e);
+        }
+        m = __shfl_sync(0xffffffffu, m, 0);
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (m == 0ull) {
+          if (done == served) break;
+          if (clock64() - t0 > wait_lim) {
+            if (lane == 0) atomicOr(err, kErrWait);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        while (m) {
+          const int l = __ffsll((long long)m) - 1;
+          m &= m - 1ull;
+          const int ew = q * per + (l >> 5);  // epilogue warp of the row
+          const int r = ew * 32 + (l & 31);
+          const uint32_t rq = ld_volatile(sReq + r);
+          const uint32_t b = rq & 1u;
+          uint64_t* keys = row_buf(row0 + (uint32_t)r, b);
+          const int co = (int)ld_volatile(reinterpret_cast<const uint32_t*>(sKept + 2 * r + (b ^ 1u)));
+          int t = 0;
+          const int kept =
+              compact_buffer(keys, (int)(rq >> 1), row_buf(row0 + (uint32_t)r, b ^ 1u), co, C, keep_limit, hist, stage,
+                             lane, t);
+          __threadfence_block();
+          if (lane == 0) {
+            sKept[2 * r + b] = kept;
+            sThr[r] = fmaxf(sThr[r], (float)t);
+            __threadfence_block();
+            atomicAnd(sMask + ew, ~(1u << (l & 31)));
+          }
+          __syncwarp();
+        }
+        t0 = clock64();
+      }
+    }
+  }
+
+  // ---- tear-down: tensor memory freed once every product and load is done
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(kTmemCols));
+
+  // ---- final lists: each row's C best keys of its two buffers, sorted (the
+  // ring is free: every copy landed)
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + kOffStages + warp * kFinalBytes);
+  uint64_t* sort = reinterpret_cast<uint64_t*>(smem + kOffStages + warp * kFinalBytes + 1024);
+  for (int r = warp; r < kRows; r += kWarps) {
+    const uint32_t i = row0 + (uint32_t)r;
+    if (i >= P.nA) break;
+    const uint32_t fin = sFin[r];
+    const uint32_t act = fin & 1u;
+    const int ca = (int)(fin >> 1), co = sKept[2 * r + (act ^ 1u)];
+    const int c0 = act == 0 ? ca : co, c1 = act == 0 ? co : ca;
+    uint64_t* b0 = row_buf(i, 0);
+    // buffer 1's keys move down to follow buffer 0's (reads of a batch before its writes)
+    for (int x0 = 0; x0 < c1; x0 += 32 * kBatch) {
+      uint64_t k[kBatch];
+#pragma unroll
+      for (int v = 0; v < kBatch; ++v) {
+        const int x = x0 + 32 * v + lane;
+        k[v] = x < c1 ? b0[kCap + x] : 0ull;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int v = 0; v < kBatch; ++v) {
+        const int x = x0 + 32 * v + lane;
+        if (x < c1) b0[c0 + x] = k[v];
+      }
+      __syncwarp();
+    }
+    const int total = c0 + c1;
+    const uint64_t kmin = total > (int)C ? warp_select_kth(b0, total, (int)C, hist, lane) : 1ull;
+    const int kept = warp_gather_ge(b0, total, kmin, sort, lane);
+    const int size = pow2_at_least(kept);
+    for (int x = kept + lane; x < size; x += 32) sort[x] = 0ull;
+    __syncwarp();
+    warp_bitonic_desc(sort, size, lane);
     if (kSplit) {
       uint64_t* dst = P.part + ((size_t)i * P.splits + ys) * C;
-      for (uint32_t x = lane; x < C; x += 32) dst[x] = (int)x < kept ? sMine[x] : 0ull;
+      for (uint32_t x = lane; x < C; x += 32) dst[x] = (int)x < kept ? sort[x] : 0ull;
     } else {
       for (uint32_t x = lane; x < C; x += 32) {
         const bool have = (int)x < kept;
-        out_idx[(size_t)i * C + x] = have ? key_idx(sMine[x]) : 0xffffffffu;
-        out_val[(size_t)i * C + x] = have ? key_val(sMine[x]) : INT32_MIN;
+        P.out_idx[(size_t)i * C + x] = have ? key_idx(sort[x]) : 0xffffffffu;
+        P.out_val[(size_t)i * C + x] = have ? key_val(sort[x]) : INT32_MIN;
       }
     }
     __syncwarp();
-  }
-
-  // every issued copy has landed before the CTA's shared memory is released
-  // (all of them were consumed, unless a wait ran out); each wait is bounded
-  __syncthreads();
-  if (tid == 0) {
-    const uint32_t issued = *sNext;
-    for (uint32_t u = issued > (uint32_t)kStages ? issued - kStages : 0u; u < issued; ++u) {
-      if (u == P.withhold) continue;
-      if (!mbar_wait(barFull + 8 * (u % kStages), (u / kStages) & 1, P.wait_cycles)) {
-        atomicOr(err, kErrWait);
-        break;
-      }
-    }
   }
 }
 
@@ -815,20 +904,76 @@ __global__ void widen_kernel(const int8_t* __restrict__ q, uint32_t n, uint32_t 
   qb[swz_index(r, (int)(x - r * kDim))] = __float2bfloat16_rn(r < n ? (float)q[x] : 0.f);
 }
 
-__global__ void bias_float_kernel(const int32_t* __restrict__ bias, uint32_t n, uint32_t npad, float* biasf) {
-  const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < npad) biasf[x] = (bias && x < n) ? (float)bias[x] : 0.f;
+// Sweep order of the column tiles: by each tile's largest column bias,
+// highest first (a column's bias adds to its value in every row, so the tiles
+// most likely to hold every row's best values come first and the rows'
+// thresholds rise early; the order changes no result).  One block sorts up to
+// kOrderMax tiles (bitonic, in shared memory); more tiles keep their natural
+// order.
+constexpr int kOrderMax = 4096;
+__global__ void __launch_bounds__(1024) tile_order_kernel(const int32_t* __restrict__ bias, uint32_t n,
+                                                          uint32_t tiles, uint32_t* order) {
+  __shared__ uint64_t key[kOrderMax];
+  if (tiles > (uint32_t)kOrderMax || !bias) {
+    for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) order[t] = t;
+    return;
+  }
+  for (uint32_t t = threadIdx.x; t < (uint32_t)kOrderMax; t += blockDim.x) {
+    uint64_t k = 0ull;  // padding sorts last
+    if (t < tiles) {
+      int32_t m = INT32_MIN;
+      for (uint32_t j = t * kTileN; j < min(n, (t + 1) * kTileN); ++j) m = max(m, __ldg(bias + j));
+      // larger bias first, then lower tile index
+      k = ((uint64_t)((uint32_t)m ^ 0x80000000u) << 32) | (uint64_t)(0xffffffffu - t);
+    }
+    key[t] = k;
+  }
+  __syncthreads();
+  for (int sz = 2; sz <= kOrderMax; sz <<= 1)
+    for (int st = sz >> 1; st > 0; st >>= 1) {
+      for (int x = threadIdx.x; x < kOrderMax; x += blockDim.x) {
+        const int y = x ^ st;
+        if (y > x) {
+          const uint64_t a = key[x], b = key[y];
+          const bool desc = (x & sz) == 0;
+          if (desc ? (a < b) : (a > b)) {
+            key[x] = b;
+            key[y] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) order[t] = 0xffffffffu - (uint32_t)key[t];
 }
 
-size_t bias_pad(uint32_t n) { return ((size_t)n + kTileCols - 1) / kTileCols * kTileCols; }
+// one thread per (column, K half) of the padded columns: the bias digits
+// (b >> 16, (b >> 8) & 255, b & 255 at K = 0, 1, 2; zero elsewhere and past n)
+__global__ void bias_digits_kernel(const int32_t* __restrict__ bias, uint32_t n, uint32_t npad, unsigned char* ext) {
+  const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= 2u * npad) return;
+  const uint32_t j = x >> 1, h = x & 1u;
+  const int32_t b = (bias && j < n) ? bias[j] : 0;
+  __nv_bfloat16 v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(0.f);
+  if (h == 0) {
+    v[0] = __float2bfloat16_rn((float)(b >> 16));
+    v[1] = __float2bfloat16_rn((float)((b >> 8) & 255));
+    v[2] = __float2bfloat16_rn((float)(b & 255));
+  }
+  *reinterpret_cast<uint4*>(ext + ext_offset(j, 8u * h)) = *reinterpret_cast<const uint4*>(v);
+}
+
+size_t bias_pad(uint32_t n) { return ((size_t)n + kTileN - 1) / kTileN * kTileN; }
 
 }  // namespace
 
 size_t dot_topk_qb_bytes(uint32_t n) { return bias_pad(n) * kRowBytes; }
 
 // column splits of a launch over nA rows and nB columns on the current
-// device: enough CTAs for kCtasPerSm per SM when the row blocks alone are
-// fewer, each split at least 8 tiles of 64 columns
+// device: enough CTAs for one per SM when the row blocks alone are fewer,
+// each split at least two tiles of 256 columns
 uint32_t dot_topk_splits(uint32_t nA, uint32_t nB) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
@@ -836,22 +981,30 @@ uint32_t dot_topk_splits(uint32_t nA, uint32_t nB) {
     cudaGetLastError();
     sms = 152;
   }
-  const uint32_t blocks = (nA + kRowsPerCta - 1) / kRowsPerCta;
-  const uint32_t tiles = (nB + kTileCols - 1) / kTileCols;
-  const uint32_t slots = (uint32_t)kCtasPerSm * (uint32_t)sms;
-  const uint32_t want = (slots + blocks - 1) / std::max(blocks, 1u);
-  return std::max(1u, std::min(want, tiles / 8));
+  const uint32_t blocks = (nA + kRows - 1) / kRows;
+  const uint32_t tiles = (nB + kTileN - 1) / kTileN;
+  const uint32_t want = ((uint32_t)sms + blocks - 1) / std::max(blocks, 1u);
+  return std::max(1u, std::min(want, tiles / 2));
 }
+
+// scratch layout: [row buffers: nA x S x 2 x kCap keys][column bias digits:
+// bias_pad(nB) x 32 B][error word: 16 B][tile order: tiles x 4 B, rounded up
+// to 16 B][split lists: nA x S x C keys]
+static size_t ext_offset_bytes(uint32_t nA, uint32_t nB) {
+  return (size_t)nA * dot_topk_splits(nA, nB) * 2 * kCap * sizeof(uint64_t);
+}
+
+static size_t order_bytes(uint32_t nB) { return (bias_pad(nB) / kTileN * sizeof(uint32_t) + 15) & ~(size_t)15; }
 
 size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB, uint32_t C) {
   const size_t S = dot_topk_splits(nA, nB);
-  return (size_t)nA * S * kCap * sizeof(uint64_t) + bias_pad(nB) * sizeof(float) + 16 +
+  return ext_offset_bytes(nA, nB) + bias_pad(nB) * (size_t)kExtK * 2 + 16 + order_bytes(nB) +
          (S > 1 ? (size_t)nA * S * C * sizeof(uint64_t) : 0);
 }
 
 uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB) {
-  const size_t S = dot_topk_splits(nA, nB);
-  return reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(buf + (size_t)nA * S * kCap) + bias_pad(nB));
+  return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(buf) + ext_offset_bytes(nA, nB) +
+                                     bias_pad(nB) * (size_t)kExtK * 2);
 }
 
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
@@ -860,31 +1013,33 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
   if (nA == 0) return cudaSuccess;
   const uint32_t S = dot_topk_splits(nA, nB);
   const auto kernel = S > 1 ? (self ? dot_topk_kernel<true, true> : dot_topk_kernel<true, false>)
-                             : (self ? dot_topk_kernel<false, true> : dot_topk_kernel<false, false>);
+                            : (self ? dot_topk_kernel<false, true> : dot_topk_kernel<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal);
   if (e != cudaSuccess) return e;
-  const uint32_t tiles = (nB + kTileCols - 1) / kTileCols;
+  const uint32_t tiles = (nB + kTileN - 1) / kTileN;
+  unsigned char* ext = reinterpret_cast<unsigned char*>(buf) + ext_offset_bytes(nA, nB);
   DotArgs P;
   P.QA = QA;
   P.QB = QB;
-  P.biasf = reinterpret_cast<float*>(buf + (size_t)nA * S * kCap);  // after the append buffers (16-byte aligned)
+  P.ext = ext;
   P.nA = nA;
   P.nB = nB;
   P.C = C;
-  P.self = self;
   P.splits = S;
   P.tps = (tiles + S - 1) / S;
   P.buf = buf;
-  // the split lists follow the buffer's own error-word slot (err itself may live elsewhere)
-  P.part = S > 1 ? reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(dot_topk_err_word(buf, nA, nB)) + 16) : nullptr;
+  uint32_t* order = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(dot_topk_err_word(buf, nA, nB)) + 16);
+  P.order = order;
+  P.part = S > 1 ? reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(order) + order_bytes(nB)) : nullptr;
   P.out_idx = idx;
   P.out_val = val;
   P.err = err;
   P.wait_cycles = dbg.wait_cycles >= 0 ? dbg.wait_cycles : kWaitCycles;
   P.withhold = dbg.withhold;
   const uint32_t npad = (uint32_t)bias_pad(nB);
-  bias_float_kernel<<<(npad + 255) / 256 + (npad == 0), 256, 0, s>>>(biasB, nB, npad, const_cast<float*>(P.biasf));
-  const dim3 grid((nA + kRowsPerCta - 1) / kRowsPerCta, S);
+  if (npad) bias_digits_kernel<<<(2 * npad + 255) / 256, 256, 0, s>>>(biasB, nB, npad, ext);
+  if (tiles) tile_order_kernel<<<1, 1024, 0, s>>>(biasB, nB, tiles, order);
+  const dim3 grid((nA + kRows - 1) / kRows, S);
   kernel<<<grid, kThreads, kSmemTotal, s>>>(P);
   if (S > 1)
     merge_splits_kernel<<<(nA + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(P.part, nA, S, C, idx, val);

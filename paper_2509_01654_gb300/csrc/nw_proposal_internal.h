@@ -17,7 +17,7 @@ namespace prop {
 // the context a model was created on (its allocations, stream and error text)
 nw_ctx* model_ctx(const nw_model* M);
 
-constexpr int kCap = 2048;       // append-buffer keys per row of the dot-product top-C
+constexpr int kCap = 2048;       // keys per append buffer of the dot-product top-C (two buffers per row)
 constexpr int kFeat = 63;        // embedding outputs 0..62 are features, 63 is the bias
 constexpr int kBiasLimit = 1 << 23;
 
@@ -31,7 +31,7 @@ cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t
                      int32_t* bias, float* scale, cudaStream_t s, bool given_scale = false);
 // int8 rows (row-major) -> the candidate kernel's bf16 rows
 cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s);
-// bf16 rows: zero-padded to whole 64-row tiles, 16-byte chunks of row r
+// bf16 rows: zero-padded to whole 256-row tiles, 16-byte chunks of row r
 // permuted by r & 7
 size_t dot_topk_qb_bytes(uint32_t n);
 // scratch of a launch over nA rows, nB columns and C candidates (the err
