@@ -466,7 +466,7 @@ nw_status nw_debug_fail_alloc(nw_ctx *ctx, uint32_t countdown);
  *                 up after this many SM clock cycles; < 0 restores its own
  *                 bound (2e9 cycles, about a second);
  *   withhold_tile != UINT32_MAX: the candidate kernel's producer never issues
- *                 the bulk copy of this column tile (of 256 columns; the
+ *                 the bulk copy of this column tile (of 128 columns; the
  *                 tile's index in the CTA's sweep order), so every
  *                 wait for it runs out with no copy in flight; the kernel
  *                 still waits (bounded) for the copies it did issue before it

@@ -10,33 +10,37 @@
 // order, and the top-C selection is an exact, deterministic function of the
 // integers (ties: lower column index first).
 //
-// dot_topk_kernel: a CTA owns 128 rows (the 128 lanes of tensor memory) and
-// sweeps column tiles of 256.  Ten warps with fixed roles:
-//   * a producer thread streams each tile (256 rows of 128 B, already in the
-//     128-byte-swizzled K-major layout, plus 8 KiB of bias digits) into a
+// dot_topk_kernel: a CTA owns two blocks of 128 rows (each block fills the
+// 128 lanes of tensor memory) and sweeps column tiles of 128.  Fourteen warps
+// with fixed roles:
+//   * a producer thread streams each tile (128 rows of 128 B, already in the
+//     128-byte-swizzled K-major layout, plus 4 KiB of bias digits) into a
 //     four-stage shared-memory ring with cp.async.bulk, counted on mbarriers;
-//   * an MMA thread issues, per tile, four tcgen05.mma (M = 128, N = 256,
-//     K = 16, bf16 -> f32) over the 64 features and a fifth over the bias
-//     digits into one of two 256-column accumulators, then commits the stage
-//     back to the producer and the accumulator to the epilogue;
-//   * four epilogue warps, one thread per row, read the accumulator with
+//     every tile feeds both row blocks;
+//   * an MMA thread issues, per tile and row block, four tcgen05.mma
+//     (M = 128, N = 128, K = 16, bf16 -> f32) over the 64 features and a fifth
+//     over the bias digits into one of the block's two accumulators, then
+//     commits the stage back to the producer and the accumulators to the
+//     epilogue;
+//   * eight epilogue warps (two per SM sub-partition, so each hides the
+//     other's latency), one thread per row, read the accumulator with
 //     tcgen05.ld (32 columns at a time, the next load in flight while the
 //     current values are tested), release it, and append every value that
 //     reaches the row's threshold to one of the row's two global buffers;
-//   * four compactor warps, one per epilogue warp: when a row's active
-//     buffer passes its trigger, the epilogue thread hands the buffer over and
-//     keeps appending to the other one; the compactor raises the row's
-//     threshold to a value at or below the C-th best key in the handed buffer
-//     and drops the keys below it, off the path of the tensor pipe.
+//   * compactor warps: when a row's active buffer passes its trigger, the
+//     epilogue thread hands the buffer over and keeps appending to the other
+//     one; a compactor stages the handed keys and the other buffer's kept keys
+//     in shared memory, raises the row's threshold to a value at or below the
+//     C-th best of them and drops the handed keys below it, off the path of
+//     the tensor pipe.
 // A key is appended when its value is >= the threshold, so the column order
 // does not matter: a CTA starts at its own diagonal tile (similar words sit
-// near each other in the length-sorted order, so thresholds rise early), and
-// every key of the final top C is always kept (each threshold is at most the
-// C-th best value among keys already seen).  A final pass selects each row's
-// C best keys from its two buffers exactly and sorts them.  Every wait is
-// bounded and sets kErrWait when it runs out; the CTA then stops, waits
-// (bounded) for the copies and products it issued, frees its tensor memory
-// and returns.
+// near each other in the length-sorted order), and every key of the final top
+// C is always kept (each threshold is at most the C-th best value among keys
+// already seen).  A final pass selects each row's C best keys from its two
+// buffers exactly and sorts them.  Every wait is bounded and sets kErrWait
+// when it runs out; the CTA then stops, waits (bounded) for the copies and
+// products it issued, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cuda_runtime.h>
@@ -53,33 +57,36 @@ namespace {
 
 constexpr int kDim = 64;                  // values per row (bf16)
 constexpr int kRowBytes = kDim * 2;       // 128
-constexpr int kRows = 128;                // rows per CTA = tensor-memory lanes
-constexpr int kTileN = 256;               // columns per tile (MMA N)
+constexpr int kRows = 128;                // rows of one MMA = tensor-memory lanes
+constexpr int kBlocksPerCta = 2;          // row blocks per CTA (each B tile feeds both)
+constexpr int kCtaRows = kRows * kBlocksPerCta;
+constexpr int kTileN = 128;               // columns per tile (MMA N)
+constexpr int kPadRows = 256;             // row and column sets are zero-padded to this
 constexpr int kExtK = 16;                 // bias-digit K (one MMA K-step)
-constexpr int kStages = 3;
-constexpr int kMainBytes = kTileN * kRowBytes;          // 32 KiB
-constexpr int kExtBytes = kTileN * kExtK * 2;           // 8 KiB
-constexpr int kStageBytes = kMainBytes + kExtBytes;     // 40 KiB
-constexpr int kAMainBytes = kRows * kRowBytes;          // 16 KiB
-constexpr int kAExtBytes = kRows * kExtK * 2;           // 4 KiB
-constexpr int kEpiWarps = 4;                            // warps 0..3
-constexpr int kProducerWarp = 4;
-constexpr int kMmaWarp = 5;
-constexpr int kCompWarps = 4;                           // warps 6..9
+constexpr int kStages = 4;
+constexpr int kMainBytes = kTileN * kRowBytes;          // 16 KiB
+constexpr int kExtBytes = kTileN * kExtK * 2;           // 4 KiB
+constexpr int kStageBytes = kMainBytes + kExtBytes;     // 20 KiB
+constexpr int kAMainBytes = kRows * kRowBytes;          // 16 KiB per row block
+constexpr int kAExtBytes = kRows * kExtK * 2;           // 4 KiB (the same for both blocks)
+constexpr int kEpiWarps = 8;                            // warps 0..7: block = warp / 4, lanes 32 * (warp % 4)
+constexpr int kProducerWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr int kCompWarps = 4;                           // warps 10..13
 constexpr int kWarps = kEpiWarps + 2 + kCompWarps;
 constexpr int kThreads = kWarps * 32;
+constexpr int kChunks = kTileN / 32;                    // 32-column chunks of a tile
 constexpr int kSel = NW_MAX_CANDIDATES;                 // per-warp gather/sort area (keys)
-constexpr uint32_t kTmemCols = 2 * kTileN;              // two accumulators
+constexpr uint32_t kTmemCols = 2 * kBlocksPerCta * kTileN;  // two accumulators per block: 512
 
 // dynamic shared memory (bytes from a 1024-aligned base)
 constexpr int kOffAMain = 0;
-constexpr int kOffAExt = kOffAMain + kAMainBytes;
+constexpr int kOffAExt = kOffAMain + kBlocksPerCta * kAMainBytes;
 constexpr int kOffStages = kOffAExt + kAExtBytes;
 // compactor warps: a 256-bin histogram each and one staging area for the
 // handed-over keys and the kept keys of the row's other buffer, split into
 // kCompWarps areas of 1,536 keys (hand-overs of up to 1,024 keys, C <= 256) or
-// two of 3,072 (hand-overs of up to 2,048 keys, larger C: two compactors, each
-// serving two epilogue warps)
+// two of 3,072 (hand-overs of up to 2,048 keys, larger C: two compactors)
 constexpr int kStageKeysTotal = 6144;
 constexpr int kOffCompHist = kOffStages + kStages * kStageBytes;
 constexpr int kOffCompKeys = kOffCompHist + kCompWarps * 1024;
@@ -87,14 +94,14 @@ constexpr int kOffCompKeys = kOffCompHist + kCompWarps * 1024;
 // hits can be read by index (row stride 36 floats: conflict-free 16-byte stores)
 constexpr int kValStride = 36;
 constexpr int kOffVals = kOffCompKeys + kStageKeysTotal * 8;
-constexpr int kOffRow = kOffVals + kRows * kValStride * 4;
+constexpr int kOffRow = kOffVals + kCtaRows * kValStride * 4;
 constexpr int kFinalBytes = 256 * 4 + kSel * 8;        // final pass: histogram + sort area per warp
 // row state: threshold, kept counts of the two buffers, hand-over request, final state
 constexpr int kOffThr = kOffRow;
-constexpr int kOffKept = kOffThr + kRows * 4;
-constexpr int kOffReq = kOffKept + kRows * 8;
-constexpr int kOffFin = kOffReq + kRows * 4;
-constexpr int kOffMisc = kOffFin + kRows * 4;          // request masks, done flags, tmem address
+constexpr int kOffKept = kOffThr + kCtaRows * 4;
+constexpr int kOffReq = kOffKept + kCtaRows * 8;
+constexpr int kOffFin = kOffReq + kCtaRows * 4;
+constexpr int kOffMisc = kOffFin + kCtaRows * 4;       // request masks, done flags, tmem address
 constexpr int kOffBars = kOffMisc + 64;
 constexpr int kNumBars = 2 * kStages + 4 + 1;          // full, empty, acc full x2, acc empty x2, A loaded
 constexpr int kSmemUsed = kOffBars + kNumBars * 8;
@@ -102,7 +109,8 @@ constexpr int kSmemTotal = kSmemUsed + 1024;           // slack for aligning the
 static_assert(kSmemTotal <= 227 * 1024, "one CTA per SM");
 // the final pass reuses the stage ring: per warp a histogram and a sort area
 static_assert(kWarps * kFinalBytes <= kStages * kStageBytes, "final-pass scratch fits the ring");
-static_assert(kCap >= 2 * NW_MAX_CANDIDATES + kTileN, "a buffer holds a compaction's keys and a tile");
+static_assert(kCap >= 2 * NW_MAX_CANDIDATES + 256, "a buffer holds a compaction's keys and a tile");
+static_assert(kPadRows % kCtaRows == 0 && kPadRows % kTileN == 0, "padding covers whole row blocks and tiles");
 // a pipeline wait gives up after this many SM clock cycles (about a second)
 constexpr long long kWaitCycles = 2000000000ll;
 
@@ -394,7 +402,6 @@ struct DotArgs {
   uint32_t* out_idx;
   int32_t* out_val;
   uint32_t* err;
-  const uint32_t* order;  // column tiles in sweep order (each split sweeps a contiguous part)
   long long wait_cycles;  // bound of every wait (SM clock cycles)
   uint32_t withhold;      // debug: a column tile never issued (UINT32_MAX: none)
 };
@@ -469,9 +476,9 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   uint32_t* sReq = reinterpret_cast<uint32_t*>(smem + kOffReq);  // buffer | count << 1 of a hand-over
   uint32_t* sFin = reinterpret_cast<uint32_t*>(smem + kOffFin);  // active buffer | count << 1 at the end
   uint32_t* sMisc = reinterpret_cast<uint32_t*>(smem + kOffMisc);
-  uint32_t* sMask = sMisc;      // [4]: rows of each epilogue warp awaiting compaction
-  uint32_t* sDone = sMisc + 4;  // epilogue warps that finished their sweep
-  uint32_t* sTmem = sMisc + 5;  // tensor-memory base (written by tcgen05.alloc)
+  uint32_t* sMask = sMisc;                  // [kEpiWarps]: rows of each epilogue warp awaiting compaction
+  uint32_t* sDone = sMisc + kEpiWarps;      // epilogue warps that finished their sweep
+  uint32_t* sTmem = sMisc + kEpiWarps + 1;  // tensor-memory base (written by tcgen05.alloc)
   const uint32_t bar0 = smem_u32(smem + kOffBars);
   auto full_bar = [&](uint32_t s) { return bar0 + 8u * s; };
   auto empty_bar = [&](uint32_t s) { return bar0 + 8u * (kStages + s); };
@@ -479,12 +486,21 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   auto acce_bar = [&](uint32_t b) { return bar0 + 8u * (2 * kStages + 2 + b); };
   const uint32_t a_bar = bar0 + 8u * (2 * kStages + 4);
 
-  const uint32_t row0 = blockIdx.x * (uint32_t)kRows;
+  const uint32_t row0 = blockIdx.x * (uint32_t)kCtaRows;
   const uint32_t ys = kSplit ? blockIdx.y : 0u;
   const uint32_t tall = (P.nB + kTileN - 1) / kTileN;
   const uint32_t tlo = kSplit ? min(tall, ys * P.tps) : 0u;
   const uint32_t ntiles = kSplit ? min(tall - tlo, P.tps) : tall;
-  auto tile_of = [&](uint32_t u) { return __ldg(P.order + tlo + u); };
+  uint32_t start = 0;  // a square sweep starts at the CTA's own diagonal tile
+  if (kSelf) {
+    const uint32_t d = row0 / kTileN;
+    if (d >= tlo && d < tlo + ntiles) start = d - tlo;
+  }
+  auto tile_of = [&](uint32_t u) {
+    uint32_t x = u + start;
+    if (x >= ntiles) x -= ntiles;
+    return tlo + x;
+  };
   auto row_buf = [&](uint32_t i, uint32_t b) { return P.buf + (((size_t)i * P.splits + ys) * 2 + b) * kCap; };
   // compactors and their staging capacity (keys a hand-over may carry)
   const int ncomp = C <= 256u ? kCompWarps : 2;
@@ -494,14 +510,14 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
 
   // ---- set-up: row state, the rows' bias-digit weights (2^16, 2^8, 1),
   // barriers, tensor memory
-  for (int r = tid; r < kRows; r += kThreads) {
+  for (int r = tid; r < kCtaRows; r += kThreads) {
     sThr[r] = -FLT_MAX;
     sKept[2 * r] = 0;
     sKept[2 * r + 1] = 0;
     sReq[r] = 0u;
     sFin[r] = 0u;
   }
-  if (tid < 5) sMisc[tid] = 0u;
+  if (tid <= kEpiWarps) sMisc[tid] = 0u;
   for (int x = tid; x < kRows * kExtK; x += kThreads) {
     const uint32_t r = (uint32_t)x / kExtK, k = (uint32_t)x % kExtK;
     const float w = k == 0 ? 65536.f : (k == 1 ? 256.f : (k == 2 ? 1.f : 0.f));
@@ -533,9 +549,9 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   if (warp == kProducerWarp) {
     // ---- producer: the CTA's rows once, then the column tiles into the ring
     if (lane == 0) {
-      mbar_expect_tx(a_bar, kAMainBytes);
+      mbar_expect_tx(a_bar, kBlocksPerCta * kAMainBytes);
       bulk_g2s(smem_u32(smem + kOffAMain), reinterpret_cast<const unsigned char*>(P.QA) + (size_t)row0 * kRowBytes,
-               kAMainBytes, a_bar);
+               kBlocksPerCta * kAMainBytes, a_bar);
       uint32_t u = 0;
       for (; u < ntiles; ++u) {
         const uint32_t s = u % kStages;
@@ -563,7 +579,8 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       }
     }
   } else if (warp == kMmaWarp) {
-    // ---- one thread issues the products of each tile into accumulator u & 1
+    // ---- one thread issues the products of each tile for both row blocks
+    // into their accumulators u & 1
     if (lane == 0) {
       bool ok = mbar_wait(a_bar, 0u, wait_lim);
       if (!ok) atomicOr(err, kErrWait);
@@ -581,12 +598,16 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
         }
         tc_fence_after();
         const uint32_t st = smem_u32(smem + kOffStages + s * kStageBytes);
-        const uint32_t d = tbase + b * (uint32_t)kTileN;
 #pragma unroll
-        for (uint32_t ks = 0; ks < 4; ++ks)
-          tc_mma(d, smem_desc(a_main + 32u * ks, 16u, 1024u, 2u), smem_desc(st + 32u * ks, 16u, 1024u, 2u),
-                 ks > 0 ? 1u : 0u);
-        tc_mma(d, smem_desc(a_ext, 128u, 256u, 0u), smem_desc(st + kMainBytes, 128u, 256u, 0u), 1u);
+        for (uint32_t rb = 0; rb < (uint32_t)kBlocksPerCta; ++rb) {
+          const uint32_t d = tbase + (2u * rb + b) * (uint32_t)kTileN;
+          const uint32_t am = a_main + rb * (uint32_t)kAMainBytes;
+#pragma unroll
+          for (uint32_t ks = 0; ks < 4; ++ks)
+            tc_mma(d, smem_desc(am + 32u * ks, 16u, 1024u, 2u), smem_desc(st + 32u * ks, 16u, 1024u, 2u),
+                   ks > 0 ? 1u : 0u);
+          tc_mma(d, smem_desc(a_ext, 128u, 256u, 0u), smem_desc(st + kMainBytes, 128u, 256u, 0u), 1u);
+        }
         tc_commit(empty_bar(s));
         tc_commit(accf_bar(b));
       }
@@ -594,15 +615,17 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       if (u > 0 && !mbar_wait(accf_bar((u - 1u) & 1u), ((u - 1u) >> 1) & 1u, wait_lim)) atomicOr(err, kErrWait);
     }
   } else if (warp < kEpiWarps) {
-    // ---- epilogue: thread = row (tensor-memory lane 32 * warp + lane)
+    // ---- epilogue: thread = row; warp w reads row block w / 4, tensor-memory
+    // lanes 32 * (w % 4) + lane (two warps per SM sub-partition)
     const int r = warp * 32 + lane;
+    const uint32_t blk = (uint32_t)warp >> 2;
     const uint32_t i = row0 + (uint32_t)r;
     bool live = i < P.nA;
     uint32_t act = 0;  // the buffer being appended to
     int cnt = 0;
     uint64_t* rb = live ? row_buf(i, 0) : nullptr;
     float thr = -FLT_MAX;
-    const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16);
     const uint32_t bit = 1u << lane;
 
     float* sv = reinterpret_cast<float*>(smem + kOffVals) + r * kValStride;
@@ -622,10 +645,13 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       const float m2 = fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmax3(m[6], m[7], m[8]));
       const float mx = fmax3(m2, m[9], m[10]);
       if (live && mx >= thr) {
-        uint32_t miss = 0u;  // bit k: x_k < thr
+        uint32_t ms[4] = {0u, 0u, 0u, 0u};  // bit k: x_k < thr, in four independent chains
 #pragma unroll
-        for (int k = 31; k >= 0; --k) miss = __funnelshift_l(__float_as_uint(__uint_as_float(v[k]) - thr), miss, 1);
-        uint32_t hit = ~miss;
+        for (int k = 7; k >= 0; --k)
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            ms[g] = __funnelshift_l(__float_as_uint(__uint_as_float(v[8 * g + k]) - thr), ms[g], 1);
+        uint32_t hit = ~(ms[0] | (ms[1] << 8) | (ms[2] << 16) | (ms[3] << 24));
         if (colbase + 32u > P.nB || (kSelf && i - colbase < 32u)) {
           uint32_t valid = 0u;
 #pragma unroll
@@ -658,16 +684,16 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       tc_fence_after();
       thr = fmaxf(thr, *reinterpret_cast<volatile float*>(sThr + r));
       const uint32_t col0 = tile_of(u) * (uint32_t)kTileN;
-      const uint32_t tcol = lane_base + b * (uint32_t)kTileN;
+      const uint32_t tcol = lane_base + (2u * blk + b) * (uint32_t)kTileN;
       uint32_t va[32], vb[32];
       tmem_ld32(tcol, va);
       tmem_wait(va);
 #pragma unroll
-      for (int c = 0; c < kTileN / 32; c += 2) {
+      for (int c = 0; c < kChunks; c += 2) {
         tmem_ld32(tcol + 32u * (uint32_t)(c + 1), vb);
         process(va, col0 + 32u * (uint32_t)c);
         tmem_wait(vb);
-        if (c + 2 < kTileN / 32) {
+        if (c + 2 < kChunks) {
           tmem_ld32(tcol + 32u * (uint32_t)(c + 2), va);
         } else {  // every column of the accumulator is in registers: release it
           tc_fence_before();
@@ -675,7 +701,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
           if (lane == 0) mbar_arrive(acce_bar(b));
         }
         process(vb, col0 + 32u * (uint32_t)(c + 1));
-        if (c + 2 < kTileN / 32) tmem_wait(va);
+        if (c + 2 < kChunks) tmem_wait(va);
       }
       // a full buffer goes to the compactor, unless it still holds the other one
       if (live && cnt > trigger) {
@@ -721,17 +747,16 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kOffCompKeys) + (size_t)q * (kStageKeysTotal / ncomp);
       long long t0 = clock64();
       for (;;) {
-        uint32_t done = 0u;  // requests: bit (epilogue warp * 32 + lane) of a 64-bit mask
-        uint64_t m = 0ull;
+        uint32_t done = 0u, any = 0u;
         if (lane == 0) {
           done = ld_volatile(sDone) & served;
-          for (int e = 0; e < per; ++e) m |= (uint64_t)ld_volatile(sMask + q * per + e) << (32 * e);
-          if (m == 0ull && done == served)  // a last request raced with the done flags
-            for (int e = 0; e < per; ++e) m |= (uint64_t)ld_volatile(sMask + q * per + e) << (32 * e);
+          for (int e = 0; e < per; ++e) any |= ld_volatile(sMask + q * per + e);
+          if (any == 0u && done == served)  // a last request raced with the done flags
+            for (int e = 0; e < per; ++e) any |= ld_volatile(sMask + q * per + e);
         }
-        m = __shfl_sync(0xffffffffu, m, 0);
+        any = __shfl_sync(0xffffffffu, any, 0);
         done = __shfl_sync(0xffffffffu, done, 0);
-        if (m == 0ull) {
+        if (any == 0u) {
           if (done == served) break;
           if (clock64() - t0 > wait_lim) {
             if (lane == 0) atomicOr(err, kErrWait);
@@ -740,27 +765,30 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
           __nanosleep(64);
           continue;
         }
-        while (m) {
-          const int l = __ffsll((long long)m) - 1;
-          m &= m - 1ull;
-          const int ew = q * per + (l >> 5);  // epilogue warp of the row
-          const int r = ew * 32 + (l & 31);
-          const uint32_t rq = ld_volatile(sReq + r);
-          const uint32_t b = rq & 1u;
-          uint64_t* keys = row_buf(row0 + (uint32_t)r, b);
-          const int co = (int)ld_volatile(reinterpret_cast<const uint32_t*>(sKept + 2 * r + (b ^ 1u)));
-          int t = 0;
-          const int kept =
-              compact_buffer(keys, (int)(rq >> 1), row_buf(row0 + (uint32_t)r, b ^ 1u), co, C, keep_limit, hist, stage,
-                             lane, t);
-          __threadfence_block();
-          if (lane == 0) {
-            sKept[2 * r + b] = kept;
-            sThr[r] = fmaxf(sThr[r], (float)t);
+        for (int e = 0; e < per; ++e) {
+          const int ew = q * per + e;  // an epilogue warp served
+          uint32_t m = lane == 0 ? ld_volatile(sMask + ew) : 0u;
+          m = __shfl_sync(0xffffffffu, m, 0);
+          while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1u;
+            const int r = ew * 32 + l;
+            const uint32_t rq = ld_volatile(sReq + r);
+            const uint32_t b = rq & 1u;
+            uint64_t* keys = row_buf(row0 + (uint32_t)r, b);
+            const int co = (int)ld_volatile(reinterpret_cast<const uint32_t*>(sKept + 2 * r + (b ^ 1u)));
+            int t = 0;
+            const int kept = compact_buffer(keys, (int)(rq >> 1), row_buf(row0 + (uint32_t)r, b ^ 1u), co, C,
+                                            keep_limit, hist, stage, lane, t);
             __threadfence_block();
-            atomicAnd(sMask + ew, ~(1u << (l & 31)));
+            if (lane == 0) {
+              sKept[2 * r + b] = kept;
+              sThr[r] = fmaxf(sThr[r], (float)t);
+              __threadfence_block();
+              atomicAnd(sMask + ew, ~(1u << l));
+            }
+            __syncwarp();
           }
-          __syncwarp();
         }
         t0 = clock64();
       }
@@ -778,7 +806,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   // ring is free: every copy landed)
   unsigned* hist = reinterpret_cast<unsigned*>(smem + kOffStages + warp * kFinalBytes);
   uint64_t* sort = reinterpret_cast<uint64_t*>(smem + kOffStages + warp * kFinalBytes + 1024);
-  for (int r = warp; r < kRows; r += kWarps) {
+  for (int r = warp; r < kCtaRows; r += kWarps) {
     const uint32_t i = row0 + (uint32_t)r;
     if (i >= P.nA) break;
     const uint32_t fin = sFin[r];
@@ -904,49 +932,6 @@ __global__ void widen_kernel(const int8_t* __restrict__ q, uint32_t n, uint32_t 
   qb[swz_index(r, (int)(x - r * kDim))] = __float2bfloat16_rn(r < n ? (float)q[x] : 0.f);
 }
 
-// Sweep order of the column tiles: by each tile's largest column bias,
-// highest first (a column's bias adds to its value in every row, so the tiles
-// most likely to hold every row's best values come first and the rows'
-// thresholds rise early; the order changes no result).  One block sorts up to
-// kOrderMax tiles (bitonic, in shared memory); more tiles keep their natural
-// order.
-constexpr int kOrderMax = 4096;
-__global__ void __launch_bounds__(1024) tile_order_kernel(const int32_t* __restrict__ bias, uint32_t n,
-                                                          uint32_t tiles, uint32_t* order) {
-  __shared__ uint64_t key[kOrderMax];
-  if (tiles > (uint32_t)kOrderMax || !bias) {
-    for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) order[t] = t;
-    return;
-  }
-  for (uint32_t t = threadIdx.x; t < (uint32_t)kOrderMax; t += blockDim.x) {
-    uint64_t k = 0ull;  // padding sorts last
-    if (t < tiles) {
-      int32_t m = INT32_MIN;
-      for (uint32_t j = t * kTileN; j < min(n, (t + 1) * kTileN); ++j) m = max(m, __ldg(bias + j));
-      // larger bias first, then lower tile index
-      k = ((uint64_t)((uint32_t)m ^ 0x80000000u) << 32) | (uint64_t)(0xffffffffu - t);
-    }
-    key[t] = k;
-  }
-  __syncthreads();
-  for (int sz = 2; sz <= kOrderMax; sz <<= 1)
-    for (int st = sz >> 1; st > 0; st >>= 1) {
-      for (int x = threadIdx.x; x < kOrderMax; x += blockDim.x) {
-        const int y = x ^ st;
-        if (y > x) {
-          const uint64_t a = key[x], b = key[y];
-          const bool desc = (x & sz) == 0;
-          if (desc ? (a < b) : (a > b)) {
-            key[x] = b;
-            key[y] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) order[t] = 0xffffffffu - (uint32_t)key[t];
-}
-
 // one thread per (column, K half) of the padded columns: the bias digits
 // (b >> 16, (b >> 8) & 255, b & 255 at K = 0, 1, 2; zero elsewhere and past n)
 __global__ void bias_digits_kernel(const int32_t* __restrict__ bias, uint32_t n, uint32_t npad, unsigned char* ext) {
@@ -965,7 +950,7 @@ __global__ void bias_digits_kernel(const int32_t* __restrict__ bias, uint32_t n,
   *reinterpret_cast<uint4*>(ext + ext_offset(j, 8u * h)) = *reinterpret_cast<const uint4*>(v);
 }
 
-size_t bias_pad(uint32_t n) { return ((size_t)n + kTileN - 1) / kTileN * kTileN; }
+size_t bias_pad(uint32_t n) { return ((size_t)n + kPadRows - 1) / kPadRows * kPadRows; }
 
 }  // namespace
 
@@ -973,7 +958,7 @@ size_t dot_topk_qb_bytes(uint32_t n) { return bias_pad(n) * kRowBytes; }
 
 // column splits of a launch over nA rows and nB columns on the current
 // device: enough CTAs for one per SM when the row blocks alone are fewer,
-// each split at least two tiles of 256 columns
+// each split at least four tiles of 128 columns
 uint32_t dot_topk_splits(uint32_t nA, uint32_t nB) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
@@ -981,24 +966,21 @@ uint32_t dot_topk_splits(uint32_t nA, uint32_t nB) {
     cudaGetLastError();
     sms = 152;
   }
-  const uint32_t blocks = (nA + kRows - 1) / kRows;
+  const uint32_t blocks = (nA + kCtaRows - 1) / kCtaRows;
   const uint32_t tiles = (nB + kTileN - 1) / kTileN;
   const uint32_t want = ((uint32_t)sms + blocks - 1) / std::max(blocks, 1u);
-  return std::max(1u, std::min(want, tiles / 2));
+  return std::max(1u, std::min(want, tiles / 4));
 }
 
 // scratch layout: [row buffers: nA x S x 2 x kCap keys][column bias digits:
-// bias_pad(nB) x 32 B][error word: 16 B][tile order: tiles x 4 B, rounded up
-// to 16 B][split lists: nA x S x C keys]
+// bias_pad(nB) x 32 B][error word: 16 B][split lists: nA x S x C keys]
 static size_t ext_offset_bytes(uint32_t nA, uint32_t nB) {
   return (size_t)nA * dot_topk_splits(nA, nB) * 2 * kCap * sizeof(uint64_t);
 }
 
-static size_t order_bytes(uint32_t nB) { return (bias_pad(nB) / kTileN * sizeof(uint32_t) + 15) & ~(size_t)15; }
-
 size_t dot_topk_buffer_bytes(uint32_t nA, uint32_t nB, uint32_t C) {
   const size_t S = dot_topk_splits(nA, nB);
-  return ext_offset_bytes(nA, nB) + bias_pad(nB) * (size_t)kExtK * 2 + 16 + order_bytes(nB) +
+  return ext_offset_bytes(nA, nB) + bias_pad(nB) * (size_t)kExtK * 2 + 16 +
          (S > 1 ? (size_t)nA * S * C * sizeof(uint64_t) : 0);
 }
 
@@ -1028,9 +1010,7 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
   P.splits = S;
   P.tps = (tiles + S - 1) / S;
   P.buf = buf;
-  uint32_t* order = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(dot_topk_err_word(buf, nA, nB)) + 16);
-  P.order = order;
-  P.part = S > 1 ? reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(order) + order_bytes(nB)) : nullptr;
+  P.part = S > 1 ? reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(dot_topk_err_word(buf, nA, nB)) + 16) : nullptr;
   P.out_idx = idx;
   P.out_val = val;
   P.err = err;
@@ -1038,8 +1018,7 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
   P.withhold = dbg.withhold;
   const uint32_t npad = (uint32_t)bias_pad(nB);
   if (npad) bias_digits_kernel<<<(2 * npad + 255) / 256, 256, 0, s>>>(biasB, nB, npad, ext);
-  if (tiles) tile_order_kernel<<<1, 1024, 0, s>>>(biasB, nB, tiles, order);
-  const dim3 grid((nA + kRows - 1) / kRows, S);
+  const dim3 grid((nA + kCtaRows - 1) / kCtaRows, S);
   kernel<<<grid, kThreads, kSmemTotal, s>>>(P);
   if (S > 1)
     merge_splits_kernel<<<(nA + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(P.part, nA, S, C, idx, val);

@@ -62,7 +62,7 @@ def test_list_insertion_bound_reports_timeout_and_context_recovers(ctx, oracle_m
 
 @pytest.mark.parametrize("withhold", [0, 8])  # issued before the sweep, and by a refill of the ring
 def test_candidate_pipeline_wait_reports_timeout_and_context_recovers(ctx, withhold):
-    n, C = 20_000, 64  # 79 column tiles of 256 per CTA (no column splits)
+    n, C = 20_000, 64  # 157 column tiles of 128, two column splits of 79
     g = np.random.default_rng(11)
     q = g.integers(-127, 128, (n, 64)).astype(np.int8)
     bias = g.integers(-20_000, 20_001, n).astype(np.int32)
