@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   // compactors and their staging capacity (keys a hand-over may carry)
   const int ncomp = C <= 256u ? kCompWarps : 2;
   const int stage_keys = kStageKeysTotal / ncomp * 2 / 3;  // keys a hand-over may carry
-  const int trigger = min(stage_keys - kTileN, 3 * (int)C);
+  const int trigger = min(stage_keys - kTileN, (int)C + (int)C / 2);
   const unsigned keep_limit = (C + (unsigned)trigger) / 2;  // a compaction frees at least this much
 
   // ---- set-up: row state, the rows' bias-digit weights (2^16, 2^8, 1),
