@@ -504,6 +504,9 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   auto row_buf = [&](uint32_t i, uint32_t b) { return P.buf + (((size_t)i * P.splits + ys) * 2 + b) * kCap; };
   // compactors and their staging capacity (keys a hand-over may carry)
   const int ncomp = C <= 256u ? kCompWarps : 2;
+  // a hand-over carries at most stage_keys keys, and the other buffer's kept
+  // keys number at most keep_limit <= C + trigger / 2 <= area / 3: the two fit
+  // one compactor's area of kStageKeysTotal / ncomp keys
   const int stage_keys = kStageKeysTotal / ncomp * 2 / 3;  // keys a hand-over may carry
   const int trigger = min(stage_keys - kTileN, (int)C + (int)C / 2);
   const unsigned keep_limit = (C + (unsigned)trigger) / 2;  // a compaction frees at least this much
@@ -682,6 +685,10 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
         break;
       }
       tc_fence_after();
+      if (live && cnt > kCap - kTileN) {  // cannot happen (hand-overs cap the count); never write past the buffer
+        atomicOr(err, kErrCapacity);
+        live = false;
+      }
       thr = fmaxf(thr, *reinterpret_cast<volatile float*>(sThr + r));
       const uint32_t col0 = tile_of(u) * (uint32_t)kTileN;
       const uint32_t tcol = lane_base + (2u * blk + b) * (uint32_t)kTileN;
@@ -744,7 +751,8 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       const int per = kEpiWarps / ncomp;
       const uint32_t served = ((1u << per) - 1u) << (q * per);
       unsigned* hist = reinterpret_cast<unsigned*>(smem + kOffCompHist + q * 1024);
-      uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kOffCompKeys) + (size_t)q * (kStageKeysTotal / ncomp);
+      const int area = kStageKeysTotal / ncomp;  // staging keys of this compactor
+      uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kOffCompKeys) + (size_t)q * area;
       long long t0 = clock64();
       for (;;) {
         uint32_t done = 0u, any = 0u;
@@ -776,10 +784,16 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
             const uint32_t rq = ld_volatile(sReq + r);
             const uint32_t b = rq & 1u;
             uint64_t* keys = row_buf(row0 + (uint32_t)r, b);
-            const int co = (int)ld_volatile(reinterpret_cast<const uint32_t*>(sKept + 2 * r + (b ^ 1u)));
+            int co = (int)ld_volatile(reinterpret_cast<const uint32_t*>(sKept + 2 * r + (b ^ 1u)));
+            int c = (int)(rq >> 1);
+            if (c > stage_keys || co > area - stage_keys) {  // cannot happen; never stage past the area
+              if (lane == 0) atomicOr(err, kErrCapacity);
+              c = min(c, stage_keys);
+              co = min(co, area - stage_keys);
+            }
             int t = 0;
-            const int kept = compact_buffer(keys, (int)(rq >> 1), row_buf(row0 + (uint32_t)r, b ^ 1u), co, C,
-                                            keep_limit, hist, stage, lane, t);
+            const int kept = compact_buffer(keys, c, row_buf(row0 + (uint32_t)r, b ^ 1u), co, C, keep_limit, hist,
+                                            stage, lane, t);
             __threadfence_block();
             if (lane == 0) {
               sKept[2 * r + b] = kept;

@@ -663,6 +663,7 @@ nw_status check_device_flags(nw_ctx* c, const uint32_t* d_small) {
   if (err & kErrRetry) return set_err(c, NW_ETIMEOUT, "a neighbour-list update exceeded its retry bound");
   if (err & kErrWait) return set_err(c, NW_ETIMEOUT, "a pipeline wait on the device ran out");
   if (err & kErrInput) return set_err(c, NW_EINVAL, "invalid word index in the input (outputs may be partially written)");
+  if (err & kErrCapacity) return set_err(c, NW_ERANGE, "a device buffer reached its capacity (outputs are not valid)");
   if (err & kErrHistRange) return set_err(c, NW_ERANGE, "a score fell outside the histogram range");
   return NW_OK;
 }

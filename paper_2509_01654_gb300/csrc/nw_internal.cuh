@@ -43,6 +43,7 @@ constexpr uint32_t kErrRetry = 1u;      // a list insertion exceeded its retry b
 constexpr uint32_t kErrHistRange = 2u;  // a score fell outside the histogram bins
 constexpr uint32_t kErrInput = 4u;      // invalid input seen on the device (code/length/index)
 constexpr uint32_t kErrWait = 8u;       // a pipeline wait ran out (the kernel stopped early)
+constexpr uint32_t kErrCapacity = 16u;  // a buffer would have overflowed (the access was skipped)
 
 __host__ __device__ constexpr int ceil4(int x) { return (x + 3) & ~3; }
 
