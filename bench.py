@@ -497,7 +497,8 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
     n = w.n
     out_i = torch.empty((n, k), dtype=torch.int32, device=dev)
     out_s = torch.empty((n, k), dtype=torch.int16, device=dev)
-    train_cfg = dict(batch_pairs=8192, lr=1e-3, lr_final=1e-4, clip_norm=1.0, nbr_fraction=0.5, seed=1)
+    train_cfg = dict(batch_pairs=8192, lr=1e-3, lr_final=1e-4, clip_norm=1.0, nbr_fraction=0.5, seed=1,
+                     long_len=args.train_long_len, long_fraction=args.train_long_fraction)
 
     def evaluate(model, C, reps):
         model.proposal_topk(d, C, k, nbr_idx=out_i, nbr_score=out_s)  # warm-up
@@ -530,7 +531,11 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
     t0 = time.perf_counter()
     losses = model.train(d, steps=args.proposal_steps, nbr=ex_i, **train_cfg)
     train_s = time.perf_counter() - t0
+    # the proposal alone, then with the exhaustive path for long words
+    res_proposal_only = {"256": evaluate(model, 256, max(2, args.steps))}
+    model.set_exact_length(args.exact_length)
     res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (256, 384, 512)}
+    model.set_exact_length(args.query_exact_length)
     queries = proposal_queries(args, model, d, k, recall_vs_exact)
     # candidates without a network: the C words nearest in length order (stable by index)
     order = np.argsort(w.lengths, kind="stable")
@@ -557,6 +562,9 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
         "workload": (f"{n:,} words of the exhaustive workload; approximate top-{k} by the learned proposal "
                      f"(embed, quantise, C candidates by exact integer dot product, exact rescoring) against "
                      f"the exhaustive top-{k} lists of the timed leg"),
+        "exact_length": args.exact_length,
+        "query_exact_length": args.query_exact_length,
+        "proposal_only": res_proposal_only,
         "train": {"steps": args.proposal_steps, "pairs": args.proposal_steps * train_cfg["batch_pairs"],
                   "seconds": round(train_s, 2), "target": "s / max(len_i, len_j)",
                   "loss_first_100": round(float(np.mean(losses[:100])), 5),
@@ -636,6 +644,13 @@ def main():
                     help="dictionaries of the batched-launch measurement (0 skips it)")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the substitution-matrix and normalised-ranking measurements")
+    ap.add_argument("--train-long-len", type=int, default=11,
+                    help="training draws --train-long-fraction of its pairs' first words among words this long")
+    ap.add_argument("--train-long-fraction", type=float, default=0.4)
+    ap.add_argument("--exact-length", type=int, default=17,
+                    help="dictionary words of at least this many symbols take the exhaustive path (0: none)")
+    ap.add_argument("--query-exact-length", type=int, default=15,
+                    help="query words of at least this many symbols take the exhaustive path (0: none)")
     ap.add_argument("--proposal-steps", type=int, default=20000,
                     help="training steps of the learned-proposal measurement (0 skips it)")
     args = ap.parse_args()

@@ -76,7 +76,10 @@ nw_status nw_model_loss_grad(nw_model *model, nw_dict *dict, const uint32_t *pi,
  * Each step draws batch_pairs pairs from a SplitMix64 stream of `seed`: a
  * fraction nbr_fraction take j from the given neighbour lists of a uniform i
  * (nbr: n x knb original indices, UINT32_MAX entries skipped; NULL for
- * none), the rest are uniform pairs i != j.  `losses` (steps floats, may be
+ * none), the rest are uniform pairs i != j.  With long_fraction > 0, each
+ * pair's i is drawn, with that probability, uniformly among the dictionary's
+ * words of at least long_len symbols instead (long words are rare in a
+ * dictionary, and the proposal ranks them worst).  `losses` (steps floats, may be
  * NULL) receives each step's mean loss.  Steps run as one captured CUDA
  * graph replayed `steps` times. */
 typedef struct {
@@ -88,6 +91,8 @@ typedef struct {
     float lr_final;         /* > 0: the rate falls linearly from lr to lr_final over the steps; 0: constant */
     float clip_norm;        /* > 0: each step's gradient is scaled to norm <= clip_norm; 0: off */
     uint64_t seed;
+    uint32_t long_len;      /* with long_fraction: the words of at least long_len symbols ... */
+    float long_fraction;    /* ... give a pair's first word with this probability (0: uniform words) */
 } nw_train_config;
 
 nw_status nw_model_train(nw_model *model, nw_dict *dict, const nw_train_config *cfg, const uint32_t *nbr,
@@ -129,10 +134,23 @@ nw_status nw_dot_topk_cross(nw_ctx *ctx, const int8_t *qa, uint32_t na, const in
 nw_status nw_rescore_topk(nw_dict *dict, const uint32_t *cand, uint32_t C, uint32_t k, uint32_t *nbr_idx,
                           int16_t *nbr_score, uint32_t flags);
 
-/* Stage times of the last nw_proposal_topk call, milliseconds. */
+/* Stage times of the last nw_proposal_topk call, milliseconds.  exact_ms is
+ * the exhaustive pass over the long words (nw_proposal_set_exact_length);
+ * total_ms includes it. */
 typedef struct {
-    double embed_ms, quantize_ms, candidates_ms, rescore_ms, total_ms;
+    double embed_ms, quantize_ms, candidates_ms, rescore_ms, total_ms, exact_ms;
 } nw_proposal_profile;
+
+/* Words and query words with at least `min_len` symbols (0: none, the
+ * default) take their k neighbours from the exhaustive kernel instead of the
+ * learned proposal: exact lists, as nw_all_pairs_topk gives for a dictionary
+ * word (itself excluded) and nw_query for a query word.  The proposal ranks
+ * long words poorly (a mean over positions cannot see their longest shared
+ * stretches), and long words are rare in a dictionary, so the exhaustive pass
+ * over them is cheap there; for query words its cost follows the share of
+ * long queries.  Applies to nw_proposal_topk, nw_proposal_query and the
+ * proposal server.  NW_EINVAL for min_len > NW_MAX_WORD_LEN. */
+nw_status nw_proposal_set_exact_length(nw_model *model, uint32_t min_len);
 
 /* The whole proposal path for `dict`: embed every word, quantise, take C
  * candidates per word by dot product, rescore them exactly and keep the k

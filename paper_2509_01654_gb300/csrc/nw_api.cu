@@ -431,6 +431,16 @@ nw_status nw_query(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, 
   if (!d) return NW_EINVAL;
   nw_ctx* c = d->ctx;
   NW_ENTER(c);
+  return nw::query_impl(d, qcodes, qoffsets, nq, k, nbr_idx, nbr_score, flags);
+}
+
+}  // extern "C"
+
+namespace nw {
+
+nw_status query_impl(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, uint32_t nq, uint32_t k,
+                     uint32_t* nbr_idx, int16_t* nbr_score, uint32_t flags) {
+  nw_ctx* c = d->ctx;
   if (flags & NW_RANK_NORMALISED) return set_err(c, NW_EINVAL, "queries rank by raw score only");
   if (nq == 0) return NW_OK;
   if (!qoffsets || !nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null pointer argument");
@@ -535,6 +545,10 @@ nw_status nw_query(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, 
   }
   return NW_OK;
 }
+
+}  // namespace nw
+
+extern "C" {
 
 nw_status nw_measure_int_rates(nw_ctx* c, double ms_target, nw_int_rates* out) {
   NW_ENTER(c);

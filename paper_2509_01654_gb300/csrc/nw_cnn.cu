@@ -491,7 +491,9 @@ __global__ void draw_pairs_kernel(PairDraw d, uint32_t* pi, uint32_t* pj, uint32
   const uint64_t ctr = ((uint64_t)*d.step << 32) | p;
   const uint64_t u1 = splitmix64(d.seed ^ splitmix64(2 * ctr));
   const uint64_t u2 = splitmix64(d.seed ^ splitmix64(2 * ctr + 1));
-  const uint32_t i = (uint32_t)(u1 % d.n);
+  uint32_t i = (uint32_t)(u1 % d.n);
+  if (d.nlong && (uint32_t)((u2 >> 44) & 0xfffffu) < d.long_thresh)
+    i = __ldg(d.perm + d.long0 + (uint32_t)((u1 >> 1) % d.nlong));
   uint32_t j = 0xffffffffu;
   if (d.nbr && p < d.n_nbr && d.knb) {
     j = __ldg(d.nbr + (size_t)i * d.knb + (uint32_t)(u2 % d.knb));

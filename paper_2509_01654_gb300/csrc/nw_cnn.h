@@ -129,6 +129,9 @@ struct PairDraw {
   const uint32_t* nbr;    // n x knb or null
   uint32_t knb;
   uint32_t n_nbr;         // pairs [0, n_nbr) come from the lists
+  const uint32_t* perm;   // sorted position -> original index (long-word draws)
+  uint32_t long0, nlong;  // the long words' sorted positions [long0, long0 + nlong)
+  uint32_t long_thresh;   // a pair's i is a long word when 20 bits of its draw are below this
 };
 cudaError_t draw_pairs(const PairDraw& d, uint32_t* pi, uint32_t* pj, uint32_t* widx, cudaStream_t s);
 // target[p] = score[p] * raw_scale (raw_scale > 0), else score[p] / max(len_i, len_j, 1)

@@ -64,6 +64,11 @@ nw_status topk_into_scratch(nw_dict* d, ScratchProvider provide, uint32_t k, uin
                             int16_t* nbr_score, int64_t* hist, int32_t* hist_lo, uint32_t nbins,
                             uint32_t flags);
 
+// nw_query without entering the context (for library calls that hold it):
+// the k best dictionary words of each query word
+nw_status query_impl(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, uint32_t nq, uint32_t k,
+                     uint32_t* nbr_idx, int16_t* nbr_score, uint32_t flags);
+
 // microbenchmarks of the integer instruction rates
 enum RateOp { kRateViaddmax = 0, kRateVimax3, kRateVimaxRelu, kRateIadd3, kRateLop3, kRateCell, kRateOps };
 cudaError_t launch_rate(int op, int blocks, int iters, const uint32_t* in, uint32_t* out,

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "nw_cnn.h"
@@ -35,6 +36,10 @@ struct nw_model {
   // dictionary (serial) and the parameters (gen) are unchanged
   uint64_t gen = 1, prep_serial = 0, prep_gen = 0;
   DevBuf dQb, dqbias, prep_small, qQb, qcand, qcand_dot, qscore, qbuf;
+  // words of at least exact_len symbols take the exhaustive path (0: none);
+  // their codes, offsets and (k + 1)-long exhaustive lists
+  uint32_t exact_len = 0;
+  DevBuf xcodes, xoffs, xidx, xscore;
 };
 
 namespace {
@@ -48,6 +53,38 @@ prop::DotDebug dot_debug(const nw_ctx* c) {
 }
 
 constexpr int kMaxRowsPerPass = 1 << 20;  // packed positions per forward pass of nw_model_embed
+
+// codes of the dictionary's words from sorted position p0 on (contiguous in
+// a_enc: every symbol e(c) = c << shift replicated in both 16-bit halves)
+__global__ void extract_codes_kernel(const uint32_t* __restrict__ a_enc, uint32_t first, uint32_t total,
+                                     uint32_t shift, uint8_t* __restrict__ codes) {
+  const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < total) codes[x] = (uint8_t)((a_enc[first + x] & 0xffffu) >> shift);
+}
+
+// word w (sorted position p0 + w, original index perm[p0 + w]) gets the
+// first k entries of its exhaustive (k + 1)-long list that are not itself
+__global__ void splice_exact_kernel(const uint32_t* __restrict__ xi, const int16_t* __restrict__ xs, uint32_t m,
+                                    uint32_t k, const uint32_t* __restrict__ perm, uint32_t p0,
+                                    uint32_t* __restrict__ out_idx, int16_t* __restrict__ out_score) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= m) return;
+  const uint32_t self = perm[p0 + w];
+  uint32_t* oi = out_idx + (size_t)self * k;
+  int16_t* os = out_score + (size_t)self * k;
+  uint32_t j = 0;
+  for (uint32_t x = 0; x <= k && j < k; ++x) {
+    const uint32_t id = xi[(size_t)w * (k + 1) + x];
+    if (id == self) continue;
+    oi[j] = id;
+    os[j] = xs[(size_t)w * (k + 1) + x];
+    ++j;
+  }
+  for (; j < k; ++j) {
+    oi[j] = 0xffffffffu;
+    os[j] = INT16_MIN;
+  }
+}
 
 float* fptr(const DevBuf& b, uint64_t off = 0) { return b.as<float>() + off; }
 
@@ -64,7 +101,8 @@ void model_free_buffers(nw_model* M) {
                     &M->rinfo, &M->rword, &M->codes, &M->X0, &M->Y1, &M->Y2, &M->Y3, &M->P, &M->E, &M->dE, &M->dP, &M->dYa,
                     &M->dYb, &M->dX0, &M->pi, &M->pj, &M->target, &M->score16, &M->Eall, &M->Qb,
                     &M->qbias, &M->topbuf, &M->cand, &M->cand_dot, &M->cand_score, &M->nbr,
-                    &M->dQb, &M->dqbias, &M->prep_small, &M->qQb, &M->qcand, &M->qcand_dot, &M->qscore, &M->qbuf};
+                    &M->dQb, &M->dqbias, &M->prep_small, &M->qQb, &M->qcand, &M->qcand_dot, &M->qscore, &M->qbuf,
+                    &M->xcodes, &M->xoffs, &M->xidx, &M->xscore};
   for (DevBuf* b : bufs) ctx_free(c, *b);
 }
 
@@ -313,6 +351,69 @@ nw_status rescore_select(nw_ctx* c, nw_dict* d, const uint32_t* cand, uint32_t C
   return NW_OK;
 }
 
+// The exhaustive (k + 1)-long lists of the dictionary's words with at least
+// M->exact_len symbols (their sorted positions p0 .. n - 1) into M->xidx /
+// M->xscore, on the context's stream, synchronised; *m receives their number
+// and *ms the pass's time.  splice_long_rows then puts them over the proposal
+// lists.
+nw_status exact_long_rows(nw_model* M, nw_dict* d, uint32_t k, uint32_t* m_out, float* ms) {
+  *ms = 0.f;
+  *m_out = 0;
+  nw_ctx* c = M->ctx;
+  const uint32_t L0 = M->exact_len;
+  if (L0 == 0) return NW_OK;
+  const Buckets& bk = d->ws.bk;
+  const uint32_t n = d->ws.n, p0 = bk.start[L0], m = n - p0;
+  if (m == 0) return NW_OK;
+  if (k + 1 > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be below %d on the exact path", NW_MAX_K);
+  std::vector<uint32_t> offs(m + 1, 0u);
+  uint32_t w = 0;
+  for (int Lb = (int)L0; Lb < kBuckets; ++Lb)
+    for (uint32_t r = 0; r < bk.count[Lb]; ++r, ++w) offs[w + 1] = offs[w] + (uint32_t)Lb;
+  const uint32_t total = offs[m];
+  NW_TRY(ctx_ensure(c, M->xcodes, std::max<size_t>(16, total), "long-word codes"));
+  NW_TRY(ctx_ensure(c, M->xoffs, sizeof(uint32_t) * (m + 1), "long-word offsets"));
+  NW_TRY(ctx_ensure(c, M->xidx, sizeof(uint32_t) * (size_t)m * (k + 1), "long-word lists"));
+  NW_TRY(ctx_ensure(c, M->xscore, sizeof(int16_t) * (size_t)m * (k + 1), "long-word lists"));
+  cudaStream_t cs = c->stream;
+  cudaEvent_t ev[2];
+  for (auto& e : ev) NW_CK(cudaEventCreate(&e));
+  struct FreeEv {
+    cudaEvent_t* e;
+    ~FreeEv() {
+      cudaEventDestroy(e[0]);
+      cudaEventDestroy(e[1]);
+    }
+  } fe{ev};
+  NW_CK(cudaEventRecord(ev[0], cs));
+  NW_CK(cudaMemcpyAsync(M->xoffs.p, offs.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, cs));
+  if (total)
+    extract_codes_kernel<<<(total + 255) / 256, 256, 0, cs>>>(d->ws.a_enc.as<uint32_t>(), bk.aenc_base[L0], total,
+                                                            d->ss.shift, M->xcodes.as<uint8_t>());
+  NW_CK(cudaGetLastError());
+  // as nw_query with k + 1 neighbours (the word itself is among them); returns synchronised
+  NW_TRY(query_impl(d, M->xcodes.as<uint8_t>(), M->xoffs.as<uint32_t>(), m, k + 1, M->xidx.as<uint32_t>(),
+                    M->xscore.as<int16_t>(), NW_DEVICE_PTRS));
+  NW_CK(cudaEventRecord(ev[1], cs));
+  NW_CK(cudaEventSynchronize(ev[1]));
+  NW_CK(cudaEventElapsedTime(ms, ev[0], ev[1]));
+  *m_out = m;
+  return NW_OK;
+}
+
+// the m exhaustive lists of exact_long_rows over the proposal lists in
+// out_idx / out_score (device, n x k), on stream s after the work queued there
+nw_status splice_long_rows(nw_model* M, nw_dict* d, uint32_t m, uint32_t k, uint32_t* out_idx, int16_t* out_score,
+                           cudaStream_t s) {
+  nw_ctx* c = M->ctx;
+  if (m == 0) return NW_OK;
+  const uint32_t p0 = d->ws.n - m;
+  splice_exact_kernel<<<(m + 127) / 128, 128, 0, s>>>(M->xidx.as<uint32_t>(), M->xscore.as<int16_t>(), m, k,
+                                                       d->ws.perm.as<uint32_t>(), p0, out_idx, out_score);
+  NW_CK(cudaGetLastError());
+  return NW_OK;
+}
+
 }  // namespace
 
 namespace nw {
@@ -460,6 +561,9 @@ nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, co
   if (n < 2) return set_err(c, NW_EINVAL, "training needs at least 2 words");
   if (cfg->batch_pairs == 0 || cfg->batch_pairs > 65536) return set_err(c, NW_EINVAL, "batch_pairs must be in [1, 65536]");
   if (!(cfg->nbr_fraction >= 0.f && cfg->nbr_fraction <= 1.f)) return set_err(c, NW_EINVAL, "nbr_fraction in [0, 1]");
+  if (!(cfg->long_fraction >= 0.f && cfg->long_fraction <= 1.f)) return set_err(c, NW_EINVAL, "long_fraction in [0, 1]");
+  if (cfg->long_fraction > 0.f && cfg->long_len > (uint32_t)kMaxLen)
+    return set_err(c, NW_EINVAL, "long_len must be at most %d", kMaxLen);
   if (!(cfg->raw_scale >= 0.f)) return set_err(c, NW_EINVAL, "raw_scale must be >= 0");
   if (!(cfg->clip_norm >= 0.f) || !(cfg->lr_final >= 0.f)) return set_err(c, NW_EINVAL, "clip_norm, lr_final >= 0");
   if (nbr && knb == 0) return set_err(c, NW_EINVAL, "neighbour lists need knb >= 1");
@@ -496,6 +600,15 @@ nw_status nw_model_train(nw_model* M, nw_dict* d, const nw_train_config* cfg, co
   pd.nbr = d_nbr;
   pd.knb = knb;
   pd.n_nbr = d_nbr ? (uint32_t)std::lround((double)cfg->nbr_fraction * m) : 0u;
+  pd.perm = d->ws.perm.as<uint32_t>();
+  pd.long0 = 0;
+  pd.nlong = 0;
+  pd.long_thresh = 0;
+  if (cfg->long_fraction > 0.f && cfg->long_len <= (uint32_t)kMaxLen) {
+    pd.long0 = d->ws.bk.start[cfg->long_len];
+    pd.nlong = n - pd.long0;
+    pd.long_thresh = (uint32_t)std::lround((double)cfg->long_fraction * (double)(1u << 20));
+  }
   PairsParams pp = pairs_params(d, err_ptr(M));
   pp.pi = M->pi.as<uint32_t>();
   pp.pj = M->pj.as<uint32_t>();
@@ -754,11 +867,15 @@ nw_status nw_dot_topk_cross(nw_ctx* c, const int8_t* qa, uint32_t na, const int8
   return NW_OK;
 }
 
-nw_status nw_proposal_query(nw_model* M, nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, uint32_t nq,
-                            uint32_t C, uint32_t k, uint32_t* nbr_idx, int16_t* nbr_score, uint32_t flags) {
-  if (!M || !d) return NW_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// nw_proposal_query for every query word through the proposal (the context
+// is held by the caller)
+nw_status proposal_query_impl(nw_model* M, nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, uint32_t nq,
+                              uint32_t C, uint32_t k, uint32_t* nbr_idx, int16_t* nbr_score, uint32_t flags) {
   nw_ctx* c = M->ctx;
-  NW_ENTER(c);
   if (flags & NW_RANK_NORMALISED) return set_err(c, NW_EINVAL, "queries rank by raw score only");
   if (nq == 0) return NW_OK;
   if (!qoffsets || !nbr_idx || !nbr_score) return set_err(c, NW_EINVAL, "null pointer argument");
@@ -861,6 +978,74 @@ nw_status nw_proposal_query(nw_model* M, nw_dict* d, const uint8_t* qcodes, cons
   return NW_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+nw_status nw_proposal_query(nw_model* M, nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets, uint32_t nq,
+                            uint32_t C, uint32_t k, uint32_t* nbr_idx, int16_t* nbr_score, uint32_t flags) {
+  if (!M || !d) return NW_EINVAL;
+  nw_ctx* c = M->ctx;
+  NW_ENTER(c);
+  const uint32_t L0 = M->exact_len;
+  if (L0 == 0 || nq == 0 || !qoffsets || !nbr_idx || !nbr_score)
+    return proposal_query_impl(M, d, qcodes, qoffsets, nq, C, k, nbr_idx, nbr_score, flags);
+  if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  // long query words take the exhaustive path: split the set on the host
+  const bool dev = flags & NW_DEVICE_PTRS;
+  std::vector<uint32_t> off(nq + 1);
+  if (dev) NW_CK(cudaMemcpy(off.data(), qoffsets, sizeof(uint32_t) * (nq + 1), cudaMemcpyDeviceToHost));
+  else std::memcpy(off.data(), qoffsets, sizeof(uint32_t) * (nq + 1));
+  for (uint32_t q = 0; q < nq; ++q)
+    if (off[q + 1] < off[q]) return set_err(c, NW_EINVAL, "query offsets must not decrease");
+  const uint32_t total = off[nq] - off[0];
+  std::vector<uint8_t> codes(std::max<uint32_t>(1u, total));
+  if (total) {
+    if (!qcodes) return set_err(c, NW_EINVAL, "null query codes");
+    if (dev) NW_CK(cudaMemcpy(codes.data(), qcodes + off[0], total, cudaMemcpyDeviceToHost));
+    else std::memcpy(codes.data(), qcodes + off[0], total);
+  }
+  std::vector<uint8_t> sc, lc;
+  std::vector<uint32_t> so(1, 0u), lo(1, 0u), which;  // which: query -> (long << 31) | position in its set
+  for (uint32_t q = 0; q < nq; ++q) {
+    const uint32_t a = off[q] - off[0], len = off[q + 1] - off[q];
+    const bool is_long = len >= L0;
+    std::vector<uint8_t>& dst = is_long ? lc : sc;
+    std::vector<uint32_t>& o = is_long ? lo : so;
+    which.push_back((is_long ? 0x80000000u : 0u) | (uint32_t)(o.size() - 1));
+    dst.insert(dst.end(), codes.begin() + a, codes.begin() + a + len);
+    o.push_back((uint32_t)dst.size());
+  }
+  const uint32_t ns = (uint32_t)so.size() - 1, nl = (uint32_t)lo.size() - 1;
+  if (sc.empty()) sc.push_back(0);
+  if (lc.empty()) lc.push_back(0);
+  std::vector<uint32_t> si((size_t)ns * k), li((size_t)nl * k), ri((size_t)nq * k);
+  std::vector<int16_t> ss((size_t)ns * k), ls((size_t)nl * k), rs((size_t)nq * k);
+  if (ns) NW_TRY(proposal_query_impl(M, d, sc.data(), so.data(), ns, C, k, si.data(), ss.data(), 0));
+  if (nl) NW_TRY(query_impl(d, lc.data(), lo.data(), nl, k, li.data(), ls.data(), 0));
+  for (uint32_t q = 0; q < nq; ++q) {
+    const bool is_long = which[q] >> 31;
+    const size_t src = (size_t)(which[q] & 0x7fffffffu) * k;
+    std::memcpy(ri.data() + (size_t)q * k, (is_long ? li.data() : si.data()) + src, sizeof(uint32_t) * k);
+    std::memcpy(rs.data() + (size_t)q * k, (is_long ? ls.data() : ss.data()) + src, sizeof(int16_t) * k);
+  }
+  if (dev) {
+    NW_CK(cudaMemcpy(nbr_idx, ri.data(), sizeof(uint32_t) * ri.size(), cudaMemcpyHostToDevice));
+    NW_CK(cudaMemcpy(nbr_score, rs.data(), sizeof(int16_t) * rs.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(nbr_idx, ri.data(), sizeof(uint32_t) * ri.size());
+    std::memcpy(nbr_score, rs.data(), sizeof(int16_t) * rs.size());
+  }
+  return NW_OK;
+}
+
+nw_status nw_proposal_set_exact_length(nw_model* M, uint32_t min_len) {
+  if (!M) return NW_EINVAL;
+  if (min_len > (uint32_t)kMaxLen) return set_err(M->ctx, NW_EINVAL, "min_len must be at most %d", kMaxLen);
+  M->exact_len = min_len;
+  return NW_OK;
+}
+
 nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint32_t* nbr_idx, int16_t* nbr_score,
                            nw_proposal_profile* prof, uint32_t flags) {
   if (!M || !d) return NW_EINVAL;
@@ -909,6 +1094,10 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
       for (int x = 0; x < 5; ++x) cudaEventDestroy(e[x]);
     }
   } fe{ev};
+  // the long words' exhaustive lists first (their own stream, timed on their own)
+  float exact_ms = 0.f;
+  uint32_t nlong = 0;
+  NW_TRY(exact_long_rows(M, d, k, &nlong, &exact_ms));
   NW_CK(cudaEventRecord(ev[0], s));
   NW_TRY(embed_all(M, d, s));
   NW_CK(cudaEventRecord(ev[1], s));
@@ -920,6 +1109,7 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
   NW_CK(cudaEventRecord(ev[3], s));
   NW_TRY(rescore_select(c, d, M->cand.as<uint32_t>(), C, k, M->cand_score, out_i, out_s, err_ptr(M), s));
   NW_CK(cudaEventRecord(ev[4], s));
+  NW_TRY(splice_long_rows(M, d, nlong, k, out_i, out_s, s));
   if (!dev) {
     NW_TRY(copy_out(c, nbr_idx, out_i, (size_t)n * k, false, s));
     NW_TRY(copy_out(c, nbr_score, out_s, (size_t)n * k, false, s));
@@ -932,7 +1122,8 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
     prof->quantize_ms = ms[1];
     prof->candidates_ms = ms[2];
     prof->rescore_ms = ms[3];
-    prof->total_ms = (double)ms[0] + ms[1] + ms[2] + ms[3];
+    prof->exact_ms = exact_ms;
+    prof->total_ms = (double)ms[0] + ms[1] + ms[2] + ms[3] + exact_ms;
   }
   return NW_OK;
 }

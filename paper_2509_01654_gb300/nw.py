@@ -41,6 +41,7 @@ EXPORTED = [
     "nw_model_create", "nw_model_free", "nw_model_param_count", "nw_model_get_params", "nw_model_set_params",
     "nw_model_embed", "nw_model_loss_grad", "nw_model_train", "nw_quantize_embeddings", "nw_dot_topk",
     "nw_rescore_topk", "nw_proposal_topk", "nw_dot_topk_cross", "nw_proposal_query", "nw_server_create_proposal",
+    "nw_proposal_set_exact_length",
 ]
 EMBED_DIM = 64
 MAX_CANDIDATES = 512
@@ -52,12 +53,13 @@ class TrainConfig(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_uint32), ("batch_pairs", ctypes.c_uint32), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
                 ("nbr_fraction", ctypes.c_float), ("raw_scale", ctypes.c_float), ("lr_final", ctypes.c_float),
-                ("clip_norm", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("clip_norm", ctypes.c_float), ("seed", ctypes.c_uint64), ("long_len", ctypes.c_uint32),
+                ("long_fraction", ctypes.c_float)]
 
 
 class ProposalProfile(ctypes.Structure):
     _fields_ = [("embed_ms", ctypes.c_double), ("quantize_ms", ctypes.c_double), ("candidates_ms", ctypes.c_double),
-                ("rescore_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("rescore_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("exact_ms", ctypes.c_double)]
 
 
 class NwError(RuntimeError):
@@ -167,6 +169,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_proposal_topk.argtypes = [vp, vp, u32, u32, vp, vp, ctypes.POINTER(ProposalProfile), u32]
     L.nw_dot_topk_cross.argtypes = [vp, vp, u32, vp, vp, u32, u32, vp, vp, u32]
     L.nw_proposal_query.argtypes = [vp, vp, vp, vp, u32, u32, u32, vp, vp, u32]
+    L.nw_proposal_set_exact_length.argtypes = [vp, u32]
     L.nw_server_create_proposal.argtypes = [vp, vp, u32, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
@@ -712,6 +715,10 @@ class Model:
     def param_count(self) -> int:
         return int(load_library().nw_model_param_count(self.handle))
 
+    def set_exact_length(self, min_len: int):
+        """nw_proposal_set_exact_length: words and queries of at least min_len symbols take the exhaustive path (0: none)."""
+        _check(self.ctx.handle, load_library().nw_proposal_set_exact_length(self.handle, min_len))
+
     def get_params(self, out=None):
         if out is None:
             out = np.empty(self.param_count, dtype=np.float32)
@@ -743,12 +750,14 @@ class Model:
 
     def train(self, d: "Dictionary", steps: int, batch_pairs: int = 8192, lr: float = 1e-3, seed: int = 1,
               nbr=None, nbr_fraction: float = 0.5, raw_scale: float = 0.0, lr_final: float = 0.0,
-              clip_norm: float = 0.0, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+              clip_norm: float = 0.0, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+              long_len: int = 0, long_fraction: float = 0.0):
         """Adam on device-drawn pairs labelled by Algorithm 1; returns the per-step losses.
         raw_scale > 0 trains on s * raw_scale, else on s / max(len); lr_final > 0 decays
-        the rate linearly to it; clip_norm > 0 clips the gradient norm."""
+        the rate linearly to it; clip_norm > 0 clips the gradient norm; long_fraction > 0
+        draws that share of the pairs' first words among the words of >= long_len symbols."""
         cfg = TrainConfig(steps, batch_pairs, lr, beta1, beta2, eps, nbr_fraction if nbr is not None else 0.0,
-                          raw_scale, lr_final, clip_norm, seed)
+                          raw_scale, lr_final, clip_norm, seed, long_len, long_fraction)
         losses = np.zeros(max(steps, 1), dtype=np.float32)
         knb = 0
         if nbr is not None:

@@ -435,6 +435,77 @@ def test_proposal_path_properties(ctx, oracle_mod):
     assert 0.0 < strict <= tie <= 1.0
 
 
+def test_exact_length_gives_long_words_their_exhaustive_lists(ctx):
+    """With nw_proposal_set_exact_length(L), words of at least L symbols get
+    exactly the exhaustive lists (themselves excluded), and every shorter
+    word keeps its proposal list."""
+    import torch
+    w = synth.make_words(5000, 40, 1.1, 8.0, 3.0, 1, 25, seed=23)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)
+    ex_i, ex_s, _, _ = d.all_pairs_topk(10, hist=None)
+    m = nw.Model(ctx, 40, seed=3)
+    m.train(d, steps=100, batch_pairs=2048, lr=2e-3, seed=6, nbr=ex_i)
+    base_i, base_s, _ = m.proposal_topk(d, C=64, k=10)
+    L = 13
+    long_rows = w.lengths >= L
+    assert 0 < long_rows.sum() < w.n
+    m.set_exact_length(L)
+    try:
+        idx, score, prof = m.proposal_topk(d, C=64, k=10)
+        assert prof["exact_ms"] > 0 and prof["total_ms"] >= prof["exact_ms"]
+        assert np.array_equal(idx[long_rows], ex_i[long_rows])
+        assert np.array_equal(score[long_rows], ex_s[long_rows])
+        assert np.array_equal(idx[~long_rows], base_i[~long_rows])
+        assert np.array_equal(score[~long_rows], base_s[~long_rows])
+        # device outputs
+        ti = torch.empty((w.n, 10), dtype=torch.int32, device="cuda")
+        ts = torch.empty((w.n, 10), dtype=torch.int16, device="cuda")
+        m.proposal_topk(d, C=64, k=10, nbr_idx=ti, nbr_score=ts)
+        assert np.array_equal(ti.cpu().numpy().view(np.uint32), idx)
+        # every word long: the whole graph is the exhaustive one
+        m.set_exact_length(1)
+        i1, s1, _ = m.proposal_topk(d, C=64, k=10)
+        assert np.array_equal(i1[w.lengths >= 1], ex_i[w.lengths >= 1])
+    finally:
+        m.set_exact_length(0)
+    with pytest.raises(nw.NwError):
+        m.set_exact_length(nw.MAX_WORD_LEN + 1)
+
+
+def test_exact_length_routes_long_queries_to_the_exhaustive_kernel(ctx):
+    import torch
+    w = synth.make_words(4000, 40, 1.1, 8.0, 3.0, 1, 25, seed=24)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)
+    m = nw.Model(ctx, 40, seed=4)
+    m.train(d, steps=50, batch_pairs=1024, lr=2e-3, seed=7)
+    q = synth.serving_queries(700, seed=12)  # lengths 1..30
+    base_i, base_s = m.query(d, q.codes, q.offsets, 64, 10)
+    ex_i, ex_s = d.query(q.codes, q.offsets, 10)
+    L = 15
+    lng = q.lengths >= L
+    assert 0 < lng.sum() < q.n
+    m.set_exact_length(L)
+    try:
+        i, s_ = m.query(d, q.codes, q.offsets, 64, 10)
+        assert np.array_equal(i[lng], ex_i[lng]) and np.array_equal(s_[lng], ex_s[lng])
+        assert np.array_equal(i[~lng], base_i[~lng]) and np.array_equal(s_[~lng], base_s[~lng])
+        # device buffers both ways
+        tc = torch.from_numpy(q.codes).cuda()
+        to = torch.from_numpy(q.offsets.astype(np.int32)).cuda()
+        ti, tsc = m.query(d, tc, to, 64, 10)
+        assert np.array_equal(ti.cpu().numpy().view(np.uint32), i)
+        assert np.array_equal(tsc.cpu().numpy(), s_)
+        # only long queries, and a single short one
+        sub = np.where(lng)[0][:5]
+        li, ls = m.query(d, q.subset(sub).codes, q.subset(sub).offsets, 64, 10)
+        assert np.array_equal(li, ex_i[sub]) and np.array_equal(ls, ex_s[sub])
+        one = q.subset([int(np.argmin(q.lengths))])
+        oi, os_ = m.query(d, one.codes, one.offsets, 64, 10)
+        assert np.array_equal(oi, base_i[[int(np.argmin(q.lengths))]])
+    finally:
+        m.set_exact_length(0)
+
+
 def test_trained_network_beats_the_proposal_without_it(ctx):
     # The same candidate budget three ways, each rescored exactly: the trained
     # network, the same network untrained, and no network at all (the C words
