@@ -175,18 +175,21 @@ nw_status nw_proposal_query(nw_model *model, nw_dict *dict, const uint8_t *qcode
                             uint32_t flags);
 
 /* A query server (nw_server_submit / nw_server_wait / nw_server_destroy of
- * nw.h) that answers through the proposal: each GPU batch holds every queued
- * request that fits cfg->max_batch_queries and runs as
- * nw_proposal_query(model, dict, ..., C, cfg->k); requests arriving while a
- * batch runs join the next one (one batch at a time: the candidate search of
- * a batch already spreads over every SM).  A request's lists equal
+ * nw.h) that answers through the proposal, with continuous batching: each
+ * batch holds the queued requests that fit cfg->max_batch_queries (in arrival
+ * order) and runs as nw_proposal_query(model, dict, ..., C, cfg->k) on one of
+ * the server's slots; up to cfg->max_inflight batches run on the device side
+ * by side, and requests arriving meanwhile are admitted the moment a slot
+ * frees (nw_request_info.inflight_at_start counts the batches already
+ * running).  Each slot owns a context of its own (stream, workspace; capped
+ * at mem_budget_bytes / slots when a budget is given, and the slot count is
+ * lowered until the budget holds an estimate of a slot's memory), a copy of
+ * the model's parameters and exact-path length taken at creation, and a
+ * view of the dictionary's device data.  A request's lists equal
  * nw_proposal_query's for its words alone (a word's embedding, candidates and
- * scores do not depend on the rest of its batch).  cfg->max_inflight and
- * mem_budget_bytes are not used: memory comes from the model's context.  The
- * model and the dictionary must share a context and outlive the server.  The
- * batches use that context: a call of the caller's that holds it meanwhile
- * delays the next batch (retried for up to about 10 s, then NW_EBUSY), and
- * the model's parameters must not change while the server runs. */
+ * scores do not depend on the rest of its batch).  The model and the
+ * dictionary must share a context; the dictionary must outlive the server;
+ * later changes to the model do not reach the server. */
 nw_status nw_server_create_proposal(nw_dict *dict, nw_model *model, uint32_t C, const nw_server_config *cfg,
                                     nw_server **out);
 

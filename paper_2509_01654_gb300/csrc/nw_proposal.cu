@@ -1039,6 +1039,32 @@ nw_status nw_proposal_query(nw_model* M, nw_dict* d, const uint8_t* qcodes, cons
   return NW_OK;
 }
 
+}  // extern "C"
+
+namespace nw {
+namespace prop {
+
+nw_status model_clone(nw_model* src, nw_ctx* c, nw_model** out) {
+  *out = nullptr;
+  NW_TRY(nw_model_create(c, src->alphabet, 0, out));
+  nw_model* M = *out;
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaMemcpyAsync(M->params.p, src->params.p, src->params.bytes, cudaMemcpyDeviceToDevice, M->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
+  if (e != cudaSuccess) {
+    nw_model_free(M);
+    *out = nullptr;
+    return cuda_fail(c, e, "copying model parameters");
+  }
+  M->exact_len = src->exact_len;
+  return NW_OK;
+}
+
+}  // namespace prop
+}  // namespace nw
+
+extern "C" {
+
 nw_status nw_proposal_set_exact_length(nw_model* M, uint32_t min_len) {
   if (!M) return NW_EINVAL;
   if (min_len > (uint32_t)kMaxLen) return set_err(M->ctx, NW_EINVAL, "min_len must be at most %d", kMaxLen);

@@ -16,6 +16,9 @@ namespace prop {
 
 // the context a model was created on (its allocations, stream and error text)
 nw_ctx* model_ctx(const nw_model* M);
+// a model on context c with src's alphabet, parameters (copied on the
+// device) and exact-path length; src's context must not be in use
+nw_status model_clone(nw_model* src, nw_ctx* c, nw_model** out);
 
 constexpr int kCap = 2048;       // keys per append buffer of the dot-product top-C (two buffers per row)
 constexpr int kFeat = 63;        // embedding outputs 0..62 are features, 63 is the bias

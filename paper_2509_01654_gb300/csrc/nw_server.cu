@@ -12,10 +12,12 @@
 // admitted the moment a slot frees, so their GPU work overlaps the running
 // batches'.
 //
-// A proposal server (nw_server_create_proposal) runs each batch through the
-// learned proposal instead: one batch at a time (its candidate search spreads
-// over every SM), holding every queued request that fits, answered by
-// nw_proposal_query on the model's stream.
+// A proposal server (nw_server_create_proposal) answers through the learned
+// proposal instead.  Each of its slots owns a context (stream, workspace), a
+// copy of the model's parameters and a view of the dictionary's device data,
+// and a thread that runs nw_proposal_query for the batch it is given; a
+// dispatcher packs queued requests into batches and hands each to a free
+// slot, so batches run on the device side by side while new requests queue.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -77,6 +79,19 @@ struct Slot {
 
 constexpr size_t kMaxSegs = 2u * kBuckets * kBuckets;  // plan_query makes at most one rectangle per (role, La, LB)
 
+// One batch in flight through the proposal: a private context, the model's
+// parameters copied into it, a non-owning view of the dictionary, and the
+// thread that runs the slot's batches.
+struct PropSlot {
+  nw_ctx* ctx = nullptr;
+  nw_model* model = nullptr;
+  nw_dict* view = nullptr;
+  std::thread th;
+  std::vector<Request*> reqs;  // the batch handed to the slot
+  bool busy = false;           // a batch is assigned and not yet finished
+  bool taken = false;          // the slot's thread has taken the assigned batch
+};
+
 }  // namespace
 
 struct nw_server {
@@ -95,6 +110,8 @@ struct nw_server {
   bool stop = false;
   std::thread worker;
   std::string err;  // guarded by mu
+  std::vector<std::unique_ptr<PropSlot>> pslots;  // proposal mode
+  std::condition_variable cv_slots;               // wakes proposal slot threads
 };
 
 namespace {
@@ -149,6 +166,17 @@ void free_slot(nw_server* S, Slot& s) {
                   (void*)s.h_idx, (void*)s.h_score, (void*)s.h_err})
     if (p) cudaFreeHost(p);
   if (s.stream) cudaStreamDestroy(s.stream);
+}
+
+// A proposal slot's model, dictionary view (its device data stays with the
+// caller's dictionary) and context.
+void free_pslot(PropSlot& s) {
+  if (s.model) nw_model_free(s.model);
+  s.model = nullptr;
+  delete s.view;
+  s.view = nullptr;
+  if (s.ctx) nw_destroy(s.ctx);
+  s.ctx = nullptr;
 }
 
 // Prepares the slot's batch on the host and issues it on the slot's stream.
@@ -272,56 +300,38 @@ void retire(nw_server* S, Slot& s) {
   S->cv_done.notify_all();
 }
 
-// Proposal mode: each batch is every queued request that fits
-// max_batch_queries, answered synchronously by nw_proposal_query; requests
-// arriving meanwhile wait for the next batch.
-void worker_proposal(nw_server* S) {
+// Proposal mode, one slot's thread: runs each batch the dispatcher assigns
+// through nw_proposal_query on the slot's own context, then publishes the
+// results and frees the slot.
+void proposal_slot_main(nw_server* S, PropSlot* slot) {
   cudaSetDevice(S->ictx.device);
-  const uint32_t Q = S->cfg.max_batch_queries, k = S->cfg.k;
+  const uint32_t k = S->cfg.k;
   std::vector<uint8_t> codes;
   std::vector<uint32_t> offsets, idx;
   std::vector<int16_t> score;
   std::unique_lock<std::mutex> lock(S->mu);
-  while (!S->stop) {
-    if (S->queue.empty()) {
-      S->cv.wait_for(lock, std::chrono::milliseconds(2));
-      continue;
-    }
-    std::vector<Request*> batch;
-    uint32_t nq = 0;
-    while (!S->queue.empty() && nq + S->queue.front()->nq <= Q) {
-      batch.push_back(S->queue.front());
-      nq += S->queue.front()->nq;
-      S->queue.pop_front();
-    }
-    const double t0 = now_s();
-    for (Request* r : batch) {
-      r->state = 1;
-      r->info.start_s = t0;
-      r->info.batch_queries = nq;
-      r->info.batch_requests = (uint32_t)batch.size();
-      r->info.inflight_at_start = 0;
-    }
+  for (;;) {
+    S->cv_slots.wait(lock, [&] { return (slot->busy && !slot->taken) || (S->stop && !slot->busy); });
+    if (!slot->busy) break;  // stopped with nothing assigned
+    slot->taken = true;
+    std::vector<Request*> batch = slot->reqs;
     lock.unlock();
     codes.clear();
     offsets.assign(1, 0u);
+    uint32_t nq = 0;
     for (Request* r : batch) {
       const uint32_t base = (uint32_t)codes.size();
       codes.insert(codes.end(), r->codes.begin(), r->codes.end());
       for (uint32_t q = 0; q < r->nq; ++q) offsets.push_back(base + r->offsets[q + 1]);
+      nq += r->nq;
     }
     if (codes.empty()) codes.push_back(0);
     idx.resize((size_t)nq * k);
     score.resize((size_t)nq * k);
-    // a call of the user's on the model's context holds it busy: retry for up to ~10 s
-    nw_status st = NW_EBUSY;
-    for (int attempt = 0; attempt < 10000 && st == NW_EBUSY; ++attempt) {
-      st = nw_proposal_query(S->model, S->dict, codes.data(), offsets.data(), nq, S->C, k, idx.data(), score.data(),
-                             0);
-      if (st == NW_EBUSY) std::this_thread::sleep_for(std::chrono::milliseconds(1));
-    }
+    const nw_status st =
+        nw_proposal_query(slot->model, slot->view, codes.data(), offsets.data(), nq, S->C, k, idx.data(), score.data(), 0);
     lock.lock();
-    if (st != NW_OK) S->err = nw::prop::model_ctx(S->model)->err;
+    if (st != NW_OK) S->err = slot->ctx->err;
     const double t1 = now_s();
     uint32_t first = 0;
     for (Request* r : batch) {
@@ -334,7 +344,48 @@ void worker_proposal(nw_server* S) {
       r->state = 2;
       r->info.done_s = t1;
     }
+    slot->reqs.clear();
+    slot->busy = false;
+    slot->taken = false;
     S->cv_done.notify_all();
+    S->cv.notify_all();
+  }
+}
+
+// Proposal mode, the dispatcher: packs queued requests (in arrival order, at
+// most max_batch_queries words) into a batch for the first free slot; requests
+// arriving meanwhile are admitted as soon as a slot frees.
+void worker_proposal(nw_server* S) {
+  const uint32_t Q = S->cfg.max_batch_queries;
+  std::unique_lock<std::mutex> lock(S->mu);
+  while (!S->stop) {
+    PropSlot* free_slot = nullptr;
+    uint32_t inflight = 0;
+    for (auto& sp : S->pslots) {
+      if (sp->busy) ++inflight;
+      else if (!free_slot) free_slot = sp.get();
+    }
+    if (!free_slot || S->queue.empty()) {
+      S->cv.wait_for(lock, std::chrono::milliseconds(2));
+      continue;
+    }
+    uint32_t nq = 0;
+    while (!S->queue.empty() && nq + S->queue.front()->nq <= Q) {
+      free_slot->reqs.push_back(S->queue.front());
+      nq += S->queue.front()->nq;
+      S->queue.pop_front();
+    }
+    const double t0 = now_s();
+    for (Request* r : free_slot->reqs) {
+      r->state = 1;
+      r->info.start_s = t0;
+      r->info.batch_queries = nq;
+      r->info.batch_requests = (uint32_t)free_slot->reqs.size();
+      r->info.inflight_at_start = inflight;
+    }
+    free_slot->busy = true;
+    free_slot->taken = false;
+    S->cv_slots.notify_all();
   }
   for (Request* r : S->queue) {
     r->status = NW_EINVAL;
@@ -342,6 +393,7 @@ void worker_proposal(nw_server* S) {
   }
   S->queue.clear();
   S->cv_done.notify_all();
+  S->cv_slots.notify_all();
 }
 
 void worker_main(nw_server* S) {
@@ -472,13 +524,47 @@ nw_status nw_server_create_proposal(nw_dict* dict, nw_model* model, uint32_t C, 
   if (cfg->k == 0 || cfg->k > NW_MAX_K) return set_err(nullptr, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
   if (cfg->max_batch_queries == 0 || cfg->max_batch_queries > (1u << 20))
     return set_err(nullptr, NW_EINVAL, "max_batch_queries must be in [1, 2^20]");
+  if (cfg->max_inflight == 0 || cfg->max_inflight > 64)
+    return set_err(nullptr, NW_EINVAL, "max_inflight must be in [1, 64]");
+  const int device = dict->ctx->device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(nullptr, NW_ECUDA, "cudaSetDevice failed");
+  }
+  // slots: max_inflight, fewer when the memory budget does not hold that
+  // many slots' device memory (at least one; each slot's context is capped at
+  // its share of the budget)
+  const uint32_t Q = cfg->max_batch_queries, n = dict->ws.n;
+  const size_t per_slot = nw::prop::dot_topk_buffer_bytes(Q, std::max<uint32_t>(n, 1), C) +
+                          nw::prop::dot_topk_qb_bytes(n) + nw::prop::dot_topk_qb_bytes(Q) + 8 * (size_t)n +
+                          (size_t)Q * C * 16 + (size_t)Q * kMaxLen * 128 * 4 * 8;
+  uint32_t nslots = cfg->max_inflight;
+  if (cfg->mem_budget_bytes)
+    nslots = (uint32_t)std::max<size_t>(1, std::min<size_t>(nslots, cfg->mem_budget_bytes / per_slot));
+  const size_t slot_budget = cfg->mem_budget_bytes ? cfg->mem_budget_bytes / nslots : 0;
   nw_server* S = new nw_server();
   S->dict = dict;
   S->model = model;
   S->C = C;
   S->cfg = *cfg;
-  S->ictx.device = dict->ctx->device;
+  S->ictx.device = device;
   S->ictx.sm_count = dict->ctx->sm_count;
+  for (uint32_t i = 0; i < nslots; ++i) {
+    auto sp = std::make_unique<PropSlot>();
+    nw_status st = nw_create(&sp->ctx, device, slot_budget, nullptr);
+    if (st == NW_OK) st = nw::prop::model_clone(model, sp->ctx, &sp->model);
+    if (st != NW_OK) {
+      const std::string msg = sp->ctx ? sp->ctx->err : g_create_error;
+      free_pslot(*sp);
+      for (auto& q : S->pslots) free_pslot(*q);
+      delete S;
+      return set_err(nullptr, st, "proposal server slot: %s", msg.c_str());
+    }
+    sp->view = new nw_dict(*dict);  // the dictionary's device data, owned by the caller's context
+    sp->view->ctx = sp->ctx;
+    S->pslots.push_back(std::move(sp));
+  }
+  for (auto& sp : S->pslots) sp->th = std::thread(proposal_slot_main, S, sp.get());
   S->worker = std::thread(worker_main, S);
   *out = S;
   return NW_OK;
@@ -564,8 +650,12 @@ void nw_server_destroy(nw_server* S) {
   }
   S->cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  S->cv_slots.notify_all();
+  for (auto& sp : S->pslots)
+    if (sp->th.joinable()) sp->th.join();
   cudaSetDevice(S->ictx.device);
   for (auto& sp : S->slots) free_slot(S, *sp);
+  for (auto& sp : S->pslots) free_pslot(*sp);
   for (auto& kv : S->reqs) delete kv.second;
   delete S;
 }

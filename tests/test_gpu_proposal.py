@@ -659,7 +659,8 @@ def test_proposal_server_results_equal_the_call_alone(ctx):
     g = np.random.default_rng(7)
     reqs = [query_set(int(g.integers(1, 60)), 12, seed=100 + i, lo=0, hi=16) for i in range(16)]
     alone = [m.query(d, q.codes, q.offsets, C=32, k=7) for q in reqs]
-    with nw.Server(d, k=7, max_batch_queries=160, proposal=(m, 32)) as srv:
+    # one slot: requests that arrive while it runs share the next batch
+    with nw.Server(d, k=7, max_batch_queries=160, max_inflight=1, proposal=(m, 32)) as srv:
         ids = [srv.submit(q.codes, q.offsets) for q in reqs]
         shared = 0
         for rid, (wi, ws) in zip(ids, alone):
@@ -667,6 +668,26 @@ def test_proposal_server_results_equal_the_call_alone(ctx):
             assert np.array_equal(idx, wi) and np.array_equal(sc, ws)
             shared += info["batch_requests"] > 1
         assert shared > 0  # some batches carried several requests
+
+
+def test_proposal_server_batches_overlap_on_the_device(ctx):
+    """Requests submitted back to back, each filling a batch, run on several
+    slots at once (a batch starts while others are on the device), and each
+    result equals the proposal query of its words alone."""
+    w = synth.exhaustive_words(100_000)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, synth.PAPER_SCORING)
+    m = nw.Model(ctx, 40, seed=3)
+    m.train(d, steps=100, batch_pairs=2048, lr=2e-3, seed=4)
+    pool = synth.serving_queries(12_000)
+    reqs = [pool.subset(np.arange(i * 2000, (i + 1) * 2000)) for i in range(6)]
+    alone = [m.query(d, q.codes, q.offsets, C=128, k=10) for q in reqs]
+    with nw.Server(d, k=10, max_batch_queries=2000, max_inflight=3, proposal=(m, 128)) as srv:
+        ids = [srv.submit(q.codes, q.offsets) for q in reqs]
+        out = [srv.wait(i) for i in ids]
+    assert max(info["inflight_at_start"] for _, _, info in out) >= 1
+    for (idx, sc, info), (wi, ws) in zip(out, alone):
+        assert info["batch_requests"] == 1
+        assert np.array_equal(idx, wi) and np.array_equal(sc, ws)
 
 
 def test_proposal_server_refusals(ctx):
