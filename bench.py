@@ -7,14 +7,18 @@ frequency rank): ingest and length bucketing on the device, every one of the
 179,999,700,000 upper-triangle pairs scored by the DPX alignment kernel, the
 on-device per-word top-10 and score histogram, list finalisation.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sharded]
 
 Prints one JSON line (rank 0).  `value` is pairs/s with the words already in
 HBM; `e2e` is the same metric through the C ABI with host buffers (the H2D copy
 of the words and the D2H copy of lists and histogram inside the timed region).
-With N > 1 ranks every rank scores its own replica of the workload (the pairs
-are independent; no collective is on the data path), so `value` counts the
-pairs of all ranks over the slowest rank's time.
+With N > 1 ranks every rank scores its own replica of the workload by default
+(the pairs are independent; no collective is on the data path), so `value`
+counts the pairs of all ranks over the slowest rank's time ("scaling": "weak").
+With --sharded the ranks split one workload's pairs (nw_all_pairs_topk_shard)
+and exchange the partial lists on the device (NCCL all-gather, merge kernel,
+histogram all-reduce): `value` is that workload's pairs over the slowest
+rank's time ("scaling": "strong").
 """
 from __future__ import annotations
 
@@ -68,7 +72,7 @@ def tensor_roofline(flops: float, ms: float, peaks_path: str = os.path.join(ROOT
             "peak_basis": basis}
 
 
-def workload_config(n, w, info):
+def workload_config(n, w, info, sharded=False):
     return {
         "workload": f"exhaustive all-pairs NW, {n:,} synthetic words (lengths round(N(8,3)) on [1,25], "
                     f"40 codes Zipf(1.1)), scoring (+1,-1,-1), per-word top-{K_NEIGHBOURS} + score histogram",
@@ -78,7 +82,9 @@ def workload_config(n, w, info):
         "cells_per_step": int(info["cells"]),
         "max_len": int(info["max_len"]),
         "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); inputs 7 MB < L2",
-        "parallelism": "replicas (one independent workload per rank)",
+        "parallelism": ("shards (each rank scores 1/N of the pairs; NCCL all-gather of the partial lists, "
+                        "merge on the device, histogram all-reduce)" if sharded
+                        else "replicas (one independent workload per rank)"),
     }
 
 
@@ -221,10 +227,23 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     ctx.set_profiling(True)
 
+    sharded = args.sharded
+    if sharded:
+        from paper_2509_01654_gb300 import dist as nwdist
+        part_idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+        part_score = torch.empty((n, k), dtype=torch.int16, device=dev)
+
     def step_device():
         d = ctx.load_dictionary(codes_d, offs_d, 40, SCORING)
-        d.all_pairs_topk(k, nbr_idx=idx_d, nbr_score=score_d, hist=hist_d)
-        prof = ctx.last_profile()
+        if sharded:  # this rank's shard of the pairs, then the exchange on the device
+            d.all_pairs_topk(k, nbr_idx=part_idx, nbr_score=part_score, hist=hist_d, shard=(rank, world))
+            prof = ctx.last_profile()
+            mi, ms = nwdist.exchange(part_idx, part_score, k, hist=hist_d, ctx=ctx)
+            idx_d.copy_(mi)
+            score_d.copy_(ms)
+        else:
+            d.all_pairs_topk(k, nbr_idx=idx_d, nbr_score=score_d, hist=hist_d)
+            prof = ctx.last_profile()
         d.free()
         return prof
 
@@ -238,6 +257,15 @@ def run_ours(args, rank, world, local_rank):
     idx_np, score_np, hist_np = idx_h.numpy().view(np.uint32), score_h.numpy(), hist_h.numpy()
 
     def step_e2e():
+        if sharded:  # inputs from pinned host memory, the merged lists back to the host
+            codes_d.copy_(codes_h, non_blocking=True)
+            offs_d.copy_(offs_h, non_blocking=True)
+            step_device()
+            idx_h.copy_(idx_d, non_blocking=True)
+            score_h.copy_(score_d, non_blocking=True)
+            hist_h.copy_(hist_d, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+            return
         d = ctx.load_dictionary(codes_np, offs_np, 40, SCORING)
         d.all_pairs_topk(k, nbr_idx=idx_np, nbr_score=score_np, hist=hist_np)
         d.free()
@@ -262,7 +290,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         times.append(e0.elapsed_time(e1))
         dp_ms.append(prof["dp_ms"])
-        launches += 4 + prof["launches"]  # 4 ingest kernels + alignment launches + finalisation
+        launches += 4 + prof["launches"] + (1 if sharded else 0)  # ingest, alignment, finalisation (+ merge)
     clocks = sampler.stop() if sampler else None
 
     e2e_times = []
@@ -291,12 +319,15 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     pairs, cells = info["pairs"], info["cells"]
-    value = world * pairs * args.steps / (total_ms / 1e3)
-    e2e_value = world * pairs * len(e2e_times) / (total_e2e / 1e3)
+    # replicas: every rank does the whole workload; shards: the ranks share one
+    copies = 1 if sharded else world
+    value = copies * pairs * args.steps / (total_ms / 1e3)
+    e2e_value = copies * pairs * len(e2e_times) / (total_e2e / 1e3)
 
     # roofline of the alignment kernel: algorithmic cells over its launches' event time
+    # (a shard holds 1/world of the cells: the planner cuts each launch into equal task ranges)
     dp_avg_ms = statistics.mean(dp_ms)
-    achieved = cells / (dp_avg_ms / 1e3) / 1e9
+    achieved = (cells / world if sharded else cells) / (dp_avg_ms / 1e3) / 1e9
     c_min = 3.0  # packed instructions per two cells in the fewest-instruction cell update
     peak = 2.0 * rates["viaddmax_s16x2"] / c_min / 1e9
     sha = kernel_sha()
@@ -395,9 +426,9 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
-        "config": workload_config(n, w, info),
-        "gcups": world * cells * args.steps / (total_ms / 1e3) / 1e9,
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+        "config": workload_config(n, w, info, sharded),
+        "gcups": copies * cells * args.steps / (total_ms / 1e3) / 1e9,
         "dp_kernel_ms_per_step": dp_avg_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GCUPS",
                      "frac": achieved / peak, "traffic": traffic,
@@ -637,6 +668,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=600_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sharded", action="store_true",
+                    help="split one workload's pairs across the ranks (strong scaling) instead of running a replica "
+                         "per rank; the exchange (all-gather, device merge, histogram all-reduce) runs even on one GPU")
     ap.add_argument("--serving-requests", type=int, default=150,
                     help="requests of the query-server load (0 skips it)")
     ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrivals per second")
@@ -660,15 +694,18 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
-    if world > 1:
+    use_pg = world > 1 or args.sharded  # a sharded run exchanges over NCCL even on one rank
+    if use_pg:
         import torch
         import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29531")
         torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local_rank))
     try:
         run_ours(args, rank, world, local_rank)
     finally:
-        if world > 1:
+        if use_pg:
             import torch.distributed as dist
             dist.destroy_process_group()
 

@@ -210,9 +210,19 @@ nw_status nw_all_pairs_topk_shard(nw_dict *dict, uint32_t shard, uint32_t nshard
  * ranked as above, missing entries UINT32_MAX / INT16_MIN) into the k best of
  * their union per word, in the same order.  Entries with the same index in
  * several parts must carry the same score; they are kept once.  Host
- * pointers; no GPU is used. */
+ * pointers; no GPU is used.  At most 64 parts. */
 nw_status nw_topk_merge(uint32_t n, uint32_t k, uint32_t nparts, const uint32_t *const *idx_parts,
                         const int16_t *const *score_parts, uint32_t *idx_out, int16_t *score_out);
+
+/* The same merge on the context's device, for the exchange step of a sharded
+ * run after an all-gather: idx_parts / score_parts hold the nparts partial
+ * lists one after another (part p of word w at p*n*k + w*k; each list ranked,
+ * missing entries UINT32_MAX / INT16_MIN at its end), device pointers; the
+ * merged lists go to idx_out / score_out (device, n*k).  Every word is merged
+ * by the same k-way merge as nw_topk_merge.  1 <= nparts <= 64; NW_EINVAL
+ * otherwise.  Synchronous on the context's stream. */
+nw_status nw_topk_merge_device(nw_ctx *ctx, uint32_t n, uint32_t k, uint32_t nparts, const uint32_t *idx_parts,
+                               const int16_t *score_parts, uint32_t *idx_out, int16_t *score_out);
 
 /* Scores m explicit pairs (i[p], j[p]) of dictionary words (original indices,
  * i == j allowed) into out[p] (int16).  Each score is Algorithm 1's

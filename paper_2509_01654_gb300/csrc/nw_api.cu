@@ -333,34 +333,32 @@ nw_status nw_all_pairs_topk_shard(nw_dict* d, uint32_t shard, uint32_t nshards, 
 nw_status nw_topk_merge(uint32_t n, uint32_t k, uint32_t nparts, const uint32_t* const* idx_parts,
                         const int16_t* const* score_parts, uint32_t* idx_out, int16_t* score_out) {
   if (k == 0 || !idx_out || !score_out || (nparts && (!idx_parts || !score_parts))) return NW_EINVAL;
+  if (nparts > kMaxMergeParts) return NW_EINVAL;
   for (uint32_t p = 0; p < nparts; ++p)
     if (!idx_parts[p] || !score_parts[p]) return NW_EINVAL;
-  std::vector<std::pair<int32_t, uint32_t>> cand;
-  cand.reserve((size_t)nparts * k);
   for (uint32_t w = 0; w < n; ++w) {
-    cand.clear();
-    for (uint32_t p = 0; p < nparts; ++p) {
-      for (uint32_t r = 0; r < k; ++r) {
-        const uint32_t j = idx_parts[p][(size_t)w * k + r];
-        if (j == 0xffffffffu) continue;
-        cand.emplace_back(score_parts[p][(size_t)w * k + r], j);
-      }
-    }
-    std::sort(cand.begin(), cand.end(), [](const std::pair<int32_t, uint32_t>& x, const std::pair<int32_t, uint32_t>& y) {
-      return x.first != y.first ? x.first > y.first : x.second < y.second;
-    });
-    uint32_t r = 0;
-    for (size_t q = 0; q < cand.size() && r < k; ++q) {
-      if (q > 0 && cand[q].second == cand[q - 1].second) continue;  // same neighbour from two parts
-      idx_out[(size_t)w * k + r] = cand[q].second;
-      score_out[(size_t)w * k + r] = (int16_t)cand[q].first;
-      ++r;
-    }
-    for (; r < k; ++r) {
-      idx_out[(size_t)w * k + r] = 0xffffffffu;
-      score_out[(size_t)w * k + r] = INT16_MIN;
-    }
+    const size_t row = (size_t)w * k;
+    merge_ranked_row(
+        nparts, k,
+        [&](uint32_t p, uint32_t r, uint32_t& j, int32_t& s) {
+          j = idx_parts[p][row + r];
+          s = score_parts[p][row + r];
+        },
+        idx_out + row, score_out + row);
   }
+  return NW_OK;
+}
+
+nw_status nw_topk_merge_device(nw_ctx* c, uint32_t n, uint32_t k, uint32_t nparts, const uint32_t* idx_parts,
+                               const int16_t* score_parts, uint32_t* idx_out, int16_t* score_out) {
+  NW_ENTER(c);
+  if (k == 0 || k > NW_MAX_K) return set_err(c, NW_EINVAL, "k must be in [1, %d]", NW_MAX_K);
+  if (nparts == 0 || nparts > kMaxMergeParts)
+    return set_err(c, NW_EINVAL, "nparts must be in [1, %u]", kMaxMergeParts);
+  if (n == 0) return NW_OK;
+  if (!idx_parts || !score_parts || !idx_out || !score_out) return set_err(c, NW_EINVAL, "null pointer argument");
+  NW_CK(launch_topk_merge(n, k, nparts, idx_parts, score_parts, idx_out, score_out, c->stream));
+  NW_CK(cudaStreamSynchronize(c->stream));
   return NW_OK;
 }
 

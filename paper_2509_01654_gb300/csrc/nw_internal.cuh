@@ -128,6 +128,48 @@ __host__ __device__ __forceinline__ bool pair_valid(const TaskGeom& g, uint32_t 
   return b < g.bend && (!g.tri || a < b);
 }
 
+// The k best distinct neighbours of one word from nparts ranked lists (each
+// sorted by score descending, then index ascending, UINT32_MAX entries
+// ending it): a k-way merge.  at(p, r) gives entry r of list p as
+// (index, score); an index met in two lists carries the same score there and
+// is kept once (the two copies are adjacent in the merged order).
+constexpr uint32_t kMaxMergeParts = 64;
+template <class At>
+__host__ __device__ inline void merge_ranked_row(uint32_t nparts, uint32_t k, At at, uint32_t* out_idx,
+                                                 int16_t* out_score) {
+  uint32_t pos[kMaxMergeParts];
+  for (uint32_t p = 0; p < nparts; ++p) pos[p] = 0;
+  uint32_t r = 0, last = 0xffffffffu;
+  while (r < k) {
+    int best = -1;
+    int32_t bs = 0;
+    uint32_t bi = 0;
+    for (uint32_t p = 0; p < nparts; ++p) {
+      if (pos[p] >= k) continue;
+      uint32_t j;
+      int32_t s;
+      at(p, pos[p], j, s);
+      if (j == 0xffffffffu) continue;
+      if (best < 0 || s > bs || (s == bs && j < bi)) {
+        best = (int)p;
+        bs = s;
+        bi = j;
+      }
+    }
+    if (best < 0) break;
+    ++pos[best];
+    if (bi == last) continue;  // the same neighbour from two lists
+    out_idx[r] = bi;
+    out_score[r] = (int16_t)bs;
+    last = bi;
+    ++r;
+  }
+  for (; r < k; ++r) {
+    out_idx[r] = 0xffffffffu;
+    out_score[r] = (int16_t)-32768;
+  }
+}
+
 enum { kModeMatrix = 0, kModeLists = 1 };
 enum { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2, kHistLane = 3 };
 

@@ -287,4 +287,27 @@ cudaError_t launch_rate(int op, int blocks, int iters, const uint32_t* in, uint3
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void topk_merge_kernel(uint32_t n, uint32_t k, uint32_t nparts, const uint32_t* __restrict__ idx_parts,
+                                  const int16_t* __restrict__ score_parts, uint32_t* __restrict__ idx_out,
+                                  int16_t* __restrict__ score_out) {
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  const size_t row = (size_t)w * k, part = (size_t)n * k;
+  merge_ranked_row(
+      nparts, k,
+      [&](uint32_t p, uint32_t r, uint32_t& j, int32_t& s) {
+        j = __ldg(idx_parts + p * part + row + r);
+        s = __ldg(score_parts + p * part + row + r);
+      },
+      idx_out + row, score_out + row);
+}
+}  // namespace
+
+cudaError_t launch_topk_merge(uint32_t n, uint32_t k, uint32_t nparts, const uint32_t* idx_parts,
+                              const int16_t* score_parts, uint32_t* idx_out, int16_t* score_out, cudaStream_t s) {
+  topk_merge_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, k, nparts, idx_parts, score_parts, idx_out, score_out);
+  return cudaGetLastError();
+}
+
 }  // namespace nw

@@ -36,6 +36,11 @@ cudaError_t launch_finalize(const uint32_t* slots, uint32_t nlists, uint32_t k, 
                             int16_t* out_score, cudaStream_t s, const int16_t* norm_frac = nullptr,
                             const uint8_t* slen = nullptr, const uint32_t* rank = nullptr);
 
+// per word, the k best distinct neighbours of nparts ranked lists stored one
+// after another (part p of word w at p * n * k + w * k), one thread per word
+cudaError_t launch_topk_merge(uint32_t n, uint32_t k, uint32_t nparts, const uint32_t* idx_parts,
+                              const int16_t* score_parts, uint32_t* idx_out, int16_t* score_out, cudaStream_t s);
+
 // explicit pairs of one encoded set
 struct PairsParams {
   const uint32_t* pi;

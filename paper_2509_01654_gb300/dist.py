@@ -5,8 +5,12 @@ each rank scores its shard and holds, per word, its k best neighbours among that
 shard's pairs plus that shard's score histogram.  The full result is the
 k best of the union of all ranks' lists (``nw_topk_merge``, associative and
 order-independent because neighbour keys are totally ordered) and the sum of
-the histograms.  This module moves the partial results with torch.distributed
-(NCCL between GPUs, gloo on CPU) and merges them on the host.  The same
+the histograms.  This module moves the partial results with torch.distributed:
+``exchange`` gathers every rank's lists into one contiguous tensor and merges
+them where they live (CUDA tensors over NCCL: on the device by
+``nw_topk_merge_device``; CPU tensors over gloo: on the host by
+``nw_topk_merge``, the same per-word merge) and sums the histograms;
+``gather_merge_topk`` is the older host-side form.  The same
 shards make a long exhaustive run resumable: ``topk_with_checkpoints`` saves
 each finished shard and, after an interruption, scores only the missing ones.
 """
@@ -40,6 +44,34 @@ def gather_merge_topk(idx, score, k: int, group=None):
     dist.all_gather(gs, ts, group=group)
     parts = [(a.cpu().numpy().view(np.uint32), b.cpu().numpy().astype(np.int16)) for a, b in zip(gi, gs)]
     return nw.topk_merge(parts, k)
+
+
+def exchange(idx, score, k: int, hist=None, ctx=None, group=None):
+    """The exchange step of a sharded run.  idx (int32 view of the uint32
+    indices) and score (int16) are this rank's (n, k) partial lists as torch
+    tensors, CUDA (NCCL; ctx: the library context of their device) or CPU
+    (gloo); hist (int64, optional) is this rank's histogram and is summed in
+    place.  Returns the merged (idx, score) lists, on every rank, on the same
+    device as the inputs."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    n = int(idx.shape[0])
+    # outputs concatenated along the first dimension (rank r's rows at r * n)
+    gi = torch.empty((world * n, k), dtype=torch.int32, device=idx.device)
+    dist.all_gather_into_tensor(gi, idx.contiguous(), group=group)
+    # int16 scores travel as raw bytes: the collectives have no 16-bit integer type
+    gb = torch.empty((world * n, 2 * k), dtype=torch.uint8, device=score.device)
+    dist.all_gather_into_tensor(gb, score.contiguous().view(torch.uint8), group=group)
+    gi = gi.view(world, n, k)
+    gs = gb.view(torch.int16).view(world, n, k)
+    if hist is not None:
+        dist.all_reduce(hist, op=dist.ReduceOp.SUM, group=group)
+    if idx.is_cuda:
+        return nw.topk_merge_device(ctx, gi, gs, k)
+    mi, ms = nw.topk_merge([(gi[r].numpy().view(np.uint32), gs[r].numpy()) for r in range(world)], k)
+    return torch.from_numpy(mi.view(np.int32)), torch.from_numpy(ms)
 
 
 def allreduce_histogram(hist, group=None):

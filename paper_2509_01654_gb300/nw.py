@@ -30,7 +30,8 @@ MISSING_SCORE = -32768
 EXPORTED = [
     "nw_create", "nw_destroy", "nw_last_error", "nw_set_profiling", "nw_last_profile",
     "nw_load_dictionary", "nw_dict_info_get", "nw_dict_free", "nw_all_pairs_matrix",
-    "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_score_pairs", "nw_query",
+    "nw_all_pairs_topk", "nw_all_pairs_topk_shard", "nw_topk_merge", "nw_topk_merge_device", "nw_score_pairs",
+    "nw_query",
     "nw_measure_int_rates", "nw_debug_enumerate_pairs", "nw_debug_enumerate_query_pairs", "nw_debug_fail_alloc",
     "nw_debug_set_bounds",
     "nw_all_pairs_topk_noalloc",
@@ -145,6 +146,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_all_pairs_topk.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_all_pairs_topk_shard.argtypes = [vp, u32, u32, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_topk_merge.argtypes = [u32, u32, u32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
+    L.nw_topk_merge_device.argtypes = [vp, u32, u32, u32, vp, vp, vp, vp]
     L.nw_score_pairs.argtypes = [vp, vp, vp, sz, vp, u32]
     L.nw_query.argtypes = [vp, vp, vp, u32, u32, vp, vp, u32]
     L.nw_measure_int_rates.argtypes = [vp, ctypes.c_double, ctypes.POINTER(IntRates)]
@@ -456,6 +458,20 @@ def topk_merge(parts, k: int):
                          ctypes.c_void_p(os_.ctypes.data))
     if st != NW_OK:
         raise NwError(st, "nw_topk_merge failed")
+    return oi, os_
+
+
+def topk_merge_device(ctx: "Context", idx_parts, score_parts, k: int):
+    """nw_topk_merge_device: idx_parts / score_parts are CUDA tensors of shape
+    (nparts, n, k) (int32 / int16); returns the merged (n, k) CUDA tensors."""
+    import torch
+    nparts, n = int(idx_parts.shape[0]), int(idx_parts.shape[1])
+    idx_parts = idx_parts.contiguous()
+    score_parts = score_parts.contiguous()
+    oi = torch.empty((n, k), dtype=torch.int32, device=idx_parts.device)
+    os_ = torch.empty((n, k), dtype=torch.int16, device=idx_parts.device)
+    _check(ctx.handle, load_library().nw_topk_merge_device(ctx.handle, n, k, nparts, idx_parts.data_ptr(),
+                                                           score_parts.data_ptr(), oi.data_ptr(), os_.data_ptr()))
     return oi, os_
 
 

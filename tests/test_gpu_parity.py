@@ -208,6 +208,59 @@ def test_shards_merge_to_full_result(ctx, oracle_mod, G):
     assert np.array_equal(hsum, full[2])
 
 
+@pytest.mark.parametrize("G", [1, 3, 8])
+def test_shards_merge_on_the_device(ctx, G):
+    """Shards scored into device buffers, stacked as an all-gather would
+    leave them, and merged by nw_topk_merge_device give the one-call lists;
+    the host merge of the same parts agrees."""
+    import torch
+    w = synth.make_words(3000, 40, 1.1, 8.0, 3.0, 1, 25, seed=9)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    k = 10
+    full_i, full_s, full_h, _ = d.all_pairs_topk(k)
+    gi = torch.empty((G, w.n, k), dtype=torch.int32, device="cuda")
+    gs = torch.empty((G, w.n, k), dtype=torch.int16, device="cuda")
+    hs = torch.zeros(d.info()["nbins"], dtype=torch.int64, device="cuda")
+    for g in range(G):
+        h = torch.empty_like(hs)
+        d.all_pairs_topk(k, nbr_idx=gi[g], nbr_score=gs[g], hist=h, shard=(g, G))
+        hs += h
+    mi, ms = nw.topk_merge_device(ctx, gi, gs, k)
+    assert np.array_equal(mi.cpu().numpy().view(np.uint32), full_i)
+    assert np.array_equal(ms.cpu().numpy(), full_s)
+    assert np.array_equal(hs.cpu().numpy(), full_h)
+    hi, hsc = nw.topk_merge([(gi[g].cpu().numpy().view(np.uint32), gs[g].cpu().numpy()) for g in range(G)], k)
+    assert np.array_equal(hi, full_i) and np.array_equal(hsc, full_s)
+
+
+def test_exchange_over_nccl_on_one_rank(ctx):
+    """dist.exchange over a one-rank NCCL group: the gather, the raw-byte
+    score transfer and the device merge leave the lists unchanged."""
+    import os
+    import torch
+    import torch.distributed as tdist
+    from paper_2509_01654_gb300 import dist as nwdist
+    w = synth.make_words(1500, 40, 1.1, 8.0, 3.0, 1, 25, seed=10)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    k = 10
+    full_i, full_s, full_h, _ = d.all_pairs_topk(k)
+    ti = torch.empty((w.n, k), dtype=torch.int32, device="cuda")
+    ts = torch.empty((w.n, k), dtype=torch.int16, device="cuda")
+    th = torch.empty(d.info()["nbins"], dtype=torch.int64, device="cuda")
+    d.all_pairs_topk(k, nbr_idx=ti, nbr_score=ts, hist=th, shard=(0, 1))
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ.setdefault("MASTER_PORT", "29561")
+    tdist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        mi, ms = nwdist.exchange(ti, ts, k, hist=th, ctx=ctx)
+        torch.cuda.synchronize()
+    finally:
+        tdist.destroy_process_group()
+    assert np.array_equal(mi.cpu().numpy().view(np.uint32), full_i)
+    assert np.array_equal(ms.cpu().numpy(), full_s)
+    assert np.array_equal(th.cpu().numpy(), full_h)
+
+
 def test_interrupted_run_resumes_from_checkpoints(ctx, oracle_mod, tmp_path):
     # a run that stops after its third shard (an exception raised on the host
     # between shards) resumes from the saved shards and scores only the rest

@@ -44,7 +44,7 @@ def partial_lists(n, a, b, s, k):
     return idx, out
 
 
-def worker(rank, world, port, n, seed, q):
+def worker(rank, world, port, n, seed, q, mode="host"):
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import oracle
@@ -59,8 +59,16 @@ def worker(rank, world, port, n, seed, q):
         idx, score = partial_lists(w.n, a, b, s, K)
         lo, nb = -40, 80
         hist = np.bincount(s - lo, minlength=nb).astype(np.int64)
-        mi, ms = nwdist.gather_merge_topk(idx, score, K)
-        mh = nwdist.allreduce_histogram(hist)
+        if mode == "exchange":
+            # the tensor exchange (all_gather_into_tensor of the lists, scores
+            # as raw bytes, merge where the tensors live, in-place all_reduce)
+            th = torch.from_numpy(hist.copy())
+            ti, ts = nwdist.exchange(torch.from_numpy(idx.view(np.int32).copy()), torch.from_numpy(score.copy()), K,
+                                     hist=th)
+            mi, ms, mh = ti.numpy().view(np.uint32), ts.numpy(), th.numpy()
+        else:
+            mi, ms = nwdist.gather_merge_topk(idx, score, K)
+            mh = nwdist.allreduce_histogram(hist)
         npairs = torch.tensor([a.size], dtype=torch.int64)
         dist.all_reduce(npairs)
         if rank == 0:
@@ -77,14 +85,14 @@ def worker(rank, world, port, n, seed, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_sharded_lists_merge_across_ranks(world):
+@pytest.mark.parametrize("world,mode", [(2, "host"), (3, "host"), (2, "exchange"), (3, "exchange")])
+def test_sharded_lists_merge_across_ranks(world, mode):
     from paper_2509_01654_gb300 import build
     build.build()  # the planner and merge are host functions of libnw
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = free_port()
-    procs = [ctx.Process(target=worker, args=(r, world, port, 240, 17 + world, q)) for r in range(world)]
+    procs = [ctx.Process(target=worker, args=(r, world, port, 240, 17 + world, q, mode)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
