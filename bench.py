@@ -564,6 +564,12 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
     train_s = time.perf_counter() - t0
     # the proposal alone, then with the exhaustive path for long words
     res_proposal_only = {"256": evaluate(model, 256, max(2, args.steps))}
+    # the same stages with the candidate sweep in dictionary order (identical lists)
+    model.set_sweep_order(False)
+    dict_order = evaluate(model, 256, max(2, args.steps))
+    model.set_sweep_order(True)
+    ablation["dictionary_order_C256"] = {"ms": dict_order["ms"],
+                                         "recall_at_10_tie_aware": dict_order["recall_at_10_tie_aware"]}
     model.set_exact_length(args.exact_length)
     res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (256, 384, 512)}
     model.set_exact_length(args.query_exact_length)

@@ -108,13 +108,19 @@ nw_status nw_model_train(nw_model *model, nw_dict *dict, const nw_train_config *
 nw_status nw_quantize_embeddings(nw_ctx *ctx, const float *E, uint32_t n, int8_t *q, int32_t *bias,
                                  float *scale, uint32_t flags);
 
+/* nw_dot_topk flag: sweep the rows in a locality order (sorted by their
+ * first two principal components, so that a row's best columns tend to come
+ * early and its threshold rises sooner).  Changes the time, never the
+ * result.  Without it the rows are swept in their given order. */
+#define NW_LOCALITY_ORDER 0x8u
+
 /* For every row i of the n x 64 int8 matrix q, the C other rows j with the
  * largest value q_i . q_j + bias[j] (exact integers; bias may be NULL for
  * 0, |bias| <= 2^23), higher first and lower j first on equal values:
  * idx[i * C + r], val[i * C + r].  Rows with fewer than C others end in
  * (UINT32_MAX, INT32_MIN).  1 <= C <= NW_MAX_CANDIDATES.  The products run
  * on the tensor cores in bf16 with float32 accumulation, which is exact for
- * these integers. */
+ * these integers.  flags: NW_DEVICE_PTRS, NW_LOCALITY_ORDER. */
 nw_status nw_dot_topk(nw_ctx *ctx, const int8_t *q, const int32_t *bias, uint32_t n, uint32_t C, uint32_t *idx,
                       int32_t *val, uint32_t flags);
 
@@ -151,6 +157,17 @@ typedef struct {
  * long queries.  Applies to nw_proposal_topk, nw_proposal_query and the
  * proposal server.  NW_EINVAL for min_len > NW_MAX_WORD_LEN. */
 nw_status nw_proposal_set_exact_length(nw_model *model, uint32_t min_len);
+
+/* The row order of the candidate sweep in nw_proposal_topk: nonzero (the
+ * default) sorts the words by (length, first principal component of their
+ * embeddings in 16 equal-count buckets, second principal component) and
+ * sweeps each row block's column tiles outward from its own, so that a
+ * word's best candidates tend to come first and its threshold rises early;
+ * 0 sweeps the words in dictionary order.  The candidates, and so every
+ * result, are the same either way (ties still go to the lower original
+ * index); only the time of the candidate stage, which includes building the
+ * order, changes. */
+nw_status nw_proposal_set_sweep_order(nw_model *model, int locality);
 
 /* The whole proposal path for `dict`: embed every word, quantise, take C
  * candidates per word by dot product, rescore them exactly and keep the k

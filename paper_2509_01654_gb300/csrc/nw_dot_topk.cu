@@ -104,7 +104,10 @@ constexpr int kOffFin = kOffReq + kCtaRows * 4;
 constexpr int kOffMisc = kOffFin + kCtaRows * 4;       // request masks, done flags, tmem address
 constexpr int kOffBars = kOffMisc + 64;
 constexpr int kNumBars = 2 * kStages + 4 + 1;          // full, empty, acc full x2, acc empty x2, A loaded
-constexpr int kSmemUsed = kOffBars + kNumBars * 8;
+// per epilogue warp: the original ids of the current tile's columns (sweeps
+// over rows in a locality order)
+constexpr int kOffIds = (kOffBars + kNumBars * 8 + 15) / 16 * 16;
+constexpr int kSmemUsed = kOffIds + kEpiWarps * kTileN * 4;
 constexpr int kSmemTotal = kSmemUsed + 1024;           // slack for aligning the base
 static_assert(kSmemTotal <= 227 * 1024, "one CTA per SM");
 // the final pass reuses the stage ring: per warp a histogram and a sort area
@@ -399,6 +402,11 @@ struct DotArgs {
   uint32_t splits, tps;
   uint64_t* buf;   // (nA x splits) x 2 buffers x kCap keys
   uint64_t* part;  // (nA x splits) x C keys when splits > 1
+  // original ids when the rows or columns are stored in another order
+  // (nullptr: position = id): col_ids covers every column tile (tiles x 128
+  // entries) and names the columns in the keys; row_ids places the output rows
+  const uint32_t* col_ids;
+  const uint32_t* row_ids;
   uint32_t* out_idx;
   int32_t* out_val;
   uint32_t* err;
@@ -491,14 +499,24 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   const uint32_t tall = (P.nB + kTileN - 1) / kTileN;
   const uint32_t tlo = kSplit ? min(tall, ys * P.tps) : 0u;
   const uint32_t ntiles = kSplit ? min(tall - tlo, P.tps) : tall;
-  uint32_t start = 0;  // a square sweep starts at the CTA's own diagonal tile
+  // A square sweep starts at the CTA's own diagonal tile and moves outward
+  // in both directions (start, +1, -1, +2, -2, ..., then the longer side
+  // alone): with rows in a locality order the tiles nearest the diagonal hold
+  // most of a row's best columns, so its threshold rises early.
+  uint32_t start = 0;
   if (kSelf) {
     const uint32_t d = row0 / kTileN;
     if (d >= tlo && d < tlo + ntiles) start = d - tlo;
   }
+  const uint32_t side_lo = start, side_hi = ntiles - 1u - start, side = min(side_lo, side_hi);
   auto tile_of = [&](uint32_t u) {
-    uint32_t x = u + start;
-    if (x >= ntiles) x -= ntiles;
+    uint32_t x;
+    if (u <= 2u * side) {
+      const uint32_t k = (u + 1u) >> 1;
+      x = (u & 1u) ? start + k : start - k;
+    } else {
+      x = side_hi > side_lo ? start + (u - side) : start - (u - side);
+    }
     return tlo + x;
   };
   auto row_buf = [&](uint32_t i, uint32_t b) { return P.buf + (((size_t)i * P.splits + ys) * 2 + b) * kCap; };
@@ -632,6 +650,15 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
     const uint32_t bit = 1u << lane;
 
     float* sv = reinterpret_cast<float*>(smem + kOffVals) + r * kValStride;
+    // the original ids of the tile's columns, loaded one tile ahead
+    uint32_t* sid = reinterpret_cast<uint32_t*>(smem + kOffIds) + warp * kTileN;
+    const uint32_t* __restrict__ col_ids = P.col_ids;
+    uint4 idn = make_uint4(0u, 0u, 0u, 0u);
+    if (col_ids && ntiles > 0) {
+      *reinterpret_cast<uint4*>(sid + 4 * lane) = __ldg(reinterpret_cast<const uint4*>(col_ids + (size_t)tile_of(0) * kTileN) + lane);
+      if (ntiles > 1) idn = __ldg(reinterpret_cast<const uint4*>(col_ids + (size_t)tile_of(1) * kTileN) + lane);
+      __syncwarp();
+    }
     // values of one 32-column chunk (column colbase + k in v[k]) that reach
     // the threshold are appended.  The chunk's maximum is tested first; a
     // thread whose maximum passes builds its hit mask with two instructions
@@ -639,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
     // so the difference has the exact sign, and it is +0 when they are equal)
     // and reads the hits back from shared memory, so the work beyond the test
     // follows the number of hits.
-    auto process = [&](const uint32_t (&v)[32], uint32_t colbase) {
+    auto process = [&](const uint32_t (&v)[32], uint32_t colbase, uint32_t cofs) {
       float m[11];
 #pragma unroll
       for (int x = 0; x < 10; ++x)
@@ -671,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
           do {
             const int k = __ffs(hit) - 1;
             hit &= hit - 1u;
-            rb[cnt++] = make_key(__float2int_rn(sv[k]), colbase + (uint32_t)k);
+            rb[cnt++] = make_key(__float2int_rn(sv[k]), col_ids ? sid[cofs + (uint32_t)k] : colbase + (uint32_t)k);
           } while (hit);
         }
       }
@@ -698,7 +725,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
 #pragma unroll
       for (int c = 0; c < kChunks; c += 2) {
         tmem_ld32(tcol + 32u * (uint32_t)(c + 1), vb);
-        process(va, col0 + 32u * (uint32_t)c);
+        process(va, col0 + 32u * (uint32_t)c, 32u * (uint32_t)c);
         tmem_wait(vb);
         if (c + 2 < kChunks) {
           tmem_ld32(tcol + 32u * (uint32_t)(c + 2), va);
@@ -707,8 +734,14 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
           __syncwarp();
           if (lane == 0) mbar_arrive(acce_bar(b));
         }
-        process(vb, col0 + 32u * (uint32_t)(c + 1));
+        process(vb, col0 + 32u * (uint32_t)(c + 1), 32u * (uint32_t)(c + 1));
         if (c + 2 < kChunks) tmem_wait(va);
+      }
+      if (col_ids && u + 1u < ntiles) {  // the next tile's ids, once every hit of this one is appended
+        __syncwarp();
+        *reinterpret_cast<uint4*>(sid + 4 * lane) = idn;
+        __syncwarp();
+        if (u + 2u < ntiles) idn = __ldg(reinterpret_cast<const uint4*>(col_ids + (size_t)tile_of(u + 2u) * kTileN) + lane);
       }
       // a full buffer goes to the compactor, unless it still holds the other one
       if (live && cnt > trigger) {
@@ -855,10 +888,11 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       uint64_t* dst = P.part + ((size_t)i * P.splits + ys) * C;
       for (uint32_t x = lane; x < C; x += 32) dst[x] = (int)x < kept ? sort[x] : 0ull;
     } else {
+      const size_t orow = P.row_ids ? P.row_ids[i] : i;
       for (uint32_t x = lane; x < C; x += 32) {
         const bool have = (int)x < kept;
-        P.out_idx[(size_t)i * C + x] = have ? key_idx(sort[x]) : 0xffffffffu;
-        P.out_val[(size_t)i * C + x] = have ? key_val(sort[x]) : INT32_MIN;
+        P.out_idx[orow * C + x] = have ? key_idx(sort[x]) : 0xffffffffu;
+        P.out_val[orow * C + x] = have ? key_val(sort[x]) : INT32_MIN;
       }
     }
     __syncwarp();
@@ -870,7 +904,8 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
 constexpr int kMergeWarps = 8;
 __global__ void __launch_bounds__(kMergeWarps * 32)
     merge_splits_kernel(const uint64_t* __restrict__ part, uint32_t nA, uint32_t S, uint32_t C,
-                        uint32_t* __restrict__ out_idx, int32_t* __restrict__ out_val) {
+                        const uint32_t* __restrict__ row_ids, uint32_t* __restrict__ out_idx,
+                        int32_t* __restrict__ out_val) {
   __shared__ unsigned hist[kMergeWarps][256];
   __shared__ uint64_t keep[kMergeWarps][kSel];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -886,10 +921,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
   for (int x = kept + lane; x < size; x += 32) keep[warp][x] = 0ull;
   __syncwarp();
   warp_bitonic_desc(keep[warp], size, lane);
+  const size_t orow = row_ids ? row_ids[i] : i;
   for (uint32_t x = lane; x < C; x += 32) {
     const bool have = (int)x < kept;
-    out_idx[(size_t)i * C + x] = have ? key_idx(keep[warp][x]) : 0xffffffffu;
-    out_val[(size_t)i * C + x] = have ? key_val(keep[warp][x]) : INT32_MIN;
+    out_idx[orow * C + x] = have ? key_idx(keep[warp][x]) : 0xffffffffu;
+    out_val[orow * C + x] = have ? key_val(keep[warp][x]) : INT32_MIN;
   }
 }
 
@@ -966,6 +1002,236 @@ __global__ void bias_digits_kernel(const int32_t* __restrict__ bias, uint32_t n,
 
 size_t bias_pad(uint32_t n) { return ((size_t)n + kPadRows - 1) / kPadRows * kPadRows; }
 
+// ---- sweep order of the self product (see sweep_order)
+constexpr int kOrdBins = 4096;     // histogram of the first projection
+constexpr int kOrdBuckets = 16;    // equal-count buckets of the first projection
+constexpr int kOrdLevels = 256;    // levels of the second projection
+constexpr int kOrdLens = 64;       // lengths clamp to 63
+constexpr int kOrdKeys = kOrdLens * kOrdBuckets * kOrdLevels;
+constexpr int kMomRows = 8;        // rows staged per step of moments_kernel
+
+// sums over the rows of x and of x x^T, x = a row's 64 values (integers in
+// [-127, 127], so 64-bit integer sums are exact and order-free): mom[0, 64)
+// and mom[64 + 64 k + l].  Thread t owns entries (t / 4, 16 (t % 4) + 0..15).
+__global__ void __launch_bounds__(256) moments_kernel(const __nv_bfloat16* __restrict__ Qb, uint32_t n,
+                                                      unsigned long long* mom) {
+  __shared__ int row[kMomRows][kDim];
+  const int t = threadIdx.x, k = t >> 2, l0 = (t & 3) * 16;
+  long long acc[16], s1 = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = 0;
+  for (uint32_t r0 = blockIdx.x * kMomRows; r0 < n; r0 += gridDim.x * kMomRows) {
+    __syncthreads();
+    for (int x = t; x < kMomRows * kDim; x += 256) {
+      const uint32_t r = r0 + (uint32_t)(x / kDim);
+      const int c = x % kDim;
+      row[x / kDim][c] = r < n ? (int)__bfloat162float(Qb[swz_index(r, c)]) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < kMomRows; ++rr) {
+      const int a = row[rr][k];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] += a * row[rr][l0 + j];
+      s1 += a;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) atomicAdd(&mom[kDim + k * kDim + l0 + j], (unsigned long long)acc[j]);
+  if ((t & 3) == 0) atomicAdd(&mom[k], (unsigned long long)s1);
+}
+
+// One block of 64 threads: the covariance of the rows from their moments and
+// its two leading eigenvectors by power iteration (the second after
+// deflating the first), written to dirs[0, 64) and dirs[64, 128); also resets
+// the projection ranges that project_kernel raises.
+__global__ void __launch_bounds__(kDim) pca_kernel(const unsigned long long* __restrict__ mom, uint32_t n,
+                                                   float* dirs, unsigned* range) {
+  __shared__ float cov[kDim][kDim + 1];
+  __shared__ float v[kDim], w[kDim];
+  const int t = threadIdx.x;
+  const double inv = 1.0 / (double)max(n, 1u);
+  const double mt = (double)(long long)mom[t] * inv;
+  for (int l = 0; l < kDim; ++l)
+    cov[t][l] = (float)((double)(long long)mom[kDim + t * kDim + l] * inv - mt * ((double)(long long)mom[l] * inv));
+  if (t < 4) range[t] = (t & 1) ? 0u : 0xffffffffu;  // min, max, min, max of the ordered float bits
+  for (int e = 0; e < 2; ++e) {
+    v[t] = 1.f + (e ? -0.013f : 0.011f) * (float)t;  // fixed starting vectors
+    __syncthreads();
+    for (int it = 0; it < 256; ++it) {
+      float x = 0.f;
+      for (int l = 0; l < kDim; ++l) x = fmaf(cov[t][l], v[l], x);
+      w[t] = x;
+      __syncthreads();
+      float nn = 0.f;
+      for (int l = 0; l < kDim; ++l) nn = fmaf(w[l], w[l], nn);
+      v[t] = nn > 0.f ? w[t] * rsqrtf(nn) : 0.f;
+      __syncthreads();
+    }
+    dirs[e * kDim + t] = v[t];
+    float x = 0.f;
+    for (int l = 0; l < kDim; ++l) x = fmaf(cov[t][l], v[l], x);
+    w[t] = x;
+    __syncthreads();
+    float lam = 0.f;
+    for (int l = 0; l < kDim; ++l) lam = fmaf(v[l], w[l], lam);
+    for (int l = 0; l < kDim; ++l) cov[t][l] -= lam * v[t] * v[l];
+    __syncthreads();
+  }
+}
+
+// floats as unsigned integers of the same order
+__device__ __forceinline__ unsigned ord_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord_float(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// one thread per row: its projections on the two directions, and their
+// ranges (range[0..3] = min, max of the first, min, max of the second)
+__global__ void __launch_bounds__(256) project_kernel(const __nv_bfloat16* __restrict__ Qb, uint32_t n,
+                                                      const float* __restrict__ dirs, float2* proj,
+                                                      unsigned* range) {
+  __shared__ float d[2 * kDim];
+  if (threadIdx.x < 2 * kDim) d[threadIdx.x] = dirs[threadIdx.x];
+  __syncthreads();
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  float a = 0.f, b = 0.f;
+  if (r < n) {
+    const uint4* row = reinterpret_cast<const uint4*>(Qb + (size_t)r * kDim);
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      const uint4 u = __ldg(row + ch);
+      const int lc = (ch ^ (int)(r & 7u)) * 8;  // stored chunk ch holds values lc .. lc + 7
+      const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float x = __bfloat162float(h[e]);
+        a = fmaf(x, d[lc + e], a);
+        b = fmaf(x, d[kDim + lc + e], b);
+      }
+    }
+    proj[r] = make_float2(a, b);
+  }
+  unsigned mn1 = r < n ? ord_bits(a) : 0xffffffffu, mx1 = r < n ? ord_bits(a) : 0u;
+  unsigned mn2 = r < n ? ord_bits(b) : 0xffffffffu, mx2 = r < n ? ord_bits(b) : 0u;
+  mn1 = __reduce_min_sync(0xffffffffu, mn1);
+  mx1 = __reduce_max_sync(0xffffffffu, mx1);
+  mn2 = __reduce_min_sync(0xffffffffu, mn2);
+  mx2 = __reduce_max_sync(0xffffffffu, mx2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(range + 0, mn1);
+    atomicMax(range + 1, mx1);
+    atomicMin(range + 2, mn2);
+    atomicMax(range + 3, mx2);
+  }
+}
+
+__device__ __forceinline__ int ord_level(float x, float lo, float hi, int levels) {
+  if (!(hi > lo)) return 0;
+  const int v = (int)((x - lo) / (hi - lo) * (float)levels);
+  return min(max(v, 0), levels - 1);
+}
+
+// histogram of the first projection over kOrdBins equal-width bins
+__global__ void __launch_bounds__(256) proj_hist_kernel(const float2* __restrict__ proj, uint32_t n,
+                                                        const unsigned* __restrict__ range, unsigned* hist) {
+  __shared__ unsigned h[kOrdBins];
+  for (int x = threadIdx.x; x < kOrdBins; x += blockDim.x) h[x] = 0u;
+  __syncthreads();
+  const float lo = ord_float(range[0]), hi = ord_float(range[1]);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    atomicAdd(&h[ord_level(proj[r].x, lo, hi, kOrdBins)], 1u);
+  __syncthreads();
+  for (int x = threadIdx.x; x < kOrdBins; x += blockDim.x)
+    if (h[x]) atomicAdd(&hist[x], h[x]);
+}
+
+// one block: an exclusive scan of a[0, m) in place (m a multiple of blockDim.x)
+__device__ void block_exclusive_scan(unsigned* a, int m) {
+  __shared__ unsigned part[1024];
+  const int t = threadIdx.x, per = m / (int)blockDim.x;
+  unsigned sum = 0;
+  for (int j = 0; j < per; ++j) sum += a[t * per + j];
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const unsigned x = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  unsigned run = part[t] - sum;
+  for (int j = 0; j < per; ++j) {
+    const unsigned x = a[t * per + j];
+    a[t * per + j] = run;
+    run += x;
+  }
+}
+
+// one block of 1024: hist[b] becomes the equal-count bucket of bin b (by the
+// rank of the bin's middle row)
+__global__ void __launch_bounds__(1024) proj_buckets_kernel(unsigned* hist, uint32_t n) {
+  __shared__ unsigned cnt[kOrdBins];
+  for (int x = threadIdx.x; x < kOrdBins; x += blockDim.x) cnt[x] = hist[x];
+  __syncthreads();
+  block_exclusive_scan(hist, kOrdBins);
+  __syncthreads();
+  for (int x = threadIdx.x; x < kOrdBins; x += blockDim.x) {
+    const unsigned long long mid = (unsigned long long)hist[x] + cnt[x] / 2u;
+    const unsigned long long bk = mid * kOrdBuckets / max(n, 1u);
+    hist[x] = bk < (unsigned long long)(kOrdBuckets - 1) ? (unsigned)bk : (unsigned)(kOrdBuckets - 1);
+  }
+}
+
+// one thread per row: its sort key and the key's count
+__global__ void __launch_bounds__(256) order_key_kernel(const float2* __restrict__ proj, uint32_t n,
+                                                        const unsigned* __restrict__ range,
+                                                        const unsigned* __restrict__ bucket_of,
+                                                        const uint32_t* __restrict__ rank,
+                                                        const uint8_t* __restrict__ slen, uint32_t* key,
+                                                        unsigned* cnt) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const float2 p = proj[r];
+  const unsigned b = bucket_of[ord_level(p.x, ord_float(range[0]), ord_float(range[1]), kOrdBins)];
+  int lv = ord_level(p.y, ord_float(range[2]), ord_float(range[3]), kOrdLevels);
+  if (b & 1u) lv = kOrdLevels - 1 - lv;
+  const unsigned len = (rank && slen) ? min(63u, (unsigned)slen[rank[r]]) : 0u;
+  const uint32_t k = (len * kOrdBuckets + b) * kOrdLevels + (uint32_t)lv;
+  key[r] = k;
+  atomicAdd(&cnt[k], 1u);
+}
+
+__global__ void __launch_bounds__(1024) key_scan_kernel(unsigned* cnt) { block_exclusive_scan(cnt, kOrdKeys); }
+
+__global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ key, uint32_t n,
+                                                            unsigned* cursor, uint32_t* perm) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) perm[atomicAdd(&cursor[key[r]], 1u)] = r;
+}
+
+// one thread per (position, 16-byte chunk) of the padded rows: row perm[p]
+// moved to position p (its chunks re-permuted for p & 7), and its bias
+__global__ void __launch_bounds__(256) order_gather_kernel(const __nv_bfloat16* __restrict__ Qb,
+                                                           const int32_t* __restrict__ bias, uint32_t n,
+                                                           uint32_t npad, const uint32_t* __restrict__ perm,
+                                                           __nv_bfloat16* Qp, int32_t* bp) {
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (size_t)npad * 8) return;
+  const uint32_t p = (uint32_t)(x >> 3), ch = (uint32_t)(x & 7u);
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (p < n) {
+    const uint32_t r = perm[p];
+    v = __ldg(reinterpret_cast<const uint4*>(Qb + (size_t)r * kDim) + (ch ^ (r & 7u)));
+    if (ch == 0 && bp) bp[p] = bias ? bias[r] : 0;
+  }
+  *(reinterpret_cast<uint4*>(Qp + (size_t)p * kDim) + (ch ^ (p & 7u))) = v;
+}
+
+
 }  // namespace
 
 size_t dot_topk_qb_bytes(uint32_t n) { return bias_pad(n) * kRowBytes; }
@@ -1005,7 +1271,8 @@ uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB) {
 
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* val,
-                          uint32_t* err, cudaStream_t s, DotDebug dbg) {
+                          uint32_t* err, cudaStream_t s, DotDebug dbg, const uint32_t* col_ids,
+                          const uint32_t* row_ids) {
   if (nA == 0) return cudaSuccess;
   const uint32_t S = dot_topk_splits(nA, nB);
   const auto kernel = S > 1 ? (self ? dot_topk_kernel<true, true> : dot_topk_kernel<true, false>)
@@ -1030,18 +1297,22 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
   P.err = err;
   P.wait_cycles = dbg.wait_cycles >= 0 ? dbg.wait_cycles : kWaitCycles;
   P.withhold = dbg.withhold;
+  P.col_ids = col_ids;
+  P.row_ids = row_ids;
   const uint32_t npad = (uint32_t)bias_pad(nB);
   if (npad) bias_digits_kernel<<<(2 * npad + 255) / 256, 256, 0, s>>>(biasB, nB, npad, ext);
   const dim3 grid((nA + kCtaRows - 1) / kCtaRows, S);
   kernel<<<grid, kThreads, kSmemTotal, s>>>(P);
   if (S > 1)
-    merge_splits_kernel<<<(nA + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(P.part, nA, S, C, idx, val);
+    merge_splits_kernel<<<(nA + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(P.part, nA, S, C, row_ids, idx,
+                                                                                         val);
   return cudaGetLastError();
 }
 
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
-                     uint32_t* idx, int32_t* val, uint32_t* err, cudaStream_t s, DotDebug dbg) {
-  return dot_topk_rect(Qb, n, Qb, bias, n, C, true, buf, idx, val, err, s, dbg);
+                     uint32_t* idx, int32_t* val, uint32_t* err, cudaStream_t s, DotDebug dbg,
+                     const uint32_t* ids) {
+  return dot_topk_rect(Qb, n, Qb, bias, n, C, true, buf, idx, val, err, s, dbg, ids, ids);
 }
 
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,
@@ -1054,6 +1325,51 @@ cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t
   }
   quantize_kernel<<<(unsigned)((count + 255) / 256 + (count == 0)), 256, 0, s>>>(E, n, (uint32_t)bias_pad(n),
                                                                                    amax_bits, q, qb, bias, scale);
+  return cudaGetLastError();
+}
+
+// sweep-order scratch: [moments 64 + 64 x 64 x 8 B][directions 128 floats][ranges 4]
+// [p1 histogram / buckets][key counts / cursors][projections n x 8 B][keys n x 4 B]
+namespace {
+constexpr size_t kOrdMomBytes = (kDim + kDim * kDim) * 8;
+constexpr size_t kOrdDirOff = kOrdMomBytes;
+constexpr size_t kOrdRangeOff = kOrdDirOff + 2 * kDim * 4;
+constexpr size_t kOrdHistOff = kOrdRangeOff + 16;
+constexpr size_t kOrdCntOff = kOrdHistOff + kOrdBins * 4;
+constexpr size_t kOrdProjOff = kOrdCntOff + (size_t)kOrdKeys * 4;
+}  // namespace
+
+size_t sweep_perm_entries(uint32_t n) { return bias_pad(n); }
+size_t sweep_order_bytes(uint32_t n) { return kOrdProjOff + (size_t)n * 8 + (size_t)n * 4 + 16; }
+
+cudaError_t sweep_order(const __nv_bfloat16* Qb, const int32_t* bias, const uint32_t* rank, const uint8_t* slen,
+                        uint32_t n, void* scratch, uint32_t* perm, __nv_bfloat16* Qp, int32_t* bp, cudaStream_t s) {
+  const uint32_t npad = (uint32_t)bias_pad(n);
+  char* sc = static_cast<char*>(scratch);
+  auto* mom = reinterpret_cast<unsigned long long*>(sc);
+  auto* dirs = reinterpret_cast<float*>(sc + kOrdDirOff);
+  auto* range = reinterpret_cast<unsigned*>(sc + kOrdRangeOff);
+  auto* hist = reinterpret_cast<unsigned*>(sc + kOrdHistOff);
+  auto* cnt = reinterpret_cast<unsigned*>(sc + kOrdCntOff);
+  auto* proj = reinterpret_cast<float2*>(sc + kOrdProjOff);
+  auto* key = reinterpret_cast<uint32_t*>(sc + kOrdProjOff + (size_t)n * 8);
+  cudaError_t e = cudaMemsetAsync(sc, 0, kOrdProjOff, s);  // moments, histogram, counts
+  if (e == cudaSuccess) e = cudaMemsetAsync(perm, 0xff, sizeof(uint32_t) * npad, s);
+  if (e != cudaSuccess) return e;
+  if (n) {
+    const unsigned rows_grid = std::min<unsigned>(304u, (n + kMomRows - 1) / kMomRows);
+    const unsigned grid = (n + 255) / 256;
+    moments_kernel<<<rows_grid, 256, 0, s>>>(Qb, n, mom);
+    pca_kernel<<<1, kDim, 0, s>>>(mom, n, dirs, range);
+    project_kernel<<<grid, 256, 0, s>>>(Qb, n, dirs, proj, range);
+    proj_hist_kernel<<<std::min(grid, 608u), 256, 0, s>>>(proj, n, range, hist);
+    proj_buckets_kernel<<<1, 1024, 0, s>>>(hist, n);
+    order_key_kernel<<<grid, 256, 0, s>>>(proj, n, range, hist, rank, slen, key, cnt);
+    key_scan_kernel<<<1, 1024, 0, s>>>(cnt);
+    order_scatter_kernel<<<grid, 256, 0, s>>>(key, n, cnt, perm);
+  }
+  if (npad)
+    order_gather_kernel<<<(unsigned)(((size_t)npad * 8 + 255) / 256), 256, 0, s>>>(Qb, bias, n, npad, perm, Qp, bp);
   return cudaGetLastError();
 }
 

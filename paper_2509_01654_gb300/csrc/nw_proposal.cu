@@ -40,6 +40,10 @@ struct nw_model {
   // their codes, offsets and (k + 1)-long exhaustive lists
   uint32_t exact_len = 0;
   DevBuf xcodes, xoffs, xidx, xscore;
+  // the candidate sweep over the rows in a locality order (prop::sweep_order):
+  // the rows and biases in that order, the order, its scratch
+  bool sweep_order = true;
+  DevBuf oQb, obias, operm, oscratch;
 };
 
 namespace {
@@ -102,7 +106,7 @@ void model_free_buffers(nw_model* M) {
                     &M->dYb, &M->dX0, &M->pi, &M->pj, &M->target, &M->score16, &M->Eall, &M->Qb,
                     &M->qbias, &M->topbuf, &M->cand, &M->cand_dot, &M->cand_score, &M->nbr,
                     &M->dQb, &M->dqbias, &M->prep_small, &M->qQb, &M->qcand, &M->qcand_dot, &M->qscore, &M->qbuf,
-                    &M->xcodes, &M->xoffs, &M->xidx, &M->xscore};
+                    &M->xcodes, &M->xoffs, &M->xidx, &M->xscore, &M->oQb, &M->obias, &M->operm, &M->oscratch};
   for (DevBuf* b : bufs) ctx_free(c, *b);
 }
 
@@ -736,6 +740,21 @@ nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, const int32_t* bias, uint32_t 
   }
   NW_TRY(ctx_alloc(c, qb, prop::dot_topk_qb_bytes(n), "bf16 embeddings"));
   NW_TRY(ctx_alloc(c, buf, prop::dot_topk_buffer_bytes(n, C), "candidate buffers"));
+  const bool locality = flags & NW_LOCALITY_ORDER;
+  DevBuf oq, ob, op, osc;
+  struct FreeOrder {
+    nw_ctx* c;
+    DevBuf* b[4];
+    ~FreeOrder() {
+      for (DevBuf* x : b) ctx_free(c, *x);
+    }
+  } fro{c, {&oq, &ob, &op, &osc}};
+  if (locality) {
+    NW_TRY(ctx_alloc(c, oq, prop::dot_topk_qb_bytes(n), "bf16 embeddings in sweep order"));
+    NW_TRY(ctx_alloc(c, ob, sizeof(int32_t) * n, "biases in sweep order"));
+    NW_TRY(ctx_alloc(c, op, sizeof(uint32_t) * prop::sweep_perm_entries(n), "sweep order"));
+    NW_TRY(ctx_alloc(c, osc, prop::sweep_order_bytes(n), "sweep order scratch"));
+  }
   uint32_t* out_i = idx;
   int32_t* out_v = val;
   if (!dev) {
@@ -747,7 +766,15 @@ nw_status nw_dot_topk(nw_ctx* c, const int8_t* q, const int32_t* bias, uint32_t 
   uint32_t* derr = prop::dot_topk_err_word(buf.as<uint64_t>(), n);
   NW_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
   NW_CK(prop::widen(srcq, n, qb.as<__nv_bfloat16>(), s));
-  NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), srcb, n, C, buf.as<uint64_t>(), out_i, out_v, derr, s, dot_debug(c)));
+  if (locality) {
+    NW_CK(prop::sweep_order(qb.as<__nv_bfloat16>(), srcb, nullptr, nullptr, n, osc.p, op.as<uint32_t>(),
+                            oq.as<__nv_bfloat16>(), srcb ? ob.as<int32_t>() : nullptr, s));
+    NW_CK(prop::dot_topk(oq.as<__nv_bfloat16>(), srcb ? ob.as<int32_t>() : nullptr, n, C, buf.as<uint64_t>(), out_i,
+                         out_v, derr, s, dot_debug(c), op.as<uint32_t>()));
+  } else {
+    NW_CK(prop::dot_topk(qb.as<__nv_bfloat16>(), srcb, n, C, buf.as<uint64_t>(), out_i, out_v, derr, s,
+                         dot_debug(c)));
+  }
   NW_TRY(check_device_flags(c, derr));
   if (!dev) {
     NW_TRY(copy_out(c, idx, out_i, outc, false, s));
@@ -1057,6 +1084,7 @@ nw_status model_clone(nw_model* src, nw_ctx* c, nw_model** out) {
     return cuda_fail(c, e, "copying model parameters");
   }
   M->exact_len = src->exact_len;
+  M->sweep_order = src->sweep_order;
   return NW_OK;
 }
 
@@ -1069,6 +1097,12 @@ nw_status nw_proposal_set_exact_length(nw_model* M, uint32_t min_len) {
   if (!M) return NW_EINVAL;
   if (min_len > (uint32_t)kMaxLen) return set_err(M->ctx, NW_EINVAL, "min_len must be at most %d", kMaxLen);
   M->exact_len = min_len;
+  return NW_OK;
+}
+
+nw_status nw_proposal_set_sweep_order(nw_model* M, int locality) {
+  if (!M) return NW_EINVAL;
+  M->sweep_order = locality != 0;
   return NW_OK;
 }
 
@@ -1093,6 +1127,12 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
   NW_TRY(ctx_ensure(c, M->topbuf, prop::dot_topk_buffer_bytes(n, C), "candidate buffers"));
   NW_TRY(ctx_ensure(c, M->cand, sizeof(uint32_t) * outc, "candidate lists"));
   NW_TRY(ctx_ensure(c, M->cand_dot, sizeof(int32_t) * outc, "candidate lists"));
+  if (M->sweep_order) {
+    NW_TRY(ctx_ensure(c, M->oQb, prop::dot_topk_qb_bytes(n), "bf16 embeddings in sweep order"));
+    NW_TRY(ctx_ensure(c, M->obias, sizeof(int32_t) * (size_t)n, "quantised biases in sweep order"));
+    NW_TRY(ctx_ensure(c, M->operm, sizeof(uint32_t) * prop::sweep_perm_entries(n), "sweep order"));
+    NW_TRY(ctx_ensure(c, M->oscratch, prop::sweep_order_bytes(n), "sweep order scratch"));
+  }
   DevBuf oi, os;
   struct Free {
     nw_ctx* c;
@@ -1130,8 +1170,17 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
   NW_CK(prop::quantize(fptr(M->Eall), n, amax_ptr(M), nullptr, M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(),
                        nullptr, s));
   NW_CK(cudaEventRecord(ev[2], s));
-  NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
-                       M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s, dot_debug(c)));
+  if (M->sweep_order) {  // the rows in a locality order; the lists come back in the original rows and ids
+    NW_CK(prop::sweep_order(M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(), d->ws.rank.as<uint32_t>(),
+                            d->ws.slen.as<uint8_t>(), n, M->oscratch.p, M->operm.as<uint32_t>(),
+                            M->oQb.as<__nv_bfloat16>(), M->obias.as<int32_t>(), s));
+    NW_CK(prop::dot_topk(M->oQb.as<__nv_bfloat16>(), M->obias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
+                         M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s, dot_debug(c),
+                         M->operm.as<uint32_t>()));
+  } else {
+    NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
+                         M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s, dot_debug(c)));
+  }
   NW_CK(cudaEventRecord(ev[3], s));
   NW_TRY(rescore_select(c, d, M->cand.as<uint32_t>(), C, k, M->cand_score, out_i, out_s, err_ptr(M), s));
   NW_CK(cudaEventRecord(ev[4], s));

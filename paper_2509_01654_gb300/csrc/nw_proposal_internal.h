@@ -54,14 +54,38 @@ struct DotDebug {
   uint32_t withhold = 0xffffffffu;
 };
 // each row's C best q_i . q_j + bias_j over the other rows (bias may be
-// null: 0); a pipeline wait that runs out sets kErrWait in *err
+// null: 0); a pipeline wait that runs out sets kErrWait in *err.  ids
+// (nullable): the rows are stored in another order and ids[p] is the
+// original id of the row at position p (sweep_order's perm); the lists are
+// then written to the original rows and name original ids, ties broken by
+// the lower original id, exactly as for the rows in their own order.
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
-                     uint32_t* idx, int32_t* dot, uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{});
+                     uint32_t* idx, int32_t* dot, uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{},
+                     const uint32_t* ids = nullptr);
 // each row i of QA's C best QA_i . QB_j + biasB_j over all nB columns (self:
-// the two are one set and column i is skipped)
+// the two are one set and column i is skipped).  col_ids / row_ids
+// (nullable): original ids of the columns (at least ceil(nB / 128) * 128
+// entries) and of the rows, when either set is stored in another order.
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* dot,
-                          uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{});
+                          uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{}, const uint32_t* col_ids = nullptr,
+                          const uint32_t* row_ids = nullptr);
+
+// The sweep order of the self product: the rows' positions sorted by
+// (word length, first principal component of the rows in 16 equal-count
+// buckets, second principal component rising in even buckets and falling in
+// odd ones), so that most of a row's best columns lie in the tiles near its
+// own.  The order changes only the time of dot_topk, never its result.
+// rank / slen (nullable: every length 0) give word i's length as
+// slen[rank[i]].  Writes perm[p] = the row at position p (sweep_perm_entries
+// entries, UINT32_MAX past n) and Qp / bp = the rows (dot_topk_qb_bytes) and
+// biases (n entries, bias nullable: none) in that order.  scratch holds
+// sweep_order_bytes(n) bytes.  Positions within one sort key follow the
+// order of atomic arrival.
+size_t sweep_order_bytes(uint32_t n);
+size_t sweep_perm_entries(uint32_t n);
+cudaError_t sweep_order(const __nv_bfloat16* Qb, const int32_t* bias, const uint32_t* rank, const uint8_t* slen,
+                        uint32_t n, void* scratch, uint32_t* perm, __nv_bfloat16* Qp, int32_t* bp, cudaStream_t s);
 
 // Algorithm 1's scores of every row i against its candidates cand[i * C +
 // r] (UINT32_MAX entries score INT32_MIN; out-of-range or self candidates

@@ -43,10 +43,12 @@ EXPORTED = [
     "nw_model_embed", "nw_model_loss_grad", "nw_model_train", "nw_quantize_embeddings", "nw_dot_topk",
     "nw_rescore_topk", "nw_proposal_topk", "nw_dot_topk_cross", "nw_proposal_query", "nw_server_create_proposal",
     "nw_proposal_set_exact_length",
+    "nw_proposal_set_sweep_order",
 ]
 EMBED_DIM = 64
 MAX_CANDIDATES = 512
 NW_BATCH_AUTOTUNE = 0x10
+NW_LOCALITY_ORDER = 0x8
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -172,6 +174,7 @@ def load_library(path: str = LIB_PATH):
     L.nw_dot_topk_cross.argtypes = [vp, vp, u32, vp, vp, u32, u32, vp, vp, u32]
     L.nw_proposal_query.argtypes = [vp, vp, vp, vp, u32, u32, u32, vp, vp, u32]
     L.nw_proposal_set_exact_length.argtypes = [vp, u32]
+    L.nw_proposal_set_sweep_order.argtypes = [vp, ctypes.c_int]
     L.nw_server_create_proposal.argtypes = [vp, vp, u32, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     L.nw_all_pairs_topk_noalloc.argtypes = [vp, u32, vp, vp, vp, ctypes.POINTER(i32), u32, u32]
     L.nw_server_create.argtypes = [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
@@ -735,6 +738,11 @@ class Model:
         """nw_proposal_set_exact_length: words and queries of at least min_len symbols take the exhaustive path (0: none)."""
         _check(self.ctx.handle, load_library().nw_proposal_set_exact_length(self.handle, min_len))
 
+    def set_sweep_order(self, locality: bool):
+        """nw_proposal_set_sweep_order: sweep the candidate product in a locality order (default) or in
+        dictionary order; the results are the same."""
+        _check(self.ctx.handle, load_library().nw_proposal_set_sweep_order(self.handle, 1 if locality else 0))
+
     def get_params(self, out=None):
         if out is None:
             out = np.empty(self.param_count, dtype=np.float32)
@@ -828,8 +836,9 @@ def quantize_embeddings(ctx: Context, E):
     return q, b[:n], np.float32(sc.value)
 
 
-def dot_topk(ctx: Context, q, C: int, bias=None):
-    """(idx uint32 [n, C], val int32 [n, C]) by nw_dot_topk (host or CUDA buffers)."""
+def dot_topk(ctx: Context, q, C: int, bias=None, locality: bool = False):
+    """(idx uint32 [n, C], val int32 [n, C]) by nw_dot_topk (host or CUDA buffers);
+    locality sets NW_LOCALITY_ORDER (same result, another sweep order)."""
     if not _is_torch(q):
         q = np.ascontiguousarray(q, dtype=np.int8)
         if bias is not None:
@@ -838,7 +847,8 @@ def dot_topk(ctx: Context, q, C: int, bias=None):
     idx = _empty_like_kind(q, (n, C), np.uint32, _torch_dtype("int32"))
     val = _empty_like_kind(q, (n, C), np.int32, _torch_dtype("int32"))
     _check(ctx.handle, load_library().nw_dot_topk(ctx.handle, _ptr(q)[0], _ptr(bias)[0], n, C, _ptr(idx)[0],
-                                                  _ptr(val)[0], _flags(q, bias, idx, val)))
+                                                  _ptr(val)[0], _flags(q, bias, idx, val) |
+                                                  (NW_LOCALITY_ORDER if locality else 0)))
     return idx, val
 
 

@@ -324,6 +324,54 @@ def test_dot_topk_compaction_value_spreads(ctx, kind):
     assert np.array_equal(idx[rows], wi)
 
 
+# n = 700: one column split; 3000 and 20,000: several splits (their lists are
+# merged into the original rows); 60,000: one split again, rows written by
+# the candidate kernel itself.  Few levels give many equal values, so the
+# lower-original-index tie rule decides which columns make the list.
+@pytest.mark.parametrize("n,C,levels,bias_range", [(700, 64, 1, 0), (3000, 16, 2, 40), (20_000, 64, 1, 0),
+                                                   (20_000, 256, 127, 300_000), (60_000, 128, 3, 0),
+                                                   (3000, 64, 127, -1)])
+def test_dot_topk_locality_order_matches_oracle(ctx, n, C, levels, bias_range):
+    """NW_LOCALITY_ORDER sweeps the rows sorted by their principal components;
+    the lists must equal the oracle's for the rows in their own order."""
+    g = np.random.default_rng(n + C + levels)
+    q = g.integers(-levels, levels + 1, (n, 64)).astype(np.int8)
+    q[n // 3] = q[1]  # duplicate rows
+    bias = None
+    if bias_range > 0:
+        bias = g.integers(-bias_range, bias_range + 1, n).astype(np.int32)
+    elif bias_range < 0:
+        bias = g.choice(np.array([-(1 << 23), (1 << 23), 0, 1], np.int32), n)
+    idx, dot = nw.dot_topk(ctx, q, C, bias=bias, locality=True)
+    pi, pd = nw.dot_topk(ctx, q, C, bias=bias)
+    assert np.array_equal(dot, pd)
+    assert np.array_equal(idx, pi)
+    rows = np.arange(n) if n <= 3000 else np.unique(np.concatenate([synth.sample_rows(n, 200), [0, 1, n - 1]]))
+    wi, wd = PR.dot_topk(q, C, rows=rows, bias=bias)
+    assert np.array_equal(dot[rows], wd)
+    assert np.array_equal(idx[rows], wi)
+
+
+def test_proposal_sweep_order_does_not_change_results(ctx):
+    w = synth.make_words(20000, 40, 1.1, 8.0, 3.0, 1, 25, seed=31)
+    d = ctx.load_dictionary(w.codes, w.offsets, 40, (1, -1, -1))
+    m = nw.Model(ctx, 40, seed=4)
+    ex_i, _, _, _ = d.all_pairs_topk(10, hist=None)
+    m.train(d, steps=300, batch_pairs=2048, lr=2e-3, seed=5, nbr=ex_i, nbr_fraction=0.5)
+    try:
+        for C in (32, 256):
+            m.set_sweep_order(True)
+            li, ls, prof = m.proposal_topk(d, C=C, k=10)
+            assert prof["candidates_ms"] > 0
+            m.set_sweep_order(False)
+            di, ds, _ = m.proposal_topk(d, C=C, k=10)
+            assert np.array_equal(li, di)
+            assert np.array_equal(ls, ds)
+    finally:
+        m.set_sweep_order(True)
+        m.free()
+
+
 def test_dot_topk_rejects_bad_C(ctx):
     q = np.zeros((10, 64), np.int8)
     for C in (0, nw.MAX_CANDIDATES + 1):
