@@ -95,7 +95,8 @@ constexpr int kOffCompKeys = kOffCompHist + kCompWarps * 1024;
 constexpr int kValStride = 36;
 constexpr int kOffVals = kOffCompKeys + kStageKeysTotal * 8;
 constexpr int kOffRow = kOffVals + kCtaRows * kValStride * 4;
-constexpr int kFinalBytes = 256 * 4 + kSel * 8;        // final pass: histogram + sort area per warp
+constexpr int kFinalSort = 2 * NW_MAX_CANDIDATES;      // final pass: keys sorted per row at most
+constexpr int kFinalBytes = 256 * 4 + kFinalSort * 8;  // final pass: histogram + sort area per warp
 // row state: threshold, kept counts of the two buffers, hand-over request, final state
 constexpr int kOffThr = kOffRow;
 constexpr int kOffKept = kOffThr + kCtaRows * 4;
@@ -110,8 +111,9 @@ constexpr int kOffIds = (kOffBars + kNumBars * 8 + 15) / 16 * 16;
 constexpr int kSmemUsed = kOffIds + kEpiWarps * kTileN * 4;
 constexpr int kSmemTotal = kSmemUsed + 1024;           // slack for aligning the base
 static_assert(kSmemTotal <= 227 * 1024, "one CTA per SM");
-// the final pass reuses the stage ring: per warp a histogram and a sort area
-static_assert(kWarps * kFinalBytes <= kStages * kStageBytes, "final-pass scratch fits the ring");
+// the final pass reuses the ring, compactor and value areas: per warp a
+// histogram and a sort area
+static_assert(kOffStages + kWarps * kFinalBytes <= kOffRow, "final-pass scratch stays below the row state");
 static_assert(kCap >= 2 * NW_MAX_CANDIDATES + 256, "a buffer holds a compaction's keys and a tile");
 static_assert(kPadRows % kCtaRows == 0 && kPadRows % kTileN == 0, "padding covers whole row blocks and tiles");
 // a pipeline wait gives up after this many SM clock cycles (about a second)
@@ -223,6 +225,7 @@ __device__ __forceinline__ uint32_t key_idx(uint64_t k) { return 0xffffffffu - (
 
 // Sorts s[0, size) descending (size a power of two) with the warp.
 __device__ void warp_bitonic_desc(uint64_t* s, int size, int lane) {
+  __syncwarp();
   for (int k = 2; k <= size; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = lane; i < size; i += 32) {
@@ -318,7 +321,8 @@ __device__ uint64_t warp_select_kth(const uint64_t* buf, int cnt, int r, unsigne
   return prefix;
 }
 
-// Copies the keys >= kmin of buf[0, cnt) into s (in any order); returns how many.
+// Copies the keys >= kmin of buf[0, cnt) into s (in their order); returns
+// how many.  s may be buf itself (each key moves down or stays).
 __device__ int warp_gather_ge(const uint64_t* buf, int cnt, uint64_t kmin, uint64_t* s, int lane) {
   int base = 0;
   for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
@@ -328,6 +332,7 @@ __device__ int warp_gather_ge(const uint64_t* buf, int cnt, uint64_t kmin, uint6
       const int i = i0 + 32 * u + lane;
       k[u] = i < cnt ? buf[i] : 0ull;
     }
+    __syncwarp();
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const bool keep = i0 + 32 * u + lane < cnt && k[u] >= kmin;
@@ -407,6 +412,7 @@ struct DotArgs {
   // entries) and names the columns in the keys; row_ids places the output rows
   const uint32_t* col_ids;
   const uint32_t* row_ids;
+  bool sorted;  // lists in descending key order (else in any order)
   uint32_t* out_idx;
   int32_t* out_val;
   uint32_t* err;
@@ -417,17 +423,26 @@ struct DotArgs {
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) { return *reinterpret_cast<const volatile uint32_t*>(p); }
 
 // Copies the keys of src[0, cnt) whose value is >= t to dst (in their order);
-// returns how many.
+// returns how many.  dst may be src itself (each key moves down or stays).
 __device__ int warp_keep_value_ge_to(const uint64_t* src, int cnt, int t, uint64_t* dst, int lane) {
   int base = 0;
-  for (int i0 = 0; i0 < cnt; i0 += 32) {
-    const int i = i0 + lane;
-    const uint64_t k = i < cnt ? src[i] : 0ull;
-    const bool keep = i < cnt && key_val(k) >= t;
-    const unsigned ball = __ballot_sync(0xffffffffu, keep);
-    if (keep) dst[base + __popc(ball & ((1u << lane) - 1u))] = k;
-    base += __popc(ball);
+  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
+    uint64_t k[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + 32 * u + lane;
+      k[u] = i < cnt ? src[i] : 0ull;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const bool keep = i0 + 32 * u + lane < cnt && key_val(k[u]) >= t;
+      const unsigned ball = __ballot_sync(0xffffffffu, keep);
+      if (keep) dst[base + __popc(ball & ((1u << lane) - 1u))] = k[u];
+      base += __popc(ball);
+    }
   }
+  __syncwarp();
   return base;
 }
 
@@ -850,7 +865,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(kTmemCols));
 
   // ---- final lists: each row's C best keys of its two buffers, sorted (the
-  // ring is free: every copy landed)
+  // ring, compactor and value areas are free: every copy landed)
   unsigned* hist = reinterpret_cast<unsigned*>(smem + kOffStages + warp * kFinalBytes);
   uint64_t* sort = reinterpret_cast<uint64_t*>(smem + kOffStages + warp * kFinalBytes + 1024);
   for (int r = warp; r < kCtaRows; r += kWarps) {
@@ -877,13 +892,43 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       }
       __syncwarp();
     }
+    // The C best keys: a 256-bin histogram of the values finds the bin that
+    // holds the C-th; the keys at or above that bin's lower edge (C or more,
+    // at most kFinalSort) are gathered into shared memory, and when there
+    // are more than C the exact select of the C-th key runs there, among
+    // them.  A bin too crowded for the area falls back to the exact select
+    // over the buffers.  Sorted only when the caller wants it.
     const int total = c0 + c1;
-    const uint64_t kmin = total > (int)C ? warp_select_kth(b0, total, (int)C, hist, lane) : 1ull;
-    const int kept = warp_gather_ge(b0, total, kmin, sort, lane);
-    const int size = pow2_at_least(kept);
-    for (int x = kept + lane; x < size; x += 32) sort[x] = 0ull;
-    __syncwarp();
-    warp_bitonic_desc(sort, size, lane);
+    int kept;
+    if (total <= (int)C) {
+      kept = warp_gather_ge(b0, total, 1ull, sort, lane);
+    } else {
+      int lo, hi;
+      warp_value_range(b0, total, lane, lo, hi);
+      const unsigned span = (unsigned)(hi - lo);
+      const int sh = span < 256u ? 0 : 24 - __clz((int)span);
+      warp_value_hist(b0, total, lo, sh, hist, lane);
+      int bin;
+      unsigned above;
+      hist_find_desc(hist, C, lane, bin, above);
+      const unsigned cand = above + hist[bin];
+      __syncwarp();
+      if (cand <= (unsigned)kFinalSort) {
+        kept = warp_keep_value_ge_to(b0, total, lo + (bin << sh), sort, lane);
+        if (kept > (int)C) {
+          const uint64_t kth = warp_select_kth(sort, kept, (int)C, hist, lane);
+          kept = warp_gather_ge(sort, kept, kth, sort, lane);
+        }
+      } else {
+        const uint64_t kth = warp_select_kth(b0, total, (int)C, hist, lane);
+        kept = warp_gather_ge(b0, total, kth, sort, lane);
+      }
+    }
+    if (P.sorted) {
+      const int size = pow2_at_least(kept);
+      for (int x = kept + lane; x < size; x += 32) sort[x] = 0ull;
+      warp_bitonic_desc(sort, size, lane);
+    }
     if (kSplit) {
       uint64_t* dst = P.part + ((size_t)i * P.splits + ys) * C;
       for (uint32_t x = lane; x < C; x += 32) dst[x] = (int)x < kept ? sort[x] : 0ull;
@@ -899,11 +944,11 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   }
 }
 
-// one warp per row: the C best of the row's splits' sorted lists (S x C
-// keys, 0 for missing) by the exact select, then sorted
+// one warp per row: the C best of the row's splits' lists (S x C keys, 0
+// for missing) by the exact select, sorted when asked
 constexpr int kMergeWarps = 8;
 __global__ void __launch_bounds__(kMergeWarps * 32)
-    merge_splits_kernel(const uint64_t* __restrict__ part, uint32_t nA, uint32_t S, uint32_t C,
+    merge_splits_kernel(const uint64_t* __restrict__ part, uint32_t nA, uint32_t S, uint32_t C, bool sorted,
                         const uint32_t* __restrict__ row_ids, uint32_t* __restrict__ out_idx,
                         int32_t* __restrict__ out_val) {
   __shared__ unsigned hist[kMergeWarps][256];
@@ -917,10 +962,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
   const uint64_t kth = warp_select_kth(keys, cnt, (int)C, hist[warp], lane);
   const uint64_t kmin = kth ? kth : 1ull;
   const int kept = warp_gather_ge(keys, cnt, kmin, keep[warp], lane);  // <= C
-  const int size = pow2_at_least(kept);
-  for (int x = kept + lane; x < size; x += 32) keep[warp][x] = 0ull;
-  __syncwarp();
-  warp_bitonic_desc(keep[warp], size, lane);
+  if (sorted) {
+    const int size = pow2_at_least(kept);
+    for (int x = kept + lane; x < size; x += 32) keep[warp][x] = 0ull;
+    warp_bitonic_desc(keep[warp], size, lane);
+  }
   const size_t orow = row_ids ? row_ids[i] : i;
   for (uint32_t x = lane; x < C; x += 32) {
     const bool have = (int)x < kept;
@@ -1272,7 +1318,7 @@ uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB) {
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* val,
                           uint32_t* err, cudaStream_t s, DotDebug dbg, const uint32_t* col_ids,
-                          const uint32_t* row_ids) {
+                          const uint32_t* row_ids, bool sorted) {
   if (nA == 0) return cudaSuccess;
   const uint32_t S = dot_topk_splits(nA, nB);
   const auto kernel = S > 1 ? (self ? dot_topk_kernel<true, true> : dot_topk_kernel<true, false>)
@@ -1299,20 +1345,21 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
   P.withhold = dbg.withhold;
   P.col_ids = col_ids;
   P.row_ids = row_ids;
+  P.sorted = sorted;
   const uint32_t npad = (uint32_t)bias_pad(nB);
   if (npad) bias_digits_kernel<<<(2 * npad + 255) / 256, 256, 0, s>>>(biasB, nB, npad, ext);
   const dim3 grid((nA + kCtaRows - 1) / kCtaRows, S);
   kernel<<<grid, kThreads, kSmemTotal, s>>>(P);
   if (S > 1)
-    merge_splits_kernel<<<(nA + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(P.part, nA, S, C, row_ids, idx,
+    merge_splits_kernel<<<(nA + kMergeWarps - 1) / kMergeWarps, kMergeWarps * 32, 0, s>>>(P.part, nA, S, C, sorted, row_ids, idx,
                                                                                          val);
   return cudaGetLastError();
 }
 
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
                      uint32_t* idx, int32_t* val, uint32_t* err, cudaStream_t s, DotDebug dbg,
-                     const uint32_t* ids) {
-  return dot_topk_rect(Qb, n, Qb, bias, n, C, true, buf, idx, val, err, s, dbg, ids, ids);
+                     const uint32_t* ids, bool sorted) {
+  return dot_topk_rect(Qb, n, Qb, bias, n, C, true, buf, idx, val, err, s, dbg, ids, ids, sorted);
 }
 
 cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t* q, __nv_bfloat16* qb,

@@ -961,7 +961,7 @@ nw_status proposal_query_impl(nw_model* M, nw_dict* d, const uint8_t* qcodes, co
   NW_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
   NW_CK(prop::dot_topk_rect(M->qQb.as<__nv_bfloat16>(), nq, M->dQb.as<__nv_bfloat16>(), M->dqbias.as<int32_t>(), n,
                             C, false, M->qbuf.as<uint64_t>(), M->qcand.as<uint32_t>(), M->qcand_dot.as<int32_t>(),
-                            derr, s, dot_debug(c)));
+                            derr, s, dot_debug(c), nullptr, nullptr, /*sorted=*/false));
   NW_CK(cudaStreamSynchronize(s));
   NW_TRY(check_device_flags(c, derr));
 
@@ -1176,12 +1176,15 @@ nw_status nw_proposal_topk(nw_model* M, nw_dict* d, uint32_t C, uint32_t k, uint
                             M->oQb.as<__nv_bfloat16>(), M->obias.as<int32_t>(), s));
     NW_CK(prop::dot_topk(M->oQb.as<__nv_bfloat16>(), M->obias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
                          M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s, dot_debug(c),
-                         M->operm.as<uint32_t>()));
+                         M->operm.as<uint32_t>(), /*sorted=*/false));
   } else {
     NW_CK(prop::dot_topk(M->Qb.as<__nv_bfloat16>(), M->qbias.as<int32_t>(), n, C, M->topbuf.as<uint64_t>(),
-                         M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s, dot_debug(c)));
+                         M->cand.as<uint32_t>(), M->cand_dot.as<int32_t>(), err_ptr(M), s, dot_debug(c), nullptr,
+                         /*sorted=*/false));
   }
   NW_CK(cudaEventRecord(ev[3], s));
+  // (the candidates of a row come in no particular order: the rescoring
+  // regroups them by length and the k best are taken by score, then index)
   NW_TRY(rescore_select(c, d, M->cand.as<uint32_t>(), C, k, M->cand_score, out_i, out_s, err_ptr(M), s));
   NW_CK(cudaEventRecord(ev[4], s));
   NW_TRY(splice_long_rows(M, d, nlong, k, out_i, out_s, s));

@@ -59,9 +59,11 @@ struct DotDebug {
 // original id of the row at position p (sweep_order's perm); the lists are
 // then written to the original rows and name original ids, ties broken by
 // the lower original id, exactly as for the rows in their own order.
+// sorted: each list in descending order (value, then lower id); otherwise
+// the same C entries in an order that may differ from call to call.
 cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, uint32_t C, uint64_t* buf,
                      uint32_t* idx, int32_t* dot, uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{},
-                     const uint32_t* ids = nullptr);
+                     const uint32_t* ids = nullptr, bool sorted = true);
 // each row i of QA's C best QA_i . QB_j + biasB_j over all nB columns (self:
 // the two are one set and column i is skipped).  col_ids / row_ids
 // (nullable): original ids of the columns (at least ceil(nB / 128) * 128
@@ -69,7 +71,7 @@ cudaError_t dot_topk(const __nv_bfloat16* Qb, const int32_t* bias, uint32_t n, u
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* dot,
                           uint32_t* err, cudaStream_t s, DotDebug dbg = DotDebug{}, const uint32_t* col_ids = nullptr,
-                          const uint32_t* row_ids = nullptr);
+                          const uint32_t* row_ids = nullptr, bool sorted = true);
 
 // The sweep order of the self product: the rows' positions sorted by
 // (word length, first principal component of the rows in 16 equal-count
