@@ -439,8 +439,9 @@ nw_status nw_debug_enumerate_pairs(const uint32_t *lengths, uint32_t n, uint32_t
 
 /* Host-only: the (query, dictionary word) pairs that nw_query's kernels
  * would score for query words of lengths q_lengths[0..nq) against dictionary
- * words of lengths d_lengths[0..nd), with `ta` A words per task (0 = the
- * default; batches use 64, 128 or 256), as original-index pairs (q[p], d[p]).
+ * words of lengths d_lengths[0..nd), with at most `ta` A words per task (0 =
+ * the default; a launch with few tasks takes smaller chunks, down to 32
+ * words, as nw_query plans it), as original-index pairs (q[p], d[p]).
  * Writes at most `cap` pairs and sets *count to the total.  Runs the same
  * query planner and task-to-pair mapping as the kernels, on the CPU, so tests
  * can check that every (query, word) pair is covered exactly once. */

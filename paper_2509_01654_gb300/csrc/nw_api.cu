@@ -470,7 +470,7 @@ nw_status query_impl(nw_dict* d, const uint8_t* qcodes, const uint32_t* qoffsets
   if ((uint64_t)(hi - key_lo) >= (1ull << (32 - ib)))
     return set_err(c, NW_ERANGE, "score range with %u dictionary words does not fit 32-bit list keys", n);
   Plan plan;
-  plan_query(q.bk, d->ws.bk, kDefaultTA, plan);
+  plan_query(q.bk, d->ws.bk, kDefaultTA, plan, kQueryMinTasks);
   NW_TRY(ctx_ensure(c, c->ws_segs, sizeof(Seg) * std::max<size_t>(1, plan.segs.size()), "query segments"));
   NW_TRY(ctx_ensure(c, c->ws_slots, sizeof(uint32_t) * (size_t)nq * k, "list slots"));
   NW_TRY(ctx_ensure(c, c->ws_thr, sizeof(uint32_t) * (size_t)nq, "list thresholds"));
@@ -687,13 +687,13 @@ nw_status nw_debug_enumerate_query_pairs(const uint32_t* q_lengths, uint32_t nq,
   if (!bucket(q_lengths, nq, qb, qperm) || !bucket(d_lengths, nd, db, dperm)) return NW_EINVAL;
   const uint32_t TA = ta ? ta : kDefaultTA;
   Plan plan;
-  plan_query(qb, db, TA, plan);
+  plan_query(qb, db, TA, plan, kQueryMinTasks);
   uint64_t cnt = 0;
   for (const LaunchPlan& lp : plan.launches) {
     const Seg* segs = plan.segs.data() + lp.seg_first;
     for (uint64_t t = 0; t < lp.ntasks; ++t) {
       const Seg& S = segs[find_seg(segs, lp.nsegs, t)];
-      const TaskGeom g = task_geom(S, t, TA);
+      const TaskGeom g = task_geom(S, t, lp.ta ? lp.ta : TA);
       for (uint32_t x = g.a0; x < g.a1; ++x) {
         for (uint32_t y = g.b0; y < g.bend; ++y) {
           if (!pair_valid(g, x, y)) continue;

@@ -367,6 +367,8 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
       T = TaskTerms{P.a_enc, P.b_rec, P.A, P.B, P.C1, P.C2, P.match, P.mismatch, P.gap, P.key_lo, P.ib, P.imask};
     }
     const bool listsA = kLists && T.A.slots != nullptr;
+    // (queries run without a histogram: the histogram kernels keep the lanes' own offers)
+    const bool serialA = EPI == kEpiLists && listsA && P.serial_a != 0u;
     const bool listsB = kLists && T.B.slots != nullptr;
     const uint32_t blo = g.b0 + 2u * lane;
     const uint32_t bhi = blo + 1u;
@@ -477,6 +479,7 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
           // formed only for the rare candidates.
           const uint32_t nA2 = __shfl_sync(0xffffffffu, my_nA2, (int)w);
           const bool pre = check || (__viaddmax_s16x2_relu(res, __vmaxs2(nB2, nA2), 0u) & okmask) != 0u;
+          uint32_t ka_lo = 0u, ka_hi = 0u;  // this lane's keys for the A word's list
           if (pre) {
             const uint32_t thrA = sT[w];
             const int tA = listsA ? g_bound(P, T, thrA, LB, pconst) : INT_MAX;
@@ -484,7 +487,6 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
             const bool c_hi = ok_hi && g_hi >= min(tB_hi, tA);
             if (c_lo || c_hi) {
               const uint32_t oa = __ldg(T.A.perm + a);
-              uint32_t* rowA = listsA ? T.A.slots + (size_t)a * P.k : nullptr;
               if (c_lo) {
                 const int s = g_lo + pconst;
                 if (g_lo >= tB_lo) {  // the lane's word takes the A word as a neighbour
@@ -500,7 +502,10 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
                 }
                 if (g_lo >= tA) {  // the A word takes the lane's word as a neighbour
                   const uint32_t key = list_key(P, T, s, LB, ob_lo);
-                  if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
+                  if (key > thrA) {
+                    if (serialA) ka_lo = key;
+                    else list_offer(T.A.slots + (size_t)a * P.k, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
+                  }
                 }
               }
               if (c_hi) {
@@ -518,9 +523,33 @@ __global__ void __launch_bounds__(kBlock, dp_min_blocks(LB)) nw_dp_kernel(const 
                 }
                 if (g_hi >= tA) {
                   const uint32_t key = list_key(P, T, s, LB, ob_hi);
-                  if (key > thrA) list_offer(rowA, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
+                  if (key > thrA) {
+                    if (serialA) ka_hi = key;
+                    else list_offer(T.A.slots + (size_t)a * P.k, T.A.thr + a, P.k, key, P.err, inserts, max_iters);
+                  }
                 }
               }
+            }
+          }
+          if (serialA) {
+            // Every lane may hold keys for the same A word's list.  The warp
+            // offers them one at a time from the best down, each against the
+            // bound the previous offer returned, and stops at the first key
+            // below it: the lanes never race on that list, and a list that
+            // is already full costs one offer.
+            uint32_t best = ka_lo > ka_hi ? ka_lo : ka_hi;
+            uint32_t thrW = sT[w];
+            while (__any_sync(0xffffffffu, best > thrW)) {
+              const uint32_t m = __reduce_max_sync(0xffffffffu, best);
+              const int src = __ffs(__ballot_sync(0xffffffffu, best == m)) - 1;
+              uint32_t nm = 0u;
+              if (lane == src) {
+                nm = list_offer(T.A.slots + (size_t)a * P.k, T.A.thr + a, P.k, m, P.err, inserts, max_iters);
+                if (ka_lo == m) ka_lo = 0u; else ka_hi = 0u;
+                best = ka_lo > ka_hi ? ka_lo : ka_hi;
+              }
+              nm = __shfl_sync(0xffffffffu, nm, src);
+              thrW = nm > thrW ? nm : thrW;
             }
           }
         }

@@ -337,8 +337,16 @@ void plan_all_pairs(const Buckets& bk, uint32_t TA, Plan& out) {
   order_launches(out);
 }
 
+// Tasks a query launch should have at least (a few per warp of a full GPU)
+// before its A chunks are cut below the default size.
+constexpr uint64_t kQueryMinTasks = 8192;
+
 // Every (query, dictionary word) pair once; the longer word goes to the lanes.
-void plan_query(const Buckets& qb, const Buckets& db, uint32_t TA, Plan& out) {
+// A launch whose B words are few (long dictionary words, or a small query
+// set in the lanes) has few tasks at TA A words per task: with min_tasks > 0
+// its chunk is halved, down to 32 words, until it has min_tasks tasks, and
+// the launch records the chunk in its ta.
+void plan_query(const Buckets& qb, const Buckets& db, uint32_t TA, Plan& out, uint64_t min_tasks = 0) {
   out = Plan{};
   for (int role = 1; role <= 2; ++role) {
     for (int LB = 0; LB < kBuckets; ++LB) {
@@ -353,12 +361,22 @@ void plan_query(const Buckets& qb, const Buckets& db, uint32_t TA, Plan& out) {
       if (nB == 0) continue;
       // role 1: query length La <= LB (dictionary length); role 2: dictionary length La < LB (query length)
       const int La_hi = role == 1 ? LB : LB - 1;
+      uint32_t ta = TA;
+      if (min_tasks) {
+        auto tasks_at = [&](uint32_t t) {
+          uint64_t x = 0;
+          for (int La = La_hi; La >= 0; --La) x += cdiv(Aset.count[La], t) * cdiv(nB, kWarpB);
+          return x;
+        };
+        while (ta > 32 && tasks_at(ta) < min_tasks) ta /= 2;
+        lp.ta = ta;
+      }
       for (int La = La_hi; La >= 0; --La) {
         const uint32_t nA = Aset.count[La];
         if (nA == 0) continue;
         uint64_t nt = 0;
         out.segs.push_back(make_seg(Aset, La, Aset.start[La], Aset.start[La] + nA, Bset, LB, Bset.start[LB],
-                                    Bset.start[LB] + nB, false, TA, task, nt));
+                                    Bset.start[LB] + nB, false, ta, task, nt));
         task += nt;
         lp.pairs += (uint64_t)nA * nB;
         lp.cells += (uint64_t)nA * nB * (uint64_t)(La * LB);
@@ -624,6 +642,7 @@ nw_status run_plan(nw_ctx* c, cudaStream_t stream, const Plan& plan, const Seg* 
     P.segs = d_segs + lp.seg_first;
     P.nsegs = lp.nsegs;
     if (lp.ta) P.TA = lp.ta;
+    P.serial_a = lp.role == 1 ? 1u : 0u;  // query words are the A side
     P.task_lo = lo;
     P.task_hi = hi;
     P.counter = counters + li;

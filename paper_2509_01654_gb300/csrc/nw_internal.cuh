@@ -238,6 +238,10 @@ struct DpParams {
   // debug setting: 0 = list insertions retry up to kInsertMaxIters times;
   // otherwise they give up after dbg_insert_limit - 1 tries (NW_ETIMEOUT)
   uint32_t dbg_insert_limit;
+  // nonzero: the A words' list offers of one A word go through the warp one at
+  // a time (A words that many tasks share, such as query words, whose lists
+  // the 64 lanes of a task would otherwise race on)
+  uint32_t serial_a;
 };
 
 // The substitution table of a dictionary scored with a full similarity

@@ -224,7 +224,7 @@ nw_status launch_batch(nw_server* S, Slot& s) {
   const int32_t key_lo = lo - 1;
   if ((uint64_t)(hi - key_lo) >= (1ull << (32 - ib)))
     return set_err(c, NW_ERANGE, "score range with %u dictionary words does not fit 32-bit list keys", d->ws.n);
-  plan_query(bk, d->ws.bk, kDefaultTA, s.plan);
+  plan_query(bk, d->ws.bk, kDefaultTA, s.plan, kQueryMinTasks);
   if (s.plan.segs.size() > kMaxSegs) return set_err(c, NW_ERANGE, "batch plan too large");
   std::memcpy(s.h_segs, s.plan.segs.data(), sizeof(Seg) * s.plan.segs.size());
 
