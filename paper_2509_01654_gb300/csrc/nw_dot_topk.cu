@@ -102,8 +102,8 @@ constexpr int kOffThr = kOffRow;
 constexpr int kOffKept = kOffThr + kCtaRows * 4;
 constexpr int kOffReq = kOffKept + kCtaRows * 8;
 constexpr int kOffFin = kOffReq + kCtaRows * 4;
-constexpr int kOffMisc = kOffFin + kCtaRows * 4;       // request masks, done flags, tmem address
-constexpr int kOffBars = kOffMisc + 64;
+constexpr int kOffMisc = kOffFin + kCtaRows * 4;       // request masks, done flags, tmem address, progress
+constexpr int kOffBars = kOffMisc + 128;
 constexpr int kNumBars = 2 * kStages + 4 + 1;          // full, empty, acc full x2, acc empty x2, A loaded
 // per epilogue warp: the original ids of the current tile's columns (sweeps
 // over rows in a locality order)
@@ -502,6 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   uint32_t* sMask = sMisc;                  // [kEpiWarps]: rows of each epilogue warp awaiting compaction
   uint32_t* sDone = sMisc + kEpiWarps;      // epilogue warps that finished their sweep
   uint32_t* sTmem = sMisc + kEpiWarps + 1;  // tensor-memory base (written by tcgen05.alloc)
+  uint32_t* sProg = sMisc + kEpiWarps + 2;  // [kEpiWarps]: tiles each epilogue warp has finished
   const uint32_t bar0 = smem_u32(smem + kOffBars);
   auto full_bar = [&](uint32_t s) { return bar0 + 8u * s; };
   auto empty_bar = [&](uint32_t s) { return bar0 + 8u * (kStages + s); };
@@ -553,7 +554,8 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
     sReq[r] = 0u;
     sFin[r] = 0u;
   }
-  if (tid <= kEpiWarps) sMisc[tid] = 0u;
+  if (tid <= kEpiWarps) sMisc[tid] = 0u;  // request masks, done flags (not the tensor-memory word)
+  if (tid < kEpiWarps) sProg[tid] = 0u;
   for (int x = tid; x < kRows * kExtK; x += kThreads) {
     const uint32_t r = (uint32_t)x / kExtK, k = (uint32_t)x % kExtK;
     const float w = k == 0 ? 65536.f : (k == 1 ? 256.f : (k == 2 ? 1.f : 0.f));
@@ -752,6 +754,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
         process(vb, col0 + 32u * (uint32_t)(c + 1), 32u * (uint32_t)(c + 1));
         if (c + 2 < kChunks) tmem_wait(va);
       }
+      if (lane == 0) *reinterpret_cast<volatile uint32_t*>(sProg + warp) = u + 1u;  // seen by the compactors
       if (col_ids && u + 1u < ntiles) {  // the next tile's ids, once every hit of this one is appended
         __syncwarp();
         *reinterpret_cast<uint4*>(sid + 4 * lane) = idn;
@@ -802,6 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       const int area = kStageKeysTotal / ncomp;  // staging keys of this compactor
       uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kOffCompKeys) + (size_t)q * area;
       long long t0 = clock64();
+      uint32_t last_prog = 0u;
       for (;;) {
         uint32_t done = 0u, any = 0u;
         if (lane == 0) {
@@ -814,7 +818,16 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
         done = __shfl_sync(0xffffffffu, done, 0);
         if (any == 0u) {
           if (done == served) break;
-          if (clock64() - t0 > wait_lim) {
+          // no request: the bound runs only while the epilogue warps served
+          // make no progress either (a sweep may go long without a hand-over)
+          uint32_t prog = 0u;
+          if (lane == 0)
+            for (int e = 0; e < per; ++e) prog += ld_volatile(sProg + q * per + e);
+          prog = __shfl_sync(0xffffffffu, prog, 0);
+          if (prog != last_prog) {
+            last_prog = prog;
+            t0 = clock64();
+          } else if (clock64() - t0 > wait_lim) {
             if (lane == 0) atomicOr(err, kErrWait);
             break;
           }
