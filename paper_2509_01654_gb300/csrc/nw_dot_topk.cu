@@ -102,7 +102,8 @@ constexpr int kOffThr = kOffRow;
 constexpr int kOffKept = kOffThr + kCtaRows * 4;
 constexpr int kOffReq = kOffKept + kCtaRows * 8;
 constexpr int kOffFin = kOffReq + kCtaRows * 4;
-constexpr int kOffMisc = kOffFin + kCtaRows * 4;       // request masks, done flags, tmem address, progress
+constexpr int kOffHi = kOffFin + kCtaRows * 4;          // per row: a bound on every value appended
+constexpr int kOffMisc = kOffHi + kCtaRows * 4;        // request masks, done flags, tmem address, progress
 constexpr int kOffBars = kOffMisc + 128;
 constexpr int kNumBars = 2 * kStages + 4 + 1;          // full, empty, acc full x2, acc empty x2, A loaded
 // per epilogue warp: the original ids of the current tile's columns (sweeps
@@ -385,6 +386,33 @@ __device__ void warp_value_hist(const uint64_t* buf, int cnt, int lo, int sh, un
   __syncwarp();
 }
 
+// Like warp_value_hist, counting only the keys whose value is >= lo (the
+// others are skipped; a value past the last bin counts in it); returns how
+// many were counted.
+__device__ unsigned warp_value_hist_ge(const uint64_t* buf, int cnt, int lo, int sh, unsigned* hist, int lane) {
+  for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+  __syncwarp();
+  unsigned mine = 0u;
+  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
+    uint64_t k[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + 32 * u + lane;
+      k[u] = i < cnt ? buf[i] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int v = key_val(k[u]);
+      if (i0 + 32 * u + lane < cnt && v >= lo) {
+        atomicAdd(&hist[min((uint32_t)(v - lo) >> sh, 255u)], 1u);
+        ++mine;
+      }
+    }
+  }
+  __syncwarp();
+  return __reduce_add_sync(0xffffffffu, mine);
+}
+
 __device__ __forceinline__ int pow2_at_least(int x) {
   int p = 32;
   while (p < x) p <<= 1;
@@ -455,31 +483,46 @@ __device__ int warp_keep_value_ge_to(const uint64_t* src, int cnt, int t, uint64
 // key when that bin is crowded), so it is at or below the row's C-th best
 // value so far; the handed-over keys that reach it are written back to the
 // front of their buffer.  Returns the number kept there.
+//
+// thr_now is the row's current threshold and hi_now a bound on every value
+// the row has appended.  Once the row has a threshold, keys below it cannot
+// reach its C best, so the histogram covers [thr_now, hi_now] and skips them
+// (no pass for the range); if fewer than C keys reach thr_now, it stays.
 __device__ int compact_buffer(uint64_t* keys, int c, const uint64_t* other, int co, uint32_t C, unsigned keep_limit,
-                              unsigned* hist, uint64_t* stage, int lane, int& t) {
+                              float thr_now, float hi_now, unsigned* hist, uint64_t* stage, int lane, int& t) {
   for (int x = lane; x < c; x += 32) cp_async8(stage + x, keys + x);
   for (int x = lane; x < co; x += 32) cp_async8(stage + c + x, other + x);
   cp_async_wait_all();
   __syncwarp();
   const int n = c + co;
   int lo, hi;
-  warp_value_range(stage, n, lane, lo, hi);
+  if (thr_now > -FLT_MAX && hi_now >= thr_now) {  // integers held exactly in float
+    lo = (int)thr_now;
+    hi = (int)hi_now;
+  } else {
+    warp_value_range(stage, n, lane, lo, hi);
+  }
   const unsigned span = (unsigned)(hi - lo);
   const int sh = span < 256u ? 0 : 24 - __clz((int)span);
-  warp_value_hist(stage, n, lo, sh, hist, lane);
-  int bin;
-  unsigned above;
-  hist_find_desc(hist, C, lane, bin, above);
-  const unsigned keep = above + hist[bin];
-  __syncwarp();
+  const unsigned counted = warp_value_hist_ge(stage, n, lo, sh, hist, lane);
   int kept;
-  if (keep <= keep_limit) {
-    t = lo + (bin << sh);
-    kept = warp_keep_value_ge_to(stage, c, t, keys, lane);
+  if (counted < C) {
+    t = lo;
+    kept = warp_keep_value_ge_to(stage, c, lo, keys, lane);
   } else {
-    const uint64_t kth = warp_select_kth(stage, n, (int)C, hist, lane);
-    kept = warp_gather_ge(stage, c, kth, keys, lane);
-    t = key_val(kth);
+    int bin;
+    unsigned above;
+    hist_find_desc(hist, C, lane, bin, above);
+    const unsigned keep = above + hist[bin];
+    __syncwarp();
+    if (keep <= keep_limit) {
+      t = lo + (bin << sh);
+      kept = warp_keep_value_ge_to(stage, c, t, keys, lane);
+    } else {
+      const uint64_t kth = warp_select_kth(stage, n, (int)C, hist, lane);
+      kept = warp_gather_ge(stage, c, kth, keys, lane);
+      t = key_val(kth);
+    }
   }
   __syncwarp();
   return kept;
@@ -495,6 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
   const long long wait_lim = P.wait_cycles;
 
   float* sThr = reinterpret_cast<float*>(smem + kOffThr);
+  float* sHi = reinterpret_cast<float*>(smem + kOffHi);
   int* sKept = reinterpret_cast<int*>(smem + kOffKept);          // [row][buffer]
   uint32_t* sReq = reinterpret_cast<uint32_t*>(smem + kOffReq);  // buffer | count << 1 of a hand-over
   uint32_t* sFin = reinterpret_cast<uint32_t*>(smem + kOffFin);  // active buffer | count << 1 at the end
@@ -663,6 +707,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
     int cnt = 0;
     uint64_t* rb = live ? row_buf(i, 0) : nullptr;
     float thr = -FLT_MAX;
+    float amax = -FLT_MAX;  // at least every value this row has appended
     const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16);
     const uint32_t bit = 1u << lane;
 
@@ -709,6 +754,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
           hit &= valid;
         }
         if (hit) {
+          amax = fmaxf(amax, mx);
 #pragma unroll
           for (int q4 = 0; q4 < 8; ++q4)
             *reinterpret_cast<uint4*>(sv + 4 * q4) = make_uint4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
@@ -773,6 +819,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
           }
         }
         if (live && !pending) {
+          sHi[r] = amax;
           sReq[r] = act | ((uint32_t)cnt << 1);
           __threadfence_block();
           atomicOr(sMask + warp, bit);
@@ -853,8 +900,10 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
               co = min(co, area - stage_keys);
             }
             int t = 0;
-            const int kept = compact_buffer(keys, c, row_buf(row0 + (uint32_t)r, b ^ 1u), co, C, keep_limit, hist,
-                                            stage, lane, t);
+            const float thr_now = *reinterpret_cast<volatile float*>(sThr + r);
+            const float hi_now = *reinterpret_cast<volatile float*>(sHi + r);
+            const int kept = compact_buffer(keys, c, row_buf(row0 + (uint32_t)r, b ^ 1u), co, C, keep_limit,
+                                            thr_now, hi_now, hist, stage, lane, t);
             __threadfence_block();
             if (lane == 0) {
               sKept[2 * r + b] = kept;
@@ -1065,29 +1114,41 @@ size_t bias_pad(uint32_t n) { return ((size_t)n + kPadRows - 1) / kPadRows * kPa
 constexpr int kOrdBins = 4096;     // histogram of the first projection
 constexpr int kOrdBuckets = 16;    // equal-count buckets of the first projection
 constexpr int kOrdLevels = 256;    // levels of the second projection
-constexpr int kOrdLens = 64;       // lengths clamp to 63
+constexpr int kOrdLens = NW_MAX_WORD_LEN + 1;
 constexpr int kOrdKeys = kOrdLens * kOrdBuckets * kOrdLevels;
-constexpr int kMomRows = 8;        // rows staged per step of moments_kernel
+constexpr int kMomRows = 32;       // rows staged per step of moments_kernel (one 16-byte load per thread)
+constexpr uint32_t kMomMaxRows = 1u << 17;  // rows per block at most: 2^17 x 127^2 < 2^31
+static_assert(kOrdKeys % 4096 == 0 && kOrdBins % 4096 == 0, "block_exclusive_scan tiles of 4,096");
+static_assert(kMomRows * 8 == 256, "one 16-byte chunk per thread of moments_kernel");
 
 // sums over the rows of x and of x x^T, x = a row's 64 values (integers in
-// [-127, 127], so 64-bit integer sums are exact and order-free): mom[0, 64)
-// and mom[64 + 64 k + l].  Thread t owns entries (t / 4, 16 (t % 4) + 0..15).
+// [-127, 127], so integer sums are exact and order-free): mom[0, 64) and
+// mom[64 + 64 k + l].  A step stages kMomRows rows with one 16-byte load per
+// thread; thread t owns entries (t / 4, 16 (t % 4) + 0..15) and sums them in
+// 32 bits (a block covers at most kMomMaxRows rows: |sum| < 2^31), then adds
+// them to the 64-bit totals.
 __global__ void __launch_bounds__(256) moments_kernel(const __nv_bfloat16* __restrict__ Qb, uint32_t n,
                                                       unsigned long long* mom) {
   __shared__ int row[kMomRows][kDim];
   const int t = threadIdx.x, k = t >> 2, l0 = (t & 3) * 16;
-  long long acc[16], s1 = 0;
+  int acc[16], s1 = 0;
 #pragma unroll
   for (int j = 0; j < 16; ++j) acc[j] = 0;
-  for (uint32_t r0 = blockIdx.x * kMomRows; r0 < n; r0 += gridDim.x * kMomRows) {
+  const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t rbeg = min(n, blockIdx.x * per), rend = min(n, rbeg + per);
+  for (uint32_t r0 = rbeg; r0 < rend; r0 += kMomRows) {
     __syncthreads();
-    for (int x = t; x < kMomRows * kDim; x += 256) {
-      const uint32_t r = r0 + (uint32_t)(x / kDim);
-      const int c = x % kDim;
-      row[x / kDim][c] = r < n ? (int)__bfloat162float(Qb[swz_index(r, c)]) : 0;
+    {  // kMomRows x 8 chunks of 16 bytes: chunk ch of row r holds values 8 (ch ^ (r & 7)) ..
+      const uint32_t rr = (uint32_t)t >> 3, ch = (uint32_t)t & 7u, r = r0 + rr;
+      uint4 u = make_uint4(0u, 0u, 0u, 0u);
+      if (r < rend) u = __ldg(reinterpret_cast<const uint4*>(Qb + (size_t)r * kDim) + ch);
+      const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+      const int lc = (int)((ch ^ (r & 7u)) * 8u);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) row[rr][lc + e] = (int)__bfloat162float(h[e]);
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 4
     for (int rr = 0; rr < kMomRows; ++rr) {
       const int a = row[rr][k];
 #pragma unroll
@@ -1096,8 +1157,9 @@ __global__ void __launch_bounds__(256) moments_kernel(const __nv_bfloat16* __res
     }
   }
 #pragma unroll
-  for (int j = 0; j < 16; ++j) atomicAdd(&mom[kDim + k * kDim + l0 + j], (unsigned long long)acc[j]);
-  if ((t & 3) == 0) atomicAdd(&mom[k], (unsigned long long)s1);
+  for (int j = 0; j < 16; ++j)
+    if (acc[j]) atomicAdd(&mom[kDim + k * kDim + l0 + j], (unsigned long long)(long long)acc[j]);
+  if ((t & 3) == 0 && s1) atomicAdd(&mom[k], (unsigned long long)(long long)s1);
 }
 
 // One block of 64 threads: the covariance of the rows from their moments and
@@ -1208,25 +1270,35 @@ __global__ void __launch_bounds__(256) proj_hist_kernel(const float2* __restrict
     if (h[x]) atomicAdd(&hist[x], h[x]);
 }
 
-// one block: an exclusive scan of a[0, m) in place (m a multiple of blockDim.x)
+// one block of 1024 threads: an exclusive scan of a[0, m) in place, m a
+// multiple of 4096 (a 16-byte-aligned array), in coalesced tiles of 4,096
 __device__ void block_exclusive_scan(unsigned* a, int m) {
   __shared__ unsigned part[1024];
-  const int t = threadIdx.x, per = m / (int)blockDim.x;
-  unsigned sum = 0;
-  for (int j = 0; j < per; ++j) sum += a[t * per + j];
-  part[t] = sum;
+  __shared__ unsigned carry;
+  const int t = threadIdx.x;
+  if (t == 0) carry = 0u;
   __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    const unsigned x = t >= o ? part[t - o] : 0u;
+  for (int base = 0; base < m; base += 4096) {
+    uint4 v = reinterpret_cast<const uint4*>(a + base)[t];
+    const unsigned sum = v.x + v.y + v.z + v.w;
+    part[t] = sum;
     __syncthreads();
-    part[t] += x;
+    for (int o = 1; o < 1024; o <<= 1) {
+      const unsigned x = t >= o ? part[t - o] : 0u;
+      __syncthreads();
+      part[t] += x;
+      __syncthreads();
+    }
+    const unsigned e = carry + part[t] - sum;
+    uint4 w;
+    w.x = e;
+    w.y = e + v.x;
+    w.z = w.y + v.y;
+    w.w = w.z + v.z;
+    reinterpret_cast<uint4*>(a + base)[t] = w;
     __syncthreads();
-  }
-  unsigned run = part[t] - sum;
-  for (int j = 0; j < per; ++j) {
-    const unsigned x = a[t * per + j];
-    a[t * per + j] = run;
-    run += x;
+    if (t == 1023) carry += part[1023];
+    __syncthreads();
   }
 }
 
@@ -1258,7 +1330,7 @@ __global__ void __launch_bounds__(256) order_key_kernel(const float2* __restrict
   const unsigned b = bucket_of[ord_level(p.x, ord_float(range[0]), ord_float(range[1]), kOrdBins)];
   int lv = ord_level(p.y, ord_float(range[2]), ord_float(range[3]), kOrdLevels);
   if (b & 1u) lv = kOrdLevels - 1 - lv;
-  const unsigned len = (rank && slen) ? min(63u, (unsigned)slen[rank[r]]) : 0u;
+  const unsigned len = (rank && slen) ? min((unsigned)(kOrdLens - 1), (unsigned)slen[rank[r]]) : 0u;
   const uint32_t k = (len * kOrdBuckets + b) * kOrdLevels + (uint32_t)lv;
   key[r] = k;
   atomicAdd(&cnt[k], 1u);
@@ -1417,7 +1489,9 @@ cudaError_t sweep_order(const __nv_bfloat16* Qb, const int32_t* bias, const uint
   if (e == cudaSuccess) e = cudaMemsetAsync(perm, 0xff, sizeof(uint32_t) * npad, s);
   if (e != cudaSuccess) return e;
   if (n) {
-    const unsigned rows_grid = std::min<unsigned>(304u, (n + kMomRows - 1) / kMomRows);
+    // enough blocks to hide the loads, and never more than kMomMaxRows rows per block
+    const unsigned rows_grid = std::max<unsigned>(std::min<unsigned>(1216u, (n + kMomRows - 1) / kMomRows),
+                                                  (unsigned)((n + kMomMaxRows - 1) / kMomMaxRows));
     const unsigned grid = (n + 255) / 256;
     moments_kernel<<<rows_grid, 256, 0, s>>>(Qb, n, mom);
     pca_kernel<<<1, kDim, 0, s>>>(mom, n, dirs, range);
