@@ -371,8 +371,14 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_run": bms, "pairs_per_s": binfo["pairs"] / (bms / 1e3),
             "gcups": binfo["cells"] / (bms / 1e3) / 1e9, "autotune_ms": binfo["tune_ms"],
             "words_per_task_by_length": {str(L): t for L, t in enumerate(binfo["words_per_task"]) if t},
+            "blocks_per_sm_by_length": {str(L): b for L, b in enumerate(binfo["blocks_per_sm"]) if b},
         }
         batch.free()
+        # a second batch of the same shape takes its tile shapes from the autotuner's cache
+        again = nw.Batch(ctx, [(x.words.codes, x.words.offsets, x.words.alphabet, x.scoring) for x in dl], k=k)
+        ainfo = again.info()
+        batched_stats["same_shape_again"] = {"autotune_ms": ainfo["tune_ms"], "tune_cached": int(ainfo["tune_cached"])}
+        again.free()
         # the same dictionaries, each with a query set of its own, in one graph
         qsets = synth.batched_query_sets(dl)
         batch = nw.Batch(ctx, [(x.words.codes, x.words.offsets, x.words.alphabet, x.scoring, (q.codes, q.offsets))

@@ -272,7 +272,15 @@ typedef struct {
                                 * dictionary's own lists are not computed */
 } nw_batch_dict;
 
-#define NW_BATCH_AUTOTUNE 0x10u /* nw_batch_create flag: time tile-shape candidates per launch */
+/* nw_batch_create flag: time tile-shape candidates per launch.  Per longer
+ * length, the A words per task are chosen from {64, 128, 256}, then the
+ * resident blocks per SM from {2, 3, as many as fit} at that size, by timing
+ * whole launches on the batch.  (A task's B chunk is 64 words: two words per
+ * lane in the kernel's int16x2 registers, fixed at compile time.)  The
+ * choices are cached for the life of the process, keyed by the device's SM
+ * count, k, and every dictionary's and query set's length histogram, scoring
+ * and flags: a batch of the same shape is not timed again (tune_cached = 1). */
+#define NW_BATCH_AUTOTUNE 0x10u
 
 typedef struct {
     uint32_t ndicts;
@@ -282,6 +290,8 @@ typedef struct {
     uint32_t words_per_task[NW_MAX_WORD_LEN + 1]; /* chosen A words per task by longer length (0: none) */
     uint32_t query_words;                       /* words of all query sets */
     uint64_t query_pairs, query_cells;          /* the part of pairs / cells from query sets */
+    uint32_t blocks_per_sm[NW_MAX_WORD_LEN + 1]; /* chosen resident blocks per SM by longer length (0: as many as fit) */
+    uint32_t tune_cached;                       /* 1: the tile shapes came from the autotuner's cache */
 } nw_batch_info;
 
 /* flags: NW_DEVICE_PTRS (the dictionaries' and query sets' buffers are

@@ -13,6 +13,8 @@
 // candidates on the batch.  The whole reduction is captured once into a CUDA
 // graph and replayed by nw_batch_run / nw_batch_run_queries.
 #include <chrono>
+#include <map>
+#include <mutex>
 
 #include "nw_host.h"
 
@@ -24,6 +26,8 @@ struct nw_batch {
   std::vector<uint8_t> self;      // 1: the dictionary's own lists are computed
   uint32_t k = 0;
   uint32_t ta_by_lb[kBuckets] = {0};
+  uint32_t bps_by_lb[kBuckets] = {0};  // resident blocks per SM at most (0: as many as fit)
+  bool tune_cached = false;
   Plan plan;
   std::vector<size_t> list_off;   // first list of each dictionary's own lists in the combined arrays
   std::vector<size_t> qlist_off;  // first list of each query set in the combined arrays
@@ -65,11 +69,12 @@ DictPlans dict_plans(const nw_batch* B, uint32_t ta) {
 // The segments of every dictionary and query set whose longer length is LB,
 // taken from plans made with A chunks of `ta` words, appended as one launch
 // (task0 rebased, terms tagged).
-void append_launch(const nw_batch* B, const DictPlans& plans, int LB, uint32_t ta, Plan& out) {
+void append_launch(const nw_batch* B, const DictPlans& plans, int LB, uint32_t ta, Plan& out, uint32_t bps = 0) {
   LaunchPlan lp;
   lp.LB = LB;
   lp.role = 0;
   lp.ta = ta;
+  lp.bps = bps;
   lp.seg_first = (uint32_t)out.segs.size();
   uint64_t task = 0;
   for (size_t d = 0; d < B->dicts.size(); ++d) {
@@ -165,9 +170,67 @@ nw_status issue_finalize(nw_batch* B) {
   return NW_OK;
 }
 
-// Times each launch length with each A-chunk candidate and keeps the fastest.
+// The autotuner's choices, kept for the life of the process and keyed by the
+// batch's shape (tune_key): a batch of the same shape is not timed again.
+struct TunedShape {
+  uint32_t ta[kBuckets];
+  uint32_t bps[kBuckets];
+};
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::map<uint64_t, TunedShape>& tune_cache() {
+  static std::map<uint64_t, TunedShape> m;
+  return m;
+}
+
+// FNV-1a over the device's SM count, k, and every dictionary's and query
+// set's length histogram, scoring and flags: what the launches' work and
+// their timing follow.
+uint64_t tune_key(const nw_batch* B) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](uint64_t v) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (v >> (8 * i)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((uint64_t)B->ctx->sm_count);
+  mix(B->k);
+  mix(B->dicts.size());
+  for (size_t d = 0; d < B->dicts.size(); ++d) {
+    const nw_dict* D = B->dicts[d];
+    mix(B->self[d]);
+    mix(D->alphabet);
+    mix((uint32_t)D->sc.match);
+    mix((uint32_t)D->sc.mismatch);
+    mix((uint32_t)D->sc.gap);
+    mix(D->subst ? 1u : 0u);
+    for (int L = 0; L < kBuckets; ++L) mix(D->ws.bk.count[L]);
+    for (int L = 0; L < kBuckets; ++L) mix(B->qsets[d].bk.count[L]);
+  }
+  return h;
+}
+
+constexpr uint32_t kBpsCandidates[] = {3, 2};
+
+// Per launch length: the fastest A-chunk candidate, then the fastest cap on
+// resident blocks per SM at that chunk (whole launches timed on the batch).
 nw_status autotune(nw_batch* B) {
   nw_ctx* c = B->ctx;
+  const uint64_t key = tune_key(B);
+  {
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {
+      std::copy(it->second.ta, it->second.ta + kBuckets, B->ta_by_lb);
+      std::copy(it->second.bps, it->second.bps + kBuckets, B->bps_by_lb);
+      B->tune_cached = true;
+      B->tune_ms = 0;
+      return NW_OK;
+    }
+  }
   const auto t0 = std::chrono::steady_clock::now();
   cudaEvent_t e0, e1;
   NW_CK(cudaEventCreate(&e0));
@@ -176,36 +239,57 @@ nw_status autotune(nw_batch* B) {
     cudaEvent_t a, b;
     ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
   } evfree{e0, e1};
+  constexpr size_t kNta = sizeof(kTaCandidates) / sizeof(kTaCandidates[0]);
   std::vector<DictPlans> plans;
   for (uint32_t ta : kTaCandidates) plans.push_back(dict_plans(B, ta));
+  // one timed launch of length LB with chunk candidate ci and cap bps; false if the length has no pairs
+  auto time_launch = [&](int LB, size_t ci, uint32_t bps, bool& warm, float& ms) -> nw_status {
+    Plan p;
+    append_launch(B, plans[ci], LB, kTaCandidates[ci], p, bps);
+    ms = -1.f;
+    if (p.launches.empty()) return NW_OK;
+    NW_TRY(upload_plan(B, p));
+    if (!warm) {  // the kernel's first launch pays its set-up; keep it out of the timings
+      NW_TRY(issue_lists(B, p));
+      warm = true;
+    }
+    NW_CK(cudaEventRecord(e0, B->stream));
+    NW_TRY(issue_lists(B, p));
+    NW_CK(cudaEventRecord(e1, B->stream));
+    NW_CK(cudaEventSynchronize(e1));
+    NW_CK(cudaEventElapsedTime(&ms, e0, e1));
+    return NW_OK;
+  };
   for (int LB = 0; LB < kBuckets; ++LB) {
     float best = 0;
-    uint32_t best_ta = 0;
+    size_t best_ci = kNta;
     bool warm = false;
-    for (size_t ci = 0; ci < sizeof(kTaCandidates) / sizeof(kTaCandidates[0]); ++ci) {
-      const uint32_t ta = kTaCandidates[ci];
-      Plan p;
-      append_launch(B, plans[ci], LB, ta, p);
-      if (p.launches.empty()) break;
-      NW_TRY(upload_plan(B, p));
-      if (!warm) {  // the kernel's first launch pays its set-up; keep it out of the timings
-        NW_TRY(issue_lists(B, p));
-        warm = true;
-      }
-      NW_CK(cudaEventRecord(e0, B->stream));
-      NW_TRY(issue_lists(B, p));
-      NW_CK(cudaEventRecord(e1, B->stream));
-      NW_CK(cudaEventSynchronize(e1));
-      float ms = 0;
-      NW_CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (best_ta == 0 || ms < best) {
+    for (size_t ci = 0; ci < kNta; ++ci) {
+      float ms;
+      NW_TRY(time_launch(LB, ci, 0, warm, ms));
+      if (ms < 0) break;
+      if (best_ci == kNta || ms < best) {
         best = ms;
-        best_ta = ta;
+        best_ci = ci;
       }
     }
-    if (best_ta) B->ta_by_lb[LB] = best_ta;  // lengths without pairs keep the default
+    if (best_ci == kNta) continue;  // lengths without pairs keep the defaults
+    B->ta_by_lb[LB] = kTaCandidates[best_ci];
+    for (uint32_t bps : kBpsCandidates) {
+      float ms;
+      NW_TRY(time_launch(LB, best_ci, bps, warm, ms));
+      if (ms >= 0 && ms < best) {
+        best = ms;
+        B->bps_by_lb[LB] = bps;
+      }
+    }
   }
   B->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  TunedShape t;
+  std::copy(B->ta_by_lb, B->ta_by_lb + kBuckets, t.ta);
+  std::copy(B->bps_by_lb, B->bps_by_lb + kBuckets, t.bps);
+  std::lock_guard<std::mutex> lk(tune_mutex());
+  tune_cache()[key] = t;
   return NW_OK;
 }
 
@@ -316,13 +400,13 @@ nw_status create_impl(nw_batch* B, const nw_batch_dict* dicts, uint32_t ndicts, 
     for (uint32_t ta : tas) plans.push_back(dict_plans(B, ta));
     for (int LB = 0; LB < kBuckets; ++LB) {
       const size_t ci = std::find(tas.begin(), tas.end(), B->ta_by_lb[LB]) - tas.begin();
-      append_launch(B, plans[ci], LB, B->ta_by_lb[LB], B->plan);
+      append_launch(B, plans[ci], LB, B->ta_by_lb[LB], B->plan, B->bps_by_lb[LB]);
     }
   }
   for (int LB = 0; LB < kBuckets; ++LB) {
     bool present = false;
     for (const LaunchPlan& lp : B->plan.launches) present |= lp.LB == LB;
-    if (!present) B->ta_by_lb[LB] = 0;
+    if (!present) B->ta_by_lb[LB] = B->bps_by_lb[LB] = 0;
   }
   NW_TRY(upload_plan(B, B->plan));
   // one uncaptured run sets the kernels' shared-memory attributes
@@ -434,6 +518,8 @@ nw_status nw_batch_info_get(const nw_batch* B, nw_batch_info* out) {
   i.cells = B->plan.cells;
   i.tune_ms = B->tune_ms;
   for (int L = 0; L < kBuckets; ++L) i.words_per_task[L] = B->ta_by_lb[L];
+  for (int L = 0; L < kBuckets; ++L) i.blocks_per_sm[L] = B->bps_by_lb[L];
+  i.tune_cached = B->tune_cached ? 1u : 0u;
   i.query_words = B->query_words;
   i.query_pairs = B->query_pairs;
   i.query_cells = B->query_cells;

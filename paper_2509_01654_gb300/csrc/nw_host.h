@@ -50,6 +50,7 @@ struct LaunchPlan {
   int LB = 0;
   int role = 0;  // 0: A and B from one set; 1: A = queries, B = dictionary; 2: A = dictionary, B = queries
   uint32_t ta = 0;  // A words per task of this launch (0: the launch parameters' TA)
+  uint32_t bps = 0; // resident blocks per SM at most (0: as many as fit)
   uint32_t seg_first = 0, nsegs = 0;
   uint64_t ntasks = 0;
   uint64_t pairs = 0, cells = 0;
@@ -661,6 +662,7 @@ nw_status run_plan(nw_ctx* c, cudaStream_t stream, const Plan& plan, const Seg* 
     int occ = 0;
     NW_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, smem));
     if (occ < 1) occ = 1;
+    if (lp.bps && occ > (int)lp.bps) occ = (int)lp.bps;
     uint64_t grid = (uint64_t)c->sm_count * occ;
     grid = std::min<uint64_t>(grid, cdiv(hi - lo, kWarpsPerBlock));
     void* args[] = {&P};

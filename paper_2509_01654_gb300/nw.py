@@ -116,7 +116,8 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("ndicts", ctypes.c_uint32), ("launches", ctypes.c_uint32), ("pairs", ctypes.c_uint64),
                 ("cells", ctypes.c_uint64), ("tune_ms", ctypes.c_double),
                 ("words_per_task", ctypes.c_uint32 * (MAX_WORD_LEN + 1)), ("query_words", ctypes.c_uint32),
-                ("query_pairs", ctypes.c_uint64), ("query_cells", ctypes.c_uint64)]
+                ("query_pairs", ctypes.c_uint64), ("query_cells", ctypes.c_uint64),
+                ("blocks_per_sm", ctypes.c_uint32 * (MAX_WORD_LEN + 1)), ("tune_cached", ctypes.c_uint32)]
 
 
 _lib = None
@@ -584,8 +585,9 @@ class Batch:
     def info(self) -> dict:
         i = BatchInfo()
         _check(self.ctx.handle, load_library().nw_batch_info_get(self.handle, ctypes.byref(i)))
-        out = {f: getattr(i, f) for f, _ in BatchInfo._fields_ if f != "words_per_task"}
+        out = {f: getattr(i, f) for f, _ in BatchInfo._fields_ if f not in ("words_per_task", "blocks_per_sm")}
         out["words_per_task"] = list(i.words_per_task)
+        out["blocks_per_sm"] = list(i.blocks_per_sm)
         return out
 
     def _host_lists(self, sizes):

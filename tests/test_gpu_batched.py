@@ -56,6 +56,26 @@ def test_batch_equals_each_dictionary_alone(ctx, dicts, oracle_mod):
     batch.free()
 
 
+def test_autotuner_choices_are_cached_per_batch_shape(ctx, dicts):
+    """A second batch of the same shape reuses the first one's tile shapes
+    (chunk sizes and blocks per SM) without timing, and gives the same lists;
+    a batch of another shape is tuned afresh."""
+    entries = [(d.words.codes, d.words.offsets, d.words.alphabet, d.scoring) for d in dicts[:5]]
+    b1 = nw.Batch(ctx, entries, k=K)
+    i1 = b1.info()
+    b2 = nw.Batch(ctx, entries, k=K)
+    i2 = b2.info()
+    assert i2["tune_cached"] == 1 and i2["tune_ms"] == 0
+    assert i2["words_per_task"] == i1["words_per_task"] and i2["blocks_per_sm"] == i1["blocks_per_sm"]
+    assert all(b in (0, 2, 3) for b in i1["blocks_per_sm"])
+    for (a1, s1), (a2, s2) in zip(b1.run(), b2.run()):
+        assert np.array_equal(a1, a2) and np.array_equal(s1, s2)
+    b3 = nw.Batch(ctx, entries[:4], k=K)
+    assert b3.info()["tune_cached"] == 0
+    for b in (b1, b2, b3):
+        b.free()
+
+
 def test_batch_device_outputs_and_fixed_tiles(ctx, dicts):
     import torch
     sub = dicts[:4]
