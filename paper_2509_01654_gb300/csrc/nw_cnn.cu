@@ -8,6 +8,7 @@
 
 #include "nw_cnn.h"
 #include "nw_internal.cuh"
+#include "nw_tc.cuh"
 
 namespace nw {
 namespace cnn {
@@ -253,6 +254,159 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(AV A, BV B, int M, int N, i
     }
 }
 
+// ---- the same products on the fifth-generation tensor cores, for operands
+// that are both contiguous along K (the forward convolutions and the linear
+// layer).  One CTA of 256 threads computes a 128 x 128 output tile into a
+// 128-column tensor-memory accumulator.  K advances 32 at a time through two
+// shared stages in the canonical K-major layout (8-row x 16-byte core
+// matrices, no swizzle): each thread loads its four 16-byte vectors of each
+// operand for the next stage while the tensor cores multiply the current
+// one, and stores them (rounded to bf16) once the products that last read
+// that stage have completed, which its mbarrier tells.  Thread 0 issues the
+// two K = 16 products of a stage and commits them to the stage's barrier.
+// Epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31
+// (one output row per thread) and columns 64 (w / 4) .. + 63 with
+// tcgen05.ld.  Every wait is bounded: on a timeout the CTA sets kErrWait,
+// waits (bounded) for the products it issued, frees its tensor memory and
+// writes nothing.
+constexpr int kTcK = 32;
+constexpr int kTcTileBytes = BM * kTcK * 2;  // one operand's stage: 8 KiB
+constexpr uint32_t kTcIdesc = tc::idesc_bf16(BM, BN);
+constexpr long long kTcWaitCycles = 2000000000ll;  // about a second
+
+template <class AV, class BV>
+__global__ void __launch_bounds__(NT, 3) gemm_tc_kernel(AV A, BV B, int M, int N, int K, float* C, int ldc, Epi e,
+                                                     const int* Mlim) {
+  static_assert(AV::kColFast && !BV::kColFast, "both operands contiguous along K");
+  __shared__ __align__(1024) unsigned char sm[2][2][kTcTileBytes];  // [stage][A, B]
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ uint32_t tmem_base;
+  if (Mlim) M = min(M, *Mlim);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  if (m0 >= M) return;  // block-uniform, before any barrier or allocation
+  const uint32_t bar0 = tc::smem_u32(&bars[0]), bar1 = tc::smem_u32(&bars[1]);
+  if (tid == 0) {
+    tc::mbar_init(bar0, 1);
+    tc::mbar_init(bar1, 1);
+    tc::mbar_init_fence();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_base), BN);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = tmem_base;
+
+  float4 ra[4], rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int x = tid + q * NT, o = x >> 3, k = (x & 7) * 4;
+      ra[q] = (m0 + o < M && k0 + k < K) ? A.vec4(m0 + o, k0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      rb[q] = (n0 + o < N && k0 + k < K) ? B.vec4(k0 + k, n0 + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int x = tid + q * NT, o = x >> 3, k = (x & 7) * 4;
+      const uint32_t off = tc::kmajor_offset((uint32_t)o, (uint32_t)k, kTcK);
+      *reinterpret_cast<uint2*>(&sm[buf][0][off]) = pack4_bf16(ra[q]);
+      *reinterpret_cast<uint2*>(&sm[buf][1][off]) = pack4_bf16(rb[q]);
+    }
+  };
+  const int nk = (K + kTcK - 1) / kTcK;
+  uint32_t parity = 0u;  // bit b: parity of stage b's barrier's next completion
+  int last = -1;         // stage of the last committed products
+  bool ok = true;
+  load(0);
+  for (int kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    if (kt >= 2) {  // the products of stage kt - 2 read this buffer
+      const bool got = tc::mbar_wait(buf ? bar1 : bar0, (parity >> buf) & 1u, kTcWaitCycles);
+      parity ^= 1u << buf;
+      if (!__syncthreads_and(got)) {
+        ok = false;
+        break;
+      }
+    }
+    stage(buf);
+    tc::fence_proxy_async();  // the stores, for the tensor cores
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t a = tc::smem_u32(&sm[buf][0][0]), b = tc::smem_u32(&sm[buf][1][0]);
+#pragma unroll
+      for (uint32_t ks = 0; ks < (uint32_t)(kTcK / 16); ++ks)
+        tc::mma(tbase, tc::smem_desc(a + 256u * ks, 128u, 16u * kTcK, 0u),
+                tc::smem_desc(b + 256u * ks, 128u, 16u * kTcK, 0u), kTcIdesc, (kt > 0 || ks > 0) ? 1u : 0u);
+      tc::commit(buf ? bar1 : bar0);
+    }
+    last = buf;
+    if (kt + 1 < nk) load((kt + 1) * kTcK);  // in flight while the products run
+  }
+  // every product issued has completed before the accumulator is read or freed
+  // (the last commit covers all earlier products of thread 0)
+  if (last >= 0) {
+    const bool got = tc::mbar_wait(last ? bar1 : bar0, (parity >> last) & 1u, kTcWaitCycles);
+    ok = __syncthreads_and(got && ok) != 0;
+  }
+  tc::fence_after();
+  if (ok) {
+    const int lq = warp & 3, half = warp >> 2;
+    const int m = m0 + lq * 32 + lane;
+    const uint32_t taddr = tbase + ((uint32_t)(lq * 32) << 16) + (uint32_t)(half * 64);
+#pragma unroll
+    for (int c = 0; c < 64; c += 32) {
+      uint32_t v[32];
+      tc::tmem_ld32(taddr + (uint32_t)c, v);
+      tc::tmem_wait(v);
+      if (m < M) {
+        const int nb = n0 + half * 64 + c;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const int n = nb + j;
+          if (n >= N) break;
+          float4 r = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                                 __uint_as_float(v[j + 3]));
+          if (e.bias) {
+            r.x += __ldg(e.bias + n);
+            r.y += __ldg(e.bias + min(n + 1, N - 1));
+            r.z += __ldg(e.bias + min(n + 2, N - 1));
+            r.w += __ldg(e.bias + min(n + 3, N - 1));
+          }
+          if (e.relu) {
+            r.x = fmaxf(r.x, 0.f);
+            r.y = fmaxf(r.y, 0.f);
+            r.z = fmaxf(r.z, 0.f);
+            r.w = fmaxf(r.w, 0.f);
+          }
+          if (e.gate) {
+            const float* gp = e.gate + (size_t)m * ldc;
+            if (!(__ldg(gp + n) > 0.f)) r.x = 0.f;
+            if (!(__ldg(gp + min(n + 1, N - 1)) > 0.f)) r.y = 0.f;
+            if (!(__ldg(gp + min(n + 2, N - 1)) > 0.f)) r.z = 0.f;
+            if (!(__ldg(gp + min(n + 3, N - 1)) > 0.f)) r.w = 0.f;
+          }
+          float* dst = C + (size_t)m * ldc + n;
+          if (n + 4 <= N) {
+            *reinterpret_cast<float4*>(dst) = r;
+          } else {  // N is a multiple of four: not reached, kept for safety
+            dst[0] = r.x;
+            if (n + 1 < N) dst[1] = r.y;
+            if (n + 2 < N) dst[2] = r.z;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    if (e.err) atomicOr(e.err, kErrWait);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, BN);
+}
+
 template <class AV, class BV>
 cudaError_t run_gemm(AV A, BV B, int M, int N, int K, float* C, int ldc, const Epi& e, int splits, cudaStream_t s,
                      const int* Mlim = nullptr, const int* Klim = nullptr) {
@@ -268,6 +422,13 @@ cudaError_t run_gemm(AV A, BV B, int M, int N, int K, float* C, int ldc, const E
     gz = (K + kchunk - 1) / kchunk;
   }
   if (K <= 0) gz = 1;
+  if constexpr (AV::kColFast && !BV::kColFast) {
+    // both operands contiguous along K: the tcgen05 kernel, when nothing is split or accumulated
+    if (gz == 1 && !e.atomic && !Klim && K > 0 && ldc % 4 == 0) {
+      gemm_tc_kernel<AV, BV><<<dim3(gx, gy), NT, 0, s>>>(A, B, M, N, K, C, ldc, e, Mlim);
+      return cudaGetLastError();
+    }
+  }
   gemm_kernel<AV, BV><<<dim3(gx, gy, gz), NT, 0, s>>>(A, B, M, N, K, kchunk, C, ldc, e, Mlim, Klim);
   return cudaGetLastError();
 }

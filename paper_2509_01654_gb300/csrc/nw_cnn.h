@@ -64,6 +64,7 @@ struct Epi {
   bool relu = false;
   const float* gate = nullptr;   // same layout as C
   bool atomic = false;
+  uint32_t* err = nullptr;       // receives kErrWait if a tensor-core pipeline wait runs out (may be null)
 };
 
 // The network's matrix products: bf16 tensor-core tiles, operands rounded

@@ -187,6 +187,7 @@ nw_status forward(nw_model* M, const WordSet& ws, uint32_t shift, int Bw, int Tm
                         err_ptr(M), M->alphabet, s));
   cnn::Epi e;
   e.relu = true;
+  e.err = err_ptr(M);
   e.bias = W + L.b1;
   NW_CK(cnn::conv_fwd(fptr(M->X0), cnn::kEmb, W + L.W1, cnn::kCh, pk, fptr(M->Y1), e, s));
   e.bias = W + L.b2;
@@ -196,6 +197,7 @@ nw_status forward(nw_model* M, const WordSet& ws, uint32_t shift, int Bw, int Tm
   NW_CK(cnn::mean_pool(fptr(M->Y3), pk, fptr(M->P), s));
   cnn::Epi el;
   el.bias = W + L.bl;
+  el.err = err_ptr(M);
   NW_CK(cnn::lin_fwd(fptr(M->P), cnn::kCh, W + L.Wl, cnn::kOut, Bw, fptr(M->E), el, s));
   return NW_OK;
 }
