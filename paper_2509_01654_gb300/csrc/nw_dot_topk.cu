@@ -779,6 +779,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
       }
       if (pending) atomicOr(err, kErrWait);
     }
+    sHi[r] = amax;  // for the final pass
     sFin[r] = act | ((uint32_t)cnt << 1);
     __threadfence_block();
     __syncwarp();
@@ -906,15 +907,25 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
     if (total <= (int)C) {
       kept = warp_gather_ge(b0, total, 1ull, sort, lane);
     } else {
+      // with a threshold, every key of the C best is at or above it and at
+      // most the row's value bound: the histogram covers that range only
       int lo, hi;
-      warp_value_range(b0, total, lane, lo, hi);
+      const float thr_f = sThr[r], hi_f = sHi[r];
+      if (thr_f > -FLT_MAX && hi_f >= thr_f) {
+        lo = (int)thr_f;
+        hi = (int)hi_f;
+      } else {
+        warp_value_range(b0, total, lane, lo, hi);
+      }
       const unsigned span = (unsigned)(hi - lo);
       const int sh = span < 256u ? 0 : 24 - __clz((int)span);
-      warp_value_hist(b0, total, lo, sh, hist, lane);
-      int bin;
-      unsigned above;
-      hist_find_desc(hist, C, lane, bin, above);
-      const unsigned cand = above + hist[bin];
+      const unsigned counted = warp_value_hist_ge(b0, total, lo, sh, hist, lane);
+      int bin = 0;
+      unsigned above = 0u, cand = 0xffffffffu;
+      if (counted >= C) {
+        hist_find_desc(hist, C, lane, bin, above);
+        cand = above + hist[bin];
+      }
       __syncwarp();
       if (cand <= (unsigned)kFinalSort) {
         kept = warp_keep_value_ge_to(b0, total, lo + (bin << sh), sort, lane);
