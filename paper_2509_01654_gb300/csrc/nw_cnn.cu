@@ -27,6 +27,9 @@ struct Dense {  // row-major
   __device__ __forceinline__ float4 vec4(int r, int c) const {
     return __ldg(reinterpret_cast<const float4*>(p + (size_t)r * ld + c));
   }
+  // the same, with the row's table entry read ahead (none for a dense view)
+  __device__ __forceinline__ int row_info(int) const { return 0; }
+  __device__ __forceinline__ float4 vec4r(int r, int c, int) const { return vec4(r, c); }
 };
 
 struct DenseT {  // transpose of a row-major matrix
@@ -45,9 +48,11 @@ struct Im2col {
   const int* rinfo;
   int lg;  // log2 Ci
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ float4 vec4(int t, int k) const {
+  __device__ __forceinline__ float4 vec4(int t, int k) const { return vec4r(t, k, row_info(t)); }
+  // the same with row t's table entry given (a kernel that keeps its rows' entries at hand)
+  __device__ __forceinline__ int row_info(int t) const { return __ldg(rinfo + t); }
+  __device__ __forceinline__ float4 vec4r(int t, int k, int info) const {
     const int tap = k >> lg;
-    const int info = __ldg(rinfo + t);
     const int pos = (info >> 8) + tap - 1;
     if (pos < 0 || pos >= (info & 255)) return make_float4(0.f, 0.f, 0.f, 0.f);
     return __ldg(reinterpret_cast<const float4*>(X + ((size_t)(t + tap - 1) << lg) + (k & ((1 << lg) - 1))));
@@ -275,12 +280,13 @@ constexpr uint32_t kTcIdesc = tc::idesc_bf16(BM, BN);
 constexpr long long kTcWaitCycles = 2000000000ll;  // about a second
 
 template <class AV, class BV>
-__global__ void __launch_bounds__(NT, 3) gemm_tc_kernel(AV A, BV B, int M, int N, int K, float* C, int ldc, Epi e,
+__global__ void __launch_bounds__(NT, 4) gemm_tc_kernel(AV A, BV B, int M, int N, int K, float* C, int ldc, Epi e,
                                                      const int* Mlim) {
   static_assert(AV::kColFast && !BV::kColFast, "both operands contiguous along K");
   __shared__ __align__(1024) unsigned char sm[2][2][kTcTileBytes];  // [stage][A, B]
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ uint32_t tmem_base;
+  __shared__ int rows_info[BM];  // the A view's table entries of the tile's rows, read once
   if (Mlim) M = min(M, *Mlim);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -292,17 +298,21 @@ __global__ void __launch_bounds__(NT, 3) gemm_tc_kernel(AV A, BV B, int M, int N
     tc::mbar_init_fence();
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(&tmem_base), BN);
+  if (tid < BM) rows_info[tid] = m0 + tid < M ? A.row_info(m0 + tid) : 0;
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = tmem_base;
+  int info[4];  // this thread's four A rows (fixed for the whole K loop)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) info[q] = rows_info[(tid + q * NT) >> 3];
 
   float4 ra[4], rb[4];
   auto load = [&](int k0) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int x = tid + q * NT, o = x >> 3, k = (x & 7) * 4;
-      ra[q] = (m0 + o < M && k0 + k < K) ? A.vec4(m0 + o, k0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      ra[q] = (m0 + o < M && k0 + k < K) ? A.vec4r(m0 + o, k0 + k, info[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
       rb[q] = (n0 + o < N && k0 + k < K) ? B.vec4(k0 + k, n0 + o) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
