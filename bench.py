@@ -578,6 +578,16 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
                                          "recall_at_10_tie_aware": dict_order["recall_at_10_tie_aware"]}
     model.set_exact_length(args.exact_length)
     res = {str(C): evaluate(model, C, max(2, args.steps)) for C in (256, 384, 512)}
+    # the same path trained on the configuration's budget of 2e7 pairs
+    budget_pairs = 20_000_000
+    budget_steps = -(-budget_pairs // train_cfg["batch_pairs"])
+    small = nw.Model(ctx, 40, seed=1)
+    t1 = time.perf_counter()
+    small.train(d, steps=budget_steps, nbr=ex_i, **train_cfg)
+    budget_train_s = time.perf_counter() - t1
+    small.set_exact_length(args.exact_length)
+    res_budget = {str(C): evaluate(small, C, max(2, args.steps)) for C in (256, 512)}
+    small.free()
     model.set_exact_length(args.query_exact_length)
     queries = proposal_queries(args, model, d, k, recall_vs_exact)
     # candidates without a network: the C words nearest in length order (stable by index)
@@ -594,12 +604,14 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
     model.free()
     d.free()
     # the metric's second half: top-10 graph time at >= 0.99 (tie-aware) recall
-    at99 = [(int(C), r) for C, r in res.items() if r["recall_at_10_tie_aware"] >= 0.99]
-    graph99 = None
-    if at99:
+    def graph_at_99(results):
+        at99 = [(int(C), r) for C, r in results.items() if r["recall_at_10_tie_aware"] >= 0.99]
+        if not at99:
+            return None
         C99, r99 = min(at99)
-        graph99 = {"C": C99, "total_ms": r99["ms"]["total_ms"], "recall_at_10_tie_aware": r99["recall_at_10_tie_aware"],
-                   "speedup_vs_exhaustive": r99["speedup_vs_exhaustive"]}
+        return {"C": C99, "total_ms": r99["ms"]["total_ms"], "recall_at_10_tie_aware": r99["recall_at_10_tie_aware"],
+                "speedup_vs_exhaustive": r99["speedup_vs_exhaustive"]}
+    graph99 = graph_at_99(res)
     return {
         "graph_time_at_recall_0.99": graph99,
         "workload": (f"{n:,} words of the exhaustive workload; approximate top-{k} by the learned proposal "
@@ -614,6 +626,10 @@ def proposal_leg(args, ctx, nw, w, codes_d, offs_d, idx_d, score_d, exhaustive_m
                   "loss_last_100": round(float(np.mean(losses[-100:])), 5), **train_cfg},
         "exhaustive_ms": round(exhaustive_ms, 3),
         "by_candidates": res,
+        "config_training_budget": {
+            "pairs": budget_steps * train_cfg["batch_pairs"], "steps": budget_steps,
+            "seconds": round(budget_train_s, 2), "by_candidates": res_budget,
+            "graph_time_at_recall_0.99": graph_at_99(res_budget)},
         # the candidate kernel: 2 n^2 d FLOP of bf16 products (d = 64) per launch
         "candidates_roofline": {str(C): tensor_roofline(2.0 * n * n * 64, r["ms"]["candidates_ms"])
                                 for C, r in res.items()},
