@@ -13,10 +13,11 @@
 // dot_topk_kernel: a CTA owns two blocks of 128 rows (each block fills the
 // 128 lanes of tensor memory) and sweeps column tiles of 128.  Fourteen warps
 // with fixed roles:
-//   * a producer thread streams each tile (128 rows of 128 B, already in the
-//     128-byte-swizzled K-major layout, plus 4 KiB of bias digits) into a
-//     four-stage shared-memory ring with cp.async.bulk, counted on mbarriers;
-//     every tile feeds both row blocks;
+//   * a producer thread streams each tile (128 rows of 128 B by a 2-D
+//     tensor-map copy, cp.async.bulk.tensor, whose 128-byte swizzle lays them
+//     out as the K-major operand, plus 4 KiB of bias digits by cp.async.bulk)
+//     into a four-stage shared-memory ring, counted on mbarriers; the CTA's
+//     own 256 rows arrive once the same way; every tile feeds both row blocks;
 //   * an MMA thread issues, per tile and row block, four tcgen05.mma
 //     (M = 128, N = 128, K = 16, bf16 -> f32) over the 64 features and a fifth
 //     over the bias digits into one of the block's two accumulators, then
@@ -41,8 +42,10 @@
 // buffers exactly and sorts them.  Every wait is bounded and sets kErrWait
 // when it runs out; the CTA then stops, waits (bounded) for the copies and
 // products it issued, frees its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <cstring>
 #include <cuda_runtime.h>
 #include <float.h>
 #include <stdint.h>
@@ -361,16 +364,18 @@ __device__ __forceinline__ int pow2_at_least(int x) {
 }
 
 
-// One launch: rows QA[0, nA) against columns QB[0, nB) (both bf16, zero-padded
-// to whole 256-row tiles, 16-byte chunks of row r permuted by r & 7: the
-// 128-byte-swizzled K-major layout); ext holds the columns' bias digits in the
-// K = 16 layout of ext_offset.  self: rows and columns are one set, and row i
+// One launch: rows QA[0, nA) against columns QB[0, nB) (both bf16 rows of
+// 128 bytes, zero-padded to whole 256-row tiles), loaded through the tensor
+// maps tmA (boxes of the CTA's 256 rows) and tmB (boxes of a 128-column
+// tile), whose 128-byte swizzle lays them out as the products' K-major
+// operands; ext holds the columns' bias digits in the K = 16 layout of
+// ext_offset.  self: rows and columns are one set, and row i
 // skips column i.  With splits > 1, CTA (x, y) sweeps only the column tiles
 // [y * tps, (y + 1) * tps) and writes its rows' C best keys, sorted, to part
 // (a merge kernel then takes each row's C best of its splits' lists).
 struct DotArgs {
-  const __nv_bfloat16* QA;
-  const __nv_bfloat16* QB;
+  CUtensorMap tmA;  // QA as [rows][64] bf16, boxes of kCtaRows rows, 128-byte swizzle
+  CUtensorMap tmB;  // QB likewise, boxes of kTileN rows
   const unsigned char* ext;
   uint32_t nA, nB, C;
   uint32_t splits, tps;
@@ -470,7 +475,7 @@ __device__ int compact_buffer(uint64_t* keys, int c, const uint64_t* other, int 
 }
 
 template <bool kSplit, bool kSelf>
-__global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) {
+__global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const __grid_constant__ DotArgs P) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -573,8 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
     // ---- producer: the CTA's rows once, then the column tiles into the ring
     if (lane == 0) {
       mbar_expect_tx(a_bar, kBlocksPerCta * kAMainBytes);
-      bulk_g2s(smem_u32(smem + kOffAMain), reinterpret_cast<const unsigned char*>(P.QA) + (size_t)row0 * kRowBytes,
-               kBlocksPerCta * kAMainBytes, a_bar);
+      tc::tma_load_2d(smem_u32(smem + kOffAMain), &P.tmA, 0, (int)row0, a_bar);
       uint32_t u = 0;
       for (; u < ntiles; ++u) {
         const uint32_t s = u % kStages;
@@ -587,8 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1) dot_topk_kernel(const DotArgs P) 
         const uint32_t t = tile_of(u);
         unsigned char* st = smem + kOffStages + s * kStageBytes;
         mbar_expect_tx(full_bar(s), kStageBytes);
-        bulk_g2s(smem_u32(st), reinterpret_cast<const unsigned char*>(P.QB) + (size_t)t * kMainBytes, kMainBytes,
-                 full_bar(s));
+        tc::tma_load_2d(smem_u32(st), &P.tmB, 0, (int)(t * (uint32_t)kTileN), full_bar(s));
         bulk_g2s(smem_u32(st + kMainBytes), P.ext + (size_t)t * kExtBytes, kExtBytes, full_bar(s));
       }
       // every copy issued has landed before the CTA's shared memory is reused (bounded)
@@ -1001,12 +1004,10 @@ __global__ void absmax_kernel(const float* __restrict__ E, uint32_t n, unsigned 
   if ((threadIdx.x & 31) == 0) atomicMax(amax_bits, __float_as_uint(m));  // non-negative floats order as integers
 }
 
-// Element (r, c) of the bf16 rows the candidate kernel reads: rows padded
-// with zeros to a whole number of column tiles, and the 16-byte chunks of row
-// r permuted by r & 7, the shared-memory swizzle its tiles are copied into.
-__device__ __forceinline__ size_t swz_index(size_t r, int c) {
-  return r * kDim + (size_t)((((c >> 3) ^ (int)(r & 7)) << 3) | (c & 7));
-}
+// Element (r, c) of the bf16 rows the candidate kernel reads: row-major
+// rows of 64 values (128 bytes), padded with zeros to whole 256-row tiles.
+// The kernel's tensor-map loads apply the 128-byte shared-memory swizzle.
+__device__ __forceinline__ size_t qb_index(size_t r, int c) { return r * kDim + (size_t)c; }
 
 // one thread per (row, value) of the padded rows: the quantised values
 // (row-major int8, optional), their bf16 copy (optional) and the biases
@@ -1032,14 +1033,14 @@ __global__ void quantize_kernel(const float* __restrict__ E, uint32_t n, uint32_
     }
     if (q) q[x] = (int8_t)v;
   }
-  if (qb) qb[swz_index(r, c)] = __float2bfloat16_rn(v);
+  if (qb) qb[qb_index(r, c)] = __float2bfloat16_rn(v);
 }
 
 __global__ void widen_kernel(const int8_t* __restrict__ q, uint32_t n, uint32_t npad, __nv_bfloat16* qb) {
   const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= (size_t)npad * kDim) return;
   const size_t r = x / kDim;
-  qb[swz_index(r, (int)(x - r * kDim))] = __float2bfloat16_rn(r < n ? (float)q[x] : 0.f);
+  qb[qb_index(r, (int)(x - r * kDim))] = __float2bfloat16_rn(r < n ? (float)q[x] : 0.f);
 }
 
 // one thread per (column, K half) of the padded columns: the bias digits
@@ -1090,12 +1091,12 @@ __global__ void __launch_bounds__(256) moments_kernel(const __nv_bfloat16* __res
   const uint32_t rbeg = min(n, blockIdx.x * per), rend = min(n, rbeg + per);
   for (uint32_t r0 = rbeg; r0 < rend; r0 += kMomRows) {
     __syncthreads();
-    {  // kMomRows x 8 chunks of 16 bytes: chunk ch of row r holds values 8 (ch ^ (r & 7)) ..
+    {  // kMomRows x 8 chunks of 16 bytes: chunk ch of row r holds values 8 ch .. 8 ch + 7
       const uint32_t rr = (uint32_t)t >> 3, ch = (uint32_t)t & 7u, r = r0 + rr;
       uint4 u = make_uint4(0u, 0u, 0u, 0u);
       if (r < rend) u = __ldg(reinterpret_cast<const uint4*>(Qb + (size_t)r * kDim) + ch);
       const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
-      const int lc = (int)((ch ^ (r & 7u)) * 8u);
+      const int lc = (int)(ch * 8u);
 #pragma unroll
       for (int e = 0; e < 8; ++e) row[rr][lc + e] = (int)__bfloat162float(h[e]);
     }
@@ -1177,7 +1178,7 @@ __global__ void __launch_bounds__(256) project_kernel(const __nv_bfloat16* __res
 #pragma unroll
     for (int ch = 0; ch < 8; ++ch) {
       const uint4 u = __ldg(row + ch);
-      const int lc = (ch ^ (int)(r & 7u)) * 8;  // stored chunk ch holds values lc .. lc + 7
+      const int lc = ch * 8;  // chunk ch holds values lc .. lc + 7
       const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -1297,7 +1298,7 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __re
 }
 
 // one thread per (position, 16-byte chunk) of the padded rows: row perm[p]
-// moved to position p (its chunks re-permuted for p & 7), and its bias
+// moved to position p, and its bias
 __global__ void __launch_bounds__(256) order_gather_kernel(const __nv_bfloat16* __restrict__ Qb,
                                                            const int32_t* __restrict__ bias, uint32_t n,
                                                            uint32_t npad, const uint32_t* __restrict__ perm,
@@ -1308,10 +1309,10 @@ __global__ void __launch_bounds__(256) order_gather_kernel(const __nv_bfloat16* 
   uint4 v = make_uint4(0u, 0u, 0u, 0u);
   if (p < n) {
     const uint32_t r = perm[p];
-    v = __ldg(reinterpret_cast<const uint4*>(Qb + (size_t)r * kDim) + (ch ^ (r & 7u)));
+    v = __ldg(reinterpret_cast<const uint4*>(Qb + (size_t)r * kDim) + ch);
     if (ch == 0 && bp) bp[p] = bias ? bias[r] : 0;
   }
-  *(reinterpret_cast<uint4*>(Qp + (size_t)p * kDim) + (ch ^ (p & 7u))) = v;
+  *(reinterpret_cast<uint4*>(Qp + (size_t)p * kDim) + ch) = v;
 }
 
 
@@ -1352,6 +1353,39 @@ uint32_t* dot_topk_err_word(uint64_t* buf, uint32_t nA, uint32_t nB) {
                                      bias_pad(nB) * (size_t)kExtK * 2);
 }
 
+// the driver's tensor-map encoder, looked up once through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled_fn() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// `rows` bf16 rows of 64 values (128 bytes) at base, loaded in boxes of
+// box_rows rows with the 128-byte swizzle of the products' K-major operands
+static cudaError_t encode_rows(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_rows) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)kDim, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kRowBytes};
+  const cuuint32_t box[2] = {(cuuint32_t)kDim, box_rows};
+  const cuuint32_t elem[2] = {1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, elem,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloat16* QB, const int32_t* biasB,
                           uint32_t nB, uint32_t C, bool self, uint64_t* buf, uint32_t* idx, int32_t* val,
                           uint32_t* err, cudaStream_t s, DotDebug dbg, const uint32_t* col_ids,
@@ -1365,8 +1399,11 @@ cudaError_t dot_topk_rect(const __nv_bfloat16* QA, uint32_t nA, const __nv_bfloa
   const uint32_t tiles = (nB + kTileN - 1) / kTileN;
   unsigned char* ext = reinterpret_cast<unsigned char*>(buf) + ext_offset_bytes(nA, nB);
   DotArgs P;
-  P.QA = QA;
-  P.QB = QB;
+  std::memset(&P, 0, sizeof P);
+  // the row sets as allocated: zero-padded to whole 256-row tiles
+  e = encode_rows(&P.tmA, QA, bias_pad(nA), (uint32_t)kCtaRows);
+  if (e == cudaSuccess && nB) e = encode_rows(&P.tmB, QB, bias_pad(nB), (uint32_t)kTileN);
+  if (e != cudaSuccess) return e;
   P.ext = ext;
   P.nA = nA;
   P.nB = nB;

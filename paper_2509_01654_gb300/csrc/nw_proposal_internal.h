@@ -34,8 +34,7 @@ cudaError_t quantize(const float* E, uint32_t n, unsigned int* amax_bits, int8_t
                      int32_t* bias, float* scale, cudaStream_t s, bool given_scale = false);
 // int8 rows (row-major) -> the candidate kernel's bf16 rows
 cudaError_t widen(const int8_t* q, uint32_t n, __nv_bfloat16* qb, cudaStream_t s);
-// bf16 rows: zero-padded to whole 256-row tiles, 16-byte chunks of row r
-// permuted by r & 7
+// bf16 rows: row-major rows of 64 values, zero-padded to whole 256-row tiles
 size_t dot_topk_qb_bytes(uint32_t n);
 // scratch of a launch over nA rows, nB columns and C candidates (the err
 // word must follow the returned layout: use dot_topk_err_word)
