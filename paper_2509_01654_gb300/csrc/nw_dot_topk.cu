@@ -35,13 +35,17 @@
 //     C-th best of them and drops the handed keys below it, off the path of
 //     the tensor pipe.
 // A key is appended when its value is >= the threshold, so the column order
-// does not matter: a CTA starts at its own diagonal tile (similar words sit
-// near each other in the length-sorted order), and every key of the final top
-// C is always kept (each threshold is at most the C-th best value among keys
-// already seen).  A final pass selects each row's C best keys from its two
-// buffers exactly and sorts them.  Every wait is bounded and sets kErrWait
-// when it runs out; the CTA then stops, waits (bounded) for the copies and
-// products it issued, frees its tensor memory and returns.
+// does not change the result, only the time: every key of the final top C is
+// always kept (each threshold is at most the C-th best value among keys
+// already seen).  A CTA visits its column tiles outward from its own diagonal
+// tile; with the rows in a locality order (sweep_order: sorted by length and
+// principal components, keys carrying the original ids) a row's best columns
+// come early and its threshold rises sooner.  A final pass selects each row's
+// C best keys from its two buffers exactly (a value histogram, then the exact
+// select among the keys of the boundary bin) and sorts them when the caller
+// wants sorted lists.  Every wait is bounded and sets kErrWait when it runs
+// out; the CTA then stops, waits (bounded) for the copies and products it
+// issued, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <algorithm>
