@@ -315,28 +315,9 @@ __device__ void warp_value_range(const uint64_t* buf, int cnt, int lane, int& lo
   hi = __reduce_max_sync(0xffffffffu, mx);
 }
 
-// hist[b] = number of keys of buf[0, cnt) with (value - lo) >> sh == b; every
-// value lies in [lo, lo + (256 << sh)).
-__device__ void warp_value_hist(const uint64_t* buf, int cnt, int lo, int sh, unsigned* hist, int lane) {
-  for (int b = lane; b < 256; b += 32) hist[b] = 0u;
-  __syncwarp();
-  for (int i0 = 0; i0 < cnt; i0 += 32 * kBatch) {
-    uint64_t k[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int i = i0 + 32 * u + lane;
-      k[u] = i < cnt ? buf[i] : 0ull;
-    }
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u)
-      if (i0 + 32 * u + lane < cnt) atomicAdd(&hist[(uint32_t)(key_val(k[u]) - lo) >> sh], 1u);
-  }
-  __syncwarp();
-}
-
-// Like warp_value_hist, counting only the keys whose value is >= lo (the
-// others are skipped; a value past the last bin counts in it); returns how
-// many were counted.
+// hist[b] = number of keys of buf[0, cnt) whose value v is >= lo and has
+// (v - lo) >> sh == b (keys below lo are skipped; a value past the last bin
+// counts in it); returns how many were counted.
 __device__ unsigned warp_value_hist_ge(const uint64_t* buf, int cnt, int lo, int sh, unsigned* hist, int lane) {
   for (int b = lane; b < 256; b += 32) hist[b] = 0u;
   __syncwarp();
